@@ -1,0 +1,269 @@
+"""FP64 CPU oracle for the hot path (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package.  It wraps ``oracle.c`` (plain C, FP64, OpenMP) through ctypes and adds
+the per-stream bookkeeping of Sec. 3.1 (first frame ``O_1 = P_1``; later frames need
+``I_{t-1}, P_{t-1}, O_{t-1}``).  It shares no code with the CUDA library; the two read the
+same weight *file*, each with its own parser.
+
+Arrays are NumPy, planar (C, H, W).  Inputs are converted to float64.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import struct
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.c")
+
+# Defaults of the consistency step: k1 (Eq. 3 clamp), alpha (Eq. 3/7), lambda (Eq. 7) are the
+# paper's final setting (Sec. 4.2); c1, c2 are the forward-backward test constants.
+PAPER_FINAL = dict(k1=0.3, k2=0.5, alpha=6.5e3, lam=2.0)
+PAPER_OBJECTIVE = dict(k1=0.3, k2=0.3, alpha=1.0e4, lam=0.7)
+FB_C1, FB_C2 = 0.01, 0.5
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc -O2 -fopenmp)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        dp, ip, u8p = (ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                       ctypes.POINTER(ctypes.c_uint8))
+        c_int, c_double, vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+        _lib.orc_conv3x3.argtypes = [dp, c_int, c_int, c_int, dp, dp, c_int, c_int, c_int, dp]
+        _lib.orc_warp.argtypes = [dp, c_int, c_int, c_int, dp, c_int, dp, u8p]
+        _lib.orc_correlation.argtypes = [dp, dp, c_int, c_int, c_int, c_int, dp]
+        _lib.orc_upsample_flow.argtypes = [dp, c_int, c_int, c_int, dp]
+        _lib.orc_pad_replicate.argtypes = [dp, c_int, c_int, c_int, c_int, c_int, dp]
+        _lib.orc_pyramid.argtypes = [dp, c_int, c_int, c_int, vp, vp]
+        _lib.orc_flow.argtypes = [vp, vp, ip, c_int, c_int, c_int, c_int, vp, dp, vp]
+        _lib.orc_consistency.argtypes = [c_int, c_int, dp, dp, dp, dp, dp, dp, dp, c_double,
+                                         c_double, c_double, c_int, c_double, c_double, dp, dp,
+                                         u8p, u8p, dp]
+        _lib.orc_bruteforce_flow.argtypes = [dp, dp, c_int, c_int, c_int, c_int, ip]
+    return _lib
+
+
+def _d(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a, t=ctypes.c_double):
+    return a.ctypes.data_as(ctypes.POINTER(t)) if a is not None else None
+
+
+class _Layer(ctypes.Structure):
+    _fields_ = [("cin", ctypes.c_int), ("cout", ctypes.c_int), ("stride", ctypes.c_int),
+                ("leaky", ctypes.c_int), ("w", ctypes.POINTER(ctypes.c_double)),
+                ("b", ctypes.POINTER(ctypes.c_double))]
+
+
+# ----------------------------------------------------------------------------- primitives
+
+def conv3x3(x, w, b=None, stride=1, leaky=True):
+    """3x3 conv, zero pad 1 (Sec. 3.2).  x (cin,h,w), w (cout,cin,3,3) -> (cout,ho,wo)."""
+    x, w = _d(x), _d(w)
+    cin, h, wd = x.shape
+    cout = w.shape[0]
+    b = _d(b) if b is not None else None
+    out = np.empty((cout, (h - 1) // stride + 1, (wd - 1) // stride + 1))
+    lib().orc_conv3x3(_p(x), cin, h, wd, _p(w), _p(b), cout, stride, int(leaky), _p(out))
+    return out
+
+
+def warp(src, flow, zero_outside):
+    """Backward bilinear warp (Sec. 3.1 Gamma).  Returns (warped, in_bounds)."""
+    src, flow = _d(src), _d(flow)
+    c, h, w = src.shape
+    out = np.empty_like(src)
+    inb = np.empty((h, w), np.uint8)
+    lib().orc_warp(_p(src), c, h, w, _p(flow), int(zero_outside), _p(out), _p(inb, ctypes.c_uint8))
+    return out, inb
+
+
+def correlation(f1, f2, r):
+    """Cost volume with LeakyReLU, ((2r+1)^2, h, w) (Sec. 3.2)."""
+    f1, f2 = _d(f1), _d(f2)
+    c, h, w = f1.shape
+    out = np.empty(((2 * r + 1) ** 2, h, w))
+    lib().orc_correlation(_p(f1), _p(f2), c, h, w, r, _p(out))
+    return out
+
+
+def upsample_flow(flow, s):
+    """s-times bilinear flow upsampling with values times s."""
+    flow = _d(flow)
+    _, h, w = flow.shape
+    out = np.empty((2, s * h, s * w))
+    lib().orc_upsample_flow(_p(flow), h, w, s, _p(out))
+    return out
+
+
+def pad_replicate(img, hp, wp):
+    img = _d(img)
+    c, h, w = img.shape
+    out = np.empty((c, hp, wp))
+    lib().orc_pad_replicate(_p(img), c, h, w, hp, wp, _p(out))
+    return out
+
+
+def consistency(It, Pt, Ip, Pp, Op, Fb, Ff, k1=0.3, alpha=6.5e3, lam=2.0, fb_check=True,
+                c1=FB_C1, c2=FB_C2):
+    """Causal consistency step (Eqs. 2-7, w_n = 0).  Returns dict(O, wc, mask, band, wp)."""
+    arrs = [_d(a) for a in (It, Pt, Ip, Pp, Op, Fb, Ff)]
+    _, h, w = arrs[0].shape
+    O = np.empty((3, h, w)); wc = np.empty((h, w)); wp = np.empty((h, w))
+    mask = np.empty((h, w), np.uint8); band = np.empty((h, w), np.uint8)
+    lib().orc_consistency(h, w, *[_p(a) for a in arrs], float(k1), float(alpha), float(lam),
+                          int(fb_check), float(c1), float(c2), _p(O), _p(wc),
+                          _p(mask, ctypes.c_uint8), _p(band, ctypes.c_uint8), _p(wp))
+    return dict(O=O, wc=wc, mask=mask, band=band, wp=wp)
+
+
+def bruteforce_flow(a, b, r):
+    """Integer SSD-argmin displacement index per pixel (3x3 patches, border clamp)."""
+    a, b = _d(a), _d(b)
+    c, h, w = a.shape
+    k = np.empty((h, w), np.int32)
+    lib().orc_bruteforce_flow(_p(a), _p(b), c, h, w, r, _p(k, ctypes.c_int))
+    return k
+
+
+def epe(f, g):
+    """Average end-point error, Eq. 10: mean over pixels of ||f - g||_2."""
+    f, g = _d(f), _d(g)
+    return float(np.sqrt(((f - g) ** 2).sum(0)).mean())
+
+
+# ----------------------------------------------------------------------------- network
+
+@dataclass
+class Net:
+    levels: int
+    radius: int
+    chans: tuple
+    decoder: tuple
+    layers: list  # dicts with cin, cout, stride, leaky, w (float64), b (float64)
+
+    def _table(self, lo, hi):
+        arr = (_Layer * (hi - lo))()
+        for i, L in enumerate(self.layers[lo:hi]):
+            arr[i] = _Layer(L["cin"], L["cout"], L["stride"], L["leaky"], _p(L["w"]), _p(L["b"]))
+        return arr
+
+
+def load_weights(path) -> Net:
+    """Parse the flat weight file (magic 'TCW1', little-endian)."""
+    with open(path, "rb") as f:
+        data = f.read()
+    if data[:4] != b"TCW1":
+        raise ValueError("not a TCW1 weight file")
+    off = 4
+    levels, radius = struct.unpack_from("<ii", data, off); off += 8
+    chans = struct.unpack_from(f"<{levels}i", data, off); off += 4 * levels
+    decoder = struct.unpack_from("<4i", data, off); off += 16
+    (n,) = struct.unpack_from("<i", data, off); off += 4
+    layers = []
+    for _ in range(n):
+        cout, cin, stride, leaky = struct.unpack_from("<4i", data, off); off += 16
+        w = np.frombuffer(data, "<f4", cout * cin * 9, off).reshape(cout, cin, 3, 3); off += 4 * w.size
+        b = np.frombuffer(data, "<f4", cout, off); off += 4 * cout
+        layers.append(dict(cin=cin, cout=cout, stride=stride, leaky=leaky,
+                           w=w.astype(np.float64), b=b.astype(np.float64)))
+    return Net(levels, radius, tuple(chans), tuple(decoder), layers)
+
+
+def net_from_layers(spec_levels, radius, chans, decoder, layers) -> Net:
+    return Net(spec_levels, radius, tuple(chans), tuple(decoder),
+               [dict(cin=L["cin"], cout=L["cout"], stride=L["stride"], leaky=L["leaky"],
+                     w=_d(L["w"]), b=_d(L["b"])) for L in layers])
+
+
+def padded_size(h, w, levels):
+    m = 1 << levels
+    return -(-h // m) * m, -(-w // m) * m
+
+
+def pyramid(net: Net, img_padded):
+    """Feature pyramid of a padded (3, hp, wp) image: list of (chans[l], hp>>l, wp>>l)."""
+    img = _d(img_padded)
+    _, hp, wp = img.shape
+    feats = [np.empty((c, hp >> l, wp >> l)) for l, c in enumerate(net.chans, start=1)]
+    ptrs = (ctypes.c_void_p * net.levels)(*[f.ctypes.data for f in feats])
+    tab = net._table(0, 3 * net.levels)
+    lib().orc_pyramid(_p(img), hp, wp, net.levels, ctypes.cast(tab, ctypes.c_void_p),
+                      ctypes.cast(ptrs, ctypes.c_void_p))
+    return feats
+
+
+def flow_from_pyramids(net: Net, feat_self, feat_other, hp, wp, level_flows=False):
+    """Coarse-to-fine flow F_{self->other} at the padded resolution (2, hp, wp)."""
+    out = np.empty((2, hp, wp))
+    tab = net._table(3 * net.levels, len(net.layers))
+    ps = (ctypes.c_void_p * net.levels)(*[f.ctypes.data for f in feat_self])
+    po = (ctypes.c_void_p * net.levels)(*[f.ctypes.data for f in feat_other])
+    chans = (ctypes.c_int * net.levels)(*net.chans)
+    lf = None
+    lfp = None
+    if level_flows:
+        lf = [np.empty((2, hp >> l, wp >> l)) for l in range(2, net.levels + 1)]
+        lfp = ctypes.cast((ctypes.c_void_p * len(lf))(*[a.ctypes.data for a in lf]), ctypes.c_void_p)
+    lib().orc_flow(ctypes.cast(ps, ctypes.c_void_p), ctypes.cast(po, ctypes.c_void_p), chans,
+                   hp, wp, net.levels, net.radius, ctypes.cast(tab, ctypes.c_void_p), _p(out), lfp)
+    return (out, lf) if level_flows else out
+
+
+def flow_pair(net: Net, I_a, I_b):
+    """F_{a->b} and F_{b->a} for two (3, h, w) frames, cropped to (2, h, w)."""
+    _, h, w = I_a.shape
+    hp, wp = padded_size(h, w, net.levels)
+    pa = pyramid(net, pad_replicate(I_a, hp, wp))
+    pb = pyramid(net, pad_replicate(I_b, hp, wp))
+    fab = flow_from_pyramids(net, pa, pb, hp, wp)[:, :h, :w]
+    fba = flow_from_pyramids(net, pb, pa, hp, wp)[:, :h, :w]
+    return np.ascontiguousarray(fab), np.ascontiguousarray(fba)
+
+
+class Stream:
+    """Oracle of one video stream (Sec. 3.1): O_1 = P_1; later frames blend along the flow."""
+
+    def __init__(self, net: Net, k1=0.3, alpha=6.5e3, lam=2.0, fb_check=True, c1=FB_C1, c2=FB_C2):
+        self.net = net
+        self.params = dict(k1=k1, alpha=alpha, lam=lam, fb_check=fb_check, c1=c1, c2=c2)
+        self.prev = None  # (I, P, O, pyramid)
+
+    def step(self, I, P):
+        I, P = _d(I), _d(P)
+        _, h, w = I.shape
+        hp, wp = padded_size(h, w, self.net.levels)
+        pyr = pyramid(self.net, pad_replicate(I, hp, wp))
+        if self.prev is None:
+            self.prev = (I, P, P.copy(), pyr)
+            return dict(O=P.copy(), wc=np.zeros((h, w)), mask=np.zeros((h, w), np.uint8),
+                        band=np.zeros((h, w), np.uint8), Fb=None, Ff=None)
+        Ip, Pp, Op, pyr_p = self.prev
+        Fb = np.ascontiguousarray(flow_from_pyramids(self.net, pyr, pyr_p, hp, wp)[:, :h, :w])
+        Ff = np.ascontiguousarray(flow_from_pyramids(self.net, pyr_p, pyr, hp, wp)[:, :h, :w])
+        r = consistency(I, P, Ip, Pp, Op, Fb, Ff, **self.params)
+        self.prev = (I, P, r["O"], pyr)
+        r.update(Fb=Fb, Ff=Ff)
+        return r
