@@ -1,0 +1,416 @@
+"""Benchmark: 1080p frames/s of the per-frame hot path (flow network + consistency step).
+
+One step = one frame of one stream through tc_process_frame: feature pyramid of frame t,
+the flow network in both directions (t->t-1, t-1->t), and the fused warp + mask + blend,
+on the synthetic 1920x1080 sequence (textured canvas under affine camera motion with 3
+occluding squares), 5-level network 16/32/64/96/128, correlation radius 4, He-init
+weights, consistency weight k1 swept over {0, .25, .5, .75, 1} frame by frame.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank runs its own independent stream (the
+path shards by stream, no collective on the data path); value = frames of all ranks / the
+slowest rank's time (weak scaling).  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "1080p frames/s (flow+consistency) vs FP32 plain at fixed EPE; p99 frame latency"
+UNIT = "frames/s"
+K1_SWEEP = (0.0, 0.25, 0.5, 0.75, 1.0)
+WIDTH, HEIGHT = 1920, 1080
+SPEC = dict(chans=(16, 32, 64, 96, 128), radius=4)
+N_FRAMES = 8
+# Peak of plain float32 FMA issue: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz.
+FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+
+
+# ----------------------------------------------------------------------------- workload
+
+def net_spec():
+    return synth.NetSpec(chans=SPEC["chans"], radius=SPEC["radius"])
+
+
+def write_weights(path):
+    spec = net_spec()
+    synth.write_weights(path, spec, synth.he_weights(spec, seed=0))
+
+
+def make_frames(seed, n=N_FRAMES, width=WIDTH, height=HEIGHT):
+    seq = synth.Sequence(width=width, height=height, seed=seed)
+    frames = [seq.frame(t) for t in range(n)]
+    return frames, [seq.stylized(t, f) for t, f in enumerate(frames)]
+
+
+def frame_order(step):
+    """Ping-pong through the resident frames so consecutive frames stay consecutive."""
+    period = 2 * (N_FRAMES - 1)
+    k = step % period
+    return k if k < N_FRAMES else period - k
+
+
+def conv_flops_per_frame(spec, width=WIDTH, height=HEIGHT):
+    """Algorithmic FLOPs (2 per multiply-add, true channel counts, no padding) per frame:
+    pyramid of one frame + estimator convs (conv1..conv4) and the flow head in both
+    directions + the correlation (both directions)."""
+    L = spec.levels
+    m = 1 << L
+    hp, wp = -(-height // m) * m, -(-width // m) * m
+    pyr = est = head = corr = 0
+    for name, cin, cout, stride, _ in spec.layer_table():
+        if name.startswith("pyr"):
+            l = int(name[3])
+            px = (hp >> l) * (wp >> l)
+            pyr += 2 * px * cout * cin * 9
+        else:
+            l = int(name[3])
+            px = 2 * (hp >> l) * (wp >> l)
+            f = 2 * px * cout * cin * 9
+            if name.endswith("c5"):
+                head += f
+            else:
+                est += f
+    d = (2 * spec.radius + 1) ** 2
+    for l in range(2, L + 1):
+        corr += 2 * 2 * (hp >> l) * (wp >> l) * d * spec.chans[l - 1]
+    return dict(pyramid_conv=pyr, estimator_conv=est, head=head, correlation=corr)
+
+
+# Algorithmic bytes per pixel of the fused consistency pass: read I_t, P_t (24 B), gather
+# I, P, O of frame t-1 (36 B), write O_t (12 B), the kept copies of I_t, P_t, O_t (36 B),
+# w_c (4 B) and the mask (1 B).  The level-2 flows it upsamples are < 1% of this.
+CONSISTENCY_BYTES_PER_PX = 24 + 36 + 12 + 36 + 4 + 1
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"], samples=0)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(smax) if smax else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_stream(tc, torch, path, dev_frames, dev_styl, precision, steps, warmup, profile=False):
+    """Runs warmup + steps frames through one stream; returns timings (device events)."""
+    H, W = dev_frames[0].shape[1:]
+    s = tc.Stream(W, H, precision, weights_path=path)
+    O = torch.empty((3, H, W), device="cuda")
+    wc = torch.empty((H, W), device="cuda")
+    mask = torch.empty((H, W), device="cuda", dtype=torch.uint8)
+    step = 0
+    for _ in range(warmup):
+        s.set_consistency(k1=K1_SWEEP[step % len(K1_SWEEP)])
+        i = frame_order(step)
+        s.process_frame(dev_frames[i], dev_styl[i], O, wc, mask)
+        step += 1
+    torch.cuda.synchronize()
+    if profile:
+        s.set_profiling(True)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    launches = 0
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for k in range(steps):
+        s.set_consistency(k1=K1_SWEEP[step % len(K1_SWEEP)])
+        i = frame_order(step)
+        s.process_frame(dev_frames[i], dev_styl[i], O, wc, mask)
+        launches += s.launch_count
+        ev[k + 1].record(stream)
+        step += 1
+    torch.cuda.synchronize()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    total = ev[0].elapsed_time(ev[steps])
+    prof = s.get_profile() if profile else None
+    s.destroy()
+    return dict(total_ms=total, per_frame_ms=per, launches=launches, profile=prof)
+
+
+def e2e_host(tc, torch, path, frames, styl, precision, steps, warmup):
+    """End-to-end through tc_process_frame_host: pinned host I_t, P_t in, O_t out per frame."""
+    H, W = frames[0].shape[1:]
+    s = tc.Stream(W, H, precision, weights_path=path)
+    hI = [torch.from_numpy(f).pin_memory() for f in frames]
+    hP = [torch.from_numpy(p).pin_memory() for p in styl]
+    hO = torch.empty((3, H, W), dtype=torch.float32).pin_memory()
+    step = 0
+    for _ in range(warmup):
+        i = frame_order(step)
+        s.process_frame_host(hI[i], hP[i], hO)
+        step += 1
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        i = frame_order(step)
+        s.set_consistency(k1=K1_SWEEP[step % len(K1_SWEEP)])
+        s.process_frame_host(hI[i], hP[i], hO)
+        step += 1
+    dt = time.perf_counter() - t0
+    s.destroy()
+    img = 3 * H * W * 4
+    return dict(value=steps / dt, h2d=2 * img, d2h=img)
+
+
+def cpu_baseline_oracle(seed=0):
+    """The FP64 oracle timed on this host's cores on a bounded sample: one full 1080p frame
+    step (pyramid of frame t, both flow directions, consistency) after frame t-1."""
+    import oracle
+    spec = net_spec()
+    layers = synth.he_weights(spec, seed=0)
+    net = oracle.net_from_layers(spec.levels, spec.radius, spec.chans, spec.decoder, layers)
+    seq = synth.Sequence(width=WIDTH, height=HEIGHT, seed=seed)
+    f0, f1 = seq.frame(0), seq.frame(1)
+    p0, p1 = seq.stylized(0, f0), seq.stylized(1, f1)
+    st = oracle.Stream(net, k1=0.5)
+    st.step(f0, p0)
+    t0 = time.perf_counter()
+    st.step(f1, p1)
+    dt = time.perf_counter() - t0
+    return dict(value=1.0 / dt, unit=UNIT, cores=os.cpu_count(), kind="oracle",
+                sample=f"one 1920x1080 frame step of the FP64 oracle (pyramid, both flow directions, "
+                       f"consistency), {dt:.1f} s")
+
+
+def run_ours(args):
+    import torch
+    import paper_2301_00750_b300 as tc
+
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    tmp = tempfile.mkdtemp(prefix="tcbench")
+    path = os.path.join(tmp, "net.tcw")
+    write_weights(path)
+    frames, styl = make_frames(seed=rank)
+    dev_frames = [torch.from_numpy(f).cuda() for f in frames]
+    dev_styl = [torch.from_numpy(p).cuda() for p in styl]
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier(world)
+    clocks.start()
+    time.sleep(0.3)
+    main = time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, args.steps, args.warmup)
+    clk = clocks.stop()
+    barrier(world)
+    total_s = max_over_ranks(main["total_ms"] / 1e3, world)
+
+    # Per-stage device times over the same number of steps (events around every launch).
+    prof = time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, args.steps, 2, profile=True)
+    fp32 = None
+    if args.precision != "fp32" and not args.skip_fp32:
+        fp32 = time_stream(tc, torch, path, dev_frames, dev_styl, "fp32", max(3, args.steps // 4), 2)
+    e2e = e2e_host(tc, torch, path, frames, styl, args.precision, max(3, min(args.steps, 50)), 2)
+    e2e_v = e2e["value"]
+    if world > 1:
+        e2e_v = world / max_over_ranks(1.0 / e2e["value"], world)
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    flops = conv_flops_per_frame(net_spec())
+    p = prof["profile"]
+    steps = args.steps
+    dom = max(p, key=lambda k: p[k][0])
+    tensor_path = False  # set by the library once the tcgen05 convs are in the BF16 path
+    if dom in ("estimator_conv", "pyramid_conv", "head", "correlation"):
+        achieved = flops[dom] * steps / (p[dom][0] / 1e3) / 1e12
+        if tensor_path:
+            peak, unit, bound = None, "TFLOP/s", "tensor"
+        else:
+            peak, unit, bound = FP32_SIMT_PEAK_TFLOPS, "TFLOP/s", "alu"
+    else:
+        achieved = CONSISTENCY_BYTES_PER_PX * WIDTH * HEIGHT * steps / (p[dom][0] / 1e3) / 1e9
+        peak, unit, bound = measured_peaks().get("hbm_gbs"), "GB/s", "hbm"
+    per = sorted(main["per_frame_ms"])
+    line = {
+        "metric": METRIC, "value": round(world * steps / total_s, 3), "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": round(total_s * 1e3 / steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+        "data": "synthetic (seeded 1080p sequence, He-init weights)",
+        "config": {"workload": "1920x1080 RGB stream, lite flow net 5 levels 16/32/64/96/128, radius 4, "
+                               "decoder 128/96/64/32/2, both flow directions + fused consistency, k1 swept "
+                               "{0,.25,.5,.75,1}", "frames_resident": N_FRAMES, "streams_per_gpu": 1,
+                   "precision": args.precision, "l2": "per-frame working set > 126 MB L2 (no flush needed)"},
+        "latency_ms": {"p50": round(per[len(per) // 2], 4), "p99": round(per[min(len(per) - 1, int(0.99 * len(per)))], 4)},
+        "stage_ms_per_frame": {k: round(v[0] / steps, 4) for k, v in p.items() if v[1]},
+        "roofline": {"kernel": dom, "bound": bound, "achieved": round(achieved, 2), "peak": peak, "unit": unit,
+                     "frac": round(achieved / peak, 4) if peak else None, "traffic": None,
+                     "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2032 MHz" if bound == "alu"
+                     else "of measured (MEASURED_PEAKS.json)"},
+        "gpu_launches": main["launches"],
+        "clocks": clk,
+        "e2e": {"value": round(e2e_v * (world if world > 1 else 1), 3), "unit": UNIT,
+                "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
+    }
+    if fp32 is not None:
+        line["fp32_plain"] = {"value": round(len(fp32["per_frame_ms"]) / (fp32["total_ms"] / 1e3), 3), "unit": UNIT}
+    if world == 1 and not args.skip_cpu:
+        line["cpu_baseline"] = cpu_baseline_oracle()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "_fallback": True}
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The FP64 oracle on this host's cores, same workload family; each step is a bounded
+    sample: a 1920x128 band of the sequence (two frames, pyramid + both flows +
+    consistency), reported as 1080p-frame equivalents per second."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    spec = net_spec()
+    layers = synth.he_weights(spec, seed=0)
+    net = oracle.net_from_layers(spec.levels, spec.radius, spec.chans, spec.decoder, layers)
+    bh = 128
+    seq = synth.Sequence(width=WIDTH, height=bh, seed=0)
+    frames = [seq.frame(t) for t in range(2)]
+    styl = [seq.stylized(t, f) for t, f in enumerate(frames)]
+
+    def one_step():
+        st = oracle.Stream(net, k1=0.5)
+        st.step(frames[0], styl[0])
+        t0 = time.perf_counter()
+        st.step(frames[1], styl[1])
+        return time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        one_step()
+    times = [one_step() for _ in range(args.steps)]
+    frac = (WIDTH * bh) / (WIDTH * HEIGHT)
+    total = sum(times)
+    value = args.steps * frac / total
+    sample = f"per step: one frame step of a 1920x{bh} band ({frac:.4f} of a 1080p frame), FP64 oracle"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total * 1e3 / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": "1920x1080 stream (1920x128 bands), same network"},
+        "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--skip-fp32", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * tc_stream.h -- C ABI of the per-frame hot path of "Interactive Control over Temporal
+ * Consistency while Stylizing Video Streams" (arXiv 2301.00750), for NVIDIA B300 (sm_103a).
+ *
+ * For each new frame I_t of a video stream and its per-frame stylised version P_t, the
+ * library computes the temporally consistent output O_t (Sec. 3.1, problem statement):
+ *   1. the lite optical-flow network (Sec. 3.2): feature pyramid, correlation cost volume,
+ *      bilinear feature warping and coarse-to-fine flow estimators, run in both directions
+ *      between frames t and t-1;
+ *   2. backward warping of I_{t-1}, P_{t-1}, O_{t-1} along F_{t->t-1} (the warping function
+ *      Gamma of Sec. 3.1), a forward-backward non-occlusion mask (the mask used with the
+ *      warping error, Eq. 9), the photometric weight w_p (Eq. 3, clamped to [0, k1]), the
+ *      local and global consistency images L_t, G_t (Eqs. 2, 4), their adaptive blend A_t
+ *      (Eq. 5), the warped input A^I_t (Eq. 6) and the consistency weight w_c (Eq. 7).
+ *   O_t := A_t (causal form: no next frame, w_n = 0; the screened-Poisson solve of Eq. 1 is
+ *   not part of this path).  The first frame of a stream returns O_1 = P_1.
+ *
+ * Conventions
+ *   - Images are planar CHW float32, 3 channels (RGB), values nominally in [0, 1].
+ *   - Flows are float32 displacements in pixels, F_{a->b}(x) with I_a(x) ~ I_b(x + F(x)).
+ *   - "device" pointers are CUDA device (or managed) memory on the stream's device;
+ *     "host" pointers are CPU memory (pinned memory gives asynchronous copies).
+ *   - cuda_stream is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - Every call returns a tc_status and never aborts the process.  After a CUDA error a
+ *     stream is poisoned: later calls return TC_ERR_STATE.  tc_last_error() describes the
+ *     last failure of a stream (or of the last stream-less call when passed NULL).
+ *   - One stream object must not be used from two host threads at once; distinct stream
+ *     objects are independent and may run concurrently.
+ *
+ * Precision: TC_FP32 runs every stage in float32.  TC_BF16 runs the convolutions and the
+ * correlation with bfloat16 operands and float32 accumulation; flow coordinates, feature
+ * warp interpolation weights, the mask thresholds and the consistency step stay float32.
+ */
+#ifndef TC_STREAM_H
+#define TC_STREAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TC_API __attribute__((visibility("default")))
+#else
+#define TC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tc_stream tc_stream;   /* opaque, owned by the library */
+
+typedef enum {
+    TC_OK = 0,
+    TC_ERR_INVALID_ARG = 1,   /* a NULL pointer, a bad size, a value out of range */
+    TC_ERR_OOM = 2,           /* device or host allocation failed */
+    TC_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed */
+    TC_ERR_BUSY = 4,          /* resource in use (reserved) */
+    TC_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+    TC_ERR_STATE = 6,         /* the stream is poisoned by an earlier CUDA error */
+    TC_ERR_IO = 7,            /* the weight file could not be read or parsed */
+    TC_ERR_UNSUPPORTED = 8    /* the request is valid but not built in this library */
+} tc_status;
+
+typedef enum { TC_FP32 = 0, TC_BF16 = 1, TC_FP8_E4M3 = 2 } tc_precision;
+
+/* Consistency controls (Sec. 3.1 "Consistency Control Modes", values of Sec. 4.2).
+ *   k1      upper clamp of w_p (Eq. 3); the global/local proportion of A_t.  [0, 1]
+ *   k2      upper clamp of w_n (Eq. 3); unused by the causal path (w_n = 0).
+ *   alpha   sharpness of the photometric weights (Eqs. 3, 7).  >= 0
+ *   lambda  scale of the consistency weight w_c (Eq. 7).  >= 0
+ *   fb_check, fb_c1, fb_c2: forward-backward occlusion test
+ *           |Fb + Ff~|^2 > c1 (|Fb|^2 + |Ff~|^2) + c2 marks a pixel occluded (mask 0).
+ *   solver_iters, eta, kappa: Eq. 8 settings, reserved; must be 0 / ignored here. */
+typedef struct {
+    float k1, k2, alpha, lambda;
+    int fb_check;
+    float fb_c1, fb_c2;
+    int solver_iters;
+    float eta, kappa;
+} tc_consistency;
+
+/* Stream description.
+ *   width, height   frame size in pixels, each >= 2^levels of the network.
+ *   precision       TC_FP32 or TC_BF16.
+ *   weights_path    path of a 'TCW1' weight file, or NULL to use weights_blob.
+ *   weights_blob    host pointer to the same bytes as such a file (copied at creation).
+ * The weight file fixes the number of pyramid levels, the channel counts and the
+ * correlation radius.  Its layout, little-endian: "TCW1"; int32 levels, radius,
+ * chans[levels], decoder[4] (128,96,64,32), n_layers; per layer int32 cout, cin, stride,
+ * leaky, float32 w[cout][cin][3][3], float32 b[cout].  Layer order: pyramid levels 1..L
+ * (three convs each), then the estimators at levels L..2 (five convs each; conv4 reads
+ * cat(x3, x2), conv5 reads cat(x4, x3)). */
+typedef struct {
+    int width, height;
+    tc_precision precision;
+    const char *weights_path;
+    const void *weights_blob;
+    size_t weights_bytes;
+} tc_stream_desc;
+
+/* Fills *p with the paper's final setting (Sec. 4.2: k1 = 0.3, k2 = 0.5, alpha = 6.5e3,
+ * lambda = 2.0), the forward-backward test on with c1 = 0.01, c2 = 0.5, solver off. */
+TC_API void tc_default_consistency(tc_consistency *p);
+
+/* Creates a stream (Sec. 3.1: per-stream state I_{t-1}, P_{t-1}, O_{t-1} and the cached
+ * feature pyramid of frame t-1 live on the device).  Allocates all device memory the
+ * stream needs.  Errors: TC_ERR_INVALID_ARG (sizes, precision), TC_ERR_IO (weights),
+ * TC_ERR_OOM, TC_ERR_CUDA.  On error *out is NULL. */
+TC_API tc_status tc_create_stream(const tc_stream_desc *desc, void *cuda_stream, tc_stream **out);
+
+/* Sets the consistency controls; they apply from the next tc_process_frame call.
+ * Errors: TC_ERR_INVALID_ARG (k1 outside [0,1], alpha or lambda negative, NaN). */
+TC_API tc_status tc_set_consistency(tc_stream *s, const tc_consistency *p);
+
+/* Processes the next frame.  I_t, P_t: device (3, H, W) float32, read only.  O_t: device
+ * (3, H, W) float32, written.  wc_opt: device (H, W) float32 consistency weight w_c, or
+ * NULL.  mask_opt: device (H, W) uint8 non-occlusion mask M (1 = usable), or NULL.
+ * Work is enqueued on the stream's CUDA stream and the call returns without waiting; the
+ * library copies what it keeps, so the caller may reuse I_t and P_t once that work has
+ * completed.  On the first frame O_t = P_t, w_c = 0 and M = 0. */
+TC_API tc_status tc_process_frame(tc_stream *s, const float *I_t, const float *P_t, float *O_t,
+                           float *wc_opt, uint8_t *mask_opt);
+
+/* As tc_process_frame with HOST buffers: copies I_t, P_t to the device, runs the frame and
+ * copies O_t (and the optional outputs) back, then waits for the stream.  The same
+ * layouts as above; host pointers.  Pinned host memory makes the copies faster. */
+TC_API tc_status tc_process_frame_host(tc_stream *s, const float *I_t, const float *P_t, float *O_t,
+                                float *wc_opt, uint8_t *mask_opt);
+
+/* Writes the flows of the last processed frame at full resolution: Fb = F_{t->t-1} and
+ * Ff = F_{t-1->t}, each device (2, H, W) float32 (planar u then v).  Either may be NULL.
+ * Errors: TC_ERR_STATE before the second frame. */
+TC_API tc_status tc_get_flows(tc_stream *s, float *Fb, float *Ff);
+
+/* Destroys a stream and frees its device memory (waits for its pending work). */
+TC_API tc_status tc_destroy(tc_stream *s);
+
+/* Human-readable description of the last error of s (s may be NULL for stream-less calls).
+ * The string is owned by the library and valid until the next call on s. */
+TC_API const char *tc_last_error(const tc_stream *s);
+
+/* Number of kernel launches enqueued by the last tc_process_frame on s (for accounting). */
+TC_API int tc_last_launch_count(const tc_stream *s);
+
+/* Per-stage timing.  With profiling on, the library records a CUDA event pair around every
+ * kernel it launches for s and adds the elapsed device time to the stage's total.
+ * Categories (index into the arrays of tc_get_profile): */
+enum {
+    TC_PROF_PYRAMID_CONV = 0,    /* feature pyramid convolutions (Sec. 3.2) */
+    TC_PROF_ESTIMATOR_CONV = 1,  /* estimator convolutions conv1..conv4 */
+    TC_PROF_HEAD = 2,            /* flow head conv5 + residual */
+    TC_PROF_CORRELATION = 3,     /* cost volume */
+    TC_PROF_WARP = 4,            /* bilinear feature warp */
+    TC_PROF_UPSAMPLE = 5,        /* x2 flow upsampling */
+    TC_PROF_CONSISTENCY = 6,     /* fused warp + mask + blend (Eqs. 2-7) */
+    TC_PROF_OTHER = 7,
+    TC_PROF_CATEGORIES = 8
+};
+
+/* Turns per-stage timing on (enable != 0) or off and resets the totals. */
+TC_API tc_status tc_set_profiling(tc_stream *s, int enable);
+
+/* Waits for the recorded events and writes the per-category totals since the last
+ * tc_set_profiling: ms[k] milliseconds and launches[k] (may be NULL) launch counts, for
+ * k < n (n <= TC_PROF_CATEGORIES).  Host arrays. */
+TC_API tc_status tc_get_profile(tc_stream *s, double *ms, long long *launches, int n);
+
+/* ------------------------------------------------------------------------------------
+ * Single-stage entry points.  Each runs one stage of the path on caller-owned device
+ * buffers, enqueued on cuda_stream, and returns without waiting.  Feature maps are NHWC
+ * float32 (n, h, w, c) contiguous; flows are (n, h, w, 2) float32 (u, v interleaved).
+ * `precision` selects the arithmetic: TC_FP32, or TC_BF16 (inputs rounded to bfloat16
+ * on load, float32 accumulation, float32 outputs).  These allocate temporary device
+ * memory for reformatted weights where noted and free it before returning.
+ * ---------------------------------------------------------------------------------- */
+
+/* 3x3 convolution, zero padding 1, stride 1 or 2, bias, optional LeakyReLU(0.1)
+ * (Sec. 3.2 pyramid and estimator layers).  in (n, h, w, cin); w_oihw, bias: HOST float32
+ * (cout, cin, 3, 3) and (cout); out (n, (h-1)/stride+1, (w-1)/stride+1, cout).
+ * Allocates temporary device memory for the weights.  cin, cout >= 1. */
+TC_API tc_status tc_op_conv3x3(tc_precision precision, const float *in, int n, int h, int w, int cin,
+                        const float *w_oihw, const float *bias, int cout, int stride, int leaky,
+                        float *out, void *cuda_stream);
+
+/* Cost volume (Sec. 3.2): out[n][y][x][k] = LeakyReLU((1/c) sum_ch f1[n][y][x][ch] *
+ * f2[n][y+dy][x+dx][ch]), zero off the map, k = (dy+r)(2r+1) + (dx+r).  f1, f2
+ * (n, h, w, c); out (n, h, w, (2r+1)^2).  1 <= r <= 4, c a multiple of 4. */
+TC_API tc_status tc_op_correlation(tc_precision precision, const float *f1, const float *f2, int n,
+                            int h, int w, int c, int r, float *out, void *cuda_stream);
+
+/* Bilinear backward warp of features with zeros off the map (Sec. 3.2 feature warping):
+ * out[n][y][x] = sum of the bilinear taps of f[n] at (x + u, y + v) that lie on the map.
+ * f (n, h, w, c), flow (n, h, w, 2), out (n, h, w, c).  c a multiple of 4. */
+TC_API tc_status tc_op_warp_features(tc_precision precision, const float *f, const float *flow, int n,
+                              int h, int w, int c, float *out, void *cuda_stream);
+
+/* Flow upsampling by s in {2, 4}: bilinear, half-pixel centres (sample positions clamped
+ * at 0 and at the last row/column), values multiplied by s.  flow (n, h, w, 2) ->
+ * out (n, s h, s w, 2). */
+TC_API tc_status tc_op_upsample_flow(const float *flow, int n, int h, int w, int s, float *out,
+                              void *cuda_stream);
+
+/* The consistency step alone (Sec. 3.1, Eqs. 2-7 with w_n = 0, O_t := A_t) on images of
+ * h x w pixels.  It, Pt, Ip, Pp, Op: device (3, h, w) float32 (I_t, P_t, I_{t-1},
+ * P_{t-1}, O_{t-1}).  Fb, Ff: device (fh, fw, 2) float32 flows at 1/scale resolution,
+ * scale in {1, 2, 4, ...} (1 = full resolution, fh = h, fw = w); they are upsampled on
+ * the fly as by tc_op_upsample_flow and read on the h x w crop.  Requires fh * scale >= h
+ * and fw * scale >= w.  O: device (3, h, w); wc_opt (h, w) float32 or NULL; mask_opt
+ * (h, w) uint8 or NULL. */
+TC_API tc_status tc_op_consistency(const float *It, const float *Pt, const float *Ip, const float *Pp,
+                            const float *Op, const float *Fb, const float *Ff, int h, int w,
+                            int fh, int fw, int scale, const tc_consistency *p, float *O,
+                            float *wc_opt, uint8_t *mask_opt, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_STREAM_H */

@@ -1,0 +1,258 @@
+"""Python binding of libtcstream (the C ABI in include/tc_stream.h).
+
+Argument marshalling only: every stage of the hot path runs in the library's CUDA kernels.
+PyTorch is used for device memory and streams; tensors are passed as raw pointers.  If
+the compiled library is missing this module raises on import -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtcstream.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2301_00750_b300/build.py` "
+                      "(or __graft_entry__.build()); there is no CPU fallback")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+TC_OK, TC_ERR_INVALID_ARG, TC_ERR_OOM, TC_ERR_CUDA, TC_ERR_BUSY, TC_ERR_TIMEOUT, TC_ERR_STATE, TC_ERR_IO, \
+    TC_ERR_UNSUPPORTED = range(9)
+_STATUS = ["TC_OK", "TC_ERR_INVALID_ARG", "TC_ERR_OOM", "TC_ERR_CUDA", "TC_ERR_BUSY", "TC_ERR_TIMEOUT",
+           "TC_ERR_STATE", "TC_ERR_IO", "TC_ERR_UNSUPPORTED"]
+PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2}
+
+EXPORTED = ["tc_default_consistency", "tc_create_stream", "tc_set_consistency", "tc_process_frame",
+            "tc_process_frame_host", "tc_get_flows", "tc_destroy", "tc_last_error", "tc_last_launch_count",
+            "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
+            "tc_op_consistency", "tc_set_profiling", "tc_get_profile"]
+PROFILE_CATEGORIES = ["pyramid_conv", "estimator_conv", "head", "correlation", "warp", "upsample", "consistency",
+                      "other"]
+
+
+class TcConsistency(ctypes.Structure):
+    _fields_ = [("k1", ctypes.c_float), ("k2", ctypes.c_float), ("alpha", ctypes.c_float),
+                ("lambda_", ctypes.c_float), ("fb_check", ctypes.c_int), ("fb_c1", ctypes.c_float),
+                ("fb_c2", ctypes.c_float), ("solver_iters", ctypes.c_int), ("eta", ctypes.c_float),
+                ("kappa", ctypes.c_float)]
+
+
+class TcStreamDesc(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("precision", ctypes.c_int),
+                ("weights_path", ctypes.c_char_p), ("weights_blob", ctypes.c_void_p),
+                ("weights_bytes", ctypes.c_size_t)]
+
+
+_vp, _i, _f = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+_lib.tc_default_consistency.argtypes = [ctypes.POINTER(TcConsistency)]
+_lib.tc_default_consistency.restype = None
+_lib.tc_create_stream.argtypes = [ctypes.POINTER(TcStreamDesc), _vp, ctypes.POINTER(_vp)]
+_lib.tc_set_consistency.argtypes = [_vp, ctypes.POINTER(TcConsistency)]
+_lib.tc_process_frame.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+_lib.tc_process_frame_host.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+_lib.tc_get_flows.argtypes = [_vp, _vp, _vp]
+_lib.tc_destroy.argtypes = [_vp]
+_lib.tc_last_error.argtypes = [_vp]
+_lib.tc_last_error.restype = ctypes.c_char_p
+_lib.tc_last_launch_count.argtypes = [_vp]
+_lib.tc_op_conv3x3.argtypes = [_i, _vp, _i, _i, _i, _i, _vp, _vp, _i, _i, _i, _vp, _vp]
+_lib.tc_op_correlation.argtypes = [_i, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp]
+_lib.tc_op_warp_features.argtypes = [_i, _vp, _vp, _i, _i, _i, _i, _vp, _vp]
+_lib.tc_op_upsample_flow.argtypes = [_vp, _i, _i, _i, _i, _vp, _vp]
+_lib.tc_op_consistency.argtypes = [_vp] * 7 + [_i] * 5 + [ctypes.POINTER(TcConsistency), _vp, _vp, _vp, _vp]
+_lib.tc_set_profiling.argtypes = [_vp, _i]
+_lib.tc_get_profile.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), _i]
+for _n in ["tc_set_profiling", "tc_get_profile", "tc_create_stream", "tc_set_consistency", "tc_process_frame", "tc_process_frame_host", "tc_get_flows",
+           "tc_destroy", "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
+           "tc_op_consistency"]:
+    getattr(_lib, _n).restype = ctypes.c_int
+
+
+class TcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS[status] if 0 <= status < len(_STATUS) else status}: {msg}")
+        self.status = status
+
+
+def _check(status, handle=None):
+    if status != TC_OK:
+        raise TcError(status, (_lib.tc_last_error(handle) or b"").decode())
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (or None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _stream_handle(cuda_stream):
+    if cuda_stream is None:
+        import torch
+        if not torch.cuda.is_available():
+            return None
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(cuda_stream, "cuda_stream", cuda_stream)
+
+
+def default_consistency() -> dict:
+    c = TcConsistency()
+    _lib.tc_default_consistency(ctypes.byref(c))
+    return dict(k1=c.k1, k2=c.k2, alpha=c.alpha, lam=c.lambda_, fb_check=bool(c.fb_check), fb_c1=c.fb_c1,
+                fb_c2=c.fb_c2)
+
+
+def _consistency_struct(**kw) -> TcConsistency:
+    c = TcConsistency()
+    _lib.tc_default_consistency(ctypes.byref(c))
+    for k, v in kw.items():
+        if k == "lam":
+            c.lambda_ = v
+        elif k == "fb_check":
+            c.fb_check = int(bool(v))
+        else:
+            setattr(c, k, v)
+    return c
+
+
+class Stream:
+    """One video stream: tc_create_stream / tc_set_consistency / tc_process_frame / tc_destroy."""
+
+    def __init__(self, width, height, precision="fp32", weights_path=None, weights_blob=None, cuda_stream=None):
+        desc = TcStreamDesc()
+        desc.width, desc.height = int(width), int(height)
+        desc.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        self._blob = None
+        if weights_path is not None:
+            desc.weights_path = os.fsencode(weights_path)
+        elif weights_blob is not None:
+            self._blob = ctypes.create_string_buffer(bytes(weights_blob), len(weights_blob))
+            desc.weights_blob = ctypes.cast(self._blob, ctypes.c_void_p)
+            desc.weights_bytes = len(weights_blob)
+        h = _vp()
+        self.cuda_stream = _stream_handle(cuda_stream)
+        _check(_lib.tc_create_stream(ctypes.byref(desc), self.cuda_stream, ctypes.byref(h)))
+        self._h = h
+        self.width, self.height = int(width), int(height)
+
+    def set_consistency(self, **kw):
+        c = _consistency_struct(**kw)
+        _check(_lib.tc_set_consistency(self._h, ctypes.byref(c)), self._h)
+
+    def process_frame(self, I, P, O, wc=None, mask=None):
+        import torch
+        _check(_lib.tc_process_frame(self._h, _ptr(I, torch.float32, "I_t"), _ptr(P, torch.float32, "P_t"),
+                                     _ptr(O, torch.float32, "O_t"), _ptr(wc, torch.float32, "wc"),
+                                     _ptr(mask, torch.uint8, "mask")), self._h)
+
+    def process_frame_host(self, I, P, O, wc=None, mask=None):
+        """Host buffers (NumPy or CPU torch tensors, contiguous float32 / uint8)."""
+        def hp(a, dt):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                return a.data_ptr()
+            if a.dtype != dt or not a.flags.c_contiguous:
+                raise TypeError("host buffers must be contiguous " + str(dt))
+            return a.ctypes.data
+        _check(_lib.tc_process_frame_host(self._h, hp(I, np.float32), hp(P, np.float32), hp(O, np.float32),
+                                          hp(wc, np.float32), hp(mask, np.uint8)), self._h)
+
+    def get_flows(self, Fb=None, Ff=None):
+        import torch
+        _check(_lib.tc_get_flows(self._h, _ptr(Fb, torch.float32, "Fb"), _ptr(Ff, torch.float32, "Ff")), self._h)
+
+    def set_profiling(self, enable: bool):
+        _check(_lib.tc_set_profiling(self._h, int(bool(enable))), self._h)
+
+    def get_profile(self) -> dict:
+        """{category: (milliseconds, launches)} since the last set_profiling."""
+        n = len(PROFILE_CATEGORIES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_longlong * n)()
+        _check(_lib.tc_get_profile(self._h, ms, cnt, n), self._h)
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(PROFILE_CATEGORIES)}
+
+    @property
+    def launch_count(self) -> int:
+        return _lib.tc_last_launch_count(self._h)
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            _check(_lib.tc_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------- stage ops
+
+def op_conv3x3(x, w, b, stride=1, leaky=True, precision="fp32", cuda_stream=None):
+    """x: CUDA (n, h, w, cin) float32; w: (cout, cin, 3, 3), b: (cout) on the host."""
+    import torch
+    n, h, wd, cin = x.shape
+    w = np.ascontiguousarray(w, np.float32)
+    b = np.ascontiguousarray(b, np.float32)
+    cout = w.shape[0]
+    out = torch.empty((n, (h - 1) // stride + 1, (wd - 1) // stride + 1, cout), device=x.device, dtype=torch.float32)
+    _check(_lib.tc_op_conv3x3(PRECISION[precision], _ptr(x, torch.float32), n, h, wd, cin, w.ctypes.data,
+                              b.ctypes.data, cout, stride, int(leaky), out.data_ptr(), _stream_handle(cuda_stream)))
+    return out
+
+
+def op_correlation(f1, f2, r, precision="fp32", cuda_stream=None):
+    import torch
+    n, h, w, c = f1.shape
+    out = torch.empty((n, h, w, (2 * r + 1) ** 2), device=f1.device, dtype=torch.float32)
+    _check(_lib.tc_op_correlation(PRECISION[precision], _ptr(f1, torch.float32), _ptr(f2, torch.float32), n, h, w,
+                                  c, r, out.data_ptr(), _stream_handle(cuda_stream)))
+    return out
+
+
+def op_warp_features(f, flow, precision="fp32", cuda_stream=None):
+    import torch
+    n, h, w, c = f.shape
+    out = torch.empty_like(f)
+    _check(_lib.tc_op_warp_features(PRECISION[precision], _ptr(f, torch.float32), _ptr(flow, torch.float32), n, h,
+                                    w, c, out.data_ptr(), _stream_handle(cuda_stream)))
+    return out
+
+
+def op_upsample_flow(flow, s, cuda_stream=None):
+    import torch
+    n, h, w, _ = flow.shape
+    out = torch.empty((n, s * h, s * w, 2), device=flow.device, dtype=torch.float32)
+    _check(_lib.tc_op_upsample_flow(_ptr(flow, torch.float32), n, h, w, s, out.data_ptr(),
+                                    _stream_handle(cuda_stream)))
+    return out
+
+
+def op_consistency(It, Pt, Ip, Pp, Op, Fb, Ff, scale=1, O=None, wc=None, mask=None, cuda_stream=None, **params):
+    """Images (3, h, w) float32 CUDA; flows (fh, fw, 2) float32 CUDA at 1/scale resolution."""
+    import torch
+    _, h, w = It.shape
+    fh, fw, _ = Fb.shape
+    O = torch.empty_like(It) if O is None else O
+    wc = torch.empty((h, w), device=It.device, dtype=torch.float32) if wc is None else wc
+    mask = torch.empty((h, w), device=It.device, dtype=torch.uint8) if mask is None else mask
+    c = _consistency_struct(**params)
+    f32 = torch.float32
+    _check(_lib.tc_op_consistency(_ptr(It, f32), _ptr(Pt, f32), _ptr(Ip, f32), _ptr(Pp, f32), _ptr(Op, f32),
+                                  _ptr(Fb, f32), _ptr(Ff, f32), h, w, fh, fw, scale, ctypes.byref(c), O.data_ptr(),
+                                  wc.data_ptr(), mask.data_ptr(), _stream_handle(cuda_stream)))
+    return O, wc, mask

@@ -1,0 +1,159 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tc {
+
+// Activation storage types: float (TC_FP32) and bfloat16 (TC_BF16).
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename T> __device__ __forceinline__ T from_f(float v);
+template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+
+// Loads 4 consecutive activations (16-byte aligned for float, 8-byte for bf16) as float4.
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ float4 ld4(const __nv_bfloat16 *p) {
+    uint2 u = *reinterpret_cast<const uint2 *>(p);
+    __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162 *>(&u.x);
+    __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162 *>(&u.y);
+    float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ void st4(__nv_bfloat16 *p, float4 v) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    uint2 u;
+    u.x = *reinterpret_cast<uint32_t *>(&a);
+    u.y = *reinterpret_cast<uint32_t *>(&b);
+    *reinterpret_cast<uint2 *>(p) = u;
+}
+
+__device__ __forceinline__ float lrelu(float v) { return v >= 0.f ? v : 0.1f * v; }
+
+// ---------------------------------------------------------------------------------------
+// Launch parameter blocks
+// ---------------------------------------------------------------------------------------
+
+// Implicit-GEMM 3x3 convolution over NHWC activations.  Input and output buffers are
+// dense [n][h][w][cs] with the layer's channels at a fixed offset (already applied to the
+// pointers).  wk is [9 * cin][cout] (k = tap * cin + c, tap = ky * 3 + kx).
+struct ConvArgs {
+    const void *in;
+    int in_cs;
+    int n, h, w, cin, stride;
+    int ho, wo;
+    const float *wk;
+    const float *bias;
+    int cout;
+    void *out;
+    int out_cs;
+    int leaky;
+};
+
+// First pyramid conv: planar float image (3, H, W), edge-replicated to (Hp, Wp) and
+// zero-padded by one, stride 2.  wk is [27][cout] (k = c * 9 + tap).
+struct ConvFirstArgs {
+    const float *img;
+    int H, W, Hp, Wp;
+    const float *wk;
+    const float *bias;
+    int cout;
+    void *out;  // [Hp/2][Wp/2][cout]
+};
+
+// Flow head: conv5 (cin -> 2, no activation) plus the residual up-flow.
+struct HeadArgs {
+    const void *in;  // [n][h][w][cs], offset applied
+    int in_cs, cin, n, h, w;
+    const float *wk;   // [9 * cin][2]
+    const float *bias; // [2]
+    const float *up;   // [n][h][w][2] or NULL
+    float *flow;       // [n][h][w][2]
+};
+
+// Cost volume over a batch of directions; self/other pointers are per batch entry.
+struct CorrArgs {
+    const void *fs[2];
+    const void *fo[2];
+    int fs_cs, fo_cs;
+    int n, h, w, c, r;
+    void *out;        // [n][h][w][out_cs], correlation at channel 0
+    int out_cs;
+    void *self_copy;  // same buffer at channel offset D (or NULL)
+};
+
+struct WarpArgs {
+    const void *f[2];  // per batch entry, [h][w][f_cs]
+    int f_cs;
+    const float *flow;  // [n][h][w][2]
+    int n, h, w, c;
+    void *out;          // [n][h][w][out_cs]
+    int out_cs;
+};
+
+struct UpArgs {
+    const float *flow;  // [n][h][w][2]
+    int n, h, w, s;
+    float *out;         // [n][s h][s w][2]
+    void *act;          // optional copy into an activation buffer [n][s h][s w][act_cs]
+    int act_cs;
+};
+
+struct ConsistArgs {
+    const float *It, *Pt, *Ip, *Pp, *Op;  // planar (3, H, W)
+    const float *Fb, *Ff;                 // (fh, fw, 2)
+    int H, W, fh, fw, scale;
+    float k1, alpha, lambda, c1, c2;
+    int fb_check;
+    int first;
+    float *O, *wc;
+    uint8_t *mask;
+    float *sI, *sP, *sO;  // state copies (nullable)
+};
+
+// Host launchers (return cudaGetLastError()).
+template <typename T> cudaError_t launch_conv_simt(const ConvArgs &a, cudaStream_t st);
+template <typename T> cudaError_t launch_conv_first(const ConvFirstArgs &a, cudaStream_t st);
+template <typename T> cudaError_t launch_head(const HeadArgs &a, cudaStream_t st);
+template <typename T> cudaError_t launch_corr(const CorrArgs &a, cudaStream_t st);
+template <typename T> cudaError_t launch_warp(const WarpArgs &a, cudaStream_t st);
+template <typename T> cudaError_t launch_up(const UpArgs &a, cudaStream_t st);
+cudaError_t launch_consistency(const ConsistArgs &a, cudaStream_t st);
+cudaError_t launch_flow_out(const float *flow, int fh, int fw, int scale, int H, int W,
+                            float *out, cudaStream_t st);
+template <typename T> cudaError_t launch_to_act(const float *in, size_t n, T *out, cudaStream_t st);
+template <typename T> cudaError_t launch_from_act(const T *in, size_t n, float *out, cudaStream_t st);
+
+}  // namespace tc
+
+namespace tc {
+
+// Value at integer position (X, Y) of the s-times bilinear upsampling (half-pixel centres,
+// sample position clamped at 0 and at the last row/column) of a (fh, fw, 2) flow field,
+// multiplied by s.  s = 1 reads the field directly.  s must be a power of two, so every
+// coordinate and interpolation weight below is exact in float32.
+__device__ __forceinline__ float2 upsampled_flow_at(const float *F, int fh, int fw, int s,
+                                                    int X, int Y) {
+    const float2 *f = reinterpret_cast<const float2 *>(F);
+    if (s == 1) return f[(size_t)Y * fw + X];
+    const float fs = (float)s;
+    float sy = (Y + 0.5f) / fs - 0.5f, sx = (X + 0.5f) / fs - 0.5f;
+    sy = fmaxf(sy, 0.f);
+    sx = fmaxf(sx, 0.f);
+    int y0 = min((int)sy, fh - 1), x0 = min((int)sx, fw - 1);
+    const int y1 = y0 < fh - 1 ? y0 + 1 : y0, x1 = x0 < fw - 1 ? x0 + 1 : x0;
+    const float ly = sy - y0, lx = sx - x0;
+    const float2 a = f[(size_t)y0 * fw + x0], b = f[(size_t)y0 * fw + x1];
+    const float2 c = f[(size_t)y1 * fw + x0], d = f[(size_t)y1 * fw + x1];
+    float u = (1.f - ly) * ((1.f - lx) * a.x + lx * b.x) + ly * ((1.f - lx) * c.x + lx * d.x);
+    float v = (1.f - ly) * ((1.f - lx) * a.y + lx * b.y) + ly * ((1.f - lx) * c.y + lx * d.y);
+    return make_float2(fs * u, fs * v);
+}
+
+}  // namespace tc

@@ -1,0 +1,854 @@
+// Stream engine and C ABI (see include/tc_stream.h): per-stream device state, weight
+// loading, the per-frame launch sequence of the flow network and the consistency step,
+// and the single-stage entry points.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/tc_stream.h"
+#include "common.cuh"
+#include "conv_tc.cuh"
+
+namespace tc {
+
+// ------------------------------------------------------------------------------- weights
+
+struct HostLayer {
+    int cout, cin, stride, leaky;
+    std::vector<float> w;  // OIHW
+    std::vector<float> b;
+};
+
+struct HostNet {
+    int levels = 0, radius = 0;
+    std::vector<int> chans;
+    int dec[4] = {0, 0, 0, 0};
+    std::vector<HostLayer> layers;
+};
+
+static bool parse_weights(const uint8_t *p, size_t n, HostNet &net, std::string &err) {
+    size_t off = 0;
+    auto rd = [&](void *dst, size_t k) -> bool {
+        if (off + k > n) return false;
+        memcpy(dst, p + off, k);
+        off += k;
+        return true;
+    };
+    char magic[4];
+    if (!rd(magic, 4) || memcmp(magic, "TCW1", 4) != 0) { err = "weights: bad magic (want TCW1)"; return false; }
+    int32_t lv, rad;
+    if (!rd(&lv, 4) || !rd(&rad, 4)) { err = "weights: truncated header"; return false; }
+    if (lv < 2 || lv > 7 || rad < 1 || rad > 4) { err = "weights: levels must be 2..7 and radius 1..4"; return false; }
+    net.levels = lv;
+    net.radius = rad;
+    net.chans.resize(lv);
+    if (!rd(net.chans.data(), 4 * lv) || !rd(net.dec, 16)) { err = "weights: truncated header"; return false; }
+    int32_t nl;
+    if (!rd(&nl, 4)) { err = "weights: truncated header"; return false; }
+    const int want = 3 * lv + 5 * (lv - 1);
+    if (nl != want) { err = "weights: layer count does not match the level count"; return false; }
+    const int D = (2 * rad + 1) * (2 * rad + 1);
+    for (int i = 0; i < nl; ++i) {
+        HostLayer L;
+        int32_t h4[4];
+        if (!rd(h4, 16)) { err = "weights: truncated layer header"; return false; }
+        L.cout = h4[0]; L.cin = h4[1]; L.stride = h4[2]; L.leaky = h4[3];
+        if (L.cout < 1 || L.cin < 1 || L.cout > 4096 || L.cin > 4096) { err = "weights: bad layer shape"; return false; }
+        L.w.resize((size_t)L.cout * L.cin * 9);
+        L.b.resize(L.cout);
+        if (!rd(L.w.data(), 4 * L.w.size()) || !rd(L.b.data(), 4 * L.b.size())) { err = "weights: truncated layer data"; return false; }
+        net.layers.push_back(std::move(L));
+    }
+    // Shape checks against the architecture (Sec. 3.2).
+    int prev = 3;
+    for (int l = 0; l < lv; ++l) {
+        const int c = net.chans[l];
+        const HostLayer *P = &net.layers[3 * l];
+        if (c % 4 != 0 || c > 256) { err = "weights: pyramid channels must be multiples of 4, <= 256"; return false; }
+        if (P[0].cin != prev || P[0].cout != c || P[0].stride != 2 || P[1].cin != c || P[1].cout != c ||
+            P[2].cin != c || P[2].cout != c || P[1].stride != 1 || P[2].stride != 1) {
+            err = "weights: pyramid layer shapes do not match the channel list"; return false;
+        }
+        prev = c;
+    }
+    if (net.chans[0] > 64) { err = "weights: first pyramid level must have <= 64 channels"; return false; }
+    for (int k = 0; k < 4; ++k)
+        if (net.dec[k] % 4 != 0 || net.dec[k] <= 0) { err = "weights: decoder widths must be multiples of 4"; return false; }
+    for (int l = lv; l >= 2; --l) {
+        const HostLayer *E = &net.layers[3 * lv + 5 * (lv - l)];
+        const int c0 = D + net.chans[l - 1] + 2;
+        if (E[0].cin != c0 || E[0].cout != net.dec[0] || E[1].cin != net.dec[0] || E[1].cout != net.dec[1] ||
+            E[2].cin != net.dec[1] || E[2].cout != net.dec[2] || E[3].cin != net.dec[2] + net.dec[1] ||
+            E[3].cout != net.dec[3] || E[4].cin != net.dec[3] + net.dec[2] || E[4].cout != 2) {
+            err = "weights: estimator layer shapes do not match the architecture"; return false;
+        }
+        for (int j = 0; j < 5; ++j)
+            if (E[j].stride != 1) { err = "weights: estimator convs must have stride 1"; return false; }
+    }
+    return true;
+}
+
+// [9 * cin_pad][cout] layout for the SIMT conv; input channel ci of the buffer maps to
+// channel perm[ci] of the file's layer (-1 = zero padding).  bf16 = round weights to
+// bfloat16 values (the BF16 path's operands).
+static std::vector<float> simt_weights(const HostLayer &L, const std::vector<int> &perm, bool bf16) {
+    const int cp = (int)perm.size();
+    std::vector<float> out((size_t)9 * cp * L.cout, 0.f);
+    for (int tap = 0; tap < 9; ++tap)
+        for (int ci = 0; ci < cp; ++ci) {
+            const int c = perm[ci];
+            if (c < 0) continue;
+            for (int o = 0; o < L.cout; ++o) {
+                float v = L.w[(((size_t)o * L.cin + c) * 3 + tap / 3) * 3 + tap % 3];
+                if (bf16) v = __bfloat162float(__float2bfloat16_rn(v));
+                out[((size_t)tap * cp + ci) * L.cout + o] = v;
+            }
+        }
+    return out;
+}
+
+static std::vector<int> iota_perm(int n, int pad_to) {
+    std::vector<int> p(pad_to, -1);
+    for (int i = 0; i < n; ++i) p[i] = i;
+    return p;
+}
+
+static inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+}  // namespace tc
+
+using namespace tc;
+
+// ------------------------------------------------------------------------------- stream
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct LevelBufs {
+    int h = 0, w = 0, c = 0;
+    void *pyr = nullptr;   // [2 slots][h][w][c]
+    void *tmpA = nullptr;  // [h][w][c]
+    void *tmpB = nullptr;
+    // estimator (l >= 2)
+    int x0p = 0, ctot = 0;
+    int off_x1 = 0, off_x2 = 0, off_x3 = 0, off_x4 = 0;
+    void *dec = nullptr;   // [2 dirs][h][w][ctot]
+    void *f2w = nullptr;   // [2][h][w][c]
+    float *flow = nullptr; // [2][h][w][2]
+    float *up = nullptr;   // [2][h][w][2]
+    // device weights of the estimator
+    float *wk[4] = {nullptr, nullptr, nullptr, nullptr};
+    float *bias[4] = {nullptr, nullptr, nullptr, nullptr};
+    float *head_w = nullptr, *head_b = nullptr;
+    TcConvPlan tcplan[4];
+};
+
+}  // namespace
+
+struct tc_stream {
+    int W = 0, H = 0, Wp = 0, Hp = 0;
+    tc_precision prec = TC_FP32;
+    cudaStream_t st = nullptr;
+    HostNet net;
+    int L = 0, R = 0, D = 0;
+    tc_consistency params{};
+    std::vector<void *> allocs;
+    std::vector<LevelBufs> lv;  // index l-1
+    // pyramid weights per level (3 convs)
+    std::vector<float *> pyr_w, pyr_b;
+    TcConvPlan pyr_plan[8][3];
+    // state ring: [2 slots] planar (3, H, W)
+    float *sI[2] = {nullptr, nullptr}, *sP[2] = {nullptr, nullptr}, *sO[2] = {nullptr, nullptr};
+    // staging for the host entry point
+    float *hI = nullptr, *hP = nullptr, *hO = nullptr, *hwc = nullptr;
+    uint8_t *hmask = nullptr;
+    long long t = 0;
+    bool poisoned = false;
+    bool use_tc = false;
+    int launches = 0;
+    std::string err;
+    // per-stage timing (tc_set_profiling): events around every launch, folded lazily
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_cat;       // category of pending pair k (events 2k, 2k+1)
+    double prof_ms[TC_PROF_CATEGORIES] = {0};
+    long long prof_n[TC_PROF_CATEGORIES] = {0};
+};
+
+static std::mutex g_err_mu;
+static std::string g_err;
+
+static tc_status fail(tc_stream *s, tc_status code, const std::string &msg) {
+    if (s) {
+        s->err = msg;
+        if (code == TC_ERR_CUDA) s->poisoned = true;
+    } else {
+        std::lock_guard<std::mutex> lk(g_err_mu);
+        g_err = msg;
+    }
+    return code;
+}
+
+static tc_status cuda_fail(tc_stream *s, cudaError_t e, const char *what) {
+    return fail(s, TC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define TC_TRY(stream, expr, what)                                  \
+    do {                                                            \
+        cudaError_t _e = (expr);                                    \
+        if (_e != cudaSuccess) return cuda_fail(stream, _e, what);  \
+    } while (0)
+
+static tc_status dalloc(tc_stream *s, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(s, TC_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    s->allocs.push_back(*p);
+    return TC_OK;
+}
+
+template <typename P>
+static tc_status dalloc_t(tc_stream *s, P **p, size_t bytes) {
+    void *v = nullptr;
+    tc_status r = dalloc(s, &v, bytes);
+    *p = static_cast<P *>(v);
+    return r;
+}
+
+static tc_status upload(tc_stream *s, float **dst, const std::vector<float> &v) {
+    tc_status r = dalloc_t(s, dst, v.size() * sizeof(float));
+    if (r != TC_OK) return r;
+    TC_TRY(s, cudaMemcpy(*dst, v.data(), v.size() * sizeof(float), cudaMemcpyHostToDevice), "weight upload");
+    return TC_OK;
+}
+
+static void free_all(tc_stream *s) {
+    for (void *p : s->allocs) cudaFree(p);
+    s->allocs.clear();
+}
+
+extern "C" void tc_default_consistency(tc_consistency *p) {
+    if (!p) return;
+    p->k1 = 0.3f;
+    p->k2 = 0.5f;
+    p->alpha = 6.5e3f;
+    p->lambda = 2.0f;
+    p->fb_check = 1;
+    p->fb_c1 = 0.01f;
+    p->fb_c2 = 0.5f;
+    p->solver_iters = 0;
+    p->eta = 0.15f;
+    p->kappa = 0.2f;
+}
+
+static bool valid_params(const tc_consistency *p, std::string &why) {
+    auto finite = [](float v) { return std::isfinite(v); };
+    if (!finite(p->k1) || !finite(p->alpha) || !finite(p->lambda) || !finite(p->fb_c1) || !finite(p->fb_c2)) {
+        why = "consistency parameters must be finite";
+        return false;
+    }
+    if (p->k1 < 0.f || p->k1 > 1.f) { why = "k1 must lie in [0, 1]"; return false; }
+    if (p->alpha < 0.f || p->lambda < 0.f) { why = "alpha and lambda must be >= 0"; return false; }
+    if (p->solver_iters != 0) { why = "the screened-Poisson solver is not part of this library (solver_iters must be 0)"; return false; }
+    return true;
+}
+
+extern "C" tc_status tc_set_consistency(tc_stream *s, const tc_consistency *p) {
+    if (!s || !p) return fail(s, TC_ERR_INVALID_ARG, "tc_set_consistency: NULL argument");
+    std::string why;
+    if (!valid_params(p, why)) return fail(s, TC_ERR_INVALID_ARG, why);
+    s->params = *p;
+    return TC_OK;
+}
+
+template <typename T>
+static tc_status build_stream(tc_stream *s) {
+    const HostNet &net = s->net;
+    const bool bf = s->prec != TC_FP32;
+    const size_t es = sizeof(T);
+    const int L = s->L, D = s->D;
+    s->lv.resize(L);
+    s->pyr_w.assign(3 * L, nullptr);
+    s->pyr_b.assign(3 * L, nullptr);
+    tc_status r;
+    for (int l = 1; l <= L; ++l) {
+        LevelBufs &B = s->lv[l - 1];
+        B.h = s->Hp >> l;
+        B.w = s->Wp >> l;
+        B.c = net.chans[l - 1];
+        const size_t px = (size_t)B.h * B.w;
+        if ((r = dalloc(s, &B.pyr, 2 * px * B.c * es)) != TC_OK) return r;
+        if ((r = dalloc(s, &B.tmpA, px * B.c * es)) != TC_OK) return r;
+        if ((r = dalloc(s, &B.tmpB, px * B.c * es)) != TC_OK) return r;
+        for (int j = 0; j < 3; ++j) {
+            const HostLayer &HL = net.layers[3 * (l - 1) + j];
+            std::vector<float> wk;
+            if (l == 1 && j == 0) {
+                // [27][cout], k = c * 9 + tap
+                wk.assign(27 * HL.cout, 0.f);
+                for (int o = 0; o < HL.cout; ++o)
+                    for (int k = 0; k < 27; ++k) {
+                        float v = HL.w[(size_t)o * 27 + k];
+                        if (bf) v = __bfloat162float(__float2bfloat16_rn(v));
+                        wk[(size_t)k * HL.cout + o] = v;
+                    }
+            } else {
+                wk = simt_weights(HL, iota_perm(HL.cin, HL.cin), bf);
+            }
+            if ((r = upload(s, &s->pyr_w[3 * (l - 1) + j], wk)) != TC_OK) return r;
+            if ((r = upload(s, &s->pyr_b[3 * (l - 1) + j], HL.b)) != TC_OK) return r;
+        }
+        if (l < 2) continue;
+        // Estimator buffers: x0 = [corr D | self c | up 2 | zero pad] then x1..x4.
+        B.x0p = round_up(D + B.c + 2, 8);
+        B.off_x1 = B.x0p;
+        B.off_x2 = B.off_x1 + net.dec[0];
+        B.off_x3 = B.off_x2 + net.dec[1];
+        B.off_x4 = B.off_x3 + net.dec[2];
+        B.ctot = B.off_x4 + net.dec[3];
+        if ((r = dalloc(s, &B.dec, 2 * px * B.ctot * es)) != TC_OK) return r;
+        TC_TRY(s, cudaMemset(B.dec, 0, 2 * px * B.ctot * es), "memset");
+        if ((r = dalloc(s, &B.f2w, 2 * px * B.c * es)) != TC_OK) return r;
+        if ((r = dalloc_t(s, &B.flow, 2 * px * 2 * sizeof(float))) != TC_OK) return r;
+        if ((r = dalloc_t(s, &B.up, 2 * px * 2 * sizeof(float))) != TC_OK) return r;
+        TC_TRY(s, cudaMemset(B.up, 0, 2 * px * 2 * sizeof(float)), "memset");
+        const HostLayer *E = &net.layers[3 * L + 5 * (L - l)];
+        // conv1 reads x0 (padded to x0p), conv2 x1, conv3 x2, conv4 [x2 | x3], head [x3 | x4].
+        std::vector<int> p1 = iota_perm(E[0].cin, B.x0p);
+        std::vector<int> p4(net.dec[1] + net.dec[2]);
+        for (int i = 0; i < net.dec[1]; ++i) p4[i] = net.dec[2] + i;          // x2 = file channels [dec2, dec2+dec1)
+        for (int i = 0; i < net.dec[2]; ++i) p4[net.dec[1] + i] = i;          // x3 = file channels [0, dec2)
+        std::vector<int> p5(net.dec[2] + net.dec[3]);
+        for (int i = 0; i < net.dec[2]; ++i) p5[i] = net.dec[3] + i;          // x3 = file channels [dec3, dec3+dec2)
+        for (int i = 0; i < net.dec[3]; ++i) p5[net.dec[2] + i] = i;          // x4 = file channels [0, dec3)
+        const std::vector<int> perms[4] = {p1, iota_perm(E[1].cin, E[1].cin), iota_perm(E[2].cin, E[2].cin), p4};
+        for (int j = 0; j < 4; ++j) {
+            if ((r = upload(s, &B.wk[j], simt_weights(E[j], perms[j], bf))) != TC_OK) return r;
+            if ((r = upload(s, &B.bias[j], E[j].b)) != TC_OK) return r;
+        }
+        if ((r = upload(s, &B.head_w, simt_weights(E[4], p5, bf))) != TC_OK) return r;
+        if ((r = upload(s, &B.head_b, E[4].b)) != TC_OK) return r;
+    }
+    const size_t img = (size_t)3 * s->H * s->W * sizeof(float);
+    for (int k = 0; k < 2; ++k) {
+        if ((r = dalloc_t(s, &s->sI[k], img)) != TC_OK) return r;
+        if ((r = dalloc_t(s, &s->sP[k], img)) != TC_OK) return r;
+        if ((r = dalloc_t(s, &s->sO[k], img)) != TC_OK) return r;
+    }
+    return TC_OK;
+}
+
+extern "C" tc_status tc_create_stream(const tc_stream_desc *desc, void *cuda_stream, tc_stream **out) {
+    if (out) *out = nullptr;
+    if (!desc || !out) return fail(nullptr, TC_ERR_INVALID_ARG, "tc_create_stream: NULL argument");
+    if (desc->precision != TC_FP32 && desc->precision != TC_BF16)
+        return fail(nullptr, desc->precision == TC_FP8_E4M3 ? TC_ERR_UNSUPPORTED : TC_ERR_INVALID_ARG,
+                    "tc_create_stream: precision must be TC_FP32 or TC_BF16");
+    std::unique_ptr<tc_stream> s(new (std::nothrow) tc_stream());
+    if (!s) return fail(nullptr, TC_ERR_OOM, "tc_create_stream: host allocation failed");
+    std::vector<uint8_t> blob;
+    if (desc->weights_path) {
+        FILE *f = fopen(desc->weights_path, "rb");
+        if (!f) return fail(nullptr, TC_ERR_IO, std::string("cannot open weights file ") + desc->weights_path);
+        fseek(f, 0, SEEK_END);
+        long n = ftell(f);
+        fseek(f, 0, SEEK_SET);
+        blob.resize(n > 0 ? (size_t)n : 0);
+        size_t got = n > 0 ? fread(blob.data(), 1, (size_t)n, f) : 0;
+        fclose(f);
+        if (got != blob.size()) return fail(nullptr, TC_ERR_IO, "short read of the weights file");
+    } else if (desc->weights_blob && desc->weights_bytes) {
+        blob.assign((const uint8_t *)desc->weights_blob, (const uint8_t *)desc->weights_blob + desc->weights_bytes);
+    } else {
+        return fail(nullptr, TC_ERR_INVALID_ARG, "tc_create_stream: no weights given");
+    }
+    std::string err;
+    if (!parse_weights(blob.data(), blob.size(), s->net, err)) return fail(nullptr, TC_ERR_IO, err);
+    s->L = s->net.levels;
+    s->R = s->net.radius;
+    s->D = (2 * s->R + 1) * (2 * s->R + 1);
+    const int m = 1 << s->L;
+    if (desc->width < m || desc->height < m || desc->width > 16384 || desc->height > 16384)
+        return fail(nullptr, TC_ERR_INVALID_ARG, "tc_create_stream: width and height must lie in [2^levels, 16384]");
+    s->W = desc->width;
+    s->H = desc->height;
+    s->Wp = round_up(s->W, m);
+    s->Hp = round_up(s->H, m);
+    s->prec = desc->precision;
+    s->st = static_cast<cudaStream_t>(cuda_stream);
+    tc_default_consistency(&s->params);
+    tc_status r = s->prec == TC_FP32 ? build_stream<float>(s.get()) : build_stream<__nv_bfloat16>(s.get());
+    if (r != TC_OK) {
+        std::string msg = s->err;
+        free_all(s.get());
+        return fail(nullptr, r, msg);
+    }
+    if (s->prec == TC_BF16) {
+        r = (tc_status)tc_prepare_tensor_core_path(s.get());
+        if (r != TC_OK) {
+            std::string msg = s->err;
+            free_all(s.get());
+            return fail(nullptr, r, msg);
+        }
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_all(s.get());
+        return fail(nullptr, TC_ERR_CUDA, std::string("tc_create_stream: ") + cudaGetErrorString(e));
+    }
+    *out = s.release();
+    return TC_OK;
+}
+
+// Folds the pending profiling events of s into its per-category totals.
+static tc_status prof_flush(tc_stream *s) {
+    const size_t n = s->ev_cat.size();
+    if (n == 0) return TC_OK;
+    TC_TRY(s, cudaEventSynchronize(s->ev_pool[2 * n - 1]), "profiling event synchronize");
+    for (size_t k = 0; k < n; ++k) {
+        float ms = 0.f;
+        TC_TRY(s, cudaEventElapsedTime(&ms, s->ev_pool[2 * k], s->ev_pool[2 * k + 1]), "profiling elapsed time");
+        s->prof_ms[s->ev_cat[k]] += ms;
+        s->prof_n[s->ev_cat[k]] += 1;
+    }
+    s->ev_cat.clear();
+    return TC_OK;
+}
+
+static tc_status prof_begin(tc_stream *s, int cat) {
+    const size_t k = s->ev_cat.size();
+    while (s->ev_pool.size() < 2 * (k + 1)) {
+        cudaEvent_t e;
+        TC_TRY(s, cudaEventCreate(&e), "cudaEventCreate");
+        s->ev_pool.push_back(e);
+    }
+    s->ev_cat.push_back(cat);
+    TC_TRY(s, cudaEventRecord(s->ev_pool[2 * k], s->st), "cudaEventRecord");
+    return TC_OK;
+}
+
+static tc_status prof_end(tc_stream *s) {
+    TC_TRY(s, cudaEventRecord(s->ev_pool[2 * (s->ev_cat.size() - 1) + 1], s->st), "cudaEventRecord");
+    return TC_OK;
+}
+
+#define TC_LAUNCH_CAT(s, cat, expr)                                               \
+    do {                                                                          \
+        if ((s)->prof) {                                                          \
+            tc_status _r = prof_begin(s, cat);                                    \
+            if (_r != TC_OK) return _r;                                           \
+        }                                                                         \
+        cudaError_t _e = (expr);                                                  \
+        ++(s)->launches;                                                          \
+        if (_e != cudaSuccess) return cuda_fail(s, _e, "kernel launch");          \
+        if ((s)->prof) {                                                          \
+            tc_status _r = prof_end(s);                                           \
+            if (_r != TC_OK) return _r;                                           \
+        }                                                                         \
+    } while (0)
+#define TC_LAUNCH(s, expr) TC_LAUNCH_CAT(s, TC_PROF_OTHER, expr)
+
+template <typename T>
+static tc_status conv_layer(tc_stream *s, const ConvArgs &a, const TcConvPlan *plan, int cat) {
+    if (plan && plan->enabled) {
+        TC_LAUNCH_CAT(s, cat, launch_conv_tc(*plan, a, s->st));
+    } else {
+        TC_LAUNCH_CAT(s, cat, launch_conv_simt<T>(a, s->st));
+    }
+    return TC_OK;
+}
+
+template <typename T>
+static tc_status run_pyramid(tc_stream *s, const float *img, int slot) {
+    tc_status r;
+    for (int l = 1; l <= s->L; ++l) {
+        LevelBufs &B = s->lv[l - 1];
+        const size_t px = (size_t)B.h * B.w;
+        T *dst = static_cast<T *>(B.pyr) + (size_t)slot * px * B.c;
+        if (l == 1) {
+            ConvFirstArgs f{img, s->H, s->W, s->Hp, s->Wp, s->pyr_w[0], s->pyr_b[0], B.c, B.tmpA};
+            TC_LAUNCH_CAT(s, TC_PROF_PYRAMID_CONV, launch_conv_first<T>(f, s->st));
+        } else {
+            LevelBufs &P = s->lv[l - 2];
+            const T *src = static_cast<const T *>(P.pyr) + (size_t)slot * P.h * P.w * P.c;
+            ConvArgs a{src, P.c, 1, P.h, P.w, P.c, 2, B.h, B.w, s->pyr_w[3 * (l - 1)], s->pyr_b[3 * (l - 1)],
+                       B.c, B.tmpA, B.c, 1};
+            if ((r = conv_layer<T>(s, a, &s->pyr_plan[l - 1][0], TC_PROF_PYRAMID_CONV)) != TC_OK) return r;
+        }
+        ConvArgs b{B.tmpA, B.c, 1, B.h, B.w, B.c, 1, B.h, B.w, s->pyr_w[3 * (l - 1) + 1], s->pyr_b[3 * (l - 1) + 1],
+                   B.c, B.tmpB, B.c, 1};
+        if ((r = conv_layer<T>(s, b, &s->pyr_plan[l - 1][1], TC_PROF_PYRAMID_CONV)) != TC_OK) return r;
+        ConvArgs c{B.tmpB, B.c, 1, B.h, B.w, B.c, 1, B.h, B.w, s->pyr_w[3 * (l - 1) + 2], s->pyr_b[3 * (l - 1) + 2],
+                   B.c, dst, B.c, 1};
+        if ((r = conv_layer<T>(s, c, &s->pyr_plan[l - 1][2], TC_PROF_PYRAMID_CONV)) != TC_OK) return r;
+    }
+    return TC_OK;
+}
+
+// Both directions at once (batch entry 0: self = frame t, other = t-1, giving F_{t->t-1};
+// entry 1: self = t-1, other = t, giving F_{t-1->t}).
+template <typename T>
+static tc_status run_estimators(tc_stream *s, int slot_cur) {
+    tc_status r;
+    const HostNet &net = s->net;
+    for (int l = s->L; l >= 2; --l) {
+        LevelBufs &B = s->lv[l - 1];
+        const size_t px = (size_t)B.h * B.w;
+        const T *pyr = static_cast<const T *>(B.pyr);
+        const T *self_p[2] = {pyr + (size_t)slot_cur * px * B.c, pyr + (size_t)(slot_cur ^ 1) * px * B.c};
+        const T *other_p[2] = {self_p[1], self_p[0]};
+        T *dec = static_cast<T *>(B.dec);
+        const void *fo[2] = {other_p[0], other_p[1]};
+        int fo_cs = B.c;
+        if (l < s->L) {
+            LevelBufs &C = s->lv[l];
+            UpArgs u{C.flow, 2, C.h, C.w, 2, B.up, dec + s->D + B.c, B.ctot};
+            TC_LAUNCH_CAT(s, TC_PROF_UPSAMPLE, launch_up<T>(u, s->st));
+            WarpArgs wa{{other_p[0], other_p[1]}, B.c, B.up, 2, B.h, B.w, B.c, B.f2w, B.c};
+            TC_LAUNCH_CAT(s, TC_PROF_WARP, launch_warp<T>(wa, s->st));
+            fo[0] = static_cast<T *>(B.f2w);
+            fo[1] = static_cast<T *>(B.f2w) + px * B.c;
+        }
+        CorrArgs ca{{self_p[0], self_p[1]}, {fo[0], fo[1]}, B.c, fo_cs, 2, B.h, B.w, B.c, s->R, dec, B.ctot,
+                    dec + s->D};
+        TC_LAUNCH_CAT(s, TC_PROF_CORRELATION, launch_corr<T>(ca, s->st));
+        ConvArgs c1{dec, B.ctot, 2, B.h, B.w, B.x0p, 1, B.h, B.w, B.wk[0], B.bias[0], net.dec[0], dec + B.off_x1, B.ctot, 1};
+        if ((r = conv_layer<T>(s, c1, &B.tcplan[0], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
+        ConvArgs c2{dec + B.off_x1, B.ctot, 2, B.h, B.w, net.dec[0], 1, B.h, B.w, B.wk[1], B.bias[1], net.dec[1], dec + B.off_x2, B.ctot, 1};
+        if ((r = conv_layer<T>(s, c2, &B.tcplan[1], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
+        ConvArgs c3{dec + B.off_x2, B.ctot, 2, B.h, B.w, net.dec[1], 1, B.h, B.w, B.wk[2], B.bias[2], net.dec[2], dec + B.off_x3, B.ctot, 1};
+        if ((r = conv_layer<T>(s, c3, &B.tcplan[2], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
+        ConvArgs c4{dec + B.off_x2, B.ctot, 2, B.h, B.w, net.dec[1] + net.dec[2], 1, B.h, B.w, B.wk[3], B.bias[3], net.dec[3], dec + B.off_x4, B.ctot, 1};
+        if ((r = conv_layer<T>(s, c4, &B.tcplan[3], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
+        HeadArgs ha{dec + B.off_x3, B.ctot, net.dec[2] + net.dec[3], 2, B.h, B.w, B.head_w, B.head_b,
+                    l < s->L ? B.up : nullptr, B.flow};
+        TC_LAUNCH_CAT(s, TC_PROF_HEAD, launch_head<T>(ha, s->st));
+    }
+    return TC_OK;
+}
+
+static tc_status check_stream(tc_stream *s, const char *fn) {
+    if (!s) return fail(nullptr, TC_ERR_INVALID_ARG, std::string(fn) + ": NULL stream");
+    if (s->poisoned) return fail(s, TC_ERR_STATE, std::string(fn) + ": stream is poisoned by an earlier CUDA error: " + s->err);
+    return TC_OK;
+}
+
+template <typename T>
+static tc_status process(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask) {
+    tc_status r;
+    s->launches = 0;
+    if (s->ev_cat.size() > 4096 && (r = prof_flush(s)) != TC_OK) return r;
+    const int cur = (int)(s->t & 1), prev = cur ^ 1;
+    if ((r = run_pyramid<T>(s, I, cur)) != TC_OK) return r;
+    ConsistArgs ca{};
+    ca.It = I; ca.Pt = P;
+    ca.H = s->H; ca.W = s->W;
+    ca.k1 = s->params.k1; ca.alpha = s->params.alpha; ca.lambda = s->params.lambda;
+    ca.c1 = s->params.fb_c1; ca.c2 = s->params.fb_c2; ca.fb_check = s->params.fb_check;
+    ca.O = O; ca.wc = wc; ca.mask = mask;
+    ca.sI = s->sI[cur]; ca.sP = s->sP[cur]; ca.sO = s->sO[cur];
+    if (s->t == 0) {
+        ca.first = 1;
+        ca.Fb = ca.Ff = nullptr;
+        ca.fh = ca.fw = 1; ca.scale = 1;
+        ca.Ip = ca.Pp = ca.Op = nullptr;
+    } else {
+        if ((r = run_estimators<T>(s, cur)) != TC_OK) return r;
+        LevelBufs &B2 = s->lv[1];
+        ca.first = 0;
+        ca.Ip = s->sI[prev]; ca.Pp = s->sP[prev]; ca.Op = s->sO[prev];
+        ca.Fb = B2.flow;
+        ca.Ff = B2.flow + (size_t)B2.h * B2.w * 2;
+        ca.fh = B2.h; ca.fw = B2.w; ca.scale = 4;
+    }
+    TC_LAUNCH_CAT(s, TC_PROF_CONSISTENCY, launch_consistency(ca, s->st));
+    s->t += 1;
+    return TC_OK;
+}
+
+extern "C" tc_status tc_process_frame(tc_stream *s, const float *I_t, const float *P_t, float *O_t,
+                                      float *wc_opt, uint8_t *mask_opt) {
+    tc_status r = check_stream(s, "tc_process_frame");
+    if (r != TC_OK) return r;
+    if (!I_t || !P_t || !O_t) return fail(s, TC_ERR_INVALID_ARG, "tc_process_frame: NULL image pointer");
+    return s->prec == TC_FP32 ? process<float>(s, I_t, P_t, O_t, wc_opt, mask_opt)
+                              : process<__nv_bfloat16>(s, I_t, P_t, O_t, wc_opt, mask_opt);
+}
+
+extern "C" tc_status tc_process_frame_host(tc_stream *s, const float *I_t, const float *P_t, float *O_t,
+                                           float *wc_opt, uint8_t *mask_opt) {
+    tc_status r = check_stream(s, "tc_process_frame_host");
+    if (r != TC_OK) return r;
+    if (!I_t || !P_t || !O_t) return fail(s, TC_ERR_INVALID_ARG, "tc_process_frame_host: NULL image pointer");
+    const size_t img = (size_t)3 * s->H * s->W * sizeof(float), plane = (size_t)s->H * s->W;
+    if (!s->hI) {
+        if ((r = dalloc_t(s, &s->hI, img)) != TC_OK) return r;
+        if ((r = dalloc_t(s, &s->hP, img)) != TC_OK) return r;
+        if ((r = dalloc_t(s, &s->hO, img)) != TC_OK) return r;
+        if ((r = dalloc_t(s, &s->hwc, plane * sizeof(float))) != TC_OK) return r;
+        if ((r = dalloc_t(s, &s->hmask, plane)) != TC_OK) return r;
+    }
+    TC_TRY(s, cudaMemcpyAsync(s->hI, I_t, img, cudaMemcpyHostToDevice, s->st), "H2D I_t");
+    TC_TRY(s, cudaMemcpyAsync(s->hP, P_t, img, cudaMemcpyHostToDevice, s->st), "H2D P_t");
+    r = tc_process_frame(s, s->hI, s->hP, s->hO, wc_opt ? s->hwc : nullptr, mask_opt ? s->hmask : nullptr);
+    if (r != TC_OK) return r;
+    TC_TRY(s, cudaMemcpyAsync(O_t, s->hO, img, cudaMemcpyDeviceToHost, s->st), "D2H O_t");
+    if (wc_opt) TC_TRY(s, cudaMemcpyAsync(wc_opt, s->hwc, plane * sizeof(float), cudaMemcpyDeviceToHost, s->st), "D2H w_c");
+    if (mask_opt) TC_TRY(s, cudaMemcpyAsync(mask_opt, s->hmask, plane, cudaMemcpyDeviceToHost, s->st), "D2H mask");
+    TC_TRY(s, cudaStreamSynchronize(s->st), "stream synchronize");
+    return TC_OK;
+}
+
+extern "C" tc_status tc_get_flows(tc_stream *s, float *Fb, float *Ff) {
+    tc_status r = check_stream(s, "tc_get_flows");
+    if (r != TC_OK) return r;
+    if (s->t < 2) return fail(s, TC_ERR_STATE, "tc_get_flows: no flow before the second frame");
+    LevelBufs &B2 = s->lv[1];
+    if (Fb) TC_LAUNCH(s, launch_flow_out(B2.flow, B2.h, B2.w, 4, s->H, s->W, Fb, s->st));
+    if (Ff) TC_LAUNCH(s, launch_flow_out(B2.flow + (size_t)B2.h * B2.w * 2, B2.h, B2.w, 4, s->H, s->W, Ff, s->st));
+    return TC_OK;
+}
+
+extern "C" tc_status tc_destroy(tc_stream *s) {
+    if (!s) return fail(nullptr, TC_ERR_INVALID_ARG, "tc_destroy: NULL stream");
+    if (s->st) cudaStreamSynchronize(s->st);
+    else cudaDeviceSynchronize();
+    for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+    free_all(s);
+    delete s;
+    return TC_OK;
+}
+
+extern "C" tc_status tc_set_profiling(tc_stream *s, int enable) {
+    tc_status r = check_stream(s, "tc_set_profiling");
+    if (r != TC_OK) return r;
+    if ((r = prof_flush(s)) != TC_OK) return r;
+    s->prof = enable != 0;
+    for (int k = 0; k < TC_PROF_CATEGORIES; ++k) {
+        s->prof_ms[k] = 0.0;
+        s->prof_n[k] = 0;
+    }
+    return TC_OK;
+}
+
+extern "C" tc_status tc_get_profile(tc_stream *s, double *ms, long long *launches, int n) {
+    tc_status r = check_stream(s, "tc_get_profile");
+    if (r != TC_OK) return r;
+    if (!ms || n < 1) return fail(s, TC_ERR_INVALID_ARG, "tc_get_profile: bad argument");
+    if ((r = prof_flush(s)) != TC_OK) return r;
+    for (int k = 0; k < n && k < TC_PROF_CATEGORIES; ++k) {
+        ms[k] = s->prof_ms[k];
+        if (launches) launches[k] = s->prof_n[k];
+    }
+    return TC_OK;
+}
+
+extern "C" const char *tc_last_error(const tc_stream *s) {
+    if (s) return s->err.c_str();
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    return g_err.c_str();
+}
+
+extern "C" int tc_last_launch_count(const tc_stream *s) { return s ? s->launches : 0; }
+
+// Accessors used by the tensor-core planner (conv_tc.cu).
+int tc_stream_levels(const tc_stream *s) { return s->L; }
+
+// ------------------------------------------------------------------------------- stage ops
+
+namespace {
+struct TmpAlloc {
+    std::vector<void *> ps;
+    ~TmpAlloc() {
+        for (void *p : ps) cudaFree(p);
+    }
+    cudaError_t get(void **p, size_t bytes) {
+        cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+        if (e == cudaSuccess) ps.push_back(*p);
+        return e;
+    }
+};
+}  // namespace
+
+#define OP_TRY(expr, what)                                               \
+    do {                                                                 \
+        cudaError_t _e = (expr);                                         \
+        if (_e != cudaSuccess) return cuda_fail(nullptr, _e, what);      \
+    } while (0)
+
+template <typename T>
+static tc_status op_conv(const float *in, int n, int h, int w, int cin, const float *w_oihw, const float *bias,
+                         int cout, int stride, int leaky, float *out, cudaStream_t st) {
+    HostLayer L;
+    L.cout = cout; L.cin = cin; L.stride = stride; L.leaky = leaky;
+    L.w.assign(w_oihw, w_oihw + (size_t)cout * cin * 9);
+    L.b.assign(bias, bias + cout);
+    const bool bf = sizeof(T) == 2;
+    const int cin_p = round_up(cin, 4), cout_p = round_up(cout, 4);
+    const int ho = (h - 1) / stride + 1, wo = (w - 1) / stride + 1;
+    std::vector<float> wk = simt_weights(L, iota_perm(cin, cin_p), bf);
+    // pad cout to a multiple of 4
+    std::vector<float> wkp((size_t)9 * cin_p * cout_p, 0.f), bp(cout_p, 0.f);
+    for (size_t k = 0; k < (size_t)9 * cin_p; ++k)
+        for (int o = 0; o < cout; ++o) wkp[k * cout_p + o] = wk[k * cout + o];
+    for (int o = 0; o < cout; ++o) bp[o] = bias[o];
+    TmpAlloc tmp;
+    float *dw, *db;
+    T *din, *dout;
+    OP_TRY(tmp.get((void **)&dw, wkp.size() * 4), "tc_op_conv3x3 alloc");
+    OP_TRY(tmp.get((void **)&db, bp.size() * 4), "tc_op_conv3x3 alloc");
+    OP_TRY(cudaMemcpyAsync(dw, wkp.data(), wkp.size() * 4, cudaMemcpyHostToDevice, st), "tc_op_conv3x3 copy");
+    OP_TRY(cudaMemcpyAsync(db, bp.data(), bp.size() * 4, cudaMemcpyHostToDevice, st), "tc_op_conv3x3 copy");
+    const size_t nin = (size_t)n * h * w * cin_p, nout = (size_t)n * ho * wo * cout_p;
+    OP_TRY(tmp.get((void **)&din, nin * sizeof(T)), "tc_op_conv3x3 alloc");
+    OP_TRY(tmp.get((void **)&dout, nout * sizeof(T)), "tc_op_conv3x3 alloc");
+    // Repack the input to cin_p channels in the activation type.
+    std::vector<float> dummy;
+    if (cin_p == cin) {
+        OP_TRY(launch_to_act<T>(in, nin, din, st), "tc_op_conv3x3 convert");
+    } else {
+        float *tmpf;
+        OP_TRY(tmp.get((void **)&tmpf, nin * 4), "tc_op_conv3x3 alloc");
+        OP_TRY(cudaMemsetAsync(tmpf, 0, nin * 4, st), "tc_op_conv3x3 memset");
+        OP_TRY(cudaMemcpy2DAsync(tmpf, cin_p * 4, in, cin * 4, cin * 4, (size_t)n * h * w, cudaMemcpyDeviceToDevice, st),
+               "tc_op_conv3x3 repack");
+        OP_TRY(launch_to_act<T>(tmpf, nin, din, st), "tc_op_conv3x3 convert");
+    }
+    ConvArgs a{din, cin_p, n, h, w, cin_p, stride, ho, wo, dw, db, cout_p, dout, cout_p, leaky};
+    TcConvPlan plan;
+    bool use_tc = bf && tc_plan_conv(plan, a, /*tma_in=*/true);
+    if (use_tc) {
+        OP_TRY(launch_conv_tc(plan, a, st), "tc_op_conv3x3 tensor-core launch");
+    } else {
+        OP_TRY(launch_conv_simt<T>(a, st), "tc_op_conv3x3 launch");
+    }
+    float *outp;
+    if (cout_p == cout) {
+        OP_TRY(launch_from_act<T>(dout, nout, out, st), "tc_op_conv3x3 convert");
+    } else {
+        OP_TRY(tmp.get((void **)&outp, nout * 4), "tc_op_conv3x3 alloc");
+        OP_TRY(launch_from_act<T>(dout, nout, outp, st), "tc_op_conv3x3 convert");
+        OP_TRY(cudaMemcpy2DAsync(out, cout * 4, outp, cout_p * 4, cout * 4, (size_t)n * ho * wo, cudaMemcpyDeviceToDevice, st),
+               "tc_op_conv3x3 repack");
+    }
+    OP_TRY(cudaStreamSynchronize(st), "tc_op_conv3x3 sync");
+    return TC_OK;
+}
+
+extern "C" tc_status tc_op_conv3x3(tc_precision precision, const float *in, int n, int h, int w, int cin,
+                                   const float *w_oihw, const float *bias, int cout, int stride, int leaky,
+                                   float *out, void *cuda_stream) {
+    if (!in || !w_oihw || !bias || !out || n < 1 || h < 1 || w < 1 || cin < 1 || cout < 1 ||
+        (stride != 1 && stride != 2))
+        return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_conv3x3: bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (precision == TC_FP32) return op_conv<float>(in, n, h, w, cin, w_oihw, bias, cout, stride, leaky, out, st);
+    if (precision == TC_BF16) return op_conv<__nv_bfloat16>(in, n, h, w, cin, w_oihw, bias, cout, stride, leaky, out, st);
+    return fail(nullptr, TC_ERR_UNSUPPORTED, "tc_op_conv3x3: precision");
+}
+
+template <typename T>
+static tc_status op_corr(const float *f1, const float *f2, int n, int h, int w, int c, int r, float *out,
+                         cudaStream_t st) {
+    const int D = (2 * r + 1) * (2 * r + 1);
+    const size_t nf = (size_t)n * h * w * c, no = (size_t)n * h * w * D;
+    TmpAlloc tmp;
+    T *a, *b, *o;
+    OP_TRY(tmp.get((void **)&a, nf * sizeof(T)), "tc_op_correlation alloc");
+    OP_TRY(tmp.get((void **)&b, nf * sizeof(T)), "tc_op_correlation alloc");
+    OP_TRY(tmp.get((void **)&o, no * sizeof(T)), "tc_op_correlation alloc");
+    OP_TRY(launch_to_act<T>(f1, nf, a, st), "tc_op_correlation convert");
+    OP_TRY(launch_to_act<T>(f2, nf, b, st), "tc_op_correlation convert");
+    const size_t img = (size_t)h * w * c;
+    for (int i = 0; i < n; i += 2) {
+        const int nb = n - i < 2 ? n - i : 2;
+        CorrArgs ca{{a + i * img, a + (i + nb - 1) * img}, {b + i * img, b + (i + nb - 1) * img}, c, c, nb, h, w, c, r,
+                    o + (size_t)i * h * w * D, D, nullptr};
+        OP_TRY(launch_corr<T>(ca, st), "tc_op_correlation launch");
+    }
+    OP_TRY(launch_from_act<T>(o, no, out, st), "tc_op_correlation convert");
+    OP_TRY(cudaStreamSynchronize(st), "tc_op_correlation sync");
+    return TC_OK;
+}
+
+extern "C" tc_status tc_op_correlation(tc_precision precision, const float *f1, const float *f2, int n, int h,
+                                       int w, int c, int r, float *out, void *cuda_stream) {
+    if (!f1 || !f2 || !out || n < 1 || h < 1 || w < 1 || c < 4 || c % 4 != 0 || r < 1 || r > 4)
+        return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_correlation: bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (precision == TC_FP32) return op_corr<float>(f1, f2, n, h, w, c, r, out, st);
+    if (precision == TC_BF16) return op_corr<__nv_bfloat16>(f1, f2, n, h, w, c, r, out, st);
+    return fail(nullptr, TC_ERR_UNSUPPORTED, "tc_op_correlation: precision");
+}
+
+template <typename T>
+static tc_status op_warp(const float *f, const float *flow, int n, int h, int w, int c, float *out, cudaStream_t st) {
+    const size_t nf = (size_t)n * h * w * c;
+    TmpAlloc tmp;
+    T *a, *o;
+    OP_TRY(tmp.get((void **)&a, nf * sizeof(T)), "tc_op_warp_features alloc");
+    OP_TRY(tmp.get((void **)&o, nf * sizeof(T)), "tc_op_warp_features alloc");
+    OP_TRY(launch_to_act<T>(f, nf, a, st), "tc_op_warp_features convert");
+    const size_t img = (size_t)h * w * c;
+    for (int i = 0; i < n; i += 2) {
+        const int nb = n - i < 2 ? n - i : 2;
+        WarpArgs wa{{a + i * img, a + (i + nb - 1) * img}, c, flow + (size_t)i * h * w * 2, nb, h, w, c, o + i * img, c};
+        OP_TRY(launch_warp<T>(wa, st), "tc_op_warp_features launch");
+    }
+    OP_TRY(launch_from_act<T>(o, nf, out, st), "tc_op_warp_features convert");
+    OP_TRY(cudaStreamSynchronize(st), "tc_op_warp_features sync");
+    return TC_OK;
+}
+
+extern "C" tc_status tc_op_warp_features(tc_precision precision, const float *f, const float *flow, int n, int h,
+                                         int w, int c, float *out, void *cuda_stream) {
+    if (!f || !flow || !out || n < 1 || h < 1 || w < 1 || c < 4 || c % 4 != 0)
+        return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_warp_features: bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (precision == TC_FP32) return op_warp<float>(f, flow, n, h, w, c, out, st);
+    if (precision == TC_BF16) return op_warp<__nv_bfloat16>(f, flow, n, h, w, c, out, st);
+    return fail(nullptr, TC_ERR_UNSUPPORTED, "tc_op_warp_features: precision");
+}
+
+extern "C" tc_status tc_op_upsample_flow(const float *flow, int n, int h, int w, int s, float *out, void *cuda_stream) {
+    if (!flow || !out || n < 1 || h < 1 || w < 1 || (s != 2 && s != 4))
+        return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_upsample_flow: bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    UpArgs u{flow, n, h, w, s, out, nullptr, 0};
+    OP_TRY(launch_up<float>(u, st), "tc_op_upsample_flow launch");
+    return TC_OK;
+}
+
+extern "C" tc_status tc_op_consistency(const float *It, const float *Pt, const float *Ip, const float *Pp,
+                                       const float *Op, const float *Fb, const float *Ff, int h, int w, int fh,
+                                       int fw, int scale, const tc_consistency *p, float *O, float *wc_opt,
+                                       uint8_t *mask_opt, void *cuda_stream) {
+    if (!It || !Pt || !Ip || !Pp || !Op || !Fb || !Ff || !p || !O || h < 1 || w < 1 || fh < 1 || fw < 1 ||
+        scale < 1 || (scale & (scale - 1)) != 0 || (size_t)fh * scale < (size_t)h || (size_t)fw * scale < (size_t)w)
+        return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_consistency: bad argument");
+    std::string why;
+    if (!valid_params(p, why)) return fail(nullptr, TC_ERR_INVALID_ARG, why);
+    ConsistArgs ca{};
+    ca.It = It; ca.Pt = Pt; ca.Ip = Ip; ca.Pp = Pp; ca.Op = Op; ca.Fb = Fb; ca.Ff = Ff;
+    ca.H = h; ca.W = w; ca.fh = fh; ca.fw = fw; ca.scale = scale;
+    ca.k1 = p->k1; ca.alpha = p->alpha; ca.lambda = p->lambda; ca.c1 = p->fb_c1; ca.c2 = p->fb_c2;
+    ca.fb_check = p->fb_check; ca.first = 0;
+    ca.O = O; ca.wc = wc_opt; ca.mask = mask_opt;
+    OP_TRY(launch_consistency(ca, static_cast<cudaStream_t>(cuda_stream)), "tc_op_consistency launch");
+    return TC_OK;
+}

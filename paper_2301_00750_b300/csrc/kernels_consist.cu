@@ -1,0 +1,144 @@
+// Fused consistency step (Sec. 3.1, Eqs. 2-7 in causal form): final flow upsampling,
+// backward warp of I_{t-1}, P_{t-1}, O_{t-1}, forward-backward non-occlusion mask,
+// photometric weight, local/global blend, warped input and consistency weight, plus the
+// copies of I_t, P_t, O_t that the stream keeps for the next frame.  One pass over the
+// frame, one thread per pixel, float32 throughout.
+#include "common.cuh"
+
+namespace tc {
+
+// Bilinear interpolation weights and clamped tap positions for the sample x + u.  The
+// integer part floor(u) and the fraction u - floor(u) are exact in float32, so the taps and
+// weights equal those of the exact sample position.
+struct Taps {
+    int xa, xb, ya, yb;
+    float w00, w01, w10, w11;
+};
+
+__device__ __forceinline__ Taps clamp_taps(int x, int y, float u, float v, int W, int H) {
+    const float fu = floorf(u), fv = floorf(v);
+    const float ax = u - fu, ay = v - fv;
+    const int x0 = x + (int)fu, y0 = y + (int)fv;
+    Taps t;
+    t.xa = min(max(x0, 0), W - 1);
+    t.xb = min(max(x0 + 1, 0), W - 1);
+    t.ya = min(max(y0, 0), H - 1);
+    t.yb = min(max(y0 + 1, 0), H - 1);
+    t.w00 = (1.f - ax) * (1.f - ay);
+    t.w01 = ax * (1.f - ay);
+    t.w10 = (1.f - ax) * ay;
+    t.w11 = ax * ay;
+    return t;
+}
+
+__device__ __forceinline__ float gather(const float *p, int W, const Taps &t) {
+    float acc = t.w00 * __ldg(p + (size_t)t.ya * W + t.xa);
+    acc += t.w01 * __ldg(p + (size_t)t.ya * W + t.xb);
+    acc += t.w10 * __ldg(p + (size_t)t.yb * W + t.xa);
+    acc += t.w11 * __ldg(p + (size_t)t.yb * W + t.xb);
+    return acc;
+}
+
+__global__ void __launch_bounds__(256) consistency_kernel(ConsistArgs a) {
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (x >= a.W || y >= a.H) return;
+    const size_t hw = (size_t)a.H * a.W;
+    const size_t i = (size_t)y * a.W + x;
+    float It[3], Pt[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        It[c] = __ldg(a.It + c * hw + i);
+        Pt[c] = __ldg(a.Pt + c * hw + i);
+    }
+    if (a.first) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a.O[c * hw + i] = Pt[c];
+            if (a.sI) a.sI[c * hw + i] = It[c];
+            if (a.sP) a.sP[c * hw + i] = Pt[c];
+            if (a.sO) a.sO[c * hw + i] = Pt[c];
+        }
+        if (a.wc) a.wc[i] = 0.f;
+        if (a.mask) a.mask[i] = 0;
+        return;
+    }
+    float2 fb = upsampled_flow_at(a.Fb, a.fh, a.fw, a.scale, x, y);
+    // Keep the sample position finite and far outside the frame for absurd flows.
+    const float u = fminf(fmaxf(fb.x, -1e6f), 1e6f), v = fminf(fmaxf(fb.y, -1e6f), 1e6f);
+    // In bounds: 0 <= x + u <= W - 1 and 0 <= y + v <= H - 1, compared exactly.
+    const bool inb = u >= (float)(-x) && u <= (float)(a.W - 1 - x) && v >= (float)(-y) &&
+                     v <= (float)(a.H - 1 - y);
+    const Taps t = clamp_taps(x, y, u, v, a.W, a.H);
+    bool occ = false;
+    if (a.fb_check) {
+        const float2 f00 = upsampled_flow_at(a.Ff, a.fh, a.fw, a.scale, t.xa, t.ya);
+        const float2 f01 = upsampled_flow_at(a.Ff, a.fh, a.fw, a.scale, t.xb, t.ya);
+        const float2 f10 = upsampled_flow_at(a.Ff, a.fh, a.fw, a.scale, t.xa, t.yb);
+        const float2 f11 = upsampled_flow_at(a.Ff, a.fh, a.fw, a.scale, t.xb, t.yb);
+        float fu = t.w00 * f00.x;
+        fu += t.w01 * f01.x;
+        fu += t.w10 * f10.x;
+        fu += t.w11 * f11.x;
+        float fv = t.w00 * f00.y;
+        fv += t.w01 * f01.y;
+        fv += t.w10 * f10.y;
+        fv += t.w11 * f11.y;
+        const float su = u + fu, sv = v + fv;
+        const float lhs = su * su + sv * sv;
+        const float rhs = a.c1 * ((u * u + v * v) + (fu * fu + fv * fv)) + a.c2;
+        occ = lhs > rhs;
+    }
+    const bool m = inb && !occ;
+    float gI[3], gP[3], gO[3], d = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        gI[c] = gather(a.Ip + c * hw, a.W, t);
+        gP[c] = gather(a.Pp + c * hw, a.W, t);
+        gO[c] = gather(a.Op + c * hw, a.W, t);
+        const float e = It[c] - gI[c];
+        d += e * e;
+    }
+    float wp = 0.f;
+    if (m) wp = fminf(a.k1, expf(-a.alpha * d));
+    float dI = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float L = (1.f - wp) * Pt[c] + wp * gP[c];
+        const float A = wp * gO[c] + (1.f - wp) * L;
+        const float AI = (1.f - wp) * It[c] + wp * gI[c];
+        const float e = It[c] - AI;
+        dI += e * e;
+        a.O[c * hw + i] = A;
+        if (a.sI) a.sI[c * hw + i] = It[c];
+        if (a.sP) a.sP[c * hw + i] = Pt[c];
+        if (a.sO) a.sO[c * hw + i] = A;
+    }
+    if (a.wc) a.wc[i] = a.lambda * expf(-a.alpha * dI);
+    if (a.mask) a.mask[i] = m ? 1 : 0;
+}
+
+cudaError_t launch_consistency(const ConsistArgs &a, cudaStream_t st) {
+    dim3 grid((a.W + 31) / 32, (a.H + 7) / 8);
+    consistency_kernel<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Full-resolution flow, cropped to (H, W), planar (2, H, W), from a (fh, fw, 2) field.
+__global__ void flow_out_kernel(const float *F, int fh, int fw, int s, int H, int W, float *out) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)H * W) return;
+    const int y = (int)(i / W), x = (int)(i - (size_t)y * W);
+    const float2 v = upsampled_flow_at(F, fh, fw, s, x, y);
+    out[i] = v.x;
+    out[(size_t)H * W + i] = v.y;
+}
+
+cudaError_t launch_flow_out(const float *flow, int fh, int fw, int scale, int H, int W,
+                            float *out, cudaStream_t st) {
+    const size_t n = (size_t)H * W;
+    flow_out_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(flow, fh, fw, scale, H, W, out);
+    return cudaGetLastError();
+}
+
+}  // namespace tc

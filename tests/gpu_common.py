@@ -1,0 +1,53 @@
+"""Helpers shared by the GPU test files (inputs come from synth, expectations from oracle)."""
+import os
+import tempfile
+
+import numpy as np
+
+import oracle
+import synth
+
+_CACHE = {}
+
+
+def weights_file(chans=(16, 32, 48), radius=3, seed=0, head_gain=1.0):
+    """Writes (once per process) the seeded He-init weight file; returns (path, oracle net)."""
+    key = (tuple(chans), radius, seed, head_gain)
+    if key not in _CACHE:
+        spec = synth.NetSpec(chans=tuple(chans), radius=radius)
+        layers = synth.he_weights(spec, seed=seed, head_gain=head_gain)
+        d = tempfile.mkdtemp(prefix="tcw")
+        path = os.path.join(d, "net.tcw")
+        synth.write_weights(path, spec, layers)
+        _CACHE[key] = (path, oracle.net_from_layers(spec.levels, spec.radius, spec.chans, spec.decoder, layers))
+    return _CACHE[key]
+
+
+def to_dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()
+
+
+def planar_to_hw2(flow):
+    """(2, h, w) -> (h, w, 2) float32."""
+    return np.ascontiguousarray(np.moveaxis(np.asarray(flow, np.float32), 0, -1))
+
+
+def nchw_to_nhwc(a):
+    return np.ascontiguousarray(np.moveaxis(np.asarray(a), 1, -1), np.float32)
+
+
+def nhwc_to_nchw(a):
+    return np.ascontiguousarray(np.moveaxis(np.asarray(a), -1, 1))
+
+
+def bf16_round(a):
+    """Round float32 values to the nearest bfloat16 (ties to even), returned as float32."""
+    a = np.ascontiguousarray(a, np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)

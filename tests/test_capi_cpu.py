@@ -1,0 +1,99 @@
+"""The C-ABI library loads on a machine without a GPU, exports every symbol the header
+declares, and rejects bad arguments before touching the device.  CPU only."""
+import ctypes
+import json
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2301_00750_b300 as tc
+    return tc
+
+
+def _declared_symbols():
+    hdrs = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
+    names = set()
+    for h in hdrs:
+        names |= set(re.findall(r"^TC_API\s+[\w\s\*]+?\b(tc_\w+)\s*\(", open(h).read(), flags=re.M))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_symbols()
+    for want in ["tc_create_stream", "tc_set_consistency", "tc_process_frame", "tc_destroy"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared_symbols()
+    assert len(names) >= 14
+    so = ctypes.CDLL(lib.LIB_PATH)
+    for n in names:
+        assert hasattr(so, n), n
+    assert set(lib.EXPORTED) <= set(names)
+
+
+def test_default_consistency_is_the_paper_final_setting(lib):
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_params.json")))["final"]
+    d = lib.default_consistency()
+    assert d["k1"] == pytest.approx(g["k1"]) and d["k2"] == pytest.approx(g["k2"])
+    assert d["alpha"] == pytest.approx(g["alpha"]) and d["lam"] == pytest.approx(g["lambda"])
+
+
+def _weights_blob(tmp_path):
+    import synth
+    spec = synth.NetSpec(chans=(16, 32, 48), radius=3)
+    p = tmp_path / "w.tcw"
+    synth.write_weights(str(p), spec, synth.he_weights(spec, seed=0))
+    return p
+
+
+def test_create_stream_rejects_bad_arguments(lib, tmp_path):
+    with pytest.raises(lib.TcError) as e:
+        lib.Stream(64, 64, "fp32", weights_path=str(tmp_path / "missing.tcw"))
+    assert e.value.status == lib.TC_ERR_IO
+    bad = tmp_path / "bad.tcw"
+    bad.write_bytes(b"XXXX" + b"\0" * 64)
+    with pytest.raises(lib.TcError) as e:
+        lib.Stream(64, 64, "fp32", weights_path=str(bad))
+    assert e.value.status == lib.TC_ERR_IO
+    good = _weights_blob(tmp_path)
+    truncated = tmp_path / "trunc.tcw"
+    truncated.write_bytes(good.read_bytes()[:1000])
+    with pytest.raises(lib.TcError) as e:
+        lib.Stream(64, 64, "fp32", weights_path=str(truncated))
+    assert e.value.status == lib.TC_ERR_IO and "truncated" in str(e.value)
+    with pytest.raises(lib.TcError) as e:
+        lib.Stream(4, 64, "fp32", weights_path=str(good))      # smaller than 2^levels
+    assert e.value.status == lib.TC_ERR_INVALID_ARG
+    with pytest.raises(lib.TcError) as e:
+        lib.Stream(64, 64, "fp8", weights_path=str(good))
+    assert e.value.status == lib.TC_ERR_UNSUPPORTED
+    with pytest.raises(lib.TcError) as e:
+        lib.Stream(64, 64, "fp32")                                # no weights
+    assert e.value.status == lib.TC_ERR_INVALID_ARG
+
+
+def test_null_and_range_checks(lib):
+    so = lib._lib
+    assert so.tc_create_stream(None, None, None) == lib.TC_ERR_INVALID_ARG
+    assert so.tc_set_consistency(None, None) == lib.TC_ERR_INVALID_ARG
+    assert so.tc_process_frame(None, None, None, None, None, None) == lib.TC_ERR_INVALID_ARG
+    assert so.tc_destroy(None) == lib.TC_ERR_INVALID_ARG
+    assert so.tc_op_correlation(0, None, None, 1, 8, 8, 16, 3, None, None) == lib.TC_ERR_INVALID_ARG
+    assert so.tc_op_upsample_flow(None, 1, 4, 4, 3, None, None) == lib.TC_ERR_INVALID_ARG
+    c = lib._consistency_struct(k1=1.5)
+    # tc_op_consistency validates pointers first, then the parameters; fake non-NULL pointers
+    # are never dereferenced on the host and the call fails before any launch.
+    p = ctypes.c_void_p(16)
+    st = so.tc_op_consistency(p, p, p, p, p, p, p, 8, 8, 8, 8, 1, ctypes.byref(c), p, None, None, None)
+    assert st == lib.TC_ERR_INVALID_ARG
+    assert b"k1" in so.tc_last_error(None)

@@ -1,0 +1,144 @@
+"""End-to-end parity of a stream (tc_create_stream / tc_process_frame / tc_get_flows)
+against the oracle's stream.
+
+Staging of the tolerances (float32 vs the FP64 oracle):
+  * flows: average end-point error (Eq. 10) <= 1e-3 px per direction for the FP32 path and
+    <= 0.05 px for the BF16 path;
+  * outputs: with alpha = 6.5e3 the photometric weight amplifies a flow difference of
+    1e-4 px into weight differences of ~1e-2, so O_t is compared bit-for-bit only through
+    the staged tests (identical flows, test_gpu_stages) and end to end with alpha = 0
+    (w_p = k1 M), where O_t depends on the flow only through bilinear taps: max-abs <= 1e-4
+    on pixels whose mask decision is not within the flow error of its threshold.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import to_dev, to_np, weights_file
+
+pytestmark = pytest.mark.gpu
+tc = pytest.importorskip("paper_2301_00750_b300")
+
+
+def _run_gpu(path, frames, styl, prec="fp32", **params):
+    import torch
+    _, H, W = frames[0].shape
+    s = tc.Stream(W, H, prec, weights_path=path)
+    s.set_consistency(**params)
+    outs = []
+    for I, P in zip(frames, styl):
+        O = torch.empty((3, H, W), device="cuda")
+        wc = torch.empty((H, W), device="cuda")
+        m = torch.empty((H, W), device="cuda", dtype=torch.uint8)
+        s.process_frame(to_dev(I), to_dev(P), O, wc, m)
+        Fb = torch.empty((2, H, W), device="cuda")
+        Ff = torch.empty((2, H, W), device="cuda")
+        flows = None
+        if len(outs) > 0:
+            s.get_flows(Fb, Ff)
+            flows = (to_np(Fb), to_np(Ff))
+        torch.cuda.synchronize()
+        outs.append(dict(O=to_np(O), wc=to_np(wc), mask=to_np(m), flows=flows))
+    s.destroy()
+    return outs
+
+
+def _oracle_run(net, frames, styl, **params):
+    st = oracle.Stream(net, **params)
+    return [st.step(I, P) for I, P in zip(frames, styl)]
+
+
+def _pair(W, H, seed=0, n=3):
+    seq = synth.Sequence(width=W, height=H, seed=seed, side_range=(max(8, W // 12), max(10, W // 6)),
+                         max_vel=max(2.0, W / 160))
+    frames = [seq.frame(t) for t in range(n)]
+    return frames, [seq.stylized(t, f) for t, f in enumerate(frames)]
+
+
+def test_first_frame_returns_processed_frame():
+    path, net = weights_file()
+    d = synth.pair64()
+    out = _run_gpu(path, [d["I0"]], [d["P0"]])
+    assert np.array_equal(out[0]["O"], d["P0"])
+    assert (out[0]["mask"] == 0).all() and (out[0]["wc"] == 0).all()
+
+
+CASES = [
+    # name, chans, radius, W, H
+    ("64x64 3-level r3", (16, 32, 48), 3, 64, 64),
+    ("5-level r4 ragged", (16, 32, 64, 96, 128), 4, 200, 136),
+]
+
+
+@pytest.mark.parametrize("name,chans,radius,W,H", CASES)
+def test_stream_flows_fp32(name, chans, radius, W, H):
+    path, net = weights_file(chans, radius)
+    if W == 64:
+        d = synth.pair64()
+        frames, styl = [d["I0"], d["I1"], d["I1"][:, ::-1].copy()], [d["P0"], d["P1"], d["P1"][:, ::-1].copy()]
+    else:
+        frames, styl = _pair(W, H)
+    params = dict(k1=0.5, alpha=0.0, lam=2.0)
+    got = _run_gpu(path, frames, styl, **params)
+    ref = _oracle_run(net, frames, styl, **params)
+    for t in range(1, len(frames)):
+        eb = oracle.epe(got[t]["flows"][0], ref[t]["Fb"])
+        ef = oracle.epe(got[t]["flows"][1], ref[t]["Ff"])
+        assert eb <= 1e-3 and ef <= 1e-3, (t, eb, ef)
+        fmax = max(np.abs(got[t]["flows"][0] - ref[t]["Fb"]).max(), np.abs(got[t]["flows"][1] - ref[t]["Ff"]).max())
+        # alpha = 0: O = k1-blend of warped frames; compare where the mask decision is robust
+        # to the flow difference (margin > 20x the max flow deviation).
+        same = got[t]["mask"] == ref[t]["mask"]
+        assert same.mean() > 0.97
+        ok = same & (ref[t]["band"] == 0)
+        # pixels whose warp taps move by less than the flow deviation agree to within
+        # gradient * deviation; blurred noise has |grad| < 0.5 / px
+        err = np.abs(got[t]["O"] - ref[t]["O"]).max(0)
+        assert err[ok].max() <= max(1e-4, 1.0 * fmax), (err[ok].max(), fmax)
+
+
+@pytest.mark.parametrize("name,chans,radius,W,H", CASES)
+def test_stream_flows_bf16(name, chans, radius, W, H):
+    path, net = weights_file(chans, radius)
+    frames, styl = _pair(W, H, seed=1, n=2) if W != 64 else (
+        [synth.pair64()["I0"], synth.pair64()["I1"]], [synth.pair64()["P0"], synth.pair64()["P1"]])
+    got = _run_gpu(path, frames, styl, prec="bf16", k1=0.5)
+    ref = _oracle_run(net, frames, styl, k1=0.5)
+    eb = oracle.epe(got[1]["flows"][0], ref[1]["Fb"])
+    ef = oracle.epe(got[1]["flows"][1], ref[1]["Ff"])
+    print(f"{name}: bf16 EPE vs FP64 oracle: Fb {eb:.4f} px, Ff {ef:.4f} px")
+    assert eb <= 0.05 and ef <= 0.05, (eb, ef)
+
+
+def test_host_entry_point_matches_device_entry_point():
+    import torch
+    path, _ = weights_file()
+    d = synth.pair64()
+    frames, styl = [d["I0"], d["I1"]], [d["P0"], d["P1"]]
+    dev = _run_gpu(path, frames, styl, k1=0.4)
+    s = tc.Stream(64, 64, "fp32", weights_path=path)
+    s.set_consistency(k1=0.4)
+    for t in range(2):
+        O = np.empty((3, 64, 64), np.float32)
+        wc = np.empty((64, 64), np.float32)
+        m = np.empty((64, 64), np.uint8)
+        s.process_frame_host(np.ascontiguousarray(frames[t]), np.ascontiguousarray(styl[t]), O, wc, m)
+        assert np.array_equal(O, dev[t]["O"]) and np.array_equal(m, dev[t]["mask"])
+        assert np.array_equal(wc, dev[t]["wc"])
+    s.destroy()
+    torch.cuda.synchronize()
+
+
+def test_stream_1080p_flows_fp32():
+    """Full-size workload: the 1920x1080 5-level r=4 network, flows of one frame pair
+    against the oracle over the whole frame."""
+    path, net = weights_file((16, 32, 64, 96, 128), 4)
+    seq = synth.Sequence(seed=0)
+    frames = [seq.frame(0), seq.frame(1)]
+    styl = [seq.stylized(t, f) for t, f in enumerate(frames)]
+    got = _run_gpu(path, frames, styl, k1=0.5)
+    fab, fba = oracle.flow_pair(net, frames[1], frames[0])
+    eb, ef = oracle.epe(got[1]["flows"][0], fab), oracle.epe(got[1]["flows"][1], fba)
+    print(f"1080p FP32 EPE vs FP64 oracle: Fb {eb:.2e} px, Ff {ef:.2e} px")
+    assert eb <= 1e-3 and ef <= 1e-3
