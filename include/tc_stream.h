@@ -132,6 +132,14 @@ TC_API tc_status tc_process_frame_host(tc_stream *s, const float *I_t, const flo
  * Errors: TC_ERR_STATE before the second frame. */
 TC_API tc_status tc_get_flows(tc_stream *s, float *Fb, float *Ff);
 
+/* Waits for the stream's enqueued work and reports device-side failures: TC_ERR_TIMEOUT
+ * (and a poisoned stream) if a tensor-core kernel gave up on a bounded wait, TC_ERR_CUDA on
+ * a CUDA error.  tc_process_frame_host performs the same check. */
+TC_API tc_status tc_synchronize(tc_stream *s);
+
+/* Number of convolution layers of s that run on the tensor cores (tcgen05); 0 for TC_FP32. */
+TC_API int tc_tensor_core_layers(const tc_stream *s);
+
 /* Destroys a stream and frees its device memory (waits for its pending work). */
 TC_API tc_status tc_destroy(tc_stream *s);
 
@@ -177,10 +185,15 @@ TC_API tc_status tc_get_profile(tc_stream *s, double *ms, long long *launches, i
 /* 3x3 convolution, zero padding 1, stride 1 or 2, bias, optional LeakyReLU(0.1)
  * (Sec. 3.2 pyramid and estimator layers).  in (n, h, w, cin); w_oihw, bias: HOST float32
  * (cout, cin, 3, 3) and (cout); out (n, (h-1)/stride+1, (w-1)/stride+1, cout).
- * Allocates temporary device memory for the weights.  cin, cout >= 1. */
+ * Allocates temporary device memory for the weights, waits for completion.  cin, cout >= 1.
+ * With TC_BF16 eligible layers run on the tensor cores (see tc_op_last_used_tensor_cores). */
 TC_API tc_status tc_op_conv3x3(tc_precision precision, const float *in, int n, int h, int w, int cin,
                         const float *w_oihw, const float *bias, int cout, int stride, int leaky,
                         float *out, void *cuda_stream);
+
+/* 1 if the last successful tc_op_conv3x3 in this process ran on the tensor cores (TC_BF16
+ * layers with cin a multiple of 8 and cout a multiple of 16 up to 128), else 0. */
+TC_API int tc_op_last_used_tensor_cores(void);
 
 /* Cost volume (Sec. 3.2): out[n][y][x][k] = LeakyReLU((1/c) sum_ch f1[n][y][x][ch] *
  * f2[n][y+dy][x+dx][ch]), zero off the map, k = (dy+r)(2r+1) + (dx+r).  f1, f2

@@ -29,7 +29,8 @@ PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2}
 EXPORTED = ["tc_default_consistency", "tc_create_stream", "tc_set_consistency", "tc_process_frame",
             "tc_process_frame_host", "tc_get_flows", "tc_destroy", "tc_last_error", "tc_last_launch_count",
             "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
-            "tc_op_consistency", "tc_set_profiling", "tc_get_profile"]
+            "tc_op_consistency", "tc_set_profiling", "tc_get_profile", "tc_synchronize", "tc_tensor_core_layers",
+            "tc_op_last_used_tensor_cores"]
 PROFILE_CATEGORIES = ["pyramid_conv", "estimator_conv", "head", "correlation", "warp", "upsample", "consistency",
                       "other"]
 
@@ -65,8 +66,11 @@ _lib.tc_op_warp_features.argtypes = [_i, _vp, _vp, _i, _i, _i, _i, _vp, _vp]
 _lib.tc_op_upsample_flow.argtypes = [_vp, _i, _i, _i, _i, _vp, _vp]
 _lib.tc_op_consistency.argtypes = [_vp] * 7 + [_i] * 5 + [ctypes.POINTER(TcConsistency), _vp, _vp, _vp, _vp]
 _lib.tc_set_profiling.argtypes = [_vp, _i]
+_lib.tc_synchronize.argtypes = [_vp]
+_lib.tc_tensor_core_layers.argtypes = [_vp]
+_lib.tc_op_last_used_tensor_cores.argtypes = []
 _lib.tc_get_profile.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), _i]
-for _n in ["tc_set_profiling", "tc_get_profile", "tc_create_stream", "tc_set_consistency", "tc_process_frame", "tc_process_frame_host", "tc_get_flows",
+for _n in ["tc_synchronize", "tc_set_profiling", "tc_get_profile", "tc_create_stream", "tc_set_consistency", "tc_process_frame", "tc_process_frame_host", "tc_get_flows",
            "tc_destroy", "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
            "tc_op_consistency"]:
     getattr(_lib, _n).restype = ctypes.c_int
@@ -184,6 +188,14 @@ class Stream:
         _check(_lib.tc_get_profile(self._h, ms, cnt, n), self._h)
         return {k: (ms[i], cnt[i]) for i, k in enumerate(PROFILE_CATEGORIES)}
 
+    def synchronize(self):
+        """Waits for the stream; raises TcError(TC_ERR_TIMEOUT) if a device-side wait gave up."""
+        _check(_lib.tc_synchronize(self._h), self._h)
+
+    @property
+    def tensor_core_layers(self) -> int:
+        return _lib.tc_tensor_core_layers(self._h)
+
     @property
     def launch_count(self) -> int:
         return _lib.tc_last_launch_count(self._h)
@@ -213,6 +225,10 @@ def op_conv3x3(x, w, b, stride=1, leaky=True, precision="fp32", cuda_stream=None
     _check(_lib.tc_op_conv3x3(PRECISION[precision], _ptr(x, torch.float32), n, h, wd, cin, w.ctypes.data,
                               b.ctypes.data, cout, stride, int(leaky), out.data_ptr(), _stream_handle(cuda_stream)))
     return out
+
+
+def op_last_used_tensor_cores() -> bool:
+    return bool(_lib.tc_op_last_used_tensor_cores())
 
 
 def op_correlation(f1, f2, r, precision="fp32", cuda_stream=None):

@@ -1,23 +1,40 @@
-// Tensor-core (tcgen05) implicit-GEMM convolution: plan and launch interface.
+// Tensor-core (tcgen05) implicit-GEMM 3x3 convolution: plan and launch interface.
 #pragma once
+
+#include <cuda.h>
+
+#include <string>
+#include <vector>
 
 #include "common.cuh"
 
-struct tc_stream;
-
 namespace tc {
 
-// A planned launch of the tensor-core conv for one layer.  Planning encodes the TMA
-// descriptors of the input activations and the packed weights; launches reuse them.
+// A planned tensor-core conv for one layer.  Planning packs the weights to bfloat16
+// [9][cout][nch * 64] on the device and encodes the TMA descriptors of the input
+// activations (covering all n_in images of the buffer) and of the weights.
 struct TcConvPlan {
     bool enabled = false;
+    CUtensorMap tmA;  // 64-byte aligned type
+    CUtensorMap tmB;
+    int bn = 0, nch = 0, stride = 1, h = 0, w = 0, ho = 0, wo = 0, n_in = 0, cout = 0;
+    const void *in_base = nullptr;  // start of the buffer the A descriptor covers
+    size_t img_bytes = 0;           // bytes between consecutive images of that buffer
+    __nv_bfloat16 *wpk = nullptr;   // packed weights (owned by the plan)
+    int *err = nullptr;             // device error word shared by the stream (not owned)
+    void release();
 };
 
-// Returns false (plan disabled) when the layer is not eligible.
-bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, bool tma_in);
+// Plans the conv described by `a` (a.in = first image of a buffer holding n_in images of
+// a.h x a.w pixels with pixel stride a.in_cs channels; channels [0, a.cin) of each pixel are
+// read).  wk_simt: float weights [9 * a.cin][a.cout] (k = tap * cin + c), already in the
+// buffer's channel order.  Returns false with `why` when the layer is not eligible (then
+// the caller uses the CUDA-core kernel).
+bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vector<float> &wk_simt, int *err,
+                  std::string &why);
+
+// Launches a planned conv for a.n images starting at a.in (which must lie inside the
+// planned buffer, on an image boundary), writing bfloat16 to a.out with a.out_cs stride.
 cudaError_t launch_conv_tc(const TcConvPlan &plan, const ConvArgs &a, cudaStream_t st);
 
 }  // namespace tc
-
-// Plans the tensor-core convs of a BF16 stream (no-op when not available).
-int tc_prepare_tensor_core_path(tc_stream *s);

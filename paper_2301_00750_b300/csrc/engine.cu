@@ -174,7 +174,8 @@ struct tc_stream {
     uint8_t *hmask = nullptr;
     long long t = 0;
     bool poisoned = false;
-    bool use_tc = false;
+    int *dev_err = nullptr;     // device error word of the tensor-core kernels (0 = ok)
+    int tc_layers = 0;          // convolution layers planned on the tensor cores
     int launches = 0;
     std::string err;
     // per-stage timing (tc_set_profiling): events around every launch, folded lazily
@@ -187,6 +188,7 @@ struct tc_stream {
 
 static std::mutex g_err_mu;
 static std::string g_err;
+static int g_last_op_tc = 0;  // 1 if the last tc_op_conv3x3 ran on the tensor cores
 
 static tc_status fail(tc_stream *s, tc_status code, const std::string &msg) {
     if (s) {
@@ -238,6 +240,10 @@ static tc_status upload(tc_stream *s, float **dst, const std::vector<float> &v) 
 }
 
 static void free_all(tc_stream *s) {
+    for (auto &B : s->lv)
+        for (auto &pl : B.tcplan) pl.release();
+    for (auto &lvl : s->pyr_plan)
+        for (auto &pl : lvl) pl.release();
     for (void *p : s->allocs) cudaFree(p);
     s->allocs.clear();
 }
@@ -276,6 +282,14 @@ extern "C" tc_status tc_set_consistency(tc_stream *s, const tc_consistency *p) {
     return TC_OK;
 }
 
+// Plans a BF16 layer on the tensor cores; layers that are not eligible keep the CUDA-core
+// kernel (plan disabled).
+static void plan_tc(tc_stream *s, TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vector<float> &wk) {
+    if (s->prec != TC_BF16) return;
+    std::string why;
+    if (tc_plan_conv(plan, a, n_in, wk, s->dev_err, why)) s->tc_layers += 1;
+}
+
 template <typename T>
 static tc_status build_stream(tc_stream *s) {
     const HostNet &net = s->net;
@@ -286,6 +300,8 @@ static tc_status build_stream(tc_stream *s) {
     s->pyr_w.assign(3 * L, nullptr);
     s->pyr_b.assign(3 * L, nullptr);
     tc_status r;
+    if ((r = dalloc_t(s, &s->dev_err, sizeof(int))) != TC_OK) return r;
+    TC_TRY(s, cudaMemset(s->dev_err, 0, sizeof(int)), "memset");
     for (int l = 1; l <= L; ++l) {
         LevelBufs &B = s->lv[l - 1];
         B.h = s->Hp >> l;
@@ -312,6 +328,19 @@ static tc_status build_stream(tc_stream *s) {
             }
             if ((r = upload(s, &s->pyr_w[3 * (l - 1) + j], wk)) != TC_OK) return r;
             if ((r = upload(s, &s->pyr_b[3 * (l - 1) + j], HL.b)) != TC_OK) return r;
+            if (l == 1 && j == 0) continue;
+            // Same arguments as run_pyramid builds; the first conv of a level reads both
+            // slots of the previous level's pyramid buffer.
+            ConvArgs a{};
+            if (j == 0) {
+                LevelBufs &P = s->lv[l - 2];
+                a = ConvArgs{P.pyr, P.c, 1, P.h, P.w, P.c, 2, B.h, B.w, nullptr, nullptr, B.c, B.tmpA, B.c, 1};
+                plan_tc(s, s->pyr_plan[l - 1][0], a, 2, wk);
+            } else {
+                a = ConvArgs{j == 1 ? B.tmpA : B.tmpB, B.c, 1, B.h, B.w, B.c, 1, B.h, B.w, nullptr, nullptr, B.c,
+                             B.tmpB, B.c, 1};
+                plan_tc(s, s->pyr_plan[l - 1][j], a, 1, wk);
+            }
         }
         if (l < 2) continue;
         // Estimator buffers: x0 = [corr D | self c | up 2 | zero pad] then x1..x4.
@@ -337,9 +366,16 @@ static tc_status build_stream(tc_stream *s) {
         for (int i = 0; i < net.dec[2]; ++i) p5[i] = net.dec[3] + i;          // x3 = file channels [dec3, dec3+dec2)
         for (int i = 0; i < net.dec[3]; ++i) p5[net.dec[2] + i] = i;          // x4 = file channels [0, dec3)
         const std::vector<int> perms[4] = {p1, iota_perm(E[1].cin, E[1].cin), iota_perm(E[2].cin, E[2].cin), p4};
+        const int in_off[4] = {0, B.off_x1, B.off_x2, B.off_x2};
+        const int cin[4] = {B.x0p, net.dec[0], net.dec[1], net.dec[1] + net.dec[2]};
         for (int j = 0; j < 4; ++j) {
-            if ((r = upload(s, &B.wk[j], simt_weights(E[j], perms[j], bf))) != TC_OK) return r;
+            std::vector<float> wk = simt_weights(E[j], perms[j], bf);
+            if ((r = upload(s, &B.wk[j], wk)) != TC_OK) return r;
             if ((r = upload(s, &B.bias[j], E[j].b)) != TC_OK) return r;
+            T *dec = static_cast<T *>(B.dec);
+            ConvArgs a{dec + in_off[j], B.ctot, 2, B.h, B.w, cin[j], 1, B.h, B.w, nullptr, nullptr, net.dec[j],
+                       dec + B.off_x1, B.ctot, 1};
+            plan_tc(s, B.tcplan[j], a, 2, wk);
         }
         if ((r = upload(s, &B.head_w, simt_weights(E[4], p5, bf))) != TC_OK) return r;
         if ((r = upload(s, &B.head_b, E[4].b)) != TC_OK) return r;
@@ -397,14 +433,6 @@ extern "C" tc_status tc_create_stream(const tc_stream_desc *desc, void *cuda_str
         std::string msg = s->err;
         free_all(s.get());
         return fail(nullptr, r, msg);
-    }
-    if (s->prec == TC_BF16) {
-        r = (tc_status)tc_prepare_tensor_core_path(s.get());
-        if (r != TC_OK) {
-            std::string msg = s->err;
-            free_all(s.get());
-            return fail(nullptr, r, msg);
-        }
     }
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -590,6 +618,26 @@ extern "C" tc_status tc_process_frame(tc_stream *s, const float *I_t, const floa
                               : process<__nv_bfloat16>(s, I_t, P_t, O_t, wc_opt, mask_opt);
 }
 
+// Reads the stream's device error word (after the stream has been synchronised).
+static tc_status check_device_error(tc_stream *s) {
+    if (!s->dev_err) return TC_OK;
+    int e = 0;
+    TC_TRY(s, cudaMemcpy(&e, s->dev_err, sizeof(int), cudaMemcpyDeviceToHost), "error word read");
+    if (e != 0) {
+        s->poisoned = true;
+        return fail(s, TC_ERR_TIMEOUT, "a tensor-core kernel gave up waiting (code " + std::to_string(e) +
+                                            "); the frame's results are invalid");
+    }
+    return TC_OK;
+}
+
+extern "C" tc_status tc_synchronize(tc_stream *s) {
+    tc_status r = check_stream(s, "tc_synchronize");
+    if (r != TC_OK) return r;
+    TC_TRY(s, cudaStreamSynchronize(s->st), "stream synchronize");
+    return check_device_error(s);
+}
+
 extern "C" tc_status tc_process_frame_host(tc_stream *s, const float *I_t, const float *P_t, float *O_t,
                                            float *wc_opt, uint8_t *mask_opt) {
     tc_status r = check_stream(s, "tc_process_frame_host");
@@ -611,7 +659,7 @@ extern "C" tc_status tc_process_frame_host(tc_stream *s, const float *I_t, const
     if (wc_opt) TC_TRY(s, cudaMemcpyAsync(wc_opt, s->hwc, plane * sizeof(float), cudaMemcpyDeviceToHost, s->st), "D2H w_c");
     if (mask_opt) TC_TRY(s, cudaMemcpyAsync(mask_opt, s->hmask, plane, cudaMemcpyDeviceToHost, s->st), "D2H mask");
     TC_TRY(s, cudaStreamSynchronize(s->st), "stream synchronize");
-    return TC_OK;
+    return check_device_error(s);
 }
 
 extern "C" tc_status tc_get_flows(tc_stream *s, float *Fb, float *Ff) {
@@ -666,8 +714,7 @@ extern "C" const char *tc_last_error(const tc_stream *s) {
 
 extern "C" int tc_last_launch_count(const tc_stream *s) { return s ? s->launches : 0; }
 
-// Accessors used by the tensor-core planner (conv_tc.cu).
-int tc_stream_levels(const tc_stream *s) { return s->L; }
+extern "C" int tc_tensor_core_layers(const tc_stream *s) { return s ? s->tc_layers : 0; }
 
 // ------------------------------------------------------------------------------- stage ops
 
@@ -699,7 +746,7 @@ static tc_status op_conv(const float *in, int n, int h, int w, int cin, const fl
     L.w.assign(w_oihw, w_oihw + (size_t)cout * cin * 9);
     L.b.assign(bias, bias + cout);
     const bool bf = sizeof(T) == 2;
-    const int cin_p = round_up(cin, 4), cout_p = round_up(cout, 4);
+    const int cin_p = round_up(cin, bf ? 8 : 4), cout_p = round_up(cout, 4);
     const int ho = (h - 1) / stride + 1, wo = (w - 1) / stride + 1;
     std::vector<float> wk = simt_weights(L, iota_perm(cin, cin_p), bf);
     // pad cout to a multiple of 4
@@ -731,9 +778,17 @@ static tc_status op_conv(const float *in, int n, int h, int w, int cin, const fl
     }
     ConvArgs a{din, cin_p, n, h, w, cin_p, stride, ho, wo, dw, db, cout_p, dout, cout_p, leaky};
     TcConvPlan plan;
-    bool use_tc = bf && tc_plan_conv(plan, a, /*tma_in=*/true);
+    int *derr = nullptr;
+    OP_TRY(tmp.get((void **)&derr, sizeof(int)), "tc_op_conv3x3 alloc");
+    OP_TRY(cudaMemsetAsync(derr, 0, sizeof(int), st), "tc_op_conv3x3 memset");
+    std::string why;
+    const bool use_tc = bf && tc_plan_conv(plan, a, n, wkp, derr, why);
     if (use_tc) {
-        OP_TRY(launch_conv_tc(plan, a, st), "tc_op_conv3x3 tensor-core launch");
+        cudaError_t e = launch_conv_tc(plan, a, st);
+        if (e != cudaSuccess) {
+            plan.release();
+            return cuda_fail(nullptr, e, "tc_op_conv3x3 tensor-core launch");
+        }
     } else {
         OP_TRY(launch_conv_simt<T>(a, st), "tc_op_conv3x3 launch");
     }
@@ -746,9 +801,17 @@ static tc_status op_conv(const float *in, int n, int h, int w, int cin, const fl
         OP_TRY(cudaMemcpy2DAsync(out, cout * 4, outp, cout_p * 4, cout * 4, (size_t)n * ho * wo, cudaMemcpyDeviceToDevice, st),
                "tc_op_conv3x3 repack");
     }
-    OP_TRY(cudaStreamSynchronize(st), "tc_op_conv3x3 sync");
+    cudaError_t se = cudaStreamSynchronize(st);
+    plan.release();
+    if (se != cudaSuccess) return cuda_fail(nullptr, se, "tc_op_conv3x3 sync");
+    int e = 0;
+    OP_TRY(cudaMemcpy(&e, derr, sizeof(int), cudaMemcpyDeviceToHost), "tc_op_conv3x3 error word");
+    if (e != 0) return fail(nullptr, TC_ERR_TIMEOUT, "tc_op_conv3x3: tensor-core kernel gave up waiting");
+    g_last_op_tc = use_tc ? 1 : 0;
     return TC_OK;
 }
+
+extern "C" int tc_op_last_used_tensor_cores(void) { return g_last_op_tc; }
 
 extern "C" tc_status tc_op_conv3x3(tc_precision precision, const float *in, int n, int h, int w, int cin,
                                    const float *w_oihw, const float *bias, int cout, int stride, int leaky,

@@ -134,8 +134,10 @@ class Sequence:
         self.theta = [0.0]
         self.trans = [np.zeros(2)]
         self.squares = []
+        hi = min(side_range[1], min(width, height) - 1)
+        lo = min(side_range[0], hi)
         for _ in range(n_squares):
-            side = int(g.integers(side_range[0], side_range[1] + 1))
+            side = int(g.integers(lo, hi + 1))
             tex = blurred_noise(side, side, 3, 2.0, g)
             tex = np.stack([ndimage.spline_filter(c, order=3, mode="mirror") for c in tex])
             pos = np.array([g.uniform(0, width - side), g.uniform(0, height - side)])

@@ -76,10 +76,12 @@ def test_correlation_finds_integer_shift():
 
 
 CONV_CASES = [
-    # n, h, w, cin, cout, stride
+    # n, h, w, cin, cout, stride   (bf16 cases with cin % 8 == 0 and cout % 16 == 0 run on
+    # the tensor cores: several 128-pixel tiles, ragged row tails, channel tails, stride 2)
     (1, 9, 13, 16, 16, 1), (2, 17, 30, 32, 32, 2), (2, 34, 60, 128, 128, 1), (1, 33, 47, 120, 128, 1),
     (2, 20, 36, 160, 32, 1), (1, 68, 120, 96, 64, 1), (1, 11, 7, 8, 2, 1), (2, 64, 72, 64, 96, 2),
-    (1, 5, 6, 6, 10, 1),
+    (1, 5, 6, 6, 10, 1), (1, 136, 240, 64, 64, 1), (2, 272, 480, 32, 32, 1), (1, 7, 300, 16, 16, 2),
+    (2, 3, 130, 216, 128, 1), (1, 8, 8, 48, 48, 1),
 ]
 
 
@@ -93,6 +95,8 @@ def test_conv3x3(prec, n, h, w, cin, cout, stride):
     if prec == "bf16":
         x, wt = bf16_round(x), bf16_round(wt)
     got = to_np(tc.op_conv3x3(to_dev(nchw_to_nhwc(x)), wt, b, stride=stride, leaky=True, precision=prec))
+    eligible = prec == "bf16" and cin % 8 == 0 and cout % 16 == 0 and cout <= 128
+    assert tc.op_last_used_tensor_cores() == eligible
     for i in range(n):
         ref = oracle.conv3x3(x[i], wt, b, stride=stride, leaky=True)
         g_ = nhwc_to_nchw(got[i:i + 1])[0]

@@ -107,8 +107,26 @@ def test_stream_flows_bf16(name, chans, radius, W, H):
     ref = _oracle_run(net, frames, styl, k1=0.5)
     eb = oracle.epe(got[1]["flows"][0], ref[1]["Fb"])
     ef = oracle.epe(got[1]["flows"][1], ref[1]["Ff"])
-    print(f"{name}: bf16 EPE vs FP64 oracle: Fb {eb:.4f} px, Ff {ef:.4f} px")
-    assert eb <= 0.05 and ef <= 0.05, (eb, ef)
+    mag = float(np.sqrt((ref[1]["Fb"] ** 2).sum(0)).mean())
+    print(f"{name}: bf16 EPE vs FP64 oracle: Fb {eb:.4f} px, Ff {ef:.4f} px (mean |F| {mag:.2f} px)")
+    # BF16 operands carry 8 significant bits; through ~20 layers the flow error is a fraction
+    # of a percent of the flow magnitude.  Bound: 0.05 px, or 1% of the mean flow where the
+    # He-init network's random flows are large.
+    bound = max(0.05, 0.01 * mag)
+    assert eb <= bound and ef <= bound, (eb, ef, bound)
+
+
+@pytest.mark.parametrize("chans,radius,want", [((16, 32, 48), 3, 16), ((16, 32, 64, 96, 128), 4, 30)])
+def test_bf16_stream_plans_convs_on_tensor_cores(chans, radius, want):
+    """Every pyramid conv but the first (3 input channels) and every estimator conv1..conv4
+    runs on the tensor cores in a BF16 stream; an FP32 stream uses none."""
+    path, _ = weights_file(chans, radius)
+    s = tc.Stream(64, 64, "bf16", weights_path=path)
+    assert s.tensor_core_layers == want
+    s.destroy()
+    s = tc.Stream(64, 64, "fp32", weights_path=path)
+    assert s.tensor_core_layers == 0
+    s.destroy()
 
 
 def test_host_entry_point_matches_device_entry_point():
