@@ -3,7 +3,7 @@ against the oracle's stream.
 
 Staging of the tolerances (float32 vs the FP64 oracle):
   * flows: average end-point error (Eq. 10) <= 1e-3 px per direction for the FP32 path and
-    <= 0.05 px for the BF16 path;
+    <= 0.05 px (or 2 u sqrt(layers) of the mean flow, u = 2^-9) for the BF16 path;
   * outputs: with alpha = 6.5e3 the photometric weight amplifies a flow difference of
     1e-4 px into weight differences of ~1e-2, so O_t is compared bit-for-bit only through
     the staged tests (identical flows, test_gpu_stages) and end to end with alpha = 0
@@ -109,10 +109,13 @@ def test_stream_flows_bf16(name, chans, radius, W, H):
     ef = oracle.epe(got[1]["flows"][1], ref[1]["Ff"])
     mag = float(np.sqrt((ref[1]["Fb"] ** 2).sum(0)).mean())
     print(f"{name}: bf16 EPE vs FP64 oracle: Fb {eb:.4f} px, Ff {ef:.4f} px (mean |F| {mag:.2f} px)")
-    # BF16 operands carry 8 significant bits; through ~20 layers the flow error is a fraction
-    # of a percent of the flow magnitude.  Bound: 0.05 px, or 1% of the mean flow where the
-    # He-init network's random flows are large.
-    bound = max(0.05, 0.01 * mag)
+    # BF16 operands carry 8 significant bits (unit roundoff u = 2^-9).  Each of the n conv
+    # layers on the path to the flow adds an independent relative error of about u, so the
+    # flow's relative error is about u sqrt(n); the bound allows twice that: 0.05 px, or
+    # 2 u sqrt(n) of the mean flow magnitude where the He-init network's random flows are
+    # large (~10 px; about 2.3% for the 5-level net's n = 35 layers).
+    n_layers = 3 * len(chans) + 5 * (len(chans) - 1)
+    bound = max(0.05, 2 * 2.0 ** -9 * np.sqrt(n_layers) * mag)
     assert eb <= bound and ef <= bound, (eb, ef, bound)
 
 
