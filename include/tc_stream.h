@@ -225,6 +225,36 @@ TC_API tc_status tc_op_consistency(const float *It, const float *Pt, const float
                             int fh, int fw, int scale, const tc_consistency *p, float *O,
                             float *wc_opt, uint8_t *mask_opt, void *cuda_stream);
 
+/* ------------------------------------------------------------------------------------
+ * Allocation-free variant.  The paper has no counterpart: this entry point exists for hosts
+ * that cannot let the library allocate device memory -- an application whose memory pool
+ * has reserved the device memory up front and passes only pre-allocated buffers, or a
+ * real-time loop that cannot afford cudaMalloc/cudaFree (both may synchronise the device).
+ * ---------------------------------------------------------------------------------- */
+
+/* Size of the fixed device staging array behind tc_op_correlation_bf16_noalloc.  Every GPU
+ * that loads the library holds it until the process exits. */
+#define TC_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* Same result as tc_op_correlation(TC_BF16, f1, f2, n, h, w, c, r, out, cuda_stream) -- the
+ * bfloat16 cost volume returned as float32 -- but it allocates nothing: the bfloat16 copies
+ * of f1, f2 and of the cost volume are staged in a fixed array of TC_NOALLOC_SCRATCH_BYTES in
+ * device memory instead of temporary buffers.  Same arguments, layouts and limits as
+ * tc_op_correlation (device NHWC float32 inputs, output (n, h, w, (2r+1)^2) float32).
+ *   - Sizes: requires 2 * align256(2 n h w c) + align256(2 n h w (2r+1)^2) <=
+ *     TC_NOALLOC_SCRATCH_BYTES, else TC_ERR_INVALID_ARG with the needed size in
+ *     tc_last_error(NULL).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call before any
+ *     stream capture.
+ *   - Every call on a device shares the one array, which keeps the last call's contents
+ *     (each call writes every byte it reads, so nothing needs clearing).  Calls whose work
+ *     overlaps on the GPU (other streams, other host threads) race on it: order them on one
+ *     stream or synchronise between them.
+ *   - Enqueued on cuda_stream; returns without waiting. */
+TC_API tc_status tc_op_correlation_bf16_noalloc(const float *f1, const float *f2, int n, int h, int w, int c,
+                                               int r, float *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

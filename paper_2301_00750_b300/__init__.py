@@ -30,7 +30,8 @@ EXPORTED = ["tc_default_consistency", "tc_create_stream", "tc_set_consistency", 
             "tc_process_frame_host", "tc_get_flows", "tc_destroy", "tc_last_error", "tc_last_launch_count",
             "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
             "tc_op_consistency", "tc_set_profiling", "tc_get_profile", "tc_synchronize", "tc_tensor_core_layers",
-            "tc_op_last_used_tensor_cores"]
+            "tc_op_last_used_tensor_cores", "tc_op_correlation_bf16_noalloc"]
+NOALLOC_SCRATCH_BYTES = 16 << 20
 PROFILE_CATEGORIES = ["pyramid_conv", "estimator_conv", "head", "correlation", "warp", "upsample", "consistency",
                       "other"]
 
@@ -66,11 +67,12 @@ _lib.tc_op_warp_features.argtypes = [_i, _vp, _vp, _i, _i, _i, _i, _vp, _vp]
 _lib.tc_op_upsample_flow.argtypes = [_vp, _i, _i, _i, _i, _vp, _vp]
 _lib.tc_op_consistency.argtypes = [_vp] * 7 + [_i] * 5 + [ctypes.POINTER(TcConsistency), _vp, _vp, _vp, _vp]
 _lib.tc_set_profiling.argtypes = [_vp, _i]
+_lib.tc_op_correlation_bf16_noalloc.argtypes = [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp]
 _lib.tc_synchronize.argtypes = [_vp]
 _lib.tc_tensor_core_layers.argtypes = [_vp]
 _lib.tc_op_last_used_tensor_cores.argtypes = []
 _lib.tc_get_profile.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), _i]
-for _n in ["tc_synchronize", "tc_set_profiling", "tc_get_profile", "tc_create_stream", "tc_set_consistency", "tc_process_frame", "tc_process_frame_host", "tc_get_flows",
+for _n in ["tc_op_correlation_bf16_noalloc", "tc_synchronize", "tc_set_profiling", "tc_get_profile", "tc_create_stream", "tc_set_consistency", "tc_process_frame", "tc_process_frame_host", "tc_get_flows",
            "tc_destroy", "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
            "tc_op_consistency"]:
     getattr(_lib, _n).restype = ctypes.c_int
@@ -237,6 +239,20 @@ def op_correlation(f1, f2, r, precision="fp32", cuda_stream=None):
     out = torch.empty((n, h, w, (2 * r + 1) ** 2), device=f1.device, dtype=torch.float32)
     _check(_lib.tc_op_correlation(PRECISION[precision], _ptr(f1, torch.float32), _ptr(f2, torch.float32), n, h, w,
                                   c, r, out.data_ptr(), _stream_handle(cuda_stream)))
+    return out
+
+
+def op_correlation_bf16_noalloc(f1, f2, r, out=None, cuda_stream=None):
+    """tc_op_correlation_bf16_noalloc: the BF16 cost volume without any device allocation
+    inside the library (its staging lives in a fixed device array), for hosts that cannot
+    allocate on the library's behalf.  Pass `out` pre-allocated ((n, h, w, (2r+1)^2) float32
+    CUDA) to allocate nothing at all here either; returns without waiting."""
+    import torch
+    n, h, w, c = f1.shape
+    if out is None:
+        out = torch.empty((n, h, w, (2 * r + 1) ** 2), device=f1.device, dtype=torch.float32)
+    _check(_lib.tc_op_correlation_bf16_noalloc(_ptr(f1, torch.float32), _ptr(f2, torch.float32), n, h, w, c, r,
+                                               _ptr(out, torch.float32, "out"), _stream_handle(cuda_stream)))
     return out
 
 

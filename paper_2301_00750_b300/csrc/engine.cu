@@ -201,6 +201,9 @@ static tc_status fail(tc_stream *s, tc_status code, const std::string &msg) {
     return code;
 }
 
+// Records the error of a stream-less call (read back with tc_last_error(NULL)).
+tc_status tc_record_error(tc_status code, const std::string &msg) { return fail(nullptr, code, msg); }
+
 static tc_status cuda_fail(tc_stream *s, cudaError_t e, const char *what) {
     return fail(s, TC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
