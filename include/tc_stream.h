@@ -137,8 +137,12 @@ TC_API tc_status tc_get_flows(tc_stream *s, float *Fb, float *Ff);
  * a CUDA error.  tc_process_frame_host performs the same check. */
 TC_API tc_status tc_synchronize(tc_stream *s);
 
-/* Number of convolution layers of s that run on the tensor cores (tcgen05); 0 for TC_FP32. */
+/* Number of convolution layers of s that run on the tensor cores (tcgen05), flow heads
+ * included; 0 for TC_FP32. */
 TC_API int tc_tensor_core_layers(const tc_stream *s);
+
+/* Number of pyramid levels of s whose correlation runs on the tensor cores; 0 for TC_FP32. */
+TC_API int tc_tensor_core_correlation_levels(const tc_stream *s);
 
 /* Destroys a stream and frees its device memory (waits for its pending work). */
 TC_API tc_status tc_destroy(tc_stream *s);
@@ -191,8 +195,9 @@ TC_API tc_status tc_op_conv3x3(tc_precision precision, const float *in, int n, i
                         const float *w_oihw, const float *bias, int cout, int stride, int leaky,
                         float *out, void *cuda_stream);
 
-/* 1 if the last successful tc_op_conv3x3 in this process ran on the tensor cores (TC_BF16
- * layers with cin a multiple of 8 and cout a multiple of 16 up to 128), else 0. */
+/* 1 if the last successful tc_op_conv3x3 or tc_op_correlation in this process ran on the
+ * tensor cores, else 0.  TC_BF16 convs with cin a multiple of 8 and cout a multiple of 16 up
+ * to 128, and TC_BF16 correlations with c a multiple of 8 up to 128, do. */
 TC_API int tc_op_last_used_tensor_cores(void);
 
 /* Cost volume (Sec. 3.2): out[n][y][x][k] = LeakyReLU((1/c) sum_ch f1[n][y][x][ch] *

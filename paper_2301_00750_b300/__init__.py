@@ -30,7 +30,8 @@ EXPORTED = ["tc_default_consistency", "tc_create_stream", "tc_set_consistency", 
             "tc_process_frame_host", "tc_get_flows", "tc_destroy", "tc_last_error", "tc_last_launch_count",
             "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
             "tc_op_consistency", "tc_set_profiling", "tc_get_profile", "tc_synchronize", "tc_tensor_core_layers",
-            "tc_op_last_used_tensor_cores", "tc_op_correlation_bf16_noalloc"]
+            "tc_op_last_used_tensor_cores", "tc_op_correlation_bf16_noalloc",
+            "tc_tensor_core_correlation_levels"]
 NOALLOC_SCRATCH_BYTES = 16 << 20
 PROFILE_CATEGORIES = ["pyramid_conv", "estimator_conv", "head", "correlation", "warp", "upsample", "consistency",
                       "other"]
@@ -70,6 +71,7 @@ _lib.tc_set_profiling.argtypes = [_vp, _i]
 _lib.tc_op_correlation_bf16_noalloc.argtypes = [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp]
 _lib.tc_synchronize.argtypes = [_vp]
 _lib.tc_tensor_core_layers.argtypes = [_vp]
+_lib.tc_tensor_core_correlation_levels.argtypes = [_vp]
 _lib.tc_op_last_used_tensor_cores.argtypes = []
 _lib.tc_get_profile.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), _i]
 for _n in ["tc_op_correlation_bf16_noalloc", "tc_synchronize", "tc_set_profiling", "tc_get_profile", "tc_create_stream", "tc_set_consistency", "tc_process_frame", "tc_process_frame_host", "tc_get_flows",
@@ -197,6 +199,10 @@ class Stream:
     @property
     def tensor_core_layers(self) -> int:
         return _lib.tc_tensor_core_layers(self._h)
+
+    @property
+    def tensor_core_correlation_levels(self) -> int:
+        return _lib.tc_tensor_core_correlation_levels(self._h)
 
     @property
     def launch_count(self) -> int:

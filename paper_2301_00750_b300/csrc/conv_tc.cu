@@ -20,15 +20,17 @@
 #include <mutex>
 
 #include "conv_tc.cuh"
+#include "tc_ptx.cuh"
 
 namespace tc {
 
 namespace {
 
+using namespace ptx;
+
 constexpr int BM = 128;                    // output pixels per CTA (MMA M)
 constexpr int BK = 64;                     // input channels per step (128 B of bf16)
 constexpr uint32_t A_BYTES = BM * BK * 2;  // 16 KB
-constexpr unsigned long long WAIT_NS = 2000000000ull;
 
 enum : int { ERR_PRODUCER = 1, ERR_MMA = 2, ERR_EPILOGUE = 3, ERR_DRAIN = 4 };
 
@@ -48,121 +50,13 @@ struct TcLaunch {
     const float *bias;
     int leaky;
     int *err;
+    float *flow;      // flow-head mode: (n, ho, wo, 2) float output
+    const float *up;  // flow-head mode: residual base flow, same layout, or NULL
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Waits for the phase of `bar` with the given parity; gives up after WAIT_NS or as soon as
-// another role of this CTA (or another CTA) has recorded an error.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, int code) {
-    unsigned long long t0 = 0;
-    for (uint32_t i = 0;; ++i) {
-        if (mbar_try(bar, parity)) return true;
-        if ((i & 63) == 63) {
-            if (*(volatile int *)err != 0) return false;
-            const unsigned long long t = global_ns();
-            if (t0 == 0) t0 = t;
-            else if (t - t0 > WAIT_NS) {
-                atomicCAS(err, 0, code);
-                return false;
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ void tma_load_3d(const CUtensorMap *map, uint32_t bar, uint32_t dst, int c0, int c1, int c2) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_load_4d(const CUtensorMap *map, uint32_t bar, uint32_t dst, int c0, int c1, int c2,
-                                            int c3) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
-        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_load_5d(const CUtensorMap *map, uint32_t bar, uint32_t dst, int c0, int c1, int c2,
-                                            int c3, int c4) {
-    asm volatile(
-        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
-        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
-        : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand in the 128-byte swizzled layout written
-// by TMA (rows of 128 B, 8-row groups 1024 B apart), version 1 (tcgen05).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;            // leading-dimension byte offset (unused for this layout)
-    d |= (uint64_t)(1024 >> 4) << 32;  // stride-dimension byte offset: 8 rows x 128 B
-    d |= (uint64_t)1 << 46;            // descriptor version
-    d |= (uint64_t)2 << 61;            // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor of kind::f16: D f32, A and B bf16, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-
-__device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<uint32_t *>(&v);
-}
-
-template <int BN>
+// HEAD = true: the flow head (cout = 2, zero-padded to BN = 16 for the MMA); the epilogue
+// writes float32 flow = up + (acc[0], acc[1]) + bias without activation.
+template <int BN, bool HEAD>
 __global__ void __launch_bounds__(128, 1)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcLaunch p) {
     constexpr int STAGES = stages_for(BN);
@@ -257,7 +151,18 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (lane == 0) ok = mbar_wait(accum, 0, p.err, ERR_EPILOGUE) && *(volatile int *)p.err == 0;
     ok = __shfl_sync(0xffffffffu, ok, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
+    if (HEAD && ok) {
+        const int x = x0 + warp * 32 + lane;
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), r);
+        if (x < p.wo) {
+            const size_t pix = (size_t)(img * p.ho + y) * p.wo + x;
+            float2 up = make_float2(0.f, 0.f);
+            if (p.up) up = reinterpret_cast<const float2 *>(p.up)[pix];
+            reinterpret_cast<float2 *>(p.flow)[pix] =
+                make_float2(up.x + (__uint_as_float(r[0]) + __ldg(p.bias)), up.y + (__uint_as_float(r[1]) + __ldg(p.bias + 1)));
+        }
+    } else if (ok) {
         const int row = warp * 32 + lane;
         const int x = x0 + row;
         __nv_bfloat16 *dst = p.out + ((size_t)(img * p.ho + y) * p.wo + x) * p.out_cs;
@@ -294,6 +199,23 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
 }
 
+template <int BN, bool HEAD = false>
+cudaError_t launch_bn(const TcConvPlan &plan, const TcLaunch &lp, int n_img, cudaStream_t st) {
+    static bool attr_set = false;
+    const size_t smem = smem_bytes_for(BN);
+    if (!attr_set) {
+        cudaError_t e =
+            cudaFuncSetAttribute(conv_tc_kernel<BN, HEAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    dim3 grid((plan.wo + BM - 1) / BM, plan.ho, n_img);
+    conv_tc_kernel<BN, HEAD><<<grid, 128, smem, st>>>(plan.tmA, plan.tmB, lp);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
@@ -310,22 +232,6 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-template <int BN>
-cudaError_t launch_bn(const TcConvPlan &plan, const TcLaunch &lp, int n_img, cudaStream_t st) {
-    static bool attr_set = false;
-    const size_t smem = smem_bytes_for(BN);
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    dim3 grid((plan.wo + BM - 1) / BM, plan.ho, n_img);
-    conv_tc_kernel<BN><<<grid, 128, smem, st>>>(plan.tmA, plan.tmB, lp);
-    return cudaGetLastError();
-}
-
-}  // namespace
-
 void TcConvPlan::release() {
     if (wpk) cudaFree(wpk);
     wpk = nullptr;
@@ -335,6 +241,7 @@ void TcConvPlan::release() {
 bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vector<float> &wk_simt, int *err,
                   std::string &why) {
     plan.enabled = false;
+    plan.head = false;
     const int bn = a.cout;
     if (bn < 16 || bn > 128 || bn % 16 != 0) { why = "cout must be a multiple of 16 in [16, 128]"; return false; }
     if (a.cin % 8 != 0 || a.in_cs % 8 != 0 || a.out_cs % 8 != 0) { why = "channel counts must be multiples of 8"; return false; }
@@ -407,15 +314,41 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
     return true;
 }
 
+bool tc_plan_head(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vector<float> &wk_simt, int *err,
+                  std::string &why) {
+    if (a.cout > 16) { why = "head has more than 16 outputs"; return false; }
+    std::vector<float> wk16((size_t)9 * a.cin * 16, 0.f);
+    for (size_t k = 0; k < (size_t)9 * a.cin; ++k)
+        for (int o = 0; o < a.cout; ++o) wk16[k * 16 + o] = wk_simt[k * a.cout + o];
+    ConvArgs a16 = a;
+    a16.cout = 16;
+    a16.out_cs = 16;  // not used by the head epilogue
+    if (!tc_plan_conv(plan, a16, n_in, wk16, err, why)) return false;
+    plan.head = true;
+    plan.cout = a.cout;
+    return true;
+}
+
+cudaError_t launch_conv_tc_head(const TcConvPlan &plan, const ConvArgs &a, const float *up, float *flow,
+                                cudaStream_t st) {
+    if (!plan.enabled || !plan.head) return cudaErrorInvalidValue;
+    const ptrdiff_t off = static_cast<const char *>(a.in) - static_cast<const char *>(plan.in_base);
+    if (off < 0 || off % (ptrdiff_t)plan.img_bytes != 0) return cudaErrorInvalidValue;
+    const int img_off = (int)(off / (ptrdiff_t)plan.img_bytes);
+    if (img_off + a.n > plan.n_in || a.n < 1) return cudaErrorInvalidValue;
+    TcLaunch lp{plan.nch, plan.stride, plan.ho, plan.wo, img_off, nullptr, 0, a.bias, 0, plan.err, flow, up};
+    return launch_bn<16, true>(plan, lp, a.n, st);
+}
+
 cudaError_t launch_conv_tc(const TcConvPlan &plan, const ConvArgs &a, cudaStream_t st) {
-    if (!plan.enabled) return cudaErrorInvalidValue;
+    if (!plan.enabled || plan.head) return cudaErrorInvalidValue;
     const ptrdiff_t off = static_cast<const char *>(a.in) - static_cast<const char *>(plan.in_base);
     if (off < 0 || off % (ptrdiff_t)plan.img_bytes != 0) return cudaErrorInvalidValue;
     const int img_off = (int)(off / (ptrdiff_t)plan.img_bytes);
     if (img_off + a.n > plan.n_in || a.n < 1) return cudaErrorInvalidValue;
     if (reinterpret_cast<uintptr_t>(a.out) % 16 != 0 || a.out_cs % 8 != 0) return cudaErrorInvalidValue;
     TcLaunch lp{plan.nch, plan.stride, plan.ho, plan.wo, img_off, static_cast<__nv_bfloat16 *>(a.out), a.out_cs,
-                a.bias, a.leaky, plan.err};
+                a.bias, a.leaky, plan.err, nullptr, nullptr};
     switch (plan.bn) {
         case 16: return launch_bn<16>(plan, lp, a.n, st);
         case 32: return launch_bn<32>(plan, lp, a.n, st);

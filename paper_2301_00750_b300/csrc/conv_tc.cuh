@@ -15,6 +15,7 @@ namespace tc {
 // activations (covering all n_in images of the buffer) and of the weights.
 struct TcConvPlan {
     bool enabled = false;
+    bool head = false;  // flow-head plan (float flow output, see tc_plan_head)
     CUtensorMap tmA;  // 64-byte aligned type
     CUtensorMap tmB;
     int bn = 0, nch = 0, stride = 1, h = 0, w = 0, ho = 0, wo = 0, n_in = 0, cout = 0;
@@ -32,6 +33,15 @@ struct TcConvPlan {
 // the caller uses the CUDA-core kernel).
 bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vector<float> &wk_simt, int *err,
                   std::string &why);
+
+// Plans the flow head (cout <= 16, no activation; in practice 2) on the tensor cores: the
+// weights are zero-padded to 16 outputs for the MMA.
+bool tc_plan_head(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vector<float> &wk_simt, int *err,
+                  std::string &why);
+
+// Launches a planned head: flow[i] = up[i] (if up) + bias + conv(a.in)[i][0..1], float (n, ho, wo, 2).
+cudaError_t launch_conv_tc_head(const TcConvPlan &plan, const ConvArgs &a, const float *up, float *flow,
+                                cudaStream_t st);
 
 // Launches a planned conv for a.n images starting at a.in (which must lie inside the
 // planned buffer, on an image boundary), writing bfloat16 to a.out with a.out_cs stride.

@@ -1,0 +1,282 @@
+// Correlation cost volume (Sec. 3.2) on the 5th-generation tensor cores.
+//
+// For a block of 16 x 8 output pixels the products f_self(x) . f_other(q) are a dense GEMM
+// D[m][n] = sum_c A[m][c] B[n][c] with M = 128 block pixels and N = the (16+2R) x (8+2R)
+// halo positions q around the block; the cost volume of pixel m at displacement d is the
+// entry D[m][q = m + d] (81 of the 384 columns of its row for R = 4).  One TMA load brings
+// the block's self features [8][16][64 ch] and one the halo of the other map
+// [8+2R][16+2R][64 ch] (zero outside the map, which gives the zero product the definition
+// asks for), 128-byte swizzled; one lane issues tcgen05.mma kind::f16 (BF16 x BF16 -> FP32)
+// for the two halves of N into TMEM; the four warps then read, per displacement row dy, the
+// two halo rows their 32 pixels need (tcgen05.ld), pick each pixel's 2R+1 entries through a
+// per-thread shared-memory slice, scale by 1/C, apply LeakyReLU, and store the (2R+1)^2
+// values in bfloat16.  The self features of the pixel are copied into the estimator input in
+// the same pass.  Waits are bounded like those of the convolution kernel.
+#include <mutex>
+
+#include "corr_tc.cuh"
+#include "tc_ptx.cuh"
+
+namespace tc {
+
+namespace {
+
+using namespace ptx;
+
+constexpr int BX = 16, BY = 8;  // output pixel block: M = 128 rows, row m = py * 16 + px
+constexpr int BK = 64;          // channels per TMA step (128 B of bf16)
+constexpr int MAX_NCH = 2;      // channels <= 128
+constexpr uint32_t A_BYTES = BX * BY * BK * 2;
+constexpr int STAGE_STRIDE = 49;  // floats per thread slice (48 used; odd stride avoids bank conflicts)
+
+enum : int { ERR_CORR_MMA = 5, ERR_CORR_EPILOGUE = 6, ERR_CORR_DRAIN = 7 };
+
+template <int R>
+struct Geo {
+    static constexpr int HX = BX + 2 * R, HY = BY + 2 * R, NPOS = HX * HY;
+    static constexpr int NP = (NPOS + 31) / 32 * 32, NH = NP / 2;
+    static constexpr uint32_t B_BYTES = (uint32_t)NP * BK * 2;
+    static constexpr int ND = (2 * R + 1) * (2 * R + 1);
+    static constexpr uint32_t TMEM_COLS = NP <= 256 ? 256 : 512;
+    static constexpr size_t SMEM = (size_t)MAX_NCH * (A_BYTES + B_BYTES) + 1024 + 256;
+    static_assert(NH % 16 == 0 && NH <= 256, "MMA N");
+    static_assert((2 * (BY / 2 - 1) + 2 * R) * HX + 48 <= NP, "epilogue column window");
+};
+
+struct CorrTcLaunch {
+    int h, w, nch;
+    int img_s[2], img_o[2];
+    __nv_bfloat16 *out;
+    int out_cs;
+    int vec_out;  // out and out_cs allow 16-byte stores
+    const __nv_bfloat16 *fs[2];
+    int c;
+    __nv_bfloat16 *self_copy;
+    float inv_c;
+    int *err;
+};
+
+template <int R>
+__global__ void __launch_bounds__(128, 1)
+corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmO, const CorrTcLaunch p) {
+    using G = Geo<R>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + MAX_NCH * A_BYTES;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + MAX_NCH * (A_BYTES + G::B_BYTES));
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + MAX_NCH + 1);
+    const uint32_t full0 = smem_u32(bars), accum = smem_u32(bars + MAX_NCH);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.z, x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+
+    if (threadIdx.x == 0) {
+        for (int ch = 0; ch < MAX_NCH; ++ch) mbar_init(full0 + 8 * ch, 1);
+        mbar_init(accum, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(G::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (threadIdx.x == 0) {
+        // ---- producer: every channel step at once (the whole block fits in shared memory)
+        for (int ch = 0; ch < p.nch; ++ch) {
+            const uint32_t fb = full0 + 8 * ch;
+            mbar_expect_tx(fb, A_BYTES + (uint32_t)G::NPOS * BK * 2);
+            tma_load_4d(&tmS, fb, smem_u32(sA + ch * A_BYTES), ch * BK, x0, y0, p.img_s[b]);
+            tma_load_4d(&tmO, fb, smem_u32(sB + ch * G::B_BYTES), ch * BK, x0 - R, y0 - R, p.img_o[b]);
+        }
+    } else if (threadIdx.x == 32) {
+        // ---- MMA issuer: D[:, 0:NH] and D[:, NH:NP]
+        constexpr uint32_t idesc = idesc_bf16(128, G::NH);
+        bool ok = true;
+        for (int ch = 0; ch < p.nch && ok; ++ch) {
+            if (!mbar_wait(full0 + 8 * ch, 0, p.err, ERR_CORR_MMA)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint64_t da = sw128_desc(smem_u32(sA + ch * A_BYTES));
+            const uint64_t db0 = sw128_desc(smem_u32(sB + ch * G::B_BYTES));
+            const uint64_t db1 = sw128_desc(smem_u32(sB + ch * G::B_BYTES + (uint32_t)G::NH * BK * 2));
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+                const uint32_t acc = (ch | kk) != 0 ? 1u : 0u;
+                umma_bf16(tmem, da + (uint64_t)(kk * 2), db0 + (uint64_t)(kk * 2), idesc, acc);
+                umma_bf16(tmem + (uint32_t)G::NH, da + (uint64_t)(kk * 2), db1 + (uint64_t)(kk * 2), idesc, acc);
+            }
+        }
+        umma_commit(accum);
+        if (!ok) {
+            // Error path: let every issued load land before the CTA exits.
+            for (int ch = 0; ch < p.nch; ++ch) {
+                const unsigned long long t0 = global_ns();
+                while (!mbar_try(full0 + 8 * ch, 0))
+                    if (global_ns() - t0 > WAIT_NS) {
+                        atomicCAS(p.err, 0, ERR_CORR_DRAIN);
+                        break;
+                    }
+            }
+        }
+    }
+
+    int ok = 1;
+    if (lane == 0) ok = mbar_wait(accum, 0, p.err, ERR_CORR_EPILOGUE) && *(volatile int *)p.err == 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        // The MMAs have completed, so the operand buffers are free: reuse them as the
+        // per-thread slices that turn a window of TMEM columns into indexed values.
+        float *slice = reinterpret_cast<float *>(smem) + threadIdx.x * STAGE_STRIDE;
+        const int py = threadIdx.x >> 4, px = threadIdx.x & 15;
+        const int y = y0 + py, x = x0 + px;
+        const bool valid = y < p.h && x < p.w;
+        const int base = (py & 1) * G::HX + px;
+        float res[G::ND];
+#pragma unroll
+        for (int j = 0; j <= 2 * R; ++j) {
+            // halo rows 2 warp + j and 2 warp + j + 1 cover both pixel rows of this warp
+            const uint32_t col0 = (uint32_t)((2 * warp + j) * G::HX);
+            uint32_t r0[16], r1[16], r2[16];
+            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + col0;
+            tmem_ld16(ta, r0);
+            tmem_ld16(ta + 16, r1);
+            tmem_ld16(ta + 32, r2);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                slice[i] = __uint_as_float(r0[i]);
+                slice[16 + i] = __uint_as_float(r1[i]);
+                slice[32 + i] = __uint_as_float(r2[i]);
+            }
+#pragma unroll
+            for (int i = 0; i <= 2 * R; ++i) {
+                const float v = slice[base + i] * p.inv_c;
+                res[j * (2 * R + 1) + i] = v >= 0.f ? v : 0.1f * v;
+            }
+        }
+        if (valid) {
+            const size_t pix = ((size_t)b * p.h + y) * p.w + x;
+            __nv_bfloat16 *dst = p.out + pix * p.out_cs;
+            if (p.vec_out) {
+#pragma unroll
+                for (int k = 0; k + 8 <= G::ND; k += 8) {
+                    uint4 v;
+                    v.x = pack_bf16x2(res[k], res[k + 1]);
+                    v.y = pack_bf16x2(res[k + 2], res[k + 3]);
+                    v.z = pack_bf16x2(res[k + 4], res[k + 5]);
+                    v.w = pack_bf16x2(res[k + 6], res[k + 7]);
+                    *reinterpret_cast<uint4 *>(dst + k) = v;
+                }
+#pragma unroll
+                for (int k = G::ND / 8 * 8; k < G::ND; ++k) dst[k] = __float2bfloat16_rn(res[k]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < G::ND; ++k) dst[k] = __float2bfloat16_rn(res[k]);
+            }
+            if (p.self_copy) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(p.fs[b] + ((size_t)y * p.w + x) * p.c);
+                uint4 *cp = reinterpret_cast<uint4 *>(p.self_copy + pix * p.out_cs);
+                for (int q = 0; q < p.c / 8; ++q) cp[q] = __ldg(src + q);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G::TMEM_COLS) : "memory");
+    }
+}
+
+bool encode_features(CUtensorMap *map, const void *base, int n, int cs, int h, int w, int c, int box_x, int box_y) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)c, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
+    const cuuint64_t strides[3] = {(cuuint64_t)cs * 2, (cuuint64_t)w * cs * 2, (cuuint64_t)h * w * cs * 2};
+    const cuuint32_t box[4] = {BK, (cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+    const cuuint32_t ones[4] = {1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims, strides, box, ones,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int R>
+cudaError_t launch_r(const CorrTcPlan &plan, const CorrTcLaunch &lp, int nb, cudaStream_t st) {
+    using G = Geo<R>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(corr_tc_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    dim3 grid((plan.w + BX - 1) / BX, (plan.h + BY - 1) / BY, nb);
+    corr_tc_kernel<R><<<grid, 128, G::SMEM, st>>>(plan.tmS, plan.tmO, lp);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_plan_corr(CorrTcPlan &plan, const void *self, int n_self, int self_cs, const void *other, int n_other,
+                  int other_cs, int h, int w, int c, int r, int *err, std::string &why) {
+    plan.enabled = false;
+    if (c % 8 != 0 || c < 8 || c > BK * MAX_NCH) { why = "channels must be a multiple of 8 up to 128"; return false; }
+    if (r < 1 || r > 4) { why = "radius must be 1..4"; return false; }
+    if (self_cs % 8 != 0 || other_cs % 8 != 0) { why = "pixel strides must be multiples of 8"; return false; }
+    if (reinterpret_cast<uintptr_t>(self) % 16 || reinterpret_cast<uintptr_t>(other) % 16) { why = "misaligned"; return false; }
+    if (!encode_features(&plan.tmS, self, n_self, self_cs, h, w, c, BX, BY) ||
+        !encode_features(&plan.tmO, other, n_other, other_cs, h, w, c, BX + 2 * r, BY + 2 * r)) {
+        why = "tensor map encoding failed";
+        return false;
+    }
+    plan.h = h;
+    plan.w = w;
+    plan.c = c;
+    plan.r = r;
+    plan.nch = (c + BK - 1) / BK;
+    plan.err = err;
+    plan.enabled = true;
+    return true;
+}
+
+cudaError_t launch_corr_tc(const CorrTcPlan &plan, int nb, const int img_self[2], const int img_other[2],
+                           __nv_bfloat16 *out, int out_cs, const __nv_bfloat16 *const fs[2],
+                           __nv_bfloat16 *self_copy, cudaStream_t st) {
+    if (!plan.enabled || nb < 1 || nb > 2) return cudaErrorInvalidValue;
+    if (self_copy && (out_cs % 8 != 0 || reinterpret_cast<uintptr_t>(self_copy) % 16 != 0 || !fs ||
+                      reinterpret_cast<uintptr_t>(fs[0]) % 16 || reinterpret_cast<uintptr_t>(fs[nb - 1]) % 16))
+        return cudaErrorInvalidValue;
+    CorrTcLaunch lp{};
+    lp.h = plan.h;
+    lp.w = plan.w;
+    lp.nch = plan.nch;
+    for (int b = 0; b < 2; ++b) {
+        lp.img_s[b] = img_self[b < nb ? b : 0];
+        lp.img_o[b] = img_other[b < nb ? b : 0];
+        lp.fs[b] = fs ? fs[b < nb ? b : 0] : nullptr;
+    }
+    lp.out = out;
+    lp.out_cs = out_cs;
+    lp.vec_out = (out_cs % 8 == 0 && reinterpret_cast<uintptr_t>(out) % 16 == 0) ? 1 : 0;
+    lp.c = plan.c;
+    lp.self_copy = self_copy;
+    lp.inv_c = 1.f / (float)plan.c;
+    lp.err = plan.err;
+    switch (plan.r) {
+        case 1: return launch_r<1>(plan, lp, nb, st);
+        case 2: return launch_r<2>(plan, lp, nb, st);
+        case 3: return launch_r<3>(plan, lp, nb, st);
+        case 4: return launch_r<4>(plan, lp, nb, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace tc

@@ -1,0 +1,39 @@
+// Tensor-core (tcgen05) correlation cost volume: plan and launch interface.
+#pragma once
+
+#include <cuda.h>
+
+#include <string>
+
+#include "common.cuh"
+
+namespace tc {
+
+// A planned tensor-core correlation over bfloat16 NHWC feature buffers.  tmS covers the
+// "self" buffer, tmO the "other" buffer (they may be the same buffer); both hold n_img
+// images of h x w pixels with c channels at pixel stride cs.
+struct CorrTcPlan {
+    bool enabled = false;
+    CUtensorMap tmS;
+    CUtensorMap tmO;
+    int h = 0, w = 0, c = 0, r = 0, nch = 0;
+    int *err = nullptr;  // device error word (not owned)
+};
+
+// Plans the correlation between channels [0, c) of `self` (n_self images, pixel stride
+// self_cs) and of `other` (n_other images, pixel stride other_cs).  Returns false with `why`
+// when not eligible (c % 8 != 0, c > 128, r > 4, misaligned buffers).
+bool tc_plan_corr(CorrTcPlan &plan, const void *self, int n_self, int self_cs, const void *other, int n_other,
+                  int other_cs, int h, int w, int c, int r, int *err, std::string &why);
+
+// Launches the planned correlation for nb <= 2 batch entries: entry b correlates image
+// img_self[b] of the self buffer with image img_other[b] of the other buffer and writes
+// LeakyReLU(mean over channels) for the (2r+1)^2 displacements, bfloat16, to
+// out + ((b h + y) w + x) out_cs + k.  If self_copy is set, it also copies the c self
+// features of pixel (b, y, x) (read from fs[b], [h][w][c]) to self_copy + ((b h + y) w + x)
+// out_cs.
+cudaError_t launch_corr_tc(const CorrTcPlan &plan, int nb, const int img_self[2], const int img_other[2],
+                           __nv_bfloat16 *out, int out_cs, const __nv_bfloat16 *const fs[2],
+                           __nv_bfloat16 *self_copy, cudaStream_t st);
+
+}  // namespace tc

@@ -14,6 +14,7 @@
 #include "../../include/tc_stream.h"
 #include "common.cuh"
 #include "conv_tc.cuh"
+#include "corr_tc.cuh"
 
 namespace tc {
 
@@ -151,6 +152,8 @@ struct LevelBufs {
     float *bias[4] = {nullptr, nullptr, nullptr, nullptr};
     float *head_w = nullptr, *head_b = nullptr;
     TcConvPlan tcplan[4];
+    TcConvPlan headplan;
+    CorrTcPlan corrplan;   // BF16: self = pyramid slots, other = pyramid (coarsest) or f2w
 };
 
 }  // namespace
@@ -176,6 +179,7 @@ struct tc_stream {
     bool poisoned = false;
     int *dev_err = nullptr;     // device error word of the tensor-core kernels (0 = ok)
     int tc_layers = 0;          // convolution layers planned on the tensor cores
+    int tc_corr_levels = 0;     // pyramid levels whose correlation runs on the tensor cores
     int launches = 0;
     std::string err;
     // per-stage timing (tc_set_profiling): events around every launch, folded lazily
@@ -243,8 +247,10 @@ static tc_status upload(tc_stream *s, float **dst, const std::vector<float> &v) 
 }
 
 static void free_all(tc_stream *s) {
-    for (auto &B : s->lv)
+    for (auto &B : s->lv) {
         for (auto &pl : B.tcplan) pl.release();
+        B.headplan.release();
+    }
     for (auto &lvl : s->pyr_plan)
         for (auto &pl : lvl) pl.release();
     for (void *p : s->allocs) cudaFree(p);
@@ -346,8 +352,9 @@ static tc_status build_stream(tc_stream *s) {
             }
         }
         if (l < 2) continue;
-        // Estimator buffers: x0 = [corr D | self c | up 2 | zero pad] then x1..x4.
-        B.x0p = round_up(D + B.c + 2, 8);
+        // Estimator buffers: x0 = [self c | corr D | up 2 | zero pad] then x1..x4 (the file's
+        // order cat(corr, self, up) is restored by permuting conv1's input channels).
+        B.x0p = round_up(B.c + D + 2, 8);
         B.off_x1 = B.x0p;
         B.off_x2 = B.off_x1 + net.dec[0];
         B.off_x3 = B.off_x2 + net.dec[1];
@@ -361,7 +368,10 @@ static tc_status build_stream(tc_stream *s) {
         TC_TRY(s, cudaMemset(B.up, 0, 2 * px * 2 * sizeof(float)), "memset");
         const HostLayer *E = &net.layers[3 * L + 5 * (L - l)];
         // conv1 reads x0 (padded to x0p), conv2 x1, conv3 x2, conv4 [x2 | x3], head [x3 | x4].
-        std::vector<int> p1 = iota_perm(E[0].cin, B.x0p);
+        std::vector<int> p1(B.x0p, -1);
+        for (int i = 0; i < B.c; ++i) p1[i] = D + i;          // self = file channels [D, D+c)
+        for (int i = 0; i < D; ++i) p1[B.c + i] = i;          // corr = file channels [0, D)
+        for (int i = 0; i < 2; ++i) p1[B.c + D + i] = D + B.c + i;  // up-flow
         std::vector<int> p4(net.dec[1] + net.dec[2]);
         for (int i = 0; i < net.dec[1]; ++i) p4[i] = net.dec[2] + i;          // x2 = file channels [dec2, dec2+dec1)
         for (int i = 0; i < net.dec[2]; ++i) p4[net.dec[1] + i] = i;          // x3 = file channels [0, dec2)
@@ -380,8 +390,23 @@ static tc_status build_stream(tc_stream *s) {
                        dec + B.off_x1, B.ctot, 1};
             plan_tc(s, B.tcplan[j], a, 2, wk);
         }
-        if ((r = upload(s, &B.head_w, simt_weights(E[4], p5, bf))) != TC_OK) return r;
+        std::vector<float> wk5 = simt_weights(E[4], p5, bf);
+        if ((r = upload(s, &B.head_w, wk5)) != TC_OK) return r;
         if ((r = upload(s, &B.head_b, E[4].b)) != TC_OK) return r;
+        if (s->prec == TC_BF16) {
+            std::string why;
+            // level L correlates the two pyramid slots; finer levels correlate with f2w
+            const void *other = l == L ? B.pyr : B.f2w;
+            if (tc_plan_corr(B.corrplan, B.pyr, 2, B.c, other, 2, B.c, B.h, B.w, B.c, s->R, s->dev_err, why))
+                s->tc_corr_levels += 1;
+        }
+        if (s->prec == TC_BF16) {
+            T *dec = static_cast<T *>(B.dec);
+            ConvArgs a{dec + B.off_x3, B.ctot, 2, B.h, B.w, net.dec[2] + net.dec[3], 1, B.h, B.w, nullptr, nullptr, 2,
+                       nullptr, 2, 0};
+            std::string why;
+            if (tc_plan_head(B.headplan, a, 2, wk5, s->dev_err, why)) s->tc_layers += 1;
+        }
     }
     const size_t img = (size_t)3 * s->H * s->W * sizeof(float);
     for (int k = 0; k < 2; ++k) {
@@ -548,16 +573,26 @@ static tc_status run_estimators(tc_stream *s, int slot_cur) {
         int fo_cs = B.c;
         if (l < s->L) {
             LevelBufs &C = s->lv[l];
-            UpArgs u{C.flow, 2, C.h, C.w, 2, B.up, dec + s->D + B.c, B.ctot};
+            UpArgs u{C.flow, 2, C.h, C.w, 2, B.up, dec + B.c + s->D, B.ctot};
             TC_LAUNCH_CAT(s, TC_PROF_UPSAMPLE, launch_up<T>(u, s->st));
             WarpArgs wa{{other_p[0], other_p[1]}, B.c, B.up, 2, B.h, B.w, B.c, B.f2w, B.c};
             TC_LAUNCH_CAT(s, TC_PROF_WARP, launch_warp<T>(wa, s->st));
             fo[0] = static_cast<T *>(B.f2w);
             fo[1] = static_cast<T *>(B.f2w) + px * B.c;
         }
-        CorrArgs ca{{self_p[0], self_p[1]}, {fo[0], fo[1]}, B.c, fo_cs, 2, B.h, B.w, B.c, s->R, dec, B.ctot,
-                    dec + s->D};
-        TC_LAUNCH_CAT(s, TC_PROF_CORRELATION, launch_corr<T>(ca, s->st));
+        if (B.corrplan.enabled) {
+            const int img_s[2] = {slot_cur, slot_cur ^ 1};
+            const int img_o[2] = {l < s->L ? 0 : slot_cur ^ 1, l < s->L ? 1 : slot_cur};
+            const __nv_bfloat16 *fs[2] = {reinterpret_cast<const __nv_bfloat16 *>(self_p[0]),
+                                          reinterpret_cast<const __nv_bfloat16 *>(self_p[1])};
+            TC_LAUNCH_CAT(s, TC_PROF_CORRELATION,
+                          launch_corr_tc(B.corrplan, 2, img_s, img_o, reinterpret_cast<__nv_bfloat16 *>(dec + B.c),
+                                         B.ctot, fs, reinterpret_cast<__nv_bfloat16 *>(dec), s->st));
+        } else {
+            CorrArgs ca{{self_p[0], self_p[1]}, {fo[0], fo[1]}, B.c, fo_cs, 2, B.h, B.w, B.c, s->R, dec + B.c, B.ctot,
+                        dec};
+            TC_LAUNCH_CAT(s, TC_PROF_CORRELATION, launch_corr<T>(ca, s->st));
+        }
         ConvArgs c1{dec, B.ctot, 2, B.h, B.w, B.x0p, 1, B.h, B.w, B.wk[0], B.bias[0], net.dec[0], dec + B.off_x1, B.ctot, 1};
         if ((r = conv_layer<T>(s, c1, &B.tcplan[0], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
         ConvArgs c2{dec + B.off_x1, B.ctot, 2, B.h, B.w, net.dec[0], 1, B.h, B.w, B.wk[1], B.bias[1], net.dec[1], dec + B.off_x2, B.ctot, 1};
@@ -566,9 +601,15 @@ static tc_status run_estimators(tc_stream *s, int slot_cur) {
         if ((r = conv_layer<T>(s, c3, &B.tcplan[2], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
         ConvArgs c4{dec + B.off_x2, B.ctot, 2, B.h, B.w, net.dec[1] + net.dec[2], 1, B.h, B.w, B.wk[3], B.bias[3], net.dec[3], dec + B.off_x4, B.ctot, 1};
         if ((r = conv_layer<T>(s, c4, &B.tcplan[3], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
-        HeadArgs ha{dec + B.off_x3, B.ctot, net.dec[2] + net.dec[3], 2, B.h, B.w, B.head_w, B.head_b,
-                    l < s->L ? B.up : nullptr, B.flow};
-        TC_LAUNCH_CAT(s, TC_PROF_HEAD, launch_head<T>(ha, s->st));
+        if (B.headplan.enabled) {
+            ConvArgs a5{dec + B.off_x3, B.ctot, 2, B.h, B.w, net.dec[2] + net.dec[3], 1, B.h, B.w, B.head_w, B.head_b,
+                        2, nullptr, 2, 0};
+            TC_LAUNCH_CAT(s, TC_PROF_HEAD, launch_conv_tc_head(B.headplan, a5, l < s->L ? B.up : nullptr, B.flow, s->st));
+        } else {
+            HeadArgs ha{dec + B.off_x3, B.ctot, net.dec[2] + net.dec[3], 2, B.h, B.w, B.head_w, B.head_b,
+                        l < s->L ? B.up : nullptr, B.flow};
+            TC_LAUNCH_CAT(s, TC_PROF_HEAD, launch_head<T>(ha, s->st));
+        }
     }
     return TC_OK;
 }
@@ -719,6 +760,8 @@ extern "C" int tc_last_launch_count(const tc_stream *s) { return s ? s->launches
 
 extern "C" int tc_tensor_core_layers(const tc_stream *s) { return s ? s->tc_layers : 0; }
 
+extern "C" int tc_tensor_core_correlation_levels(const tc_stream *s) { return s ? s->tc_corr_levels : 0; }
+
 // ------------------------------------------------------------------------------- stage ops
 
 namespace {
@@ -841,14 +884,31 @@ static tc_status op_corr(const float *f1, const float *f2, int n, int h, int w, 
     OP_TRY(launch_to_act<T>(f1, nf, a, st), "tc_op_correlation convert");
     OP_TRY(launch_to_act<T>(f2, nf, b, st), "tc_op_correlation convert");
     const size_t img = (size_t)h * w * c;
+    CorrTcPlan plan;
+    int *derr = nullptr;
+    OP_TRY(tmp.get((void **)&derr, sizeof(int)), "tc_op_correlation alloc");
+    OP_TRY(cudaMemsetAsync(derr, 0, sizeof(int), st), "tc_op_correlation memset");
+    std::string why;
+    const bool use_tc = sizeof(T) == 2 && tc_plan_corr(plan, a, n, c, b, n, c, h, w, c, r, derr, why);
     for (int i = 0; i < n; i += 2) {
         const int nb = n - i < 2 ? n - i : 2;
-        CorrArgs ca{{a + i * img, a + (i + nb - 1) * img}, {b + i * img, b + (i + nb - 1) * img}, c, c, nb, h, w, c, r,
-                    o + (size_t)i * h * w * D, D, nullptr};
-        OP_TRY(launch_corr<T>(ca, st), "tc_op_correlation launch");
+        if (use_tc) {
+            const int imgs[2] = {i, i + nb - 1};
+            OP_TRY(launch_corr_tc(plan, nb, imgs, imgs, reinterpret_cast<__nv_bfloat16 *>(o + (size_t)i * h * w * D), D,
+                                  nullptr, nullptr, st),
+                   "tc_op_correlation tensor-core launch");
+        } else {
+            CorrArgs ca{{a + i * img, a + (i + nb - 1) * img}, {b + i * img, b + (i + nb - 1) * img}, c, c, nb, h, w, c,
+                        r, o + (size_t)i * h * w * D, D, nullptr};
+            OP_TRY(launch_corr<T>(ca, st), "tc_op_correlation launch");
+        }
     }
     OP_TRY(launch_from_act<T>(o, no, out, st), "tc_op_correlation convert");
     OP_TRY(cudaStreamSynchronize(st), "tc_op_correlation sync");
+    int e = 0;
+    OP_TRY(cudaMemcpy(&e, derr, sizeof(int), cudaMemcpyDeviceToHost), "tc_op_correlation error word");
+    if (e != 0) return fail(nullptr, TC_ERR_TIMEOUT, "tc_op_correlation: tensor-core kernel gave up waiting");
+    g_last_op_tc = use_tc ? 1 : 0;
     return TC_OK;
 }
 

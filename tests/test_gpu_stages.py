@@ -43,7 +43,8 @@ def test_warp_features(prec, n, h, w, c, mag):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
-@pytest.mark.parametrize("n,h,w,c,r", [(2, 19, 21, 32, 4), (1, 34, 60, 128, 4), (2, 8, 8, 48, 3), (2, 33, 47, 16, 2)])
+@pytest.mark.parametrize("n,h,w,c,r", [(2, 19, 21, 32, 4), (1, 34, 60, 128, 4), (2, 8, 8, 48, 3), (2, 33, 47, 16, 2),
+                                       (1, 21, 37, 24, 1), (3, 68, 120, 96, 4), (2, 136, 240, 64, 4)])
 def test_correlation(prec, n, h, w, c, r):
     g = synth.rng(22)
     f1 = g.normal(size=(n, c, h, w)).astype(np.float32)
@@ -51,6 +52,8 @@ def test_correlation(prec, n, h, w, c, r):
     if prec == "bf16":
         f1, f2 = bf16_round(f1), bf16_round(f2)
     got = to_np(tc.op_correlation(to_dev(nchw_to_nhwc(f1)), to_dev(nchw_to_nhwc(f2)), r, precision=prec))
+    # BF16 cost volumes with c a multiple of 8 up to 128 run on the tensor cores (banded GEMM)
+    assert tc.op_last_used_tensor_cores() == (prec == "bf16" and c % 8 == 0 and c <= 128)
     for i in range(n):
         ref = oracle.correlation(f1[i], f2[i], r)
         g_ = nhwc_to_nchw(got[i:i + 1])[0]

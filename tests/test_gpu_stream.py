@@ -119,16 +119,18 @@ def test_stream_flows_bf16(name, chans, radius, W, H):
     assert eb <= bound and ef <= bound, (eb, ef, bound)
 
 
-@pytest.mark.parametrize("chans,radius,want", [((16, 32, 48), 3, 16), ((16, 32, 64, 96, 128), 4, 30)])
+@pytest.mark.parametrize("chans,radius,want", [((16, 32, 48), 3, 18), ((16, 32, 64, 96, 128), 4, 34)])
 def test_bf16_stream_plans_convs_on_tensor_cores(chans, radius, want):
-    """Every pyramid conv but the first (3 input channels) and every estimator conv1..conv4
-    runs on the tensor cores in a BF16 stream; an FP32 stream uses none."""
+    """Every pyramid conv but the first (3 input channels), every estimator conv1..conv4 and
+    every flow head runs on the tensor cores in a BF16 stream, and so does the correlation of
+    every estimator level; an FP32 stream uses none."""
     path, _ = weights_file(chans, radius)
     s = tc.Stream(64, 64, "bf16", weights_path=path)
     assert s.tensor_core_layers == want
+    assert s.tensor_core_correlation_levels == len(chans) - 1
     s.destroy()
     s = tc.Stream(64, 64, "fp32", weights_path=path)
-    assert s.tensor_core_layers == 0
+    assert s.tensor_core_layers == 0 and s.tensor_core_correlation_levels == 0
     s.destroy()
 
 
