@@ -212,8 +212,10 @@ def time_stream(tc, torch, path, dev_frames, dev_styl, precision, steps, warmup,
     per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
     total = ev[0].elapsed_time(ev[steps])
     prof = s.get_profile() if profile else None
+    tc_layers, tc_corr = s.tensor_core_layers, s.tensor_core_correlation_levels
     s.destroy()
-    return dict(total_ms=total, per_frame_ms=per, launches=launches, profile=prof)
+    return dict(total_ms=total, per_frame_ms=per, launches=launches, profile=prof, tc_layers=tc_layers,
+                tc_corr=tc_corr)
 
 
 def e2e_host(tc, torch, path, frames, styl, precision, steps, warmup):
@@ -303,16 +305,20 @@ def run_ours(args):
     p = prof["profile"]
     steps = args.steps
     dom = max(p, key=lambda k: p[k][0])
-    tensor_path = False  # set by the library once the tcgen05 convs are in the BF16 path
+    # Convs (and the correlation) of a BF16 stream run on the tensor cores: roofline against
+    # the measured dense bf16 peak, the sustained figure since the kernels run inside a long
+    # step.  FP32 streams run on the CUDA cores: derived FP32 FMA peak.
+    tensor_path = prof["tc_layers"] > 0 if dom != "correlation" else prof["tc_corr"] > 0
+    peaks = measured_peaks()
     if dom in ("estimator_conv", "pyramid_conv", "head", "correlation"):
         achieved = flops[dom] * steps / (p[dom][0] / 1e3) / 1e12
         if tensor_path:
-            peak, unit, bound = None, "TFLOP/s", "tensor"
+            peak, unit, bound = peaks.get("bf16_tflops_sustained"), "TFLOP/s", "tensor"
         else:
             peak, unit, bound = FP32_SIMT_PEAK_TFLOPS, "TFLOP/s", "alu"
     else:
         achieved = CONSISTENCY_BYTES_PER_PX * WIDTH * HEIGHT * steps / (p[dom][0] / 1e3) / 1e9
-        peak, unit, bound = measured_peaks().get("hbm_gbs"), "GB/s", "hbm"
+        peak, unit, bound = peaks.get("hbm_gbs"), "GB/s", "hbm"
     per = sorted(main["per_frame_ms"])
     line = {
         "metric": METRIC, "value": round(world * steps / total_s, 3), "unit": UNIT, "n_gpus": world,
@@ -328,7 +334,8 @@ def run_ours(args):
         "roofline": {"kernel": dom, "bound": bound, "achieved": round(achieved, 2), "peak": peak, "unit": unit,
                      "frac": round(achieved / peak, 4) if peak else None, "traffic": None,
                      "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2032 MHz" if bound == "alu"
-                     else "of measured (MEASURED_PEAKS.json)"},
+                     else ("of measured bf16 sustained (MEASURED_PEAKS.json)" if bound == "tensor"
+                           else "of measured HBM copy (MEASURED_PEAKS.json)")},
         "gpu_launches": main["launches"],
         "clocks": clk,
         "e2e": {"value": round(e2e_v * (world if world > 1 else 1), 3), "unit": UNIT,

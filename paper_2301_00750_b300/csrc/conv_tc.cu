@@ -1,6 +1,9 @@
 // Implicit-GEMM 3x3 convolution on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
-// GEMM view: M = output pixels, N = cout, K = 9 taps x input channels.  One CTA computes a
+// GEMM view: M = output pixels, N = cout, K = 9 taps x input channels.  Stride-1 layers use
+// conv_tc_halo_kernel (below), which loads each activation tile once per kernel row and
+// reuses it for the three horizontal taps; the description here is of the per-tap kernel,
+// which serves the stride-2 layers.  One CTA computes a
 // tile of 128 consecutive output pixels of one row (M = 128) and all cout (N = BN, a
 // multiple of 16 up to 128):
 //   * warp 0, lane 0 (producer): for every (tap, 64-channel chunk) step, one TMA tiled load
@@ -53,6 +56,53 @@ struct TcLaunch {
     float *flow;      // flow-head mode: (n, ho, wo, 2) float output
     const float *up;  // flow-head mode: residual base flow, same layout, or NULL
 };
+
+// Epilogue shared by the conv kernels: thread r of the CTA owns accumulator row r, i.e.
+// output pixel (img, y, x0 + r).
+template <int BN, bool HEAD>
+__device__ __forceinline__ void conv_epilogue(uint32_t tmem, const TcLaunch &p, int warp, int lane, int x0, int y,
+                                              int img) {
+    if (HEAD) {
+        const int x = x0 + warp * 32 + lane;
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), r);
+        if (x < p.wo) {
+            const size_t pix = (size_t)(img * p.ho + y) * p.wo + x;
+            float2 up = make_float2(0.f, 0.f);
+            if (p.up) up = reinterpret_cast<const float2 *>(p.up)[pix];
+            reinterpret_cast<float2 *>(p.flow)[pix] =
+                make_float2(up.x + (__uint_as_float(r[0]) + __ldg(p.bias)), up.y + (__uint_as_float(r[1]) + __ldg(p.bias + 1)));
+        }
+    } else {
+        const int row = warp * 32 + lane;
+        const int x = x0 + row;
+        __nv_bfloat16 *dst = p.out + ((size_t)(img * p.ho + y) * p.wo + x) * p.out_cs;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t r[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+            if (x < p.wo) {
+                float v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    v[j] = __uint_as_float(r[j]) + __ldg(p.bias + c0 + j);
+                    if (p.leaky) v[j] = v[j] >= 0.f ? v[j] : 0.1f * v[j];
+                }
+                uint4 lo, hi;
+                lo.x = pack_bf16x2(v[0], v[1]);
+                lo.y = pack_bf16x2(v[2], v[3]);
+                lo.z = pack_bf16x2(v[4], v[5]);
+                lo.w = pack_bf16x2(v[6], v[7]);
+                hi.x = pack_bf16x2(v[8], v[9]);
+                hi.y = pack_bf16x2(v[10], v[11]);
+                hi.z = pack_bf16x2(v[12], v[13]);
+                hi.w = pack_bf16x2(v[14], v[15]);
+                *reinterpret_cast<uint4 *>(dst + c0) = lo;
+                *reinterpret_cast<uint4 *>(dst + c0 + 8) = hi;
+            }
+        }
+    }
+}
 
 // HEAD = true: the flow head (cout = 2, zero-padded to BN = 16 for the MMA); the epilogue
 // writes float32 flow = up + (acc[0], acc[1]) + bias without activation.
@@ -151,46 +201,138 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (lane == 0) ok = mbar_wait(accum, 0, p.err, ERR_EPILOGUE) && *(volatile int *)p.err == 0;
     ok = __shfl_sync(0xffffffffu, ok, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (HEAD && ok) {
-        const int x = x0 + warp * 32 + lane;
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), r);
-        if (x < p.wo) {
-            const size_t pix = (size_t)(img * p.ho + y) * p.wo + x;
-            float2 up = make_float2(0.f, 0.f);
-            if (p.up) up = reinterpret_cast<const float2 *>(p.up)[pix];
-            reinterpret_cast<float2 *>(p.flow)[pix] =
-                make_float2(up.x + (__uint_as_float(r[0]) + __ldg(p.bias)), up.y + (__uint_as_float(r[1]) + __ldg(p.bias + 1)));
+    if (ok) conv_epilogue<BN, HEAD>(tmem, p, warp, lane, x0, y, img);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// Stride-1 variant that fetches each activation tile once per (kernel row ky, channel
+// step): a TMA load of the 130-pixel halo row [x0 - 1, x0 + 129) x 64 channels, reused by
+// the three horizontal taps through descriptors whose start is shifted by kx rows of the
+// 128-byte-swizzled tile.  Activation halos and weight tiles travel in two separate rings
+// (2 halo slots, SB weight slots), so a halo stays resident while its three taps run.
+constexpr uint32_t HALO_ROWS = BM + 2;
+constexpr uint32_t HALO_TX = HALO_ROWS * BK * 2;  // 16,640 B
+constexpr uint32_t HALO_SLOT = 17408;             // rounded up to the 1024-byte swizzle atom
+constexpr int HALO_SA = 2;
+__host__ __device__ constexpr int halo_sb(int bn) { return bn >= 96 ? 3 : 4; }
+__host__ __device__ constexpr size_t halo_smem_for(int bn) {
+    return (size_t)HALO_SA * HALO_SLOT + (size_t)halo_sb(bn) * bn * BK * 2 + 1024 + 256;
+}
+
+template <int BN, bool HEAD>
+__global__ void __launch_bounds__(128, 1)
+conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcLaunch p) {
+    constexpr int SB = halo_sb(BN);
+    constexpr uint32_t B_BYTES = BN * BK * 2;
+    constexpr uint32_t TMEM_COLS = tmem_cols_for(BN);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + HALO_SA * HALO_SLOT;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + SB * B_BYTES);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * HALO_SA + 2 * SB + 1);
+    const uint32_t fullA = smem_u32(bars), emptyA = fullA + 8 * HALO_SA;
+    const uint32_t fullB = emptyA + 8 * HALO_SA, emptyB = fullB + 8 * SB;
+    const uint32_t accum = emptyB + 8 * SB;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x0 = blockIdx.x * BM, y = blockIdx.y, img = blockIdx.z;
+    const int ng = 3 * p.nch;  // (ky, channel step) groups
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < HALO_SA; ++s) {
+            mbar_init(fullA + 8 * s, 1);
+            mbar_init(emptyA + 8 * s, 1);
         }
-    } else if (ok) {
-        const int row = warp * 32 + lane;
-        const int x = x0 + row;
-        __nv_bfloat16 *dst = p.out + ((size_t)(img * p.ho + y) * p.wo + x) * p.out_cs;
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            uint32_t r[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-            if (x < p.wo) {
-                float v[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    v[j] = __uint_as_float(r[j]) + __ldg(p.bias + c0 + j);
-                    if (p.leaky) v[j] = v[j] >= 0.f ? v[j] : 0.1f * v[j];
+        for (int s = 0; s < SB; ++s) {
+            mbar_init(fullB + 8 * s, 1);
+            mbar_init(emptyB + 8 * s, 1);
+        }
+        mbar_init(accum, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (threadIdx.x == 0) {
+        // ---- producer
+        int ga = 0, gb = 0;  // halo loads and weight loads issued
+        bool fine = true;
+        for (int g = 0; g < ng && fine; ++g) {
+            const int ky = g / p.nch, ch = g - ky * p.nch;
+            const int sa = g % HALO_SA;
+            if (!mbar_wait(emptyA + 8 * sa, ((uint32_t)(g / HALO_SA) & 1u) ^ 1u, p.err, ERR_PRODUCER)) break;
+            mbar_expect_tx(fullA + 8 * sa, HALO_TX);
+            tma_load_4d(&tmA, fullA + 8 * sa, smem_u32(sA + sa * HALO_SLOT), ch * BK, x0 - 1, y + ky - 1,
+                        img + p.img_off);
+            ga = g + 1;
+            for (int kx = 0; kx < 3; ++kx) {
+                const int kb = 3 * g + kx, sb = kb % SB;
+                if (!mbar_wait(emptyB + 8 * sb, ((uint32_t)(kb / SB) & 1u) ^ 1u, p.err, ERR_PRODUCER)) {
+                    fine = false;
+                    break;
                 }
-                uint4 lo, hi;
-                lo.x = pack_bf16x2(v[0], v[1]);
-                lo.y = pack_bf16x2(v[2], v[3]);
-                lo.z = pack_bf16x2(v[4], v[5]);
-                lo.w = pack_bf16x2(v[6], v[7]);
-                hi.x = pack_bf16x2(v[8], v[9]);
-                hi.y = pack_bf16x2(v[10], v[11]);
-                hi.z = pack_bf16x2(v[12], v[13]);
-                hi.w = pack_bf16x2(v[14], v[15]);
-                *reinterpret_cast<uint4 *>(dst + c0) = lo;
-                *reinterpret_cast<uint4 *>(dst + c0 + 8) = hi;
+                mbar_expect_tx(fullB + 8 * sb, B_BYTES);
+                tma_load_3d(&tmB, fullB + 8 * sb, smem_u32(sB + sb * B_BYTES), ch * BK, 0, ky * 3 + kx);
+                gb = kb + 1;
             }
         }
+        if (ga < ng || gb < 3 * ng) {
+            // Error path: let the loads already issued land before the CTA exits.
+            const unsigned long long t0 = global_ns();
+            for (int g = ga - HALO_SA < 0 ? 0 : ga - HALO_SA; g < ga; ++g)
+                while (!mbar_try(fullA + 8 * (g % HALO_SA), (uint32_t)(g / HALO_SA) & 1u))
+                    if (global_ns() - t0 > WAIT_NS) { atomicCAS(p.err, 0, ERR_DRAIN); break; }
+            for (int kb = gb - SB < 0 ? 0 : gb - SB; kb < gb; ++kb)
+                while (!mbar_try(fullB + 8 * (kb % SB), (uint32_t)(kb / SB) & 1u))
+                    if (global_ns() - t0 > WAIT_NS) { atomicCAS(p.err, 0, ERR_DRAIN); break; }
+        }
+    } else if (threadIdx.x == 32) {
+        // ---- MMA issuer
+        constexpr uint32_t idesc = idesc_bf16(BM, BN);
+        bool fine = true;
+        for (int g = 0; g < ng && fine; ++g) {
+            const int sa = g % HALO_SA;
+            if (!mbar_wait(fullA + 8 * sa, (uint32_t)(g / HALO_SA) & 1u, p.err, ERR_MMA)) break;
+            const uint32_t a0 = smem_u32(sA + sa * HALO_SLOT);
+            for (int kx = 0; kx < 3; ++kx) {
+                const int kb = 3 * g + kx, sb = kb % SB;
+                if (!mbar_wait(fullB + 8 * sb, (uint32_t)(kb / SB) & 1u, p.err, ERR_MMA)) {
+                    fine = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint64_t da = sw128_desc_shifted(a0 + 128u * (uint32_t)kx);
+                const uint64_t db = sw128_desc(smem_u32(sB + sb * B_BYTES));
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                    umma_bf16(tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                              (g | kx | kk) != 0 ? 1u : 0u);
+                umma_commit(emptyB + 8 * sb);
+            }
+            if (fine) umma_commit(emptyA + 8 * sa);  // the halo's three taps are done
+        }
+        umma_commit(accum);
     }
+
+    int ok = 1;
+    if (lane == 0) ok = mbar_wait(accum, 0, p.err, ERR_EPILOGUE) && *(volatile int *)p.err == 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) conv_epilogue<BN, HEAD>(tmem, p, warp, lane, x0, y, img);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -201,16 +343,28 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
 template <int BN, bool HEAD = false>
 cudaError_t launch_bn(const TcConvPlan &plan, const TcLaunch &lp, int n_img, cudaStream_t st) {
-    static bool attr_set = false;
-    const size_t smem = smem_bytes_for(BN);
-    if (!attr_set) {
-        cudaError_t e =
-            cudaFuncSetAttribute(conv_tc_kernel<BN, HEAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
     dim3 grid((plan.wo + BM - 1) / BM, plan.ho, n_img);
-    conv_tc_kernel<BN, HEAD><<<grid, 128, smem, st>>>(plan.tmA, plan.tmB, lp);
+    if (plan.stride == 1) {
+        static bool attr_set = false;
+        const size_t smem = halo_smem_for(BN);
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(conv_tc_halo_kernel<BN, HEAD>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        conv_tc_halo_kernel<BN, HEAD><<<grid, 128, smem, st>>>(plan.tmA, plan.tmB, lp);
+    } else {
+        static bool attr_set = false;
+        const size_t smem = smem_bytes_for(BN);
+        if (!attr_set) {
+            cudaError_t e =
+                cudaFuncSetAttribute(conv_tc_kernel<BN, HEAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        conv_tc_kernel<BN, HEAD><<<grid, 128, smem, st>>>(plan.tmA, plan.tmB, lp);
+    }
     return cudaGetLastError();
 }
 
@@ -271,7 +425,7 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
     if (a.stride == 1) {
         const cuuint64_t dims[4] = {(cuuint64_t)a.cin, (cuuint64_t)a.w, (cuuint64_t)a.h, (cuuint64_t)n_in};
         const cuuint64_t strides[3] = {a.in_cs * esz, (cuuint64_t)a.w * a.in_cs * esz, (cuuint64_t)a.h * a.w * a.in_cs * esz};
-        const cuuint32_t box[4] = {BK, BM, 1, 1};
+        const cuuint32_t box[4] = {BK, HALO_ROWS, 1, 1};  // the stride-1 kernel loads halo rows
         r = enc(&plan.tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(a.in), dims, strides, box, ones,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

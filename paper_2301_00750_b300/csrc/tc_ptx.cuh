@@ -93,6 +93,11 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
+// The same descriptor for an operand whose first row does not start a 1024-byte swizzle
+// atom (a row-shifted view of a 1024-aligned tile).  The 128-byte swizzle is applied to the
+// address bits of each row, so the shifted start alone selects the right rows.
+__device__ __forceinline__ uint64_t sw128_desc_shifted(uint32_t saddr) { return sw128_desc(saddr); }
+
 // Instruction descriptor of kind::f16: D f32, A and B bf16, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
