@@ -91,10 +91,17 @@ struct CorrArgs {
 struct WarpArgs {
     const void *f[2];  // per batch entry, [h][w][f_cs]
     int f_cs;
-    const float *flow;  // [n][h][w][2]
+    const float *flow;  // [n][h][w][2], or NULL when `coarse` is given
     int n, h, w, c;
     void *out;          // [n][h][w][out_cs]
     int out_cs;
+    // Optional fused x2 upsampling: the flow at (x, y) is the upsampled coarse flow
+    // [n][h/2][w/2][2]; it is also written to up_out [n][h][w][2] and, in the activation
+    // type, to act [n][h][w][act_cs] (the up-flow channels of the estimator input).
+    const float *coarse;
+    float *up_out;
+    void *act;
+    int act_cs;
 };
 
 struct UpArgs {

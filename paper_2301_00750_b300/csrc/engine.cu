@@ -573,9 +573,10 @@ static tc_status run_estimators(tc_stream *s, int slot_cur) {
         int fo_cs = B.c;
         if (l < s->L) {
             LevelBufs &C = s->lv[l];
-            UpArgs u{C.flow, 2, C.h, C.w, 2, B.up, dec + B.c + s->D, B.ctot};
-            TC_LAUNCH_CAT(s, TC_PROF_UPSAMPLE, launch_up<T>(u, s->st));
-            WarpArgs wa{{other_p[0], other_p[1]}, B.c, B.up, 2, B.h, B.w, B.c, B.f2w, B.c};
+            // x2 upsampling of the coarser flow fused into the feature warp; the up-flow also
+            // lands in B.up (residual base) and in the estimator input.
+            WarpArgs wa{{other_p[0], other_p[1]}, B.c, nullptr, 2, B.h, B.w, B.c, B.f2w, B.c,
+                        C.flow, B.up, dec + B.c + s->D, B.ctot};
             TC_LAUNCH_CAT(s, TC_PROF_WARP, launch_warp<T>(wa, s->st));
             fo[0] = static_cast<T *>(B.f2w);
             fo[1] = static_cast<T *>(B.f2w) + px * B.c;
@@ -933,7 +934,8 @@ static tc_status op_warp(const float *f, const float *flow, int n, int h, int w,
     const size_t img = (size_t)h * w * c;
     for (int i = 0; i < n; i += 2) {
         const int nb = n - i < 2 ? n - i : 2;
-        WarpArgs wa{{a + i * img, a + (i + nb - 1) * img}, c, flow + (size_t)i * h * w * 2, nb, h, w, c, o + i * img, c};
+        WarpArgs wa{{a + i * img, a + (i + nb - 1) * img}, c, flow + (size_t)i * h * w * 2, nb, h, w, c, o + i * img, c,
+                    nullptr, nullptr, nullptr, 0};
         OP_TRY(launch_warp<T>(wa, st), "tc_op_warp_features launch");
     }
     OP_TRY(launch_from_act<T>(o, nf, out, st), "tc_op_warp_features convert");

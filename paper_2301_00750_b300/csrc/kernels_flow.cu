@@ -315,7 +315,9 @@ cudaError_t launch_corr(const CorrArgs &a, cudaStream_t st) {
 
 // =====================================================================================
 // Bilinear feature warp, zeros off the map: out(x) = sum of on-map taps of f at x + flow.
-// One thread per (pixel, 4 channels).  The integer part of the sample position and the
+// One thread per (pixel, 4 channels).  With `coarse` set, the flow is the x2 upsampling of
+// the coarser level's flow, computed here (and stored once per pixel) instead of by a
+// separate pass.  The integer part of the sample position and the
 // interpolation weights are taken from the flow alone (floor(u), u - floor(u)), which is
 // exact in float32.
 // =====================================================================================
@@ -330,7 +332,21 @@ __global__ void __launch_bounds__(256) warp_kernel(WarpArgs a) {
     const int hwp = a.h * a.w;
     const int b = (int)(p / hwp), rem = (int)(p - (size_t)b * hwp);
     const int y = rem / a.w, x = rem - y * a.w;
-    const float2 fl = reinterpret_cast<const float2 *>(a.flow)[p];
+    float2 fl;
+    if (a.coarse) {
+        const int ch = a.h / 2, cw = a.w / 2;
+        fl = upsampled_flow_at(a.coarse + (size_t)b * ch * cw * 2, ch, cw, 2, x, y);
+        if (q == 0) {
+            reinterpret_cast<float2 *>(a.up_out)[p] = fl;
+            if (a.act) {
+                T *dst = static_cast<T *>(a.act) + p * a.act_cs;
+                dst[0] = from_f<T>(fl.x);
+                dst[1] = from_f<T>(fl.y);
+            }
+        }
+    } else {
+        fl = reinterpret_cast<const float2 *>(a.flow)[p];
+    }
     const float u = fminf(fmaxf(fl.x, -1e6f), 1e6f), v = fminf(fmaxf(fl.y, -1e6f), 1e6f);
     const float fu = floorf(u), fv = floorf(v);
     const float ax = u - fu, ay = v - fv;
