@@ -127,6 +127,12 @@ TC_API tc_status tc_process_frame(tc_stream *s, const float *I_t, const float *P
 TC_API tc_status tc_process_frame_host(tc_stream *s, const float *I_t, const float *P_t, float *O_t,
                                 float *wc_opt, uint8_t *mask_opt);
 
+/* CUDA graphs (on by default): from the third frame on, a stream replays one captured graph
+ * per slot parity -- every launch of the frame in one cudaGraphLaunch -- after updating the
+ * two kernel nodes that read the caller's buffers.  enable = 0 returns to one launch per
+ * kernel.  Waits for the stream.  Per-stage profiling always runs without graphs. */
+TC_API tc_status tc_set_graphs(tc_stream *s, int enable);
+
 /* Writes the flows of the last processed frame at full resolution: Fb = F_{t->t-1} and
  * Ff = F_{t-1->t}, each device (2, H, W) float32 (planar u then v).  Either may be NULL.
  * Errors: TC_ERR_STATE before the second frame. */

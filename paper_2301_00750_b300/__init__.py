@@ -31,7 +31,7 @@ EXPORTED = ["tc_default_consistency", "tc_create_stream", "tc_set_consistency", 
             "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
             "tc_op_consistency", "tc_set_profiling", "tc_get_profile", "tc_synchronize", "tc_tensor_core_layers",
             "tc_op_last_used_tensor_cores", "tc_op_correlation_bf16_noalloc",
-            "tc_tensor_core_correlation_levels"]
+            "tc_tensor_core_correlation_levels", "tc_set_graphs"]
 NOALLOC_SCRATCH_BYTES = 16 << 20
 PROFILE_CATEGORIES = ["pyramid_conv", "estimator_conv", "head", "correlation", "warp", "upsample", "consistency",
                       "other"]
@@ -68,13 +68,14 @@ _lib.tc_op_warp_features.argtypes = [_i, _vp, _vp, _i, _i, _i, _i, _vp, _vp]
 _lib.tc_op_upsample_flow.argtypes = [_vp, _i, _i, _i, _i, _vp, _vp]
 _lib.tc_op_consistency.argtypes = [_vp] * 7 + [_i] * 5 + [ctypes.POINTER(TcConsistency), _vp, _vp, _vp, _vp]
 _lib.tc_set_profiling.argtypes = [_vp, _i]
+_lib.tc_set_graphs.argtypes = [_vp, _i]
 _lib.tc_op_correlation_bf16_noalloc.argtypes = [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp]
 _lib.tc_synchronize.argtypes = [_vp]
 _lib.tc_tensor_core_layers.argtypes = [_vp]
 _lib.tc_tensor_core_correlation_levels.argtypes = [_vp]
 _lib.tc_op_last_used_tensor_cores.argtypes = []
 _lib.tc_get_profile.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), _i]
-for _n in ["tc_op_correlation_bf16_noalloc", "tc_synchronize", "tc_set_profiling", "tc_get_profile", "tc_create_stream", "tc_set_consistency", "tc_process_frame", "tc_process_frame_host", "tc_get_flows",
+for _n in ["tc_set_graphs", "tc_op_correlation_bf16_noalloc", "tc_synchronize", "tc_set_profiling", "tc_get_profile", "tc_create_stream", "tc_set_consistency", "tc_process_frame", "tc_process_frame_host", "tc_get_flows",
            "tc_destroy", "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
            "tc_op_consistency"]:
     getattr(_lib, _n).restype = ctypes.c_int
@@ -180,6 +181,10 @@ class Stream:
     def get_flows(self, Fb=None, Ff=None):
         import torch
         _check(_lib.tc_get_flows(self._h, _ptr(Fb, torch.float32, "Fb"), _ptr(Ff, torch.float32, "Ff")), self._h)
+
+    def set_graphs(self, enable: bool):
+        """Replay each frame as one CUDA graph launch (default) or launch kernel by kernel."""
+        _check(_lib.tc_set_graphs(self._h, int(bool(enable))), self._h)
 
     def set_profiling(self, enable: bool):
         _check(_lib.tc_set_profiling(self._h, int(bool(enable))), self._h)

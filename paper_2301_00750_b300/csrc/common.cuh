@@ -132,6 +132,10 @@ template <typename T> cudaError_t launch_corr(const CorrArgs &a, cudaStream_t st
 template <typename T> cudaError_t launch_warp(const WarpArgs &a, cudaStream_t st);
 template <typename T> cudaError_t launch_up(const UpArgs &a, cudaStream_t st);
 cudaError_t launch_consistency(const ConsistArgs &a, cudaStream_t st);
+// Device entry addresses of the two kernels whose arguments change every frame (used to
+// find their nodes in a captured CUDA graph).
+template <typename T> const void *conv_first_kernel_fn();
+const void *consistency_kernel_fn();
 cudaError_t launch_flow_out(const float *flow, int fh, int fw, int scale, int H, int W,
                             float *out, cudaStream_t st);
 template <typename T> cudaError_t launch_to_act(const float *in, size_t n, T *out, cudaStream_t st);

@@ -188,6 +188,19 @@ struct tc_stream {
     std::vector<int> ev_cat;       // category of pending pair k (events 2k, 2k+1)
     double prof_ms[TC_PROF_CATEGORIES] = {0};
     long long prof_n[TC_PROF_CATEGORIES] = {0};
+    // CUDA graphs of a whole frame, one per slot parity (the pointers of every launch depend
+    // only on the parity, except the caller's buffers read by the first pyramid conv and the
+    // consistency pass, whose nodes are updated before each replay).
+    bool graphs = true;
+    cudaStream_t gst = nullptr;               // library stream the graphs are captured on and replayed on
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;  // fence gst to the caller's stream
+    struct FrameGraph {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaGraphNode_t n_first = nullptr, n_cons = nullptr;
+        cudaKernelNodeParams p_first{}, p_cons{};
+        int launches = 0;
+    } fg[2];
 };
 
 static std::mutex g_err_mu;
@@ -621,13 +634,8 @@ static tc_status check_stream(tc_stream *s, const char *fn) {
     return TC_OK;
 }
 
-template <typename T>
-static tc_status process(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask) {
-    tc_status r;
-    s->launches = 0;
-    if (s->ev_cat.size() > 4096 && (r = prof_flush(s)) != TC_OK) return r;
-    const int cur = (int)(s->t & 1), prev = cur ^ 1;
-    if ((r = run_pyramid<T>(s, I, cur)) != TC_OK) return r;
+static ConsistArgs consist_args(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask,
+                                int cur) {
     ConsistArgs ca{};
     ca.It = I; ca.Pt = P;
     ca.H = s->H; ca.W = s->W;
@@ -641,7 +649,7 @@ static tc_status process(tc_stream *s, const float *I, const float *P, float *O,
         ca.fh = ca.fw = 1; ca.scale = 1;
         ca.Ip = ca.Pp = ca.Op = nullptr;
     } else {
-        if ((r = run_estimators<T>(s, cur)) != TC_OK) return r;
+        const int prev = cur ^ 1;
         LevelBufs &B2 = s->lv[1];
         ca.first = 0;
         ca.Ip = s->sI[prev]; ca.Pp = s->sP[prev]; ca.Op = s->sO[prev];
@@ -649,8 +657,140 @@ static tc_status process(tc_stream *s, const float *I, const float *P, float *O,
         ca.Ff = B2.flow + (size_t)B2.h * B2.w * 2;
         ca.fh = B2.h; ca.fw = B2.w; ca.scale = 4;
     }
+    return ca;
+}
+
+// Every launch of one frame, in order.
+template <typename T>
+static tc_status frame_launches(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask,
+                                int cur) {
+    tc_status r;
+    if ((r = run_pyramid<T>(s, I, cur)) != TC_OK) return r;
+    if (s->t > 0 && (r = run_estimators<T>(s, cur)) != TC_OK) return r;
+    const ConsistArgs ca = consist_args(s, I, P, O, wc, mask, cur);
     TC_LAUNCH_CAT(s, TC_PROF_CONSISTENCY, launch_consistency(ca, s->st));
+    return TC_OK;
+}
+
+// Captures the frame's launches for slot parity `cur` into a graph and finds the two nodes
+// whose arguments change from frame to frame.
+template <typename T>
+static tc_status capture_frame(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask,
+                               int cur) {
+    tc_stream::FrameGraph &G = s->fg[cur];
+    // Capture on the library's own stream (capture is not allowed on the legacy default
+    // stream a caller may pass); the launch helpers use s->st, so point it there meanwhile.
+    cudaStream_t caller = s->st;
+    TC_TRY(s, cudaStreamBeginCapture(s->gst, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    s->st = s->gst;
+    const tc_status r = frame_launches<T>(s, I, P, O, wc, mask, cur);
+    s->st = caller;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s->gst, &g);
+    if (r != TC_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+    }
+    if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamEndCapture");
+    size_t n = 0;
+    TC_TRY(s, cudaGraphGetNodes(g, nullptr, &n), "cudaGraphGetNodes");
+    std::vector<cudaGraphNode_t> nodes(n);
+    TC_TRY(s, cudaGraphGetNodes(g, nodes.data(), &n), "cudaGraphGetNodes");
+    for (cudaGraphNode_t node : nodes) {
+        cudaGraphNodeType ty;
+        TC_TRY(s, cudaGraphNodeGetType(node, &ty), "cudaGraphNodeGetType");
+        if (ty != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp{};
+        TC_TRY(s, cudaGraphKernelNodeGetParams(node, &kp), "cudaGraphKernelNodeGetParams");
+        if (kp.func == conv_first_kernel_fn<T>()) { G.n_first = node; G.p_first = kp; }
+        if (kp.func == consistency_kernel_fn()) { G.n_cons = node; G.p_cons = kp; }
+    }
+    if (!G.n_first || !G.n_cons) {
+        cudaGraphDestroy(g);
+        return fail(s, TC_ERR_STATE, "frame graph: per-frame kernel nodes not found");
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+    if (ei != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(s, ei, "cudaGraphInstantiate");
+    }
+    G.g = g;
+    G.exec = ex;
+    G.launches = s->launches;
+    return TC_OK;
+}
+
+template <typename T>
+static tc_status process(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask) {
+    tc_status r;
+    s->launches = 0;
+    if (s->ev_cat.size() > 4096 && (r = prof_flush(s)) != TC_OK) return r;
+    const int cur = (int)(s->t & 1);
+    // The first two frames run eagerly (the first has no flow; the second sets every kernel
+    // attribute); later frames replay the graph of their parity.  Profiling runs eagerly.
+    if (!s->graphs || s->prof || s->t < 2) {
+        if ((r = frame_launches<T>(s, I, P, O, wc, mask, cur)) != TC_OK) return r;
+        s->t += 1;
+        return TC_OK;
+    }
+    tc_stream::FrameGraph &G = s->fg[cur];
+    if (!s->gst) {
+        TC_TRY(s, cudaStreamCreateWithFlags(&s->gst, cudaStreamNonBlocking), "cudaStreamCreate");
+        TC_TRY(s, cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming), "cudaEventCreate");
+        TC_TRY(s, cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming), "cudaEventCreate");
+    }
+    if (!G.exec) {
+        if ((r = capture_frame<T>(s, I, P, O, wc, mask, cur)) != TC_OK) return r;
+    } else {
+        ConvFirstArgs f{I, s->H, s->W, s->Hp, s->Wp, s->pyr_w[0], s->pyr_b[0], s->lv[0].c, s->lv[0].tmpA};
+        ConsistArgs ca = consist_args(s, I, P, O, wc, mask, cur);
+        void *fa[1] = {&f};
+        void *cargs[1] = {&ca};
+        cudaKernelNodeParams pf = G.p_first, pc = G.p_cons;
+        pf.kernelParams = fa;
+        pf.extra = nullptr;
+        pc.kernelParams = cargs;
+        pc.extra = nullptr;
+        TC_TRY(s, cudaGraphExecKernelNodeSetParams(G.exec, G.n_first, &pf), "graph node update");
+        TC_TRY(s, cudaGraphExecKernelNodeSetParams(G.exec, G.n_cons, &pc), "graph node update");
+    }
+    // caller's stream -> library stream -> caller's stream
+    TC_TRY(s, cudaEventRecord(s->ev_in, s->st), "cudaEventRecord");
+    TC_TRY(s, cudaStreamWaitEvent(s->gst, s->ev_in, 0), "cudaStreamWaitEvent");
+    TC_TRY(s, cudaGraphLaunch(G.exec, s->gst), "cudaGraphLaunch");
+    TC_TRY(s, cudaEventRecord(s->ev_out, s->gst), "cudaEventRecord");
+    TC_TRY(s, cudaStreamWaitEvent(s->st, s->ev_out, 0), "cudaStreamWaitEvent");
+    s->launches = G.launches;
     s->t += 1;
+    return TC_OK;
+}
+
+static void release_graphs(tc_stream *s) {
+    for (auto &G : s->fg) {
+        if (G.exec) cudaGraphExecDestroy(G.exec);
+        if (G.g) cudaGraphDestroy(G.g);
+        G = tc_stream::FrameGraph{};
+    }
+}
+
+static void release_graph_stream(tc_stream *s) {
+    if (s->gst) {
+        cudaStreamSynchronize(s->gst);
+        cudaStreamDestroy(s->gst);
+    }
+    if (s->ev_in) cudaEventDestroy(s->ev_in);
+    if (s->ev_out) cudaEventDestroy(s->ev_out);
+    s->gst = nullptr;
+    s->ev_in = s->ev_out = nullptr;
+}
+
+extern "C" tc_status tc_set_graphs(tc_stream *s, int enable) {
+    tc_status r = check_stream(s, "tc_set_graphs");
+    if (r != TC_OK) return r;
+    TC_TRY(s, cudaStreamSynchronize(s->st), "stream synchronize");
+    release_graphs(s);
+    s->graphs = enable != 0;
     return TC_OK;
 }
 
@@ -722,6 +862,8 @@ extern "C" tc_status tc_destroy(tc_stream *s) {
     if (s->st) cudaStreamSynchronize(s->st);
     else cudaDeviceSynchronize();
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+    release_graphs(s);
+    release_graph_stream(s);
     free_all(s);
     delete s;
     return TC_OK;

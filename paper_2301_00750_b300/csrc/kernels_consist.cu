@@ -118,6 +118,8 @@ __global__ void __launch_bounds__(256) consistency_kernel(ConsistArgs a) {
     if (a.mask) a.mask[i] = m ? 1 : 0;
 }
 
+const void *consistency_kernel_fn() { return reinterpret_cast<const void *>(consistency_kernel); }
+
 cudaError_t launch_consistency(const ConsistArgs &a, cudaStream_t st) {
     dim3 grid((a.W + 31) / 32, (a.H + 7) / 8);
     consistency_kernel<<<grid, 256, 0, st>>>(a);

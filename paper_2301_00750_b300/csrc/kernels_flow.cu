@@ -172,6 +172,11 @@ __global__ void __launch_bounds__(256) conv_first_kernel(ConvFirstArgs a) {
 }
 
 template <typename T>
+const void *conv_first_kernel_fn() {
+    return reinterpret_cast<const void *>(conv_first_kernel<T>);
+}
+
+template <typename T>
 cudaError_t launch_conv_first(const ConvFirstArgs &a, cudaStream_t st) {
     const int n = (a.Hp / 2) * (a.Wp / 2);
     conv_first_kernel<T><<<(n + 255) / 256, 256, 0, st>>>(a);
@@ -435,6 +440,7 @@ cudaError_t launch_from_act(const T *in, size_t n, float *out, cudaStream_t st) 
 #define TC_INST(T)                                                                      \
     template cudaError_t launch_conv_simt<T>(const ConvArgs &, cudaStream_t);           \
     template cudaError_t launch_conv_first<T>(const ConvFirstArgs &, cudaStream_t);     \
+    template const void *conv_first_kernel_fn<T>();                                     \
     template cudaError_t launch_head<T>(const HeadArgs &, cudaStream_t);                \
     template cudaError_t launch_corr<T>(const CorrArgs &, cudaStream_t);                \
     template cudaError_t launch_warp<T>(const WarpArgs &, cudaStream_t);                \

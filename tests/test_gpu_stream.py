@@ -165,3 +165,36 @@ def test_stream_1080p_flows_fp32():
     eb, ef = oracle.epe(got[1]["flows"][0], fab), oracle.epe(got[1]["flows"][1], fba)
     print(f"1080p FP32 EPE vs FP64 oracle: Fb {eb:.2e} px, Ff {ef:.2e} px")
     assert eb <= 1e-3 and ef <= 1e-3
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_graph_replay_matches_eager_launches(prec):
+    """From the third frame on a stream replays one captured CUDA graph per slot parity,
+    updating only the nodes that read the caller's buffers and the consistency controls;
+    outputs and flows must be bit-identical to launching kernel by kernel."""
+    import torch
+    path, _ = weights_file((16, 32, 64, 96, 128), 4)
+    frames, styl = _pair(200, 136, seed=4, n=6)
+    runs = []
+    for graphs in (False, True):
+        s = tc.Stream(200, 136, prec, weights_path=path)
+        s.set_graphs(graphs)
+        outs = []
+        for t, (I, P) in enumerate(zip(frames, styl)):
+            s.set_consistency(k1=(0.2, 0.5, 0.9)[t % 3])
+            O = torch.empty((3, 136, 200), device="cuda")
+            wc = torch.empty((136, 200), device="cuda")
+            m = torch.empty((136, 200), device="cuda", dtype=torch.uint8)
+            s.process_frame(to_dev(I), to_dev(P), O, wc, m)
+            Fb = torch.empty((2, 136, 200), device="cuda")
+            if t > 0:
+                s.get_flows(Fb, None)
+            s.synchronize()
+            outs.append((to_np(O), to_np(wc), to_np(m), to_np(Fb) if t > 0 else None))
+        s.destroy()
+        runs.append(outs)
+    for t in range(len(frames)):
+        for k in range(3):
+            assert np.array_equal(runs[0][t][k], runs[1][t][k]), (t, k)
+        if t > 0:
+            assert np.array_equal(runs[0][t][3], runs[1][t][3])
