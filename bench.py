@@ -401,6 +401,85 @@ def run_reference(args):
     }), flush=True)
 
 
+# ----------------------------------------------------------------------------- serving
+
+SERVE_MIX = [(640, 360, 4), (1280, 720, 4), (1920, 1080, 6), (2560, 1440, 2)]
+
+
+def run_serve(args):
+    """16 concurrent streams at mixed resolutions through tc_server_*: Poisson frame arrivals
+    at 30 fps per stream, host buffers in and out, HBM-budget admission, continuous batching;
+    reports aggregate frames/s and p50/p99 submit-to-done latency."""
+    import torch
+    import paper_2301_00750_b300 as tc
+
+    tmp = tempfile.mkdtemp(prefix="tcserve")
+    path = os.path.join(tmp, "net.tcw")
+    write_weights(path)
+    g = np.random.Generator(np.random.PCG64(7))
+    srv = tc.Server(path, precision=args.precision, workers=args.workers,
+                    hbm_budget_bytes=int(args.budget_gb * (1 << 30)) if args.budget_gb else 0)
+    streams = []
+    frames_by_size = {}
+    for W, H, count in SERVE_MIX:
+        if (W, H) not in frames_by_size:
+            fr, st = make_frames(seed=W, n=3, width=W, height=H)
+            frames_by_size[(W, H)] = ([torch.from_numpy(f).pin_memory() for f in fr],
+                                      [torch.from_numpy(p).pin_memory() for p in st])
+        for _ in range(count):
+            sid = srv.open(W, H)
+            srv.set_consistency(sid, k1=0.5)
+            outs = [torch.empty((3, H, W), dtype=torch.float32).pin_memory() for _ in range(args.ring)]
+            streams.append(dict(id=sid, W=W, H=H, outs=outs, free=list(range(args.ring)), next=0.0, n=0))
+    rate = 30.0
+    duration = args.seconds
+    latencies, done_n, dropped = [], 0, 0
+    tag_slot = {}
+    t0 = time.perf_counter()
+    for s_ in streams:
+        s_["next"] = g.exponential(1.0 / rate)
+    warm = 1.0  # seconds excluded from the statistics
+    while True:
+        now = time.perf_counter() - t0
+        if now > duration + warm:
+            break
+        for s_ in streams:
+            while s_["next"] <= now:
+                if not s_["free"]:
+                    dropped += 1  # client found no free output slot: frame skipped
+                else:
+                    slot = s_["free"].pop()
+                    fr, st = frames_by_size[(s_["W"], s_["H"])]
+                    k = s_["n"] % len(fr)
+                    tag = (s_["id"] << 32) | s_["n"]
+                    tag_slot[tag] = (s_, slot, s_["next"])
+                    srv.submit(s_["id"], fr[k], st[k], s_["outs"][slot], tag=tag)
+                    s_["n"] += 1
+                s_["next"] += g.exponential(1.0 / rate)
+        for c in srv.poll(timeout_ms=1):
+            s_, slot, t_sub = tag_slot.pop(c["tag"])
+            s_["free"].append(slot)
+            if c["status"] == 0 and t_sub >= warm:
+                latencies.append(c["total_us"] / 1e3)
+                done_n += 1
+    end = time.perf_counter() - t0
+    for c in srv.poll(max_n=4096, timeout_ms=2000):
+        pass
+    srv.destroy()
+    lat = sorted(latencies)
+    px = sum(W * H * c for W, H, c in SERVE_MIX)
+    print(json.dumps({
+        "metric": "serving: aggregate frames/s and p50/p99 frame latency, 16 mixed-resolution streams, Poisson 30 fps",
+        "value": round(done_n / (end - warm), 2), "unit": "frames/s", "higher_is_better": True,
+        "p50_ms": round(lat[len(lat) // 2], 3) if lat else None,
+        "p99_ms": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3) if lat else None,
+        "offered_frames_per_s": rate * len(streams), "dropped_no_slot": dropped,
+        "dtype": args.precision, "data": "synthetic", "workers": args.workers,
+        "config": {"workload": "4x640x360, 4x1280x720, 6x1920x1080, 2x2560x1440; host buffers in/out per frame",
+                   "megapixels_per_round": round(px / 1e6, 2), "seconds": duration},
+    }), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -410,10 +489,17 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="run the multi-stream serving benchmark instead")
+    ap.add_argument("--workers", type=int, default=8)
+    ap.add_argument("--ring", type=int, default=4, help="output buffers per stream (frames in flight)")
+    ap.add_argument("--seconds", type=float, default=10.0)
+    ap.add_argument("--budget-gb", type=float, default=0.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.serve:
+        run_serve(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -236,6 +236,73 @@ TC_API tc_status tc_op_consistency(const float *It, const float *Pt, const float
                             int fh, int fw, int scale, const tc_consistency *p, float *O,
                             float *wc_opt, uint8_t *mask_opt, void *cuda_stream);
 
+/* Device bytes held by s (its buffers, packed weights and host-entry staging). */
+TC_API size_t tc_stream_device_bytes(const tc_stream *s);
+
+/* ------------------------------------------------------------------------------------
+ * Multi-stream server.  Many concurrent streams (each with its own state on the device, as
+ * Sec. 3.1 requires: I_{t-1}, P_{t-1}, O_{t-1} and the cached pyramid) of mixed
+ * resolutions share one GPU.  Admission reserves a stream's device memory against an HBM
+ * budget; frames are submitted with host buffers and run, in order per stream, by a pool of
+ * worker threads as soon as a worker is free and the stream's previous frame has finished
+ * (continuous batching: work of different streams overlaps on the device, each frame on its
+ * stream's own CUDA stream as one CUDA-graph replay).
+ * ---------------------------------------------------------------------------------- */
+typedef struct tc_server tc_server;
+
+typedef struct {
+    tc_precision precision;          /* TC_FP32 or TC_BF16 for every stream */
+    const char *weights_path;        /* TCW1 file, or NULL and weights_blob (copied) */
+    const void *weights_blob;
+    size_t weights_bytes;
+    size_t hbm_budget_bytes;         /* device bytes the streams may hold together; 0 = unlimited */
+    int workers;                     /* frames in flight at once, 1..64 */
+    int max_streams;                 /* stream slots, >= 1 */
+} tc_server_desc;
+
+typedef struct {
+    int stream_id;
+    long long frame;                 /* index of the frame within its stream (0-based) */
+    unsigned long long tag;          /* as passed to tc_server_submit */
+    tc_status status;                /* TC_OK, TC_ERR_STATE if cancelled, or the frame's error */
+    double queued_us, gpu_us, total_us;  /* submit -> start, start -> done, submit -> done */
+} tc_completion;
+
+/* Creates a server and its worker threads on the current device. */
+TC_API tc_status tc_server_create(const tc_server_desc *desc, tc_server **out);
+
+/* Device bytes a stream of width x height would hold (the admission charge). */
+TC_API size_t tc_server_stream_bytes(const tc_server *srv, int width, int height);
+
+/* Device bytes currently reserved by admitted streams. */
+TC_API size_t tc_server_bytes_in_use(const tc_server *srv);
+
+/* Admits a stream: TC_OK and *stream_id > 0, or TC_ERR_BUSY when every slot is taken or the
+ * stream would exceed the HBM budget (nothing is allocated then; retry after a close). */
+TC_API tc_status tc_server_open(tc_server *srv, int width, int height, int *stream_id);
+
+/* Consistency controls of one stream, applied from its next frame to run. */
+TC_API tc_status tc_server_set_consistency(tc_server *srv, int stream_id, const tc_consistency *p);
+
+/* Queues the next frame of a stream.  I_host, P_host: host (3, H, W) float32; O_host: host
+ * output, written before the frame's completion is reported.  The caller keeps all three
+ * alive and unchanged until then (pinned memory makes the copies faster). */
+TC_API tc_status tc_server_submit(tc_server *srv, int stream_id, const float *I_host, const float *P_host,
+                                 float *O_host, unsigned long long tag);
+
+/* Copies up to max finished frames into out, waiting up to timeout_ms for the first one;
+ * returns how many. */
+TC_API int tc_server_poll(tc_server *srv, tc_completion *out, int max, int timeout_ms);
+
+/* Drops the stream's queued frames (each reported with status TC_ERR_STATE). */
+TC_API tc_status tc_server_cancel(tc_server *srv, int stream_id);
+
+/* Waits for the stream's queued frames, then frees its slot and device memory. */
+TC_API tc_status tc_server_close(tc_server *srv, int stream_id);
+
+/* Cancels every queued frame, stops the workers and frees everything. */
+TC_API tc_status tc_server_destroy(tc_server *srv);
+
 /* ------------------------------------------------------------------------------------
  * Allocation-free variant.  The paper has no counterpart: this entry point exists for hosts
  * that cannot let the library allocate device memory -- an application whose memory pool

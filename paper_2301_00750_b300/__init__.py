@@ -299,3 +299,117 @@ def op_consistency(It, Pt, Ip, Pp, Op, Fb, Ff, scale=1, O=None, wc=None, mask=No
                                   _ptr(Fb, f32), _ptr(Ff, f32), h, w, fh, fw, scale, ctypes.byref(c), O.data_ptr(),
                                   wc.data_ptr(), mask.data_ptr(), _stream_handle(cuda_stream)))
     return O, wc, mask
+
+
+# ----------------------------------------------------------------------------- server
+
+class TcServerDesc(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("weights_path", ctypes.c_char_p), ("weights_blob", ctypes.c_void_p),
+                ("weights_bytes", ctypes.c_size_t), ("hbm_budget_bytes", ctypes.c_size_t), ("workers", ctypes.c_int),
+                ("max_streams", ctypes.c_int)]
+
+
+class TcCompletion(ctypes.Structure):
+    _fields_ = [("stream_id", ctypes.c_int), ("frame", ctypes.c_longlong), ("tag", ctypes.c_ulonglong),
+                ("status", ctypes.c_int), ("queued_us", ctypes.c_double), ("gpu_us", ctypes.c_double),
+                ("total_us", ctypes.c_double)]
+
+
+_lib.tc_server_create.argtypes = [ctypes.POINTER(TcServerDesc), ctypes.POINTER(_vp)]
+_lib.tc_server_stream_bytes.argtypes = [_vp, _i, _i]
+_lib.tc_server_stream_bytes.restype = ctypes.c_size_t
+_lib.tc_server_bytes_in_use.argtypes = [_vp]
+_lib.tc_server_bytes_in_use.restype = ctypes.c_size_t
+_lib.tc_server_open.argtypes = [_vp, _i, _i, ctypes.POINTER(_i)]
+_lib.tc_server_set_consistency.argtypes = [_vp, _i, ctypes.POINTER(TcConsistency)]
+_lib.tc_server_submit.argtypes = [_vp, _i, _vp, _vp, _vp, ctypes.c_ulonglong]
+_lib.tc_server_poll.argtypes = [_vp, ctypes.POINTER(TcCompletion), _i, _i]
+_lib.tc_server_poll.restype = ctypes.c_int
+_lib.tc_server_cancel.argtypes = [_vp, _i]
+_lib.tc_server_close.argtypes = [_vp, _i]
+_lib.tc_server_destroy.argtypes = [_vp]
+_lib.tc_stream_device_bytes.argtypes = [_vp]
+_lib.tc_stream_device_bytes.restype = ctypes.c_size_t
+for _n in ["tc_server_create", "tc_server_open", "tc_server_set_consistency", "tc_server_submit", "tc_server_cancel",
+           "tc_server_close", "tc_server_destroy"]:
+    getattr(_lib, _n).restype = ctypes.c_int
+EXPORTED += ["tc_server_create", "tc_server_stream_bytes", "tc_server_bytes_in_use", "tc_server_open",
+             "tc_server_set_consistency", "tc_server_submit", "tc_server_poll", "tc_server_cancel",
+             "tc_server_close", "tc_server_destroy", "tc_stream_device_bytes"]
+
+
+def _host_ptr(a):
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if a.dtype != np.float32 or not a.flags.c_contiguous:
+        raise TypeError("host buffers must be contiguous float32")
+    return a.ctypes.data
+
+
+class Server:
+    """tc_server_*: many streams of mixed resolutions on one GPU with HBM-budget admission
+    and continuous batching.  Host buffers passed to submit() must stay alive until their
+    completion is polled."""
+
+    def __init__(self, weights_path, precision="bf16", hbm_budget_bytes=0, workers=4, max_streams=64):
+        d = TcServerDesc()
+        d.precision = PRECISION[precision]
+        d.weights_path = os.fsencode(weights_path)
+        d.hbm_budget_bytes = int(hbm_budget_bytes)
+        d.workers = int(workers)
+        d.max_streams = int(max_streams)
+        h = _vp()
+        _check(_lib.tc_server_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def stream_bytes(self, width, height) -> int:
+        return _lib.tc_server_stream_bytes(self._h, width, height)
+
+    @property
+    def bytes_in_use(self) -> int:
+        return _lib.tc_server_bytes_in_use(self._h)
+
+    def open(self, width, height) -> int:
+        sid = _i()
+        _check(_lib.tc_server_open(self._h, width, height, ctypes.byref(sid)))
+        return sid.value
+
+    def set_consistency(self, stream_id, **kw):
+        c = _consistency_struct(**kw)
+        _check(_lib.tc_server_set_consistency(self._h, stream_id, ctypes.byref(c)))
+
+    def submit(self, stream_id, I, P, O, tag=0):
+        self._keep[(stream_id, tag)] = (I, P, O)
+        _check(_lib.tc_server_submit(self._h, stream_id, _host_ptr(I), _host_ptr(P), _host_ptr(O), tag))
+
+    def poll(self, max_n=256, timeout_ms=100):
+        buf = (TcCompletion * max_n)()
+        n = _lib.tc_server_poll(self._h, buf, max_n, timeout_ms)
+        out = []
+        for c in buf[:n]:
+            self._keep.pop((c.stream_id, c.tag), None)
+            out.append(dict(stream_id=c.stream_id, frame=c.frame, tag=c.tag, status=c.status, queued_us=c.queued_us,
+                            gpu_us=c.gpu_us, total_us=c.total_us))
+        return out
+
+    def cancel(self, stream_id):
+        _check(_lib.tc_server_cancel(self._h, stream_id))
+
+    def close(self, stream_id):
+        _check(_lib.tc_server_close(self._h, stream_id))
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            _check(_lib.tc_server_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def stream_device_bytes(stream: "Stream") -> int:
+    return _lib.tc_stream_device_bytes(stream._h)

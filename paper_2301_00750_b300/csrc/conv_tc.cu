@@ -389,6 +389,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 void TcConvPlan::release() {
     if (wpk) cudaFree(wpk);
     wpk = nullptr;
+    wpk_bytes = 0;
     enabled = false;
 }
 
@@ -463,6 +464,7 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
     plan.in_base = a.in;
     plan.img_bytes = (size_t)a.h * a.w * a.in_cs * esz;
     plan.wpk = wdev;
+    plan.wpk_bytes = pk.size() * 2;
     plan.err = err;
     plan.enabled = true;
     return true;

@@ -22,6 +22,7 @@ struct TcConvPlan {
     const void *in_base = nullptr;  // start of the buffer the A descriptor covers
     size_t img_bytes = 0;           // bytes between consecutive images of that buffer
     __nv_bfloat16 *wpk = nullptr;   // packed weights (owned by the plan)
+    size_t wpk_bytes = 0;
     int *err = nullptr;             // device error word shared by the stream (not owned)
     void release();
 };

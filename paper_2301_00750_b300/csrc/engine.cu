@@ -14,26 +14,14 @@
 #include "../../include/tc_stream.h"
 #include "common.cuh"
 #include "conv_tc.cuh"
+#include "engine_internal.h"
 #include "corr_tc.cuh"
 
 namespace tc {
 
 // ------------------------------------------------------------------------------- weights
 
-struct HostLayer {
-    int cout, cin, stride, leaky;
-    std::vector<float> w;  // OIHW
-    std::vector<float> b;
-};
-
-struct HostNet {
-    int levels = 0, radius = 0;
-    std::vector<int> chans;
-    int dec[4] = {0, 0, 0, 0};
-    std::vector<HostLayer> layers;
-};
-
-static bool parse_weights(const uint8_t *p, size_t n, HostNet &net, std::string &err) {
+bool parse_weights(const uint8_t *p, size_t n, HostNet &net, std::string &err) {
     size_t off = 0;
     auto rd = [&](void *dst, size_t k) -> bool {
         if (off + k > n) return false;
@@ -122,6 +110,40 @@ static std::vector<int> iota_perm(int n, int pad_to) {
 
 static inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
+size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precision prec) {
+    const int L = net.levels, D = (2 * net.radius + 1) * (2 * net.radius + 1), m = 1 << L;
+    const size_t es = prec == TC_FP32 ? 4 : 2;
+    const size_t Hp = (size_t)round_up(height, m), Wp = (size_t)round_up(width, m);
+    const bool bf = prec != TC_FP32;
+    auto al = [](size_t b) { return (b + 511) & ~(size_t)511; };  // allocation granularity
+    auto tcw = [&](int cin, int cout) { return bf ? al((size_t)9 * cout * round_up(cin, 64) * 2) : 0; };
+    size_t total = al(sizeof(int));
+    int prev = 3;
+    for (int l = 1; l <= L; ++l) {
+        const size_t h = Hp >> l, w = Wp >> l, px = h * w;
+        const int c = net.chans[l - 1];
+        total += al(2 * px * c * es) + 2 * al(px * c * es);
+        total += al((size_t)9 * prev * c * 4) + al((size_t)c * 4) + 2 * (al((size_t)9 * c * c * 4) + al((size_t)c * 4));
+        if (l > 1) total += tcw(prev, c);
+        total += 2 * tcw(c, c);
+        prev = c;
+        if (l < 2) continue;
+        const int x0p = round_up(c + D + 2, 8);
+        const int ctot = x0p + net.dec[0] + net.dec[1] + net.dec[2] + net.dec[3];
+        total += al(2 * px * ctot * es) + al(2 * px * c * es) + 2 * al(2 * px * 2 * 4);
+        const int cin[5] = {x0p, net.dec[0], net.dec[1], net.dec[1] + net.dec[2], net.dec[2] + net.dec[3]};
+        const int cout[5] = {net.dec[0], net.dec[1], net.dec[2], net.dec[3], 2};
+        for (int j = 0; j < 5; ++j) {
+            total += al((size_t)9 * cin[j] * cout[j] * 4) + al((size_t)cout[j] * 4);
+            total += j < 4 ? tcw(cin[j], cout[j]) : tcw(cin[j], 16);
+        }
+    }
+    const size_t img = al((size_t)3 * height * width * 4), plane = (size_t)height * width;
+    total += 6 * img;                                        // state I, P, O x 2 slots
+    total += 3 * img + al(plane * 4) + al(plane);            // host-entry staging
+    return total;
+}
+
 }  // namespace tc
 
 using namespace tc;
@@ -180,6 +202,7 @@ struct tc_stream {
     int *dev_err = nullptr;     // device error word of the tensor-core kernels (0 = ok)
     int tc_layers = 0;          // convolution layers planned on the tensor cores
     int tc_corr_levels = 0;     // pyramid levels whose correlation runs on the tensor cores
+    size_t dev_bytes = 0;       // device bytes allocated by the stream itself
     int launches = 0;
     std::string err;
     // per-stage timing (tc_set_profiling): events around every launch, folded lazily
@@ -218,7 +241,6 @@ static tc_status fail(tc_stream *s, tc_status code, const std::string &msg) {
     return code;
 }
 
-// Records the error of a stream-less call (read back with tc_last_error(NULL)).
 tc_status tc_record_error(tc_status code, const std::string &msg) { return fail(nullptr, code, msg); }
 
 static tc_status cuda_fail(tc_stream *s, cudaError_t e, const char *what) {
@@ -241,6 +263,7 @@ static tc_status dalloc(tc_stream *s, void **p, size_t bytes) {
         return fail(s, TC_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
     }
     s->allocs.push_back(*p);
+    s->dev_bytes += bytes;
     return TC_OK;
 }
 
@@ -904,6 +927,18 @@ extern "C" int tc_last_launch_count(const tc_stream *s) { return s ? s->launches
 extern "C" int tc_tensor_core_layers(const tc_stream *s) { return s ? s->tc_layers : 0; }
 
 extern "C" int tc_tensor_core_correlation_levels(const tc_stream *s) { return s ? s->tc_corr_levels : 0; }
+
+extern "C" size_t tc_stream_device_bytes(const tc_stream *s) {
+    if (!s) return 0;
+    size_t b = s->dev_bytes;
+    for (const auto &B : s->lv) {
+        for (const auto &pl : B.tcplan) b += pl.wpk_bytes;
+        b += B.headplan.wpk_bytes;
+    }
+    for (const auto &lvl : s->pyr_plan)
+        for (const auto &pl : lvl) b += pl.wpk_bytes;
+    return b;
+}
 
 // ------------------------------------------------------------------------------- stage ops
 

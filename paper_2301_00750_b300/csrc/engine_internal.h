@@ -1,0 +1,36 @@
+// Host-side pieces of the engine shared with the server (csrc/server.cu).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tc_stream.h"
+
+namespace tc {
+
+struct HostLayer {
+    int cout, cin, stride, leaky;
+    std::vector<float> w;  // OIHW
+    std::vector<float> b;
+};
+
+struct HostNet {
+    int levels = 0, radius = 0;
+    std::vector<int> chans;
+    int dec[4] = {0, 0, 0, 0};
+    std::vector<HostLayer> layers;
+};
+
+// Parses and shape-checks a TCW1 weight blob (layout in include/tc_stream.h).
+bool parse_weights(const uint8_t *p, size_t n, HostNet &net, std::string &err);
+
+// Device memory a stream of width x height holds (feature pyramids, estimator buffers,
+// flows, state, weights, host-entry staging), from the same sizes the stream allocates.
+size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precision prec);
+
+}  // namespace tc
+
+// Records the error of a stream-less call (read back with tc_last_error(NULL)).
+tc_status tc_record_error(tc_status code, const std::string &msg);

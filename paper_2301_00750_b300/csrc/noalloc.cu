@@ -16,7 +16,7 @@
 #include "../../include/tc_stream.h"
 #include "common.cuh"
 
-tc_status tc_record_error(tc_status code, const std::string &msg);  // engine.cu
+#include "engine_internal.h"
 
 // Staging area shared by every call on a device.  In host code this name is only a
 // host-side stand-in for the symbol, never a device address: the device address comes

@@ -97,3 +97,24 @@ def test_null_and_range_checks(lib):
     st = so.tc_op_consistency(p, p, p, p, p, p, p, 8, 8, 8, 8, 1, ctypes.byref(c), p, None, None, None)
     assert st == lib.TC_ERR_INVALID_ARG
     assert b"k1" in so.tc_last_error(None)
+
+
+def test_server_admission_is_decided_before_any_allocation(lib, tmp_path):
+    """HBM-budget admission happens on the host: a budget smaller than one stream's charge
+    answers TC_ERR_BUSY without touching the device (this runs on a machine without a GPU)."""
+    w = _weights_blob(tmp_path)
+    srv = lib.Server(str(w), precision="bf16", hbm_budget_bytes=1 << 20, workers=2, max_streams=4)
+    small, big = srv.stream_bytes(64, 64), srv.stream_bytes(1920, 1080)
+    assert 0 < small < big and big > (1 << 20)
+    assert srv.stream_bytes(128, 128) > small
+    with pytest.raises(lib.TcError) as e:
+        srv.open(1920, 1080)
+    assert e.value.status == lib.TC_ERR_BUSY and "budget" in str(e.value)
+    assert srv.bytes_in_use == 0
+    with pytest.raises(lib.TcError) as e:
+        srv.open(4, 4)
+    assert e.value.status == lib.TC_ERR_INVALID_ARG
+    srv.destroy()
+    with pytest.raises(lib.TcError) as e:
+        lib.Server(str(w), workers=0)
+    assert e.value.status == lib.TC_ERR_INVALID_ARG

@@ -1,0 +1,120 @@
+"""The multi-stream server (tc_server_*): results of a stream are the same alone and in a
+mix with other streams running concurrently, HBM-budget admission, and cancellation."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_common import weights_file
+
+pytestmark = pytest.mark.gpu
+tc = pytest.importorskip("paper_2301_00750_b300")
+
+NET = ((16, 32, 64, 96, 128), 4)
+
+
+def _frames(W, H, seed, n):
+    seq = synth.Sequence(width=W, height=H, seed=seed, side_range=(max(8, W // 12), max(10, W // 6)),
+                         max_vel=max(2.0, W / 160))
+    I = [seq.frame(t) for t in range(n)]
+    return I, [seq.stylized(t, f) for t, f in enumerate(I)]
+
+
+def _drain(srv, n, timeout_s=60):
+    import time
+    got, t0 = [], time.time()
+    while len(got) < n and time.time() - t0 < timeout_s:
+        got += srv.poll(timeout_ms=200)
+    return got
+
+
+STREAMS = [(320, 200, 11), (256, 160, 12), (320, 200, 13), (200, 136, 14)]
+N_FRAMES = 4
+
+
+def test_each_stream_alone_equals_in_the_mix():
+    path, _ = weights_file(*NET)
+    data = {k: _frames(W, H, seed, N_FRAMES) for k, (W, H, seed) in enumerate(STREAMS)}
+    # alone: one worker, one stream at a time
+    alone = {}
+    srv = tc.Server(path, precision="bf16", workers=1)
+    for k, (W, H, _) in enumerate(STREAMS):
+        sid = srv.open(W, H)
+        outs = [np.zeros((3, H, W), np.float32) for _ in range(N_FRAMES)]
+        for t in range(N_FRAMES):
+            srv.submit(sid, data[k][0][t], data[k][1][t], outs[t], tag=t)
+        done = _drain(srv, N_FRAMES)
+        assert len(done) == N_FRAMES and all(c["status"] == 0 for c in done)
+        assert [c["frame"] for c in done] == list(range(N_FRAMES))
+        alone[k] = outs
+        srv.close(sid)
+    srv.destroy()
+    # mix: four workers, all streams open, frames submitted interleaved
+    srv = tc.Server(path, precision="bf16", workers=4)
+    sids = {k: srv.open(W, H) for k, (W, H, _) in enumerate(STREAMS)}
+    mixed = {k: [np.zeros((3, H, W), np.float32) for _ in range(N_FRAMES)] for k, (W, H, _) in enumerate(STREAMS)}
+    for t in range(N_FRAMES):
+        for k in range(len(STREAMS)):
+            srv.submit(sids[k], data[k][0][t], data[k][1][t], mixed[k][t], tag=100 * k + t)
+    done = _drain(srv, N_FRAMES * len(STREAMS))
+    assert len(done) == N_FRAMES * len(STREAMS) and all(c["status"] == 0 for c in done)
+    for k in range(len(STREAMS)):
+        frames = [c["frame"] for c in done if c["stream_id"] == sids[k]]
+        assert frames == sorted(frames)            # per-stream order kept
+    srv.destroy()
+    for k in range(len(STREAMS)):
+        for t in range(N_FRAMES):
+            # same kernels, same inputs: bit-identical whatever else runs on the GPU
+            assert np.array_equal(alone[k][t], mixed[k][t]), (k, t)
+
+
+def test_budget_admission_and_release():
+    path, _ = weights_file(*NET)
+    srv = tc.Server(path, precision="bf16", workers=2)
+    per = srv.stream_bytes(320, 200)
+    srv.destroy()
+    srv = tc.Server(path, precision="bf16", workers=2, hbm_budget_bytes=2 * per + per // 2)
+    a = srv.open(320, 200)
+    b = srv.open(320, 200)
+    with pytest.raises(tc.TcError) as e:
+        srv.open(320, 200)
+    assert e.value.status == tc.TC_ERR_BUSY
+    assert srv.bytes_in_use == 2 * per
+    srv.close(a)
+    c = srv.open(320, 200)                          # the freed memory admits a new stream
+    assert c not in (a, b) and srv.bytes_in_use == 2 * per
+    srv.destroy()
+
+
+def test_admission_charge_covers_what_a_stream_allocates():
+    path, _ = weights_file(*NET)
+    for prec in ("bf16", "fp32"):
+        srv = tc.Server(path, precision=prec, workers=1)
+        want = srv.stream_bytes(320, 200)
+        srv.destroy()
+        s = tc.Stream(320, 200, prec, weights_path=path)
+        I = np.zeros((3, 200, 320), np.float32)
+        s.process_frame_host(I, I, np.zeros_like(I))   # allocates the host-entry staging too
+        got = tc.stream_device_bytes(s)
+        s.destroy()
+        assert got <= want <= 1.05 * got + (1 << 20), (prec, got, want)
+
+
+def test_cancel_drops_queued_frames_in_order():
+    path, _ = weights_file(*NET)
+    srv = tc.Server(path, precision="bf16", workers=1)
+    sid = srv.open(256, 160)
+    I, P = _frames(256, 160, 21, 2)
+    outs = [np.zeros((3, 160, 256), np.float32) for _ in range(12)]
+    for t in range(12):
+        srv.submit(sid, I[t % 2], P[t % 2], outs[t], tag=t)
+    srv.cancel(sid)
+    done = _drain(srv, 12)
+    assert len(done) == 12
+    ok = [c for c in done if c["status"] == 0]
+    dropped = [c for c in done if c["status"] == tc.TC_ERR_STATE]
+    assert len(ok) + len(dropped) == 12 and len(dropped) >= 1
+    # what ran ran in order and first; the rest was dropped
+    assert sorted(c["frame"] for c in ok) == list(range(len(ok)))
+    assert sorted(c["frame"] for c in dropped) == list(range(len(ok), 12))
+    srv.close(sid)
+    srv.destroy()
