@@ -6,7 +6,10 @@ on the synthetic 1920x1080 sequence (textured canvas under affine camera motion 
 occluding squares), 5-level network 16/32/64/96/128, correlation radius 4, He-init
 weights, consistency weight k1 swept over {0, .25, .5, .75, 1} frame by frame.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp8|fp32] [--impl ours|reference]
+
+E4M3 streams take their activation scales from a BF16 pass over frames 0-2 of the sequence
+(amax / 448 per activation segment), outside the timed region.
 
 Multi-GPU (torchrun, one rank per GPU): every rank runs its own independent stream (the
 path shards by stream, no collective on the data path); value = frames of all ranks / the
@@ -180,10 +183,23 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
-def time_stream(tc, torch, path, dev_frames, dev_styl, precision, steps, warmup, profile=False):
+def fp8_scales(tc, path, dev_frames, dev_styl):
+    """E4M3 activation scales from a BF16 pass over frames 0-2 (static calibration)."""
+    H, W = dev_frames[0].shape[1:]
+    return tc.calibrate_fp8(W, H, list(zip(dev_frames[:3], dev_styl[:3])), weights_path=path)
+
+
+def open_stream(tc, path, W, H, precision, scales):
+    s = tc.Stream(W, H, precision, weights_path=path)
+    if precision == "fp8":
+        s.set_fp8_scales(scales)
+    return s
+
+
+def time_stream(tc, torch, path, dev_frames, dev_styl, precision, steps, warmup, profile=False, scales=None):
     """Runs warmup + steps frames through one stream; returns timings (device events)."""
     H, W = dev_frames[0].shape[1:]
-    s = tc.Stream(W, H, precision, weights_path=path)
+    s = open_stream(tc, path, W, H, precision, scales)
     O = torch.empty((3, H, W), device="cuda")
     wc = torch.empty((H, W), device="cuda")
     mask = torch.empty((H, W), device="cuda", dtype=torch.uint8)
@@ -218,10 +234,10 @@ def time_stream(tc, torch, path, dev_frames, dev_styl, precision, steps, warmup,
                 tc_corr=tc_corr)
 
 
-def e2e_host(tc, torch, path, frames, styl, precision, steps, warmup):
+def e2e_host(tc, torch, path, frames, styl, precision, steps, warmup, scales=None):
     """End-to-end through tc_process_frame_host: pinned host I_t, P_t in, O_t out per frame."""
     H, W = frames[0].shape[1:]
-    s = tc.Stream(W, H, precision, weights_path=path)
+    s = open_stream(tc, path, W, H, precision, scales)
     hI = [torch.from_numpy(f).pin_memory() for f in frames]
     hP = [torch.from_numpy(p).pin_memory() for p in styl]
     hO = torch.empty((3, H, W), dtype=torch.float32).pin_memory()
@@ -275,22 +291,27 @@ def run_ours(args):
     dev_frames = [torch.from_numpy(f).cuda() for f in frames]
     dev_styl = [torch.from_numpy(p).cuda() for p in styl]
     torch.cuda.synchronize()
+    scales = fp8_scales(tc, path, dev_frames, dev_styl) if args.precision == "fp8" or not args.skip_fp8 else None
 
     clocks = ClockSampler(local)
     barrier(world)
     clocks.start()
     time.sleep(0.3)
-    main = time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, args.steps, args.warmup)
+    main = time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, args.steps, args.warmup,
+                       scales=scales)
     clk = clocks.stop()
     barrier(world)
     total_s = max_over_ranks(main["total_ms"] / 1e3, world)
 
     # Per-stage device times over the same number of steps (events around every launch).
-    prof = time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, args.steps, 2, profile=True)
-    fp32 = None
+    prof = time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, args.steps, 2, profile=True,
+                       scales=scales)
+    fp32 = fp8 = None
     if args.precision != "fp32" and not args.skip_fp32:
         fp32 = time_stream(tc, torch, path, dev_frames, dev_styl, "fp32", max(3, args.steps // 4), 2)
-    e2e = e2e_host(tc, torch, path, frames, styl, args.precision, max(3, min(args.steps, 50)), 2)
+    if args.precision != "fp8" and not args.skip_fp8:
+        fp8 = time_stream(tc, torch, path, dev_frames, dev_styl, "fp8", args.steps, 3, scales=scales)
+    e2e = e2e_host(tc, torch, path, frames, styl, args.precision, max(3, min(args.steps, 50)), 2, scales=scales)
     e2e_v = e2e["value"]
     if world > 1:
         e2e_v = world / max_over_ranks(1.0 / e2e["value"], world)
@@ -312,18 +333,30 @@ def run_ours(args):
     peaks = measured_peaks()
     if dom in ("estimator_conv", "pyramid_conv", "head", "correlation"):
         achieved = flops[dom] * steps / (p[dom][0] / 1e3) / 1e12
-        if tensor_path:
+        if tensor_path and args.precision == "fp8":
+            # no measured e4m3 peak: the bf16 one x the nominal dense fp8 : bf16 ratio (4.5 : 2.25)
+            peak, unit, bound = 2 * peaks.get("bf16_tflops_sustained"), "TFLOP/s", "tensor"
+        elif tensor_path:
             peak, unit, bound = peaks.get("bf16_tflops_sustained"), "TFLOP/s", "tensor"
         else:
             peak, unit, bound = FP32_SIMT_PEAK_TFLOPS, "TFLOP/s", "alu"
     else:
         achieved = CONSISTENCY_BYTES_PER_PX * WIDTH * HEIGHT * steps / (p[dom][0] / 1e3) / 1e9
         peak, unit, bound = peaks.get("hbm_gbs"), "GB/s", "hbm"
+    if bound == "alu":
+        peak_source = "derived: 148 SM x 128 FP32 lanes x 2 x 2032 MHz"
+    elif bound == "tensor" and args.precision == "fp8":
+        peak_source = "of measured bf16 sustained x 2 (nominal fp8:bf16), MEASURED_PEAKS.json"
+    elif bound == "tensor":
+        peak_source = "of measured bf16 sustained (MEASURED_PEAKS.json)"
+    else:
+        peak_source = "of measured HBM copy (MEASURED_PEAKS.json)"
     per = sorted(main["per_frame_ms"])
     line = {
         "metric": METRIC, "value": round(world * steps / total_s, 3), "unit": UNIT, "n_gpus": world,
         "steps": steps, "warmup": args.warmup, "ms_per_step": round(total_s * 1e3 / steps, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp8": "e4m3", "fp32": "f32"}.get(args.precision, args.precision),
         "data": "synthetic (seeded 1080p sequence, He-init weights)",
         "config": {"workload": "1920x1080 RGB stream, lite flow net 5 levels 16/32/64/96/128, radius 4, "
                                "decoder 128/96/64/32/2, both flow directions + fused consistency, k1 swept "
@@ -333,9 +366,7 @@ def run_ours(args):
         "stage_ms_per_frame": {k: round(v[0] / steps, 4) for k, v in p.items() if v[1]},
         "roofline": {"kernel": dom, "bound": bound, "achieved": round(achieved, 2), "peak": peak, "unit": unit,
                      "frac": round(achieved / peak, 4) if peak else None, "traffic": None,
-                     "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2032 MHz" if bound == "alu"
-                     else ("of measured bf16 sustained (MEASURED_PEAKS.json)" if bound == "tensor"
-                           else "of measured HBM copy (MEASURED_PEAKS.json)")},
+                     "peak_source": peak_source},
         "gpu_launches": main["launches"],
         "clocks": clk,
         "e2e": {"value": round(e2e_v * (world if world > 1 else 1), 3), "unit": UNIT,
@@ -343,6 +374,11 @@ def run_ours(args):
     }
     if fp32 is not None:
         line["fp32_plain"] = {"value": round(len(fp32["per_frame_ms"]) / (fp32["total_ms"] / 1e3), 3), "unit": UNIT}
+    if fp8 is not None:
+        p8 = sorted(fp8["per_frame_ms"])
+        line["fp8_e4m3"] = {"value": round(len(p8) / (fp8["total_ms"] / 1e3), 3), "unit": UNIT,
+                            "p99_ms": round(p8[min(len(p8) - 1, int(0.99 * len(p8)))], 4),
+                            "scales": "static, amax/448 from a BF16 pass over frames 0-2"}
     if world == 1 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline_oracle()
     print(json.dumps(line), flush=True)
@@ -486,8 +522,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp8", "fp32"])
     ap.add_argument("--skip-fp32", action="store_true")
+    ap.add_argument("--skip-fp8", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--serve", action="store_true", help="run the multi-stream serving benchmark instead")
     ap.add_argument("--workers", type=int, default=8)

@@ -30,6 +30,11 @@
  * Precision: TC_FP32 runs every stage in float32.  TC_BF16 runs the convolutions and the
  * correlation with bfloat16 operands and float32 accumulation; flow coordinates, feature
  * warp interpolation weights, the mask thresholds and the consistency step stay float32.
+ * TC_FP8_E4M3 stores every network activation as e4m3 with one float scale per activation
+ * segment (see tc_set_fp8_scales) and every weight as e4m3 with one scale per output
+ * channel; the products accumulate in float32 on the tensor cores.  The flows, the
+ * residual base flow and the consistency step stay float32.  The paper runs in float32
+ * (Sec. 4); this precision has no counterpart there.
  */
 #ifndef TC_STREAM_H
 #define TC_STREAM_H
@@ -81,7 +86,8 @@ typedef struct {
 
 /* Stream description.
  *   width, height   frame size in pixels, each >= 2^levels of the network.
- *   precision       TC_FP32 or TC_BF16.
+ *   precision       TC_FP32, TC_BF16 or TC_FP8_E4M3 (the latter processes frames only
+ *                   after tc_set_fp8_scales).
  *   weights_path    path of a 'TCW1' weight file, or NULL to use weights_blob.
  *   weights_blob    host pointer to the same bytes as such a file (copied at creation).
  * The weight file fixes the number of pyramid levels, the channel counts and the
@@ -133,6 +139,34 @@ TC_API tc_status tc_process_frame_host(tc_stream *s, const float *I_t, const flo
  * kernel.  Waits for the stream.  Per-stage profiling always runs without graphs. */
 TC_API tc_status tc_set_graphs(tc_stream *s, int enable);
 
+/* ---- E4M3 calibration --------------------------------------------------------------
+ * An activation segment is one group of channels that shares an e4m3 scale: for each
+ * pyramid level l = 1..L the outputs of its three convs (index 3(l-1) + j, j = 0, 1, 2);
+ * for each estimator level l = L..2 the six input groups of its decoder, cost volume,
+ * up-sampled flow, x1, x2, x3, x4 (index 3L + 6(L-l) + k, k = 0..5).
+ * tc_activation_segments(s) = 3L + 6(L-1); 0 for s == NULL. */
+TC_API int tc_activation_segments(const tc_stream *s);
+
+/* TC_FP32 / TC_BF16 streams: enable != 0 clears the record and from then on folds the
+ * largest |value| of every activation segment of every processed frame into it (frames run
+ * without graphs while recording).  enable = 0 stops recording and keeps the record.
+ * Errors: TC_ERR_INVALID_ARG for a TC_FP8_E4M3 stream. */
+TC_API tc_status tc_set_amax_recording(tc_stream *s, int enable);
+
+/* Copies the record into amax[0 .. tc_activation_segments(s)) (host floats; n is the
+ * array's length).  Waits for the stream. */
+TC_API tc_status tc_get_amax(tc_stream *s, float *amax, int n);
+
+/* TC_FP8_E4M3 streams: sets the scale of every activation segment (host array of exactly
+ * tc_activation_segments(s) floats; an activation x is stored as e4m3(x / scale), so
+ * amax / 448 uses the whole e4m3 range; 0 means "always zero" and is taken as 1).  Folds
+ * the scales into the e4m3 weights and plans every layer and correlation on the tensor
+ * cores; may be called again to re-calibrate.  Waits for the stream and drops its captured
+ * graphs.  Errors: TC_ERR_INVALID_ARG (not e4m3, wrong n, negative or non-finite scale),
+ * TC_ERR_UNSUPPORTED (a layer the e4m3 tensor-core kernels cannot take: every layer needs
+ * cin and cout multiples of 16, cout <= 128). */
+TC_API tc_status tc_set_fp8_scales(tc_stream *s, const float *scales, int n);
+
 /* Writes the flows of the last processed frame at full resolution: Fb = F_{t->t-1} and
  * Ff = F_{t-1->t}, each device (2, H, W) float32 (planar u then v).  Either may be NULL.
  * Errors: TC_ERR_STATE before the second frame. */
@@ -144,7 +178,7 @@ TC_API tc_status tc_get_flows(tc_stream *s, float *Fb, float *Ff);
 TC_API tc_status tc_synchronize(tc_stream *s);
 
 /* Number of convolution layers of s that run on the tensor cores (tcgen05), flow heads
- * included; 0 for TC_FP32. */
+ * included; 0 for TC_FP32 (and for TC_FP8_E4M3 before tc_set_fp8_scales). */
 TC_API int tc_tensor_core_layers(const tc_stream *s);
 
 /* Number of pyramid levels of s whose correlation runs on the tensor cores; 0 for TC_FP32. */
@@ -196,25 +230,33 @@ TC_API tc_status tc_get_profile(tc_stream *s, double *ms, long long *launches, i
  * (Sec. 3.2 pyramid and estimator layers).  in (n, h, w, cin); w_oihw, bias: HOST float32
  * (cout, cin, 3, 3) and (cout); out (n, (h-1)/stride+1, (w-1)/stride+1, cout).
  * Allocates temporary device memory for the weights, waits for completion.  cin, cout >= 1.
- * With TC_BF16 eligible layers run on the tensor cores (see tc_op_last_used_tensor_cores). */
+ * With TC_BF16 eligible layers run on the tensor cores (see tc_op_last_used_tensor_cores).
+ * TC_FP8_E4M3 (tensor cores only; cout <= 128, else TC_ERR_UNSUPPORTED): the input is
+ * rounded to e4m3 as given (activation scale 1), each output channel's weights to e4m3
+ * after dividing by s_o = max |w[o]| / 448, the products accumulate in float32, and
+ * out = e4m3(LeakyReLU(s_o acc + bias)) (scale 1), returned as float32. */
 TC_API tc_status tc_op_conv3x3(tc_precision precision, const float *in, int n, int h, int w, int cin,
                         const float *w_oihw, const float *bias, int cout, int stride, int leaky,
                         float *out, void *cuda_stream);
 
 /* 1 if the last successful tc_op_conv3x3 or tc_op_correlation in this process ran on the
  * tensor cores, else 0.  TC_BF16 convs with cin a multiple of 8 and cout a multiple of 16 up
- * to 128, and TC_BF16 correlations with c a multiple of 8 up to 128, do. */
+ * to 128, and TC_BF16 correlations with c a multiple of 8 up to 128, do; TC_FP8_E4M3 ones
+ * always do. */
 TC_API int tc_op_last_used_tensor_cores(void);
 
 /* Cost volume (Sec. 3.2): out[n][y][x][k] = LeakyReLU((1/c) sum_ch f1[n][y][x][ch] *
  * f2[n][y+dy][x+dx][ch]), zero off the map, k = (dy+r)(2r+1) + (dx+r).  f1, f2
- * (n, h, w, c); out (n, h, w, (2r+1)^2).  1 <= r <= 4, c a multiple of 4. */
+ * (n, h, w, c); out (n, h, w, (2r+1)^2).  1 <= r <= 4, c a multiple of 4.  TC_FP8_E4M3
+ * (tensor cores only; c a multiple of 16 up to 128, else TC_ERR_UNSUPPORTED): f1, f2 rounded
+ * to e4m3 as given, float32 accumulation, out = e4m3(LeakyReLU(sum / c)) (scale 1). */
 TC_API tc_status tc_op_correlation(tc_precision precision, const float *f1, const float *f2, int n,
                             int h, int w, int c, int r, float *out, void *cuda_stream);
 
 /* Bilinear backward warp of features with zeros off the map (Sec. 3.2 feature warping):
  * out[n][y][x] = sum of the bilinear taps of f[n] at (x + u, y + v) that lie on the map.
- * f (n, h, w, c), flow (n, h, w, 2), out (n, h, w, c).  c a multiple of 4. */
+ * f (n, h, w, c), flow (n, h, w, 2), out (n, h, w, c).  c a multiple of 4.  TC_FP8_E4M3:
+ * f rounded to e4m3 as given, float32 interpolation, out rounded to e4m3 (scale 1). */
 TC_API tc_status tc_op_warp_features(tc_precision precision, const float *f, const float *flow, int n,
                               int h, int w, int c, float *out, void *cuda_stream);
 

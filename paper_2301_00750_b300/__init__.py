@@ -31,7 +31,9 @@ EXPORTED = ["tc_default_consistency", "tc_create_stream", "tc_set_consistency", 
             "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
             "tc_op_consistency", "tc_set_profiling", "tc_get_profile", "tc_synchronize", "tc_tensor_core_layers",
             "tc_op_last_used_tensor_cores", "tc_op_correlation_bf16_noalloc",
-            "tc_tensor_core_correlation_levels", "tc_set_graphs"]
+            "tc_tensor_core_correlation_levels", "tc_set_graphs", "tc_activation_segments",
+            "tc_set_amax_recording", "tc_get_amax", "tc_set_fp8_scales"]
+E4M3_MAX = 448.0
 NOALLOC_SCRATCH_BYTES = 16 << 20
 PROFILE_CATEGORIES = ["pyramid_conv", "estimator_conv", "head", "correlation", "warp", "upsample", "consistency",
                       "other"]
@@ -74,8 +76,12 @@ _lib.tc_synchronize.argtypes = [_vp]
 _lib.tc_tensor_core_layers.argtypes = [_vp]
 _lib.tc_tensor_core_correlation_levels.argtypes = [_vp]
 _lib.tc_op_last_used_tensor_cores.argtypes = []
+_lib.tc_activation_segments.argtypes = [_vp]
+_lib.tc_set_amax_recording.argtypes = [_vp, _i]
+_lib.tc_get_amax.argtypes = [_vp, ctypes.POINTER(_f), _i]
+_lib.tc_set_fp8_scales.argtypes = [_vp, ctypes.POINTER(_f), _i]
 _lib.tc_get_profile.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), _i]
-for _n in ["tc_set_graphs", "tc_op_correlation_bf16_noalloc", "tc_synchronize", "tc_set_profiling", "tc_get_profile", "tc_create_stream", "tc_set_consistency", "tc_process_frame", "tc_process_frame_host", "tc_get_flows",
+for _n in ["tc_set_amax_recording", "tc_get_amax", "tc_set_fp8_scales", "tc_set_graphs", "tc_op_correlation_bf16_noalloc", "tc_synchronize", "tc_set_profiling", "tc_get_profile", "tc_create_stream", "tc_set_consistency", "tc_process_frame", "tc_process_frame_host", "tc_get_flows",
            "tc_destroy", "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
            "tc_op_consistency"]:
     getattr(_lib, _n).restype = ctypes.c_int
@@ -202,6 +208,25 @@ class Stream:
         _check(_lib.tc_synchronize(self._h), self._h)
 
     @property
+    def activation_segments(self) -> int:
+        return _lib.tc_activation_segments(self._h)
+
+    def set_amax_recording(self, enable: bool):
+        """FP32/BF16 streams: record the largest |activation| of every segment from now on."""
+        _check(_lib.tc_set_amax_recording(self._h, int(bool(enable))), self._h)
+
+    def get_amax(self) -> np.ndarray:
+        n = self.activation_segments
+        a = (_f * n)()
+        _check(_lib.tc_get_amax(self._h, a, n), self._h)
+        return np.array(a[:], np.float32)
+
+    def set_fp8_scales(self, scales):
+        """E4M3 streams: one scale per activation segment (x is stored as e4m3(x / scale))."""
+        sc = np.ascontiguousarray(scales, np.float32)
+        _check(_lib.tc_set_fp8_scales(self._h, sc.ctypes.data_as(ctypes.POINTER(_f)), int(sc.size)), self._h)
+
+    @property
     def tensor_core_layers(self) -> int:
         return _lib.tc_tensor_core_layers(self._h)
 
@@ -223,6 +248,23 @@ class Stream:
             self.destroy()
         except Exception:
             pass
+
+
+def calibrate_fp8(width, height, frames, weights_path=None, weights_blob=None, margin=1.0):
+    """E4M3 scales from a BF16 pass: runs `frames` (a list of (I, P) CUDA (3, H, W) float32
+    pairs) through a BF16 stream recording the amax of every activation segment, and returns
+    margin * amax / 448 per segment (the scales tc_set_fp8_scales takes)."""
+    import torch
+    s = Stream(width, height, "bf16", weights_path=weights_path, weights_blob=weights_blob)
+    try:
+        s.set_amax_recording(True)
+        out = torch.empty((3, height, width), device="cuda", dtype=torch.float32)
+        for I, P in frames:
+            s.process_frame(I, P, out)
+        amax = s.get_amax()
+    finally:
+        s.destroy()
+    return (margin * amax / E4M3_MAX).astype(np.float32)
 
 
 # ----------------------------------------------------------------------------- stage ops

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -16,6 +17,12 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float
     return __float2bfloat16_rn(v);
 }
 
+// E4M3 activations hold the value divided by a per-tensor scale; the kernels here move the
+// scaled codes (warps interpolate them, copies copy them) and the scale is applied where the
+// arithmetic needs it (tensor-core epilogues, the first conv's output, the up-flow channels).
+__device__ __forceinline__ float to_f(__nv_fp8_e4m3 v) { return float(v); }
+template <> __device__ __forceinline__ __nv_fp8_e4m3 from_f<__nv_fp8_e4m3>(float v) { return __nv_fp8_e4m3(v); }
+
 // Loads 4 consecutive activations (16-byte aligned for float, 8-byte for bf16) as float4.
 __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ float4 ld4(const __nv_bfloat16 *p) {
@@ -24,6 +31,13 @@ __device__ __forceinline__ float4 ld4(const __nv_bfloat16 *p) {
     __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162 *>(&u.y);
     float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
     return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+__device__ __forceinline__ float4 ld4(const __nv_fp8_e4m3 *p) {
+    const __nv_fp8x4_e4m3 q = *reinterpret_cast<const __nv_fp8x4_e4m3 *>(p);
+    return float4(q);
+}
+__device__ __forceinline__ void st4(__nv_fp8_e4m3 *p, float4 v) {
+    *reinterpret_cast<__nv_fp8x4_e4m3 *>(p) = __nv_fp8x4_e4m3(v);
 }
 __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 __device__ __forceinline__ void st4(__nv_bfloat16 *p, float4 v) {
@@ -54,6 +68,7 @@ struct ConvArgs {
     void *out;
     int out_cs;
     int leaky;
+    float q_out;  // e4m3 outputs: 1 / output activation scale (unused otherwise)
 };
 
 // First pyramid conv: planar float image (3, H, W), edge-replicated to (Hp, Wp) and
@@ -65,6 +80,7 @@ struct ConvFirstArgs {
     const float *bias;
     int cout;
     void *out;  // [Hp/2][Wp/2][cout]
+    float q_out;  // outputs are multiplied by q_out before storing (1 / scale for e4m3, else 1)
 };
 
 // Flow head: conv5 (cin -> 2, no activation) plus the residual up-flow.
@@ -102,6 +118,7 @@ struct WarpArgs {
     float *up_out;
     void *act;
     int act_cs;
+    float act_q;  // the up-flow is multiplied by act_q before the activation store (1 unless e4m3)
 };
 
 struct UpArgs {
@@ -138,6 +155,8 @@ template <typename T> const void *conv_first_kernel_fn();
 const void *consistency_kernel_fn();
 cudaError_t launch_flow_out(const float *flow, int fh, int fw, int scale, int H, int W,
                             float *out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_amax(const T *base, size_t npix, int cs, int nc, unsigned *slot, cudaStream_t st);
 template <typename T> cudaError_t launch_to_act(const float *in, size_t n, T *out, cudaStream_t st);
 template <typename T> cudaError_t launch_from_act(const T *in, size_t n, float *out, cudaStream_t st);
 

@@ -18,6 +18,7 @@
 // Every mbarrier wait is bounded by a 2 s timer: on timeout the CTA records a code in the
 // stream's device error word, stops issuing work, drains what it issued and frees its TMEM.
 #include <cudaTypedefs.h>
+#include <cuda_fp8.h>
 
 #include <cstring>
 #include <mutex>
@@ -32,7 +33,8 @@ namespace {
 using namespace ptx;
 
 constexpr int BM = 128;                    // output pixels per CTA (MMA M)
-constexpr int BK = 64;                     // input channels per step (128 B of bf16)
+constexpr int BK = 64;                     // bf16 channels per step (128 B); e4m3 steps hold 128
+template <bool F8> __host__ __device__ constexpr int kch() { return F8 ? 128 : 64; }
 constexpr uint32_t A_BYTES = BM * BK * 2;  // 16 KB
 
 enum : int { ERR_PRODUCER = 1, ERR_MMA = 2, ERR_EPILOGUE = 3, ERR_DRAIN = 4 };
@@ -48,18 +50,20 @@ struct TcLaunch {
     int stride;   // 1 or 2
     int ho, wo;
     int img_off;  // first input image in the A descriptor
-    __nv_bfloat16 *out;
+    void *out;        // bf16 or e4m3 NHWC output (channel offset applied)
     int out_cs;
     const float *bias;
     int leaky;
     int *err;
     float *flow;      // flow-head mode: (n, ho, wo, 2) float output
     const float *up;  // flow-head mode: residual base flow, same layout, or NULL
+    const float *wscale;  // e4m3: per-output-channel weight scale (activation scales folded in)
+    float q_out;          // e4m3: 1 / output activation scale
 };
 
 // Epilogue shared by the conv kernels: thread r of the CTA owns accumulator row r, i.e.
 // output pixel (img, y, x0 + r).
-template <int BN, bool HEAD>
+template <int BN, bool HEAD, bool F8>
 __device__ __forceinline__ void conv_epilogue(uint32_t tmem, const TcLaunch &p, int warp, int lane, int x0, int y,
                                               int img) {
     if (HEAD) {
@@ -70,13 +74,15 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, const TcLaunch &p, 
             const size_t pix = (size_t)(img * p.ho + y) * p.wo + x;
             float2 up = make_float2(0.f, 0.f);
             if (p.up) up = reinterpret_cast<const float2 *>(p.up)[pix];
+            const float s0 = F8 ? __ldg(p.wscale) : 1.f, s1 = F8 ? __ldg(p.wscale + 1) : 1.f;
             reinterpret_cast<float2 *>(p.flow)[pix] =
-                make_float2(up.x + (__uint_as_float(r[0]) + __ldg(p.bias)), up.y + (__uint_as_float(r[1]) + __ldg(p.bias + 1)));
+                make_float2(up.x + (__uint_as_float(r[0]) * s0 + __ldg(p.bias)),
+                            up.y + (__uint_as_float(r[1]) * s1 + __ldg(p.bias + 1)));
         }
     } else {
         const int row = warp * 32 + lane;
         const int x = x0 + row;
-        __nv_bfloat16 *dst = p.out + ((size_t)(img * p.ho + y) * p.wo + x) * p.out_cs;
+        const size_t pix = (size_t)(img * p.ho + y) * p.wo + x;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 16) {
             uint32_t r[16];
@@ -85,20 +91,31 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, const TcLaunch &p, 
                 float v[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    v[j] = __uint_as_float(r[j]) + __ldg(p.bias + c0 + j);
+                    const float a = __uint_as_float(r[j]);
+                    v[j] = (F8 ? a * __ldg(p.wscale + c0 + j) : a) + __ldg(p.bias + c0 + j);
                     if (p.leaky) v[j] = v[j] >= 0.f ? v[j] : 0.1f * v[j];
                 }
-                uint4 lo, hi;
-                lo.x = pack_bf16x2(v[0], v[1]);
-                lo.y = pack_bf16x2(v[2], v[3]);
-                lo.z = pack_bf16x2(v[4], v[5]);
-                lo.w = pack_bf16x2(v[6], v[7]);
-                hi.x = pack_bf16x2(v[8], v[9]);
-                hi.y = pack_bf16x2(v[10], v[11]);
-                hi.z = pack_bf16x2(v[12], v[13]);
-                hi.w = pack_bf16x2(v[14], v[15]);
-                *reinterpret_cast<uint4 *>(dst + c0) = lo;
-                *reinterpret_cast<uint4 *>(dst + c0 + 8) = hi;
+                if (F8) {
+                    uint4 q;
+                    q.x = pack_e4m3x4(v[0] * p.q_out, v[1] * p.q_out, v[2] * p.q_out, v[3] * p.q_out);
+                    q.y = pack_e4m3x4(v[4] * p.q_out, v[5] * p.q_out, v[6] * p.q_out, v[7] * p.q_out);
+                    q.z = pack_e4m3x4(v[8] * p.q_out, v[9] * p.q_out, v[10] * p.q_out, v[11] * p.q_out);
+                    q.w = pack_e4m3x4(v[12] * p.q_out, v[13] * p.q_out, v[14] * p.q_out, v[15] * p.q_out);
+                    *reinterpret_cast<uint4 *>(static_cast<uint8_t *>(p.out) + pix * p.out_cs + c0) = q;
+                } else {
+                    __nv_bfloat16 *dst = static_cast<__nv_bfloat16 *>(p.out) + pix * p.out_cs;
+                    uint4 lo, hi;
+                    lo.x = pack_bf16x2(v[0], v[1]);
+                    lo.y = pack_bf16x2(v[2], v[3]);
+                    lo.z = pack_bf16x2(v[4], v[5]);
+                    lo.w = pack_bf16x2(v[6], v[7]);
+                    hi.x = pack_bf16x2(v[8], v[9]);
+                    hi.y = pack_bf16x2(v[10], v[11]);
+                    hi.z = pack_bf16x2(v[12], v[13]);
+                    hi.w = pack_bf16x2(v[14], v[15]);
+                    *reinterpret_cast<uint4 *>(dst + c0) = lo;
+                    *reinterpret_cast<uint4 *>(dst + c0 + 8) = hi;
+                }
             }
         }
     }
@@ -106,7 +123,7 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, const TcLaunch &p, 
 
 // HEAD = true: the flow head (cout = 2, zero-padded to BN = 16 for the MMA); the epilogue
 // writes float32 flow = up + (acc[0], acc[1]) + bias without activation.
-template <int BN, bool HEAD>
+template <int BN, bool HEAD, bool F8>
 __global__ void __launch_bounds__(128, 1)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcLaunch p) {
     constexpr int STAGES = stages_for(BN);
@@ -157,13 +174,13 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             mbar_expect_tx(fb, STAGE_TX);
             const uint32_t dA = smem_u32(sA + s * A_BYTES), dB = smem_u32(sB + s * B_BYTES);
             if (p.stride == 1) {
-                tma_load_4d(&tmA, fb, dA, ch * BK, x0 + kx - 1, y + ky - 1, img + p.img_off);
+                tma_load_4d(&tmA, fb, dA, ch * kch<F8>(), x0 + kx - 1, y + ky - 1, img + p.img_off);
             } else {
                 const int dx = kx - 1;
-                tma_load_5d(&tmA, fb, dA, ch * BK, dx != 0 ? 1 : 0, x0 + (dx < 0 ? -1 : 0), 2 * y + ky - 1,
+                tma_load_5d(&tmA, fb, dA, ch * kch<F8>(), dx != 0 ? 1 : 0, x0 + (dx < 0 ? -1 : 0), 2 * y + ky - 1,
                             img + p.img_off);
             }
-            tma_load_3d(&tmB, fb, dB, ch * BK, 0, tap);
+            tma_load_3d(&tmB, fb, dB, ch * kch<F8>(), 0, tap);
             issued = ks + 1;
         }
         if (issued < nk) {
@@ -179,7 +196,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
     } else if (threadIdx.x == 32) {
         // ---- MMA issuer
-        constexpr uint32_t idesc = idesc_bf16(BM, BN);
+        constexpr uint32_t idesc = F8 ? idesc_e4m3(BM, BN) : idesc_bf16(BM, BN);
         for (int ks = 0; ks < nk; ++ks) {
             const int s = ks % STAGES;
             if (!mbar_wait(full0 + 8 * s, (uint32_t)(ks / STAGES) & 1u, p.err, ERR_MMA)) break;
@@ -188,7 +205,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             const uint64_t db = sw128_desc(smem_u32(sB + s * B_BYTES));
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk)
-                umma_bf16(tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, (ks | kk) != 0 ? 1u : 0u);
+                umma<F8>(tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, (ks | kk) != 0 ? 1u : 0u);
             umma_commit(empty0 + 8 * s);
         }
         umma_commit(accum);  // arrives when every MMA issued above has completed
@@ -201,7 +218,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (lane == 0) ok = mbar_wait(accum, 0, p.err, ERR_EPILOGUE) && *(volatile int *)p.err == 0;
     ok = __shfl_sync(0xffffffffu, ok, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) conv_epilogue<BN, HEAD>(tmem, p, warp, lane, x0, y, img);
+    if (ok) conv_epilogue<BN, HEAD, F8>(tmem, p, warp, lane, x0, y, img);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -224,7 +241,7 @@ __host__ __device__ constexpr size_t halo_smem_for(int bn) {
     return (size_t)HALO_SA * HALO_SLOT + (size_t)halo_sb(bn) * bn * BK * 2 + 1024 + 256;
 }
 
-template <int BN, bool HEAD>
+template <int BN, bool HEAD, bool F8>
 __global__ void __launch_bounds__(128, 1)
 conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcLaunch p) {
     constexpr int SB = halo_sb(BN);
@@ -276,7 +293,7 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
             const int sa = g % HALO_SA;
             if (!mbar_wait(emptyA + 8 * sa, ((uint32_t)(g / HALO_SA) & 1u) ^ 1u, p.err, ERR_PRODUCER)) break;
             mbar_expect_tx(fullA + 8 * sa, HALO_TX);
-            tma_load_4d(&tmA, fullA + 8 * sa, smem_u32(sA + sa * HALO_SLOT), ch * BK, x0 - 1, y + ky - 1,
+            tma_load_4d(&tmA, fullA + 8 * sa, smem_u32(sA + sa * HALO_SLOT), ch * kch<F8>(), x0 - 1, y + ky - 1,
                         img + p.img_off);
             ga = g + 1;
             for (int kx = 0; kx < 3; ++kx) {
@@ -286,7 +303,7 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                     break;
                 }
                 mbar_expect_tx(fullB + 8 * sb, B_BYTES);
-                tma_load_3d(&tmB, fullB + 8 * sb, smem_u32(sB + sb * B_BYTES), ch * BK, 0, ky * 3 + kx);
+                tma_load_3d(&tmB, fullB + 8 * sb, smem_u32(sB + sb * B_BYTES), ch * kch<F8>(), 0, ky * 3 + kx);
                 gb = kb + 1;
             }
         }
@@ -302,7 +319,7 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
         }
     } else if (threadIdx.x == 32) {
         // ---- MMA issuer
-        constexpr uint32_t idesc = idesc_bf16(BM, BN);
+        constexpr uint32_t idesc = F8 ? idesc_e4m3(BM, BN) : idesc_bf16(BM, BN);
         bool fine = true;
         for (int g = 0; g < ng && fine; ++g) {
             const int sa = g % HALO_SA;
@@ -319,7 +336,7 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                 const uint64_t db = sw128_desc(smem_u32(sB + sb * B_BYTES));
 #pragma unroll
                 for (int kk = 0; kk < BK / 16; ++kk)
-                    umma_bf16(tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                    umma<F8>(tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
                               (g | kx | kk) != 0 ? 1u : 0u);
                 umma_commit(emptyB + 8 * sb);
             }
@@ -332,7 +349,7 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     if (lane == 0) ok = mbar_wait(accum, 0, p.err, ERR_EPILOGUE) && *(volatile int *)p.err == 0;
     ok = __shfl_sync(0xffffffffu, ok, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) conv_epilogue<BN, HEAD>(tmem, p, warp, lane, x0, y, img);
+    if (ok) conv_epilogue<BN, HEAD, F8>(tmem, p, warp, lane, x0, y, img);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -341,29 +358,29 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     }
 }
 
-template <int BN, bool HEAD = false>
+template <int BN, bool HEAD = false, bool F8 = false>
 cudaError_t launch_bn(const TcConvPlan &plan, const TcLaunch &lp, int n_img, cudaStream_t st) {
     dim3 grid((plan.wo + BM - 1) / BM, plan.ho, n_img);
     if (plan.stride == 1) {
         static bool attr_set = false;
         const size_t smem = halo_smem_for(BN);
         if (!attr_set) {
-            cudaError_t e = cudaFuncSetAttribute(conv_tc_halo_kernel<BN, HEAD>,
+            cudaError_t e = cudaFuncSetAttribute(conv_tc_halo_kernel<BN, HEAD, F8>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             attr_set = true;
         }
-        conv_tc_halo_kernel<BN, HEAD><<<grid, 128, smem, st>>>(plan.tmA, plan.tmB, lp);
+        conv_tc_halo_kernel<BN, HEAD, F8><<<grid, 128, smem, st>>>(plan.tmA, plan.tmB, lp);
     } else {
         static bool attr_set = false;
         const size_t smem = smem_bytes_for(BN);
         if (!attr_set) {
             cudaError_t e =
-                cudaFuncSetAttribute(conv_tc_kernel<BN, HEAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                cudaFuncSetAttribute(conv_tc_kernel<BN, HEAD, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             attr_set = true;
         }
-        conv_tc_kernel<BN, HEAD><<<grid, 128, smem, st>>>(plan.tmA, plan.tmB, lp);
+        conv_tc_kernel<BN, HEAD, F8><<<grid, 128, smem, st>>>(plan.tmA, plan.tmB, lp);
     }
     return cudaGetLastError();
 }
@@ -388,73 +405,105 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 void TcConvPlan::release() {
     if (wpk) cudaFree(wpk);
+    if (wscale) cudaFree(wscale);
     wpk = nullptr;
+    wscale = nullptr;
     wpk_bytes = 0;
     enabled = false;
 }
 
 bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vector<float> &wk_simt, int *err,
-                  std::string &why) {
+                  std::string &why, bool f8) {
     plan.enabled = false;
     plan.head = false;
     const int bn = a.cout;
+    const int align = f8 ? 16 : 8;  // 16-byte TMA strides and vector stores
     if (bn < 16 || bn > 128 || bn % 16 != 0) { why = "cout must be a multiple of 16 in [16, 128]"; return false; }
-    if (a.cin % 8 != 0 || a.in_cs % 8 != 0 || a.out_cs % 8 != 0) { why = "channel counts must be multiples of 8"; return false; }
+    if (a.cin % align != 0 || a.in_cs % align != 0 || a.out_cs % align != 0) {
+        why = "channel counts must be multiples of 16 bytes";
+        return false;
+    }
     if (reinterpret_cast<uintptr_t>(a.in) % 16 != 0) { why = "input not 16-byte aligned"; return false; }
     if (a.stride != 1 && (a.stride != 2 || a.w % 2 != 0)) { why = "stride must be 1, or 2 with even width"; return false; }
     if (a.ho != (a.h - 1) / a.stride + 1 || a.wo != (a.w - 1) / a.stride + 1) { why = "output size mismatch"; return false; }
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) { why = "cuTensorMapEncodeTiled unavailable"; return false; }
-    const int nch = (a.cin + BK - 1) / BK, cinp = nch * BK;
-    // Packed weights [9][cout][cinp] in bfloat16 (zero beyond cin).
-    std::vector<__nv_bfloat16> pk((size_t)9 * bn * cinp, __float2bfloat16_rn(0.f));
+    const int kc = f8 ? 128 : 64;  // channels per 128-byte step
+    const int nch = (a.cin + kc - 1) / kc, cinp = nch * kc;
+    const cuuint64_t esz = f8 ? 1 : 2;
+    // Packed weights [9][cout][cinp] (zero beyond cin): bfloat16, or e4m3 with one scale per
+    // output channel (amax / 448 over its 9 x cin weights).
+    std::vector<uint8_t> pk((size_t)9 * bn * cinp * esz, 0);
+    std::vector<float> ws(bn, 1.f);
+    if (f8) {
+        for (int o = 0; o < bn; ++o) {
+            float amax = 0.f;
+            for (size_t k = 0; k < (size_t)9 * a.cin; ++k) amax = fmaxf(amax, fabsf(wk_simt[k * bn + o]));
+            ws[o] = amax > 0.f ? amax / 448.f : 1.f;
+        }
+    }
     for (int tap = 0; tap < 9; ++tap)
         for (int c = 0; c < a.cin; ++c)
-            for (int o = 0; o < bn; ++o)
-                pk[((size_t)tap * bn + o) * cinp + c] = __float2bfloat16_rn(wk_simt[((size_t)tap * a.cin + c) * bn + o]);
-    __nv_bfloat16 *wdev = nullptr;
-    if (cudaMalloc(&wdev, pk.size() * 2) != cudaSuccess) { cudaGetLastError(); why = "weight allocation failed"; return false; }
-    if (cudaMemcpy(wdev, pk.data(), pk.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) {
+            for (int o = 0; o < bn; ++o) {
+                const float v = wk_simt[((size_t)tap * a.cin + c) * bn + o];
+                const size_t idx = ((size_t)tap * bn + o) * cinp + c;
+                if (f8) {
+                    pk[idx] = (uint8_t)__nv_cvt_float_to_fp8(v / ws[o], __NV_SATFINITE, __NV_E4M3);
+                } else {
+                    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+                    memcpy(&pk[2 * idx], &b, 2);
+                }
+            }
+    void *wdev = nullptr;
+    float *sdev = nullptr;
+    if (cudaMalloc(&wdev, pk.size()) != cudaSuccess || (f8 && cudaMalloc(&sdev, bn * sizeof(float)) != cudaSuccess)) {
+        cudaGetLastError();
+        if (wdev) cudaFree(wdev);
+        why = "weight allocation failed";
+        return false;
+    }
+    if (cudaMemcpy(wdev, pk.data(), pk.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        (f8 && cudaMemcpy(sdev, ws.data(), bn * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)) {
         cudaGetLastError();
         cudaFree(wdev);
+        if (sdev) cudaFree(sdev);
         why = "weight upload failed";
         return false;
     }
+    const CUtensorMapDataType dt = f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
     CUresult r;
-    const cuuint64_t esz = 2;
     if (a.stride == 1) {
         const cuuint64_t dims[4] = {(cuuint64_t)a.cin, (cuuint64_t)a.w, (cuuint64_t)a.h, (cuuint64_t)n_in};
         const cuuint64_t strides[3] = {a.in_cs * esz, (cuuint64_t)a.w * a.in_cs * esz, (cuuint64_t)a.h * a.w * a.in_cs * esz};
-        const cuuint32_t box[4] = {BK, HALO_ROWS, 1, 1};  // the stride-1 kernel loads halo rows
-        r = enc(&plan.tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(a.in), dims, strides, box, ones,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        const cuuint32_t box[4] = {(cuuint32_t)kc, HALO_ROWS, 1, 1};  // the stride-1 kernel loads halo rows
+        r = enc(&plan.tmA, dt, 4, const_cast<void *>(a.in), dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     } else {
         const cuuint64_t dims[5] = {(cuuint64_t)a.cin, 2, (cuuint64_t)(a.w / 2), (cuuint64_t)a.h, (cuuint64_t)n_in};
         const cuuint64_t strides[4] = {a.in_cs * esz, 2 * a.in_cs * esz, (cuuint64_t)a.w * a.in_cs * esz,
                                        (cuuint64_t)a.h * a.w * a.in_cs * esz};
-        const cuuint32_t box[5] = {BK, 1, BM, 1, 1};
-        r = enc(&plan.tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(a.in), dims, strides, box, ones,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        const cuuint32_t box[5] = {(cuuint32_t)kc, 1, BM, 1, 1};
+        r = enc(&plan.tmA, dt, 5, const_cast<void *>(a.in), dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     }
     if (r == CUDA_SUCCESS) {
         const cuuint64_t dims[3] = {(cuuint64_t)cinp, (cuuint64_t)bn, 9};
         const cuuint64_t strides[2] = {(cuuint64_t)cinp * esz, (cuuint64_t)bn * cinp * esz};
-        const cuuint32_t box[3] = {BK, (cuuint32_t)bn, 1};
-        r = enc(&plan.tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, wdev, dims, strides, box, ones,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        const cuuint32_t box[3] = {(cuuint32_t)kc, (cuuint32_t)bn, 1};
+        r = enc(&plan.tmB, dt, 3, wdev, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     }
     if (r != CUDA_SUCCESS) {
         cudaFree(wdev);
+        if (sdev) cudaFree(sdev);
         why = "tensor map encoding failed (" + std::to_string((int)r) + ")";
         return false;
     }
     plan.bn = bn;
     plan.cout = bn;
     plan.nch = nch;
+    plan.f8 = f8;
     plan.stride = a.stride;
     plan.h = a.h;
     plan.w = a.w;
@@ -464,14 +513,15 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
     plan.in_base = a.in;
     plan.img_bytes = (size_t)a.h * a.w * a.in_cs * esz;
     plan.wpk = wdev;
-    plan.wpk_bytes = pk.size() * 2;
+    plan.wscale = sdev;
+    plan.wpk_bytes = pk.size() + (f8 ? bn * sizeof(float) : 0);
     plan.err = err;
     plan.enabled = true;
     return true;
 }
 
 bool tc_plan_head(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vector<float> &wk_simt, int *err,
-                  std::string &why) {
+                  std::string &why, bool f8) {
     if (a.cout > 16) { why = "head has more than 16 outputs"; return false; }
     std::vector<float> wk16((size_t)9 * a.cin * 16, 0.f);
     for (size_t k = 0; k < (size_t)9 * a.cin; ++k)
@@ -479,43 +529,50 @@ bool tc_plan_head(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
     ConvArgs a16 = a;
     a16.cout = 16;
     a16.out_cs = 16;  // not used by the head epilogue
-    if (!tc_plan_conv(plan, a16, n_in, wk16, err, why)) return false;
+    if (!tc_plan_conv(plan, a16, n_in, wk16, err, why, f8)) return false;
     plan.head = true;
     plan.cout = a.cout;
     return true;
 }
 
+static bool image_offset(const TcConvPlan &plan, const ConvArgs &a, int *img_off) {
+    const ptrdiff_t off = static_cast<const char *>(a.in) - static_cast<const char *>(plan.in_base);
+    if (off < 0 || off % (ptrdiff_t)plan.img_bytes != 0) return false;
+    *img_off = (int)(off / (ptrdiff_t)plan.img_bytes);
+    return *img_off + a.n <= plan.n_in && a.n >= 1;
+}
+
 cudaError_t launch_conv_tc_head(const TcConvPlan &plan, const ConvArgs &a, const float *up, float *flow,
                                 cudaStream_t st) {
-    if (!plan.enabled || !plan.head) return cudaErrorInvalidValue;
-    const ptrdiff_t off = static_cast<const char *>(a.in) - static_cast<const char *>(plan.in_base);
-    if (off < 0 || off % (ptrdiff_t)plan.img_bytes != 0) return cudaErrorInvalidValue;
-    const int img_off = (int)(off / (ptrdiff_t)plan.img_bytes);
-    if (img_off + a.n > plan.n_in || a.n < 1) return cudaErrorInvalidValue;
-    TcLaunch lp{plan.nch, plan.stride, plan.ho, plan.wo, img_off, nullptr, 0, a.bias, 0, plan.err, flow, up};
-    return launch_bn<16, true>(plan, lp, a.n, st);
+    int img_off = 0;
+    if (!plan.enabled || !plan.head || !image_offset(plan, a, &img_off)) return cudaErrorInvalidValue;
+    TcLaunch lp{plan.nch, plan.stride, plan.ho, plan.wo, img_off, nullptr, 0, a.bias, 0, plan.err, flow, up,
+                plan.wscale, 1.f};
+    return plan.f8 ? launch_bn<16, true, true>(plan, lp, a.n, st) : launch_bn<16, true, false>(plan, lp, a.n, st);
+}
+
+template <bool F8>
+static cudaError_t launch_any_bn(const TcConvPlan &plan, const TcLaunch &lp, int n, cudaStream_t st) {
+    switch (plan.bn) {
+        case 16: return launch_bn<16, false, F8>(plan, lp, n, st);
+        case 32: return launch_bn<32, false, F8>(plan, lp, n, st);
+        case 48: return launch_bn<48, false, F8>(plan, lp, n, st);
+        case 64: return launch_bn<64, false, F8>(plan, lp, n, st);
+        case 80: return launch_bn<80, false, F8>(plan, lp, n, st);
+        case 96: return launch_bn<96, false, F8>(plan, lp, n, st);
+        case 112: return launch_bn<112, false, F8>(plan, lp, n, st);
+        case 128: return launch_bn<128, false, F8>(plan, lp, n, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_conv_tc(const TcConvPlan &plan, const ConvArgs &a, cudaStream_t st) {
-    if (!plan.enabled || plan.head) return cudaErrorInvalidValue;
-    const ptrdiff_t off = static_cast<const char *>(a.in) - static_cast<const char *>(plan.in_base);
-    if (off < 0 || off % (ptrdiff_t)plan.img_bytes != 0) return cudaErrorInvalidValue;
-    const int img_off = (int)(off / (ptrdiff_t)plan.img_bytes);
-    if (img_off + a.n > plan.n_in || a.n < 1) return cudaErrorInvalidValue;
-    if (reinterpret_cast<uintptr_t>(a.out) % 16 != 0 || a.out_cs % 8 != 0) return cudaErrorInvalidValue;
-    TcLaunch lp{plan.nch, plan.stride, plan.ho, plan.wo, img_off, static_cast<__nv_bfloat16 *>(a.out), a.out_cs,
-                a.bias, a.leaky, plan.err, nullptr, nullptr};
-    switch (plan.bn) {
-        case 16: return launch_bn<16>(plan, lp, a.n, st);
-        case 32: return launch_bn<32>(plan, lp, a.n, st);
-        case 48: return launch_bn<48>(plan, lp, a.n, st);
-        case 64: return launch_bn<64>(plan, lp, a.n, st);
-        case 80: return launch_bn<80>(plan, lp, a.n, st);
-        case 96: return launch_bn<96>(plan, lp, a.n, st);
-        case 112: return launch_bn<112>(plan, lp, a.n, st);
-        case 128: return launch_bn<128>(plan, lp, a.n, st);
-        default: return cudaErrorInvalidValue;
-    }
+    int img_off = 0;
+    if (!plan.enabled || plan.head || !image_offset(plan, a, &img_off)) return cudaErrorInvalidValue;
+    if (reinterpret_cast<uintptr_t>(a.out) % 16 != 0 || a.out_cs % (plan.f8 ? 16 : 8) != 0) return cudaErrorInvalidValue;
+    TcLaunch lp{plan.nch, plan.stride, plan.ho, plan.wo, img_off, a.out, a.out_cs, a.bias, a.leaky, plan.err,
+                nullptr, nullptr, plan.wscale, a.q_out};
+    return plan.f8 ? launch_any_bn<true>(plan, lp, a.n, st) : launch_any_bn<false>(plan, lp, a.n, st);
 }
 
 }  // namespace tc

@@ -16,13 +16,15 @@ namespace tc {
 struct TcConvPlan {
     bool enabled = false;
     bool head = false;  // flow-head plan (float flow output, see tc_plan_head)
+    bool f8 = false;    // e4m3 operands (kind::f8f6f4) instead of bf16
     CUtensorMap tmA;  // 64-byte aligned type
     CUtensorMap tmB;
     int bn = 0, nch = 0, stride = 1, h = 0, w = 0, ho = 0, wo = 0, n_in = 0, cout = 0;
     const void *in_base = nullptr;  // start of the buffer the A descriptor covers
     size_t img_bytes = 0;           // bytes between consecutive images of that buffer
-    __nv_bfloat16 *wpk = nullptr;   // packed weights (owned by the plan)
+    void *wpk = nullptr;            // packed weights (owned by the plan)
     size_t wpk_bytes = 0;
+    float *wscale = nullptr;        // e4m3: per-output-channel weight scales (owned)
     int *err = nullptr;             // device error word shared by the stream (not owned)
     void release();
 };
@@ -32,13 +34,16 @@ struct TcConvPlan {
 // read).  wk_simt: float weights [9 * a.cin][a.cout] (k = tap * cin + c), already in the
 // buffer's channel order.  Returns false with `why` when the layer is not eligible (then
 // the caller uses the CUDA-core kernel).
+// f8: e4m3 operands; wk_simt then holds the weights with the input activations' scales
+// already folded in (w[o][c] * s_in[c]); the epilogue multiplies by the per-output-channel
+// weight scale and quantizes with a.q_out.
 bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vector<float> &wk_simt, int *err,
-                  std::string &why);
+                  std::string &why, bool f8 = false);
 
 // Plans the flow head (cout <= 16, no activation; in practice 2) on the tensor cores: the
 // weights are zero-padded to 16 outputs for the MMA.
 bool tc_plan_head(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vector<float> &wk_simt, int *err,
-                  std::string &why);
+                  std::string &why, bool f8 = false);
 
 // Launches a planned head: flow[i] = up[i] (if up) + bias + conv(a.in)[i][0..1], float (n, ho, wo, 2).
 cudaError_t launch_conv_tc_head(const TcConvPlan &plan, const ConvArgs &a, const float *up, float *flow,

@@ -46,17 +46,18 @@ struct Geo {
 struct CorrTcLaunch {
     int h, w, nch;
     int img_s[2], img_o[2];
-    __nv_bfloat16 *out;
+    void *out;    // bf16 or e4m3 cost volume
     int out_cs;
     int vec_out;  // out and out_cs allow 16-byte stores
-    const __nv_bfloat16 *fs[2];
+    const void *fs[2];
     int c;
-    __nv_bfloat16 *self_copy;
-    float inv_c;
+    void *self_copy;
+    float scale;  // dot product -> cost: 1/C (bf16), s_f^2 / C (e4m3 features with scale s_f)
+    float q_out;  // e4m3: 1 / scale of the stored cost volume
     int *err;
 };
 
-template <int R>
+template <int R, bool F8>
 __global__ void __launch_bounds__(128, 1)
 corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmO, const CorrTcLaunch p) {
     using G = Geo<R>;
@@ -92,12 +93,13 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
         for (int ch = 0; ch < p.nch; ++ch) {
             const uint32_t fb = full0 + 8 * ch;
             mbar_expect_tx(fb, A_BYTES + (uint32_t)G::NPOS * BK * 2);
-            tma_load_4d(&tmS, fb, smem_u32(sA + ch * A_BYTES), ch * BK, x0, y0, p.img_s[b]);
-            tma_load_4d(&tmO, fb, smem_u32(sB + ch * G::B_BYTES), ch * BK, x0 - R, y0 - R, p.img_o[b]);
+            const int c0 = ch * (F8 ? 2 * BK : BK);  // 128-byte steps: 64 bf16 or 128 e4m3 channels
+            tma_load_4d(&tmS, fb, smem_u32(sA + ch * A_BYTES), c0, x0, y0, p.img_s[b]);
+            tma_load_4d(&tmO, fb, smem_u32(sB + ch * G::B_BYTES), c0, x0 - R, y0 - R, p.img_o[b]);
         }
     } else if (threadIdx.x == 32) {
         // ---- MMA issuer: D[:, 0:NH] and D[:, NH:NP]
-        constexpr uint32_t idesc = idesc_bf16(128, G::NH);
+        constexpr uint32_t idesc = F8 ? idesc_e4m3(128, G::NH) : idesc_bf16(128, G::NH);
         bool ok = true;
         for (int ch = 0; ch < p.nch && ok; ++ch) {
             if (!mbar_wait(full0 + 8 * ch, 0, p.err, ERR_CORR_MMA)) {
@@ -111,8 +113,8 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
                 const uint32_t acc = (ch | kk) != 0 ? 1u : 0u;
-                umma_bf16(tmem, da + (uint64_t)(kk * 2), db0 + (uint64_t)(kk * 2), idesc, acc);
-                umma_bf16(tmem + (uint32_t)G::NH, da + (uint64_t)(kk * 2), db1 + (uint64_t)(kk * 2), idesc, acc);
+                umma<F8>(tmem, da + (uint64_t)(kk * 2), db0 + (uint64_t)(kk * 2), idesc, acc);
+                umma<F8>(tmem + (uint32_t)G::NH, da + (uint64_t)(kk * 2), db1 + (uint64_t)(kk * 2), idesc, acc);
             }
         }
         umma_commit(accum);
@@ -159,33 +161,57 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
             }
 #pragma unroll
             for (int i = 0; i <= 2 * R; ++i) {
-                const float v = slice[base + i] * p.inv_c;
+                const float v = slice[base + i] * p.scale;
                 res[j * (2 * R + 1) + i] = v >= 0.f ? v : 0.1f * v;
             }
         }
         if (valid) {
             const size_t pix = ((size_t)b * p.h + y) * p.w + x;
-            __nv_bfloat16 *dst = p.out + pix * p.out_cs;
-            if (p.vec_out) {
+            if (F8) {
+                uint8_t *dst = static_cast<uint8_t *>(p.out) + pix * p.out_cs;
+                if (p.vec_out) {
 #pragma unroll
-                for (int k = 0; k + 8 <= G::ND; k += 8) {
-                    uint4 v;
-                    v.x = pack_bf16x2(res[k], res[k + 1]);
-                    v.y = pack_bf16x2(res[k + 2], res[k + 3]);
-                    v.z = pack_bf16x2(res[k + 4], res[k + 5]);
-                    v.w = pack_bf16x2(res[k + 6], res[k + 7]);
-                    *reinterpret_cast<uint4 *>(dst + k) = v;
+                    for (int k = 0; k + 16 <= G::ND; k += 16) {
+                        uint4 v;
+                        v.x = pack_e4m3x4(res[k] * p.q_out, res[k + 1] * p.q_out, res[k + 2] * p.q_out, res[k + 3] * p.q_out);
+                        v.y = pack_e4m3x4(res[k + 4] * p.q_out, res[k + 5] * p.q_out, res[k + 6] * p.q_out, res[k + 7] * p.q_out);
+                        v.z = pack_e4m3x4(res[k + 8] * p.q_out, res[k + 9] * p.q_out, res[k + 10] * p.q_out, res[k + 11] * p.q_out);
+                        v.w = pack_e4m3x4(res[k + 12] * p.q_out, res[k + 13] * p.q_out, res[k + 14] * p.q_out, res[k + 15] * p.q_out);
+                        *reinterpret_cast<uint4 *>(dst + k) = v;
+                    }
+#pragma unroll
+                    for (int k = G::ND / 16 * 16; k < G::ND; ++k)
+                        dst[k] = (uint8_t)__nv_cvt_float_to_fp8(res[k] * p.q_out, __NV_SATFINITE, __NV_E4M3);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < G::ND; ++k)
+                        dst[k] = (uint8_t)__nv_cvt_float_to_fp8(res[k] * p.q_out, __NV_SATFINITE, __NV_E4M3);
                 }
-#pragma unroll
-                for (int k = G::ND / 8 * 8; k < G::ND; ++k) dst[k] = __float2bfloat16_rn(res[k]);
             } else {
+                __nv_bfloat16 *dst = static_cast<__nv_bfloat16 *>(p.out) + pix * p.out_cs;
+                if (p.vec_out) {
 #pragma unroll
-                for (int k = 0; k < G::ND; ++k) dst[k] = __float2bfloat16_rn(res[k]);
+                    for (int k = 0; k + 8 <= G::ND; k += 8) {
+                        uint4 v;
+                        v.x = pack_bf16x2(res[k], res[k + 1]);
+                        v.y = pack_bf16x2(res[k + 2], res[k + 3]);
+                        v.z = pack_bf16x2(res[k + 4], res[k + 5]);
+                        v.w = pack_bf16x2(res[k + 6], res[k + 7]);
+                        *reinterpret_cast<uint4 *>(dst + k) = v;
+                    }
+#pragma unroll
+                    for (int k = G::ND / 8 * 8; k < G::ND; ++k) dst[k] = __float2bfloat16_rn(res[k]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < G::ND; ++k) dst[k] = __float2bfloat16_rn(res[k]);
+                }
             }
             if (p.self_copy) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(p.fs[b] + ((size_t)y * p.w + x) * p.c);
-                uint4 *cp = reinterpret_cast<uint4 *>(p.self_copy + pix * p.out_cs);
-                for (int q = 0; q < p.c / 8; ++q) cp[q] = __ldg(src + q);
+                const size_t esz = F8 ? 1 : 2;
+                const uint4 *src = reinterpret_cast<const uint4 *>(static_cast<const uint8_t *>(p.fs[b]) +
+                                                                   ((size_t)y * p.w + x) * p.c * esz);
+                uint4 *cp = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(p.self_copy) + pix * p.out_cs * esz);
+                for (int q = 0; q < (int)(p.c * esz / 16); ++q) cp[q] = __ldg(src + q);
             }
         }
     }
@@ -197,43 +223,47 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
     }
 }
 
-bool encode_features(CUtensorMap *map, const void *base, int n, int cs, int h, int w, int c, int box_x, int box_y) {
+bool encode_features(CUtensorMap *map, const void *base, int n, int cs, int h, int w, int c, int box_x, int box_y,
+                     bool f8) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return false;
+    const cuuint64_t es = f8 ? 1 : 2;
     const cuuint64_t dims[4] = {(cuuint64_t)c, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
-    const cuuint64_t strides[3] = {(cuuint64_t)cs * 2, (cuuint64_t)w * cs * 2, (cuuint64_t)h * w * cs * 2};
-    const cuuint32_t box[4] = {BK, (cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+    const cuuint64_t strides[3] = {(cuuint64_t)cs * es, (cuuint64_t)w * cs * es, (cuuint64_t)h * w * cs * es};
+    const cuuint32_t box[4] = {(cuuint32_t)(128 / es), (cuuint32_t)box_x, (cuuint32_t)box_y, 1};
     const cuuint32_t ones[4] = {1, 1, 1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims, strides, box, ones,
+    return enc(map, f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims, strides, box, ones,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int R>
+template <int R, bool F8>
 cudaError_t launch_r(const CorrTcPlan &plan, const CorrTcLaunch &lp, int nb, cudaStream_t st) {
     using G = Geo<R>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(corr_tc_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+        cudaError_t e =
+            cudaFuncSetAttribute(corr_tc_kernel<R, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     dim3 grid((plan.w + BX - 1) / BX, (plan.h + BY - 1) / BY, nb);
-    corr_tc_kernel<R><<<grid, 128, G::SMEM, st>>>(plan.tmS, plan.tmO, lp);
+    corr_tc_kernel<R, F8><<<grid, 128, G::SMEM, st>>>(plan.tmS, plan.tmO, lp);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 bool tc_plan_corr(CorrTcPlan &plan, const void *self, int n_self, int self_cs, const void *other, int n_other,
-                  int other_cs, int h, int w, int c, int r, int *err, std::string &why) {
+                  int other_cs, int h, int w, int c, int r, int *err, std::string &why, bool f8) {
     plan.enabled = false;
-    if (c % 8 != 0 || c < 8 || c > BK * MAX_NCH) { why = "channels must be a multiple of 8 up to 128"; return false; }
+    const int al = f8 ? 16 : 8;  // 16-byte strides
+    if (c % al != 0 || c < al || c > BK * MAX_NCH) { why = "channels must be a multiple of 16 bytes, up to 128"; return false; }
     if (r < 1 || r > 4) { why = "radius must be 1..4"; return false; }
-    if (self_cs % 8 != 0 || other_cs % 8 != 0) { why = "pixel strides must be multiples of 8"; return false; }
+    if (self_cs % al != 0 || other_cs % al != 0) { why = "pixel strides must be multiples of 16 bytes"; return false; }
     if (reinterpret_cast<uintptr_t>(self) % 16 || reinterpret_cast<uintptr_t>(other) % 16) { why = "misaligned"; return false; }
-    if (!encode_features(&plan.tmS, self, n_self, self_cs, h, w, c, BX, BY) ||
-        !encode_features(&plan.tmO, other, n_other, other_cs, h, w, c, BX + 2 * r, BY + 2 * r)) {
+    if (!encode_features(&plan.tmS, self, n_self, self_cs, h, w, c, BX, BY, f8) ||
+        !encode_features(&plan.tmO, other, n_other, other_cs, h, w, c, BX + 2 * r, BY + 2 * r, f8)) {
         why = "tensor map encoding failed";
         return false;
     }
@@ -241,17 +271,19 @@ bool tc_plan_corr(CorrTcPlan &plan, const void *self, int n_self, int self_cs, c
     plan.w = w;
     plan.c = c;
     plan.r = r;
-    plan.nch = (c + BK - 1) / BK;
+    plan.nch = f8 ? 1 : (c + BK - 1) / BK;
+    plan.f8 = f8;
     plan.err = err;
     plan.enabled = true;
     return true;
 }
 
-cudaError_t launch_corr_tc(const CorrTcPlan &plan, int nb, const int img_self[2], const int img_other[2],
-                           __nv_bfloat16 *out, int out_cs, const __nv_bfloat16 *const fs[2],
-                           __nv_bfloat16 *self_copy, cudaStream_t st) {
+cudaError_t launch_corr_tc(const CorrTcPlan &plan, int nb, const int img_self[2], const int img_other[2], void *out,
+                           int out_cs, const void *const fs[2], void *self_copy, cudaStream_t st, float feat_scale,
+                           float q_out) {
     if (!plan.enabled || nb < 1 || nb > 2) return cudaErrorInvalidValue;
-    if (self_copy && (out_cs % 8 != 0 || reinterpret_cast<uintptr_t>(self_copy) % 16 != 0 || !fs ||
+    const int esz = plan.f8 ? 1 : 2;
+    if (self_copy && ((out_cs * esz) % 16 != 0 || reinterpret_cast<uintptr_t>(self_copy) % 16 != 0 || !fs ||
                       reinterpret_cast<uintptr_t>(fs[0]) % 16 || reinterpret_cast<uintptr_t>(fs[nb - 1]) % 16))
         return cudaErrorInvalidValue;
     CorrTcLaunch lp{};
@@ -265,16 +297,26 @@ cudaError_t launch_corr_tc(const CorrTcPlan &plan, int nb, const int img_self[2]
     }
     lp.out = out;
     lp.out_cs = out_cs;
-    lp.vec_out = (out_cs % 8 == 0 && reinterpret_cast<uintptr_t>(out) % 16 == 0) ? 1 : 0;
+    lp.vec_out = ((out_cs * esz) % 16 == 0 && reinterpret_cast<uintptr_t>(out) % 16 == 0) ? 1 : 0;
     lp.c = plan.c;
     lp.self_copy = self_copy;
-    lp.inv_c = 1.f / (float)plan.c;
+    lp.scale = feat_scale * feat_scale / (float)plan.c;
+    lp.q_out = q_out;
     lp.err = plan.err;
+    if (plan.f8) {
+        switch (plan.r) {
+            case 1: return launch_r<1, true>(plan, lp, nb, st);
+            case 2: return launch_r<2, true>(plan, lp, nb, st);
+            case 3: return launch_r<3, true>(plan, lp, nb, st);
+            case 4: return launch_r<4, true>(plan, lp, nb, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (plan.r) {
-        case 1: return launch_r<1>(plan, lp, nb, st);
-        case 2: return launch_r<2>(plan, lp, nb, st);
-        case 3: return launch_r<3>(plan, lp, nb, st);
-        case 4: return launch_r<4>(plan, lp, nb, st);
+        case 1: return launch_r<1, false>(plan, lp, nb, st);
+        case 2: return launch_r<2, false>(plan, lp, nb, st);
+        case 3: return launch_r<3, false>(plan, lp, nb, st);
+        case 4: return launch_r<4, false>(plan, lp, nb, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -17,6 +17,7 @@ struct CorrTcPlan {
     CUtensorMap tmS;
     CUtensorMap tmO;
     int h = 0, w = 0, c = 0, r = 0, nch = 0;
+    bool f8 = false;  // e4m3 features (kind::f8f6f4)
     int *err = nullptr;  // device error word (not owned)
 };
 
@@ -24,16 +25,18 @@ struct CorrTcPlan {
 // self_cs) and of `other` (n_other images, pixel stride other_cs).  Returns false with `why`
 // when not eligible (c % 8 != 0, c > 128, r > 4, misaligned buffers).
 bool tc_plan_corr(CorrTcPlan &plan, const void *self, int n_self, int self_cs, const void *other, int n_other,
-                  int other_cs, int h, int w, int c, int r, int *err, std::string &why);
+                  int other_cs, int h, int w, int c, int r, int *err, std::string &why, bool f8 = false);
 
 // Launches the planned correlation for nb <= 2 batch entries: entry b correlates image
 // img_self[b] of the self buffer with image img_other[b] of the other buffer and writes
-// LeakyReLU(mean over channels) for the (2r+1)^2 displacements, bfloat16, to
+// LeakyReLU(mean over channels) for the (2r+1)^2 displacements, bfloat16 or e4m3, to
 // out + ((b h + y) w + x) out_cs + k.  If self_copy is set, it also copies the c self
 // features of pixel (b, y, x) (read from fs[b], [h][w][c]) to self_copy + ((b h + y) w + x)
 // out_cs.
-cudaError_t launch_corr_tc(const CorrTcPlan &plan, int nb, const int img_self[2], const int img_other[2],
-                           __nv_bfloat16 *out, int out_cs, const __nv_bfloat16 *const fs[2],
-                           __nv_bfloat16 *self_copy, cudaStream_t st);
+// For e4m3 features stored with scale feat_scale, the cost is feat_scale^2 / c times the
+// integer-grid dot product, stored e4m3 after multiplying by q_out (1 / its scale).
+cudaError_t launch_corr_tc(const CorrTcPlan &plan, int nb, const int img_self[2], const int img_other[2], void *out,
+                           int out_cs, const void *const fs[2], void *self_copy, cudaStream_t st,
+                           float feat_scale = 1.f, float q_out = 1.f);
 
 }  // namespace tc

@@ -112,12 +112,17 @@ static inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
 size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precision prec) {
     const int L = net.levels, D = (2 * net.radius + 1) * (2 * net.radius + 1), m = 1 << L;
-    const size_t es = prec == TC_FP32 ? 4 : 2;
+    const bool f8 = prec == TC_FP8_E4M3;
+    const size_t es = prec == TC_FP32 ? 4 : (f8 ? 1 : 2);
     const size_t Hp = (size_t)round_up(height, m), Wp = (size_t)round_up(width, m);
     const bool bf = prec != TC_FP32;
     auto al = [](size_t b) { return (b + 511) & ~(size_t)511; };  // allocation granularity
-    auto tcw = [&](int cin, int cout) { return bf ? al((size_t)9 * cout * round_up(cin, 64) * 2) : 0; };
-    size_t total = al(sizeof(int));
+    // packed tensor-core weights (bf16, or e4m3 plus one float scale per output channel)
+    auto tcw = [&](int cin, int cout) {
+        return !bf ? 0 : f8 ? al((size_t)9 * cout * round_up(cin, 128)) + al((size_t)cout * 4)
+                            : al((size_t)9 * cout * round_up(cin, 64) * 2);
+    };
+    size_t total = al(sizeof(int)) + al(sizeof(unsigned) * (3 * L + 6 * (L - 1)));  // error word, amax slots
     int prev = 3;
     for (int l = 1; l <= L; ++l) {
         const size_t h = Hp >> l, w = Wp >> l, px = h * w;
@@ -128,7 +133,7 @@ size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precisi
         total += 2 * tcw(c, c);
         prev = c;
         if (l < 2) continue;
-        const int x0p = round_up(c + D + 2, 8);
+        const int x0p = round_up(c + D + 2, f8 ? 16 : 8);
         const int ctot = x0p + net.dec[0] + net.dec[1] + net.dec[2] + net.dec[3];
         total += al(2 * px * ctot * es) + al(2 * px * c * es) + 2 * al(2 * px * 2 * 4);
         const int cin[5] = {x0p, net.dec[0], net.dec[1], net.dec[1] + net.dec[2], net.dec[2] + net.dec[3]};
@@ -175,6 +180,10 @@ struct LevelBufs {
     float *head_w = nullptr, *head_b = nullptr;
     TcConvPlan tcplan[4];
     TcConvPlan headplan;
+    // activation scales (e4m3 streams; 1 otherwise): pyramid conv a/b/c outputs, and the
+    // estimator segments cost volume, up-flow, x1..x4.  q = 1 / s.
+    float s_pyr[3] = {1.f, 1.f, 1.f}, q_pyr[3] = {1.f, 1.f, 1.f};
+    float s_est[6] = {1.f, 1.f, 1.f, 1.f, 1.f, 1.f}, q_est[6] = {1.f, 1.f, 1.f, 1.f, 1.f, 1.f};
     CorrTcPlan corrplan;   // BF16: self = pyramid slots, other = pyramid (coarsest) or f2w
 };
 
@@ -203,6 +212,21 @@ struct tc_stream {
     int tc_layers = 0;          // convolution layers planned on the tensor cores
     int tc_corr_levels = 0;     // pyramid levels whose correlation runs on the tensor cores
     size_t dev_bytes = 0;       // device bytes allocated by the stream itself
+    // Tensor-core layers with what planning them needs (planned at creation for BF16, when
+    // the activation scales arrive for E4M3).
+    struct LayerRec {
+        TcConvPlan *plan;
+        ConvArgs a;
+        int n_in;
+        std::vector<float> wk;      // [9 * cin][cout] in buffer channel order
+        std::vector<int> in_seg;    // activation segment of each input channel (-1: zero pad)
+        bool head;
+    };
+    std::vector<LayerRec> recs;
+    bool fp8_ready = false;
+    // amax of every activation segment (FP32 / BF16 streams, for E4M3 calibration)
+    bool rec_amax = false;
+    unsigned *amax_dev = nullptr;
     int launches = 0;
     std::string err;
     // per-stage timing (tc_set_profiling): events around every launch, folded lazily
@@ -327,12 +351,26 @@ extern "C" tc_status tc_set_consistency(tc_stream *s, const tc_consistency *p) {
     return TC_OK;
 }
 
-// Plans a BF16 layer on the tensor cores; layers that are not eligible keep the CUDA-core
-// kernel (plan disabled).
-static void plan_tc(tc_stream *s, TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vector<float> &wk) {
-    if (s->prec != TC_BF16) return;
-    std::string why;
-    if (tc_plan_conv(plan, a, n_in, wk, s->dev_err, why)) s->tc_layers += 1;
+// Activation segments: the outputs of pyramid conv a/b/c of level l, and the estimator
+// input segments of level l (cost volume, up-flow, x1, x2, x3, x4).  E4M3 scales and amax
+// records are indexed this way.
+static int seg_pyr(const tc_stream *s, int l, int j) { return 3 * (l - 1) + j; }
+static int seg_est(const tc_stream *s, int l, int k) { return 3 * s->L + 6 * (s->L - l) + k; }
+static int n_segments(const tc_stream *s) { return 3 * s->L + 6 * (s->L - 1); }
+
+// Records a tensor-core layer; BF16 layers are planned at once (layers that are not
+// eligible keep the CUDA-core kernel), E4M3 layers when the scales are set.
+static void add_layer(tc_stream *s, TcConvPlan &plan, const ConvArgs &a, int n_in, std::vector<float> wk,
+                      std::vector<int> in_seg, bool head) {
+    if (s->prec == TC_FP32) return;
+    if (s->prec == TC_BF16) {
+        std::string why;
+        const bool ok = head ? tc_plan_head(plan, a, n_in, wk, s->dev_err, why)
+                             : tc_plan_conv(plan, a, n_in, wk, s->dev_err, why);
+        if (ok) s->tc_layers += 1;
+        return;
+    }
+    s->recs.push_back(tc_stream::LayerRec{&plan, a, n_in, std::move(wk), std::move(in_seg), head});
 }
 
 template <typename T>
@@ -341,12 +379,15 @@ static tc_status build_stream(tc_stream *s) {
     const bool bf = s->prec != TC_FP32;
     const size_t es = sizeof(T);
     const int L = s->L, D = s->D;
+    const int cal = es == 1 ? 16 : 8;  // channel-offset alignment: 16 bytes
     s->lv.resize(L);
     s->pyr_w.assign(3 * L, nullptr);
     s->pyr_b.assign(3 * L, nullptr);
     tc_status r;
     if ((r = dalloc_t(s, &s->dev_err, sizeof(int))) != TC_OK) return r;
     TC_TRY(s, cudaMemset(s->dev_err, 0, sizeof(int)), "memset");
+    if ((r = dalloc_t(s, &s->amax_dev, sizeof(unsigned) * n_segments(s))) != TC_OK) return r;
+    TC_TRY(s, cudaMemset(s->amax_dev, 0, sizeof(unsigned) * n_segments(s)), "memset");
     for (int l = 1; l <= L; ++l) {
         LevelBufs &B = s->lv[l - 1];
         B.h = s->Hp >> l;
@@ -369,28 +410,27 @@ static tc_status build_stream(tc_stream *s) {
                         wk[(size_t)k * HL.cout + o] = v;
                     }
             } else {
-                wk = simt_weights(HL, iota_perm(HL.cin, HL.cin), bf);
+                wk = simt_weights(HL, iota_perm(HL.cin, HL.cin), s->prec == TC_BF16);
             }
             if ((r = upload(s, &s->pyr_w[3 * (l - 1) + j], wk)) != TC_OK) return r;
             if ((r = upload(s, &s->pyr_b[3 * (l - 1) + j], HL.b)) != TC_OK) return r;
             if (l == 1 && j == 0) continue;
             // Same arguments as run_pyramid builds; the first conv of a level reads both
             // slots of the previous level's pyramid buffer.
-            ConvArgs a{};
             if (j == 0) {
                 LevelBufs &P = s->lv[l - 2];
-                a = ConvArgs{P.pyr, P.c, 1, P.h, P.w, P.c, 2, B.h, B.w, nullptr, nullptr, B.c, B.tmpA, B.c, 1};
-                plan_tc(s, s->pyr_plan[l - 1][0], a, 2, wk);
+                ConvArgs a{P.pyr, P.c, 1, P.h, P.w, P.c, 2, B.h, B.w, nullptr, nullptr, B.c, B.tmpA, B.c, 1};
+                add_layer(s, s->pyr_plan[l - 1][0], a, 2, wk, std::vector<int>(P.c, seg_pyr(s, l - 1, 2)), false);
             } else {
-                a = ConvArgs{j == 1 ? B.tmpA : B.tmpB, B.c, 1, B.h, B.w, B.c, 1, B.h, B.w, nullptr, nullptr, B.c,
-                             B.tmpB, B.c, 1};
-                plan_tc(s, s->pyr_plan[l - 1][j], a, 1, wk);
+                ConvArgs a{j == 1 ? B.tmpA : B.tmpB, B.c, 1, B.h, B.w, B.c, 1, B.h, B.w, nullptr, nullptr, B.c,
+                           B.tmpB, B.c, 1};
+                add_layer(s, s->pyr_plan[l - 1][j], a, 1, wk, std::vector<int>(B.c, seg_pyr(s, l, j - 1)), false);
             }
         }
         if (l < 2) continue;
         // Estimator buffers: x0 = [self c | corr D | up 2 | zero pad] then x1..x4 (the file's
         // order cat(corr, self, up) is restored by permuting conv1's input channels).
-        B.x0p = round_up(B.c + D + 2, 8);
+        B.x0p = round_up(B.c + D + 2, cal);
         B.off_x1 = B.x0p;
         B.off_x2 = B.off_x1 + net.dec[0];
         B.off_x3 = B.off_x2 + net.dec[1];
@@ -404,29 +444,31 @@ static tc_status build_stream(tc_stream *s) {
         TC_TRY(s, cudaMemset(B.up, 0, 2 * px * 2 * sizeof(float)), "memset");
         const HostLayer *E = &net.layers[3 * L + 5 * (L - l)];
         // conv1 reads x0 (padded to x0p), conv2 x1, conv3 x2, conv4 [x2 | x3], head [x3 | x4].
-        std::vector<int> p1(B.x0p, -1);
-        for (int i = 0; i < B.c; ++i) p1[i] = D + i;          // self = file channels [D, D+c)
-        for (int i = 0; i < D; ++i) p1[B.c + i] = i;          // corr = file channels [0, D)
-        for (int i = 0; i < 2; ++i) p1[B.c + D + i] = D + B.c + i;  // up-flow
-        std::vector<int> p4(net.dec[1] + net.dec[2]);
-        for (int i = 0; i < net.dec[1]; ++i) p4[i] = net.dec[2] + i;          // x2 = file channels [dec2, dec2+dec1)
-        for (int i = 0; i < net.dec[2]; ++i) p4[net.dec[1] + i] = i;          // x3 = file channels [0, dec2)
-        std::vector<int> p5(net.dec[2] + net.dec[3]);
-        for (int i = 0; i < net.dec[2]; ++i) p5[i] = net.dec[3] + i;          // x3 = file channels [dec3, dec3+dec2)
-        for (int i = 0; i < net.dec[3]; ++i) p5[net.dec[2] + i] = i;          // x4 = file channels [0, dec3)
+        std::vector<int> p1(B.x0p, -1), g1(B.x0p, -1);
+        for (int i = 0; i < B.c; ++i) { p1[i] = D + i; g1[i] = seg_pyr(s, l, 2); }            // self
+        for (int i = 0; i < D; ++i) { p1[B.c + i] = i; g1[B.c + i] = seg_est(s, l, 0); }       // corr
+        for (int i = 0; i < 2; ++i) { p1[B.c + D + i] = D + B.c + i; g1[B.c + D + i] = seg_est(s, l, 1); }  // up
+        std::vector<int> p4(net.dec[1] + net.dec[2]), g4(net.dec[1] + net.dec[2]);
+        for (int i = 0; i < net.dec[1]; ++i) { p4[i] = net.dec[2] + i; g4[i] = seg_est(s, l, 3); }   // x2
+        for (int i = 0; i < net.dec[2]; ++i) { p4[net.dec[1] + i] = i; g4[net.dec[1] + i] = seg_est(s, l, 4); }  // x3
+        std::vector<int> p5(net.dec[2] + net.dec[3]), g5(net.dec[2] + net.dec[3]);
+        for (int i = 0; i < net.dec[2]; ++i) { p5[i] = net.dec[3] + i; g5[i] = seg_est(s, l, 4); }   // x3
+        for (int i = 0; i < net.dec[3]; ++i) { p5[net.dec[2] + i] = i; g5[net.dec[2] + i] = seg_est(s, l, 5); }  // x4
         const std::vector<int> perms[4] = {p1, iota_perm(E[1].cin, E[1].cin), iota_perm(E[2].cin, E[2].cin), p4};
+        const std::vector<int> segs[4] = {g1, std::vector<int>(E[1].cin, seg_est(s, l, 2)),
+                                          std::vector<int>(E[2].cin, seg_est(s, l, 3)), g4};
         const int in_off[4] = {0, B.off_x1, B.off_x2, B.off_x2};
         const int cin[4] = {B.x0p, net.dec[0], net.dec[1], net.dec[1] + net.dec[2]};
         for (int j = 0; j < 4; ++j) {
-            std::vector<float> wk = simt_weights(E[j], perms[j], bf);
+            std::vector<float> wk = simt_weights(E[j], perms[j], s->prec == TC_BF16);
             if ((r = upload(s, &B.wk[j], wk)) != TC_OK) return r;
             if ((r = upload(s, &B.bias[j], E[j].b)) != TC_OK) return r;
             T *dec = static_cast<T *>(B.dec);
             ConvArgs a{dec + in_off[j], B.ctot, 2, B.h, B.w, cin[j], 1, B.h, B.w, nullptr, nullptr, net.dec[j],
                        dec + B.off_x1, B.ctot, 1};
-            plan_tc(s, B.tcplan[j], a, 2, wk);
+            add_layer(s, B.tcplan[j], a, 2, wk, segs[j], false);
         }
-        std::vector<float> wk5 = simt_weights(E[4], p5, bf);
+        std::vector<float> wk5 = simt_weights(E[4], p5, s->prec == TC_BF16);
         if ((r = upload(s, &B.head_w, wk5)) != TC_OK) return r;
         if ((r = upload(s, &B.head_b, E[4].b)) != TC_OK) return r;
         if (s->prec == TC_BF16) {
@@ -436,12 +478,11 @@ static tc_status build_stream(tc_stream *s) {
             if (tc_plan_corr(B.corrplan, B.pyr, 2, B.c, other, 2, B.c, B.h, B.w, B.c, s->R, s->dev_err, why))
                 s->tc_corr_levels += 1;
         }
-        if (s->prec == TC_BF16) {
+        {
             T *dec = static_cast<T *>(B.dec);
             ConvArgs a{dec + B.off_x3, B.ctot, 2, B.h, B.w, net.dec[2] + net.dec[3], 1, B.h, B.w, nullptr, nullptr, 2,
                        nullptr, 2, 0};
-            std::string why;
-            if (tc_plan_head(B.headplan, a, 2, wk5, s->dev_err, why)) s->tc_layers += 1;
+            add_layer(s, B.headplan, a, 2, wk5, g5, true);
         }
     }
     const size_t img = (size_t)3 * s->H * s->W * sizeof(float);
@@ -456,9 +497,8 @@ static tc_status build_stream(tc_stream *s) {
 extern "C" tc_status tc_create_stream(const tc_stream_desc *desc, void *cuda_stream, tc_stream **out) {
     if (out) *out = nullptr;
     if (!desc || !out) return fail(nullptr, TC_ERR_INVALID_ARG, "tc_create_stream: NULL argument");
-    if (desc->precision != TC_FP32 && desc->precision != TC_BF16)
-        return fail(nullptr, desc->precision == TC_FP8_E4M3 ? TC_ERR_UNSUPPORTED : TC_ERR_INVALID_ARG,
-                    "tc_create_stream: precision must be TC_FP32 or TC_BF16");
+    if (desc->precision != TC_FP32 && desc->precision != TC_BF16 && desc->precision != TC_FP8_E4M3)
+        return fail(nullptr, TC_ERR_INVALID_ARG, "tc_create_stream: precision must be TC_FP32, TC_BF16 or TC_FP8_E4M3");
     std::unique_ptr<tc_stream> s(new (std::nothrow) tc_stream());
     if (!s) return fail(nullptr, TC_ERR_OOM, "tc_create_stream: host allocation failed");
     std::vector<uint8_t> blob;
@@ -492,7 +532,9 @@ extern "C" tc_status tc_create_stream(const tc_stream_desc *desc, void *cuda_str
     s->prec = desc->precision;
     s->st = static_cast<cudaStream_t>(cuda_stream);
     tc_default_consistency(&s->params);
-    tc_status r = s->prec == TC_FP32 ? build_stream<float>(s.get()) : build_stream<__nv_bfloat16>(s.get());
+    tc_status r = s->prec == TC_FP32   ? build_stream<float>(s.get())
+                  : s->prec == TC_BF16 ? build_stream<__nv_bfloat16>(s.get())
+                                       : build_stream<__nv_fp8_e4m3>(s.get());
     if (r != TC_OK) {
         std::string msg = s->err;
         free_all(s.get());
@@ -559,6 +601,8 @@ template <typename T>
 static tc_status conv_layer(tc_stream *s, const ConvArgs &a, const TcConvPlan *plan, int cat) {
     if (plan && plan->enabled) {
         TC_LAUNCH_CAT(s, cat, launch_conv_tc(*plan, a, s->st));
+    } else if constexpr (sizeof(T) == 1) {
+        return fail(s, TC_ERR_UNSUPPORTED, "e4m3 layer without a tensor-core plan");
     } else {
         TC_LAUNCH_CAT(s, cat, launch_conv_simt<T>(a, s->st));
     }
@@ -573,20 +617,20 @@ static tc_status run_pyramid(tc_stream *s, const float *img, int slot) {
         const size_t px = (size_t)B.h * B.w;
         T *dst = static_cast<T *>(B.pyr) + (size_t)slot * px * B.c;
         if (l == 1) {
-            ConvFirstArgs f{img, s->H, s->W, s->Hp, s->Wp, s->pyr_w[0], s->pyr_b[0], B.c, B.tmpA};
+            ConvFirstArgs f{img, s->H, s->W, s->Hp, s->Wp, s->pyr_w[0], s->pyr_b[0], B.c, B.tmpA, B.q_pyr[0]};
             TC_LAUNCH_CAT(s, TC_PROF_PYRAMID_CONV, launch_conv_first<T>(f, s->st));
         } else {
             LevelBufs &P = s->lv[l - 2];
             const T *src = static_cast<const T *>(P.pyr) + (size_t)slot * P.h * P.w * P.c;
             ConvArgs a{src, P.c, 1, P.h, P.w, P.c, 2, B.h, B.w, s->pyr_w[3 * (l - 1)], s->pyr_b[3 * (l - 1)],
-                       B.c, B.tmpA, B.c, 1};
+                       B.c, B.tmpA, B.c, 1, B.q_pyr[0]};
             if ((r = conv_layer<T>(s, a, &s->pyr_plan[l - 1][0], TC_PROF_PYRAMID_CONV)) != TC_OK) return r;
         }
         ConvArgs b{B.tmpA, B.c, 1, B.h, B.w, B.c, 1, B.h, B.w, s->pyr_w[3 * (l - 1) + 1], s->pyr_b[3 * (l - 1) + 1],
-                   B.c, B.tmpB, B.c, 1};
+                   B.c, B.tmpB, B.c, 1, B.q_pyr[1]};
         if ((r = conv_layer<T>(s, b, &s->pyr_plan[l - 1][1], TC_PROF_PYRAMID_CONV)) != TC_OK) return r;
         ConvArgs c{B.tmpB, B.c, 1, B.h, B.w, B.c, 1, B.h, B.w, s->pyr_w[3 * (l - 1) + 2], s->pyr_b[3 * (l - 1) + 2],
-                   B.c, dst, B.c, 1};
+                   B.c, dst, B.c, 1, B.q_pyr[2]};
         if ((r = conv_layer<T>(s, c, &s->pyr_plan[l - 1][2], TC_PROF_PYRAMID_CONV)) != TC_OK) return r;
     }
     return TC_OK;
@@ -612,7 +656,7 @@ static tc_status run_estimators(tc_stream *s, int slot_cur) {
             // x2 upsampling of the coarser flow fused into the feature warp; the up-flow also
             // lands in B.up (residual base) and in the estimator input.
             WarpArgs wa{{other_p[0], other_p[1]}, B.c, nullptr, 2, B.h, B.w, B.c, B.f2w, B.c,
-                        C.flow, B.up, dec + B.c + s->D, B.ctot};
+                        C.flow, B.up, dec + B.c + s->D, B.ctot, B.q_est[1]};
             TC_LAUNCH_CAT(s, TC_PROF_WARP, launch_warp<T>(wa, s->st));
             fo[0] = static_cast<T *>(B.f2w);
             fo[1] = static_cast<T *>(B.f2w) + px * B.c;
@@ -620,28 +664,31 @@ static tc_status run_estimators(tc_stream *s, int slot_cur) {
         if (B.corrplan.enabled) {
             const int img_s[2] = {slot_cur, slot_cur ^ 1};
             const int img_o[2] = {l < s->L ? 0 : slot_cur ^ 1, l < s->L ? 1 : slot_cur};
-            const __nv_bfloat16 *fs[2] = {reinterpret_cast<const __nv_bfloat16 *>(self_p[0]),
-                                          reinterpret_cast<const __nv_bfloat16 *>(self_p[1])};
+            const void *fs[2] = {self_p[0], self_p[1]};
             TC_LAUNCH_CAT(s, TC_PROF_CORRELATION,
-                          launch_corr_tc(B.corrplan, 2, img_s, img_o, reinterpret_cast<__nv_bfloat16 *>(dec + B.c),
-                                         B.ctot, fs, reinterpret_cast<__nv_bfloat16 *>(dec), s->st));
+                          launch_corr_tc(B.corrplan, 2, img_s, img_o, dec + B.c, B.ctot, fs, dec, s->st, B.s_pyr[2],
+                                         B.q_est[0]));
+        } else if constexpr (sizeof(T) == 1) {
+            return fail(s, TC_ERR_UNSUPPORTED, "e4m3 correlation without a tensor-core plan");
         } else {
             CorrArgs ca{{self_p[0], self_p[1]}, {fo[0], fo[1]}, B.c, fo_cs, 2, B.h, B.w, B.c, s->R, dec + B.c, B.ctot,
                         dec};
             TC_LAUNCH_CAT(s, TC_PROF_CORRELATION, launch_corr<T>(ca, s->st));
         }
-        ConvArgs c1{dec, B.ctot, 2, B.h, B.w, B.x0p, 1, B.h, B.w, B.wk[0], B.bias[0], net.dec[0], dec + B.off_x1, B.ctot, 1};
+        ConvArgs c1{dec, B.ctot, 2, B.h, B.w, B.x0p, 1, B.h, B.w, B.wk[0], B.bias[0], net.dec[0], dec + B.off_x1, B.ctot, 1, B.q_est[2]};
         if ((r = conv_layer<T>(s, c1, &B.tcplan[0], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
-        ConvArgs c2{dec + B.off_x1, B.ctot, 2, B.h, B.w, net.dec[0], 1, B.h, B.w, B.wk[1], B.bias[1], net.dec[1], dec + B.off_x2, B.ctot, 1};
+        ConvArgs c2{dec + B.off_x1, B.ctot, 2, B.h, B.w, net.dec[0], 1, B.h, B.w, B.wk[1], B.bias[1], net.dec[1], dec + B.off_x2, B.ctot, 1, B.q_est[3]};
         if ((r = conv_layer<T>(s, c2, &B.tcplan[1], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
-        ConvArgs c3{dec + B.off_x2, B.ctot, 2, B.h, B.w, net.dec[1], 1, B.h, B.w, B.wk[2], B.bias[2], net.dec[2], dec + B.off_x3, B.ctot, 1};
+        ConvArgs c3{dec + B.off_x2, B.ctot, 2, B.h, B.w, net.dec[1], 1, B.h, B.w, B.wk[2], B.bias[2], net.dec[2], dec + B.off_x3, B.ctot, 1, B.q_est[4]};
         if ((r = conv_layer<T>(s, c3, &B.tcplan[2], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
-        ConvArgs c4{dec + B.off_x2, B.ctot, 2, B.h, B.w, net.dec[1] + net.dec[2], 1, B.h, B.w, B.wk[3], B.bias[3], net.dec[3], dec + B.off_x4, B.ctot, 1};
+        ConvArgs c4{dec + B.off_x2, B.ctot, 2, B.h, B.w, net.dec[1] + net.dec[2], 1, B.h, B.w, B.wk[3], B.bias[3], net.dec[3], dec + B.off_x4, B.ctot, 1, B.q_est[5]};
         if ((r = conv_layer<T>(s, c4, &B.tcplan[3], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
         if (B.headplan.enabled) {
             ConvArgs a5{dec + B.off_x3, B.ctot, 2, B.h, B.w, net.dec[2] + net.dec[3], 1, B.h, B.w, B.head_w, B.head_b,
                         2, nullptr, 2, 0};
             TC_LAUNCH_CAT(s, TC_PROF_HEAD, launch_conv_tc_head(B.headplan, a5, l < s->L ? B.up : nullptr, B.flow, s->st));
+        } else if constexpr (sizeof(T) == 1) {
+            return fail(s, TC_ERR_UNSUPPORTED, "e4m3 flow head without a tensor-core plan");
         } else {
             HeadArgs ha{dec + B.off_x3, B.ctot, net.dec[2] + net.dec[3], 2, B.h, B.w, B.head_w, B.head_b,
                         l < s->L ? B.up : nullptr, B.flow};
@@ -744,6 +791,32 @@ static tc_status capture_frame(tc_stream *s, const float *I, const float *P, flo
     return TC_OK;
 }
 
+static void release_graphs(tc_stream *s);
+
+// Folds the amax of every activation segment of the frame just launched into amax_dev.
+template <typename T>
+static tc_status record_amax(tc_stream *s, int cur) {
+    if constexpr (sizeof(T) == 1) {
+        return fail(s, TC_ERR_INVALID_ARG, "amax recording needs a TC_FP32 or TC_BF16 stream");
+    } else {
+        for (int l = 1; l <= s->L; ++l) {
+            LevelBufs &B = s->lv[l - 1];
+            const size_t px = (size_t)B.h * B.w;
+            const T *pyr = static_cast<const T *>(B.pyr) + (size_t)cur * px * B.c;
+            TC_LAUNCH(s, launch_amax<T>(static_cast<const T *>(B.tmpA), px, B.c, B.c, s->amax_dev + seg_pyr(s, l, 0), s->st));
+            TC_LAUNCH(s, launch_amax<T>(static_cast<const T *>(B.tmpB), px, B.c, B.c, s->amax_dev + seg_pyr(s, l, 1), s->st));
+            TC_LAUNCH(s, launch_amax<T>(pyr, px, B.c, B.c, s->amax_dev + seg_pyr(s, l, 2), s->st));
+            if (l < 2 || s->t == 0) continue;
+            const T *dec = static_cast<const T *>(B.dec);
+            const int off[6] = {B.c, B.c + s->D, B.off_x1, B.off_x2, B.off_x3, B.off_x4};
+            const int nc[6] = {s->D, 2, s->net.dec[0], s->net.dec[1], s->net.dec[2], s->net.dec[3]};
+            for (int k = 0; k < 6; ++k)
+                TC_LAUNCH(s, launch_amax<T>(dec + off[k], 2 * px, B.ctot, nc[k], s->amax_dev + seg_est(s, l, k), s->st));
+        }
+        return TC_OK;
+    }
+}
+
 template <typename T>
 static tc_status process(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask) {
     tc_status r;
@@ -752,8 +825,9 @@ static tc_status process(tc_stream *s, const float *I, const float *P, float *O,
     const int cur = (int)(s->t & 1);
     // The first two frames run eagerly (the first has no flow; the second sets every kernel
     // attribute); later frames replay the graph of their parity.  Profiling runs eagerly.
-    if (!s->graphs || s->prof || s->t < 2) {
+    if (!s->graphs || s->prof || s->t < 2 || s->rec_amax) {
         if ((r = frame_launches<T>(s, I, P, O, wc, mask, cur)) != TC_OK) return r;
+        if (s->rec_amax && (r = record_amax<T>(s, cur)) != TC_OK) return r;
         s->t += 1;
         return TC_OK;
     }
@@ -766,7 +840,8 @@ static tc_status process(tc_stream *s, const float *I, const float *P, float *O,
     if (!G.exec) {
         if ((r = capture_frame<T>(s, I, P, O, wc, mask, cur)) != TC_OK) return r;
     } else {
-        ConvFirstArgs f{I, s->H, s->W, s->Hp, s->Wp, s->pyr_w[0], s->pyr_b[0], s->lv[0].c, s->lv[0].tmpA};
+        ConvFirstArgs f{I, s->H, s->W, s->Hp, s->Wp, s->pyr_w[0], s->pyr_b[0], s->lv[0].c, s->lv[0].tmpA,
+                        s->lv[0].q_pyr[0]};
         ConsistArgs ca = consist_args(s, I, P, O, wc, mask, cur);
         void *fa[1] = {&f};
         void *cargs[1] = {&ca};
@@ -808,6 +883,85 @@ static void release_graph_stream(tc_stream *s) {
     s->ev_in = s->ev_out = nullptr;
 }
 
+extern "C" int tc_activation_segments(const tc_stream *s) { return s ? n_segments(s) : 0; }
+
+extern "C" tc_status tc_set_amax_recording(tc_stream *s, int enable) {
+    tc_status r = check_stream(s, "tc_set_amax_recording");
+    if (r != TC_OK) return r;
+    if (s->prec == TC_FP8_E4M3) return fail(s, TC_ERR_INVALID_ARG, "amax recording needs a TC_FP32 or TC_BF16 stream");
+    TC_TRY(s, cudaMemsetAsync(s->amax_dev, 0, sizeof(unsigned) * n_segments(s), s->st), "memset");
+    s->rec_amax = enable != 0;
+    return TC_OK;
+}
+
+extern "C" tc_status tc_get_amax(tc_stream *s, float *amax, int n) {
+    tc_status r = check_stream(s, "tc_get_amax");
+    if (r != TC_OK) return r;
+    if (!amax || n < n_segments(s)) return fail(s, TC_ERR_INVALID_ARG, "tc_get_amax: need tc_activation_segments() floats");
+    std::vector<unsigned> bits(n_segments(s));
+    TC_TRY(s, cudaStreamSynchronize(s->st), "stream synchronize");
+    TC_TRY(s, cudaMemcpy(bits.data(), s->amax_dev, bits.size() * sizeof(unsigned), cudaMemcpyDeviceToHost), "amax read");
+    for (size_t i = 0; i < bits.size(); ++i) memcpy(&amax[i], &bits[i], sizeof(float));
+    return TC_OK;
+}
+
+extern "C" tc_status tc_set_fp8_scales(tc_stream *s, const float *scales, int n) {
+    tc_status r = check_stream(s, "tc_set_fp8_scales");
+    if (r != TC_OK) return r;
+    if (s->prec != TC_FP8_E4M3) return fail(s, TC_ERR_INVALID_ARG, "tc_set_fp8_scales: not a TC_FP8_E4M3 stream");
+    if (!scales || n != n_segments(s)) return fail(s, TC_ERR_INVALID_ARG, "tc_set_fp8_scales: need tc_activation_segments() scales");
+    std::vector<float> sc(scales, scales + n);
+    for (float &v : sc) {
+        if (!std::isfinite(v) || v < 0.f) return fail(s, TC_ERR_INVALID_ARG, "tc_set_fp8_scales: scales must be finite and >= 0");
+        if (v == 0.f) v = 1.f;  // a segment that is always zero
+    }
+    TC_TRY(s, cudaStreamSynchronize(s->st), "stream synchronize");
+    release_graphs(s);
+    for (auto &rec : s->recs) rec.plan->release();
+    for (auto &B : s->lv) B.corrplan.enabled = false;
+    s->tc_layers = 0;
+    s->tc_corr_levels = 0;
+    s->fp8_ready = false;
+    for (int l = 1; l <= s->L; ++l) {
+        LevelBufs &B = s->lv[l - 1];
+        for (int j = 0; j < 3; ++j) {
+            B.s_pyr[j] = sc[seg_pyr(s, l, j)];
+            B.q_pyr[j] = 1.f / B.s_pyr[j];
+        }
+        if (l < 2) continue;
+        for (int k = 0; k < 6; ++k) {
+            B.s_est[k] = sc[seg_est(s, l, k)];
+            B.q_est[k] = 1.f / B.s_est[k];
+        }
+    }
+    // Fold each input channel's activation scale into the weights: the MMA then sees the
+    // stored e4m3 codes, and each output channel needs only its weight scale.
+    for (auto &rec : s->recs) {
+        std::vector<float> wk = rec.wk;
+        const int cin = rec.a.cin, cout = rec.head ? 2 : rec.a.cout;
+        for (int tap = 0; tap < 9; ++tap)
+            for (int c = 0; c < cin; ++c) {
+                const float f = rec.in_seg[c] >= 0 ? sc[rec.in_seg[c]] : 0.f;
+                for (int o = 0; o < cout; ++o) wk[((size_t)tap * cin + c) * cout + o] *= f;
+            }
+        std::string why;
+        const bool ok = rec.head ? tc_plan_head(*rec.plan, rec.a, rec.n_in, wk, s->dev_err, why, true)
+                                 : tc_plan_conv(*rec.plan, rec.a, rec.n_in, wk, s->dev_err, why, true);
+        if (!ok) return fail(s, TC_ERR_UNSUPPORTED, "e4m3 layer not eligible for the tensor cores: " + why);
+        s->tc_layers += 1;
+    }
+    for (int l = 2; l <= s->L; ++l) {
+        LevelBufs &B = s->lv[l - 1];
+        std::string why;
+        const void *other = l == s->L ? B.pyr : B.f2w;
+        if (!tc_plan_corr(B.corrplan, B.pyr, 2, B.c, other, 2, B.c, B.h, B.w, B.c, s->R, s->dev_err, why, true))
+            return fail(s, TC_ERR_UNSUPPORTED, "e4m3 correlation not eligible for the tensor cores: " + why);
+        s->tc_corr_levels += 1;
+    }
+    s->fp8_ready = true;
+    return TC_OK;
+}
+
 extern "C" tc_status tc_set_graphs(tc_stream *s, int enable) {
     tc_status r = check_stream(s, "tc_set_graphs");
     if (r != TC_OK) return r;
@@ -822,8 +976,11 @@ extern "C" tc_status tc_process_frame(tc_stream *s, const float *I_t, const floa
     tc_status r = check_stream(s, "tc_process_frame");
     if (r != TC_OK) return r;
     if (!I_t || !P_t || !O_t) return fail(s, TC_ERR_INVALID_ARG, "tc_process_frame: NULL image pointer");
-    return s->prec == TC_FP32 ? process<float>(s, I_t, P_t, O_t, wc_opt, mask_opt)
-                              : process<__nv_bfloat16>(s, I_t, P_t, O_t, wc_opt, mask_opt);
+    if (s->prec == TC_FP32) return process<float>(s, I_t, P_t, O_t, wc_opt, mask_opt);
+    if (s->prec == TC_BF16) return process<__nv_bfloat16>(s, I_t, P_t, O_t, wc_opt, mask_opt);
+    if (!s->fp8_ready)
+        return fail(s, TC_ERR_STATE, "tc_process_frame: an e4m3 stream needs tc_set_fp8_scales before its first frame");
+    return process<__nv_fp8_e4m3>(s, I_t, P_t, O_t, wc_opt, mask_opt);
 }
 
 // Reads the stream's device error word (after the stream has been synchronised).
@@ -970,10 +1127,11 @@ static tc_status op_conv(const float *in, int n, int h, int w, int cin, const fl
     L.w.assign(w_oihw, w_oihw + (size_t)cout * cin * 9);
     L.b.assign(bias, bias + cout);
     const bool bf = sizeof(T) == 2;
-    const int cin_p = round_up(cin, bf ? 8 : 4), cout_p = round_up(cout, 4);
+    constexpr bool f8 = sizeof(T) == 1;  // e4m3 activations with scale 1; tensor cores only
+    const int cin_p = round_up(cin, f8 ? 16 : (bf ? 8 : 4)), cout_p = round_up(cout, f8 ? 16 : 4);
     const int ho = (h - 1) / stride + 1, wo = (w - 1) / stride + 1;
     std::vector<float> wk = simt_weights(L, iota_perm(cin, cin_p), bf);
-    // pad cout to a multiple of 4
+    // pad cout to a multiple of 4 (16 for e4m3)
     std::vector<float> wkp((size_t)9 * cin_p * cout_p, 0.f), bp(cout_p, 0.f);
     for (size_t k = 0; k < (size_t)9 * cin_p; ++k)
         for (int o = 0; o < cout; ++o) wkp[k * cout_p + o] = wk[k * cout + o];
@@ -1000,19 +1158,21 @@ static tc_status op_conv(const float *in, int n, int h, int w, int cin, const fl
                "tc_op_conv3x3 repack");
         OP_TRY(launch_to_act<T>(tmpf, nin, din, st), "tc_op_conv3x3 convert");
     }
-    ConvArgs a{din, cin_p, n, h, w, cin_p, stride, ho, wo, dw, db, cout_p, dout, cout_p, leaky};
+    ConvArgs a{din, cin_p, n, h, w, cin_p, stride, ho, wo, dw, db, cout_p, dout, cout_p, leaky, 1.f};
     TcConvPlan plan;
     int *derr = nullptr;
     OP_TRY(tmp.get((void **)&derr, sizeof(int)), "tc_op_conv3x3 alloc");
     OP_TRY(cudaMemsetAsync(derr, 0, sizeof(int), st), "tc_op_conv3x3 memset");
     std::string why;
-    const bool use_tc = bf && tc_plan_conv(plan, a, n, wkp, derr, why);
+    const bool use_tc = (bf || f8) && tc_plan_conv(plan, a, n, wkp, derr, why, f8);
     if (use_tc) {
         cudaError_t e = launch_conv_tc(plan, a, st);
         if (e != cudaSuccess) {
             plan.release();
             return cuda_fail(nullptr, e, "tc_op_conv3x3 tensor-core launch");
         }
+    } else if constexpr (f8) {
+        return fail(nullptr, TC_ERR_UNSUPPORTED, "tc_op_conv3x3: e4m3 runs on the tensor cores only: " + why);
     } else {
         OP_TRY(launch_conv_simt<T>(a, st), "tc_op_conv3x3 launch");
     }
@@ -1046,7 +1206,9 @@ extern "C" tc_status tc_op_conv3x3(tc_precision precision, const float *in, int 
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (precision == TC_FP32) return op_conv<float>(in, n, h, w, cin, w_oihw, bias, cout, stride, leaky, out, st);
     if (precision == TC_BF16) return op_conv<__nv_bfloat16>(in, n, h, w, cin, w_oihw, bias, cout, stride, leaky, out, st);
-    return fail(nullptr, TC_ERR_UNSUPPORTED, "tc_op_conv3x3: precision");
+    if (precision == TC_FP8_E4M3)
+        return op_conv<__nv_fp8_e4m3>(in, n, h, w, cin, w_oihw, bias, cout, stride, leaky, out, st);
+    return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_conv3x3: precision");
 }
 
 template <typename T>
@@ -1067,15 +1229,17 @@ static tc_status op_corr(const float *f1, const float *f2, int n, int h, int w, 
     OP_TRY(tmp.get((void **)&derr, sizeof(int)), "tc_op_correlation alloc");
     OP_TRY(cudaMemsetAsync(derr, 0, sizeof(int), st), "tc_op_correlation memset");
     std::string why;
-    const bool use_tc = sizeof(T) == 2 && tc_plan_corr(plan, a, n, c, b, n, c, h, w, c, r, derr, why);
+    constexpr bool f8 = sizeof(T) == 1;  // e4m3 features and cost volume with scale 1
+    const bool use_tc = (sizeof(T) == 2 || f8) && tc_plan_corr(plan, a, n, c, b, n, c, h, w, c, r, derr, why, f8);
+    if (f8 && !use_tc)
+        return fail(nullptr, TC_ERR_UNSUPPORTED, "tc_op_correlation: e4m3 runs on the tensor cores only: " + why);
     for (int i = 0; i < n; i += 2) {
         const int nb = n - i < 2 ? n - i : 2;
         if (use_tc) {
             const int imgs[2] = {i, i + nb - 1};
-            OP_TRY(launch_corr_tc(plan, nb, imgs, imgs, reinterpret_cast<__nv_bfloat16 *>(o + (size_t)i * h * w * D), D,
-                                  nullptr, nullptr, st),
+            OP_TRY(launch_corr_tc(plan, nb, imgs, imgs, o + (size_t)i * h * w * D, D, nullptr, nullptr, st),
                    "tc_op_correlation tensor-core launch");
-        } else {
+        } else if constexpr (!f8) {
             CorrArgs ca{{a + i * img, a + (i + nb - 1) * img}, {b + i * img, b + (i + nb - 1) * img}, c, c, nb, h, w, c,
                         r, o + (size_t)i * h * w * D, D, nullptr};
             OP_TRY(launch_corr<T>(ca, st), "tc_op_correlation launch");
@@ -1097,7 +1261,8 @@ extern "C" tc_status tc_op_correlation(tc_precision precision, const float *f1, 
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (precision == TC_FP32) return op_corr<float>(f1, f2, n, h, w, c, r, out, st);
     if (precision == TC_BF16) return op_corr<__nv_bfloat16>(f1, f2, n, h, w, c, r, out, st);
-    return fail(nullptr, TC_ERR_UNSUPPORTED, "tc_op_correlation: precision");
+    if (precision == TC_FP8_E4M3) return op_corr<__nv_fp8_e4m3>(f1, f2, n, h, w, c, r, out, st);
+    return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_correlation: precision");
 }
 
 template <typename T>
@@ -1112,7 +1277,7 @@ static tc_status op_warp(const float *f, const float *flow, int n, int h, int w,
     for (int i = 0; i < n; i += 2) {
         const int nb = n - i < 2 ? n - i : 2;
         WarpArgs wa{{a + i * img, a + (i + nb - 1) * img}, c, flow + (size_t)i * h * w * 2, nb, h, w, c, o + i * img, c,
-                    nullptr, nullptr, nullptr, 0};
+                    nullptr, nullptr, nullptr, 0, 1.f};
         OP_TRY(launch_warp<T>(wa, st), "tc_op_warp_features launch");
     }
     OP_TRY(launch_from_act<T>(o, nf, out, st), "tc_op_warp_features convert");
@@ -1127,7 +1292,8 @@ extern "C" tc_status tc_op_warp_features(tc_precision precision, const float *f,
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (precision == TC_FP32) return op_warp<float>(f, flow, n, h, w, c, out, st);
     if (precision == TC_BF16) return op_warp<__nv_bfloat16>(f, flow, n, h, w, c, out, st);
-    return fail(nullptr, TC_ERR_UNSUPPORTED, "tc_op_warp_features: precision");
+    if (precision == TC_FP8_E4M3) return op_warp<__nv_fp8_e4m3>(f, flow, n, h, w, c, out, st);
+    return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_warp_features: precision");
 }
 
 extern "C" tc_status tc_op_upsample_flow(const float *flow, int n, int h, int w, int s, float *out, void *cuda_stream) {

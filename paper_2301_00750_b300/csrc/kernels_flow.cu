@@ -167,7 +167,8 @@ __global__ void __launch_bounds__(256) conv_first_kernel(ConvFirstArgs a) {
             acc.z = fmaf(w.z, v[k], acc.z);
             acc.w = fmaf(w.w, v[k], acc.w);
         }
-        st4(out + o, make_float4(lrelu(acc.x), lrelu(acc.y), lrelu(acc.z), lrelu(acc.w)));
+        st4(out + o, make_float4(lrelu(acc.x) * a.q_out, lrelu(acc.y) * a.q_out, lrelu(acc.z) * a.q_out,
+                                 lrelu(acc.w) * a.q_out));
     }
 }
 
@@ -345,8 +346,8 @@ __global__ void __launch_bounds__(256) warp_kernel(WarpArgs a) {
             reinterpret_cast<float2 *>(a.up_out)[p] = fl;
             if (a.act) {
                 T *dst = static_cast<T *>(a.act) + p * a.act_cs;
-                dst[0] = from_f<T>(fl.x);
-                dst[1] = from_f<T>(fl.y);
+                dst[0] = from_f<T>(fl.x * a.act_q);
+                dst[1] = from_f<T>(fl.y * a.act_q);
             }
         }
     } else {
@@ -450,5 +451,41 @@ cudaError_t launch_from_act(const T *in, size_t n, float *out, cudaStream_t st) 
 TC_INST(float)
 TC_INST(__nv_bfloat16)
 #undef TC_INST
+
+// =====================================================================================
+// amax of a channel window of an NHWC activation buffer, folded into *slot with an atomic
+// max on the float's bit pattern (values are >= 0, so their bit patterns order like them).
+// =====================================================================================
+template <typename T>
+__global__ void __launch_bounds__(256) amax_kernel(const T *base, size_t npix, int cs, int nc, unsigned *slot) {
+    float m = 0.f;
+    const size_t n = npix * (size_t)nc;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t p = i / nc;
+        const int c = (int)(i - p * nc);
+        m = fmaxf(m, fabsf(to_f(base[p * cs + c])));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(slot, __float_as_uint(m));
+}
+
+template <typename T>
+cudaError_t launch_amax(const T *base, size_t npix, int cs, int nc, unsigned *slot, cudaStream_t st) {
+    const size_t n = npix * (size_t)nc;
+    if (n == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((n + 255) / 256 < 1184 ? (n + 255) / 256 : 1184);
+    amax_kernel<T><<<blocks, 256, 0, st>>>(base, npix, cs, nc, slot);
+    return cudaGetLastError();
+}
+template cudaError_t launch_amax<float>(const float *, size_t, int, int, unsigned *, cudaStream_t);
+template cudaError_t launch_amax<__nv_bfloat16>(const __nv_bfloat16 *, size_t, int, int, unsigned *, cudaStream_t);
+
+// E4M3 activations: only the kernels an E4M3 stream runs outside the tensor cores.
+template cudaError_t launch_conv_first<__nv_fp8_e4m3>(const ConvFirstArgs &, cudaStream_t);
+template const void *conv_first_kernel_fn<__nv_fp8_e4m3>();
+template cudaError_t launch_warp<__nv_fp8_e4m3>(const WarpArgs &, cudaStream_t);
+template cudaError_t launch_to_act<__nv_fp8_e4m3>(const float *, size_t, __nv_fp8_e4m3 *, cudaStream_t);
+template cudaError_t launch_from_act<__nv_fp8_e4m3>(const __nv_fp8_e4m3 *, size_t, float *, cudaStream_t);
 
 }  // namespace tc

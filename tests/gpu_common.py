@@ -51,3 +51,10 @@ def bf16_round(a):
     u = a.view(np.uint32).astype(np.uint64)
     r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
     return r.astype(np.uint32).view(np.float32)
+
+
+def weight_scales_e4m3(w):
+    """Per-output-channel E4M3 weight scales amax / 448 computed in float32, as a layer's
+    planning does (w: (cout, cin, 3, 3) float32)."""
+    a = np.abs(np.asarray(w, np.float32)).reshape(w.shape[0], -1).max(1)
+    return np.where(a > 0, a / np.float32(448), np.float32(1)).astype(np.float32)

@@ -75,8 +75,8 @@ def test_create_stream_rejects_bad_arguments(lib, tmp_path):
         lib.Stream(4, 64, "fp32", weights_path=str(good))      # smaller than 2^levels
     assert e.value.status == lib.TC_ERR_INVALID_ARG
     with pytest.raises(lib.TcError) as e:
-        lib.Stream(64, 64, "fp8", weights_path=str(good))
-    assert e.value.status == lib.TC_ERR_UNSUPPORTED
+        lib.Stream(64, 64, 7, weights_path=str(good))           # not a tc_precision
+    assert e.value.status == lib.TC_ERR_INVALID_ARG
     with pytest.raises(lib.TcError) as e:
         lib.Stream(64, 64, "fp32")                                # no weights
     assert e.value.status == lib.TC_ERR_INVALID_ARG
