@@ -69,6 +69,7 @@ struct ConvArgs {
     int out_cs;
     int leaky;
     float q_out;  // e4m3 outputs: 1 / output activation scale (unused otherwise)
+    int accumulate;  // CUDA-core kernel only: add to the output instead of overwriting it
 };
 
 // First pyramid conv: planar float image (3, H, W), edge-replicated to (Hp, Wp) and
@@ -102,6 +103,9 @@ struct CorrArgs {
     void *out;        // [n][h][w][out_cs], correlation at channel 0
     int out_cs;
     void *self_copy;  // same buffer at channel offset D (or NULL)
+    // CUDA-core kernel only: when set, batch entry b reads fs[0] + b * fs_img and
+    // fo[0] + b * fo_img (elements) instead of the per-entry pointers (any n)
+    size_t fs_img, fo_img;
 };
 
 struct WarpArgs {
@@ -119,6 +123,7 @@ struct WarpArgs {
     void *act;
     int act_cs;
     float act_q;  // the up-flow is multiplied by act_q before the activation store (1 unless e4m3)
+    size_t f_img;  // when set, batch entry b reads f[0] + b * f_img (elements; any n)
 };
 
 struct UpArgs {

@@ -114,6 +114,10 @@ __global__ void __launch_bounds__(256) conv_simt_kernel(ConvArgs a) {
         if (m >= M) continue;
         float4 v = make_float4(acc[i][0] + bias.x, acc[i][1] + bias.y, acc[i][2] + bias.z, acc[i][3] + bias.w);
         if (a.leaky) v = make_float4(lrelu(v.x), lrelu(v.y), lrelu(v.z), lrelu(v.w));
+        if (a.accumulate) {
+            const float4 o = ld4(out + (size_t)m * a.out_cs + nb);
+            v = make_float4(v.x + o.x, v.y + o.y, v.z + o.z, v.w + o.w);
+        }
         st4(out + (size_t)m * a.out_cs + nb, v);
     }
 }
@@ -247,8 +251,8 @@ __global__ void __launch_bounds__(256) corr_kernel(CorrArgs a) {
     const int x0 = blockIdx.x * CT, y0 = blockIdx.y * CT;
     const int x = x0 + tx, y = y0 + ty;
     const bool valid = x < a.w && y < a.h;
-    const T *fs = static_cast<const T *>(a.fs[b]);
-    const T *fo = static_cast<const T *>(a.fo[b]);
+    const T *fs = a.fs_img ? static_cast<const T *>(a.fs[0]) + b * a.fs_img : static_cast<const T *>(a.fs[b]);
+    const T *fo = a.fo_img ? static_cast<const T *>(a.fo[0]) + b * a.fo_img : static_cast<const T *>(a.fo[b]);
     float acc[ND];
 #pragma unroll
     for (int k = 0; k < ND; ++k) acc[k] = 0.f;
@@ -357,7 +361,7 @@ __global__ void __launch_bounds__(256) warp_kernel(WarpArgs a) {
     const float fu = floorf(u), fv = floorf(v);
     const float ax = u - fu, ay = v - fv;
     const int xa = x + (int)fu, ya = y + (int)fv;
-    const T *f = static_cast<const T *>(a.f[b]);
+    const T *f = a.f_img ? static_cast<const T *>(a.f[0]) + b * a.f_img : static_cast<const T *>(a.f[b]);
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy) {

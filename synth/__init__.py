@@ -20,6 +20,9 @@ Workloads (all seeded with NumPy's PCG64):
   and forward flows are analytic.
 * stylised frames ``P_t = M_t I_t + N(0, 0.02)`` with a per-frame colour matrix
   ``M_t = I + U(-0.1, 0.1)^{3x3}``.
+* ``training_pair``: a 256x256 pair (a, b) with known flow F = F_{a->b}: b is blurred noise,
+  a samples b at ``x + F(x)`` (F a smooth random field, max |F| <= 16 px), and 0-3 textured
+  rectangles sit at q in a and at q + d in b (F = d on them), occluding the background.
 * He-normal weights for the lite flow network, written to a flat weight file.
 """
 from __future__ import annotations
@@ -33,7 +36,8 @@ from scipy import ndimage
 
 __all__ = [
     "rng", "blurred_noise", "smooth_flow", "resample", "stylize", "pair64", "Sequence",
-    "NetSpec", "he_weights", "write_weights", "layer_names", "random_lowres_flow",
+    "NetSpec", "he_weights", "write_weights", "layer_names", "random_lowres_flow", "training_pair",
+    "training_batch",
 ]
 
 
@@ -97,6 +101,39 @@ def pair64(seed: int = 0, size: int = 64, max_flow: float = 4.0):
     p0 = stylize(i0, g2)
     p1 = stylize(i1, g2)
     return dict(I0=i0, I1=i1, P0=p0, P1=p1, flow_gt=flow)
+
+
+def training_pair(seed: int, size: int = 256, max_flow: float = 16.0, max_rects: int = 3):
+    """(a, b, F) with a(x) = b(x + F(x)) on the background and on each rectangle: (3,s,s),
+    (3,s,s), (2,s,s) float32, F in pixels (u, v).  Rectangles moving by d cover q + [0, side)
+    in a and q + d + [0, side) in b; what they cover in b, and what they uncover, has no
+    match (occlusion)."""
+    g = rng(seed)
+    b = blurred_noise(size, size, 3, 2.0, g)
+    flow = smooth_flow(size, size, g.uniform(0.25, 1.0) * max_flow, g)
+    yy, xx = np.mgrid[0:size, 0:size].astype(np.float64)
+    a = resample(b, yy + flow[1], xx + flow[0])
+    lim = max_flow / math.sqrt(2.0)
+    for _ in range(int(g.integers(0, max_rects + 1))):
+        sw, sh = (int(v) for v in g.integers(size // 8, size // 3 + 1, 2))
+        qx, qy = int(g.integers(0, size - sw + 1)), int(g.integers(0, size - sh + 1))
+        dx, dy = g.uniform(-lim, lim, 2)
+        tex = blurred_noise(sh, sw, 3, 2.0, g)
+        a[:, qy:qy + sh, qx:qx + sw] = tex
+        flow[0, qy:qy + sh, qx:qx + sw] = dx
+        flow[1, qy:qy + sh, qx:qx + sw] = dy
+        ty, tx = yy - qy - dy, xx - qx - dx
+        inside = (ty >= 0) & (ty <= sh - 1) & (tx >= 0) & (tx <= sw - 1)
+        if inside.any():
+            vals = resample(tex, ty[inside], tx[inside])
+            b[:, inside] = vals
+    return a.astype(np.float32), b.astype(np.float32), flow.astype(np.float32)
+
+
+def training_batch(seed: int, n: int, size: int = 256, max_flow: float = 16.0):
+    """n pairs of ``training_pair`` with seeds seed, seed + 1, ...: (n,3,s,s) x 2, (n,2,s,s)."""
+    ps = [training_pair(seed + i, size, max_flow) for i in range(n)]
+    return (np.stack([p[0] for p in ps]), np.stack([p[1] for p in ps]), np.stack([p[2] for p in ps]))
 
 
 def random_lowres_flow(h: int, w: int, max_mag: float, seed: int) -> np.ndarray:
