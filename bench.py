@@ -516,6 +516,106 @@ def run_serve(args):
     }), flush=True)
 
 
+TRAIN_BATCH, TRAIN_SIZE, TRAIN_POOL = 32, 256, 4
+
+
+def train_flops_per_step(spec, batch=TRAIN_BATCH, size=TRAIN_SIZE):
+    """Algorithmic FLOPs of one training step's convolutions: the forward (pyramids of 2B
+    images, the estimators a -> b for B pairs, heads included), the weight gradient of every
+    conv and the data gradient of every conv but the first (same FLOPs as its forward), plus
+    the correlation forward and backward (3 x its forward)."""
+    L = spec.levels
+    fwd = dgrad = corr = 0
+    for name, cin, cout, stride, _ in spec.layer_table():
+        l = int(name[3])
+        if name.startswith("pyr"):
+            f = 2 * (2 * batch) * (size >> l) ** 2 * cout * cin * 9
+        else:
+            f = 2 * batch * (size >> l) ** 2 * cout * cin * 9
+        fwd += f
+        if name != "pyr1a":
+            dgrad += f
+    d = (2 * spec.radius + 1) ** 2
+    for l in range(2, L + 1):
+        corr += 2 * batch * (size >> l) ** 2 * d * spec.chans[l - 1]
+    return dict(forward=fwd, wgrad=fwd, dgrad=dgrad, correlation=3 * corr, total=2 * fwd + dgrad + 3 * corr)
+
+
+def run_train(args):
+    """Training throughput (SYS-4): the 5-level net on 256x256 synthetic pairs (|F| <= 16 px,
+    0-3 occluding rectangles), batch 32, one AdamW step per batch through tc_trainer_run."""
+    import torch
+    import paper_2301_00750_b300 as tc  # noqa: F401
+    import paper_2301_00750_b300.train as tr
+
+    tmp = tempfile.mkdtemp(prefix="tctrain")
+    path = os.path.join(tmp, "net.tcw")
+    write_weights(path)
+    host = [synth.training_batch(20000 + 1000 * k, TRAIN_BATCH, TRAIN_SIZE, 16.0) for k in range(TRAIN_POOL)]
+    dev = [tuple(torch.from_numpy(x).cuda() for x in bt) for bt in host]
+    t = tr.Trainer(TRAIN_BATCH, TRAIN_SIZE, TRAIN_SIZE, args.precision if args.precision != "fp8" else "bf16",
+                   weights_path=path)
+    stream = torch.cuda.current_stream()
+    first = t.run(*dev[0], mode="forward", wait=True)
+    for k in range(args.warmup):
+        t.run(*dev[k % TRAIN_POOL], mode="step")
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for k in range(args.steps):
+        t.run(*dev[k % TRAIN_POOL], mode="step")
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = ev[0].elapsed_time(ev[args.steps])
+    per = sorted(ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps))
+    last = t.loss()
+    # end to end: pinned host batches copied in and the loss read back every step
+    pinned = [tuple(torch.from_numpy(x).pin_memory() for x in bt) for bt in host]
+    bufs = tuple(torch.empty_like(x) for x in dev[0])
+    n_e2e = max(3, min(args.steps, 30))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(n_e2e):
+        for dst, src in zip(bufs, pinned[k % TRAIN_POOL]):
+            dst.copy_(src, non_blocking=True)
+        t.run(*bufs, mode="step", wait=True)
+    e2e_s = time.perf_counter() - t0
+    steps_done = t.steps
+    t.destroy()
+    flops = train_flops_per_step(net_spec())
+    achieved = flops["total"] * args.steps / (total_ms / 1e3) / 1e12
+    h2d = sum(x.numel() * 4 for x in dev[0])
+    line = {
+        "metric": "training throughput, lite flow net 5 levels, 256x256 pairs, batch 32 (pairs/s)",
+        "value": round(args.steps * TRAIN_BATCH / (total_ms / 1e3), 2), "unit": "pairs/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32"}.get(args.precision, "bf16") + " activations, f32 gradients and master weights",
+        "data": "synthetic (seeded 256x256 pairs: blurred noise, smooth flow |F| <= 16 px, 0-3 rectangles)",
+        "config": {"workload": "train 5-level net 16/32/64/96/128, radius 4, decoder 128/96/64/32/2; multi-scale "
+                               "EPE (levels 5..2, equal weights); AdamW lr 1e-4", "batch": TRAIN_BATCH,
+                   "size": TRAIN_SIZE, "batches_resident": TRAIN_POOL,
+                   "l2": "per-step working set (activations ~4 GB) > 126 MB L2 (no flush needed)"},
+        "latency_ms": {"p50": round(per[len(per) // 2], 3), "p99": round(per[min(len(per) - 1, int(0.99 * len(per)))], 3)},
+        "loss": {"before": round(first, 4), "after_steps": round(last, 4), "steps": steps_done},
+        "roofline": {"kernel": "all convs (forward, data and weight gradients) + correlation", "bound": "alu",
+                     "achieved": round(achieved, 2), "peak": round(FP32_SIMT_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+                     "frac": round(achieved / FP32_SIMT_PEAK_TFLOPS, 4), "traffic": None,
+                     "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2032 MHz (the trainer's convs run "
+                                    "on the CUDA cores)",
+                     "gflop_per_step": round(flops["total"] / 1e9, 1)},
+        "clocks": clk,
+        "e2e": {"value": round(n_e2e * TRAIN_BATCH / e2e_s, 2), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": 8},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -531,11 +631,14 @@ def main():
     ap.add_argument("--ring", type=int, default=4, help="output buffers per stream (frames in flight)")
     ap.add_argument("--seconds", type=float, default=10.0)
     ap.add_argument("--budget-gb", type=float, default=0.0)
+    ap.add_argument("--train", action="store_true", help="run the training-throughput benchmark instead")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.serve:
         run_serve(args)
+    elif args.train:
+        run_train(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
