@@ -1,6 +1,10 @@
 // Implicit-GEMM 3x3 convolution on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
-// GEMM view: M = output pixels, N = cout, K = 9 taps x input channels.  Stride-1 layers use
+// GEMM view: M = output pixels, N = cout, K = 9 taps x input channels, taken in K steps of
+// one swizzle span: 64 bf16 (128 e4m3) channels with the 128-byte swizzle, or 32 / 16 bf16
+// channels with the 64- / 32-byte swizzle for layers that have no more input channels than
+// that (the 16- and 32-channel pyramid levels), so no step multiplies zero padding
+// wider than the layer.  The descriptions below use the 128-byte case.  Stride-1 layers use
 // conv_tc_halo_kernel (below), which loads each activation tile once per kernel row and
 // reuses it for the three horizontal taps; the description here is of the per-tap kernel,
 // which serves the stride-2 layers.  One CTA computes a
@@ -33,8 +37,7 @@ namespace {
 using namespace ptx;
 
 constexpr int BM = 128;                    // output pixels per CTA (MMA M)
-constexpr int BK = 64;                     // bf16 channels per step (128 B); e4m3 steps hold 128
-template <bool F8> __host__ __device__ constexpr int kch() { return F8 ? 128 : 64; }
+constexpr int BK = 64;                     // bf16 channels of the widest K step (128 B); e4m3 steps hold 128
 constexpr uint32_t A_BYTES = BM * BK * 2;  // 16 KB
 
 enum : int { ERR_PRODUCER = 1, ERR_MMA = 2, ERR_EPILOGUE = 3, ERR_DRAIN = 4 };
@@ -46,7 +49,8 @@ __host__ __device__ constexpr size_t smem_bytes_for(int bn) {
 }
 
 struct TcLaunch {
-    int nch;      // 64-channel steps of the input
+    int nch;      // K steps of the input channels (kc channels, rb bytes each)
+    int kc, rb;   // channels per step; bytes per step (32, 64 or 128: the TMA/MMA swizzle span)
     int stride;   // 1 or 2
     int ho, wo;
     int img_off;  // first input image in the A descriptor
@@ -127,9 +131,9 @@ template <int BN, bool HEAD, bool F8>
 __global__ void __launch_bounds__(128, 1)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcLaunch p) {
     constexpr int STAGES = stages_for(BN);
-    constexpr uint32_t B_BYTES = BN * BK * 2;
-    constexpr uint32_t STAGE_TX = A_BYTES + B_BYTES;
+    constexpr uint32_t B_BYTES = BN * BK * 2;  // slot size (128-byte rows); a step may fill less
     constexpr uint32_t TMEM_COLS = tmem_cols_for(BN);
+    const uint32_t stage_tx = (uint32_t)(BM + BN) * (uint32_t)p.rb;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = smem;
@@ -171,16 +175,16 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             const int tap = ks / p.nch, ch = ks - tap * p.nch;
             const int ky = tap / 3, kx = tap - ky * 3;
             const uint32_t fb = full0 + 8 * s;
-            mbar_expect_tx(fb, STAGE_TX);
+            mbar_expect_tx(fb, stage_tx);
             const uint32_t dA = smem_u32(sA + s * A_BYTES), dB = smem_u32(sB + s * B_BYTES);
             if (p.stride == 1) {
-                tma_load_4d(&tmA, fb, dA, ch * kch<F8>(), x0 + kx - 1, y + ky - 1, img + p.img_off);
+                tma_load_4d(&tmA, fb, dA, ch * p.kc, x0 + kx - 1, y + ky - 1, img + p.img_off);
             } else {
                 const int dx = kx - 1;
-                tma_load_5d(&tmA, fb, dA, ch * kch<F8>(), dx != 0 ? 1 : 0, x0 + (dx < 0 ? -1 : 0), 2 * y + ky - 1,
+                tma_load_5d(&tmA, fb, dA, ch * p.kc, dx != 0 ? 1 : 0, x0 + (dx < 0 ? -1 : 0), 2 * y + ky - 1,
                             img + p.img_off);
             }
-            tma_load_3d(&tmB, fb, dB, ch * kch<F8>(), 0, tap);
+            tma_load_3d(&tmB, fb, dB, ch * p.kc, 0, tap);
             issued = ks + 1;
         }
         if (issued < nk) {
@@ -201,10 +205,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             const int s = ks % STAGES;
             if (!mbar_wait(full0 + 8 * s, (uint32_t)(ks / STAGES) & 1u, p.err, ERR_MMA)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint64_t da = sw128_desc(smem_u32(sA + s * A_BYTES));
-            const uint64_t db = sw128_desc(smem_u32(sB + s * B_BYTES));
-#pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk)
+            const uint64_t da = sw_desc(smem_u32(sA + s * A_BYTES), (uint32_t)p.rb);
+            const uint64_t db = sw_desc(smem_u32(sB + s * B_BYTES), (uint32_t)p.rb);
+            for (int kk = 0; kk < p.rb / 32; ++kk)
                 umma<F8>(tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, (ks | kk) != 0 ? 1u : 0u);
             umma_commit(empty0 + 8 * s);
         }
@@ -233,7 +236,6 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 // 128-byte-swizzled tile.  Activation halos and weight tiles travel in two separate rings
 // (2 halo slots, SB weight slots), so a halo stays resident while its three taps run.
 constexpr uint32_t HALO_ROWS = BM + 2;
-constexpr uint32_t HALO_TX = HALO_ROWS * BK * 2;  // 16,640 B
 constexpr uint32_t HALO_SLOT = 17408;             // rounded up to the 1024-byte swizzle atom
 constexpr int HALO_SA = 2;
 __host__ __device__ constexpr int halo_sb(int bn) { return bn >= 96 ? 3 : 4; }
@@ -260,6 +262,7 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int x0 = blockIdx.x * BM, y = blockIdx.y, img = blockIdx.z;
     const int ng = 3 * p.nch;  // (ky, channel step) groups
+    const uint32_t halo_tx = HALO_ROWS * (uint32_t)p.rb, b_tx = (uint32_t)BN * (uint32_t)p.rb;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < HALO_SA; ++s) {
@@ -292,8 +295,8 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
             const int ky = g / p.nch, ch = g - ky * p.nch;
             const int sa = g % HALO_SA;
             if (!mbar_wait(emptyA + 8 * sa, ((uint32_t)(g / HALO_SA) & 1u) ^ 1u, p.err, ERR_PRODUCER)) break;
-            mbar_expect_tx(fullA + 8 * sa, HALO_TX);
-            tma_load_4d(&tmA, fullA + 8 * sa, smem_u32(sA + sa * HALO_SLOT), ch * kch<F8>(), x0 - 1, y + ky - 1,
+            mbar_expect_tx(fullA + 8 * sa, halo_tx);
+            tma_load_4d(&tmA, fullA + 8 * sa, smem_u32(sA + sa * HALO_SLOT), ch * p.kc, x0 - 1, y + ky - 1,
                         img + p.img_off);
             ga = g + 1;
             for (int kx = 0; kx < 3; ++kx) {
@@ -302,8 +305,8 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                     fine = false;
                     break;
                 }
-                mbar_expect_tx(fullB + 8 * sb, B_BYTES);
-                tma_load_3d(&tmB, fullB + 8 * sb, smem_u32(sB + sb * B_BYTES), ch * kch<F8>(), 0, ky * 3 + kx);
+                mbar_expect_tx(fullB + 8 * sb, b_tx);
+                tma_load_3d(&tmB, fullB + 8 * sb, smem_u32(sB + sb * B_BYTES), ch * p.kc, 0, ky * 3 + kx);
                 gb = kb + 1;
             }
         }
@@ -332,10 +335,9 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint64_t da = sw128_desc_shifted(a0 + 128u * (uint32_t)kx);
-                const uint64_t db = sw128_desc(smem_u32(sB + sb * B_BYTES));
-#pragma unroll
-                for (int kk = 0; kk < BK / 16; ++kk)
+                const uint64_t da = sw_desc(a0 + (uint32_t)p.rb * (uint32_t)kx, (uint32_t)p.rb);
+                const uint64_t db = sw_desc(smem_u32(sB + sb * B_BYTES), (uint32_t)p.rb);
+                for (int kk = 0; kk < p.rb / 32; ++kk)
                     umma<F8>(tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
                               (g | kx | kk) != 0 ? 1u : 0u);
                 umma_commit(emptyB + 8 * sb);
@@ -428,9 +430,14 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
     if (a.ho != (a.h - 1) / a.stride + 1 || a.wo != (a.w - 1) / a.stride + 1) { why = "output size mismatch"; return false; }
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) { why = "cuTensorMapEncodeTiled unavailable"; return false; }
-    const int kc = f8 ? 128 : 64;  // channels per 128-byte step
-    const int nch = (a.cin + kc - 1) / kc, cinp = nch * kc;
     const cuuint64_t esz = f8 ? 1 : 2;
+    // K step: the narrowest swizzle span (32, 64 or 128 bytes) that holds the input
+    // channels, so layers with 16 or 32 channels do not multiply zero padding
+    const int rb = a.cin * (int)esz <= 32 ? 32 : (a.cin * (int)esz <= 64 ? 64 : 128);
+    const int kc = rb / (int)esz;
+    const int nch = (a.cin + kc - 1) / kc, cinp = nch * kc;
+    const CUtensorMapSwizzle swz = rb == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                            : (rb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);
     // Packed weights [9][cout][cinp] (zero beyond cin): bfloat16, or e4m3 with one scale per
     // output channel (amax / 448 over its 9 x cin weights).
     std::vector<uint8_t> pk((size_t)9 * bn * cinp * esz, 0);
@@ -478,21 +485,21 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
         const cuuint64_t strides[3] = {a.in_cs * esz, (cuuint64_t)a.w * a.in_cs * esz, (cuuint64_t)a.h * a.w * a.in_cs * esz};
         const cuuint32_t box[4] = {(cuuint32_t)kc, HALO_ROWS, 1, 1};  // the stride-1 kernel loads halo rows
         r = enc(&plan.tmA, dt, 4, const_cast<void *>(a.in), dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     } else {
         const cuuint64_t dims[5] = {(cuuint64_t)a.cin, 2, (cuuint64_t)(a.w / 2), (cuuint64_t)a.h, (cuuint64_t)n_in};
         const cuuint64_t strides[4] = {a.in_cs * esz, 2 * a.in_cs * esz, (cuuint64_t)a.w * a.in_cs * esz,
                                        (cuuint64_t)a.h * a.w * a.in_cs * esz};
         const cuuint32_t box[5] = {(cuuint32_t)kc, 1, BM, 1, 1};
         r = enc(&plan.tmA, dt, 5, const_cast<void *>(a.in), dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     }
     if (r == CUDA_SUCCESS) {
         const cuuint64_t dims[3] = {(cuuint64_t)cinp, (cuuint64_t)bn, 9};
         const cuuint64_t strides[2] = {(cuuint64_t)cinp * esz, (cuuint64_t)bn * cinp * esz};
         const cuuint32_t box[3] = {(cuuint32_t)kc, (cuuint32_t)bn, 1};
         r = enc(&plan.tmB, dt, 3, wdev, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     }
     if (r != CUDA_SUCCESS) {
         cudaFree(wdev);
@@ -503,6 +510,8 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
     plan.bn = bn;
     plan.cout = bn;
     plan.nch = nch;
+    plan.kc = kc;
+    plan.rb = rb;
     plan.f8 = f8;
     plan.stride = a.stride;
     plan.h = a.h;
@@ -546,8 +555,8 @@ cudaError_t launch_conv_tc_head(const TcConvPlan &plan, const ConvArgs &a, const
                                 cudaStream_t st) {
     int img_off = 0;
     if (!plan.enabled || !plan.head || !image_offset(plan, a, &img_off)) return cudaErrorInvalidValue;
-    TcLaunch lp{plan.nch, plan.stride, plan.ho, plan.wo, img_off, nullptr, 0, a.bias, 0, plan.err, flow, up,
-                plan.wscale, 1.f};
+    TcLaunch lp{plan.nch, plan.kc, plan.rb, plan.stride, plan.ho, plan.wo, img_off, nullptr, 0, a.bias, 0, plan.err,
+                flow, up, plan.wscale, 1.f};
     return plan.f8 ? launch_bn<16, true, true>(plan, lp, a.n, st) : launch_bn<16, true, false>(plan, lp, a.n, st);
 }
 
@@ -570,8 +579,8 @@ cudaError_t launch_conv_tc(const TcConvPlan &plan, const ConvArgs &a, cudaStream
     int img_off = 0;
     if (!plan.enabled || plan.head || !image_offset(plan, a, &img_off)) return cudaErrorInvalidValue;
     if (reinterpret_cast<uintptr_t>(a.out) % 16 != 0 || a.out_cs % (plan.f8 ? 16 : 8) != 0) return cudaErrorInvalidValue;
-    TcLaunch lp{plan.nch, plan.stride, plan.ho, plan.wo, img_off, a.out, a.out_cs, a.bias, a.leaky, plan.err,
-                nullptr, nullptr, plan.wscale, a.q_out};
+    TcLaunch lp{plan.nch, plan.kc, plan.rb, plan.stride, plan.ho, plan.wo, img_off, a.out, a.out_cs, a.bias, a.leaky,
+                plan.err, nullptr, nullptr, plan.wscale, a.q_out};
     return plan.f8 ? launch_any_bn<true>(plan, lp, a.n, st) : launch_any_bn<false>(plan, lp, a.n, st);
 }
 

@@ -20,6 +20,7 @@ struct TcConvPlan {
     CUtensorMap tmA;  // 64-byte aligned type
     CUtensorMap tmB;
     int bn = 0, nch = 0, stride = 1, h = 0, w = 0, ho = 0, wo = 0, n_in = 0, cout = 0;
+    int kc = 0, rb = 0;  // channels and bytes of one K step (rb = 32, 64 or 128: the swizzle span)
     const void *in_base = nullptr;  // start of the buffer the A descriptor covers
     size_t img_bytes = 0;           // bytes between consecutive images of that buffer
     void *wpk = nullptr;            // packed weights (owned by the plan)

@@ -100,6 +100,18 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
 // address bits of each row, so the shifted start alone selects the right rows.
 __device__ __forceinline__ uint64_t sw128_desc_shifted(uint32_t saddr) { return sw128_desc(saddr); }
 
+// K-major descriptor for rows of rb = 32, 64 or 128 bytes written by TMA with the matching
+// swizzle (32B, 64B, 128B): 8-row groups 8 rb apart; layout codes 6, 4, 2.  Like the
+// 128-byte form, the swizzle follows the address bits, so row-shifted starts are valid.
+__device__ __forceinline__ uint64_t sw_desc(uint32_t saddr, uint32_t rb) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)((8u * rb) >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)(rb == 128u ? 2u : (rb == 64u ? 4u : 6u)) << 61;
+    return d;
+}
+
 // Instruction descriptor of kind::f16: D f32, A and B bf16, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
