@@ -63,6 +63,8 @@ struct TcLaunch {
     const float *up;  // flow-head mode: residual base flow, same layout, or NULL
     const float *wscale;  // e4m3: per-output-channel weight scale (activation scales folded in)
     float q_out;          // e4m3: 1 / output activation scale
+    int out_f32;          // bf16 operands only: write float32 (out_cs in floats) instead of bf16
+    int accumulate;       // with out_f32: add to the output instead of overwriting it
 };
 
 // Epilogue shared by the conv kernels: thread r of the CTA owns accumulator row r, i.e.
@@ -99,7 +101,18 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, const TcLaunch &p, 
                     v[j] = (F8 ? a * __ldg(p.wscale + c0 + j) : a) + __ldg(p.bias + c0 + j);
                     if (p.leaky) v[j] = v[j] >= 0.f ? v[j] : 0.1f * v[j];
                 }
-                if (F8) {
+                if (!F8 && p.out_f32) {
+                    float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(p.out) + pix * p.out_cs + c0);
+#pragma unroll
+                    for (int q4 = 0; q4 < 4; ++q4) {
+                        float4 o = make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
+                        if (p.accumulate) {
+                            const float4 e = dst[q4];
+                            o.x += e.x; o.y += e.y; o.z += e.z; o.w += e.w;
+                        }
+                        dst[q4] = o;
+                    }
+                } else if (F8) {
                     uint4 q;
                     q.x = pack_e4m3x4(v[0] * p.q_out, v[1] * p.q_out, v[2] * p.q_out, v[3] * p.q_out);
                     q.y = pack_e4m3x4(v[4] * p.q_out, v[5] * p.q_out, v[6] * p.q_out, v[7] * p.q_out);
@@ -556,7 +569,7 @@ cudaError_t launch_conv_tc_head(const TcConvPlan &plan, const ConvArgs &a, const
     int img_off = 0;
     if (!plan.enabled || !plan.head || !image_offset(plan, a, &img_off)) return cudaErrorInvalidValue;
     TcLaunch lp{plan.nch, plan.kc, plan.rb, plan.stride, plan.ho, plan.wo, img_off, nullptr, 0, a.bias, 0, plan.err,
-                flow, up, plan.wscale, 1.f};
+                flow, up, plan.wscale, 1.f, 0, 0};
     return plan.f8 ? launch_bn<16, true, true>(plan, lp, a.n, st) : launch_bn<16, true, false>(plan, lp, a.n, st);
 }
 
@@ -580,8 +593,17 @@ cudaError_t launch_conv_tc(const TcConvPlan &plan, const ConvArgs &a, cudaStream
     if (!plan.enabled || plan.head || !image_offset(plan, a, &img_off)) return cudaErrorInvalidValue;
     if (reinterpret_cast<uintptr_t>(a.out) % 16 != 0 || a.out_cs % (plan.f8 ? 16 : 8) != 0) return cudaErrorInvalidValue;
     TcLaunch lp{plan.nch, plan.kc, plan.rb, plan.stride, plan.ho, plan.wo, img_off, a.out, a.out_cs, a.bias, a.leaky,
-                plan.err, nullptr, nullptr, plan.wscale, a.q_out};
+                plan.err, nullptr, nullptr, plan.wscale, a.q_out, 0, 0};
     return plan.f8 ? launch_any_bn<true>(plan, lp, a.n, st) : launch_any_bn<false>(plan, lp, a.n, st);
+}
+
+cudaError_t launch_conv_tc_f32(const TcConvPlan &plan, const ConvArgs &a, bool accumulate, cudaStream_t st) {
+    int img_off = 0;
+    if (!plan.enabled || plan.head || plan.f8 || !image_offset(plan, a, &img_off)) return cudaErrorInvalidValue;
+    if (reinterpret_cast<uintptr_t>(a.out) % 16 != 0 || a.out_cs % 4 != 0) return cudaErrorInvalidValue;
+    TcLaunch lp{plan.nch, plan.kc, plan.rb, plan.stride, plan.ho, plan.wo, img_off, a.out, a.out_cs, a.bias, a.leaky,
+                plan.err, nullptr, nullptr, plan.wscale, 1.f, 1, accumulate ? 1 : 0};
+    return launch_any_bn<false>(plan, lp, a.n, st);
 }
 
 }  // namespace tc

@@ -54,4 +54,8 @@ cudaError_t launch_conv_tc_head(const TcConvPlan &plan, const ConvArgs &a, const
 // planned buffer, on an image boundary), writing bfloat16 to a.out with a.out_cs stride.
 cudaError_t launch_conv_tc(const TcConvPlan &plan, const ConvArgs &a, cudaStream_t st);
 
+// The same for a bf16 plan writing float32 to a.out (pixel stride a.out_cs floats, a
+// multiple of 4, 16-byte aligned), added to what is there when accumulate is set.
+cudaError_t launch_conv_tc_f32(const TcConvPlan &plan, const ConvArgs &a, bool accumulate, cudaStream_t st);
+
 }  // namespace tc

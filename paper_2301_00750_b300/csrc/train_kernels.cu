@@ -62,6 +62,70 @@ cudaError_t pack_dgrad(const float *w, int cout, int cin, int cout_p, int cin_p,
     return cudaGetLastError();
 }
 
+// Master weights -> the tensor-core packing [9][bn][cinp] (bfloat16, K-major rows):
+//   mode 0 (forward): row o, channel c = W[o][c][tap] for o < cout, c < cin;
+//   mode 1 (data gradient, output channels [lo, lo + n) of the layer's input): row o,
+//   channel c = W[c][lo + o][8 - tap] for o < n, c < cout.
+// Zero elsewhere.
+__global__ void pack_tc_kernel(const float *w, int cout, int cin, int mode, int lo, int n, int bn, int cinp,
+                               __nv_bfloat16 *out) {
+    const size_t total = (size_t)9 * bn * cinp;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int c = (int)(i % cinp);
+    const size_t r = i / cinp;
+    const int o = (int)(r % bn), tap = (int)(r / bn);
+    float v = 0.f;
+    if (mode == 0) {
+        if (o < cout && c < cin) v = w[((size_t)o * cin + c) * 9 + tap];
+    } else {
+        if (o < n && c < cout) v = w[((size_t)c * cin + lo + o) * 9 + (8 - tap)];
+    }
+    out[i] = __float2bfloat16_rn(v);
+}
+
+cudaError_t pack_tc(const float *w, int cout, int cin, int mode, int lo, int n, int bn, int cinp, void *out,
+                    cudaStream_t st) {
+    const size_t total = (size_t)9 * bn * cinp;
+    pack_tc_kernel<<<blocks_for(total), 256, 0, st>>>(w, cout, cin, mode, lo, n, bn, cinp,
+                                                     static_cast<__nv_bfloat16 *>(out));
+    return cudaGetLastError();
+}
+
+// dz = dy LeakyReLU'(y) written as float (dz, may be NULL) and bfloat16 (dzh, may be NULL),
+// and, for a stride-2 conv, bfloat16 into the zeroed dilated map dzh_dil (hd x wd).
+template <typename T>
+__global__ void lrelu_bwd2_kernel(const float *dy, int dy_cs, const T *y, int y_cs, int leaky, size_t npix, int nc,
+                                  float *dz, __nv_bfloat16 *dzh, __nv_bfloat16 *dzh_dil, int ho, int wo, int hd, int wd) {
+    const size_t total = npix * nc;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const size_t p = i / nc;
+    const int c = (int)(i - p * nc);
+    float g = dy[p * dy_cs + c];
+    if (leaky) g *= lrelu_grad(to_f(y[p * y_cs + c]));
+    if (dz) dz[i] = g;
+    const __nv_bfloat16 gh = __float2bfloat16_rn(g);
+    if (dzh) dzh[i] = gh;
+    if (dzh_dil) {
+        const size_t hw = (size_t)ho * wo;
+        const size_t b = p / hw, r = p - b * hw;
+        const int oy = (int)(r / wo), ox = (int)(r - (size_t)oy * wo);
+        dzh_dil[((b * hd + 2 * oy) * (size_t)wd + 2 * ox) * nc + c] = gh;
+    }
+}
+
+template <typename T>
+cudaError_t lrelu_bwd2(const float *dy, int dy_cs, const T *y, int y_cs, bool leaky, size_t npix, int nc, float *dz,
+                       void *dzh, void *dzh_dil, int ho, int wo, int hd, int wd, cudaStream_t st) {
+    const size_t total = npix * nc;
+    if (total == 0) return cudaSuccess;
+    lrelu_bwd2_kernel<T><<<blocks_for(total), 256, 0, st>>>(dy, dy_cs, y, y_cs, leaky ? 1 : 0, npix, nc, dz,
+                                                           static_cast<__nv_bfloat16 *>(dzh),
+                                                           static_cast<__nv_bfloat16 *>(dzh_dil), ho, wo, hd, wd);
+    return cudaGetLastError();
+}
+
 // Planar images [n][3][h][w] (two batches, a then b) -> NHWC [2n][h][w][4] with a zero 4th
 // channel, in the activation type.
 template <typename T>
@@ -623,7 +687,9 @@ cudaError_t bruteforce(const float *a, const float *b, int c, int h, int w, int 
     template cudaError_t corr_bwd<T>(const CorrBwdArgs<T> &, cudaStream_t);                                        \
     template cudaError_t warp_bwd<T>(const WarpBwdArgs<T> &, cudaStream_t);                                        \
     template cudaError_t flow_to_act<T>(const float *, size_t, T *, int, cudaStream_t);                          \
-    template cudaError_t pack_images<T>(const float *, const float *, int, int, int, T *, cudaStream_t);
+    template cudaError_t pack_images<T>(const float *, const float *, int, int, int, T *, cudaStream_t);          \
+    template cudaError_t lrelu_bwd2<T>(const float *, int, const T *, int, bool, size_t, int, float *, void *,   \
+                                       void *, int, int, int, int, cudaStream_t);
 TC_TRAIN_INST(float)
 TC_TRAIN_INST(__nv_bfloat16)
 #undef TC_TRAIN_INST

@@ -66,6 +66,11 @@ template <typename T>
 cudaError_t lrelu_bwd(const float *dy, int dy_cs, const T *y, int y_cs, bool leaky, size_t npix, int nc, float *dz,
                       float *dz_dil, int ho, int wo, int hd, int wd, cudaStream_t st);
 template <typename T> cudaError_t wgrad(const WgradArgs<T> &a, float *db, cudaStream_t st);
+cudaError_t pack_tc(const float *w, int cout, int cin, int mode, int lo, int n, int bn, int cinp, void *out,
+                    cudaStream_t st);
+template <typename T>
+cudaError_t lrelu_bwd2(const float *dy, int dy_cs, const T *y, int y_cs, bool leaky, size_t npix, int nc, float *dz,
+                       void *dzh, void *dzh_dil, int ho, int wo, int hd, int wd, cudaStream_t st);
 cudaError_t head_dgrad(const float *dflow, const float *w, int cin, int n, int h, int w_, float *dx, int dx_cs,
                        bool accumulate, cudaStream_t st);
 template <typename T> cudaError_t corr_bwd(const CorrBwdArgs<T> &a, cudaStream_t st);

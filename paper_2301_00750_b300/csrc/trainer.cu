@@ -24,6 +24,7 @@
 #include "../../include/tc_train.h"
 #include "common.cuh"
 #include "engine_internal.h"
+#include "conv_tc.cuh"
 #include "train_kernels.cuh"
 
 using namespace tc;
@@ -40,6 +41,17 @@ struct Layer {
     float *bk = nullptr;   // bias copy (the flat parameter vector does not keep it 16-byte aligned)
     int dg_cout_p = 0, dg_cin_p = 0;
     float *wkT = nullptr;  // data-gradient packed [9][cout][cin_p] (flipped, transposed)
+    // forward input and output (fixed buffers; windows at the pointers)
+    const void *in = nullptr;
+    int in_cs = 0, n = 0, h = 0, w = 0;
+    void *out = nullptr;
+    int out_cs = 0;
+    // BF16 trainer: forward and data-gradient convs on the tensor cores (weights packed from
+    // the master copy every step); the data gradient in slices of <= 128 output channels
+    bool tc = false;
+    TcConvPlan fplan;
+    TcConvPlan dplan[2];
+    int dlo[2] = {0, 0}, dn[2] = {0, 0}, ndp = 0;
 };
 
 struct Level {
@@ -70,6 +82,8 @@ struct tc_trainer {
     void *img = nullptr;     // T
     std::vector<Level> lv;
     float *dz = nullptr, *dz_dil = nullptr, *dtmp0 = nullptr, *dtmp1 = nullptr;
+    void *dzh = nullptr, *dzh_dil = nullptr;  // bfloat16 copies of dz (tensor-core data gradients)
+    int *dev_err = nullptr;                   // device error word of the tensor-core kernels
     double *loss_dev = nullptr;
     std::vector<void *> allocs;
     std::string err;
@@ -107,6 +121,11 @@ tc_status talloc(tc_trainer *t, P **p, size_t bytes) {
 }
 
 void free_trainer(tc_trainer *t) {
+    for (auto &ly : t->layers) {
+        ly.fplan.release();
+        ly.dplan[0].release();
+        ly.dplan[1].release();
+    }
     for (void *p : t->allocs) cudaFree(p);
     t->allocs.clear();
 }
@@ -191,7 +210,7 @@ tc_status build(tc_trainer *t) {
         max_tmp = std::max(max_tmp, px2 * V.c);
         if (l > 1) max_dil = std::max(max_dil, (size_t)2 * B * t->lv[l - 2].h * t->lv[l - 2].w * V.c);
         if (l < 2) continue;
-        V.x0p = round_up(t->D + V.c + 2, 4);
+        V.x0p = round_up(t->D + V.c + 2, 16);  // 16: tensor-core K steps and 16-byte pixel strides
         V.xdc = dec3 + dec2 + dec1;
         if ((r = talloc(t, &V.x0, px * V.x0p * es)) != TC_OK) return r;
         if ((r = talloc(t, &V.x1, px * dec0 * es)) != TC_OK) return r;
@@ -248,17 +267,94 @@ tc_status build(tc_trainer *t) {
         if (ly.dg_cout_p)
             if ((r = talloc(t, &ly.wkT, (size_t)9 * ly.dg_cout_p * ly.dg_cin_p * 4)) != TC_OK) return r;
     }
+    // forward I/O of every layer
+    {
+        const int dec0 = t->net.dec[0], dec2 = t->net.dec[2], dec3 = t->net.dec[3];
+        auto set = [](Layer &ly, const void *in, int in_cs, int n, int h, int w, void *out, int out_cs) {
+            ly.in = in; ly.in_cs = in_cs; ly.n = n; ly.h = h; ly.w = w; ly.out = out; ly.out_cs = out_cs;
+        };
+        for (int l = 1; l <= L; ++l) {
+            Level &V = t->lv[l - 1];
+            Layer *P = &t->layers[3 * (l - 1)];
+            if (l == 1)
+                set(P[0], t->img, 4, 2 * B, t->H, t->W, V.pyr[0], V.c);
+            else
+                set(P[0], t->lv[l - 2].pyr[2], t->lv[l - 2].c, 2 * B, t->lv[l - 2].h, t->lv[l - 2].w, V.pyr[0], V.c);
+            set(P[1], V.pyr[0], V.c, 2 * B, V.h, V.w, V.pyr[1], V.c);
+            set(P[2], V.pyr[1], V.c, 2 * B, V.h, V.w, V.pyr[2], V.c);
+        }
+        for (int l = L; l >= 2; --l) {
+            Level &V = t->lv[l - 1];
+            Layer *E = &t->layers[3 * L + 5 * (L - l)];
+            T *xd = static_cast<T *>(V.xd);
+            set(E[0], V.x0, V.x0p, B, V.h, V.w, V.x1, dec0);
+            set(E[1], V.x1, dec0, B, V.h, V.w, xd + dec3 + dec2, V.xdc);
+            set(E[2], xd + dec3 + dec2, V.xdc, B, V.h, V.w, xd + dec3, V.xdc);
+            set(E[3], xd + dec3, V.xdc, B, V.h, V.w, xd, V.xdc);
+            set(E[4], xd, V.xdc, B, V.h, V.w, V.flow, 2);
+        }
+    }
+    if (t->prec == TC_BF16) {
+        if ((r = talloc(t, &t->dev_err, sizeof(int))) != TC_OK) return r;
+        if ((r = talloc(t, &t->dzh, max_dz * 2)) != TC_OK) return r;
+        if ((r = talloc(t, &t->dzh_dil, std::max<size_t>(max_dil, 1) * 2)) != TC_OK) return r;
+        const int L5 = 3 * L;
+        for (size_t k = 1; k < t->layers.size(); ++k) {
+            Layer &ly = t->layers[k];
+            const bool head = k >= (size_t)L5 && (k - L5) % 5 == 4;
+            const int ho = (ly.h - 1) / ly.stride + 1, wo = (ly.w - 1) / ly.stride + 1;
+            std::string why;
+            ConvArgs a{ly.in, ly.in_cs, ly.n, ly.h, ly.w, ly.cin_p, ly.stride, ho, wo, nullptr, nullptr, ly.cout,
+                       ly.out, ly.out_cs, ly.leaky, 1.f, 0};
+            bool ok;
+            if (head) {
+                a.out = nullptr;
+                ok = tc_plan_head(ly.fplan, a, ly.n, std::vector<float>((size_t)9 * ly.cin_p * ly.cout, 0.f),
+                                  t->dev_err, why);
+            } else {
+                ok = tc_plan_conv(ly.fplan, a, ly.n, std::vector<float>((size_t)9 * ly.cin_p * ly.cout, 0.f),
+                                  t->dev_err, why);
+            }
+            if (!ok) return tfail(t, TC_ERR_UNSUPPORTED, "trainer: layer not eligible for the tensor cores: " + why);
+            if (head) {
+                ly.tc = true;
+                continue;
+            }
+            if (!ly.dg_cout_p) continue;
+            // data gradient: stride-1 conv of dz (or of its dilation for stride 2) with the
+            // flipped, transposed kernel, in slices of <= 128 output channels
+            const int N = ly.dg_cin_p;
+            ly.ndp = N > 128 ? 2 : 1;
+            ly.dlo[0] = 0;
+            ly.dn[0] = N > 128 ? 128 : N;
+            ly.dlo[1] = 128;
+            ly.dn[1] = N - 128;
+            for (int q = 0; q < ly.ndp; ++q) {
+                if (ly.dn[q] % 16 != 0) return tfail(t, TC_ERR_UNSUPPORTED, "trainer: data-gradient slice not a multiple of 16");
+                ConvArgs d{ly.stride == 2 ? t->dzh_dil : t->dzh, ly.cout, ly.n, ly.h, ly.w, ly.cout, 1, ly.h, ly.w,
+                           nullptr, nullptr, ly.dn[q], nullptr, ly.dn[q], 0, 1.f, 0};
+                if (!tc_plan_conv(ly.dplan[q], d, ly.n, std::vector<float>((size_t)9 * ly.cout * ly.dn[q], 0.f),
+                                  t->dev_err, why))
+                    return tfail(t, TC_ERR_UNSUPPORTED, "trainer: data gradient not eligible for the tensor cores: " + why);
+            }
+            ly.tc = true;
+        }
+        t->layers[0].tc = false;
+    }
     return TC_OK;
 }
 
 // --------------------------------------------------------------------------- forward
 
 template <typename T>
-tc_status conv_fwd(tc_trainer *t, const Layer &ly, const void *in, int in_cs, int n, int h, int w, void *out,
-                   int out_cs) {
-    const int ho = (h - 1) / ly.stride + 1, wo = (w - 1) / ly.stride + 1;
-    ConvArgs a{in, in_cs, n, h, w, ly.cin_p, ly.stride, ho, wo, ly.wk, ly.bk, ly.cout, out, out_cs, ly.leaky, 1.f, 0};
-    TT_TRY(t, launch_conv_simt<T>(a, t->st), "conv forward");
+tc_status conv_fwd(tc_trainer *t, const Layer &ly) {
+    const int ho = (ly.h - 1) / ly.stride + 1, wo = (ly.w - 1) / ly.stride + 1;
+    ConvArgs a{ly.in, ly.in_cs, ly.n, ly.h, ly.w, ly.cin_p, ly.stride, ho, wo, ly.wk, ly.bk, ly.cout, ly.out,
+               ly.out_cs, ly.leaky, 1.f, 0};
+    if (ly.tc)
+        TT_TRY(t, launch_conv_tc(ly.fplan, a, t->st), "conv forward (tensor cores)");
+    else
+        TT_TRY(t, launch_conv_simt<T>(a, t->st), "conv forward");
     return TC_OK;
 }
 
@@ -268,12 +364,25 @@ tc_status forward(tc_trainer *t, const float *Ia, const float *Ib, const float *
     const bool bf = t->prec == TC_BF16;
     tc_status r;
     for (auto &ly : t->layers) {
-        TT_TRY(t, train::pack_fwd(t->params + ly.w_off, ly.cout, ly.cin, ly.cin_p, bf, ly.wk, t->st), "pack");
         TT_TRY(t, cudaMemcpyAsync(ly.bk, t->params + ly.b_off, (size_t)ly.cout * 4, cudaMemcpyDeviceToDevice, t->st),
                "bias copy");
-        if (want_grad && ly.wkT)
-            TT_TRY(t, train::pack_dgrad(t->params + ly.w_off, ly.cout, ly.cin, ly.dg_cout_p, ly.dg_cin_p, ly.wkT, t->st),
-                   "pack");
+        const float *w = t->params + ly.w_off;
+        if (ly.tc) {
+            const TcConvPlan &f = ly.fplan;
+            TT_TRY(t, train::pack_tc(w, ly.cout, ly.cin, 0, 0, 0, f.bn, f.nch * f.kc, f.wpk, t->st), "pack");
+            if (want_grad)
+                for (int q = 0; q < ly.ndp; ++q) {
+                    const TcConvPlan &d = ly.dplan[q];
+                    TT_TRY(t, train::pack_tc(w, ly.cout, ly.cin, 1, ly.dlo[q], std::min(ly.dn[q], ly.cin - ly.dlo[q]),
+                                             d.bn, d.nch * d.kc, d.wpk, t->st),
+                           "pack");
+                }
+            if (ly.cout == 2) TT_TRY(t, train::pack_fwd(w, ly.cout, ly.cin, ly.cin_p, bf, ly.wk, t->st), "pack");
+        } else {
+            TT_TRY(t, train::pack_fwd(w, ly.cout, ly.cin, ly.cin_p, bf, ly.wk, t->st), "pack");
+            if (want_grad && ly.wkT)
+                TT_TRY(t, train::pack_dgrad(w, ly.cout, ly.cin, ly.dg_cout_p, ly.dg_cin_p, ly.wkT, t->st), "pack");
+        }
     }
     T *img = static_cast<T *>(t->img);
     TT_TRY(t, train::pack_images<T>(Ia, Ib, B, t->H, t->W, img, t->st), "pack images");
@@ -284,9 +393,9 @@ tc_status forward(tc_trainer *t, const float *Ia, const float *Ib, const float *
         const void *in = l == 1 ? (const void *)img : t->lv[l - 2].pyr[2];
         const int in_cs = l == 1 ? 4 : t->lv[l - 2].c;
         const int ih = l == 1 ? t->H : t->lv[l - 2].h, iw = l == 1 ? t->W : t->lv[l - 2].w;
-        if ((r = conv_fwd<T>(t, P[0], in, in_cs, 2 * B, ih, iw, V.pyr[0], V.c)) != TC_OK) return r;
-        if ((r = conv_fwd<T>(t, P[1], V.pyr[0], V.c, 2 * B, V.h, V.w, V.pyr[1], V.c)) != TC_OK) return r;
-        if ((r = conv_fwd<T>(t, P[2], V.pyr[1], V.c, 2 * B, V.h, V.w, V.pyr[2], V.c)) != TC_OK) return r;
+        (void)in; (void)in_cs; (void)ih; (void)iw;
+        for (int j = 0; j < 3; ++j)
+            if ((r = conv_fwd<T>(t, P[j])) != TC_OK) return r;
     }
     const int dec1 = t->net.dec[1], dec2 = t->net.dec[2], dec3 = t->net.dec[3];
     // estimators a -> b, coarse to fine
@@ -310,13 +419,17 @@ tc_status forward(tc_trainer *t, const float *Ia, const float *Ib, const float *
         TT_TRY(t, launch_corr<T>(ca, t->st), "correlation");
         T *x1 = static_cast<T *>(V.x1);
         T *xd = static_cast<T *>(V.xd);
-        if ((r = conv_fwd<T>(t, E[0], x0, V.x0p, B, V.h, V.w, x1, E[0].cout)) != TC_OK) return r;
-        if ((r = conv_fwd<T>(t, E[1], x1, E[0].cout, B, V.h, V.w, xd + dec3 + dec2, V.xdc)) != TC_OK) return r;
-        if ((r = conv_fwd<T>(t, E[2], xd + dec3 + dec2, V.xdc, B, V.h, V.w, xd + dec3, V.xdc)) != TC_OK) return r;
-        if ((r = conv_fwd<T>(t, E[3], xd + dec3, V.xdc, B, V.h, V.w, xd, V.xdc)) != TC_OK) return r;
-        (void)dec1;
-        HeadArgs ha{xd, V.xdc, E[4].cin_p, B, V.h, V.w, E[4].wk, E[4].bk, l < L ? V.up : nullptr, V.flow};
-        TT_TRY(t, launch_head<T>(ha, t->st), "flow head");
+        (void)x1; (void)dec1; (void)dec2; (void)dec3;
+        for (int j = 0; j < 4; ++j)
+            if ((r = conv_fwd<T>(t, E[j])) != TC_OK) return r;
+        if (E[4].tc) {
+            ConvArgs a5{xd, V.xdc, B, V.h, V.w, E[4].cin_p, 1, V.h, V.w, nullptr, E[4].bk, 2, nullptr, 2, 0, 1.f, 0};
+            TT_TRY(t, launch_conv_tc_head(E[4].fplan, a5, l < L ? V.up : nullptr, V.flow, t->st),
+                   "flow head (tensor cores)");
+        } else {
+            HeadArgs ha{xd, V.xdc, E[4].cin_p, B, V.h, V.w, E[4].wk, E[4].bk, l < L ? V.up : nullptr, V.flow};
+            TT_TRY(t, launch_head<T>(ha, t->st), "flow head");
+        }
     }
     // loss: sum over levels of the mean EPE against the block-averaged ground truth
     TT_TRY(t, cudaMemsetAsync(t->loss_dev, 0, sizeof(double), t->st), "memset");
@@ -341,6 +454,21 @@ tc_status conv_bwd(tc_trainer *t, const Layer &ly, const void *x, int x_cs, int 
     const int ho = (h - 1) / ly.stride + 1, wo = (w - 1) / ly.stride + 1;
     const size_t npix = (size_t)n * ho * wo;
     const bool dil = dx && ly.stride == 2;
+    if (ly.tc && dx && ly.ndp > 0) {
+        if (dil) TT_TRY(t, cudaMemsetAsync(t->dzh_dil, 0, (size_t)n * h * w * ly.cout * 2, t->st), "memset");
+        TT_TRY(t, train::lrelu_bwd2<T>(dy, dy_cs, y, y_cs, ly.leaky != 0, npix, ly.cout, t->dz, dil ? nullptr : t->dzh,
+                                       dil ? t->dzh_dil : nullptr, ho, wo, h, w, t->st),
+               "activation backward");
+        train::WgradArgs<T> wa{static_cast<const T *>(x), x_cs, n, h, w, ly.cin, ly.stride, ho, wo, t->dz, ly.cout,
+                               ly.cout, t->grads + ly.w_off};
+        TT_TRY(t, train::wgrad<T>(wa, t->grads + ly.b_off, t->st), "weight gradient");
+        for (int q = 0; q < ly.ndp; ++q) {
+            ConvArgs a{dil ? t->dzh_dil : t->dzh, ly.cout, n, h, w, ly.cout, 1, h, w, nullptr, t->zeros, ly.dn[q],
+                       dx + ly.dlo[q], dx_cs, 0, 1.f, 0};
+            TT_TRY(t, launch_conv_tc_f32(ly.dplan[q], a, dx_accumulate, t->st), "data gradient (tensor cores)");
+        }
+        return TC_OK;
+    }
     if (dil) TT_TRY(t, cudaMemsetAsync(t->dz_dil, 0, (size_t)n * h * w * ly.cout * 4, t->st), "memset");
     TT_TRY(t, train::lrelu_bwd<T>(dy, dy_cs, y, y_cs, ly.leaky != 0, npix, ly.cout, t->dz, dil ? t->dz_dil : nullptr,
                                   ho, wo, h, w, t->st),
