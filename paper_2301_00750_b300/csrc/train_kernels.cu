@@ -284,6 +284,77 @@ cudaError_t wgrad(const WgradArgs<T> &a, float *db, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Channel-major, zero-bordered ("CP") copies for the tensor-core weight gradient: pixel
+// (b, y, x) of an n_img x h x w map sits at q = (b (h + 2) + y + 1) wp + x + 1.
+//   x_to_cp: three copies shifted by kx - 1 columns: out_kx[c][q] = x at column
+//   (q's column + kx - 2), zero off the map and for c >= cin (rows up to n).
+//   dz_to_cp: out[o][q] = dz of output pixel (y / s, x / s) when s divides y and x
+//   (s = stride), zero elsewhere; dz dense [n_img][ho][wo][cout] float.
+template <typename T>
+__global__ void x_to_cp_kernel(const T *x, int x_cs, int n_img, int h, int w, int cin, int wp, int n,
+                               __nv_bfloat16 *o0, __nv_bfloat16 *o1, __nv_bfloat16 *o2) {
+    const long long P = (long long)n_img * (h + 2) * wp;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P * 3) return;
+    const int kx = (int)(i / P);
+    const long long q = i - (long long)kx * P;
+    const int xx = (int)(q % wp);
+    const long long r = q / wp;
+    const int yy = (int)(r % (h + 2)), b = (int)(r / (h + 2));
+    const int iy = yy - 1, ix = xx + kx - 2;
+    __nv_bfloat16 *out = kx == 0 ? o0 : (kx == 1 ? o1 : o2);
+    const bool in = iy >= 0 && iy < h && ix >= 0 && ix < w;
+    const T *src = x + (((size_t)b * h + (in ? iy : 0)) * w + (in ? ix : 0)) * x_cs;
+    for (int c = 0; c < n; ++c) {
+        const float v = (in && c < cin) ? to_f(src[c]) : 0.f;
+        out[(size_t)c * P + q] = __float2bfloat16_rn(v);
+    }
+}
+
+__global__ void dz_to_cp_kernel(const float *dz, int dz_cs, int n_img, int h, int w, int ho, int wo, int stride,
+                                int cout, int wp, __nv_bfloat16 *out) {
+    const long long P = (long long)n_img * (h + 2) * wp;
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= P) return;
+    const int xx = (int)(q % wp);
+    const long long r = q / wp;
+    const int yy = (int)(r % (h + 2)), b = (int)(r / (h + 2));
+    const int iy = yy - 1, ix = xx - 1;
+    bool in = iy >= 0 && iy < h && ix >= 0 && ix < w && iy % stride == 0 && ix % stride == 0;
+    const int oy = iy / stride, ox = ix / stride;
+    in = in && oy < ho && ox < wo;
+    const float *src = dz + (((size_t)b * ho + (in ? oy : 0)) * wo + (in ? ox : 0)) * dz_cs;
+    for (int o = 0; o < cout; ++o) out[(size_t)o * P + q] = __float2bfloat16_rn(in ? src[o] : 0.f);
+}
+
+template <typename T>
+cudaError_t x_to_cp(const T *x, int x_cs, int n_img, int h, int w, int cin, int wp, int n, void *const out[3],
+                    cudaStream_t st) {
+    const long long P = (long long)n_img * (h + 2) * wp;
+    x_to_cp_kernel<T><<<blocks_for((size_t)P * 3), 256, 0, st>>>(x, x_cs, n_img, h, w, cin, wp, n,
+                                                                static_cast<__nv_bfloat16 *>(out[0]),
+                                                                static_cast<__nv_bfloat16 *>(out[1]),
+                                                                static_cast<__nv_bfloat16 *>(out[2]));
+    return cudaGetLastError();
+}
+
+cudaError_t dz_to_cp(const float *dz, int dz_cs, int n_img, int h, int w, int ho, int wo, int stride, int cout, int wp,
+                     void *out, cudaStream_t st) {
+    const long long P = (long long)n_img * (h + 2) * wp;
+    dz_to_cp_kernel<<<blocks_for((size_t)P), 256, 0, st>>>(dz, dz_cs, n_img, h, w, ho, wo, stride, cout, wp,
+                                                          static_cast<__nv_bfloat16 *>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t bgrad(const float *dz, int dz_cs, size_t P, int cout, float *db, cudaStream_t st) {
+    if (P == 0) return cudaSuccess;
+    const size_t ppc = wgrad_chunk(P);
+    const unsigned chunks = (unsigned)((P + ppc - 1) / ppc);
+    dim3 g2((cout + 31) / 32, chunks);
+    bgrad_kernel<<<g2, 256, 0, st>>>(dz, dz_cs, P, cout, db, ppc);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------- head dgrad
 
 // Data gradient of the flow head (2 outputs, no activation): dx[p][c] (+)= sum over taps and
@@ -689,7 +760,8 @@ cudaError_t bruteforce(const float *a, const float *b, int c, int h, int w, int 
     template cudaError_t flow_to_act<T>(const float *, size_t, T *, int, cudaStream_t);                          \
     template cudaError_t pack_images<T>(const float *, const float *, int, int, int, T *, cudaStream_t);          \
     template cudaError_t lrelu_bwd2<T>(const float *, int, const T *, int, bool, size_t, int, float *, void *,   \
-                                       void *, int, int, int, int, cudaStream_t);
+                                       void *, int, int, int, int, cudaStream_t);                                \
+    template cudaError_t x_to_cp<T>(const T *, int, int, int, int, int, int, int, void *const[3], cudaStream_t);
 TC_TRAIN_INST(float)
 TC_TRAIN_INST(__nv_bfloat16)
 #undef TC_TRAIN_INST

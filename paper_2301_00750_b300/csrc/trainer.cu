@@ -26,6 +26,7 @@
 #include "engine_internal.h"
 #include "conv_tc.cuh"
 #include "train_kernels.cuh"
+#include "wgrad_tc.cuh"
 
 using namespace tc;
 
@@ -52,6 +53,7 @@ struct Layer {
     TcConvPlan fplan;
     TcConvPlan dplan[2];
     int dlo[2] = {0, 0}, dn[2] = {0, 0}, ndp = 0;
+    WgradTcPlan wplan;  // weight gradient on the tensor cores (over the CP scratch buffers)
 };
 
 struct Level {
@@ -83,6 +85,8 @@ struct tc_trainer {
     std::vector<Level> lv;
     float *dz = nullptr, *dz_dil = nullptr, *dtmp0 = nullptr, *dtmp1 = nullptr;
     void *dzh = nullptr, *dzh_dil = nullptr;  // bfloat16 copies of dz (tensor-core data gradients)
+    void *dz_cp = nullptr, *x_cp[3] = {nullptr, nullptr, nullptr};  // weight-gradient operands (bf16)
+    float *wg_partial = nullptr;
     int *dev_err = nullptr;                   // device error word of the tensor-core kernels
     double *loss_dev = nullptr;
     std::vector<void *> allocs;
@@ -340,7 +344,43 @@ tc_status build(tc_trainer *t) {
             ly.tc = true;
         }
         t->layers[0].tc = false;
+        // weight gradients: CP scratch sized for the largest layer
+        size_t max_dz_cp = 0, max_x_cp = 0, max_part = 0;
+        for (auto &ly : t->layers) {
+            const int wp = round_up(ly.w + 2, 8), n = round_up(ly.cin, 16);
+            const long long P = (long long)ly.n * (ly.h + 2) * wp;
+            max_dz_cp = std::max(max_dz_cp, (size_t)ly.cout * (size_t)P);
+            max_x_cp = std::max(max_x_cp, (size_t)n * (size_t)P);
+            max_part = std::max(max_part, wgrad_tc_partial_floats(P, n));
+        }
+        if ((r = talloc(t, &t->dz_cp, max_dz_cp * 2)) != TC_OK) return r;
+        for (int k = 0; k < 3; ++k)
+            if ((r = talloc(t, &t->x_cp[k], max_x_cp * 2)) != TC_OK) return r;
+        if ((r = talloc(t, &t->wg_partial, max_part * 4)) != TC_OK) return r;
+        for (auto &ly : t->layers) {
+            const int wp = round_up(ly.w + 2, 8), n = round_up(ly.cin, 16);
+            const long long P = (long long)ly.n * (ly.h + 2) * wp;
+            std::string why;
+            const void *xs[3] = {t->x_cp[0], t->x_cp[1], t->x_cp[2]};
+            if (!wgrad_tc_plan(ly.wplan, t->dz_cp, xs, ly.cout, ly.cin, n, wp, P, t->wg_partial, t->dev_err, why))
+                return tfail(t, TC_ERR_UNSUPPORTED, "trainer: weight gradient not eligible for the tensor cores: " + why);
+        }
     }
+    return TC_OK;
+}
+
+// Weight and bias gradients on the tensor cores from the float dz [n ho wo][cout] of a layer
+// whose input is x (window of x_cs channels).
+template <typename T>
+tc_status wgrad_tc(tc_trainer *t, const Layer &ly, const void *x, int x_cs, const float *dz, int dz_cs) {
+    const int ho = (ly.h - 1) / ly.stride + 1, wo = (ly.w - 1) / ly.stride + 1;
+    const WgradTcPlan &W = ly.wplan;
+    TT_TRY(t, train::dz_to_cp(dz, dz_cs, ly.n, ly.h, ly.w, ho, wo, ly.stride, ly.cout, W.wp, t->dz_cp, t->st),
+           "weight gradient operands");
+    TT_TRY(t, train::x_to_cp<T>(static_cast<const T *>(x), x_cs, ly.n, ly.h, ly.w, ly.cin, W.wp, W.n, t->x_cp, t->st),
+           "weight gradient operands");
+    TT_TRY(t, wgrad_tc_launch(W, t->grads + ly.w_off, t->st), "weight gradient (tensor cores)");
+    TT_TRY(t, train::bgrad(dz, dz_cs, (size_t)ly.n * ho * wo, ly.cout, t->grads + ly.b_off, t->st), "bias gradient");
     return TC_OK;
 }
 
@@ -459,9 +499,8 @@ tc_status conv_bwd(tc_trainer *t, const Layer &ly, const void *x, int x_cs, int 
         TT_TRY(t, train::lrelu_bwd2<T>(dy, dy_cs, y, y_cs, ly.leaky != 0, npix, ly.cout, t->dz, dil ? nullptr : t->dzh,
                                        dil ? t->dzh_dil : nullptr, ho, wo, h, w, t->st),
                "activation backward");
-        train::WgradArgs<T> wa{static_cast<const T *>(x), x_cs, n, h, w, ly.cin, ly.stride, ho, wo, t->dz, ly.cout,
-                               ly.cout, t->grads + ly.w_off};
-        TT_TRY(t, train::wgrad<T>(wa, t->grads + ly.b_off, t->st), "weight gradient");
+        tc_status rr = wgrad_tc<T>(t, ly, x, x_cs, t->dz, ly.cout);
+        if (rr != TC_OK) return rr;
         for (int q = 0; q < ly.ndp; ++q) {
             ConvArgs a{dil ? t->dzh_dil : t->dzh, ly.cout, n, h, w, ly.cout, 1, h, w, nullptr, t->zeros, ly.dn[q],
                        dx + ly.dlo[q], dx_cs, 0, 1.f, 0};
@@ -509,8 +548,13 @@ tc_status backward(tc_trainer *t) {
         TT_TRY(t, cudaMemsetAsync(V.dxd, 0, px * V.xdc * 4, t->st), "memset");
         // head: flow = up + conv5([x4 | x3])
         {
-            train::WgradArgs<T> wa{xd, V.xdc, B, V.h, V.w, E[4].cin, 1, V.h, V.w, V.dflow, 2, 2, t->grads + E[4].w_off};
-            TT_TRY(t, train::wgrad<T>(wa, t->grads + E[4].b_off, t->st), "head weight gradient");
+            if (E[4].tc) {
+                if ((r = wgrad_tc<T>(t, E[4], xd, V.xdc, V.dflow, 2)) != TC_OK) return r;
+            } else {
+                train::WgradArgs<T> wa{xd, V.xdc, B, V.h, V.w, E[4].cin, 1, V.h, V.w, V.dflow, 2, 2,
+                                       t->grads + E[4].w_off};
+                TT_TRY(t, train::wgrad<T>(wa, t->grads + E[4].b_off, t->st), "head weight gradient");
+            }
             TT_TRY(t, train::head_dgrad(V.dflow, t->params + E[4].w_off, E[4].cin, B, V.h, V.w, V.dxd, V.xdc, true,
                                         t->st),
                    "head data gradient");
