@@ -603,12 +603,19 @@ def run_train(args):
                    "l2": "per-step working set (activations ~4 GB) > 126 MB L2 (no flush needed)"},
         "latency_ms": {"p50": round(per[len(per) // 2], 3), "p99": round(per[min(len(per) - 1, int(0.99 * len(per)))], 3)},
         "loss": {"before": round(first, 4), "after_steps": round(last, 4), "steps": steps_done},
-        "roofline": {"kernel": "all convs (forward, data and weight gradients) + correlation", "bound": "alu",
-                     "achieved": round(achieved, 2), "peak": round(FP32_SIMT_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
-                     "frac": round(achieved / FP32_SIMT_PEAK_TFLOPS, 4), "traffic": None,
-                     "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2032 MHz (the trainer's convs run "
-                                    "on the CUDA cores)",
-                     "gflop_per_step": round(flops["total"] / 1e9, 1)},
+        "roofline": ({"kernel": "whole training step: all convs (forward, data and weight gradients) + correlation",
+                      "bound": "tensor", "achieved": round(achieved, 2),
+                      "peak": measured_peaks().get("bf16_tflops_sustained"), "unit": "TFLOP/s",
+                      "frac": round(achieved / measured_peaks().get("bf16_tflops_sustained"), 4), "traffic": None,
+                      "peak_source": "of measured bf16 sustained (MEASURED_PEAKS.json); convs, data and weight "
+                                     "gradients run on tcgen05, the rest of the step on the CUDA cores",
+                      "gflop_per_step": round(flops["total"] / 1e9, 1)}
+                     if args.precision != "fp32" else
+                     {"kernel": "whole training step", "bound": "alu", "achieved": round(achieved, 2),
+                      "peak": round(FP32_SIMT_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+                      "frac": round(achieved / FP32_SIMT_PEAK_TFLOPS, 4), "traffic": None,
+                      "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2032 MHz (FP32 trainer on the CUDA cores)",
+                      "gflop_per_step": round(flops["total"] / 1e9, 1)}),
         "clocks": clk,
         "e2e": {"value": round(n_e2e * TRAIN_BATCH / e2e_s, 2), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 8},

@@ -291,7 +291,7 @@ cudaError_t wgrad(const WgradArgs<T> &a, float *db, cudaStream_t st) {
 //   dz_to_cp: out[o][q] = dz of output pixel (y / s, x / s) when s divides y and x
 //   (s = stride), zero elsewhere; dz dense [n_img][ho][wo][cout] float.
 template <typename T>
-__global__ void x_to_cp_kernel(const T *x, int x_cs, int n_img, int h, int w, int cin, int wp, int n,
+__global__ void x_to_cp_kernel(const T *x, int x_cs, int n_img, int h, int w, int cin, int wp, int n, int vec,
                                __nv_bfloat16 *o0, __nv_bfloat16 *o1, __nv_bfloat16 *o2) {
     const long long P = (long long)n_img * (h + 2) * wp;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -302,36 +302,82 @@ __global__ void x_to_cp_kernel(const T *x, int x_cs, int n_img, int h, int w, in
     const long long r = q / wp;
     const int yy = (int)(r % (h + 2)), b = (int)(r / (h + 2));
     const int iy = yy - 1, ix = xx + kx - 2;
-    __nv_bfloat16 *out = kx == 0 ? o0 : (kx == 1 ? o1 : o2);
+    __nv_bfloat16 *out = (kx == 0 ? o0 : (kx == 1 ? o1 : o2)) + q;
     const bool in = iy >= 0 && iy < h && ix >= 0 && ix < w;
     const T *src = x + (((size_t)b * h + (in ? iy : 0)) * w + (in ? ix : 0)) * x_cs;
-    for (int c = 0; c < n; ++c) {
-        const float v = (in && c < cin) ? to_f(src[c]) : 0.f;
-        out[(size_t)c * P + q] = __float2bfloat16_rn(v);
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+    if (vec) {
+        // bf16 input with 16-byte aligned pixels: 8 channels per load; channels past the
+        // pixel stride read as zero (channels in [cin, x_cs) are zero in the buffers)
+        for (int c0 = 0; c0 < n; c0 += 8) {
+            uint4 u = make_uint4(0, 0, 0, 0);
+            if (in && c0 < x_cs) u = *reinterpret_cast<const uint4 *>(src + c0);
+            const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&u);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) out[(size_t)(c0 + k) * P] = c0 + k < cin ? e[k] : zero;
+        }
+    } else {
+        for (int c = 0; c < n; ++c) out[(size_t)c * P] = __float2bfloat16_rn((in && c < cin) ? to_f(src[c]) : 0.f);
     }
+    // the row of ones (bias gradient through the center tap)
+    if (kx == 1 && cin < n) out[(size_t)cin * P] = __float2bfloat16_rn(in ? 1.f : 0.f);
 }
 
-__global__ void dz_to_cp_kernel(const float *dz, int dz_cs, int n_img, int h, int w, int ho, int wo, int stride,
-                                int cout, int wp, __nv_bfloat16 *out) {
+// dz_to_cp also sums each channel over the pixels it moves (the bias gradient): per-thread
+// partial sums for its 4-channel groups, reduced over the block in shared memory, one
+// atomic add per block and channel into db.
+__global__ void __launch_bounds__(256) dz_to_cp_kernel(const float *dz, int dz_cs, int n_img, int h, int w, int ho,
+                                                       int wo, int stride, int cout, int wp, __nv_bfloat16 *out,
+                                                       float *db) {
+    extern __shared__ float bsum[];  // [cout]
+    for (int o = threadIdx.x; o < cout; o += blockDim.x) bsum[o] = 0.f;
+    __syncthreads();
     const long long P = (long long)n_img * (h + 2) * wp;
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= P) return;
-    const int xx = (int)(q % wp);
-    const long long r = q / wp;
-    const int yy = (int)(r % (h + 2)), b = (int)(r / (h + 2));
-    const int iy = yy - 1, ix = xx - 1;
-    bool in = iy >= 0 && iy < h && ix >= 0 && ix < w && iy % stride == 0 && ix % stride == 0;
-    const int oy = iy / stride, ox = ix / stride;
-    in = in && oy < ho && ox < wo;
-    const float *src = dz + (((size_t)b * ho + (in ? oy : 0)) * wo + (in ? ox : 0)) * dz_cs;
-    for (int o = 0; o < cout; ++o) out[(size_t)o * P + q] = __float2bfloat16_rn(in ? src[o] : 0.f);
+    bool in = false;
+    const float *src = dz;
+    if (q < P) {
+        const int xx = (int)(q % wp);
+        const long long r = q / wp;
+        const int yy = (int)(r % (h + 2)), b = (int)(r / (h + 2));
+        const int iy = yy - 1, ix = xx - 1;
+        in = iy >= 0 && iy < h && ix >= 0 && ix < w && iy % stride == 0 && ix % stride == 0;
+        const int oy = iy / stride, ox = ix / stride;
+        in = in && oy < ho && ox < wo;
+        src = dz + (((size_t)b * ho + (in ? oy : 0)) * wo + (in ? ox : 0)) * dz_cs;
+        if ((cout & 3) == 0 && (dz_cs & 3) == 0) {
+            for (int o = 0; o < cout; o += 4) {
+                const float4 v = in ? *reinterpret_cast<const float4 *>(src + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+                out[(size_t)o * P + q] = __float2bfloat16_rn(v.x);
+                out[(size_t)(o + 1) * P + q] = __float2bfloat16_rn(v.y);
+                out[(size_t)(o + 2) * P + q] = __float2bfloat16_rn(v.z);
+                out[(size_t)(o + 3) * P + q] = __float2bfloat16_rn(v.w);
+            }
+        } else {
+            for (int o = 0; o < cout; ++o) out[(size_t)o * P + q] = __float2bfloat16_rn(in ? src[o] : 0.f);
+        }
+    }
+    if (db) {
+        // warp-level sums per channel (lanes are consecutive pixels), then shared, then global
+        const unsigned full = 0xffffffffu;
+        for (int o = 0; o < cout; ++o) {
+            float v = in ? src[o] : 0.f;
+#pragma unroll
+            for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(full, v, m);
+            if ((threadIdx.x & 31) == 0 && v != 0.f) atomicAdd(&bsum[o], v);
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < cout; o += blockDim.x)
+            if (bsum[o] != 0.f) atomicAdd(&db[o], bsum[o]);
+    }
 }
 
 template <typename T>
 cudaError_t x_to_cp(const T *x, int x_cs, int n_img, int h, int w, int cin, int wp, int n, void *const out[3],
                     cudaStream_t st) {
     const long long P = (long long)n_img * (h + 2) * wp;
-    x_to_cp_kernel<T><<<blocks_for((size_t)P * 3), 256, 0, st>>>(x, x_cs, n_img, h, w, cin, wp, n,
+    const int vec = sizeof(T) == 2 && x_cs % 8 == 0 && reinterpret_cast<uintptr_t>(x) % 16 == 0 && n % 8 == 0;
+    x_to_cp_kernel<T><<<blocks_for((size_t)P * 3), 256, 0, st>>>(x, x_cs, n_img, h, w, cin, wp, n, vec,
                                                                 static_cast<__nv_bfloat16 *>(out[0]),
                                                                 static_cast<__nv_bfloat16 *>(out[1]),
                                                                 static_cast<__nv_bfloat16 *>(out[2]));
@@ -339,10 +385,10 @@ cudaError_t x_to_cp(const T *x, int x_cs, int n_img, int h, int w, int cin, int 
 }
 
 cudaError_t dz_to_cp(const float *dz, int dz_cs, int n_img, int h, int w, int ho, int wo, int stride, int cout, int wp,
-                     void *out, cudaStream_t st) {
+                     void *out, float *db, cudaStream_t st) {
     const long long P = (long long)n_img * (h + 2) * wp;
-    dz_to_cp_kernel<<<blocks_for((size_t)P), 256, 0, st>>>(dz, dz_cs, n_img, h, w, ho, wo, stride, cout, wp,
-                                                          static_cast<__nv_bfloat16 *>(out));
+    dz_to_cp_kernel<<<blocks_for((size_t)P), 256, (size_t)cout * sizeof(float), st>>>(
+        dz, dz_cs, n_img, h, w, ho, wo, stride, cout, wp, static_cast<__nv_bfloat16 *>(out), db);
     return cudaGetLastError();
 }
 

@@ -72,7 +72,7 @@ template <typename T>
 cudaError_t x_to_cp(const T *x, int x_cs, int n_img, int h, int w, int cin, int wp, int n, void *const out[3],
                     cudaStream_t st);
 cudaError_t dz_to_cp(const float *dz, int dz_cs, int n_img, int h, int w, int ho, int wo, int stride, int cout, int wp,
-                     void *out, cudaStream_t st);
+                     void *out, float *db, cudaStream_t st);
 cudaError_t bgrad(const float *dz, int dz_cs, size_t P, int cout, float *db, cudaStream_t st);
 template <typename T>
 cudaError_t lrelu_bwd2(const float *dy, int dy_cs, const T *y, int y_cs, bool leaky, size_t npix, int nc, float *dz,

@@ -347,18 +347,18 @@ tc_status build(tc_trainer *t) {
         // weight gradients: CP scratch sized for the largest layer
         size_t max_dz_cp = 0, max_x_cp = 0, max_part = 0;
         for (auto &ly : t->layers) {
-            const int wp = round_up(ly.w + 2, 8), n = round_up(ly.cin, 16);
+            const int wp = round_up(ly.w + 2, 8), n = round_up(ly.cin + 1, 16);
             const long long P = (long long)ly.n * (ly.h + 2) * wp;
             max_dz_cp = std::max(max_dz_cp, (size_t)ly.cout * (size_t)P);
             max_x_cp = std::max(max_x_cp, (size_t)n * (size_t)P);
-            max_part = std::max(max_part, wgrad_tc_partial_floats(P, n));
+            max_part = std::max(max_part, wgrad_tc_partial_floats(P, n, ly.cout));
         }
         if ((r = talloc(t, &t->dz_cp, max_dz_cp * 2)) != TC_OK) return r;
         for (int k = 0; k < 3; ++k)
             if ((r = talloc(t, &t->x_cp[k], max_x_cp * 2)) != TC_OK) return r;
         if ((r = talloc(t, &t->wg_partial, max_part * 4)) != TC_OK) return r;
         for (auto &ly : t->layers) {
-            const int wp = round_up(ly.w + 2, 8), n = round_up(ly.cin, 16);
+            const int wp = round_up(ly.w + 2, 8), n = round_up(ly.cin + 1, 16);  // + the row of ones
             const long long P = (long long)ly.n * (ly.h + 2) * wp;
             std::string why;
             const void *xs[3] = {t->x_cp[0], t->x_cp[1], t->x_cp[2]};
@@ -375,12 +375,12 @@ template <typename T>
 tc_status wgrad_tc(tc_trainer *t, const Layer &ly, const void *x, int x_cs, const float *dz, int dz_cs) {
     const int ho = (ly.h - 1) / ly.stride + 1, wo = (ly.w - 1) / ly.stride + 1;
     const WgradTcPlan &W = ly.wplan;
-    TT_TRY(t, train::dz_to_cp(dz, dz_cs, ly.n, ly.h, ly.w, ho, wo, ly.stride, ly.cout, W.wp, t->dz_cp, t->st),
+    TT_TRY(t, train::dz_to_cp(dz, dz_cs, ly.n, ly.h, ly.w, ho, wo, ly.stride, ly.cout, W.wp, t->dz_cp, nullptr,
+                              t->st),
            "weight gradient operands");
     TT_TRY(t, train::x_to_cp<T>(static_cast<const T *>(x), x_cs, ly.n, ly.h, ly.w, ly.cin, W.wp, W.n, t->x_cp, t->st),
            "weight gradient operands");
-    TT_TRY(t, wgrad_tc_launch(W, t->grads + ly.w_off, t->st), "weight gradient (tensor cores)");
-    TT_TRY(t, train::bgrad(dz, dz_cs, (size_t)ly.n * ho * wo, ly.cout, t->grads + ly.b_off, t->st), "bias gradient");
+    TT_TRY(t, wgrad_tc_launch(W, t->grads + ly.w_off, t->grads + ly.b_off, t->st), "weight gradient (tensor cores)");
     return TC_OK;
 }
 
@@ -494,7 +494,7 @@ tc_status conv_bwd(tc_trainer *t, const Layer &ly, const void *x, int x_cs, int 
     const int ho = (h - 1) / ly.stride + 1, wo = (w - 1) / ly.stride + 1;
     const size_t npix = (size_t)n * ho * wo;
     const bool dil = dx && ly.stride == 2;
-    if (ly.tc && dx && ly.ndp > 0) {
+    if (ly.wplan.enabled && (dx ? (ly.tc && ly.ndp > 0) : true)) {
         if (dil) TT_TRY(t, cudaMemsetAsync(t->dzh_dil, 0, (size_t)n * h * w * ly.cout * 2, t->st), "memset");
         TT_TRY(t, train::lrelu_bwd2<T>(dy, dy_cs, y, y_cs, ly.leaky != 0, npix, ly.cout, t->dz, dil ? nullptr : t->dzh,
                                        dil ? t->dzh_dil : nullptr, ho, wo, h, w, t->st),
