@@ -118,3 +118,40 @@ def test_server_admission_is_decided_before_any_allocation(lib, tmp_path):
     with pytest.raises(lib.TcError) as e:
         lib.Server(str(w), workers=0)
     assert e.value.status == lib.TC_ERR_INVALID_ARG
+
+
+def test_trainer_rejects_bad_arguments(lib, tmp_path):
+    import synth
+    import paper_2301_00750_b300.train as tr
+    spec = synth.NetSpec(chans=(16, 32, 48), radius=3)
+    good = tmp_path / "net.tcw"
+    synth.write_weights(str(good), spec, synth.he_weights(spec, seed=0))
+    for kw, want in [(dict(precision=7), lib.TC_ERR_INVALID_ARG), (dict(batch=0), lib.TC_ERR_INVALID_ARG),
+                     (dict(height=60), lib.TC_ERR_INVALID_ARG), (dict(lr=-1.0), lib.TC_ERR_INVALID_ARG)]:
+        args = dict(batch=2, height=64, width=64, precision="fp32")
+        args.update(kw)
+        hp = {k: args.pop(k) for k in list(args) if k in ("lr",)}
+        with pytest.raises(lib.TcError) as e:
+            tr.Trainer(args["batch"], args["height"], args["width"], args["precision"], weights_path=str(good), **hp)
+        assert e.value.status == want, kw
+    with pytest.raises(lib.TcError) as e:
+        tr.Trainer(2, 64, 64, "fp32", weights_path=str(tmp_path / "missing.tcw"))
+    assert e.value.status == lib.TC_ERR_IO
+    d = tr.default_hparams()
+    assert abs(d["lr"] - 1e-4) < 1e-9 and abs(d["beta1"] - 0.9) < 1e-7 and abs(d["beta2"] - 0.99) < 1e-7
+    assert abs(d["weight_decay"] - 4e-4) < 1e-9
+
+
+def test_training_pairs_carry_their_flow():
+    """a(x) = b(x + F(x)) wherever no rectangle occludes: resampling b along F (cubic
+    B-spline, the generator's own interpolant) reproduces a there."""
+    import numpy as np
+    import synth
+    yy, xx = np.mgrid[0:128, 0:128].astype(float)
+    for seed in range(4):
+        a, b, f = synth.training_pair(seed, size=128, max_flow=16.0)
+        assert a.shape == b.shape == (3, 128, 128) and f.shape == (2, 128, 128)
+        assert np.sqrt((f ** 2).sum(0)).max() <= 16.0 + 1e-4
+        back = synth.resample(b, yy + f[1], xx + f[0])
+        ok = np.abs(back - a).max(0) < 1e-3
+        assert ok.mean() > 0.85, (seed, ok.mean())
