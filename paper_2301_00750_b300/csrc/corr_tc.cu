@@ -27,7 +27,7 @@ constexpr int BX = 16, BY = 8;  // output pixel block: M = 128 rows, row m = py 
 constexpr int BK = 64;          // channels per TMA step (128 B of bf16)
 constexpr int MAX_NCH = 2;      // channels <= 128
 constexpr uint32_t A_BYTES = BX * BY * BK * 2;
-constexpr int STAGE_STRIDE = 49;  // floats per thread slice (48 used; odd stride avoids bank conflicts)
+
 
 enum : int { ERR_CORR_MMA = 5, ERR_CORR_EPILOGUE = 6, ERR_CORR_DRAIN = 7 };
 
@@ -38,9 +38,15 @@ struct Geo {
     static constexpr uint32_t B_BYTES = (uint32_t)NP * BK * 2;
     static constexpr int ND = (2 * R + 1) * (2 * R + 1);
     static constexpr uint32_t TMEM_COLS = NP <= 256 ? 256 : 512;
-    static constexpr size_t SMEM = (size_t)MAX_NCH * (A_BYTES + B_BYTES) + 1024 + 256;
+    // epilogue: every thread stages the WROWS halo rows its warp reads (2 pixel rows + 2R)
+    static constexpr int WROWS = 2 + 2 * R, WCOLS = WROWS * HX;         // 240 for R = 4
+    static constexpr int WLOAD = (WCOLS + 15) / 16 * 16;                // tcgen05.ld x16 granularity
+    static constexpr int SSTRIDE = WLOAD + 1;                            // odd: no bank conflicts
+    static constexpr size_t OPERANDS = (size_t)MAX_NCH * (A_BYTES + B_BYTES);
+    static constexpr size_t SLICES = (size_t)128 * SSTRIDE * 4;
+    static constexpr size_t SMEM = (OPERANDS > SLICES ? OPERANDS : SLICES) + 1024 + 256;
     static_assert(NH % 16 == 0 && NH <= 256, "MMA N");
-    static_assert((2 * (BY / 2 - 1) + 2 * R) * HX + 48 <= NP, "epilogue column window");
+    static_assert(2 * (BY / 2 - 1) * HX + WLOAD <= (int)TMEM_COLS, "epilogue column window inside TMEM");
 };
 
 struct CorrTcLaunch {
@@ -136,32 +142,29 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
     ok = __shfl_sync(0xffffffffu, ok, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-        // The MMAs have completed, so the operand buffers are free: reuse them as the
-        // per-thread slices that turn a window of TMEM columns into indexed values.
-        float *slice = reinterpret_cast<float *>(smem) + threadIdx.x * STAGE_STRIDE;
+        // The MMAs have completed, so the operand buffers are free: reuse them as per-thread
+        // slices.  Warp w's pixel rows 2w, 2w + 1 read halo rows 2w .. 2w + 2R + 1: those
+        // WCOLS contiguous TMEM columns are staged once, then each pixel picks its (2R+1)^2
+        // entries (row dy + (py & 1), columns px + dx of the staged window).
+        float *slice = reinterpret_cast<float *>(smem) + threadIdx.x * G::SSTRIDE;
         const int py = threadIdx.x >> 4, px = threadIdx.x & 15;
         const int y = y0 + py, x = x0 + px;
         const bool valid = y < p.h && x < p.w;
+        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(2 * warp * G::HX);
+#pragma unroll
+        for (int c0 = 0; c0 < G::WLOAD; c0 += 16) {
+            uint32_t r[16];
+            tmem_ld16(ta + (uint32_t)c0, r);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) slice[c0 + i] = __uint_as_float(r[i]);
+        }
         const int base = (py & 1) * G::HX + px;
         float res[G::ND];
 #pragma unroll
         for (int j = 0; j <= 2 * R; ++j) {
-            // halo rows 2 warp + j and 2 warp + j + 1 cover both pixel rows of this warp
-            const uint32_t col0 = (uint32_t)((2 * warp + j) * G::HX);
-            uint32_t r0[16], r1[16], r2[16];
-            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + col0;
-            tmem_ld16(ta, r0);
-            tmem_ld16(ta + 16, r1);
-            tmem_ld16(ta + 32, r2);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                slice[i] = __uint_as_float(r0[i]);
-                slice[16 + i] = __uint_as_float(r1[i]);
-                slice[32 + i] = __uint_as_float(r2[i]);
-            }
 #pragma unroll
             for (int i = 0; i <= 2 * R; ++i) {
-                const float v = slice[base + i] * p.scale;
+                const float v = slice[base + j * G::HX + i] * p.scale;
                 res[j * (2 * R + 1) + i] = v >= 0.f ? v : 0.1f * v;
             }
         }
