@@ -157,13 +157,18 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- GPU arm
 
-def dist_setup():
+def dist_setup(backend=None):
+    """One process per GPU (torchrun env).  NCCL on GPUs; gloo when no GPU is present (the
+    host-side logic is tested that way).  The data path has no collective: every rank runs
+    its own independent streams; only barriers and the max over ranks of the timed region
+    use the process group."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group(backend or ("nccl" if torch.cuda.is_available() else "gloo"))
     return rank, world, local
 
 
@@ -178,9 +183,15 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def weak_scaling_value(units_per_rank, seconds_local, world):
+    """Whole-job throughput: the units all ranks processed / the slowest rank's time."""
+    return world * units_per_rank / max_over_ranks(seconds_local, world)
 
 
 def fp8_scales(tc, path, dev_frames, dev_styl):
@@ -302,6 +313,7 @@ def run_ours(args):
     clk = clocks.stop()
     barrier(world)
     total_s = max_over_ranks(main["total_ms"] / 1e3, world)
+    value = weak_scaling_value(args.steps, main["total_ms"] / 1e3, world)
 
     # Per-stage device times over the same number of steps (events around every launch).
     prof = time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, args.steps, 2, profile=True,
@@ -353,7 +365,7 @@ def run_ours(args):
         peak_source = "of measured HBM copy (MEASURED_PEAKS.json)"
     per = sorted(main["per_frame_ms"])
     line = {
-        "metric": METRIC, "value": round(world * steps / total_s, 3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": steps, "warmup": args.warmup, "ms_per_step": round(total_s * 1e3 / steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp8": "e4m3", "fp32": "f32"}.get(args.precision, args.precision),
