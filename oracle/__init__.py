@@ -55,6 +55,8 @@ def lib():
         _lib.orc_upsample_flow.argtypes = [dp, c_int, c_int, c_int, dp]
         _lib.orc_pad_replicate.argtypes = [dp, c_int, c_int, c_int, c_int, c_int, dp]
         _lib.orc_pyramid.argtypes = [dp, c_int, c_int, c_int, vp, vp]
+        _lib.orc_poisson_grad.argtypes = [c_int, c_int, dp, dp, dp, dp, dp]
+        _lib.orc_poisson_solve.argtypes = [c_int, c_int, c_int, dp, dp, dp, c_double, c_double, c_int, dp]
         _lib.orc_flow.argtypes = [vp, vp, ip, c_int, c_int, c_int, c_int, vp, dp, vp]
         _lib.orc_consistency.argtypes = [c_int, c_int, dp, dp, dp, dp, dp, dp, dp, c_double,
                                          c_double, c_double, c_int, c_double, c_double, dp, dp,
@@ -137,6 +139,24 @@ def consistency(It, Pt, Ip, Pp, Op, Fb, Ff, k1=0.3, alpha=6.5e3, lam=2.0, fb_che
                           int(fb_check), float(c1), float(c2), _p(O), _p(wc),
                           _p(mask, ctypes.c_uint8), _p(band, ctypes.c_uint8), _p(wp))
     return dict(O=O, wc=wc, mask=mask, band=band, wp=wp)
+
+
+def poisson_grad(O, P, A, wc):
+    """Gradient of the screened-Poisson energy (Eq. 1) for one (h, w) channel."""
+    O, P, A, wc = _d(O), _d(P), _d(A), _d(wc)
+    h, w = O.shape
+    g = np.empty((h, w))
+    lib().orc_poisson_grad(h, w, _p(O), _p(P), _p(A), _p(wc), _p(g))
+    return g
+
+
+def poisson_solve(P, A, wc, eta=0.15, kappa=0.2, iters=150):
+    """Eq. 8 SGD-momentum iterations from O = A; P, A (c, h, w), wc (h, w)."""
+    P, A, wc = _d(P), _d(A), _d(wc)
+    c, h, w = P.shape
+    O = np.empty((c, h, w))
+    lib().orc_poisson_solve(c, h, w, _p(P), _p(A), _p(wc), float(eta), float(kappa), int(iters), _p(O))
+    return O
 
 
 def bruteforce_flow(a, b, r):
@@ -246,9 +266,11 @@ def flow_pair(net: Net, I_a, I_b):
 class Stream:
     """Oracle of one video stream (Sec. 3.1): O_1 = P_1; later frames blend along the flow."""
 
-    def __init__(self, net: Net, k1=0.3, alpha=6.5e3, lam=2.0, fb_check=True, c1=FB_C1, c2=FB_C2):
+    def __init__(self, net: Net, k1=0.3, alpha=6.5e3, lam=2.0, fb_check=True, c1=FB_C1, c2=FB_C2,
+                 solver_iters=0, eta=0.15, kappa=0.2):
         self.net = net
         self.params = dict(k1=k1, alpha=alpha, lam=lam, fb_check=fb_check, c1=c1, c2=c2)
+        self.solver = (int(solver_iters), float(eta), float(kappa))
         self.prev = None  # (I, P, O, pyramid)
 
     def step(self, I, P):
@@ -264,6 +286,11 @@ class Stream:
         Fb = np.ascontiguousarray(flow_from_pyramids(self.net, pyr, pyr_p, hp, wp)[:, :h, :w])
         Ff = np.ascontiguousarray(flow_from_pyramids(self.net, pyr_p, pyr, hp, wp)[:, :h, :w])
         r = consistency(I, P, Ip, Pp, Op, Fb, Ff, **self.params)
+        iters, eta, kappa = self.solver
+        if iters > 0:
+            # Eq. 1 solved by Eq. 8 from A_t: the output and the next frame's O_{t-1}
+            r["A"] = r["O"]
+            r["O"] = poisson_solve(P, r["A"], r["wc"], eta=eta, kappa=kappa, iters=iters)
         self.prev = (I, P, r["O"], pyr)
         r.update(Fb=Fb, Ff=Ff)
         return r

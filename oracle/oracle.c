@@ -395,3 +395,59 @@ ORC_API void orc_bruteforce_flow(const double *a, const double *b, int c, int h,
         }
     }
 }
+
+/* Gradient of the screened-Poisson energy of Eq. 1 for one channel (h, w), read as
+ *   E(O) = 1/2 sum over 4-neighbour pixel pairs (i, j) of ((O_i - O_j) - (P_i - P_j))^2
+ *        + 1/2 sum_i wc_i (O_i - A_i)^2,
+ * i.e. dE/dO = Lg (O - P) + wc (O - A), with Lg the graph Laplacian of the image's
+ * 4-neighbour grid: (Lg x)_i = sum over the neighbours j of i that exist of (x_i - x_j)
+ * (Neumann boundary: a border pixel has fewer neighbours). */
+ORC_API void orc_poisson_grad(int h, int w, const double *O, const double *P, const double *A,
+                              const double *wc, double *g)
+{
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < h; ++y) {
+        for (int x = 0; x < w; ++x) {
+            const size_t i = (size_t)y * w + x;
+            const double d = O[i] - P[i];
+            double lap = 0.0;
+            const int ny[4] = {y - 1, y + 1, y, y}, nx[4] = {x, x, x - 1, x + 1};
+            for (int k = 0; k < 4; ++k) {
+                if (ny[k] < 0 || ny[k] >= h || nx[k] < 0 || nx[k] >= w) continue;
+                const size_t j = (size_t)ny[k] * w + nx[k];
+                lap += d - (O[j] - P[j]);
+            }
+            g[i] = lap + wc[i] * (O[i] - A[i]);
+        }
+    }
+}
+
+/* The solver of Sec. 3.1 ("Optimization Solver", Eq. 8): SGD with momentum,
+ *   O^{j+1} = O^j - eta grad E(O^j) + kappa (O^j - O^{j-1}),
+ * started from O^0 = O^{-1} = A, for `iters` iterations, each of the c channels of the
+ * planar (c, h, w) images on its own with the same per-pixel wc (h, w).  O_out (c, h, w). */
+ORC_API void orc_poisson_solve(int c, int h, int w, const double *P, const double *A, const double *wc,
+                               double eta, double kappa, int iters, double *O_out)
+{
+    const size_t hw = (size_t)h * w;
+    double *cur = malloc(sizeof(double) * hw), *prev = malloc(sizeof(double) * hw);
+    double *next = malloc(sizeof(double) * hw), *g = malloc(sizeof(double) * hw);
+    for (int ch = 0; ch < c; ++ch) {
+        const double *Pc = P + ch * hw, *Ac = A + ch * hw;
+        memcpy(cur, Ac, sizeof(double) * hw);
+        memcpy(prev, Ac, sizeof(double) * hw);
+        for (int j = 0; j < iters; ++j) {
+            orc_poisson_grad(h, w, cur, Pc, Ac, wc, g);
+            for (size_t i = 0; i < hw; ++i) next[i] = cur[i] - eta * g[i] + kappa * (cur[i] - prev[i]);
+            double *t = prev;
+            prev = cur;
+            cur = next;
+            next = t;
+        }
+        memcpy(O_out + ch * hw, cur, sizeof(double) * hw);
+    }
+    free(cur);
+    free(prev);
+    free(next);
+    free(g);
+}
