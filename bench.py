@@ -37,6 +37,7 @@ import synth  # noqa: E402
 METRIC = "1080p frames/s (flow+consistency) vs FP32 plain at fixed EPE; p99 frame latency"
 UNIT = "frames/s"
 K1_SWEEP = (0.0, 0.25, 0.5, 0.75, 1.0)
+SOLVER_ITERS = 150  # Eq. 8 iterations per frame in the paper's full method
 WIDTH, HEIGHT = 1920, 1080
 SPEC = dict(chans=(16, 32, 64, 96, 128), radius=4)
 N_FRAMES = 8
@@ -207,7 +208,8 @@ def open_stream(tc, path, W, H, precision, scales):
     return s
 
 
-def time_stream(tc, torch, path, dev_frames, dev_styl, precision, steps, warmup, profile=False, scales=None):
+def time_stream(tc, torch, path, dev_frames, dev_styl, precision, steps, warmup, profile=False, scales=None,
+                solver_iters=0):
     """Runs warmup + steps frames through one stream; returns timings (device events)."""
     H, W = dev_frames[0].shape[1:]
     s = open_stream(tc, path, W, H, precision, scales)
@@ -216,7 +218,7 @@ def time_stream(tc, torch, path, dev_frames, dev_styl, precision, steps, warmup,
     mask = torch.empty((H, W), device="cuda", dtype=torch.uint8)
     step = 0
     for _ in range(warmup):
-        s.set_consistency(k1=K1_SWEEP[step % len(K1_SWEEP)])
+        s.set_consistency(k1=K1_SWEEP[step % len(K1_SWEEP)], solver_iters=solver_iters)
         i = frame_order(step)
         s.process_frame(dev_frames[i], dev_styl[i], O, wc, mask)
         step += 1
@@ -229,7 +231,7 @@ def time_stream(tc, torch, path, dev_frames, dev_styl, precision, steps, warmup,
     torch.cuda.synchronize()
     ev[0].record(stream)
     for k in range(steps):
-        s.set_consistency(k1=K1_SWEEP[step % len(K1_SWEEP)])
+        s.set_consistency(k1=K1_SWEEP[step % len(K1_SWEEP)], solver_iters=solver_iters)
         i = frame_order(step)
         s.process_frame(dev_frames[i], dev_styl[i], O, wc, mask)
         launches += s.launch_count
@@ -323,6 +325,14 @@ def run_ours(args):
         fp32 = time_stream(tc, torch, path, dev_frames, dev_styl, "fp32", max(3, args.steps // 4), 2)
     if args.precision != "fp8" and not args.skip_fp8:
         fp8 = time_stream(tc, torch, path, dev_frames, dev_styl, "fp8", args.steps, 3, scales=scales)
+    solver = None
+    if not args.skip_solver:
+        # the paper's full output: Eq. 1 solved by 150 Eq. 8 iterations after the blend
+        n = max(3, args.steps // 4)
+        solver = (time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 3, solver_iters=SOLVER_ITERS,
+                              scales=scales),
+                  time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 2, profile=True,
+                              solver_iters=SOLVER_ITERS, scales=scales))
     e2e = e2e_host(tc, torch, path, frames, styl, args.precision, max(3, min(args.steps, 50)), 2, scales=scales)
     e2e_v = e2e["value"]
     if world > 1:
@@ -391,6 +401,15 @@ def run_ours(args):
         line["fp8_e4m3"] = {"value": round(len(p8) / (fp8["total_ms"] / 1e3), 3), "unit": UNIT,
                             "p99_ms": round(p8[min(len(p8) - 1, int(0.99 * len(p8)))], 4),
                             "scales": "static, amax/448 from a BF16 pass over frames 0-2"}
+    if solver is not None:
+        sv, svp = solver
+        n = len(sv["per_frame_ms"])
+        ms = svp["profile"]["solver"][0] / n
+        line["with_solver"] = {
+            "value": round(n / (sv["total_ms"] / 1e3), 3), "unit": UNIT, "iters": SOLVER_ITERS,
+            "solver_ms_per_frame": round(ms, 4),
+            "pixel_iterations_per_s": round(WIDTH * HEIGHT * SOLVER_ITERS / (ms / 1e3), 1),
+            "note": "Eq. 1 by Eq. 8 (eta 0.15, kappa 0.2) after the blend, time-blocked 8 iterations per launch"}
     if world == 1 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline_oracle()
     print(json.dumps(line), flush=True)
@@ -645,6 +664,7 @@ def main():
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-fp8", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-solver", action="store_true")
     ap.add_argument("--serve", action="store_true", help="run the multi-stream serving benchmark instead")
     ap.add_argument("--workers", type=int, default=8)
     ap.add_argument("--ring", type=int, default=4, help="output buffers per stream (frames in flight)")

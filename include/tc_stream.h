@@ -75,7 +75,15 @@ typedef enum { TC_FP32 = 0, TC_BF16 = 1, TC_FP8_E4M3 = 2 } tc_precision;
  *   lambda  scale of the consistency weight w_c (Eq. 7).  >= 0
  *   fb_check, fb_c1, fb_c2: forward-backward occlusion test
  *           |Fb + Ff~|^2 > c1 (|Fb|^2 + |Ff~|^2) + c2 marks a pixel occluded (mask 0).
- *   solver_iters, eta, kappa: Eq. 8 settings, reserved; must be 0 / ignored here. */
+ *   solver_iters, eta, kappa: the screened-Poisson solve of Eq. 1 by the SGD-momentum
+ *           iteration of Eq. 8 (Sec. 3.1 "Optimization Solver"): solver_iters = 0 (default)
+ *           returns O_t = A_t (the causal blend); solver_iters > 0 (the paper uses 150)
+ *           runs that many iterations from O = A_t with step eta (> 0, paper 0.15) and
+ *           momentum kappa (in [0, 1), paper 0.2), and O_t (also the next frame's O_{t-1})
+ *           is the last iterate.  The gradient is Lg (O - P_t) + w_c (O - A_t), Lg the
+ *           4-neighbour graph Laplacian with Neumann boundary; w_c of Eq. 7 weighs the
+ *           pull toward A_t, so lambda now matters (the iteration is stable for
+ *           eta (8 + lambda) < 2 (1 + kappa)). */
 typedef struct {
     float k1, k2, alpha, lambda;
     int fb_check;
@@ -206,7 +214,8 @@ enum {
     TC_PROF_UPSAMPLE = 5,        /* x2 flow upsampling */
     TC_PROF_CONSISTENCY = 6,     /* fused warp + mask + blend (Eqs. 2-7) */
     TC_PROF_OTHER = 7,
-    TC_PROF_CATEGORIES = 8
+    TC_PROF_SOLVER = 8,          /* screened-Poisson iterations (Eq. 8) and their output copy */
+    TC_PROF_CATEGORIES = 9
 };
 
 /* Turns per-stage timing on (enable != 0) or off and resets the totals. */
@@ -278,7 +287,16 @@ TC_API tc_status tc_op_consistency(const float *It, const float *Pt, const float
                             int fh, int fw, int scale, const tc_consistency *p, float *O,
                             float *wc_opt, uint8_t *mask_opt, void *cuda_stream);
 
-/* Device bytes held by s (its buffers, packed weights and host-entry staging). */
+/* The screened-Poisson solve of tc_consistency.solver_iters on its own: from O = A, `iters`
+ * iterations of O <- O - eta (Lg (O - P) + wc (O - A)) + kappa (O - O_prev) (Eq. 1, Eq. 8,
+ * Lg the 4-neighbour graph Laplacian, Neumann boundary).  P, A, O: device (c, h, w)
+ * float32 planar, c = 1 or 3; wc: device (h, w).  Allocates temporary device memory and
+ * waits for completion. */
+TC_API tc_status tc_op_poisson_solve(const float *P, const float *A, const float *wc, int c, int h, int w,
+                                     int iters, float eta, float kappa, float *O, void *cuda_stream);
+
+/* Device bytes held by s (its buffers, packed weights and host-entry staging; the solver's
+ * buffers, about 7 x 3 x H x W floats, once solver_iters was first set > 0). */
 TC_API size_t tc_stream_device_bytes(const tc_stream *s);
 
 /* ------------------------------------------------------------------------------------
@@ -323,7 +341,9 @@ TC_API size_t tc_server_bytes_in_use(const tc_server *srv);
  * stream would exceed the HBM budget (nothing is allocated then; retry after a close). */
 TC_API tc_status tc_server_open(tc_server *srv, int width, int height, int *stream_id);
 
-/* Consistency controls of one stream, applied from its next frame to run. */
+/* Consistency controls of one stream, applied from its next frame to run.  Served streams
+ * run the causal path: solver_iters must be 0 (TC_ERR_UNSUPPORTED otherwise; the admission
+ * charge does not cover the solver's buffers). */
 TC_API tc_status tc_server_set_consistency(tc_server *srv, int stream_id, const tc_consistency *p);
 
 /* Queues the next frame of a stream.  I_host, P_host: host (3, H, W) float32; O_host: host

@@ -36,7 +36,7 @@ EXPORTED = ["tc_default_consistency", "tc_create_stream", "tc_set_consistency", 
 E4M3_MAX = 448.0
 NOALLOC_SCRATCH_BYTES = 16 << 20
 PROFILE_CATEGORIES = ["pyramid_conv", "estimator_conv", "head", "correlation", "warp", "upsample", "consistency",
-                      "other"]
+                      "other", "solver"]
 
 
 class TcConsistency(ctypes.Structure):
@@ -73,6 +73,8 @@ _lib.tc_set_profiling.argtypes = [_vp, _i]
 _lib.tc_set_graphs.argtypes = [_vp, _i]
 _lib.tc_op_correlation_bf16_noalloc.argtypes = [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp]
 _lib.tc_synchronize.argtypes = [_vp]
+_lib.tc_op_poisson_solve.argtypes = [_vp, _vp, _vp, _i, _i, _i, _i, _f, _f, _vp, _vp]
+_lib.tc_op_poisson_solve.restype = ctypes.c_int
 _lib.tc_tensor_core_layers.argtypes = [_vp]
 _lib.tc_tensor_core_correlation_levels.argtypes = [_vp]
 _lib.tc_op_last_used_tensor_cores.argtypes = []
@@ -325,6 +327,17 @@ def op_upsample_flow(flow, s, cuda_stream=None):
     _check(_lib.tc_op_upsample_flow(_ptr(flow, torch.float32), n, h, w, s, out.data_ptr(),
                                     _stream_handle(cuda_stream)))
     return out
+
+
+def op_poisson_solve(P, A, wc, iters=150, eta=0.15, kappa=0.2, cuda_stream=None):
+    """Eq. 1 by Eq. 8 from O = A: P, A (c, h, w), wc (h, w) float32 CUDA tensors."""
+    import torch
+    c, h, w = P.shape
+    O = torch.empty_like(P)
+    _check(_lib.tc_op_poisson_solve(_ptr(P, torch.float32, "P"), _ptr(A, torch.float32, "A"),
+                                    _ptr(wc, torch.float32, "wc"), c, h, w, int(iters), float(eta), float(kappa),
+                                    O.data_ptr(), _stream_handle(cuda_stream)))
+    return O
 
 
 def op_consistency(It, Pt, Ip, Pp, Op, Fb, Ff, scale=1, O=None, wc=None, mask=None, cuda_stream=None, **params):

@@ -15,6 +15,7 @@
 #include "common.cuh"
 #include "conv_tc.cuh"
 #include "engine_internal.h"
+#include "solver.cuh"
 #include "corr_tc.cuh"
 
 namespace tc {
@@ -244,10 +245,13 @@ struct tc_stream {
     struct FrameGraph {
         cudaGraph_t g = nullptr;
         cudaGraphExec_t exec = nullptr;
-        cudaGraphNode_t n_first = nullptr, n_cons = nullptr;
-        cudaKernelNodeParams p_first{}, p_cons{};
+        cudaGraphNode_t n_first = nullptr, n_cons = nullptr, n_copy = nullptr;
+        cudaKernelNodeParams p_first{}, p_cons{}, p_copy{};
         int launches = 0;
     } fg[2];
+    // screened-Poisson solver (allocated when first enabled): A_t, w_c, right-hand side and
+    // four iterate planes, each (3, H, W) float (w_c (H, W))
+    float *sv_A = nullptr, *sv_wc = nullptr, *sv_b = nullptr, *sv_s[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 static std::mutex g_err_mu;
@@ -339,14 +343,37 @@ static bool valid_params(const tc_consistency *p, std::string &why) {
     }
     if (p->k1 < 0.f || p->k1 > 1.f) { why = "k1 must lie in [0, 1]"; return false; }
     if (p->alpha < 0.f || p->lambda < 0.f) { why = "alpha and lambda must be >= 0"; return false; }
-    if (p->solver_iters != 0) { why = "the screened-Poisson solver is not part of this library (solver_iters must be 0)"; return false; }
+    if (p->solver_iters < 0 || p->solver_iters > 10000) { why = "solver_iters must lie in [0, 10000]"; return false; }
+    if (p->solver_iters > 0 && (!finite(p->eta) || !finite(p->kappa) || p->eta <= 0.f || p->kappa < 0.f ||
+                                p->kappa >= 1.f)) {
+        why = "the solver needs eta > 0 and 0 <= kappa < 1";
+        return false;
+    }
     return true;
 }
+
+static void release_graphs(tc_stream *s);
 
 extern "C" tc_status tc_set_consistency(tc_stream *s, const tc_consistency *p) {
     if (!s || !p) return fail(s, TC_ERR_INVALID_ARG, "tc_set_consistency: NULL argument");
     std::string why;
     if (!valid_params(p, why)) return fail(s, TC_ERR_INVALID_ARG, why);
+    if (p->solver_iters > 0 && !s->sv_A) {
+        const size_t img = (size_t)3 * s->H * s->W * sizeof(float), plane = (size_t)s->H * s->W * sizeof(float);
+        tc_status r;
+        if ((r = dalloc_t(s, &s->sv_A, img)) != TC_OK || (r = dalloc_t(s, &s->sv_wc, plane)) != TC_OK ||
+            (r = dalloc_t(s, &s->sv_b, img)) != TC_OK)
+            return r;
+        for (int k = 0; k < 4; ++k)
+            if ((r = dalloc_t(s, &s->sv_s[k], img)) != TC_OK) return r;
+    }
+    // the solver's launches are part of a captured frame: a change of its settings needs a
+    // new capture (the consistency controls are updated per frame without one)
+    if (p->solver_iters != s->params.solver_iters ||
+        (p->solver_iters > 0 && (p->eta != s->params.eta || p->kappa != s->params.kappa))) {
+        if (s->st) cudaStreamSynchronize(s->st);
+        release_graphs(s);
+    }
     s->params = *p;
     return TC_OK;
 }
@@ -713,6 +740,12 @@ static ConsistArgs consist_args(tc_stream *s, const float *I, const float *P, fl
     ca.c1 = s->params.fb_c1; ca.c2 = s->params.fb_c2; ca.fb_check = s->params.fb_check;
     ca.O = O; ca.wc = wc; ca.mask = mask;
     ca.sI = s->sI[cur]; ca.sP = s->sP[cur]; ca.sO = s->sO[cur];
+    if (s->t > 0 && s->params.solver_iters > 0) {
+        // A_t and w_c go to the solver's buffers; the solver writes O_t and the kept copy
+        ca.O = s->sv_A;
+        ca.wc = s->sv_wc;
+        ca.sO = nullptr;
+    }
     if (s->t == 0) {
         ca.first = 1;
         ca.Fb = ca.Ff = nullptr;
@@ -739,6 +772,15 @@ static tc_status frame_launches(tc_stream *s, const float *I, const float *P, fl
     if (s->t > 0 && (r = run_estimators<T>(s, cur)) != TC_OK) return r;
     const ConsistArgs ca = consist_args(s, I, P, O, wc, mask, cur);
     TC_LAUNCH_CAT(s, TC_PROF_CONSISTENCY, launch_consistency(ca, s->st));
+    if (s->t > 0 && s->params.solver_iters > 0) {
+        // Eq. 1 by Eq. 8 from A_t; P_t is read from the stream's own copy (written above)
+        PoissonArgs pa{s->sP[cur], s->sv_A, s->sv_wc, 3, s->H, s->W, s->params.solver_iters, s->params.eta,
+                       s->params.kappa, s->sv_b, s->sv_s[0], s->sv_s[1], s->sv_s[2], s->sv_s[3], s->sO[cur],
+                       nullptr};
+        TC_LAUNCH_CAT(s, TC_PROF_SOLVER, launch_poisson(pa, s->st));
+        const size_t hw = (size_t)s->H * s->W;
+        TC_LAUNCH_CAT(s, TC_PROF_SOLVER, launch_copy_out(s->sO[cur], O, 3 * hw, s->sv_wc, wc, hw, s->st));
+    }
     return TC_OK;
 }
 
@@ -774,8 +816,9 @@ static tc_status capture_frame(tc_stream *s, const float *I, const float *P, flo
         TC_TRY(s, cudaGraphKernelNodeGetParams(node, &kp), "cudaGraphKernelNodeGetParams");
         if (kp.func == conv_first_kernel_fn<T>()) { G.n_first = node; G.p_first = kp; }
         if (kp.func == consistency_kernel_fn()) { G.n_cons = node; G.p_cons = kp; }
+        if (kp.func == copy_out_kernel_fn()) { G.n_copy = node; G.p_copy = kp; }
     }
-    if (!G.n_first || !G.n_cons) {
+    if (!G.n_first || !G.n_cons || (s->params.solver_iters > 0 && !G.n_copy)) {
         cudaGraphDestroy(g);
         return fail(s, TC_ERR_STATE, "frame graph: per-frame kernel nodes not found");
     }
@@ -852,6 +895,17 @@ static tc_status process(tc_stream *s, const float *I, const float *P, float *O,
         pc.extra = nullptr;
         TC_TRY(s, cudaGraphExecKernelNodeSetParams(G.exec, G.n_first, &pf), "graph node update");
         TC_TRY(s, cudaGraphExecKernelNodeSetParams(G.exec, G.n_cons, &pc), "graph node update");
+        if (G.n_copy) {
+            // the solver's output copy: retarget it to this frame's O_t and w_c
+            const size_t hw = (size_t)s->H * s->W;
+            const float *src = s->sO[cur], *wsrc = s->sv_wc;
+            size_t n3 = 3 * hw, n1 = hw;
+            void *ka[6] = {&src, &O, &n3, &wsrc, &wc, &n1};
+            cudaKernelNodeParams pk = G.p_copy;
+            pk.kernelParams = ka;
+            pk.extra = nullptr;
+            TC_TRY(s, cudaGraphExecKernelNodeSetParams(G.exec, G.n_copy, &pk), "graph node update");
+        }
     }
     // caller's stream -> library stream -> caller's stream
     TC_TRY(s, cudaEventRecord(s->ev_in, s->st), "cudaEventRecord");
@@ -1302,6 +1356,30 @@ extern "C" tc_status tc_op_upsample_flow(const float *flow, int n, int h, int w,
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     UpArgs u{flow, n, h, w, s, out, nullptr, 0};
     OP_TRY(launch_up<float>(u, st), "tc_op_upsample_flow launch");
+    return TC_OK;
+}
+
+extern "C" tc_status tc_op_poisson_solve(const float *P, const float *A, const float *wc, int c, int h, int w,
+                                         int iters, float eta, float kappa, float *O, void *cuda_stream) {
+    if (!P || !A || !wc || !O || (c != 1 && c != 3) || h < 1 || w < 1 || iters < 0 || iters > 100000 ||
+        !std::isfinite(eta) || !std::isfinite(kappa))
+        return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_poisson_solve: bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const size_t n = (size_t)c * h * w;
+    TmpAlloc tmp;
+    float *b, *s0, *s1, *s2, *s3;
+    OP_TRY(tmp.get((void **)&b, n * 4), "tc_op_poisson_solve alloc");
+    OP_TRY(tmp.get((void **)&s0, n * 4), "tc_op_poisson_solve alloc");
+    OP_TRY(tmp.get((void **)&s1, n * 4), "tc_op_poisson_solve alloc");
+    OP_TRY(tmp.get((void **)&s2, n * 4), "tc_op_poisson_solve alloc");
+    OP_TRY(tmp.get((void **)&s3, n * 4), "tc_op_poisson_solve alloc");
+    if (iters == 0) {
+        OP_TRY(cudaMemcpyAsync(O, A, n * 4, cudaMemcpyDeviceToDevice, st), "tc_op_poisson_solve copy");
+    } else {
+        PoissonArgs pa{P, A, wc, c, h, w, iters, eta, kappa, b, s0, s1, s2, s3, O, nullptr};
+        OP_TRY(launch_poisson(pa, st), "tc_op_poisson_solve launch");
+    }
+    OP_TRY(cudaStreamSynchronize(st), "tc_op_poisson_solve sync");
     return TC_OK;
 }
 

@@ -233,6 +233,9 @@ extern "C" tc_status tc_server_set_consistency(tc_server *srv, int stream_id, co
     std::lock_guard<std::mutex> lk(srv->mu);
     auto it = srv->slots.find(stream_id);
     if (it == srv->slots.end()) return srv_fail(TC_ERR_INVALID_ARG, "tc_server_set_consistency: unknown stream");
+    if (p->solver_iters != 0)
+        // the admission charge covers the causal path; the solver's buffers are not budgeted
+        return srv_fail(TC_ERR_UNSUPPORTED, "tc_server_set_consistency: served streams run without the solver");
     it->second->params = *p;
     it->second->params_dirty = true;
     return TC_OK;
