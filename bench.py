@@ -38,6 +38,7 @@ METRIC = "1080p frames/s (flow+consistency) vs FP32 plain at fixed EPE; p99 fram
 UNIT = "frames/s"
 K1_SWEEP = (0.0, 0.25, 0.5, 0.75, 1.0)
 SOLVER_ITERS = 150  # Eq. 8 iterations per frame in the paper's full method
+SOLVER_FLOPS_PER_PX_ITER = 9  # per channel: neighbour sum (3 adds) and 3 FMAs
 WIDTH, HEIGHT = 1920, 1080
 SPEC = dict(chans=(16, 32, 64, 96, 128), radius=4)
 N_FRAMES = 8
@@ -409,6 +410,13 @@ def run_ours(args):
             "value": round(n / (sv["total_ms"] / 1e3), 3), "unit": UNIT, "iters": SOLVER_ITERS,
             "solver_ms_per_frame": round(ms, 4),
             "pixel_iterations_per_s": round(WIDTH * HEIGHT * SOLVER_ITERS / (ms / 1e3), 1),
+            # 9 flops (3 adds, 3 FMAs) per pixel, channel and iteration, on the CUDA cores
+            "roofline": {"kernel": "solver", "bound": "alu",
+                         "achieved": round(SOLVER_FLOPS_PER_PX_ITER * 3 * WIDTH * HEIGHT * SOLVER_ITERS / (ms / 1e3) / 1e12, 3),
+                         "peak": round(FP32_SIMT_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
+                         "frac": round(SOLVER_FLOPS_PER_PX_ITER * 3 * WIDTH * HEIGHT * SOLVER_ITERS / (ms / 1e3) / 1e12
+                                       / FP32_SIMT_PEAK_TFLOPS, 4),
+                         "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2032 MHz"},
             "note": "Eq. 1 by Eq. 8 (eta 0.15, kappa 0.2) after the blend, time-blocked 8 iterations per launch"}
     if world == 1 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline_oracle()

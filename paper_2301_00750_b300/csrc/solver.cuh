@@ -6,7 +6,7 @@
 
 namespace tc {
 
-// Planar float images (c, h, w), c = 1 or 3; wc (h, w).  b and s0..s3 are scratch of
+// Planar float images (c, h, w), 1 <= c <= 3; wc (h, w).  b and s0..s3 are scratch of
 // c * h * w floats each (none may alias the others or the inputs); O receives the last
 // iterate, O2 (may be NULL) a second copy of it.  iters = 0 computes b only.
 struct PoissonArgs {
@@ -18,7 +18,6 @@ struct PoissonArgs {
 };
 
 cudaError_t launch_poisson(const PoissonArgs &a, cudaStream_t st);
-size_t poisson_smem_bytes(int c);
 
 // dst[i] = src[i] for i < n and wdst[i] = wsrc[i] for i < nw (wdst may be NULL): the
 // solver's output and weights copied to the caller's buffers (a kernel, so that a captured
