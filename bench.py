@@ -248,7 +248,7 @@ def time_stream(tc, torch, path, dev_frames, dev_styl, precision, steps, warmup,
                 tc_corr=tc_corr)
 
 
-def e2e_host(tc, torch, path, frames, styl, precision, steps, warmup, scales=None):
+def e2e_host(tc, torch, path, frames, styl, precision, steps, warmup, scales=None, solver_iters=0):
     """End-to-end through tc_process_frame_host: pinned host I_t, P_t in, O_t out per frame."""
     H, W = frames[0].shape[1:]
     s = open_stream(tc, path, W, H, precision, scales)
@@ -258,12 +258,13 @@ def e2e_host(tc, torch, path, frames, styl, precision, steps, warmup, scales=Non
     step = 0
     for _ in range(warmup):
         i = frame_order(step)
+        s.set_consistency(k1=K1_SWEEP[step % len(K1_SWEEP)], solver_iters=solver_iters)
         s.process_frame_host(hI[i], hP[i], hO)
         step += 1
     t0 = time.perf_counter()
     for _ in range(steps):
         i = frame_order(step)
-        s.set_consistency(k1=K1_SWEEP[step % len(K1_SWEEP)])
+        s.set_consistency(k1=K1_SWEEP[step % len(K1_SWEEP)], solver_iters=solver_iters)
         s.process_frame_host(hI[i], hP[i], hO)
         step += 1
     dt = time.perf_counter() - t0
@@ -312,7 +313,7 @@ def run_ours(args):
     clocks.start()
     time.sleep(0.3)
     main = time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, args.steps, args.warmup,
-                       scales=scales)
+                       scales=scales, solver_iters=args.solver_iters)
     clk = clocks.stop()
     barrier(world)
     total_s = max_over_ranks(main["total_ms"] / 1e3, world)
@@ -320,21 +321,22 @@ def run_ours(args):
 
     # Per-stage device times over the same number of steps (events around every launch).
     prof = time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, args.steps, 2, profile=True,
-                       scales=scales)
+                       scales=scales, solver_iters=args.solver_iters)
     fp32 = fp8 = None
     if args.precision != "fp32" and not args.skip_fp32:
         fp32 = time_stream(tc, torch, path, dev_frames, dev_styl, "fp32", max(3, args.steps // 4), 2)
     if args.precision != "fp8" and not args.skip_fp8:
         fp8 = time_stream(tc, torch, path, dev_frames, dev_styl, "fp8", args.steps, 3, scales=scales)
     solver = None
-    if not args.skip_solver:
+    if not args.skip_solver and args.solver_iters == 0:
         # the paper's full output: Eq. 1 solved by 150 Eq. 8 iterations after the blend
         n = max(3, args.steps // 4)
         solver = (time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 3, solver_iters=SOLVER_ITERS,
                               scales=scales),
                   time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 2, profile=True,
                               solver_iters=SOLVER_ITERS, scales=scales))
-    e2e = e2e_host(tc, torch, path, frames, styl, args.precision, max(3, min(args.steps, 50)), 2, scales=scales)
+    e2e = e2e_host(tc, torch, path, frames, styl, args.precision, max(3, min(args.steps, 50)), 2, scales=scales,
+                   solver_iters=args.solver_iters)
     e2e_v = e2e["value"]
     if world > 1:
         e2e_v = world / max_over_ranks(1.0 / e2e["value"], world)
@@ -354,7 +356,10 @@ def run_ours(args):
     # step.  FP32 streams run on the CUDA cores: derived FP32 FMA peak.
     tensor_path = prof["tc_layers"] > 0 if dom != "correlation" else prof["tc_corr"] > 0
     peaks = measured_peaks()
-    if dom in ("estimator_conv", "pyramid_conv", "head", "correlation"):
+    if dom == "solver":
+        achieved = SOLVER_FLOPS_PER_PX_ITER * 3 * WIDTH * HEIGHT * args.solver_iters * steps / (p[dom][0] / 1e3) / 1e12
+        peak, unit, bound = FP32_SIMT_PEAK_TFLOPS, "TFLOP/s", "alu"
+    elif dom in ("estimator_conv", "pyramid_conv", "head", "correlation"):
         achieved = flops[dom] * steps / (p[dom][0] / 1e3) / 1e12
         if tensor_path and args.precision == "fp8":
             # no measured e4m3 peak: the bf16 one x the nominal dense fp8 : bf16 ratio (4.5 : 2.25)
@@ -383,7 +388,9 @@ def run_ours(args):
         "data": "synthetic (seeded 1080p sequence, He-init weights)",
         "config": {"workload": "1920x1080 RGB stream, lite flow net 5 levels 16/32/64/96/128, radius 4, "
                                "decoder 128/96/64/32/2, both flow directions + fused consistency, k1 swept "
-                               "{0,.25,.5,.75,1}", "frames_resident": N_FRAMES, "streams_per_gpu": 1,
+                               "{0,.25,.5,.75,1}" + (f", then {args.solver_iters} Eq. 8 solver iterations"
+                                                     if args.solver_iters else ""),
+                   "frames_resident": N_FRAMES, "streams_per_gpu": 1,
                    "precision": args.precision, "l2": "per-frame working set > 126 MB L2 (no flush needed)"},
         "latency_ms": {"p50": round(per[len(per) // 2], 4), "p99": round(per[min(len(per) - 1, int(0.99 * len(per)))], 4)},
         "stage_ms_per_frame": {k: round(v[0] / steps, 4) for k, v in p.items() if v[1]},
@@ -673,6 +680,8 @@ def main():
     ap.add_argument("--skip-fp8", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-solver", action="store_true")
+    ap.add_argument("--solver-iters", type=int, default=0,
+                    help="run the timed stream with the Eq. 1 / Eq. 8 solver (default: causal O_t = A_t)")
     ap.add_argument("--serve", action="store_true", help="run the multi-stream serving benchmark instead")
     ap.add_argument("--workers", type=int, default=8)
     ap.add_argument("--ring", type=int, default=4, help="output buffers per stream (frames in flight)")
