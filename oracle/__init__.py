@@ -61,6 +61,9 @@ def lib():
         _lib.orc_consistency.argtypes = [c_int, c_int, dp, dp, dp, dp, dp, dp, dp, c_double,
                                          c_double, c_double, c_int, c_double, c_double, dp, dp,
                                          u8p, u8p, dp]
+        _lib.orc_consistency_next.argtypes = [c_int, c_int, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp,
+                                              c_double, c_double, c_double, c_double, c_int, c_double,
+                                              c_double, dp, dp, u8p, u8p, dp, dp]
         _lib.orc_bruteforce_flow.argtypes = [dp, dp, c_int, c_int, c_int, c_int, ip]
     return _lib
 
@@ -139,6 +142,21 @@ def consistency(It, Pt, Ip, Pp, Op, Fb, Ff, k1=0.3, alpha=6.5e3, lam=2.0, fb_che
                           int(fb_check), float(c1), float(c2), _p(O), _p(wc),
                           _p(mask, ctypes.c_uint8), _p(band, ctypes.c_uint8), _p(wp))
     return dict(O=O, wc=wc, mask=mask, band=band, wp=wp)
+
+
+def consistency_next(It, Pt, Ip, Pp, Op, Fb, Ff, In, Pn, Fn, Fnb, k1=0.3, k2=0.5, alpha=6.5e3, lam=2.0,
+                     fb_check=True, c1=FB_C1, c2=FB_C2):
+    """Consistency step with both temporal neighbours (Eqs. 2-7): Fb = F_{t->t-1},
+    Ff = F_{t-1->t}, Fn = F_{t->t+1}, Fnb = F_{t+1->t}, all (2, h, w).  Returns dict(O, wc,
+    mask (bit 0: M_p, bit 1: M_n), band (same bits), wp, wn)."""
+    arrs = [_d(a) for a in (It, Pt, Ip, Pp, Op, Fb, Ff, In, Pn, Fn, Fnb)]
+    _, h, w = arrs[0].shape
+    O = np.empty((3, h, w)); wc = np.empty((h, w)); wp = np.empty((h, w)); wn = np.empty((h, w))
+    mask = np.empty((h, w), np.uint8); band = np.empty((h, w), np.uint8)
+    lib().orc_consistency_next(h, w, *[_p(a) for a in arrs], float(k1), float(k2), float(alpha), float(lam),
+                               int(fb_check), float(c1), float(c2), _p(O), _p(wc),
+                               _p(mask, ctypes.c_uint8), _p(band, ctypes.c_uint8), _p(wp), _p(wn))
+    return dict(O=O, wc=wc, mask=mask, band=band, wp=wp, wn=wn)
 
 
 def poisson_grad(O, P, A, wc):
@@ -264,17 +282,82 @@ def flow_pair(net: Net, I_a, I_b):
 
 
 class Stream:
-    """Oracle of one video stream (Sec. 3.1): O_1 = P_1; later frames blend along the flow."""
+    """Oracle of one video stream (Sec. 3.1): O_1 = P_1; later frames blend along the flow.
+
+    latency = 0: causal form, step(I_t, P_t) returns frame t (w_n = 0).
+    latency = 1: step(I_{t+1}, P_{t+1}) returns frame t blended with both neighbours (w_n with
+    the clamp k2), None for the first frame of a sequence; flush() returns the last frame
+    (w_n = 0, no next frame) and starts a new sequence."""
 
     def __init__(self, net: Net, k1=0.3, alpha=6.5e3, lam=2.0, fb_check=True, c1=FB_C1, c2=FB_C2,
-                 solver_iters=0, eta=0.15, kappa=0.2):
+                 solver_iters=0, eta=0.15, kappa=0.2, k2=0.5, latency=0):
         self.net = net
         self.params = dict(k1=k1, alpha=alpha, lam=lam, fb_check=fb_check, c1=c1, c2=c2)
+        self.k2 = float(k2)
+        self.latency = int(latency)
         self.solver = (int(solver_iters), float(eta), float(kappa))
         self.prev = None  # (I, P, O, pyramid)
+        # latency 1: frames t-1 and t as (I, P, pyramid), O_{t-1}, flows of the pair (t, t-1)
+        self.hist = []
+        self.O_prev = None
+        self.flows = None
+
+    def _solve(self, r, P):
+        iters, eta, kappa = self.solver
+        if iters > 0:
+            # Eq. 1 solved by Eq. 8 from A_t: the output and the next frame's O_{t-1}
+            r["A"] = r["O"]
+            r["O"] = poisson_solve(P, r["A"], r["wc"], eta=eta, kappa=kappa, iters=iters)
+        return r
+
+    def _first(self, P):
+        _, h, w = P.shape
+        return dict(O=P.copy(), wc=np.zeros((h, w)), mask=np.zeros((h, w), np.uint8),
+                    band=np.zeros((h, w), np.uint8), Fb=None, Ff=None)
+
+    def _step_latency(self, I, P):
+        _, h, w = I.shape
+        hp, wp = padded_size(h, w, self.net.levels)
+        pyr = pyramid(self.net, pad_replicate(I, hp, wp))
+        if not self.hist:
+            self.hist = [(I, P, pyr)]
+            return None
+        It, Pt, pyr_t = self.hist[-1]
+        # the pair (t+1, t): F_{t+1->t} and F_{t->t+1}
+        Fb1 = np.ascontiguousarray(flow_from_pyramids(self.net, pyr, pyr_t, hp, wp)[:, :h, :w])
+        Ff1 = np.ascontiguousarray(flow_from_pyramids(self.net, pyr_t, pyr, hp, wp)[:, :h, :w])
+        if len(self.hist) == 1:
+            r = self._first(Pt)
+        else:
+            Ip, Pp, _ = self.hist[0]
+            Fb, Ff = self.flows
+            r = consistency_next(It, Pt, Ip, Pp, self.O_prev, Fb, Ff, I, P, Ff1, Fb1, k2=self.k2, **self.params)
+            r = self._solve(r, Pt)
+            r.update(Fb=Fb, Ff=Ff, Fn=Ff1, Fnb=Fb1)
+        self.O_prev = r["O"]
+        self.flows = (Fb1, Ff1)
+        self.hist = [self.hist[-1], (I, P, pyr)]
+        return r
+
+    def flush(self):
+        """latency 1: the last frame of the sequence (no next frame: w_n = 0)."""
+        if self.latency != 1 or not self.hist:
+            return None
+        It, Pt, _ = self.hist[-1]
+        if len(self.hist) == 1:
+            r = self._first(Pt)
+        else:
+            Ip, Pp, _ = self.hist[0]
+            Fb, Ff = self.flows
+            r = self._solve(consistency(It, Pt, Ip, Pp, self.O_prev, Fb, Ff, **self.params), Pt)
+            r.update(Fb=Fb, Ff=Ff)
+        self.hist, self.O_prev, self.flows = [], None, None
+        return r
 
     def step(self, I, P):
         I, P = _d(I), _d(P)
+        if self.latency == 1:
+            return self._step_latency(I, P)
         _, h, w = I.shape
         hp, wp = padded_size(h, w, self.net.levels)
         pyr = pyramid(self.net, pad_replicate(I, hp, wp))
@@ -285,12 +368,7 @@ class Stream:
         Ip, Pp, Op, pyr_p = self.prev
         Fb = np.ascontiguousarray(flow_from_pyramids(self.net, pyr, pyr_p, hp, wp)[:, :h, :w])
         Ff = np.ascontiguousarray(flow_from_pyramids(self.net, pyr_p, pyr, hp, wp)[:, :h, :w])
-        r = consistency(I, P, Ip, Pp, Op, Fb, Ff, **self.params)
-        iters, eta, kappa = self.solver
-        if iters > 0:
-            # Eq. 1 solved by Eq. 8 from A_t: the output and the next frame's O_{t-1}
-            r["A"] = r["O"]
-            r["O"] = poisson_solve(P, r["A"], r["wc"], eta=eta, kappa=kappa, iters=iters)
+        r = self._solve(consistency(I, P, Ip, Pp, Op, Fb, Ff, **self.params), P)
         self.prev = (I, P, r["O"], pyr)
         r.update(Fb=Fb, Ff=Ff)
         return r

@@ -354,6 +354,101 @@ ORC_API void orc_consistency(int h, int w, const double *It, const double *Pt, c
     }
 }
 
+/* Validity of the warp of one neighbouring frame at pixel (x, y) along F (Sec. 3.1 with the
+ * non-occlusion mask of reading R6): in bounds and, if fb_check, not occluded by the
+ * forward-backward test against the opposite flow G sampled at x + F(x).  *near is set when
+ * the occlusion decision lies within 1e-6 (1 + |F|^2 + |G~|^2) of its threshold. */
+static int warp_valid(const double *F, const double *G, int h, int w, int x, int y, int fb_check,
+                      double c1, double c2, int *near)
+{
+    const size_t hw = (size_t)h * w, i = (size_t)y * w + x;
+    const double u = F[i], v = F[hw + i];
+    const double sx = x + u, sy = y + v;
+    const int inb = sx >= 0.0 && sx <= w - 1 && sy >= 0.0 && sy <= h - 1;
+    int occ = 0;
+    *near = 0;
+    if (fb_check) {
+        const double gu = bilinear(G, h, w, sx, sy, 0);
+        const double gv = bilinear(G + hw, h, w, sx, sy, 0);
+        const double su = u + gu, sv = v + gv;
+        const double nf = u * u + v * v, ng = gu * gu + gv * gv;
+        const double lhs = su * su + sv * sv, rhs = c1 * (nf + ng) + c2;
+        occ = lhs > rhs;
+        *near = fabs(lhs - rhs) <= 1e-6 * (1.0 + nf + ng);
+    }
+    return inb && !occ;
+}
+
+/* Consistency step of Sec. 3.1 with both temporal neighbours (one frame of latency), per
+ * pixel of frame t:
+ *   Gamma_p = backward warp along Fb = F_{t->t-1}, mask M_p from the test against
+ *             Ff = F_{t-1->t};  Gamma_n = warp along Fn = F_{t->t+1}, mask M_n from the
+ *             test against Fnb = F_{t+1->t} (bilinear, border clamp);
+ *   w_p = M_p min(k1, exp(-alpha |I_t - Gamma_p I_{t-1}|^2)),
+ *   w_n = M_n min(k2, exp(-alpha |I_t - Gamma_n I_{t+1}|^2))                         (Eq. 3)
+ *   L   = (1 - (w_p + w_n)) P_t + w_p Gamma_p P_{t-1} + w_n Gamma_n P_{t+1}             (Eq. 2)
+ *   G   = Gamma_p O_{t-1}                                                            (Eq. 4)
+ *   A   = w_p G + (1 - w_p) L                                                        (Eq. 5)
+ *   A^I = (1 - (w_p + w_n)) I_t + w_p Gamma_p I_{t-1} + w_n Gamma_n I_{t+1}             (Eq. 6)
+ *   w_c = lambda exp(-alpha |I_t - A^I|^2)                                           (Eq. 7)
+ * O = A; mask = M_p | M_n << 1; band bit 0 / bit 1 mark the decisions of M_p / M_n that
+ * lie within FP32 rounding of their threshold.  Images (3, h, w), flows (2, h, w);
+ * band, wp_out, wn_out may be NULL. */
+ORC_API void orc_consistency_next(int h, int w, const double *It, const double *Pt, const double *Ip,
+                                  const double *Pp, const double *Op, const double *Fb, const double *Ff,
+                                  const double *In, const double *Pn, const double *Fn, const double *Fnb,
+                                  double k1, double k2, double alpha, double lambda, int fb_check,
+                                  double c1, double c2, double *O, double *wc, unsigned char *mask,
+                                  unsigned char *band, double *wp_out, double *wn_out)
+{
+    const size_t hw = (size_t)h * w;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < h; ++y) {
+        for (int x = 0; x < w; ++x) {
+            const size_t i = (size_t)y * w + x;
+            int near_p, near_n;
+            const int mp = warp_valid(Fb, Ff, h, w, x, y, fb_check, c1, c2, &near_p);
+            const int mn = warp_valid(Fn, Fnb, h, w, x, y, fb_check, c1, c2, &near_n);
+            const double px = x + Fb[i], py = y + Fb[hw + i];
+            const double nx = x + Fn[i], ny = y + Fn[hw + i];
+            double gIp[3], gPp[3], gOp[3], gIn[3], gPn[3], dp = 0.0, dn = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                gIp[c] = bilinear(Ip + c * hw, h, w, px, py, 0);
+                gPp[c] = bilinear(Pp + c * hw, h, w, px, py, 0);
+                gOp[c] = bilinear(Op + c * hw, h, w, px, py, 0);
+                gIn[c] = bilinear(In + c * hw, h, w, nx, ny, 0);
+                gPn[c] = bilinear(Pn + c * hw, h, w, nx, ny, 0);
+                const double ep = It[c * hw + i] - gIp[c], en = It[c * hw + i] - gIn[c];
+                dp += ep * ep;
+                dn += en * en;
+            }
+            double wp = 0.0, wn = 0.0;
+            if (mp) {
+                wp = exp(-alpha * dp);
+                if (wp > k1) wp = k1;
+            }
+            if (mn) {
+                wn = exp(-alpha * dn);
+                if (wn > k2) wn = k2;
+            }
+            double dI = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                const double Lc = (1.0 - (wp + wn)) * Pt[c * hw + i] + wp * gPp[c] + wn * gPn[c];
+                const double Ac = wp * gOp[c] + (1.0 - wp) * Lc;
+                const double AIc = (1.0 - (wp + wn)) * It[c * hw + i] + wp * gIp[c] + wn * gIn[c];
+                const double e = It[c * hw + i] - AIc;
+                dI += e * e;
+                O[c * hw + i] = Ac;
+            }
+            if (wc) wc[i] = lambda * exp(-alpha * dI);
+            if (mask) mask[i] = (unsigned char)(mp | (mn << 1));
+            if (band) band[i] = (unsigned char)(near_p | (near_n << 1));
+            if (wp_out) wp_out[i] = wp;
+            if (wn_out) wn_out[i] = wn;
+        }
+    }
+}
+
 /* Integer-displacement flow by brute force: for each pixel the displacement d in [-r, r]^2
  * minimising the sum over a 3x3 patch and all channels of (a(x+p) - b(x+p+d))^2, with
  * border clamping; ties go to the smallest |d|^2 and then the smallest index
