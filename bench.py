@@ -209,17 +209,28 @@ def open_stream(tc, path, W, H, precision, scales):
     return s
 
 
+def consistency_controls(step, solver_iters, latency):
+    """k1 swept over K1_SWEEP; with one frame of latency the paper's final k1 = 0.3, k2 = 0.5
+    (k1 + k2 must stay below 1)."""
+    if latency:
+        return dict(k1=0.3, k2=0.5, solver_iters=solver_iters)
+    return dict(k1=K1_SWEEP[step % len(K1_SWEEP)], solver_iters=solver_iters)
+
+
 def time_stream(tc, torch, path, dev_frames, dev_styl, precision, steps, warmup, profile=False, scales=None,
-                solver_iters=0):
+                solver_iters=0, latency=0):
     """Runs warmup + steps frames through one stream; returns timings (device events)."""
     H, W = dev_frames[0].shape[1:]
     s = open_stream(tc, path, W, H, precision, scales)
+    if latency:
+        s.set_consistency(**consistency_controls(0, solver_iters, latency))
+        s.set_latency(latency)
     O = torch.empty((3, H, W), device="cuda")
     wc = torch.empty((H, W), device="cuda")
     mask = torch.empty((H, W), device="cuda", dtype=torch.uint8)
     step = 0
     for _ in range(warmup):
-        s.set_consistency(k1=K1_SWEEP[step % len(K1_SWEEP)], solver_iters=solver_iters)
+        s.set_consistency(**consistency_controls(step, solver_iters, latency))
         i = frame_order(step)
         s.process_frame(dev_frames[i], dev_styl[i], O, wc, mask)
         step += 1
@@ -232,7 +243,7 @@ def time_stream(tc, torch, path, dev_frames, dev_styl, precision, steps, warmup,
     torch.cuda.synchronize()
     ev[0].record(stream)
     for k in range(steps):
-        s.set_consistency(k1=K1_SWEEP[step % len(K1_SWEEP)], solver_iters=solver_iters)
+        s.set_consistency(**consistency_controls(step, solver_iters, latency))
         i = frame_order(step)
         s.process_frame(dev_frames[i], dev_styl[i], O, wc, mask)
         launches += s.launch_count
@@ -248,23 +259,26 @@ def time_stream(tc, torch, path, dev_frames, dev_styl, precision, steps, warmup,
                 tc_corr=tc_corr)
 
 
-def e2e_host(tc, torch, path, frames, styl, precision, steps, warmup, scales=None, solver_iters=0):
+def e2e_host(tc, torch, path, frames, styl, precision, steps, warmup, scales=None, solver_iters=0, latency=0):
     """End-to-end through tc_process_frame_host: pinned host I_t, P_t in, O_t out per frame."""
     H, W = frames[0].shape[1:]
     s = open_stream(tc, path, W, H, precision, scales)
+    if latency:
+        s.set_consistency(**consistency_controls(0, solver_iters, latency))
+        s.set_latency(latency)
     hI = [torch.from_numpy(f).pin_memory() for f in frames]
     hP = [torch.from_numpy(p).pin_memory() for p in styl]
     hO = torch.empty((3, H, W), dtype=torch.float32).pin_memory()
     step = 0
     for _ in range(warmup):
         i = frame_order(step)
-        s.set_consistency(k1=K1_SWEEP[step % len(K1_SWEEP)], solver_iters=solver_iters)
+        s.set_consistency(**consistency_controls(step, solver_iters, latency))
         s.process_frame_host(hI[i], hP[i], hO)
         step += 1
     t0 = time.perf_counter()
     for _ in range(steps):
         i = frame_order(step)
-        s.set_consistency(k1=K1_SWEEP[step % len(K1_SWEEP)], solver_iters=solver_iters)
+        s.set_consistency(**consistency_controls(step, solver_iters, latency))
         s.process_frame_host(hI[i], hP[i], hO)
         step += 1
     dt = time.perf_counter() - t0
@@ -313,7 +327,7 @@ def run_ours(args):
     clocks.start()
     time.sleep(0.3)
     main = time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, args.steps, args.warmup,
-                       scales=scales, solver_iters=args.solver_iters)
+                       scales=scales, solver_iters=args.solver_iters, latency=args.latency)
     clk = clocks.stop()
     barrier(world)
     total_s = max_over_ranks(main["total_ms"] / 1e3, world)
@@ -321,7 +335,7 @@ def run_ours(args):
 
     # Per-stage device times over the same number of steps (events around every launch).
     prof = time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, args.steps, 2, profile=True,
-                       scales=scales, solver_iters=args.solver_iters)
+                       scales=scales, solver_iters=args.solver_iters, latency=args.latency)
     fp32 = fp8 = None
     if args.precision != "fp32" and not args.skip_fp32:
         fp32 = time_stream(tc, torch, path, dev_frames, dev_styl, "fp32", max(3, args.steps // 4), 2)
@@ -335,8 +349,15 @@ def run_ours(args):
                               scales=scales),
                   time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 2, profile=True,
                               solver_iters=SOLVER_ITERS, scales=scales))
+    latency = None
+    if not args.skip_latency and args.latency == 0:
+        # the paper's one-frame-latency form (next frame in Eqs. 2, 3, 6; k1 0.3, k2 0.5)
+        n = max(3, args.steps // 4)
+        latency = (time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 3, scales=scales, latency=1),
+                   time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 3, profile=True,
+                               scales=scales, latency=1))
     e2e = e2e_host(tc, torch, path, frames, styl, args.precision, max(3, min(args.steps, 50)), 2, scales=scales,
-                   solver_iters=args.solver_iters)
+                   solver_iters=args.solver_iters, latency=args.latency)
     e2e_v = e2e["value"]
     if world > 1:
         e2e_v = world / max_over_ranks(1.0 / e2e["value"], world)
@@ -387,9 +408,10 @@ def run_ours(args):
         "dtype": {"fp8": "e4m3", "fp32": "f32"}.get(args.precision, args.precision),
         "data": "synthetic (seeded 1080p sequence, He-init weights)",
         "config": {"workload": "1920x1080 RGB stream, lite flow net 5 levels 16/32/64/96/128, radius 4, "
-                               "decoder 128/96/64/32/2, both flow directions + fused consistency, k1 swept "
-                               "{0,.25,.5,.75,1}" + (f", then {args.solver_iters} Eq. 8 solver iterations"
-                                                     if args.solver_iters else ""),
+                               "decoder 128/96/64/32/2, both flow directions + fused consistency, "
+                               + ("k1 swept {0,.25,.5,.75,1}" if not args.latency else
+                                  "k1 0.3 and k2 0.5 with the next frame (one frame of latency)")
+                               + (f", then {args.solver_iters} Eq. 8 solver iterations" if args.solver_iters else ""),
                    "frames_resident": N_FRAMES, "streams_per_gpu": 1,
                    "precision": args.precision, "l2": "per-frame working set > 126 MB L2 (no flush needed)"},
         "latency_ms": {"p50": round(per[len(per) // 2], 4), "p99": round(per[min(len(per) - 1, int(0.99 * len(per)))], 4)},
@@ -425,6 +447,13 @@ def run_ours(args):
                                        / FP32_SIMT_PEAK_TFLOPS, 4),
                          "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2032 MHz"},
             "note": "Eq. 1 by Eq. 8 (eta 0.15, kappa 0.2) after the blend, time-blocked 8 iterations per launch"}
+    if latency is not None:
+        lt, ltp = latency
+        n = len(lt["per_frame_ms"])
+        line["with_next_frame"] = {
+            "value": round(n / (lt["total_ms"] / 1e3), 3), "unit": UNIT, "latency_frames": 1,
+            "consistency_ms_per_frame": round(ltp["profile"]["consistency"][0] / n, 4),
+            "note": "frame t returned with frame t+1: w_n of Eq. 3 (k2 0.5) in Eqs. 2 and 6, k1 0.3"}
     if world == 1 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline_oracle()
     print(json.dumps(line), flush=True)
@@ -680,6 +709,9 @@ def main():
     ap.add_argument("--skip-fp8", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-solver", action="store_true")
+    ap.add_argument("--skip-latency", action="store_true")
+    ap.add_argument("--latency", type=int, default=0, choices=[0, 1],
+                    help="time the stream with one frame of latency (the next frame in the blend)")
     ap.add_argument("--solver-iters", type=int, default=0,
                     help="run the timed stream with the Eq. 1 / Eq. 8 solver (default: causal O_t = A_t)")
     ap.add_argument("--serve", action="store_true", help="run the multi-stream serving benchmark instead")

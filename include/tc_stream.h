@@ -70,7 +70,9 @@ typedef enum { TC_FP32 = 0, TC_BF16 = 1, TC_FP8_E4M3 = 2 } tc_precision;
 
 /* Consistency controls (Sec. 3.1 "Consistency Control Modes", values of Sec. 4.2).
  *   k1      upper clamp of w_p (Eq. 3); the global/local proportion of A_t.  [0, 1]
- *   k2      upper clamp of w_n (Eq. 3); unused by the causal path (w_n = 0).
+ *   k2      upper clamp of w_n (Eq. 3), the weight of the next frame; used only by streams
+ *           with one frame of latency (tc_set_latency), where k1 + k2 < 1 is required;
+ *           the causal path has w_n = 0.  [0, 1]
  *   alpha   sharpness of the photometric weights (Eqs. 3, 7).  >= 0
  *   lambda  scale of the consistency weight w_c (Eq. 7).  >= 0
  *   fb_check, fb_c1, fb_c2: forward-backward occlusion test
@@ -123,7 +125,8 @@ TC_API void tc_default_consistency(tc_consistency *p);
 TC_API tc_status tc_create_stream(const tc_stream_desc *desc, void *cuda_stream, tc_stream **out);
 
 /* Sets the consistency controls; they apply from the next tc_process_frame call.
- * Errors: TC_ERR_INVALID_ARG (k1 outside [0,1], alpha or lambda negative, NaN). */
+ * Errors: TC_ERR_INVALID_ARG (k1 or k2 outside [0,1], k1 + k2 >= 1 on a stream with one
+ * frame of latency, alpha or lambda negative, NaN, solver settings out of range). */
 TC_API tc_status tc_set_consistency(tc_stream *s, const tc_consistency *p);
 
 /* Processes the next frame.  I_t, P_t: device (3, H, W) float32, read only.  O_t: device
@@ -131,7 +134,12 @@ TC_API tc_status tc_set_consistency(tc_stream *s, const tc_consistency *p);
  * NULL.  mask_opt: device (H, W) uint8 non-occlusion mask M (1 = usable), or NULL.
  * Work is enqueued on the stream's CUDA stream and the call returns without waiting; the
  * library copies what it keeps, so the caller may reuse I_t and P_t once that work has
- * completed.  On the first frame O_t = P_t, w_c = 0 and M = 0. */
+ * completed.  On the first frame O_t = P_t, w_c = 0 and M = 0.
+ * With one frame of latency (tc_set_latency(s, 1)) the frame given is frame t+1 and the
+ * outputs are those of frame t, blended with both neighbours (Eqs. 2-7 with w_n); the
+ * mask then has bit 0 for the previous frame's warp and bit 1 for the next frame's.  The
+ * first call of a sequence writes no output; tc_last_output_frame tells which frame a
+ * call wrote, and tc_flush returns the last frame. */
 TC_API tc_status tc_process_frame(tc_stream *s, const float *I_t, const float *P_t, float *O_t,
                            float *wc_opt, uint8_t *mask_opt);
 
@@ -140,6 +148,27 @@ TC_API tc_status tc_process_frame(tc_stream *s, const float *I_t, const float *P
  * layouts as above; host pointers.  Pinned host memory makes the copies faster. */
 TC_API tc_status tc_process_frame_host(tc_stream *s, const float *I_t, const float *P_t, float *O_t,
                                 float *wc_opt, uint8_t *mask_opt);
+
+/* One frame of latency (Sec. 1, Sec. 3.1: the local term of Eq. 2 also warps the next
+ * frame).  frames = 1: each tc_process_frame call with frame t+1 returns frame t, with w_n
+ * of Eq. 3 (clamped to k2) and the next frame in L_t (Eq. 2) and A^I_t (Eq. 6); the flows
+ * of the pair (t+1, t) computed for the call give F_{t->t+1} and F_{t+1->t}.  frames = 0
+ * (default): the causal path (w_n = 0).  Only before the first frame of a sequence (a new
+ * stream, or after tc_flush).  Errors: TC_ERR_INVALID_ARG (frames not 0 or 1; k1 + k2 >= 1
+ * for frames = 1), TC_ERR_STATE (frames already processed), TC_ERR_OOM. */
+TC_API tc_status tc_set_latency(tc_stream *s, int frames);
+
+/* Streams with one frame of latency: writes the outputs of the last frame given (the
+ * causal blend, as no next frame exists; O = P for a sequence of one frame) into O_t
+ * (device (3, H, W) float32) and the optional wc_opt, mask_opt, and ends the sequence: the
+ * next tc_process_frame starts a new one.  Enqueued on the stream's CUDA stream.
+ * Errors: TC_ERR_STATE (no latency, or no frame pending), TC_ERR_INVALID_ARG (NULL O_t). */
+TC_API tc_status tc_flush(tc_stream *s, float *O_t, float *wc_opt, uint8_t *mask_opt);
+
+/* Index, within its sequence (0 = first frame), of the frame whose outputs the last
+ * tc_process_frame / tc_flush call wrote; -1 if that call wrote none (the first call with
+ * one frame of latency) or for s == NULL. */
+TC_API long long tc_last_output_frame(const tc_stream *s);
 
 /* CUDA graphs (on by default): from the third frame on, a stream replays one captured graph
  * per slot parity -- every launch of the frame in one cudaGraphLaunch -- after updating the
@@ -287,6 +316,18 @@ TC_API tc_status tc_op_consistency(const float *It, const float *Pt, const float
                             int fh, int fw, int scale, const tc_consistency *p, float *O,
                             float *wc_opt, uint8_t *mask_opt, void *cuda_stream);
 
+/* The consistency step with both temporal neighbours (Sec. 3.1, Eqs. 2-7 with w_n clamped
+ * to k2): as tc_op_consistency, plus In, Pn: device (3, h, w) float32 (I_{t+1}, P_{t+1})
+ * and Fn = F_{t->t+1}, Fnb = F_{t+1->t}: device (fh, fw, 2) float32 at the same 1/scale
+ * resolution; Fn warps the next frame and Fnb is its forward-backward test.  mask_opt
+ * receives bit 0 for M_p and bit 1 for M_n.  Errors: TC_ERR_INVALID_ARG as
+ * tc_op_consistency, and k1 + k2 >= 1. */
+TC_API tc_status tc_op_consistency_next(const float *It, const float *Pt, const float *Ip, const float *Pp,
+                                        const float *Op, const float *Fb, const float *Ff, const float *In,
+                                        const float *Pn, const float *Fn, const float *Fnb, int h, int w,
+                                        int fh, int fw, int scale, const tc_consistency *p, float *O,
+                                        float *wc_opt, uint8_t *mask_opt, void *cuda_stream);
+
 /* The screened-Poisson solve of tc_consistency.solver_iters on its own: from O = A, `iters`
  * iterations of O <- O - eta (Lg (O - P) + wc (O - A)) + kappa (O - O_prev) (Eq. 1, Eq. 8,
  * Lg the 4-neighbour graph Laplacian, Neumann boundary).  P, A, O: device (c, h, w)
@@ -296,7 +337,8 @@ TC_API tc_status tc_op_poisson_solve(const float *P, const float *A, const float
                                      int iters, float eta, float kappa, float *O, void *cuda_stream);
 
 /* Device bytes held by s (its buffers, packed weights and host-entry staging; the solver's
- * buffers, about 7 x 3 x H x W floats, once solver_iters was first set > 0). */
+ * buffers, about 7 x 3 x H x W floats, once solver_iters was first set > 0; the kept flows
+ * of one frame of latency, H x W / 4 floats, once tc_set_latency(s, 1) was called). */
 TC_API size_t tc_stream_device_bytes(const tc_stream *s);
 
 /* ------------------------------------------------------------------------------------

@@ -32,7 +32,8 @@ EXPORTED = ["tc_default_consistency", "tc_create_stream", "tc_set_consistency", 
             "tc_op_consistency", "tc_set_profiling", "tc_get_profile", "tc_synchronize", "tc_tensor_core_layers",
             "tc_op_last_used_tensor_cores", "tc_op_correlation_bf16_noalloc",
             "tc_tensor_core_correlation_levels", "tc_set_graphs", "tc_activation_segments",
-            "tc_set_amax_recording", "tc_get_amax", "tc_set_fp8_scales"]
+            "tc_set_amax_recording", "tc_get_amax", "tc_set_fp8_scales", "tc_op_poisson_solve", "tc_set_latency",
+            "tc_flush", "tc_last_output_frame", "tc_op_consistency_next"]
 E4M3_MAX = 448.0
 NOALLOC_SCRATCH_BYTES = 16 << 20
 PROFILE_CATEGORIES = ["pyramid_conv", "estimator_conv", "head", "correlation", "warp", "upsample", "consistency",
@@ -83,9 +84,14 @@ _lib.tc_set_amax_recording.argtypes = [_vp, _i]
 _lib.tc_get_amax.argtypes = [_vp, ctypes.POINTER(_f), _i]
 _lib.tc_set_fp8_scales.argtypes = [_vp, ctypes.POINTER(_f), _i]
 _lib.tc_get_profile.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), _i]
+_lib.tc_set_latency.argtypes = [_vp, _i]
+_lib.tc_flush.argtypes = [_vp, _vp, _vp, _vp]
+_lib.tc_last_output_frame.argtypes = [_vp]
+_lib.tc_last_output_frame.restype = ctypes.c_longlong
+_lib.tc_op_consistency_next.argtypes = [_vp] * 11 + [_i] * 5 + [ctypes.POINTER(TcConsistency), _vp, _vp, _vp, _vp]
 for _n in ["tc_set_amax_recording", "tc_get_amax", "tc_set_fp8_scales", "tc_set_graphs", "tc_op_correlation_bf16_noalloc", "tc_synchronize", "tc_set_profiling", "tc_get_profile", "tc_create_stream", "tc_set_consistency", "tc_process_frame", "tc_process_frame_host", "tc_get_flows",
            "tc_destroy", "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
-           "tc_op_consistency"]:
+           "tc_op_consistency", "tc_set_latency", "tc_flush", "tc_op_consistency_next"]:
     getattr(_lib, _n).restype = ctypes.c_int
 
 
@@ -185,6 +191,22 @@ class Stream:
             return a.ctypes.data
         _check(_lib.tc_process_frame_host(self._h, hp(I, np.float32), hp(P, np.float32), hp(O, np.float32),
                                           hp(wc, np.float32), hp(mask, np.uint8)), self._h)
+
+    def set_latency(self, frames: int):
+        """1: each process_frame with frame t+1 returns frame t blended with both neighbours
+        (w_n, clamp k2); 0: the causal path.  Only before the first frame of a sequence."""
+        _check(_lib.tc_set_latency(self._h, int(frames)), self._h)
+
+    def flush(self, O, wc=None, mask=None):
+        """One frame of latency: the last frame's outputs; ends the sequence."""
+        import torch
+        _check(_lib.tc_flush(self._h, _ptr(O, torch.float32, "O_t"), _ptr(wc, torch.float32, "wc"),
+                             _ptr(mask, torch.uint8, "mask")), self._h)
+
+    @property
+    def last_output_frame(self) -> int:
+        """Index in its sequence of the frame the last call wrote (-1: none)."""
+        return int(_lib.tc_last_output_frame(self._h))
 
     def get_flows(self, Fb=None, Ff=None):
         import torch
@@ -338,6 +360,24 @@ def op_poisson_solve(P, A, wc, iters=150, eta=0.15, kappa=0.2, cuda_stream=None)
                                     _ptr(wc, torch.float32, "wc"), c, h, w, int(iters), float(eta), float(kappa),
                                     O.data_ptr(), _stream_handle(cuda_stream)))
     return O
+
+
+def op_consistency_next(It, Pt, Ip, Pp, Op, Fb, Ff, In, Pn, Fn, Fnb, scale=1, O=None, wc=None, mask=None,
+                        cuda_stream=None, **params):
+    """Images (3, h, w) float32 CUDA; flows (fh, fw, 2) float32 CUDA at 1/scale resolution:
+    Fb = F_{t->t-1}, Ff = F_{t-1->t}, Fn = F_{t->t+1}, Fnb = F_{t+1->t}."""
+    import torch
+    _, h, w = It.shape
+    fh, fw, _ = Fb.shape
+    O = torch.empty_like(It) if O is None else O
+    wc = torch.empty((h, w), device=It.device, dtype=torch.float32) if wc is None else wc
+    mask = torch.empty((h, w), device=It.device, dtype=torch.uint8) if mask is None else mask
+    c = _consistency_struct(**params)
+    f32 = torch.float32
+    _check(_lib.tc_op_consistency_next(*[_ptr(a, f32) for a in (It, Pt, Ip, Pp, Op, Fb, Ff, In, Pn, Fn, Fnb)],
+                                       h, w, fh, fw, scale, ctypes.byref(c), O.data_ptr(), wc.data_ptr(),
+                                       mask.data_ptr(), _stream_handle(cuda_stream)))
+    return O, wc, mask
 
 
 def op_consistency(It, Pt, Ip, Pp, Op, Fb, Ff, scale=1, O=None, wc=None, mask=None, cuda_stream=None, **params):

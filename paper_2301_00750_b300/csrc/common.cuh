@@ -136,7 +136,7 @@ struct UpArgs {
 
 struct ConsistArgs {
     const float *It, *Pt, *Ip, *Pp, *Op;  // planar (3, H, W)
-    const float *Fb, *Ff;                 // (fh, fw, 2)
+    const float *Fb, *Ff;                 // (fh, fw, 2): F_{t->t-1}, F_{t-1->t}
     int H, W, fh, fw, scale;
     float k1, alpha, lambda, c1, c2;
     int fb_check;
@@ -144,6 +144,10 @@ struct ConsistArgs {
     float *O, *wc;
     uint8_t *mask;
     float *sI, *sP, *sO;  // state copies (nullable)
+    // next-frame term (next != 0): frame t+1 and the flows F_{t->t+1}, F_{t+1->t} (fh, fw, 2)
+    int next;
+    const float *In, *Pn, *Fn, *Fnb;
+    float k2;
 };
 
 // Host launchers (return cudaGetLastError()).
@@ -157,7 +161,7 @@ cudaError_t launch_consistency(const ConsistArgs &a, cudaStream_t st);
 // Device entry addresses of the two kernels whose arguments change every frame (used to
 // find their nodes in a captured CUDA graph).
 template <typename T> const void *conv_first_kernel_fn();
-const void *consistency_kernel_fn();
+const void *consistency_kernel_fn(bool next);
 cudaError_t launch_flow_out(const float *flow, int fh, int fw, int scale, int H, int W,
                             float *out, cudaStream_t st);
 template <typename T>

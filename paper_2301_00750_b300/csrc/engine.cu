@@ -245,13 +245,18 @@ struct tc_stream {
     struct FrameGraph {
         cudaGraph_t g = nullptr;
         cudaGraphExec_t exec = nullptr;
-        cudaGraphNode_t n_first = nullptr, n_cons = nullptr, n_copy = nullptr;
-        cudaKernelNodeParams p_first{}, p_cons{}, p_copy{};
+        cudaGraphNode_t n_first = nullptr, n_cons = nullptr, n_copy = nullptr, n_in = nullptr;
+        cudaKernelNodeParams p_first{}, p_cons{}, p_copy{}, p_in{};
         int launches = 0;
     } fg[2];
     // screened-Poisson solver (allocated when first enabled): A_t, w_c, right-hand side and
     // four iterate planes, each (3, H, W) float (w_c (H, W))
     float *sv_A = nullptr, *sv_wc = nullptr, *sv_b = nullptr, *sv_s[4] = {nullptr, nullptr, nullptr, nullptr};
+    // one frame of latency (tc_set_latency): frame t is blended when frame t+1 arrives, with
+    // the final flows of the pair (t, t-1) kept from the previous call ((2, h_2, w_2, 2) float)
+    int latency = 0;
+    float *Fprev = nullptr;
+    long long last_out = -1;  // index in its sequence of the frame the last call wrote
 };
 
 static std::mutex g_err_mu;
@@ -343,6 +348,7 @@ static bool valid_params(const tc_consistency *p, std::string &why) {
     }
     if (p->k1 < 0.f || p->k1 > 1.f) { why = "k1 must lie in [0, 1]"; return false; }
     if (p->alpha < 0.f || p->lambda < 0.f) { why = "alpha and lambda must be >= 0"; return false; }
+    if (!finite(p->k2) || p->k2 < 0.f || p->k2 > 1.f) { why = "k2 must lie in [0, 1]"; return false; }
     if (p->solver_iters < 0 || p->solver_iters > 10000) { why = "solver_iters must lie in [0, 10000]"; return false; }
     if (p->solver_iters > 0 && (!finite(p->eta) || !finite(p->kappa) || p->eta <= 0.f || p->kappa < 0.f ||
                                 p->kappa >= 1.f)) {
@@ -358,6 +364,8 @@ extern "C" tc_status tc_set_consistency(tc_stream *s, const tc_consistency *p) {
     if (!s || !p) return fail(s, TC_ERR_INVALID_ARG, "tc_set_consistency: NULL argument");
     std::string why;
     if (!valid_params(p, why)) return fail(s, TC_ERR_INVALID_ARG, why);
+    if (s->latency && !(p->k1 + p->k2 < 1.f))
+        return fail(s, TC_ERR_INVALID_ARG, "with the next-frame term k1 + k2 must be < 1");
     if (p->solver_iters > 0 && !s->sv_A) {
         const size_t img = (size_t)3 * s->H * s->W * sizeof(float), plane = (size_t)s->H * s->W * sizeof(float);
         tc_status r;
@@ -731,36 +739,75 @@ static tc_status check_stream(tc_stream *s, const char *fn) {
     return TC_OK;
 }
 
+// Arguments of the consistency pass of a call at slot parity cur.  Causal streams blend the
+// frame just given.  Streams with one frame of latency blend the frame before it (its I, P
+// are in the state slot 1 - cur, those of the frame before that in slot cur), with the
+// frame just given as the next frame unless flush (no next frame).
 static ConsistArgs consist_args(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask,
-                                int cur) {
+                                int cur, bool flush = false) {
     ConsistArgs ca{};
-    ca.It = I; ca.Pt = P;
+    const int prev = cur ^ 1;
+    const bool lat = s->latency != 0;
+    const long long n = s->t;  // frames given before this call
+    ca.It = lat ? s->sI[prev] : I;
+    ca.Pt = lat ? s->sP[prev] : P;
     ca.H = s->H; ca.W = s->W;
     ca.k1 = s->params.k1; ca.alpha = s->params.alpha; ca.lambda = s->params.lambda;
     ca.c1 = s->params.fb_c1; ca.c2 = s->params.fb_c2; ca.fb_check = s->params.fb_check;
+    ca.k2 = s->params.k2;
     ca.O = O; ca.wc = wc; ca.mask = mask;
-    ca.sI = s->sI[cur]; ca.sP = s->sP[cur]; ca.sO = s->sO[cur];
-    if (s->t > 0 && s->params.solver_iters > 0) {
+    // latency: the caller's inputs are copied into the state after this pass
+    ca.sI = lat ? nullptr : s->sI[cur];
+    ca.sP = lat ? nullptr : s->sP[cur];
+    ca.sO = s->sO[cur];
+    const bool first = lat ? n == 1 : n == 0;
+    if (!first && s->params.solver_iters > 0) {
         // A_t and w_c go to the solver's buffers; the solver writes O_t and the kept copy
         ca.O = s->sv_A;
         ca.wc = s->sv_wc;
         ca.sO = nullptr;
     }
-    if (s->t == 0) {
+    if (first) {
         ca.first = 1;
         ca.Fb = ca.Ff = nullptr;
         ca.fh = ca.fw = 1; ca.scale = 1;
         ca.Ip = ca.Pp = ca.Op = nullptr;
-    } else {
-        const int prev = cur ^ 1;
-        LevelBufs &B2 = s->lv[1];
-        ca.first = 0;
-        ca.Ip = s->sI[prev]; ca.Pp = s->sP[prev]; ca.Op = s->sO[prev];
+        return ca;
+    }
+    LevelBufs &B2 = s->lv[1];
+    const size_t half = (size_t)B2.h * B2.w * 2;
+    ca.first = 0;
+    ca.Ip = lat ? s->sI[cur] : s->sI[prev];
+    ca.Pp = lat ? s->sP[cur] : s->sP[prev];
+    ca.Op = s->sO[prev];
+    ca.fh = B2.h; ca.fw = B2.w; ca.scale = 4;
+    if (!lat) {
         ca.Fb = B2.flow;
-        ca.Ff = B2.flow + (size_t)B2.h * B2.w * 2;
-        ca.fh = B2.h; ca.fw = B2.w; ca.scale = 4;
+        ca.Ff = B2.flow + half;
+        return ca;
+    }
+    // the pair (t, t-1) from the previous call; the pair (t+1, t) just computed
+    ca.Fb = s->Fprev;
+    ca.Ff = s->Fprev + half;
+    if (!flush) {
+        ca.next = 1;
+        ca.In = I;
+        ca.Pn = P;
+        ca.Fn = B2.flow + half;  // F_{t->t+1}
+        ca.Fnb = B2.flow;        // F_{t+1->t}
     }
     return ca;
+}
+
+// The solver after the consistency pass (A_t, w_c in its buffers), then the copy of O_t and
+// w_c to the caller.  P is P_t.
+static tc_status solver_launches(tc_stream *s, const float *P, float *O, float *wc, int cur) {
+    PoissonArgs pa{P, s->sv_A, s->sv_wc, 3, s->H, s->W, s->params.solver_iters, s->params.eta, s->params.kappa,
+                   s->sv_b, s->sv_s[0], s->sv_s[1], s->sv_s[2], s->sv_s[3], s->sO[cur], nullptr};
+    TC_LAUNCH_CAT(s, TC_PROF_SOLVER, launch_poisson(pa, s->st));
+    const size_t hw = (size_t)s->H * s->W;
+    TC_LAUNCH_CAT(s, TC_PROF_SOLVER, launch_copy_out(s->sO[cur], O, 3 * hw, s->sv_wc, wc, hw, s->st, 0));
+    return TC_OK;
 }
 
 // Every launch of one frame, in order.
@@ -770,16 +817,28 @@ static tc_status frame_launches(tc_stream *s, const float *I, const float *P, fl
     tc_status r;
     if ((r = run_pyramid<T>(s, I, cur)) != TC_OK) return r;
     if (s->t > 0 && (r = run_estimators<T>(s, cur)) != TC_OK) return r;
-    const ConsistArgs ca = consist_args(s, I, P, O, wc, mask, cur);
-    TC_LAUNCH_CAT(s, TC_PROF_CONSISTENCY, launch_consistency(ca, s->st));
-    if (s->t > 0 && s->params.solver_iters > 0) {
+    if (!s->latency) {
+        const ConsistArgs ca = consist_args(s, I, P, O, wc, mask, cur);
+        TC_LAUNCH_CAT(s, TC_PROF_CONSISTENCY, launch_consistency(ca, s->st));
         // Eq. 1 by Eq. 8 from A_t; P_t is read from the stream's own copy (written above)
-        PoissonArgs pa{s->sP[cur], s->sv_A, s->sv_wc, 3, s->H, s->W, s->params.solver_iters, s->params.eta,
-                       s->params.kappa, s->sv_b, s->sv_s[0], s->sv_s[1], s->sv_s[2], s->sv_s[3], s->sO[cur],
-                       nullptr};
-        TC_LAUNCH_CAT(s, TC_PROF_SOLVER, launch_poisson(pa, s->st));
-        const size_t hw = (size_t)s->H * s->W;
-        TC_LAUNCH_CAT(s, TC_PROF_SOLVER, launch_copy_out(s->sO[cur], O, 3 * hw, s->sv_wc, wc, hw, s->st));
+        if (s->t > 0 && s->params.solver_iters > 0 && (r = solver_launches(s, s->sP[cur], O, wc, cur)) != TC_OK)
+            return r;
+        return TC_OK;
+    }
+    // one frame of latency: frame t = (frames given before) - 1 is blended now
+    if (s->t > 0) {
+        const ConsistArgs ca = consist_args(s, I, P, O, wc, mask, cur);
+        TC_LAUNCH_CAT(s, TC_PROF_CONSISTENCY, launch_consistency(ca, s->st));
+        if (s->t > 1 && s->params.solver_iters > 0 && (r = solver_launches(s, s->sP[cur ^ 1], O, wc, cur)) != TC_OK)
+            return r;
+    }
+    const size_t img = (size_t)3 * s->H * s->W;
+    TC_LAUNCH_CAT(s, TC_PROF_CONSISTENCY, launch_copy_out(I, s->sI[cur], img, P, s->sP[cur], img, s->st, 1));
+    if (s->t > 0) {
+        LevelBufs &B2 = s->lv[1];
+        TC_TRY(s, cudaMemcpyAsync(s->Fprev, B2.flow, (size_t)B2.h * B2.w * 4 * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, s->st),
+               "flow copy");
     }
     return TC_OK;
 }
@@ -815,10 +874,11 @@ static tc_status capture_frame(tc_stream *s, const float *I, const float *P, flo
         cudaKernelNodeParams kp{};
         TC_TRY(s, cudaGraphKernelNodeGetParams(node, &kp), "cudaGraphKernelNodeGetParams");
         if (kp.func == conv_first_kernel_fn<T>()) { G.n_first = node; G.p_first = kp; }
-        if (kp.func == consistency_kernel_fn()) { G.n_cons = node; G.p_cons = kp; }
-        if (kp.func == copy_out_kernel_fn()) { G.n_copy = node; G.p_copy = kp; }
+        if (kp.func == consistency_kernel_fn(s->latency != 0)) { G.n_cons = node; G.p_cons = kp; }
+        if (kp.func == copy_out_kernel_fn(0)) { G.n_copy = node; G.p_copy = kp; }
+        if (kp.func == copy_out_kernel_fn(1)) { G.n_in = node; G.p_in = kp; }
     }
-    if (!G.n_first || !G.n_cons || (s->params.solver_iters > 0 && !G.n_copy)) {
+    if (!G.n_first || !G.n_cons || (s->params.solver_iters > 0 && !G.n_copy) || (s->latency && !G.n_in)) {
         cudaGraphDestroy(g);
         return fail(s, TC_ERR_STATE, "frame graph: per-frame kernel nodes not found");
     }
@@ -868,10 +928,12 @@ static tc_status process(tc_stream *s, const float *I, const float *P, float *O,
     const int cur = (int)(s->t & 1);
     // The first two frames run eagerly (the first has no flow; the second sets every kernel
     // attribute); later frames replay the graph of their parity.  Profiling runs eagerly.
+    const long long out = s->latency ? s->t - 1 : s->t;
     if (!s->graphs || s->prof || s->t < 2 || s->rec_amax) {
         if ((r = frame_launches<T>(s, I, P, O, wc, mask, cur)) != TC_OK) return r;
         if (s->rec_amax && (r = record_amax<T>(s, cur)) != TC_OK) return r;
         s->t += 1;
+        s->last_out = out;
         return TC_OK;
     }
     tc_stream::FrameGraph &G = s->fg[cur];
@@ -906,6 +968,17 @@ static tc_status process(tc_stream *s, const float *I, const float *P, float *O,
             pk.extra = nullptr;
             TC_TRY(s, cudaGraphExecKernelNodeSetParams(G.exec, G.n_copy, &pk), "graph node update");
         }
+        if (G.n_in) {
+            // the copy of this frame's inputs into the state (one frame of latency)
+            const size_t img = (size_t)3 * s->H * s->W;
+            float *dI = s->sI[cur], *dP = s->sP[cur];
+            size_t n3 = img;
+            void *ka[6] = {&I, &dI, &n3, &P, &dP, &n3};
+            cudaKernelNodeParams pk = G.p_in;
+            pk.kernelParams = ka;
+            pk.extra = nullptr;
+            TC_TRY(s, cudaGraphExecKernelNodeSetParams(G.exec, G.n_in, &pk), "graph node update");
+        }
     }
     // caller's stream -> library stream -> caller's stream
     TC_TRY(s, cudaEventRecord(s->ev_in, s->st), "cudaEventRecord");
@@ -915,6 +988,7 @@ static tc_status process(tc_stream *s, const float *I, const float *P, float *O,
     TC_TRY(s, cudaStreamWaitEvent(s->st, s->ev_out, 0), "cudaStreamWaitEvent");
     s->launches = G.launches;
     s->t += 1;
+    s->last_out = out;
     return TC_OK;
 }
 
@@ -1074,12 +1148,56 @@ extern "C" tc_status tc_process_frame_host(tc_stream *s, const float *I_t, const
     TC_TRY(s, cudaMemcpyAsync(s->hP, P_t, img, cudaMemcpyHostToDevice, s->st), "H2D P_t");
     r = tc_process_frame(s, s->hI, s->hP, s->hO, wc_opt ? s->hwc : nullptr, mask_opt ? s->hmask : nullptr);
     if (r != TC_OK) return r;
+    if (s->last_out < 0) {  // one frame of latency: the first call writes nothing
+        TC_TRY(s, cudaStreamSynchronize(s->st), "stream synchronize");
+        return check_device_error(s);
+    }
     TC_TRY(s, cudaMemcpyAsync(O_t, s->hO, img, cudaMemcpyDeviceToHost, s->st), "D2H O_t");
     if (wc_opt) TC_TRY(s, cudaMemcpyAsync(wc_opt, s->hwc, plane * sizeof(float), cudaMemcpyDeviceToHost, s->st), "D2H w_c");
     if (mask_opt) TC_TRY(s, cudaMemcpyAsync(mask_opt, s->hmask, plane, cudaMemcpyDeviceToHost, s->st), "D2H mask");
     TC_TRY(s, cudaStreamSynchronize(s->st), "stream synchronize");
     return check_device_error(s);
 }
+
+extern "C" tc_status tc_set_latency(tc_stream *s, int frames) {
+    tc_status r = check_stream(s, "tc_set_latency");
+    if (r != TC_OK) return r;
+    if (frames != 0 && frames != 1) return fail(s, TC_ERR_INVALID_ARG, "tc_set_latency: frames must be 0 or 1");
+    if (s->t != 0) return fail(s, TC_ERR_STATE, "tc_set_latency: only before the first frame of a sequence");
+    if (frames == 1 && !(s->params.k1 + s->params.k2 < 1.f))
+        return fail(s, TC_ERR_INVALID_ARG, "with the next-frame term k1 + k2 must be < 1");
+    if (frames == 1 && !s->Fprev) {
+        const LevelBufs &B2 = s->lv[1];
+        if ((r = dalloc_t(s, &s->Fprev, (size_t)B2.h * B2.w * 4 * sizeof(float))) != TC_OK) return r;
+    }
+    if (frames != s->latency) {
+        TC_TRY(s, cudaStreamSynchronize(s->st), "stream synchronize");
+        release_graphs(s);
+    }
+    s->latency = frames;
+    s->last_out = -1;
+    return TC_OK;
+}
+
+extern "C" tc_status tc_flush(tc_stream *s, float *O_t, float *wc_opt, uint8_t *mask_opt) {
+    tc_status r = check_stream(s, "tc_flush");
+    if (r != TC_OK) return r;
+    if (!s->latency) return fail(s, TC_ERR_STATE, "tc_flush: the stream has no frame of latency");
+    if (s->t == 0) return fail(s, TC_ERR_STATE, "tc_flush: no frame pending");
+    if (!O_t) return fail(s, TC_ERR_INVALID_ARG, "tc_flush: NULL image pointer");
+    s->launches = 0;
+    const int cur = (int)(s->t & 1);
+    // the last frame has no next frame: the causal blend with the kept flows
+    const ConsistArgs ca = consist_args(s, nullptr, nullptr, O_t, wc_opt, mask_opt, cur, true);
+    TC_LAUNCH_CAT(s, TC_PROF_CONSISTENCY, launch_consistency(ca, s->st));
+    if (s->t > 1 && s->params.solver_iters > 0 && (r = solver_launches(s, s->sP[cur ^ 1], O_t, wc_opt, cur)) != TC_OK)
+        return r;
+    s->last_out = s->t - 1;
+    s->t = 0;
+    return TC_OK;
+}
+
+extern "C" long long tc_last_output_frame(const tc_stream *s) { return s ? s->last_out : -1; }
 
 extern "C" tc_status tc_get_flows(tc_stream *s, float *Fb, float *Ff) {
     tc_status r = check_stream(s, "tc_get_flows");
@@ -1399,5 +1517,28 @@ extern "C" tc_status tc_op_consistency(const float *It, const float *Pt, const f
     ca.fb_check = p->fb_check; ca.first = 0;
     ca.O = O; ca.wc = wc_opt; ca.mask = mask_opt;
     OP_TRY(launch_consistency(ca, static_cast<cudaStream_t>(cuda_stream)), "tc_op_consistency launch");
+    return TC_OK;
+}
+
+extern "C" tc_status tc_op_consistency_next(const float *It, const float *Pt, const float *Ip, const float *Pp,
+                                            const float *Op, const float *Fb, const float *Ff, const float *In,
+                                            const float *Pn, const float *Fn, const float *Fnb, int h, int w,
+                                            int fh, int fw, int scale, const tc_consistency *p, float *O,
+                                            float *wc_opt, uint8_t *mask_opt, void *cuda_stream) {
+    if (!It || !Pt || !Ip || !Pp || !Op || !Fb || !Ff || !In || !Pn || !Fn || !Fnb || !p || !O || h < 1 || w < 1 ||
+        fh < 1 || fw < 1 || scale < 1 || (scale & (scale - 1)) != 0 || (size_t)fh * scale < (size_t)h ||
+        (size_t)fw * scale < (size_t)w)
+        return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_consistency_next: bad argument");
+    std::string why;
+    if (!valid_params(p, why)) return fail(nullptr, TC_ERR_INVALID_ARG, why);
+    if (!(p->k1 + p->k2 < 1.f)) return fail(nullptr, TC_ERR_INVALID_ARG, "with the next-frame term k1 + k2 must be < 1");
+    ConsistArgs ca{};
+    ca.It = It; ca.Pt = Pt; ca.Ip = Ip; ca.Pp = Pp; ca.Op = Op; ca.Fb = Fb; ca.Ff = Ff;
+    ca.In = In; ca.Pn = Pn; ca.Fn = Fn; ca.Fnb = Fnb; ca.next = 1; ca.k2 = p->k2;
+    ca.H = h; ca.W = w; ca.fh = fh; ca.fw = fw; ca.scale = scale;
+    ca.k1 = p->k1; ca.alpha = p->alpha; ca.lambda = p->lambda; ca.c1 = p->fb_c1; ca.c2 = p->fb_c2;
+    ca.fb_check = p->fb_check; ca.first = 0;
+    ca.O = O; ca.wc = wc_opt; ca.mask = mask_opt;
+    OP_TRY(launch_consistency(ca, static_cast<cudaStream_t>(cuda_stream)), "tc_op_consistency_next launch");
     return TC_OK;
 }

@@ -1,8 +1,8 @@
-// Fused consistency step (Sec. 3.1, Eqs. 2-7 in causal form): final flow upsampling,
-// backward warp of I_{t-1}, P_{t-1}, O_{t-1}, forward-backward non-occlusion mask,
-// photometric weight, local/global blend, warped input and consistency weight, plus the
-// copies of I_t, P_t, O_t that the stream keeps for the next frame.  One pass over the
-// frame, one thread per pixel, float32 throughout.
+// Fused consistency step (Sec. 3.1, Eqs. 2-7, causal or with the next frame): final flow
+// upsampling, backward warp of I_{t-1}, P_{t-1}, O_{t-1} (and of I_{t+1}, P_{t+1}),
+// forward-backward non-occlusion masks, photometric weights, local/global blend, warped
+// input and consistency weight, plus the copies of I_t, P_t, O_t that the stream keeps for
+// the next frame.  One pass over the frame, one thread per pixel, float32 throughout.
 #include "common.cuh"
 
 namespace tc {
@@ -39,43 +39,24 @@ __device__ __forceinline__ float gather(const float *p, int W, const Taps &t) {
     return acc;
 }
 
-__global__ void __launch_bounds__(256) consistency_kernel(ConsistArgs a) {
-    const int x = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
-    if (x >= a.W || y >= a.H) return;
-    const size_t hw = (size_t)a.H * a.W;
-    const size_t i = (size_t)y * a.W + x;
-    float It[3], Pt[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        It[c] = __ldg(a.It + c * hw + i);
-        Pt[c] = __ldg(a.Pt + c * hw + i);
-    }
-    if (a.first) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            a.O[c * hw + i] = Pt[c];
-            if (a.sI) a.sI[c * hw + i] = It[c];
-            if (a.sP) a.sP[c * hw + i] = Pt[c];
-            if (a.sO) a.sO[c * hw + i] = Pt[c];
-        }
-        if (a.wc) a.wc[i] = 0.f;
-        if (a.mask) a.mask[i] = 0;
-        return;
-    }
-    float2 fb = upsampled_flow_at(a.Fb, a.fh, a.fw, a.scale, x, y);
+// The warp of a neighbouring frame along F at (x, y): taps, and whether it is valid (in
+// bounds and, with fb_check, not occluded by the forward-backward test against the
+// opposite flow G sampled at the taps).
+__device__ __forceinline__ bool warp_sample(const float *F, const float *G, const ConsistArgs &a, int x, int y,
+                                            Taps &t) {
+    const float2 f = upsampled_flow_at(F, a.fh, a.fw, a.scale, x, y);
     // Keep the sample position finite and far outside the frame for absurd flows.
-    const float u = fminf(fmaxf(fb.x, -1e6f), 1e6f), v = fminf(fmaxf(fb.y, -1e6f), 1e6f);
+    const float u = fminf(fmaxf(f.x, -1e6f), 1e6f), v = fminf(fmaxf(f.y, -1e6f), 1e6f);
     // In bounds: 0 <= x + u <= W - 1 and 0 <= y + v <= H - 1, compared exactly.
     const bool inb = u >= (float)(-x) && u <= (float)(a.W - 1 - x) && v >= (float)(-y) &&
                      v <= (float)(a.H - 1 - y);
-    const Taps t = clamp_taps(x, y, u, v, a.W, a.H);
+    t = clamp_taps(x, y, u, v, a.W, a.H);
     bool occ = false;
     if (a.fb_check) {
-        const float2 f00 = upsampled_flow_at(a.Ff, a.fh, a.fw, a.scale, t.xa, t.ya);
-        const float2 f01 = upsampled_flow_at(a.Ff, a.fh, a.fw, a.scale, t.xb, t.ya);
-        const float2 f10 = upsampled_flow_at(a.Ff, a.fh, a.fw, a.scale, t.xa, t.yb);
-        const float2 f11 = upsampled_flow_at(a.Ff, a.fh, a.fw, a.scale, t.xb, t.yb);
+        const float2 f00 = upsampled_flow_at(G, a.fh, a.fw, a.scale, t.xa, t.ya);
+        const float2 f01 = upsampled_flow_at(G, a.fh, a.fw, a.scale, t.xb, t.ya);
+        const float2 f10 = upsampled_flow_at(G, a.fh, a.fw, a.scale, t.xa, t.yb);
+        const float2 f11 = upsampled_flow_at(G, a.fh, a.fw, a.scale, t.xb, t.yb);
         float fu = t.w00 * f00.x;
         fu += t.w01 * f01.x;
         fu += t.w10 * f10.x;
@@ -89,7 +70,38 @@ __global__ void __launch_bounds__(256) consistency_kernel(ConsistArgs a) {
         const float rhs = a.c1 * ((u * u + v * v) + (fu * fu + fv * fv)) + a.c2;
         occ = lhs > rhs;
     }
-    const bool m = inb && !occ;
+    return inb && !occ;
+}
+
+// NEXT = false: causal form (w_n = 0).  NEXT = true: frame t+1 warped along F_{t->t+1}
+// enters L_t and A^I_t with the weight w_n (Eqs. 2, 3, 6); the mask gets bit 1 for it.
+template <bool NEXT>
+__global__ void __launch_bounds__(256) consistency_kernel(ConsistArgs a) {
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (x >= a.W || y >= a.H) return;
+    const size_t hw = (size_t)a.H * a.W;
+    const size_t i = (size_t)y * a.W + x;
+    float It[3], Pt[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        It[c] = __ldg(a.It + c * hw + i);
+        Pt[c] = __ldg(a.Pt + c * hw + i);
+    }
+    if (!NEXT && a.first) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a.O[c * hw + i] = Pt[c];
+            if (a.sI) a.sI[c * hw + i] = It[c];
+            if (a.sP) a.sP[c * hw + i] = Pt[c];
+            if (a.sO) a.sO[c * hw + i] = Pt[c];
+        }
+        if (a.wc) a.wc[i] = 0.f;
+        if (a.mask) a.mask[i] = 0;
+        return;
+    }
+    Taps t;
+    const bool m = warp_sample(a.Fb, a.Ff, a, x, y, t);
     float gI[3], gP[3], gO[3], d = 0.f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -102,27 +114,62 @@ __global__ void __launch_bounds__(256) consistency_kernel(ConsistArgs a) {
     float wp = 0.f;
     if (m) wp = fminf(a.k1, expf(-a.alpha * d));
     float dI = 0.f;
+    bool mn = false;
+    if constexpr (NEXT) {
+        Taps tn;
+        mn = warp_sample(a.Fn, a.Fnb, a, x, y, tn);
+        float gIn[3], gPn[3], dn = 0.f;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float L = (1.f - wp) * Pt[c] + wp * gP[c];
-        const float A = wp * gO[c] + (1.f - wp) * L;
-        const float AI = (1.f - wp) * It[c] + wp * gI[c];
-        const float e = It[c] - AI;
-        dI += e * e;
-        a.O[c * hw + i] = A;
-        if (a.sI) a.sI[c * hw + i] = It[c];
-        if (a.sP) a.sP[c * hw + i] = Pt[c];
-        if (a.sO) a.sO[c * hw + i] = A;
+        for (int c = 0; c < 3; ++c) {
+            gIn[c] = gather(a.In + c * hw, a.W, tn);
+            gPn[c] = gather(a.Pn + c * hw, a.W, tn);
+            const float e = It[c] - gIn[c];
+            dn += e * e;
+        }
+        float wn = 0.f;
+        if (mn) wn = fminf(a.k2, expf(-a.alpha * dn));
+        const float wl = 1.f - (wp + wn);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float L = wl * Pt[c] + wp * gP[c] + wn * gPn[c];
+            const float A = wp * gO[c] + (1.f - wp) * L;
+            const float AI = wl * It[c] + wp * gI[c] + wn * gIn[c];
+            const float e = It[c] - AI;
+            dI += e * e;
+            a.O[c * hw + i] = A;
+            if (a.sI) a.sI[c * hw + i] = It[c];
+            if (a.sP) a.sP[c * hw + i] = Pt[c];
+            if (a.sO) a.sO[c * hw + i] = A;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float L = (1.f - wp) * Pt[c] + wp * gP[c];
+            const float A = wp * gO[c] + (1.f - wp) * L;
+            const float AI = (1.f - wp) * It[c] + wp * gI[c];
+            const float e = It[c] - AI;
+            dI += e * e;
+            a.O[c * hw + i] = A;
+            if (a.sI) a.sI[c * hw + i] = It[c];
+            if (a.sP) a.sP[c * hw + i] = Pt[c];
+            if (a.sO) a.sO[c * hw + i] = A;
+        }
     }
     if (a.wc) a.wc[i] = a.lambda * expf(-a.alpha * dI);
-    if (a.mask) a.mask[i] = m ? 1 : 0;
+    if (a.mask) a.mask[i] = (m ? 1 : 0) | (mn ? 2 : 0);
 }
 
-const void *consistency_kernel_fn() { return reinterpret_cast<const void *>(consistency_kernel); }
+const void *consistency_kernel_fn(bool next) {
+    return next ? reinterpret_cast<const void *>(consistency_kernel<true>)
+                : reinterpret_cast<const void *>(consistency_kernel<false>);
+}
 
 cudaError_t launch_consistency(const ConsistArgs &a, cudaStream_t st) {
     dim3 grid((a.W + 31) / 32, (a.H + 7) / 8);
-    consistency_kernel<<<grid, 256, 0, st>>>(a);
+    if (a.next)
+        consistency_kernel<true><<<grid, 256, 0, st>>>(a);
+    else
+        consistency_kernel<false><<<grid, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
