@@ -131,6 +131,17 @@ def pad_replicate(img, hp, wp):
     return out
 
 
+def downscale2(img):
+    """The half-size flow input of the fast preset (Table 3: flow on 2x downscaled frames):
+    (c, h, w) -> (c, ceil(h/2), ceil(w/2)), each value the mean of a 2x2 block, the last row
+    and column replicated when h or w is odd."""
+    a = _d(img)
+    c, h, w = a.shape
+    hn, wn = (h + 1) // 2, (w + 1) // 2
+    p = np.pad(a, ((0, 0), (0, 2 * hn - h), (0, 2 * wn - w)), mode="edge")
+    return p.reshape(c, hn, 2, wn, 2).mean(axis=(2, 4))
+
+
 def consistency(It, Pt, Ip, Pp, Op, Fb, Ff, k1=0.3, alpha=6.5e3, lam=2.0, fb_check=True,
                 c1=FB_C1, c2=FB_C2):
     """Causal consistency step (Eqs. 2-7, w_n = 0).  Returns dict(O, wc, mask, band, wp)."""
@@ -287,11 +298,16 @@ class Stream:
     latency = 0: causal form, step(I_t, P_t) returns frame t (w_n = 0).
     latency = 1: step(I_{t+1}, P_{t+1}) returns frame t blended with both neighbours (w_n with
     the clamp k2), None for the first frame of a sequence; flush() returns the last frame
-    (w_n = 0, no next frame) and starts a new sequence."""
+    (w_n = 0, no next frame) and starts a new sequence.
+    flow_downscale = 2: the flow network runs on downscale2 of the frames (the fast preset
+    of Table 3, with solver_iters = 50)."""
 
     def __init__(self, net: Net, k1=0.3, alpha=6.5e3, lam=2.0, fb_check=True, c1=FB_C1, c2=FB_C2,
-                 solver_iters=0, eta=0.15, kappa=0.2, k2=0.5, latency=0):
+                 solver_iters=0, eta=0.15, kappa=0.2, k2=0.5, latency=0, flow_downscale=1):
         self.net = net
+        # flow_downscale = 2: the network sees downscale2(I) and its level-2 flow is upsampled
+        # x8 to the frame (the fast preset); 1: the frame itself, x4
+        self.fs = int(flow_downscale)
         self.params = dict(k1=k1, alpha=alpha, lam=lam, fb_check=fb_check, c1=c1, c2=c2)
         self.k2 = float(k2)
         self.latency = int(latency)
@@ -310,6 +326,19 @@ class Stream:
             r["O"] = poisson_solve(P, r["A"], r["wc"], eta=eta, kappa=kappa, iters=iters)
         return r
 
+    def _pyramid(self, I):
+        x = downscale2(I) if self.fs == 2 else I
+        _, hn, wn = x.shape
+        hp, wp = padded_size(hn, wn, self.net.levels)
+        return pyramid(self.net, pad_replicate(x, hp, wp)), hp, wp
+
+    def _flow(self, pyr_a, pyr_b, hp, wp, h, w):
+        """F_{a->b} on the (h, w) frame."""
+        if self.fs == 1:
+            return np.ascontiguousarray(flow_from_pyramids(self.net, pyr_a, pyr_b, hp, wp)[:, :h, :w])
+        _, lf = flow_from_pyramids(self.net, pyr_a, pyr_b, hp, wp, level_flows=True)
+        return np.ascontiguousarray(upsample_flow(lf[0], 4 * self.fs)[:, :h, :w])
+
     def _first(self, P):
         _, h, w = P.shape
         return dict(O=P.copy(), wc=np.zeros((h, w)), mask=np.zeros((h, w), np.uint8),
@@ -317,15 +346,14 @@ class Stream:
 
     def _step_latency(self, I, P):
         _, h, w = I.shape
-        hp, wp = padded_size(h, w, self.net.levels)
-        pyr = pyramid(self.net, pad_replicate(I, hp, wp))
+        pyr, hp, wp = self._pyramid(I)
         if not self.hist:
             self.hist = [(I, P, pyr)]
             return None
         It, Pt, pyr_t = self.hist[-1]
         # the pair (t+1, t): F_{t+1->t} and F_{t->t+1}
-        Fb1 = np.ascontiguousarray(flow_from_pyramids(self.net, pyr, pyr_t, hp, wp)[:, :h, :w])
-        Ff1 = np.ascontiguousarray(flow_from_pyramids(self.net, pyr_t, pyr, hp, wp)[:, :h, :w])
+        Fb1 = self._flow(pyr, pyr_t, hp, wp, h, w)
+        Ff1 = self._flow(pyr_t, pyr, hp, wp, h, w)
         if len(self.hist) == 1:
             r = self._first(Pt)
         else:
@@ -359,15 +387,13 @@ class Stream:
         if self.latency == 1:
             return self._step_latency(I, P)
         _, h, w = I.shape
-        hp, wp = padded_size(h, w, self.net.levels)
-        pyr = pyramid(self.net, pad_replicate(I, hp, wp))
+        pyr, hp, wp = self._pyramid(I)
         if self.prev is None:
             self.prev = (I, P, P.copy(), pyr)
-            return dict(O=P.copy(), wc=np.zeros((h, w)), mask=np.zeros((h, w), np.uint8),
-                        band=np.zeros((h, w), np.uint8), Fb=None, Ff=None)
+            return self._first(P)
         Ip, Pp, Op, pyr_p = self.prev
-        Fb = np.ascontiguousarray(flow_from_pyramids(self.net, pyr, pyr_p, hp, wp)[:, :h, :w])
-        Ff = np.ascontiguousarray(flow_from_pyramids(self.net, pyr_p, pyr, hp, wp)[:, :h, :w])
+        Fb = self._flow(pyr, pyr_p, hp, wp, h, w)
+        Ff = self._flow(pyr_p, pyr, hp, wp, h, w)
         r = self._solve(consistency(I, P, Ip, Pp, Op, Fb, Ff, **self.params), P)
         self.prev = (I, P, r["O"], pyr)
         r.update(Fb=Fb, Ff=Ff)
