@@ -105,13 +105,21 @@ typedef struct {
  * chans[levels], decoder[4] (128,96,64,32), n_layers; per layer int32 cout, cin, stride,
  * leaky, float32 w[cout][cin][3][3], float32 b[cout].  Layer order: pyramid levels 1..L
  * (three convs each), then the estimators at levels L..2 (five convs each; conv4 reads
- * cat(x3, x2), conv5 reads cat(x4, x3)). */
+ * cat(x3, x2), conv5 reads cat(x4, x3)).
+ *   flow_downscale  0 or 1: the flow network runs on the frames as given.  2: it runs on the
+ *                   frames downscaled by 2 (the mean of each 2 x 2 block, the last row and
+ *                   column replicated for odd sizes) and its final flow is upsampled x8
+ *                   (values x8) to the frame; everything else stays at full resolution.
+ *                   With solver_iters = 50 this is the paper's fast preset (Sec. 4, Table 3:
+ *                   flow on half-sized inputs, 50 iterations instead of 150).  The size
+ *                   rule then applies to ceil(width / 2) and ceil(height / 2). */
 typedef struct {
     int width, height;
     tc_precision precision;
     const char *weights_path;
     const void *weights_blob;
     size_t weights_bytes;
+    int flow_downscale;
 } tc_stream_desc;
 
 /* Fills *p with the paper's final setting (Sec. 4.2: k1 = 0.3, k2 = 0.5, alpha = 6.5e3,
@@ -303,6 +311,11 @@ TC_API tc_status tc_op_warp_features(tc_precision precision, const float *f, con
  * out (n, s h, s w, 2). */
 TC_API tc_status tc_op_upsample_flow(const float *flow, int n, int h, int w, int s, float *out,
                               void *cuda_stream);
+
+/* The flow input of flow_downscale = 2 alone: (c, h, w) -> (c, ceil(h/2), ceil(w/2)), each
+ * output the mean of a 2 x 2 block of src, the last row and column replicated when h or w
+ * is odd.  Device float32 planar buffers; enqueued on cuda_stream. */
+TC_API tc_status tc_op_downscale2(const float *src, int c, int h, int w, float *dst, void *cuda_stream);
 
 /* The consistency step alone (Sec. 3.1, Eqs. 2-7 with w_n = 0, O_t := A_t) on images of
  * h x w pixels.  It, Pt, Ip, Pp, Op: device (3, h, w) float32 (I_t, P_t, I_{t-1},

@@ -33,7 +33,7 @@ EXPORTED = ["tc_default_consistency", "tc_create_stream", "tc_set_consistency", 
             "tc_op_last_used_tensor_cores", "tc_op_correlation_bf16_noalloc",
             "tc_tensor_core_correlation_levels", "tc_set_graphs", "tc_activation_segments",
             "tc_set_amax_recording", "tc_get_amax", "tc_set_fp8_scales", "tc_op_poisson_solve", "tc_set_latency",
-            "tc_flush", "tc_last_output_frame", "tc_op_consistency_next"]
+            "tc_flush", "tc_last_output_frame", "tc_op_consistency_next", "tc_op_downscale2"]
 E4M3_MAX = 448.0
 NOALLOC_SCRATCH_BYTES = 16 << 20
 PROFILE_CATEGORIES = ["pyramid_conv", "estimator_conv", "head", "correlation", "warp", "upsample", "consistency",
@@ -50,7 +50,7 @@ class TcConsistency(ctypes.Structure):
 class TcStreamDesc(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("precision", ctypes.c_int),
                 ("weights_path", ctypes.c_char_p), ("weights_blob", ctypes.c_void_p),
-                ("weights_bytes", ctypes.c_size_t)]
+                ("weights_bytes", ctypes.c_size_t), ("flow_downscale", ctypes.c_int)]
 
 
 _vp, _i, _f = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
@@ -85,13 +85,14 @@ _lib.tc_get_amax.argtypes = [_vp, ctypes.POINTER(_f), _i]
 _lib.tc_set_fp8_scales.argtypes = [_vp, ctypes.POINTER(_f), _i]
 _lib.tc_get_profile.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), _i]
 _lib.tc_set_latency.argtypes = [_vp, _i]
+_lib.tc_op_downscale2.argtypes = [_vp, _i, _i, _i, _vp, _vp]
 _lib.tc_flush.argtypes = [_vp, _vp, _vp, _vp]
 _lib.tc_last_output_frame.argtypes = [_vp]
 _lib.tc_last_output_frame.restype = ctypes.c_longlong
 _lib.tc_op_consistency_next.argtypes = [_vp] * 11 + [_i] * 5 + [ctypes.POINTER(TcConsistency), _vp, _vp, _vp, _vp]
 for _n in ["tc_set_amax_recording", "tc_get_amax", "tc_set_fp8_scales", "tc_set_graphs", "tc_op_correlation_bf16_noalloc", "tc_synchronize", "tc_set_profiling", "tc_get_profile", "tc_create_stream", "tc_set_consistency", "tc_process_frame", "tc_process_frame_host", "tc_get_flows",
            "tc_destroy", "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
-           "tc_op_consistency", "tc_set_latency", "tc_flush", "tc_op_consistency_next"]:
+           "tc_op_consistency", "tc_set_latency", "tc_flush", "tc_op_consistency_next", "tc_op_downscale2"]:
     getattr(_lib, _n).restype = ctypes.c_int
 
 
@@ -152,9 +153,13 @@ def _consistency_struct(**kw) -> TcConsistency:
 class Stream:
     """One video stream: tc_create_stream / tc_set_consistency / tc_process_frame / tc_destroy."""
 
-    def __init__(self, width, height, precision="fp32", weights_path=None, weights_blob=None, cuda_stream=None):
+    def __init__(self, width, height, precision="fp32", weights_path=None, weights_blob=None, cuda_stream=None,
+                 flow_downscale=1):
+        """flow_downscale = 2 runs the flow network on 2x2-mean half-size frames (with
+        set_consistency(solver_iters=50): the paper's fast preset)."""
         desc = TcStreamDesc()
         desc.width, desc.height = int(width), int(height)
+        desc.flow_downscale = int(flow_downscale)
         desc.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
         self._blob = None
         if weights_path is not None:
@@ -274,12 +279,13 @@ class Stream:
             pass
 
 
-def calibrate_fp8(width, height, frames, weights_path=None, weights_blob=None, margin=1.0):
+def calibrate_fp8(width, height, frames, weights_path=None, weights_blob=None, margin=1.0, flow_downscale=1):
     """E4M3 scales from a BF16 pass: runs `frames` (a list of (I, P) CUDA (3, H, W) float32
     pairs) through a BF16 stream recording the amax of every activation segment, and returns
     margin * amax / 448 per segment (the scales tc_set_fp8_scales takes)."""
     import torch
-    s = Stream(width, height, "bf16", weights_path=weights_path, weights_blob=weights_blob)
+    s = Stream(width, height, "bf16", weights_path=weights_path, weights_blob=weights_blob,
+               flow_downscale=flow_downscale)
     try:
         s.set_amax_recording(True)
         out = torch.empty((3, height, width), device="cuda", dtype=torch.float32)
@@ -360,6 +366,15 @@ def op_poisson_solve(P, A, wc, iters=150, eta=0.15, kappa=0.2, cuda_stream=None)
                                     _ptr(wc, torch.float32, "wc"), c, h, w, int(iters), float(eta), float(kappa),
                                     O.data_ptr(), _stream_handle(cuda_stream)))
     return O
+
+
+def op_downscale2(src, cuda_stream=None):
+    """(c, h, w) float32 CUDA -> (c, ceil(h/2), ceil(w/2)): 2x2 block means, edges replicated."""
+    import torch
+    c, h, w = src.shape
+    dst = torch.empty((c, (h + 1) // 2, (w + 1) // 2), device=src.device, dtype=torch.float32)
+    _check(_lib.tc_op_downscale2(_ptr(src, torch.float32, "src"), c, h, w, dst.data_ptr(), _stream_handle(cuda_stream)))
+    return dst
 
 
 def op_consistency_next(It, Pt, Ip, Pp, Op, Fb, Ff, In, Pn, Fn, Fnb, scale=1, O=None, wc=None, mask=None,

@@ -162,6 +162,8 @@ cudaError_t launch_consistency(const ConsistArgs &a, cudaStream_t st);
 // find their nodes in a captured CUDA graph).
 template <typename T> const void *conv_first_kernel_fn();
 const void *consistency_kernel_fn(bool next);
+cudaError_t launch_downscale2(const float *src, int c, int h, int w, float *dst, cudaStream_t st);
+const void *downscale2_kernel_fn();
 cudaError_t launch_flow_out(const float *flow, int fh, int fw, int scale, int H, int W,
                             float *out, cudaStream_t st);
 template <typename T>

@@ -111,11 +111,12 @@ static std::vector<int> iota_perm(int n, int pad_to) {
 
 static inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precision prec) {
+size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precision prec, int fs) {
     const int L = net.levels, D = (2 * net.radius + 1) * (2 * net.radius + 1), m = 1 << L;
     const bool f8 = prec == TC_FP8_E4M3;
     const size_t es = prec == TC_FP32 ? 4 : (f8 ? 1 : 2);
-    const size_t Hp = (size_t)round_up(height, m), Wp = (size_t)round_up(width, m);
+    const int wn = (width + fs - 1) / fs, hn = (height + fs - 1) / fs;  // the flow network's input
+    const size_t Hp = (size_t)round_up(hn, m), Wp = (size_t)round_up(wn, m);
     const bool bf = prec != TC_FP32;
     auto al = [](size_t b) { return (b + 511) & ~(size_t)511; };  // allocation granularity
     // packed tensor-core weights (bf16, or e4m3 plus one float scale per output channel)
@@ -147,6 +148,7 @@ size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precisi
     const size_t img = al((size_t)3 * height * width * 4), plane = (size_t)height * width;
     total += 6 * img;                                        // state I, P, O x 2 slots
     total += 3 * img + al(plane * 4) + al(plane);            // host-entry staging
+    if (fs > 1) total += al((size_t)3 * hn * wn * 4);        // the downscaled frame
     return total;
 }
 
@@ -192,6 +194,10 @@ struct LevelBufs {
 
 struct tc_stream {
     int W = 0, H = 0, Wp = 0, Hp = 0;
+    // the flow network's input: the frame (fs = 1) or its 2x2 means (fs = 2, the fast
+    // preset), Wn x Hn = ceil(W / fs) x ceil(H / fs), padded to Wp x Hp
+    int fs = 1, Wn = 0, Hn = 0;
+    float *xs = nullptr;
     tc_precision prec = TC_FP32;
     cudaStream_t st = nullptr;
     HostNet net;
@@ -526,6 +532,7 @@ static tc_status build_stream(tc_stream *s) {
         if ((r = dalloc_t(s, &s->sP[k], img)) != TC_OK) return r;
         if ((r = dalloc_t(s, &s->sO[k], img)) != TC_OK) return r;
     }
+    if (s->fs == 2 && (r = dalloc_t(s, &s->xs, (size_t)3 * s->Hn * s->Wn * sizeof(float))) != TC_OK) return r;
     return TC_OK;
 }
 
@@ -558,12 +565,20 @@ extern "C" tc_status tc_create_stream(const tc_stream_desc *desc, void *cuda_str
     s->R = s->net.radius;
     s->D = (2 * s->R + 1) * (2 * s->R + 1);
     const int m = 1 << s->L;
-    if (desc->width < m || desc->height < m || desc->width > 16384 || desc->height > 16384)
-        return fail(nullptr, TC_ERR_INVALID_ARG, "tc_create_stream: width and height must lie in [2^levels, 16384]");
+    if (desc->flow_downscale < 0 || desc->flow_downscale > 2)
+        return fail(nullptr, TC_ERR_INVALID_ARG, "tc_create_stream: flow_downscale must be 0, 1 or 2");
+    const int fs = desc->flow_downscale == 2 ? 2 : 1;
+    if (desc->width > 16384 || desc->height > 16384 || (desc->width + fs - 1) / fs < m ||
+        (desc->height + fs - 1) / fs < m)
+        return fail(nullptr, TC_ERR_INVALID_ARG,
+                    "tc_create_stream: width and height must be <= 16384 and, divided by flow_downscale, >= 2^levels");
     s->W = desc->width;
     s->H = desc->height;
-    s->Wp = round_up(s->W, m);
-    s->Hp = round_up(s->H, m);
+    s->fs = fs;
+    s->Wn = (s->W + fs - 1) / fs;
+    s->Hn = (s->H + fs - 1) / fs;
+    s->Wp = round_up(s->Wn, m);
+    s->Hp = round_up(s->Hn, m);
     s->prec = desc->precision;
     s->st = static_cast<cudaStream_t>(cuda_stream);
     tc_default_consistency(&s->params);
@@ -652,7 +667,11 @@ static tc_status run_pyramid(tc_stream *s, const float *img, int slot) {
         const size_t px = (size_t)B.h * B.w;
         T *dst = static_cast<T *>(B.pyr) + (size_t)slot * px * B.c;
         if (l == 1) {
-            ConvFirstArgs f{img, s->H, s->W, s->Hp, s->Wp, s->pyr_w[0], s->pyr_b[0], B.c, B.tmpA, B.q_pyr[0]};
+            if (s->fs == 2) {
+                TC_LAUNCH_CAT(s, TC_PROF_PYRAMID_CONV, launch_downscale2(img, 3, s->H, s->W, s->xs, s->st));
+                img = s->xs;
+            }
+            ConvFirstArgs f{img, s->Hn, s->Wn, s->Hp, s->Wp, s->pyr_w[0], s->pyr_b[0], B.c, B.tmpA, B.q_pyr[0]};
             TC_LAUNCH_CAT(s, TC_PROF_PYRAMID_CONV, launch_conv_first<T>(f, s->st));
         } else {
             LevelBufs &P = s->lv[l - 2];
@@ -780,7 +799,7 @@ static ConsistArgs consist_args(tc_stream *s, const float *I, const float *P, fl
     ca.Ip = lat ? s->sI[cur] : s->sI[prev];
     ca.Pp = lat ? s->sP[cur] : s->sP[prev];
     ca.Op = s->sO[prev];
-    ca.fh = B2.h; ca.fw = B2.w; ca.scale = 4;
+    ca.fh = B2.h; ca.fw = B2.w; ca.scale = 4 * s->fs;
     if (!lat) {
         ca.Fb = B2.flow;
         ca.Ff = B2.flow + half;
@@ -873,7 +892,8 @@ static tc_status capture_frame(tc_stream *s, const float *I, const float *P, flo
         if (ty != cudaGraphNodeTypeKernel) continue;
         cudaKernelNodeParams kp{};
         TC_TRY(s, cudaGraphKernelNodeGetParams(node, &kp), "cudaGraphKernelNodeGetParams");
-        if (kp.func == conv_first_kernel_fn<T>()) { G.n_first = node; G.p_first = kp; }
+        if (s->fs == 1 && kp.func == conv_first_kernel_fn<T>()) { G.n_first = node; G.p_first = kp; }
+        if (s->fs == 2 && kp.func == downscale2_kernel_fn()) { G.n_first = node; G.p_first = kp; }
         if (kp.func == consistency_kernel_fn(s->latency != 0)) { G.n_cons = node; G.p_cons = kp; }
         if (kp.func == copy_out_kernel_fn(0)) { G.n_copy = node; G.p_copy = kp; }
         if (kp.func == copy_out_kernel_fn(1)) { G.n_in = node; G.p_in = kp; }
@@ -945,13 +965,17 @@ static tc_status process(tc_stream *s, const float *I, const float *P, float *O,
     if (!G.exec) {
         if ((r = capture_frame<T>(s, I, P, O, wc, mask, cur)) != TC_OK) return r;
     } else {
-        ConvFirstArgs f{I, s->H, s->W, s->Hp, s->Wp, s->pyr_w[0], s->pyr_b[0], s->lv[0].c, s->lv[0].tmpA,
+        ConvFirstArgs f{I, s->Hn, s->Wn, s->Hp, s->Wp, s->pyr_w[0], s->pyr_b[0], s->lv[0].c, s->lv[0].tmpA,
                         s->lv[0].q_pyr[0]};
         ConsistArgs ca = consist_args(s, I, P, O, wc, mask, cur);
+        // the node that reads the caller's I_t: the first pyramid conv, or the 2x2 downscale
+        int c3 = 3, hh = s->H, ww = s->W;
+        float *xs = s->xs;
         void *fa[1] = {&f};
+        void *da[5] = {&I, &c3, &hh, &ww, &xs};
         void *cargs[1] = {&ca};
         cudaKernelNodeParams pf = G.p_first, pc = G.p_cons;
-        pf.kernelParams = fa;
+        pf.kernelParams = s->fs == 2 ? da : fa;
         pf.extra = nullptr;
         pc.kernelParams = cargs;
         pc.extra = nullptr;
@@ -1204,8 +1228,9 @@ extern "C" tc_status tc_get_flows(tc_stream *s, float *Fb, float *Ff) {
     if (r != TC_OK) return r;
     if (s->t < 2) return fail(s, TC_ERR_STATE, "tc_get_flows: no flow before the second frame");
     LevelBufs &B2 = s->lv[1];
-    if (Fb) TC_LAUNCH(s, launch_flow_out(B2.flow, B2.h, B2.w, 4, s->H, s->W, Fb, s->st));
-    if (Ff) TC_LAUNCH(s, launch_flow_out(B2.flow + (size_t)B2.h * B2.w * 2, B2.h, B2.w, 4, s->H, s->W, Ff, s->st));
+    if (Fb) TC_LAUNCH(s, launch_flow_out(B2.flow, B2.h, B2.w, 4 * s->fs, s->H, s->W, Fb, s->st));
+    if (Ff)
+        TC_LAUNCH(s, launch_flow_out(B2.flow + (size_t)B2.h * B2.w * 2, B2.h, B2.w, 4 * s->fs, s->H, s->W, Ff, s->st));
     return TC_OK;
 }
 
@@ -1517,6 +1542,12 @@ extern "C" tc_status tc_op_consistency(const float *It, const float *Pt, const f
     ca.fb_check = p->fb_check; ca.first = 0;
     ca.O = O; ca.wc = wc_opt; ca.mask = mask_opt;
     OP_TRY(launch_consistency(ca, static_cast<cudaStream_t>(cuda_stream)), "tc_op_consistency launch");
+    return TC_OK;
+}
+
+extern "C" tc_status tc_op_downscale2(const float *src, int c, int h, int w, float *dst, void *cuda_stream) {
+    if (!src || !dst || c < 1 || h < 1 || w < 1) return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_downscale2: bad argument");
+    OP_TRY(launch_downscale2(src, c, h, w, dst, static_cast<cudaStream_t>(cuda_stream)), "tc_op_downscale2 launch");
     return TC_OK;
 }
 

@@ -28,7 +28,7 @@ bool parse_weights(const uint8_t *p, size_t n, HostNet &net, std::string &err);
 
 // Device memory a stream of width x height holds (feature pyramids, estimator buffers,
 // flows, state, weights, host-entry staging), from the same sizes the stream allocates.
-size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precision prec);
+size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precision prec, int fs = 1);
 
 }  // namespace tc
 

@@ -173,6 +173,30 @@ cudaError_t launch_consistency(const ConsistArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// (c, h, w) -> (c, ceil(h/2), ceil(w/2)): the mean of each 2 x 2 block, the last row and
+// column replicated when h or w is odd (the half-size flow input of the fast preset).
+__global__ void downscale2_kernel(const float *src, int c, int h, int w, float *dst) {
+    const int hn = (h + 1) / 2, wn = (w + 1) / 2;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)c * hn * wn) return;
+    const int ch = (int)(i / ((size_t)hn * wn));
+    const int r = (int)(i - (size_t)ch * hn * wn);
+    const int y = r / wn, x = r - y * wn;
+    const int y0 = 2 * y, y1 = min(2 * y + 1, h - 1), x0 = 2 * x, x1 = min(2 * x + 1, w - 1);
+    const float *p = src + (size_t)ch * h * w;
+    const float a = __ldg(p + (size_t)y0 * w + x0), b = __ldg(p + (size_t)y0 * w + x1);
+    const float cc = __ldg(p + (size_t)y1 * w + x0), d = __ldg(p + (size_t)y1 * w + x1);
+    dst[i] = 0.25f * ((a + b) + (cc + d));
+}
+
+const void *downscale2_kernel_fn() { return reinterpret_cast<const void *>(downscale2_kernel); }
+
+cudaError_t launch_downscale2(const float *src, int c, int h, int w, float *dst, cudaStream_t st) {
+    const size_t n = (size_t)c * ((h + 1) / 2) * ((w + 1) / 2);
+    downscale2_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, c, h, w, dst);
+    return cudaGetLastError();
+}
+
 // Full-resolution flow, cropped to (H, W), planar (2, H, W), from a (fh, fw, 2) field.
 __global__ void flow_out_kernel(const float *F, int fh, int fw, int s, int H, int W, float *out) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
