@@ -196,14 +196,15 @@ def weak_scaling_value(units_per_rank, seconds_local, world):
     return world * units_per_rank / max_over_ranks(seconds_local, world)
 
 
-def fp8_scales(tc, path, dev_frames, dev_styl):
+def fp8_scales(tc, path, dev_frames, dev_styl, flow_downscale=1):
     """E4M3 activation scales from a BF16 pass over frames 0-2 (static calibration)."""
     H, W = dev_frames[0].shape[1:]
-    return tc.calibrate_fp8(W, H, list(zip(dev_frames[:3], dev_styl[:3])), weights_path=path)
+    return tc.calibrate_fp8(W, H, list(zip(dev_frames[:3], dev_styl[:3])), weights_path=path,
+                            flow_downscale=flow_downscale)
 
 
-def open_stream(tc, path, W, H, precision, scales):
-    s = tc.Stream(W, H, precision, weights_path=path)
+def open_stream(tc, path, W, H, precision, scales, flow_downscale=1):
+    s = tc.Stream(W, H, precision, weights_path=path, flow_downscale=flow_downscale)
     if precision == "fp8":
         s.set_fp8_scales(scales)
     return s
@@ -218,10 +219,10 @@ def consistency_controls(step, solver_iters, latency):
 
 
 def time_stream(tc, torch, path, dev_frames, dev_styl, precision, steps, warmup, profile=False, scales=None,
-                solver_iters=0, latency=0):
+                solver_iters=0, latency=0, flow_downscale=1):
     """Runs warmup + steps frames through one stream; returns timings (device events)."""
     H, W = dev_frames[0].shape[1:]
-    s = open_stream(tc, path, W, H, precision, scales)
+    s = open_stream(tc, path, W, H, precision, scales, flow_downscale)
     if latency:
         s.set_consistency(**consistency_controls(0, solver_iters, latency))
         s.set_latency(latency)
@@ -259,10 +260,11 @@ def time_stream(tc, torch, path, dev_frames, dev_styl, precision, steps, warmup,
                 tc_corr=tc_corr)
 
 
-def e2e_host(tc, torch, path, frames, styl, precision, steps, warmup, scales=None, solver_iters=0, latency=0):
+def e2e_host(tc, torch, path, frames, styl, precision, steps, warmup, scales=None, solver_iters=0, latency=0,
+             flow_downscale=1):
     """End-to-end through tc_process_frame_host: pinned host I_t, P_t in, O_t out per frame."""
     H, W = frames[0].shape[1:]
-    s = open_stream(tc, path, W, H, precision, scales)
+    s = open_stream(tc, path, W, H, precision, scales, flow_downscale)
     if latency:
         s.set_consistency(**consistency_controls(0, solver_iters, latency))
         s.set_latency(latency)
@@ -320,14 +322,16 @@ def run_ours(args):
     dev_frames = [torch.from_numpy(f).cuda() for f in frames]
     dev_styl = [torch.from_numpy(p).cuda() for p in styl]
     torch.cuda.synchronize()
-    scales = fp8_scales(tc, path, dev_frames, dev_styl) if args.precision == "fp8" or not args.skip_fp8 else None
+    scales = fp8_scales(tc, path, dev_frames, dev_styl, args.flow_downscale) \
+        if args.precision == "fp8" or not args.skip_fp8 else None
 
     clocks = ClockSampler(local)
     barrier(world)
     clocks.start()
     time.sleep(0.3)
     main = time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, args.steps, args.warmup,
-                       scales=scales, solver_iters=args.solver_iters, latency=args.latency)
+                       scales=scales, solver_iters=args.solver_iters, latency=args.latency,
+                       flow_downscale=args.flow_downscale)
     clk = clocks.stop()
     barrier(world)
     total_s = max_over_ranks(main["total_ms"] / 1e3, world)
@@ -335,12 +339,15 @@ def run_ours(args):
 
     # Per-stage device times over the same number of steps (events around every launch).
     prof = time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, args.steps, 2, profile=True,
-                       scales=scales, solver_iters=args.solver_iters, latency=args.latency)
+                       scales=scales, solver_iters=args.solver_iters, latency=args.latency,
+                       flow_downscale=args.flow_downscale)
     fp32 = fp8 = None
     if args.precision != "fp32" and not args.skip_fp32:
-        fp32 = time_stream(tc, torch, path, dev_frames, dev_styl, "fp32", max(3, args.steps // 4), 2)
+        fp32 = time_stream(tc, torch, path, dev_frames, dev_styl, "fp32", max(3, args.steps // 4), 2,
+                           flow_downscale=args.flow_downscale)
     if args.precision != "fp8" and not args.skip_fp8:
-        fp8 = time_stream(tc, torch, path, dev_frames, dev_styl, "fp8", args.steps, 3, scales=scales)
+        fp8 = time_stream(tc, torch, path, dev_frames, dev_styl, "fp8", args.steps, 3, scales=scales,
+                          flow_downscale=args.flow_downscale)
     solver = None
     if not args.skip_solver and args.solver_iters == 0:
         # the paper's full output: Eq. 1 solved by 150 Eq. 8 iterations after the blend
@@ -356,8 +363,17 @@ def run_ours(args):
         latency = (time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 3, scales=scales, latency=1),
                    time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 3, profile=True,
                                scales=scales, latency=1))
+    fast = None
+    if not args.skip_fast and args.flow_downscale == 1:
+        # the paper's fast preset (Table 3): flow on half-size frames, 50 solver iterations
+        n = max(3, args.steps // 4)
+        fscales = fp8_scales(tc, path, dev_frames, dev_styl, 2) if args.precision == "fp8" else None
+        fast = (time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 3, scales=fscales,
+                            solver_iters=50, flow_downscale=2),
+                time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 3, profile=True,
+                            scales=fscales, solver_iters=50, flow_downscale=2))
     e2e = e2e_host(tc, torch, path, frames, styl, args.precision, max(3, min(args.steps, 50)), 2, scales=scales,
-                   solver_iters=args.solver_iters, latency=args.latency)
+                   solver_iters=args.solver_iters, latency=args.latency, flow_downscale=args.flow_downscale)
     e2e_v = e2e["value"]
     if world > 1:
         e2e_v = world / max_over_ranks(1.0 / e2e["value"], world)
@@ -411,7 +427,8 @@ def run_ours(args):
                                "decoder 128/96/64/32/2, both flow directions + fused consistency, "
                                + ("k1 swept {0,.25,.5,.75,1}" if not args.latency else
                                   "k1 0.3 and k2 0.5 with the next frame (one frame of latency)")
-                               + (f", then {args.solver_iters} Eq. 8 solver iterations" if args.solver_iters else ""),
+                               + (f", then {args.solver_iters} Eq. 8 solver iterations" if args.solver_iters else "")
+                               + (", flow network on 2x2-mean half-size frames" if args.flow_downscale == 2 else ""),
                    "frames_resident": N_FRAMES, "streams_per_gpu": 1,
                    "precision": args.precision, "l2": "per-frame working set > 126 MB L2 (no flush needed)"},
         "latency_ms": {"p50": round(per[len(per) // 2], 4), "p99": round(per[min(len(per) - 1, int(0.99 * len(per)))], 4)},
@@ -447,6 +464,16 @@ def run_ours(args):
                                        / FP32_SIMT_PEAK_TFLOPS, 4),
                          "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2032 MHz"},
             "note": "Eq. 1 by Eq. 8 (eta 0.15, kappa 0.2) after the blend, time-blocked 8 iterations per launch"}
+    if fast is not None:
+        ft, ftp = fast
+        n = len(ft["per_frame_ms"])
+        pf = sorted(ft["per_frame_ms"])
+        line["fast_preset"] = {
+            "value": round(n / (ft["total_ms"] / 1e3), 3), "unit": UNIT,
+            "p99_ms": round(pf[min(n - 1, int(0.99 * n))], 4),
+            "stage_ms_per_frame": {k: round(v[0] / n, 4) for k, v in ftp["profile"].items() if v[1]},
+            "note": "Table 3's fast preset: flow network on 960x540 2x2-mean frames (flow upsampled x8), "
+                    "50 Eq. 8 iterations"}
     if latency is not None:
         lt, ltp = latency
         n = len(lt["per_frame_ms"])
@@ -710,6 +737,9 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-solver", action="store_true")
     ap.add_argument("--skip-latency", action="store_true")
+    ap.add_argument("--skip-fast", action="store_true")
+    ap.add_argument("--flow-downscale", type=int, default=1, choices=[1, 2],
+                    help="time the stream with the flow network on half-size frames (the fast preset's flow)")
     ap.add_argument("--latency", type=int, default=0, choices=[0, 1],
                     help="time the stream with one frame of latency (the next frame in the blend)")
     ap.add_argument("--solver-iters", type=int, default=0,
