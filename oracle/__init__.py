@@ -14,7 +14,7 @@ import ctypes
 import os
 import struct
 import subprocess
-from dataclasses import dataclass
+from dataclasses import dataclass, field
 
 import numpy as np
 
@@ -58,6 +58,10 @@ def lib():
         _lib.orc_poisson_grad.argtypes = [c_int, c_int, dp, dp, dp, dp, dp]
         _lib.orc_poisson_solve.argtypes = [c_int, c_int, c_int, dp, dp, dp, c_double, c_double, c_int, dp]
         _lib.orc_flow.argtypes = [vp, vp, ip, c_int, c_int, c_int, c_int, vp, dp, vp]
+        _lib.orc_flow2.argtypes = [vp, vp, ip, c_int, c_int, c_int, c_int, vp, dp, vp, vp, c_int]
+        _lib.orc_depthwise3x3.argtypes = [dp, c_int, c_int, c_int, dp, dp, c_int, dp]
+        _lib.orc_pointwise.argtypes = [dp, c_int, c_int, c_int, dp, dp, c_int, c_int, dp]
+        _lib.orc_refine.argtypes = [dp, dp, c_int, dp, c_int, c_int, c_int, vp, c_int, dp]
         _lib.orc_consistency.argtypes = [c_int, c_int, dp, dp, dp, dp, dp, dp, dp, c_double,
                                          c_double, c_double, c_int, c_double, c_double, dp, dp,
                                          u8p, u8p, dp]
@@ -80,6 +84,12 @@ class _Layer(ctypes.Structure):
     _fields_ = [("cin", ctypes.c_int), ("cout", ctypes.c_int), ("stride", ctypes.c_int),
                 ("leaky", ctypes.c_int), ("w", ctypes.POINTER(ctypes.c_double)),
                 ("b", ctypes.POINTER(ctypes.c_double))]
+
+
+class _SepLayer(ctypes.Structure):
+    _fields_ = [("cin", ctypes.c_int), ("cout", ctypes.c_int), ("dil", ctypes.c_int), ("leaky", ctypes.c_int),
+                ("dw", ctypes.POINTER(ctypes.c_double)), ("db", ctypes.POINTER(ctypes.c_double)),
+                ("pw", ctypes.POINTER(ctypes.c_double)), ("pb", ctypes.POINTER(ctypes.c_double))]
 
 
 # ----------------------------------------------------------------------------- primitives
@@ -188,6 +198,46 @@ def poisson_solve(P, A, wc, eta=0.15, kappa=0.2, iters=150):
     return O
 
 
+def depthwise3x3(x, dw, db=None, dil=1):
+    """Depthwise 3x3 conv with dilation (zero padding): x (c, h, w), dw (c, 3, 3), db (c)."""
+    x, dw = _d(x), _d(dw)
+    c, h, w = x.shape
+    out = np.empty((c, h, w))
+    lib().orc_depthwise3x3(_p(x), c, h, w, _p(dw), _p(_d(db)) if db is not None else None, int(dil), _p(out))
+    return out
+
+
+def pointwise(x, pw, pb=None, leaky=True):
+    """1x1 conv: x (cin, h, w), pw (cout, cin), pb (cout); LeakyReLU 0.1 if leaky."""
+    x, pw = _d(x), _d(pw)
+    cin, h, w = x.shape
+    cout = pw.shape[0]
+    out = np.empty((cout, h, w))
+    lib().orc_pointwise(_p(x), cin, h, w, _p(pw), _p(_d(pb)) if pb is not None else None, cout, int(leaky), _p(out))
+    return out
+
+
+def _sep_table(ref):
+    arr = (_SepLayer * max(1, len(ref)))()
+    for i, L in enumerate(ref):
+        arr[i] = _SepLayer(L["cin"], L["cout"], L["dil"], L["leaky"], _p(L["dw"]), _p(L["db"]), _p(L["pw"]),
+                           _p(L["pb"]))
+    return arr
+
+
+def refine(flow, x4, x3, ref):
+    """Refinement of a flow (2, h, w) from the head input x4 (c4, h, w), x3 (c3, h, w) by
+    the depthwise-separable layers `ref` (dicts cin, cout, dil, leaky, dw, db, pw, pb)."""
+    flow, x4, x3 = _d(flow), _d(x4), _d(x3)
+    _, h, w = flow.shape
+    ref = [dict(L, dw=_d(L["dw"]), db=_d(L["db"]), pw=_d(L["pw"]), pb=_d(L["pb"])) for L in ref]
+    tab = _sep_table(ref)
+    out = np.empty((2, h, w))
+    lib().orc_refine(_p(flow), _p(x4), x4.shape[0], _p(x3), x3.shape[0], h, w, ctypes.cast(tab, ctypes.c_void_p),
+                     len(ref), _p(out))
+    return out
+
+
 def bruteforce_flow(a, b, r):
     """Integer SSD-argmin displacement index per pixel (3x3 patches, border clamp)."""
     a, b = _d(a), _d(b)
@@ -212,6 +262,7 @@ class Net:
     chans: tuple
     decoder: tuple
     layers: list  # dicts with cin, cout, stride, leaky, w (float64), b (float64)
+    ref: list = field(default_factory=list)  # refinement: dicts cin, cout, dil, leaky, dw, db, pw, pb
 
     def _table(self, lo, hi):
         arr = (_Layer * (hi - lo))()
@@ -221,11 +272,12 @@ class Net:
 
 
 def load_weights(path) -> Net:
-    """Parse the flat weight file (magic 'TCW1', little-endian)."""
+    """Parse the flat weight file (magic 'TCW1', or 'TCW2' with a refinement section after
+    the conv layers; little-endian)."""
     with open(path, "rb") as f:
         data = f.read()
-    if data[:4] != b"TCW1":
-        raise ValueError("not a TCW1 weight file")
+    if data[:4] not in (b"TCW1", b"TCW2"):
+        raise ValueError("not a TCW1 / TCW2 weight file")
     off = 4
     levels, radius = struct.unpack_from("<ii", data, off); off += 8
     chans = struct.unpack_from(f"<{levels}i", data, off); off += 4 * levels
@@ -238,13 +290,27 @@ def load_weights(path) -> Net:
         b = np.frombuffer(data, "<f4", cout, off); off += 4 * cout
         layers.append(dict(cin=cin, cout=cout, stride=stride, leaky=leaky,
                            w=w.astype(np.float64), b=b.astype(np.float64)))
-    return Net(levels, radius, tuple(chans), tuple(decoder), layers)
+    ref = []
+    if data[:4] == b"TCW2":
+        (nr,) = struct.unpack_from("<i", data, off); off += 4
+        for _ in range(nr):
+            cin, cout, dil, leaky = struct.unpack_from("<4i", data, off); off += 16
+            arrs = []
+            for shape in ((cin, 3, 3), (cin,), (cout, cin), (cout,)):
+                a = np.frombuffer(data, "<f4", int(np.prod(shape)), off).reshape(shape); off += 4 * a.size
+                arrs.append(a.astype(np.float64))
+            ref.append(dict(cin=cin, cout=cout, dil=dil, leaky=leaky, dw=arrs[0], db=arrs[1], pw=arrs[2], pb=arrs[3]))
+    return Net(levels, radius, tuple(chans), tuple(decoder), layers, ref)
 
 
 def net_from_layers(spec_levels, radius, chans, decoder, layers) -> Net:
+    conv = [L for L in layers if "dw" not in L]
+    sep = [L for L in layers if "dw" in L]
     return Net(spec_levels, radius, tuple(chans), tuple(decoder),
                [dict(cin=L["cin"], cout=L["cout"], stride=L["stride"], leaky=L["leaky"],
-                     w=_d(L["w"]), b=_d(L["b"])) for L in layers])
+                     w=_d(L["w"]), b=_d(L["b"])) for L in conv],
+               [dict(cin=L["cin"], cout=L["cout"], dil=L["dil"], leaky=L["leaky"], dw=_d(L["dw"]), db=_d(L["db"]),
+                     pw=_d(L["pw"]), pb=_d(L["pb"])) for L in sep])
 
 
 def padded_size(h, w, levels):
@@ -276,8 +342,10 @@ def flow_from_pyramids(net: Net, feat_self, feat_other, hp, wp, level_flows=Fals
     if level_flows:
         lf = [np.empty((2, hp >> l, wp >> l)) for l in range(2, net.levels + 1)]
         lfp = ctypes.cast((ctypes.c_void_p * len(lf))(*[a.ctypes.data for a in lf]), ctypes.c_void_p)
-    lib().orc_flow(ctypes.cast(ps, ctypes.c_void_p), ctypes.cast(po, ctypes.c_void_p), chans,
-                   hp, wp, net.levels, net.radius, ctypes.cast(tab, ctypes.c_void_p), _p(out), lfp)
+    rt = _sep_table(net.ref)
+    lib().orc_flow2(ctypes.cast(ps, ctypes.c_void_p), ctypes.cast(po, ctypes.c_void_p), chans,
+                    hp, wp, net.levels, net.radius, ctypes.cast(tab, ctypes.c_void_p), _p(out), lfp,
+                    ctypes.cast(rt, ctypes.c_void_p), len(net.ref))
     return (out, lf) if level_flows else out
 
 

@@ -215,6 +215,82 @@ ORC_API void orc_pyramid(const double *img, int h, int w, int levels, const orc_
     }
 }
 
+/* One depthwise-separable layer of the refinement network (Sec. 3.2 "-sepref"):
+ * a depthwise 3x3 conv with dilation dil (per channel, zero padding, bias, no activation)
+ * followed by a pointwise 1x1 conv (bias, LeakyReLU 0.1 if leaky). */
+typedef struct {
+    int cin, cout, dil, leaky;
+    const double *dw;  /* (cin, 3, 3) */
+    const double *db;  /* (cin) */
+    const double *pw;  /* (cout, cin) */
+    const double *pb;  /* (cout) */
+} orc_sep_layer;
+
+/* Depthwise 3x3 conv with dilation dil: out[c](y, x) = db[c] + sum over ky, kx of
+ * dw[c][ky][kx] x[c](y + (ky - 1) dil, x + (kx - 1) dil), taps off the map are 0. */
+ORC_API void orc_depthwise3x3(const double *x, int c, int h, int w, const double *dw, const double *db, int dil,
+                              double *out)
+{
+    const size_t hw = (size_t)h * w;
+#pragma omp parallel for schedule(static)
+    for (int ch = 0; ch < c; ++ch)
+        for (int y = 0; y < h; ++y)
+            for (int xx = 0; xx < w; ++xx) {
+                double acc = db ? db[ch] : 0.0;
+                for (int ky = 0; ky < 3; ++ky) {
+                    const int sy = y + (ky - 1) * dil;
+                    if (sy < 0 || sy >= h) continue;
+                    for (int kx = 0; kx < 3; ++kx) {
+                        const int sx = xx + (kx - 1) * dil;
+                        if (sx < 0 || sx >= w) continue;
+                        acc += dw[ch * 9 + ky * 3 + kx] * x[ch * hw + (size_t)sy * w + sx];
+                    }
+                }
+                out[ch * hw + (size_t)y * w + xx] = acc;
+            }
+}
+
+/* Pointwise 1x1 conv: out[o] = pb[o] + sum_c pw[o][c] x[c], LeakyReLU 0.1 if leaky. */
+ORC_API void orc_pointwise(const double *x, int cin, int h, int w, const double *pw, const double *pb, int cout,
+                           int leaky, double *out)
+{
+    const size_t hw = (size_t)h * w;
+#pragma omp parallel for schedule(static)
+    for (int o = 0; o < cout; ++o)
+        for (size_t i = 0; i < hw; ++i) {
+            double acc = pb ? pb[o] : 0.0;
+            for (int c = 0; c < cin; ++c) acc += pw[(size_t)o * cin + c] * x[c * hw + i];
+            out[o * hw + i] = leaky && acc < 0.0 ? 0.1 * acc : acc;
+        }
+}
+
+/* Refinement of the finest flow (Sec. 3.2, "-sepref": the refinement network with
+ * depthwise-separable convs): the input is cat(flow, x4, x3) of the level-2 estimator (the
+ * flow head's input, after the flow), the layers run in order, and the last layer's two
+ * outputs are added to the flow: out = flow + ref(cat(flow, x4, x3)). */
+ORC_API void orc_refine(const double *flow, const double *x4, int c4, const double *x3, int c3, int h, int w,
+                        const orc_sep_layer *ref, int n, double *out)
+{
+    const size_t hw = (size_t)h * w;
+    int c = 2 + c4 + c3;
+    double *cur = malloc(sizeof(double) * c * hw);
+    memcpy(cur, flow, sizeof(double) * 2 * hw);
+    memcpy(cur + 2 * hw, x4, sizeof(double) * c4 * hw);
+    memcpy(cur + (size_t)(2 + c4) * hw, x3, sizeof(double) * c3 * hw);
+    for (int k = 0; k < n; ++k) {
+        double *d = malloc(sizeof(double) * ref[k].cin * hw);
+        double *p = malloc(sizeof(double) * ref[k].cout * hw);
+        orc_depthwise3x3(cur, ref[k].cin, h, w, ref[k].dw, ref[k].db, ref[k].dil, d);
+        orc_pointwise(d, ref[k].cin, h, w, ref[k].pw, ref[k].pb, ref[k].cout, ref[k].leaky, p);
+        free(d);
+        free(cur);
+        cur = p;
+        c = ref[k].cout;
+    }
+    for (size_t i = 0; i < 2 * hw; ++i) out[i] = flow[i] + cur[i];
+    free(cur);
+}
+
 /* Concatenate planar blocks along the channel axis. */
 static void cat2(const double *a, int ca, const double *b, int cb, size_t hw, double *out)
 {
@@ -230,12 +306,14 @@ static void cat2(const double *a, int ca, const double *b, int cb, size_t hw, do
  *   x0   = cat(cv, f_self, up);  x1 = conv1(x0); x2 = conv2(x1); x3 = conv3(x2);
  *   x4   = conv4(cat(x3, x2));   res = conv5(cat(x4, x3))   (no activation on conv5),
  *   flow = up + res.
- * The flow of level 2 is upsampled 4x to the padded input resolution into flow_out
- * (2, h, w).  est[5 (L - l) + j] is conv j+1 of the estimator at level l.  If
- * level_flows is non-NULL, level_flows[l-2] receives flow of level l, (2, h>>l, w>>l). */
-ORC_API void orc_flow(double *const *feat_self, double *const *feat_other, const int *chans,
-                      int h, int w, int levels, int r, const orc_layer *est, double *flow_out,
-                      double **level_flows)
+ * With a refinement network (n_ref > 0) the flow of level 2 is refined by orc_refine from
+ * that level's flow, x4 and x3.  The flow of level 2 is upsampled 4x to the padded input
+ * resolution into flow_out (2, h, w).  est[5 (L - l) + j] is conv j+1 of the estimator at
+ * level l.  If level_flows is non-NULL, level_flows[l-2] receives flow of level l,
+ * (2, h>>l, w>>l) (the refined one at level 2). */
+ORC_API void orc_flow2(double *const *feat_self, double *const *feat_other, const int *chans,
+                       int h, int w, int levels, int r, const orc_layer *est, double *flow_out,
+                       double **level_flows, const orc_sep_layer *ref, int n_ref)
 {
     const int nd = (2 * r + 1) * (2 * r + 1);
     double *prev = NULL;
@@ -273,6 +351,12 @@ ORC_API void orc_flow(double *const *feat_self, double *const *feat_other, const
         orc_conv3x3(x43, E[4].cin, lh, lw, E[4].w, E[4].b, E[4].cout, 1, E[4].leaky, res);
         double *flow = malloc(sizeof(double) * 2 * hw);
         for (size_t i = 0; i < 2 * hw; ++i) flow[i] = up[i] + res[i];
+        if (l == 2 && n_ref > 0) {
+            double *refined = malloc(sizeof(double) * 2 * hw);
+            orc_refine(flow, x4, E[3].cout, x3, E[2].cout, lh, lw, ref, n_ref, refined);
+            free(flow);
+            flow = refined;
+        }
         if (level_flows) memcpy(level_flows[l - 2], flow, sizeof(double) * 2 * hw);
         free(up); free(f2w); free(x0); free(x1); free(x2); free(x3); free(x32);
         free(x4); free(x43); free(res); free(prev);
@@ -282,6 +366,14 @@ ORC_API void orc_flow(double *const *feat_self, double *const *feat_other, const
     }
     orc_upsample_flow(prev, ph, pw, 4, flow_out);
     free(prev);
+}
+
+/* orc_flow2 without a refinement network. */
+ORC_API void orc_flow(double *const *feat_self, double *const *feat_other, const int *chans,
+                      int h, int w, int levels, int r, const orc_layer *est, double *flow_out,
+                      double **level_flows)
+{
+    orc_flow2(feat_self, feat_other, chans, h, w, levels, r, est, flow_out, level_flows, NULL, 0);
 }
 
 /* Consistency step of Sec. 3.1 in its causal form (no next frame, no solver), per pixel:

@@ -263,6 +263,10 @@ class NetSpec:
     radius: int = 4
     decoder: tuple = (128, 96, 64, 32)
     layers: list = field(default_factory=list)
+    # refinement network (depthwise-separable layers after the finest estimator): output
+    # channels and dilations per layer, empty for none
+    refine: tuple = ()
+    refine_dil: tuple = ()
 
     @property
     def levels(self) -> int:
@@ -290,6 +294,21 @@ class NetSpec:
         return t
 
 
+REFINE_CHANS = (128, 128, 128, 96, 64, 32, 2)
+REFINE_DIL = (1, 2, 4, 8, 16, 1, 1)
+
+
+def refine_table(spec: NetSpec):
+    """(name, cin, cout, dil, leaky) of the refinement layers; the first reads cat(flow, x4,
+    x3) of the level-2 estimator, the last (2 outputs) has no activation."""
+    t = []
+    cin = 2 + spec.decoder[3] + spec.decoder[2]
+    for k, (cout, dil) in enumerate(zip(spec.refine, spec.refine_dil)):
+        t.append((f"ref{k + 1}", cin, cout, dil, 0 if k == len(spec.refine) - 1 else 1))
+        cin = cout
+    return t
+
+
 def layer_names(spec: NetSpec):
     return [n for n, *_ in spec.layer_table()]
 
@@ -306,6 +325,14 @@ def he_weights(spec: NetSpec, seed: int = 0, head_gain: float = 1.0):
             w *= head_gain
         out.append(dict(name=name, cin=cin, cout=cout, stride=stride, leaky=leaky,
                         w=w.astype(np.float32), b=np.zeros(cout, np.float32)))
+    # refinement layers after the conv layers: depthwise fan-in 9, pointwise fan-in cin
+    for name, cin, cout, dil, leaky in refine_table(spec):
+        dw = g.normal(0.0, math.sqrt(2.0 / ((1.0 + 0.01) * 9)), (cin, 3, 3))
+        pw = g.normal(0.0, math.sqrt(2.0 / ((1.0 + 0.01) * cin)), (cout, cin))
+        if not leaky:
+            pw *= head_gain
+        out.append(dict(name=name, cin=cin, cout=cout, dil=dil, leaky=leaky, dw=dw.astype(np.float32),
+                        db=np.zeros(cin, np.float32), pw=pw.astype(np.float32), pb=np.zeros(cout, np.float32)))
     return out
 
 
@@ -314,14 +341,25 @@ WEIGHT_MAGIC = b"TCW1"
 
 def write_weights(path: str, spec: NetSpec, layers) -> None:
     """Flat little-endian file: magic 'TCW1'; int32 levels, radius, chans[levels],
-    decoder[4], n_layers; per layer int32 cout, cin, stride, leaky, float32 w (OIHW), b."""
+    decoder[4], n_layers; per layer int32 cout, cin, stride, leaky, float32 w (OIHW), b.
+    With refinement layers (dicts holding 'dw') the magic is 'TCW2' and the conv layers are
+    followed by int32 n_ref and per layer int32 cin, cout, dil, leaky, float32 dw[cin][3][3],
+    db[cin], pw[cout][cin], pb[cout]."""
+    conv = [L for L in layers if "dw" not in L]
+    sep = [L for L in layers if "dw" in L]
     with open(path, "wb") as f:
-        f.write(WEIGHT_MAGIC)
+        f.write(b"TCW2" if sep else WEIGHT_MAGIC)
         f.write(struct.pack("<ii", spec.levels, spec.radius))
         f.write(struct.pack(f"<{spec.levels}i", *spec.chans))
         f.write(struct.pack("<4i", *spec.decoder))
-        f.write(struct.pack("<i", len(layers)))
-        for L in layers:
+        f.write(struct.pack("<i", len(conv)))
+        for L in conv:
             f.write(struct.pack("<4i", L["cout"], L["cin"], L["stride"], L["leaky"]))
             f.write(np.ascontiguousarray(L["w"], "<f4").tobytes())
             f.write(np.ascontiguousarray(L["b"], "<f4").tobytes())
+        if sep:
+            f.write(struct.pack("<i", len(sep)))
+            for L in sep:
+                f.write(struct.pack("<4i", L["cin"], L["cout"], L["dil"], L["leaky"]))
+                for k in ("dw", "db", "pw", "pb"):
+                    f.write(np.ascontiguousarray(L[k], "<f4").tobytes())

@@ -10,11 +10,14 @@ import synth
 _CACHE = {}
 
 
-def weights_file(chans=(16, 32, 48), radius=3, seed=0, head_gain=1.0):
-    """Writes (once per process) the seeded He-init weight file; returns (path, oracle net)."""
-    key = (tuple(chans), radius, seed, head_gain)
+def weights_file(chans=(16, 32, 48), radius=3, seed=0, head_gain=1.0, refine=False):
+    """Writes (once per process) the seeded He-init weight file; returns (path, oracle net).
+    refine: add the depthwise-separable refinement network (TCW2 file)."""
+    key = (tuple(chans), radius, seed, head_gain, refine)
     if key not in _CACHE:
         spec = synth.NetSpec(chans=tuple(chans), radius=radius)
+        if refine:
+            spec.refine, spec.refine_dil = synth.REFINE_CHANS, synth.REFINE_DIL
         layers = synth.he_weights(spec, seed=seed, head_gain=head_gain)
         d = tempfile.mkdtemp(prefix="tcw")
         path = os.path.join(d, "net.tcw")
