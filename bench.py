@@ -48,12 +48,15 @@ FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
 # ----------------------------------------------------------------------------- workload
 
-def net_spec():
-    return synth.NetSpec(chans=SPEC["chans"], radius=SPEC["radius"])
+def net_spec(refine=False):
+    spec = synth.NetSpec(chans=SPEC["chans"], radius=SPEC["radius"])
+    if refine:
+        spec.refine, spec.refine_dil = synth.REFINE_CHANS, synth.REFINE_DIL
+    return spec
 
 
-def write_weights(path):
-    spec = net_spec()
+def write_weights(path, refine=False):
+    spec = net_spec(refine)
     synth.write_weights(path, spec, synth.he_weights(spec, seed=0))
 
 
@@ -363,6 +366,16 @@ def run_ours(args):
         latency = (time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 3, scales=scales, latency=1),
                    time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 3, profile=True,
                                scales=scales, latency=1))
+    refined = None
+    if not args.skip_refine and args.precision != "fp8":
+        # the network with the depthwise-separable refinement after the level-2 estimator
+        rpath = os.path.join(tmp, "net_ref.tcw")
+        write_weights(rpath, refine=True)
+        n = max(3, args.steps // 4)
+        refined = (time_stream(tc, torch, rpath, dev_frames, dev_styl, args.precision, n, 3,
+                               flow_downscale=args.flow_downscale),
+                   time_stream(tc, torch, rpath, dev_frames, dev_styl, args.precision, n, 3, profile=True,
+                               flow_downscale=args.flow_downscale))
     fast = None
     if not args.skip_fast and args.flow_downscale == 1:
         # the paper's fast preset (Table 3): flow on half-size frames, 50 solver iterations
@@ -464,6 +477,14 @@ def run_ours(args):
                                        / FP32_SIMT_PEAK_TFLOPS, 4),
                          "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2032 MHz"},
             "note": "Eq. 1 by Eq. 8 (eta 0.15, kappa 0.2) after the blend, time-blocked 8 iterations per launch"}
+    if refined is not None:
+        rt, rtp = refined
+        n = len(rt["per_frame_ms"])
+        line["with_refinement"] = {
+            "value": round(n / (rt["total_ms"] / 1e3), 3), "unit": UNIT,
+            "refine_ms_per_frame": round(rtp["profile"]["refine"][0] / n, 4),
+            "note": "network + depthwise-separable refinement (7 layers 128/128/128/96/64/32/2, dilations "
+                    "1/2/4/8/16/1/1) on the level-2 flows of both directions"}
     if fast is not None:
         ft, ftp = fast
         n = len(ft["per_frame_ms"])
@@ -738,6 +759,7 @@ def main():
     ap.add_argument("--skip-solver", action="store_true")
     ap.add_argument("--skip-latency", action="store_true")
     ap.add_argument("--skip-fast", action="store_true")
+    ap.add_argument("--skip-refine", action="store_true")
     ap.add_argument("--flow-downscale", type=int, default=1, choices=[1, 2],
                     help="time the stream with the flow network on half-size frames (the fast preset's flow)")
     ap.add_argument("--latency", type=int, default=0, choices=[0, 1],

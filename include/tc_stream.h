@@ -105,7 +105,13 @@ typedef struct {
  * chans[levels], decoder[4] (128,96,64,32), n_layers; per layer int32 cout, cin, stride,
  * leaky, float32 w[cout][cin][3][3], float32 b[cout].  Layer order: pyramid levels 1..L
  * (three convs each), then the estimators at levels L..2 (five convs each; conv4 reads
- * cat(x3, x2), conv5 reads cat(x4, x3)).
+ * cat(x3, x2), conv5 reads cat(x4, x3)).  Magic "TCW2" adds a refinement network after
+ * the level-2 estimator (Sec. 3.2 "-sepref"): int32 n_ref; per layer int32 cin, cout,
+ * dilation, leaky, float32 dw[cin][3][3], db[cin], pw[cout][cin], pb[cout]; each layer is a
+ * depthwise 3x3 conv with that dilation (zero padding, bias, no activation) and a pointwise
+ * 1x1 conv (bias, LeakyReLU if leaky); the first reads cat(flow, x4, x3) of the level-2
+ * estimator (cin = 2 + decoder[3] + decoder[2]), the last has cout = 2, no activation, and
+ * is added to the level-2 flow.  Refinement networks run in TC_FP32 and TC_BF16 streams.
  *   flow_downscale  0 or 1: the flow network runs on the frames as given.  2: it runs on the
  *                   frames downscaled by 2 (the mean of each 2 x 2 block, the last row and
  *                   column replicated for odd sizes) and its final flow is upsampled x8
@@ -252,7 +258,8 @@ enum {
     TC_PROF_CONSISTENCY = 6,     /* fused warp + mask + blend (Eqs. 2-7) */
     TC_PROF_OTHER = 7,
     TC_PROF_SOLVER = 8,          /* screened-Poisson iterations (Eq. 8) and their output copy */
-    TC_PROF_CATEGORIES = 9
+    TC_PROF_REFINE = 9,          /* the refinement network (TCW2 weights) */
+    TC_PROF_CATEGORIES = 10
 };
 
 /* Turns per-stage timing on (enable != 0) or off and resets the totals. */
@@ -311,6 +318,18 @@ TC_API tc_status tc_op_warp_features(tc_precision precision, const float *f, con
  * out (n, s h, s w, 2). */
 TC_API tc_status tc_op_upsample_flow(const float *flow, int n, int h, int w, int s, float *out,
                               void *cuda_stream);
+
+/* One layer of the refinement network with depthwise-separable convs (Sec. 3.2 "-sepref";
+ * TCW2 weight files) on its own: out = LeakyReLU_if_leaky(pb + pw * (db + dw (*) in)), with
+ * dw (*) the depthwise 3x3 conv of dilation dil (zero padding) and pw * the pointwise 1x1
+ * conv.  in: device (n, h, w, cin) float32 NHWC, cin a multiple of 8 (<= 512); dw (cin, 3, 3),
+ * db (cin), pw (cout, cin), pb (cout): host float32; cout a multiple of 8 (<= 256) written to
+ * out (n, h, w, cout), or cout = 2 (the refinement's last layer, no activation) written as
+ * float pairs.  precision TC_FP32 (CUDA cores) or TC_BF16 (activations rounded to bfloat16,
+ * pointwise conv on the tensor cores when eligible).  Allocates temporaries and waits. */
+TC_API tc_status tc_op_sepconv(tc_precision precision, const float *in, int n, int h, int w, int cin,
+                               const float *dw, const float *db, const float *pw, const float *pb, int cout,
+                               int dil, int leaky, float *out, void *cuda_stream);
 
 /* The flow input of flow_downscale = 2 alone: (c, h, w) -> (c, ceil(h/2), ceil(w/2)), each
  * output the mean of a 2 x 2 block of src, the last row and column replicated when h or w

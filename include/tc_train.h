@@ -49,7 +49,8 @@ TC_API void tc_trainer_default_desc(tc_trainer_desc *d);
 
 /* Creates a trainer: parses the weights, allocates every activation, gradient and
  * optimiser buffer for the batch.  Errors: TC_ERR_INVALID_ARG (sizes, precision),
- * TC_ERR_IO (weights), TC_ERR_OOM, TC_ERR_CUDA. */
+ * TC_ERR_IO (weights), TC_ERR_UNSUPPORTED (a TCW2 file with a refinement network: the
+ * trainer trains the network without it), TC_ERR_OOM, TC_ERR_CUDA. */
 TC_API tc_status tc_trainer_create(const tc_trainer_desc *desc, void *cuda_stream, tc_trainer **out);
 
 /* What tc_trainer_run does. */

@@ -33,11 +33,11 @@ EXPORTED = ["tc_default_consistency", "tc_create_stream", "tc_set_consistency", 
             "tc_op_last_used_tensor_cores", "tc_op_correlation_bf16_noalloc",
             "tc_tensor_core_correlation_levels", "tc_set_graphs", "tc_activation_segments",
             "tc_set_amax_recording", "tc_get_amax", "tc_set_fp8_scales", "tc_op_poisson_solve", "tc_set_latency",
-            "tc_flush", "tc_last_output_frame", "tc_op_consistency_next", "tc_op_downscale2"]
+            "tc_flush", "tc_last_output_frame", "tc_op_consistency_next", "tc_op_downscale2", "tc_op_sepconv"]
 E4M3_MAX = 448.0
 NOALLOC_SCRATCH_BYTES = 16 << 20
 PROFILE_CATEGORIES = ["pyramid_conv", "estimator_conv", "head", "correlation", "warp", "upsample", "consistency",
-                      "other", "solver"]
+                      "other", "solver", "refine"]
 
 
 class TcConsistency(ctypes.Structure):
@@ -86,13 +86,15 @@ _lib.tc_set_fp8_scales.argtypes = [_vp, ctypes.POINTER(_f), _i]
 _lib.tc_get_profile.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), _i]
 _lib.tc_set_latency.argtypes = [_vp, _i]
 _lib.tc_op_downscale2.argtypes = [_vp, _i, _i, _i, _vp, _vp]
+_lib.tc_op_sepconv.argtypes = [_i, _vp, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _i, _i, _i, _vp, _vp]
 _lib.tc_flush.argtypes = [_vp, _vp, _vp, _vp]
 _lib.tc_last_output_frame.argtypes = [_vp]
 _lib.tc_last_output_frame.restype = ctypes.c_longlong
 _lib.tc_op_consistency_next.argtypes = [_vp] * 11 + [_i] * 5 + [ctypes.POINTER(TcConsistency), _vp, _vp, _vp, _vp]
 for _n in ["tc_set_amax_recording", "tc_get_amax", "tc_set_fp8_scales", "tc_set_graphs", "tc_op_correlation_bf16_noalloc", "tc_synchronize", "tc_set_profiling", "tc_get_profile", "tc_create_stream", "tc_set_consistency", "tc_process_frame", "tc_process_frame_host", "tc_get_flows",
            "tc_destroy", "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
-           "tc_op_consistency", "tc_set_latency", "tc_flush", "tc_op_consistency_next", "tc_op_downscale2"]:
+           "tc_op_consistency", "tc_set_latency", "tc_flush", "tc_op_consistency_next", "tc_op_downscale2",
+           "tc_op_sepconv"]:
     getattr(_lib, _n).restype = ctypes.c_int
 
 
@@ -366,6 +368,20 @@ def op_poisson_solve(P, A, wc, iters=150, eta=0.15, kappa=0.2, cuda_stream=None)
                                     _ptr(wc, torch.float32, "wc"), c, h, w, int(iters), float(eta), float(kappa),
                                     O.data_ptr(), _stream_handle(cuda_stream)))
     return O
+
+
+def op_sepconv(x, dw, db, pw, pb, dil=1, leaky=True, precision="fp32", cuda_stream=None):
+    """One depthwise-separable refinement layer: x CUDA (n, h, w, cin) float32; dw (cin, 3, 3),
+    db (cin), pw (cout, cin), pb (cout) on the host.  Returns (n, h, w, cout) float32."""
+    import torch
+    n, h, w, cin = x.shape
+    cout = pw.shape[0]
+    out = torch.empty((n, h, w, cout), device=x.device, dtype=torch.float32)
+    arr = [np.ascontiguousarray(a, np.float32) for a in (dw, db, pw, pb)]
+    _check(_lib.tc_op_sepconv(PRECISION[precision], _ptr(x, torch.float32, "x"), n, h, w, cin,
+                              *[a.ctypes.data for a in arr], cout, int(dil), int(bool(leaky)), out.data_ptr(),
+                              _stream_handle(cuda_stream)))
+    return out
 
 
 def op_downscale2(src, cuda_stream=None):

@@ -65,6 +65,7 @@ struct TcLaunch {
     float q_out;          // e4m3: 1 / output activation scale
     int out_f32;          // bf16 operands only: write float32 (out_cs in floats) instead of bf16
     int accumulate;       // with out_f32: add to the output instead of overwriting it
+    int taps;             // 9: 3x3 conv; 1: pointwise 1x1 conv (the centre tap only)
 };
 
 // Epilogue shared by the conv kernels: thread r of the CTA owns accumulator row r, i.e.
@@ -157,7 +158,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int x0 = blockIdx.x * BM, y = blockIdx.y, img = blockIdx.z;
-    const int nk = 9 * p.nch;
+    const int nk = p.taps * p.nch;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -186,7 +187,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
             if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, p.err, ERR_PRODUCER)) break;
             const int tap = ks / p.nch, ch = ks - tap * p.nch;
-            const int ky = tap / 3, kx = tap - ky * 3;
+            const int ky = p.taps == 9 ? tap / 3 : 1, kx = p.taps == 9 ? tap - (tap / 3) * 3 : 1;
             const uint32_t fb = full0 + 8 * s;
             mbar_expect_tx(fb, stage_tx);
             const uint32_t dA = smem_u32(sA + s * A_BYTES), dB = smem_u32(sB + s * B_BYTES);
@@ -376,7 +377,7 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
 template <int BN, bool HEAD = false, bool F8 = false>
 cudaError_t launch_bn(const TcConvPlan &plan, const TcLaunch &lp, int n_img, cudaStream_t st) {
     dim3 grid((plan.wo + BM - 1) / BM, plan.ho, n_img);
-    if (plan.stride == 1) {
+    if (plan.stride == 1 && plan.taps == 9) {
         static bool attr_set = false;
         const size_t smem = halo_smem_for(BN);
         if (!attr_set) {
@@ -428,9 +429,10 @@ void TcConvPlan::release() {
 }
 
 bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vector<float> &wk_simt, int *err,
-                  std::string &why, bool f8) {
+                  std::string &why, bool f8, int taps) {
     plan.enabled = false;
     plan.head = false;
+    if (taps != 9 && (taps != 1 || a.stride != 1)) { why = "taps must be 9, or 1 at stride 1"; return false; }
     const int bn = a.cout;
     const int align = f8 ? 16 : 8;  // 16-byte TMA strides and vector stores
     if (bn < 16 || bn > 128 || bn % 16 != 0) { why = "cout must be a multiple of 16 in [16, 128]"; return false; }
@@ -451,18 +453,18 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
     const int nch = (a.cin + kc - 1) / kc, cinp = nch * kc;
     const CUtensorMapSwizzle swz = rb == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
                                             : (rb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);
-    // Packed weights [9][cout][cinp] (zero beyond cin): bfloat16, or e4m3 with one scale per
-    // output channel (amax / 448 over its 9 x cin weights).
-    std::vector<uint8_t> pk((size_t)9 * bn * cinp * esz, 0);
+    // Packed weights [taps][cout][cinp] (zero beyond cin): bfloat16, or e4m3 with one scale
+    // per output channel (amax / 448 over its taps x cin weights).
+    std::vector<uint8_t> pk((size_t)taps * bn * cinp * esz, 0);
     std::vector<float> ws(bn, 1.f);
     if (f8) {
         for (int o = 0; o < bn; ++o) {
             float amax = 0.f;
-            for (size_t k = 0; k < (size_t)9 * a.cin; ++k) amax = fmaxf(amax, fabsf(wk_simt[k * bn + o]));
+            for (size_t k = 0; k < (size_t)taps * a.cin; ++k) amax = fmaxf(amax, fabsf(wk_simt[k * bn + o]));
             ws[o] = amax > 0.f ? amax / 448.f : 1.f;
         }
     }
-    for (int tap = 0; tap < 9; ++tap)
+    for (int tap = 0; tap < taps; ++tap)
         for (int c = 0; c < a.cin; ++c)
             for (int o = 0; o < bn; ++o) {
                 const float v = wk_simt[((size_t)tap * a.cin + c) * bn + o];
@@ -496,7 +498,8 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
     if (a.stride == 1) {
         const cuuint64_t dims[4] = {(cuuint64_t)a.cin, (cuuint64_t)a.w, (cuuint64_t)a.h, (cuuint64_t)n_in};
         const cuuint64_t strides[3] = {a.in_cs * esz, (cuuint64_t)a.w * a.in_cs * esz, (cuuint64_t)a.h * a.w * a.in_cs * esz};
-        const cuuint32_t box[4] = {(cuuint32_t)kc, HALO_ROWS, 1, 1};  // the stride-1 kernel loads halo rows
+        // the 3x3 stride-1 kernel loads halo rows; the pointwise one tiles of BM pixels
+        const cuuint32_t box[4] = {(cuuint32_t)kc, taps == 9 ? HALO_ROWS : (cuuint32_t)BM, 1, 1};
         r = enc(&plan.tmA, dt, 4, const_cast<void *>(a.in), dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     } else {
@@ -508,7 +511,7 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
                 swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     }
     if (r == CUDA_SUCCESS) {
-        const cuuint64_t dims[3] = {(cuuint64_t)cinp, (cuuint64_t)bn, 9};
+        const cuuint64_t dims[3] = {(cuuint64_t)cinp, (cuuint64_t)bn, (cuuint64_t)taps};
         const cuuint64_t strides[2] = {(cuuint64_t)cinp * esz, (cuuint64_t)bn * cinp * esz};
         const cuuint32_t box[3] = {(cuuint32_t)kc, (cuuint32_t)bn, 1};
         r = enc(&plan.tmB, dt, 3, wdev, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -522,6 +525,7 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
     }
     plan.bn = bn;
     plan.cout = bn;
+    plan.taps = taps;
     plan.nch = nch;
     plan.kc = kc;
     plan.rb = rb;
@@ -543,15 +547,15 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
 }
 
 bool tc_plan_head(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vector<float> &wk_simt, int *err,
-                  std::string &why, bool f8) {
+                  std::string &why, bool f8, int taps) {
     if (a.cout > 16) { why = "head has more than 16 outputs"; return false; }
-    std::vector<float> wk16((size_t)9 * a.cin * 16, 0.f);
-    for (size_t k = 0; k < (size_t)9 * a.cin; ++k)
+    std::vector<float> wk16((size_t)taps * a.cin * 16, 0.f);
+    for (size_t k = 0; k < (size_t)taps * a.cin; ++k)
         for (int o = 0; o < a.cout; ++o) wk16[k * 16 + o] = wk_simt[k * a.cout + o];
     ConvArgs a16 = a;
     a16.cout = 16;
     a16.out_cs = 16;  // not used by the head epilogue
-    if (!tc_plan_conv(plan, a16, n_in, wk16, err, why, f8)) return false;
+    if (!tc_plan_conv(plan, a16, n_in, wk16, err, why, f8, taps)) return false;
     plan.head = true;
     plan.cout = a.cout;
     return true;
@@ -569,7 +573,7 @@ cudaError_t launch_conv_tc_head(const TcConvPlan &plan, const ConvArgs &a, const
     int img_off = 0;
     if (!plan.enabled || !plan.head || !image_offset(plan, a, &img_off)) return cudaErrorInvalidValue;
     TcLaunch lp{plan.nch, plan.kc, plan.rb, plan.stride, plan.ho, plan.wo, img_off, nullptr, 0, a.bias, 0, plan.err,
-                flow, up, plan.wscale, 1.f, 0, 0};
+                flow, up, plan.wscale, 1.f, 0, 0, plan.taps};
     return plan.f8 ? launch_bn<16, true, true>(plan, lp, a.n, st) : launch_bn<16, true, false>(plan, lp, a.n, st);
 }
 
@@ -593,7 +597,7 @@ cudaError_t launch_conv_tc(const TcConvPlan &plan, const ConvArgs &a, cudaStream
     if (!plan.enabled || plan.head || !image_offset(plan, a, &img_off)) return cudaErrorInvalidValue;
     if (reinterpret_cast<uintptr_t>(a.out) % 16 != 0 || a.out_cs % (plan.f8 ? 16 : 8) != 0) return cudaErrorInvalidValue;
     TcLaunch lp{plan.nch, plan.kc, plan.rb, plan.stride, plan.ho, plan.wo, img_off, a.out, a.out_cs, a.bias, a.leaky,
-                plan.err, nullptr, nullptr, plan.wscale, a.q_out, 0, 0};
+                plan.err, nullptr, nullptr, plan.wscale, a.q_out, 0, 0, plan.taps};
     return plan.f8 ? launch_any_bn<true>(plan, lp, a.n, st) : launch_any_bn<false>(plan, lp, a.n, st);
 }
 
@@ -602,7 +606,7 @@ cudaError_t launch_conv_tc_f32(const TcConvPlan &plan, const ConvArgs &a, bool a
     if (!plan.enabled || plan.head || plan.f8 || !image_offset(plan, a, &img_off)) return cudaErrorInvalidValue;
     if (reinterpret_cast<uintptr_t>(a.out) % 16 != 0 || a.out_cs % 4 != 0) return cudaErrorInvalidValue;
     TcLaunch lp{plan.nch, plan.kc, plan.rb, plan.stride, plan.ho, plan.wo, img_off, a.out, a.out_cs, a.bias, a.leaky,
-                plan.err, nullptr, nullptr, plan.wscale, 1.f, 1, accumulate ? 1 : 0};
+                plan.err, nullptr, nullptr, plan.wscale, 1.f, 1, accumulate ? 1 : 0, plan.taps};
     return launch_any_bn<false>(plan, lp, a.n, st);
 }
 

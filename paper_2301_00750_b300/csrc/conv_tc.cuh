@@ -21,6 +21,7 @@ struct TcConvPlan {
     CUtensorMap tmB;
     int bn = 0, nch = 0, stride = 1, h = 0, w = 0, ho = 0, wo = 0, n_in = 0, cout = 0;
     int kc = 0, rb = 0;  // channels and bytes of one K step (rb = 32, 64 or 128: the swizzle span)
+    int taps = 9;        // 9: 3x3 conv; 1: pointwise 1x1 conv
     const void *in_base = nullptr;  // start of the buffer the A descriptor covers
     size_t img_bytes = 0;           // bytes between consecutive images of that buffer
     void *wpk = nullptr;            // packed weights (owned by the plan)
@@ -38,13 +39,14 @@ struct TcConvPlan {
 // f8: e4m3 operands; wk_simt then holds the weights with the input activations' scales
 // already folded in (w[o][c] * s_in[c]); the epilogue multiplies by the per-output-channel
 // weight scale and quantizes with a.q_out.
+// taps = 1 plans a pointwise 1x1 conv (stride 1; wk_simt then holds [a.cin][a.cout]).
 bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vector<float> &wk_simt, int *err,
-                  std::string &why, bool f8 = false);
+                  std::string &why, bool f8 = false, int taps = 9);
 
 // Plans the flow head (cout <= 16, no activation; in practice 2) on the tensor cores: the
 // weights are zero-padded to 16 outputs for the MMA.
 bool tc_plan_head(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vector<float> &wk_simt, int *err,
-                  std::string &why, bool f8 = false);
+                  std::string &why, bool f8 = false, int taps = 9);
 
 // Launches a planned head: flow[i] = up[i] (if up) + bias + conv(a.in)[i][0..1], float (n, ho, wo, 2).
 cudaError_t launch_conv_tc_head(const TcConvPlan &plan, const ConvArgs &a, const float *up, float *flow,

@@ -16,6 +16,7 @@
 #include "conv_tc.cuh"
 #include "engine_internal.h"
 #include "solver.cuh"
+#include "refine.cuh"
 #include "corr_tc.cuh"
 
 namespace tc {
@@ -31,7 +32,11 @@ bool parse_weights(const uint8_t *p, size_t n, HostNet &net, std::string &err) {
         return true;
     };
     char magic[4];
-    if (!rd(magic, 4) || memcmp(magic, "TCW1", 4) != 0) { err = "weights: bad magic (want TCW1)"; return false; }
+    if (!rd(magic, 4) || (memcmp(magic, "TCW1", 4) != 0 && memcmp(magic, "TCW2", 4) != 0)) {
+        err = "weights: bad magic (want TCW1 or TCW2)";
+        return false;
+    }
+    const bool v2 = memcmp(magic, "TCW2", 4) == 0;
     int32_t lv, rad;
     if (!rd(&lv, 4) || !rd(&rad, 4)) { err = "weights: truncated header"; return false; }
     if (lv < 2 || lv > 7 || rad < 1 || rad > 4) { err = "weights: levels must be 2..7 and radius 1..4"; return false; }
@@ -80,6 +85,36 @@ bool parse_weights(const uint8_t *p, size_t n, HostNet &net, std::string &err) {
         }
         for (int j = 0; j < 5; ++j)
             if (E[j].stride != 1) { err = "weights: estimator convs must have stride 1"; return false; }
+    }
+    net.ref.clear();
+    if (v2) {
+        // the refinement section: reads cat(flow, x4, x3) of the level-2 estimator
+        int32_t nr;
+        if (!rd(&nr, 4) || nr < 1 || nr > 16) { err = "weights: refinement layer count must be 1..16"; return false; }
+        int cin = 2 + net.dec[3] + net.dec[2];
+        for (int k = 0; k < nr; ++k) {
+            HostSep R;
+            int32_t h4[4];
+            if (!rd(h4, 16)) { err = "weights: truncated refinement header"; return false; }
+            R.cin = h4[0]; R.cout = h4[1]; R.dil = h4[2]; R.leaky = h4[3];
+            const bool last = k == nr - 1;
+            if (R.cin != cin || R.dil < 1 || R.dil > 64 || (last ? (R.cout != 2 || R.leaky) : (R.cout % 8 != 0 || R.cout > 256))) {
+                err = "weights: refinement layer shapes (cin chain from 2 + x4 + x3, cout multiple of 8 up to 256, "
+                      "the last 2 outputs without activation, dilation 1..64)";
+                return false;
+            }
+            R.dw.resize((size_t)R.cin * 9);
+            R.db.resize(R.cin);
+            R.pw.resize((size_t)R.cout * R.cin);
+            R.pb.resize(R.cout);
+            if (!rd(R.dw.data(), 4 * R.dw.size()) || !rd(R.db.data(), 4 * R.db.size()) ||
+                !rd(R.pw.data(), 4 * R.pw.size()) || !rd(R.pb.data(), 4 * R.pb.size())) {
+                err = "weights: truncated refinement data";
+                return false;
+            }
+            cin = R.cout;
+            net.ref.push_back(std::move(R));
+        }
     }
     return true;
 }
@@ -149,6 +184,18 @@ size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precisi
     total += 6 * img;                                        // state I, P, O x 2 slots
     total += 3 * img + al(plane * 4) + al(plane);            // host-entry staging
     if (fs > 1) total += al((size_t)3 * hn * wn * 4);        // the downscaled frame
+    if (!net.ref.empty()) {                                  // refinement buffers and weights
+        const size_t px2 = (Hp >> 2) * (Wp >> 2);
+        int dcs = 0, pcs = 8;
+        for (size_t k = 0; k < net.ref.size(); ++k) {
+            dcs = std::max(dcs, round_up(net.ref[k].cin, 8));
+            if (k + 1 < net.ref.size()) pcs = std::max(pcs, round_up(net.ref[k].cout, 8));
+            const size_t cp = round_up(net.ref[k].cin, 8);
+            total += al(9 * cp * 4) + al(cp * 4) + al(cp * net.ref[k].cout * 4) + al(net.ref[k].cout * 4);
+            if (bf) total += al(cp * std::max(16, net.ref[k].cout) * 2);
+        }
+        total += al(2 * px2 * dcs * es) + al(2 * px2 * pcs * es);
+    }
     return total;
 }
 
@@ -263,6 +310,18 @@ struct tc_stream {
     int latency = 0;
     float *Fprev = nullptr;
     long long last_out = -1;  // index in its sequence of the frame the last call wrote
+    // refinement network (TCW2): per layer the depthwise taps and bias and the pointwise
+    // weights in buffer channel order, its tensor-core plan (BF16) or none (CUDA cores);
+    // refD holds the depthwise outputs, refP the pointwise ones, both for the two flow
+    // directions at level 2
+    struct RefLayer {
+        int cin_p = 0, nin = 0, cout = 0, dil = 1, leaky = 1;
+        float *dw = nullptr, *db = nullptr, *pw = nullptr, *pb = nullptr;
+        TcConvPlan plan;
+    };
+    std::vector<RefLayer> ref;
+    void *refD = nullptr, *refP = nullptr;
+    int refD_cs = 0, refP_cs = 0;
 };
 
 static std::mutex g_err_mu;
@@ -328,6 +387,7 @@ static void free_all(tc_stream *s) {
     }
     for (auto &lvl : s->pyr_plan)
         for (auto &pl : lvl) pl.release();
+    for (auto &R : s->ref) R.plan.release();
     for (void *p : s->allocs) cudaFree(p);
     s->allocs.clear();
 }
@@ -412,6 +472,71 @@ static void add_layer(tc_stream *s, TcConvPlan &plan, const ConvArgs &a, int n_i
         return;
     }
     s->recs.push_back(tc_stream::LayerRec{&plan, a, n_in, std::move(wk), std::move(in_seg), head});
+}
+
+// Refinement layers of a TCW2 net: weights in buffer channel order (the first layer's
+// input is [x3 | x4 | flow | zero pad] in the buffers, cat(flow, x4, x3) in the file),
+// the two activation buffers, and for BF16 a pointwise tensor-core plan per layer.
+template <typename T>
+static tc_status build_refine(tc_stream *s) {
+    const HostNet &net = s->net;
+    if (s->prec == TC_FP8_E4M3)
+        return fail(s, TC_ERR_UNSUPPORTED, "the refinement network runs in TC_FP32 or TC_BF16 streams");
+    const LevelBufs &B = s->lv[1];
+    const size_t px = (size_t)B.h * B.w;
+    const int c3 = net.dec[2], c4 = net.dec[3];
+    auto ru8 = [](int v) { return (v + 7) / 8 * 8; };
+    const int nl = (int)net.ref.size();
+    s->ref.resize(nl);
+    int dcs = 0, pcs = 8;
+    for (int k = 0; k < nl; ++k) {
+        dcs = std::max(dcs, ru8(net.ref[k].cin));
+        if (k < nl - 1) pcs = std::max(pcs, ru8(net.ref[k].cout));
+    }
+    s->refD_cs = dcs;
+    s->refP_cs = pcs;
+    tc_status r;
+    if ((r = dalloc(s, &s->refD, 2 * px * dcs * sizeof(T))) != TC_OK) return r;
+    if ((r = dalloc(s, &s->refP, 2 * px * pcs * sizeof(T))) != TC_OK) return r;
+    TC_TRY(s, cudaMemset(s->refD, 0, 2 * px * dcs * sizeof(T)), "memset");
+    TC_TRY(s, cudaMemset(s->refP, 0, 2 * px * pcs * sizeof(T)), "memset");
+    for (int k = 0; k < nl; ++k) {
+        const HostSep &H = net.ref[k];
+        tc_stream::RefLayer &R = s->ref[k];
+        R.cin_p = ru8(H.cin);
+        R.nin = k == 0 ? c3 + c4 : H.cin;
+        R.cout = H.cout;
+        R.dil = H.dil;
+        R.leaky = H.leaky;
+        // buffer channel g -> file channel (-1: zero padding)
+        std::vector<int> src(R.cin_p, -1);
+        for (int g = 0; g < H.cin; ++g) {
+            if (k > 0) src[g] = g;
+            else if (g < c3) src[g] = 2 + c4 + g;            // x3
+            else if (g < c3 + c4) src[g] = 2 + (g - c3);     // x4
+            else src[g] = g - c3 - c4;                       // flow u, v
+        }
+        std::vector<float> dw((size_t)9 * R.cin_p, 0.f), db(R.cin_p, 0.f), pw((size_t)R.cin_p * H.cout, 0.f);
+        for (int g = 0; g < R.cin_p; ++g) {
+            if (src[g] < 0) continue;
+            for (int t = 0; t < 9; ++t) dw[(size_t)t * R.cin_p + g] = H.dw[(size_t)src[g] * 9 + t];
+            db[g] = H.db[src[g]];
+            for (int o = 0; o < H.cout; ++o) pw[(size_t)g * H.cout + o] = H.pw[(size_t)o * H.cin + src[g]];
+        }
+        if ((r = upload(s, &R.dw, dw)) != TC_OK || (r = upload(s, &R.db, db)) != TC_OK ||
+            (r = upload(s, &R.pw, pw)) != TC_OK || (r = upload(s, &R.pb, H.pb)) != TC_OK)
+            return r;
+        if (s->prec == TC_BF16) {
+            const bool last = k == nl - 1;
+            ConvArgs a{s->refD, dcs, 1, B.h, B.w, R.cin_p, 1, B.h, B.w, nullptr, nullptr, last ? 2 : H.cout,
+                       last ? nullptr : s->refP, last ? 16 : pcs, H.leaky};
+            std::string why;
+            const bool ok = last ? tc_plan_head(R.plan, a, 2, pw, s->dev_err, why, false, 1)
+                                 : tc_plan_conv(R.plan, a, 2, pw, s->dev_err, why, false, 1);
+            if (ok) s->tc_layers += 1;
+        }
+    }
+    return TC_OK;
 }
 
 template <typename T>
@@ -526,6 +651,7 @@ static tc_status build_stream(tc_stream *s) {
             add_layer(s, B.headplan, a, 2, wk5, g5, true);
         }
     }
+    if (!net.ref.empty() && (r = build_refine<T>(s)) != TC_OK) return r;
     const size_t img = (size_t)3 * s->H * s->W * sizeof(float);
     for (int k = 0; k < 2; ++k) {
         if ((r = dalloc_t(s, &s->sI[k], img)) != TC_OK) return r;
@@ -690,6 +816,52 @@ static tc_status run_pyramid(tc_stream *s, const float *img, int slot) {
     return TC_OK;
 }
 
+// The refinement of the level-2 flows of both directions (Sec. 3.2 "-sepref"): each layer a
+// depthwise dilated 3x3 conv (CUDA cores) and a pointwise conv (tensor cores for BF16); the
+// first reads [x3 | x4 | flow] (the buffer order of cat(flow, x4, x3)), the last adds its
+// two outputs to the flow in place.
+template <typename T>
+static tc_status run_refine(tc_stream *s) {
+    if constexpr (sizeof(T) == 1) {
+        return fail(s, TC_ERR_UNSUPPORTED, "the refinement network runs in TC_FP32 or TC_BF16 streams");
+    } else {
+    LevelBufs &B = s->lv[1];
+    T *dec = static_cast<T *>(B.dec);
+    const size_t px = (size_t)B.h * B.w;
+    const int nl = (int)s->ref.size();
+    for (int k = 0; k < nl; ++k) {
+        tc_stream::RefLayer &R = s->ref[k];
+        DwArgs d{};
+        d.in = k == 0 ? static_cast<const void *>(dec + B.off_x3) : s->refP;
+        d.in_cs = k == 0 ? B.ctot : s->refP_cs;
+        d.nin = R.nin;
+        d.flow = k == 0 ? B.flow : nullptr;
+        d.n = 2; d.h = B.h; d.w = B.w;
+        d.dw = R.dw; d.db = R.db; d.dil = R.dil;
+        d.out = s->refD; d.out_cs = s->refD_cs; d.cp = R.cin_p;
+        TC_LAUNCH_CAT(s, TC_PROF_REFINE, launch_depthwise<T>(d, s->st));
+        const bool last = k == nl - 1;
+        if (R.plan.enabled) {
+            ConvArgs a{s->refD, s->refD_cs, 2, B.h, B.w, R.cin_p, 1, B.h, B.w, nullptr, R.pb, last ? 2 : R.cout,
+                       last ? nullptr : s->refP, last ? 16 : s->refP_cs, R.leaky};
+            if (last)
+                TC_LAUNCH_CAT(s, TC_PROF_REFINE, launch_conv_tc_head(R.plan, a, B.flow, B.flow, s->st));
+            else
+                TC_LAUNCH_CAT(s, TC_PROF_REFINE, launch_conv_tc(R.plan, a, s->st));
+        } else {
+            PwArgs pa{};
+            pa.in = s->refD; pa.in_cs = s->refD_cs; pa.cin = R.cin_p;
+            pa.w = R.pw; pa.b = R.pb; pa.cout = R.cout; pa.leaky = R.leaky;
+            pa.out = last ? nullptr : s->refP; pa.out_cs = s->refP_cs;
+            pa.flow = last ? B.flow : nullptr;
+            pa.npx = 2 * px;
+            TC_LAUNCH_CAT(s, TC_PROF_REFINE, launch_pointwise<T>(pa, s->st));
+        }
+    }
+    return TC_OK;
+    }
+}
+
 // Both directions at once (batch entry 0: self = frame t, other = t-1, giving F_{t->t-1};
 // entry 1: self = t-1, other = t, giving F_{t-1->t}).
 template <typename T>
@@ -749,7 +921,7 @@ static tc_status run_estimators(tc_stream *s, int slot_cur) {
             TC_LAUNCH_CAT(s, TC_PROF_HEAD, launch_head<T>(ha, s->st));
         }
     }
-    return TC_OK;
+    return s->ref.empty() ? TC_OK : run_refine<T>(s);
 }
 
 static tc_status check_stream(tc_stream *s, const char *fn) {
@@ -1291,6 +1463,7 @@ extern "C" size_t tc_stream_device_bytes(const tc_stream *s) {
     }
     for (const auto &lvl : s->pyr_plan)
         for (const auto &pl : lvl) b += pl.wpk_bytes;
+    for (const auto &R : s->ref) b += R.plan.wpk_bytes;
     return b;
 }
 
@@ -1406,6 +1579,87 @@ extern "C" tc_status tc_op_conv3x3(tc_precision precision, const float *in, int 
     if (precision == TC_FP8_E4M3)
         return op_conv<__nv_fp8_e4m3>(in, n, h, w, cin, w_oihw, bias, cout, stride, leaky, out, st);
     return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_conv3x3: precision");
+}
+
+// One depthwise-separable layer on its own (see tc_op_sepconv).
+template <typename T>
+static tc_status op_sepconv(const float *in, int n, int h, int w, int cin, const float *dw, const float *db,
+                            const float *pw, const float *pb, int cout, int dil, int leaky, float *out,
+                            cudaStream_t st) {
+    const bool bf = sizeof(T) == 2;
+    const bool head = cout == 2;
+    const size_t npx = (size_t)n * h * w;
+    // weights in the engine's layout: depthwise [9][cin], pointwise [cin][cout]
+    std::vector<float> dwk((size_t)9 * cin), pwk((size_t)cin * cout);
+    for (int c = 0; c < cin; ++c)
+        for (int t = 0; t < 9; ++t) dwk[(size_t)t * cin + c] = dw[(size_t)c * 9 + t];
+    for (int c = 0; c < cin; ++c)
+        for (int o = 0; o < cout; ++o) pwk[(size_t)c * cout + o] = pw[(size_t)o * cin + c];
+    TmpAlloc tmp;
+    float *ddw, *ddb, *dpw, *dpb, *flow = nullptr;
+    T *x, *d, *o = nullptr;
+    OP_TRY(tmp.get((void **)&ddw, dwk.size() * 4), "tc_op_sepconv alloc");
+    OP_TRY(tmp.get((void **)&ddb, (size_t)cin * 4), "tc_op_sepconv alloc");
+    OP_TRY(tmp.get((void **)&dpw, pwk.size() * 4), "tc_op_sepconv alloc");
+    OP_TRY(tmp.get((void **)&dpb, (size_t)cout * 4), "tc_op_sepconv alloc");
+    OP_TRY(tmp.get((void **)&x, npx * cin * sizeof(T)), "tc_op_sepconv alloc");
+    OP_TRY(tmp.get((void **)&d, npx * cin * sizeof(T)), "tc_op_sepconv alloc");
+    if (head) {
+        OP_TRY(tmp.get((void **)&flow, npx * 2 * 4), "tc_op_sepconv alloc");
+        OP_TRY(cudaMemsetAsync(flow, 0, npx * 2 * 4, st), "tc_op_sepconv memset");
+    } else {
+        OP_TRY(tmp.get((void **)&o, npx * cout * sizeof(T)), "tc_op_sepconv alloc");
+    }
+    OP_TRY(cudaMemcpyAsync(ddw, dwk.data(), dwk.size() * 4, cudaMemcpyHostToDevice, st), "tc_op_sepconv copy");
+    OP_TRY(cudaMemcpyAsync(ddb, db, (size_t)cin * 4, cudaMemcpyHostToDevice, st), "tc_op_sepconv copy");
+    OP_TRY(cudaMemcpyAsync(dpw, pwk.data(), pwk.size() * 4, cudaMemcpyHostToDevice, st), "tc_op_sepconv copy");
+    OP_TRY(cudaMemcpyAsync(dpb, pb, (size_t)cout * 4, cudaMemcpyHostToDevice, st), "tc_op_sepconv copy");
+    OP_TRY(launch_to_act<T>(in, npx * cin, x, st), "tc_op_sepconv convert");
+    DwArgs da{x, cin, cin, nullptr, n, h, w, ddw, ddb, dil, d, cin, cin};
+    OP_TRY(launch_depthwise<T>(da, st), "tc_op_sepconv depthwise launch");
+    TcConvPlan plan;
+    int *derr = nullptr;
+    OP_TRY(tmp.get((void **)&derr, sizeof(int)), "tc_op_sepconv alloc");
+    OP_TRY(cudaMemsetAsync(derr, 0, sizeof(int), st), "tc_op_sepconv memset");
+    ConvArgs a{d, cin, n, h, w, cin, 1, h, w, nullptr, dpb, cout, o, head ? 16 : cout, leaky};
+    std::string why;
+    const bool use_tc = bf && (head ? tc_plan_head(plan, a, n, pwk, derr, why, false, 1)
+                                    : tc_plan_conv(plan, a, n, pwk, derr, why, false, 1));
+    if (use_tc) {
+        const cudaError_t e = head ? launch_conv_tc_head(plan, a, flow, flow, st) : launch_conv_tc(plan, a, st);
+        if (e != cudaSuccess) {
+            plan.release();
+            return fail(nullptr, TC_ERR_CUDA, std::string("tc_op_sepconv tensor-core launch: ") + cudaGetErrorString(e));
+        }
+    } else {
+        PwArgs pa{d, cin, cin, dpw, dpb, cout, leaky, o, cout, flow, npx};
+        OP_TRY(launch_pointwise<T>(pa, st), "tc_op_sepconv pointwise launch");
+    }
+    if (head)
+        OP_TRY(cudaMemcpyAsync(out, flow, npx * 2 * 4, cudaMemcpyDeviceToDevice, st), "tc_op_sepconv copy");
+    else
+        OP_TRY(launch_from_act<T>(o, npx * cout, out, st), "tc_op_sepconv convert");
+    const cudaError_t se = cudaStreamSynchronize(st);
+    plan.release();
+    OP_TRY(se, "tc_op_sepconv sync");
+    int e = 0;
+    OP_TRY(cudaMemcpy(&e, derr, sizeof(int), cudaMemcpyDeviceToHost), "tc_op_sepconv error word");
+    if (e != 0) return fail(nullptr, TC_ERR_TIMEOUT, "tc_op_sepconv: tensor-core kernel gave up waiting");
+    g_last_op_tc = use_tc ? 1 : 0;
+    return TC_OK;
+}
+
+extern "C" tc_status tc_op_sepconv(tc_precision precision, const float *in, int n, int h, int w, int cin,
+                                   const float *dw, const float *db, const float *pw, const float *pb, int cout,
+                                   int dil, int leaky, float *out, void *cuda_stream) {
+    if (!in || !dw || !db || !pw || !pb || !out || n < 1 || h < 1 || w < 1 || cin < 8 || cin % 8 != 0 ||
+        cin > 512 || (cout != 2 && (cout < 8 || cout % 8 != 0 || cout > 256)) || dil < 1 || dil > 64)
+        return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_sepconv: bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (precision == TC_FP32) return op_sepconv<float>(in, n, h, w, cin, dw, db, pw, pb, cout, dil, leaky, out, st);
+    if (precision == TC_BF16)
+        return op_sepconv<__nv_bfloat16>(in, n, h, w, cin, dw, db, pw, pb, cout, dil, leaky, out, st);
+    return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_sepconv: precision must be TC_FP32 or TC_BF16");
 }
 
 template <typename T>

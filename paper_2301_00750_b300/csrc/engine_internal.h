@@ -16,11 +16,22 @@ struct HostLayer {
     std::vector<float> b;
 };
 
+// One depthwise-separable refinement layer: depthwise 3x3 with dilation (bias, no
+// activation), then pointwise 1x1 (bias, LeakyReLU if leaky).
+struct HostSep {
+    int cin, cout, dil, leaky;
+    std::vector<float> dw;  // [cin][3][3]
+    std::vector<float> db;  // [cin]
+    std::vector<float> pw;  // [cout][cin]
+    std::vector<float> pb;  // [cout]
+};
+
 struct HostNet {
     int levels = 0, radius = 0;
     std::vector<int> chans;
     int dec[4] = {0, 0, 0, 0};
     std::vector<HostLayer> layers;
+    std::vector<HostSep> ref;  // refinement network after the level-2 estimator (TCW2), or empty
 };
 
 // Parses and shape-checks a TCW1 weight blob (layout in include/tc_stream.h).

@@ -665,6 +665,8 @@ extern "C" tc_status tc_trainer_create(const tc_trainer_desc *d, void *cuda_stre
     std::string err;
     if (!read_blob(d, blob, err)) return tc_record_error(d->weights_path ? TC_ERR_IO : TC_ERR_INVALID_ARG, err);
     if (!parse_weights(blob.data(), blob.size(), t->net, err)) return tc_record_error(TC_ERR_IO, err);
+    if (!t->net.ref.empty())
+        return tc_record_error(TC_ERR_UNSUPPORTED, "tc_trainer_create: the trainer has no refinement network");
     t->L = t->net.levels;
     t->R = t->net.radius;
     t->D = (2 * t->R + 1) * (2 * t->R + 1);
