@@ -322,7 +322,7 @@ TC_API tc_status tc_op_upsample_flow(const float *flow, int n, int h, int w, int
 /* One layer of the refinement network with depthwise-separable convs (Sec. 3.2 "-sepref";
  * TCW2 weight files) on its own: out = LeakyReLU_if_leaky(pb + pw * (db + dw (*) in)), with
  * dw (*) the depthwise 3x3 conv of dilation dil (zero padding) and pw * the pointwise 1x1
- * conv.  in: device (n, h, w, cin) float32 NHWC, cin a multiple of 8 (<= 512); dw (cin, 3, 3),
+ * conv.  in: device (n, h, w, cin) float32 NHWC, cin a multiple of 8 (<= 256); dw (cin, 3, 3),
  * db (cin), pw (cout, cin), pb (cout): host float32; cout a multiple of 8 (<= 256) written to
  * out (n, h, w, cout), or cout = 2 (the refinement's last layer, no activation) written as
  * float pairs.  precision TC_FP32 (CUDA cores) or TC_BF16 (activations rounded to bfloat16,

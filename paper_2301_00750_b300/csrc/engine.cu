@@ -1653,7 +1653,7 @@ extern "C" tc_status tc_op_sepconv(tc_precision precision, const float *in, int 
                                    const float *dw, const float *db, const float *pw, const float *pb, int cout,
                                    int dil, int leaky, float *out, void *cuda_stream) {
     if (!in || !dw || !db || !pw || !pb || !out || n < 1 || h < 1 || w < 1 || cin < 8 || cin % 8 != 0 ||
-        cin > 512 || (cout != 2 && (cout < 8 || cout % 8 != 0 || cout > 256)) || dil < 1 || dil > 64)
+        cin > 256 || (cout != 2 && (cout < 8 || cout % 8 != 0 || cout > 256)) || dil < 1 || dil > 64)
         return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_sepconv: bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (precision == TC_FP32) return op_sepconv<float>(in, n, h, w, cin, dw, db, pw, pb, cout, dil, leaky, out, st);
