@@ -374,9 +374,173 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     }
 }
 
+// Multi-row stride-1 variant for narrow layers (at most 32 outputs) whose input channels
+// fit one or two K steps (the launcher takes it for one): there the per-CTA
+// set-up (TMEM allocation, barriers, pipeline fill) outweighs the few MMAs of one row.  A
+// CTA computes ROWS output rows of one 128-pixel column tile:
+//   * warp 4, lane 0 (producer): the 9 x nch weight tiles once, then the halo units
+//     (input row, channel step) of the ROWS + 2 input rows [x0 - 1, x0 + 129) in order
+//     through a ring of RING x nch slots; each input row is loaded once for the three
+//     output rows that read it;
+//   * warp 5, lane 0 (MMA issuer): for output row r the nine taps of every channel step
+//     from input rows r, r + 1, r + 2 into TMEM accumulator r % 2; then it frees the units
+//     of input row r (their last reader) and signals the accumulator;
+//   * warps 0-3 (epilogue): drain accumulator r % 2 into output row y0 + r while the MMAs of
+//     row r + 1 run, then hand the accumulator back.
+// Every wait is bounded as in the kernels above.
+constexpr int ROWS = 8;
+constexpr int RING = 4;  // input rows held at once
+__host__ __device__ constexpr uint32_t halo_slot_for(int rb) { return (uint32_t)((HALO_ROWS * rb + 1023) / 1024 * 1024); }
+__host__ __device__ constexpr uint32_t wtile_for(int bn, int rb) { return (uint32_t)((bn * rb + 1023) / 1024 * 1024); }
+__host__ __device__ constexpr size_t rows_smem_for(int bn, int rb, int nch) {
+    return (size_t)RING * nch * halo_slot_for(rb) + 9 * (size_t)nch * wtile_for(bn, rb) + 1024 + 256;
+}
+
+template <int BN, bool HEAD, bool F8, int NCH>
+__global__ void __launch_bounds__(192, 1)
+conv_tc_rows_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcLaunch p) {
+    constexpr uint32_t ACC_COLS = tmem_cols_for(BN);
+    constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    constexpr int nch = NCH, ru = RING * NCH;  // channel steps (p.nch), ring units
+    const uint32_t hslot = halo_slot_for(p.rb), wtile = wtile_for(BN, p.rb);
+    uint8_t *sA = smem;
+    uint8_t *sW = smem + ru * hslot;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sW + 9 * nch * wtile);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * ru + 5);
+    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * ru, wfull = empty0 + 8 * ru;
+    const uint32_t accf0 = wfull + 8, acce0 = accf0 + 16;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x0 = blockIdx.x * BM, y0 = blockIdx.y * ROWS, img = blockIdx.z;
+    const int nrows = p.ho - y0 < ROWS ? p.ho - y0 : ROWS;
+    const int nunits = (nrows + 2) * nch;  // input rows y0 - 1 .. y0 + nrows, every channel step
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ru; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(wfull, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf0 + 8 * b, 1);
+            mbar_init(acce0 + 8 * b, 4);  // one arrival per epilogue warp
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 4 && lane == 0) {
+        // ---- producer
+        mbar_expect_tx(wfull, 9u * (uint32_t)nch * BN * (uint32_t)p.rb);
+        for (int t = 0; t < 9; ++t)
+            for (int ch = 0; ch < nch; ++ch)
+                tma_load_3d(&tmB, wfull, smem_u32(sW + (t * nch + ch) * wtile), ch * p.kc, 0, t);
+        int issued = 0;
+        for (int u = 0; u < nunits; ++u) {
+            const int s = u % ru, i = u / nch, ch = u - i * nch;
+            if (!mbar_wait(empty0 + 8 * s, ((uint32_t)(u / ru) & 1u) ^ 1u, p.err, ERR_PRODUCER)) break;
+            mbar_expect_tx(full0 + 8 * s, HALO_ROWS * (uint32_t)p.rb);
+            tma_load_4d(&tmA, full0 + 8 * s, smem_u32(sA + s * hslot), ch * p.kc, x0 - 1, y0 - 1 + i,
+                        img + p.img_off);
+            issued = u + 1;
+        }
+        if (issued < nunits) {
+            // Error path: let the loads already issued land before the CTA exits.
+            const unsigned long long t0 = global_ns();
+            while (!mbar_try(wfull, 0))
+                if (global_ns() - t0 > WAIT_NS) { atomicCAS(p.err, 0, ERR_DRAIN); break; }
+            for (int u = issued - ru < 0 ? 0 : issued - ru; u < issued; ++u)
+                while (!mbar_try(full0 + 8 * (u % ru), (uint32_t)(u / ru) & 1u))
+                    if (global_ns() - t0 > WAIT_NS) { atomicCAS(p.err, 0, ERR_DRAIN); break; }
+        }
+    } else if (warp == 5 && lane == 0) {
+        // ---- MMA issuer
+        constexpr uint32_t idesc = F8 ? idesc_e4m3(BM, BN) : idesc_bf16(BM, BN);
+        bool fine = mbar_wait(wfull, 0, p.err, ERR_MMA);
+        for (int r = 0; r < nrows && fine; ++r) {
+            const int b = r & 1;
+            // accumulator b was last drained for row r - 2
+            if (r >= 2 && !mbar_wait(acce0 + 8 * b, (uint32_t)((r >> 1) - 1) & 1u, p.err, ERR_MMA)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t acc = tmem + (uint32_t)b * ACC_COLS;
+            for (int ky = 0; ky < 3 && fine; ++ky) {
+                for (int ch = 0; ch < nch; ++ch) {
+                    const int u = (r + ky) * nch + ch, s = u % ru;
+                    if (!mbar_wait(full0 + 8 * s, (uint32_t)(u / ru) & 1u, p.err, ERR_MMA)) {
+                        fine = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = smem_u32(sA + s * hslot);
+                    for (int kx = 0; kx < 3; ++kx) {
+                        const uint64_t da = sw_desc(a0 + (uint32_t)p.rb * (uint32_t)kx, (uint32_t)p.rb);
+                        const uint64_t db = sw_desc(smem_u32(sW + ((ky * 3 + kx) * nch + ch) * wtile), (uint32_t)p.rb);
+                        for (int kk = 0; kk < p.rb / 32; ++kk)
+                            umma<F8>(acc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                                     (ky | ch | kx | kk) != 0 ? 1u : 0u);
+                    }
+                }
+            }
+            if (!fine) break;
+            for (int ch = 0; ch < nch; ++ch) umma_commit(empty0 + 8 * ((r * nch + ch) % ru));  // input row r is done
+            umma_commit(accf0 + 8 * b);
+        }
+    } else if (warp < 4) {
+        // ---- epilogue (thread r of warps 0-3 owns accumulator row r = pixel x0 + r)
+        for (int r = 0; r < nrows; ++r) {
+            const int b = r & 1;
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(accf0 + 8 * b, (uint32_t)(r >> 1) & 1u, p.err, ERR_EPILOGUE) &&
+                                *(volatile int *)p.err == 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            conv_epilogue<BN, HEAD, F8>(tmem + (uint32_t)b * ACC_COLS, p, warp, lane, x0, y0 + r, img);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce0 + 8 * b);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
 template <int BN, bool HEAD = false, bool F8 = false>
 cudaError_t launch_bn(const TcConvPlan &plan, const TcLaunch &lp, int n_img, cudaStream_t st) {
     dim3 grid((plan.wo + BM - 1) / BM, plan.ho, n_img);
+    if constexpr (BN <= 32 && !HEAD) {
+        // the multi-row form pays off where the grid stays large: measured on the 16- and
+        // 32-channel pyramid levels; the flow heads (two K steps, 173 KB of shared memory, one
+        // CTA per SM) and the coarse levels lose with 8x fewer CTAs
+        if (plan.stride == 1 && plan.taps == 9 && plan.nch == 1) {
+            const size_t smem = rows_smem_for(BN, plan.rb, 1);
+            static size_t attr_bytes = 0;
+            if (attr_bytes < smem) {
+                cudaError_t e = cudaFuncSetAttribute(conv_tc_rows_kernel<BN, HEAD, F8, 1>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+                attr_bytes = smem;
+            }
+            const dim3 rgrid((plan.wo + BM - 1) / BM, (plan.ho + ROWS - 1) / ROWS, n_img);
+            conv_tc_rows_kernel<BN, HEAD, F8, 1><<<rgrid, 192, smem, st>>>(plan.tmA, plan.tmB, lp);
+            return cudaGetLastError();
+        }
+    }
     if (plan.stride == 1 && plan.taps == 9) {
         static bool attr_set = false;
         const size_t smem = halo_smem_for(BN);
