@@ -8,6 +8,31 @@
 
 namespace tc {
 
+// Programmatic dependent launch: a kernel launched by launch_pdl may be scheduled as soon as
+// the previous kernel of the stream exits, without a full stream-order round trip.  It calls
+// pdl_wait() before it reads or writes any memory an earlier kernel touches (it returns once
+// the earlier grids have completed and their writes are visible; without a programmatic
+// launch it returns at once).  The kernels trigger their dependents only implicitly, at
+// exit: an explicit trigger at the start let the next kernel's CTAs compete with the last
+// wave (945 vs 954 frames/s), the implicit one measured 956 vs 954.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // Activation storage types: float (TC_FP32) and bfloat16 (TC_BF16).
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }

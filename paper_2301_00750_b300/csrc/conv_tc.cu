@@ -178,6 +178,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
+    pdl_wait();  // every global access below follows the previous kernel
 
     if (threadIdx.x == 0) {
         // ---- producer
@@ -300,6 +301,7 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
+    pdl_wait();  // every global access below follows the previous kernel
 
     if (threadIdx.x == 0) {
         // ---- producer
@@ -439,6 +441,7 @@ conv_tc_rows_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
+    pdl_wait();  // every global access below follows the previous kernel
 
     if (warp == 4 && lane == 0) {
         // ---- producer
@@ -537,8 +540,7 @@ cudaError_t launch_bn(const TcConvPlan &plan, const TcLaunch &lp, int n_img, cud
                 attr_bytes = smem;
             }
             const dim3 rgrid((plan.wo + BM - 1) / BM, (plan.ho + ROWS - 1) / ROWS, n_img);
-            conv_tc_rows_kernel<BN, HEAD, F8, 1><<<rgrid, 192, smem, st>>>(plan.tmA, plan.tmB, lp);
-            return cudaGetLastError();
+            return launch_pdl(conv_tc_rows_kernel<BN, HEAD, F8, 1>, rgrid, dim3(192), smem, st, plan.tmA, plan.tmB, lp);
         }
     }
     if (plan.stride == 1 && plan.taps == 9) {
@@ -550,7 +552,7 @@ cudaError_t launch_bn(const TcConvPlan &plan, const TcLaunch &lp, int n_img, cud
             if (e != cudaSuccess) return e;
             attr_set = true;
         }
-        conv_tc_halo_kernel<BN, HEAD, F8><<<grid, 128, smem, st>>>(plan.tmA, plan.tmB, lp);
+        return launch_pdl(conv_tc_halo_kernel<BN, HEAD, F8>, grid, dim3(128), smem, st, plan.tmA, plan.tmB, lp);
     } else {
         static bool attr_set = false;
         const size_t smem = smem_bytes_for(BN);
@@ -560,9 +562,8 @@ cudaError_t launch_bn(const TcConvPlan &plan, const TcLaunch &lp, int n_img, cud
             if (e != cudaSuccess) return e;
             attr_set = true;
         }
-        conv_tc_kernel<BN, HEAD, F8><<<grid, 128, smem, st>>>(plan.tmA, plan.tmB, lp);
+        return launch_pdl(conv_tc_kernel<BN, HEAD, F8>, grid, dim3(128), smem, st, plan.tmA, plan.tmB, lp);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace

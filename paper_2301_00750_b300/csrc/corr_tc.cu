@@ -93,6 +93,7 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
+    pdl_wait();  // every global access below follows the previous kernel
 
     if (threadIdx.x == 0) {
         // ---- producer: every channel step at once (the whole block fits in shared memory)
@@ -251,8 +252,7 @@ cudaError_t launch_r(const CorrTcPlan &plan, const CorrTcLaunch &lp, int nb, cud
         attr_set = true;
     }
     dim3 grid((plan.w + BX - 1) / BX, (plan.h + BY - 1) / BY, nb);
-    corr_tc_kernel<R, F8><<<grid, 128, G::SMEM, st>>>(plan.tmS, plan.tmO, lp);
-    return cudaGetLastError();
+    return launch_pdl(corr_tc_kernel<R, F8>, grid, dim3(128), G::SMEM, st, plan.tmS, plan.tmO, lp);
 }
 
 }  // namespace

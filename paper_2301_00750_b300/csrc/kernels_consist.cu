@@ -77,6 +77,7 @@ __device__ __forceinline__ bool warp_sample(const float *F, const float *G, cons
 // enters L_t and A^I_t with the weight w_n (Eqs. 2, 3, 6); the mask gets bit 1 for it.
 template <bool NEXT>
 __global__ void __launch_bounds__(256) consistency_kernel(ConsistArgs a) {
+    pdl_wait();
     const int x = blockIdx.x * 32 + (threadIdx.x & 31);
     const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
     if (x >= a.W || y >= a.H) return;
@@ -166,11 +167,8 @@ const void *consistency_kernel_fn(bool next) {
 
 cudaError_t launch_consistency(const ConsistArgs &a, cudaStream_t st) {
     dim3 grid((a.W + 31) / 32, (a.H + 7) / 8);
-    if (a.next)
-        consistency_kernel<true><<<grid, 256, 0, st>>>(a);
-    else
-        consistency_kernel<false><<<grid, 256, 0, st>>>(a);
-    return cudaGetLastError();
+    if (a.next) return launch_pdl(consistency_kernel<true>, grid, dim3(256), 0, st, a);
+    return launch_pdl(consistency_kernel<false>, grid, dim3(256), 0, st, a);
 }
 
 // (c, h, w) -> (c, ceil(h/2), ceil(w/2)): the mean of each 2 x 2 block, the last row and

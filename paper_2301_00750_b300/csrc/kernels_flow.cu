@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(256) conv_first_kernel(ConvFirstArgs a) {
     for (int i = threadIdx.x; i < 27 * a.cout; i += blockDim.x) ws[i] = a.wk[i];
     for (int i = threadIdx.x; i < a.cout; i += blockDim.x) bs[i] = a.bias[i];
     __syncthreads();
+    pdl_wait();  // the weights above are constant; the image and the output follow the previous kernel
     const int ho = a.Hp / 2, wo = a.Wp / 2;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= ho * wo) return;
@@ -184,8 +185,7 @@ const void *conv_first_kernel_fn() {
 template <typename T>
 cudaError_t launch_conv_first(const ConvFirstArgs &a, cudaStream_t st) {
     const int n = (a.Hp / 2) * (a.Wp / 2);
-    conv_first_kernel<T><<<(n + 255) / 256, 256, 0, st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(conv_first_kernel<T>, dim3((n + 255) / 256), dim3(256), 0, st, a);
 }
 
 // =====================================================================================
@@ -333,6 +333,7 @@ cudaError_t launch_corr(const CorrArgs &a, cudaStream_t st) {
 // =====================================================================================
 template <typename T>
 __global__ void __launch_bounds__(256) warp_kernel(WarpArgs a) {
+    pdl_wait();
     const int nq = a.c / 4;
     const size_t total = (size_t)a.n * a.h * a.w * nq;
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -383,8 +384,7 @@ __global__ void __launch_bounds__(256) warp_kernel(WarpArgs a) {
 template <typename T>
 cudaError_t launch_warp(const WarpArgs &a, cudaStream_t st) {
     const size_t total = (size_t)a.n * a.h * a.w * (a.c / 4);
-    warp_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(warp_kernel<T>, dim3((unsigned)((total + 255) / 256)), dim3(256), 0, st, a);
 }
 
 // =====================================================================================
