@@ -38,6 +38,9 @@ METRIC = "1080p frames/s (flow+consistency) vs FP32 plain at fixed EPE; p99 fram
 UNIT = "frames/s"
 K1_SWEEP = (0.0, 0.25, 0.5, 0.75, 1.0)
 SOLVER_ITERS = 150  # Eq. 8 iterations per frame in the paper's full method
+# DRAM bytes (read + write) of one frame's estimator convs at 1080p BF16, one ncu capture
+# (profiles/estimator_traffic_1080p_bf16.md); valid for the kernels as of that capture
+ESTIMATOR_TRAFFIC_BYTES_BF16 = 678.4e6
 SOLVER_FLOPS_PER_PX_ITER = 9  # per channel: neighbour sum (3 adds) and 3 FMAs
 WIDTH, HEIGHT = 1920, 1080
 SPEC = dict(chans=(16, 32, 64, 96, 128), radius=4)
@@ -447,7 +450,10 @@ def run_ours(args):
         "latency_ms": {"p50": round(per[len(per) // 2], 4), "p99": round(per[min(len(per) - 1, int(0.99 * len(per)))], 4)},
         "stage_ms_per_frame": {k: round(v[0] / steps, 4) for k, v in p.items() if v[1]},
         "roofline": {"kernel": dom, "bound": bound, "achieved": round(achieved, 2), "peak": peak, "unit": unit,
-                     "frac": round(achieved / peak, 4) if peak else None, "traffic": None,
+                     "frac": round(achieved / peak, 4) if peak else None,
+                     "traffic": (ESTIMATOR_TRAFFIC_BYTES_BF16 if dom == "estimator_conv" and args.precision == "bf16"
+                                 and args.flow_downscale == 1 else None),
+                     "traffic_note": "DRAM bytes per frame of the class (16 launches), ncu capture, cold caches",
                      "peak_source": peak_source},
         "gpu_launches": main["launches"],
         "clocks": clk,
