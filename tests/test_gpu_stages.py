@@ -85,9 +85,11 @@ CONV_CASES = [
     (2, 20, 36, 160, 32, 1), (1, 68, 120, 96, 64, 1), (1, 11, 7, 8, 2, 1), (2, 64, 72, 64, 96, 2),
     (1, 5, 6, 6, 10, 1), (1, 136, 240, 64, 64, 1), (2, 272, 480, 32, 32, 1), (1, 7, 300, 16, 16, 2),
     (2, 3, 130, 216, 128, 1), (1, 8, 8, 48, 48, 1),
-    # 96 / 128 outputs on rows of >= 192 pixels run the 256-pixel transposed kernel: two
-    # tiles with a ragged second one, a one-pixel last tile, three K steps
+    # wide rows: two tiles with a ragged second one, a one-pixel last tile, three K steps
     (1, 20, 300, 128, 128, 1), (2, 9, 480, 120, 96, 1), (1, 6, 257, 64, 128, 1), (1, 3, 192, 192, 128, 1),
+    # one K step and <= 32 outputs at stride 1 run the multi-row kernel (8 rows per CTA):
+    # row tails of 7 and 1, a one-pixel last tile, a 24-channel input, three images
+    (2, 23, 200, 64, 32, 1), (1, 1, 129, 16, 16, 1), (3, 17, 128, 24, 16, 1),
 ]
 
 
