@@ -304,7 +304,8 @@ struct tc_stream {
     } fg[2];
     // screened-Poisson solver (allocated when first enabled): A_t, w_c, right-hand side and
     // four iterate planes, each (3, H, W) float (w_c (H, W))
-    float *sv_A = nullptr, *sv_wc = nullptr, *sv_b = nullptr, *sv_s[4] = {nullptr, nullptr, nullptr, nullptr};
+    float *sv_A = nullptr, *sv_wc = nullptr, *sv_b = nullptr, *sv_c0 = nullptr,
+          *sv_s[4] = {nullptr, nullptr, nullptr, nullptr};
     // one frame of latency (tc_set_latency): frame t is blended when frame t+1 arrives, with
     // the final flows of the pair (t, t-1) kept from the previous call ((2, h_2, w_2, 2) float)
     int latency = 0;
@@ -436,7 +437,7 @@ extern "C" tc_status tc_set_consistency(tc_stream *s, const tc_consistency *p) {
         const size_t img = (size_t)3 * s->H * s->W * sizeof(float), plane = (size_t)s->H * s->W * sizeof(float);
         tc_status r;
         if ((r = dalloc_t(s, &s->sv_A, img)) != TC_OK || (r = dalloc_t(s, &s->sv_wc, plane)) != TC_OK ||
-            (r = dalloc_t(s, &s->sv_b, img)) != TC_OK)
+            (r = dalloc_t(s, &s->sv_b, img)) != TC_OK || (r = dalloc_t(s, &s->sv_c0, plane)) != TC_OK)
             return r;
         for (int k = 0; k < 4; ++k)
             if ((r = dalloc_t(s, &s->sv_s[k], img)) != TC_OK) return r;
@@ -994,7 +995,7 @@ static ConsistArgs consist_args(tc_stream *s, const float *I, const float *P, fl
 // w_c to the caller.  P is P_t.
 static tc_status solver_launches(tc_stream *s, const float *P, float *O, float *wc, int cur) {
     PoissonArgs pa{P, s->sv_A, s->sv_wc, 3, s->H, s->W, s->params.solver_iters, s->params.eta, s->params.kappa,
-                   s->sv_b, s->sv_s[0], s->sv_s[1], s->sv_s[2], s->sv_s[3], s->sO[cur], nullptr};
+                   s->sv_b, s->sv_s[0], s->sv_s[1], s->sv_s[2], s->sv_s[3], s->sO[cur], nullptr, s->sv_c0};
     TC_LAUNCH_CAT(s, TC_PROF_SOLVER, launch_poisson(pa, s->st));
     const size_t hw = (size_t)s->H * s->W;
     TC_LAUNCH_CAT(s, TC_PROF_SOLVER, launch_copy_out(s->sO[cur], O, 3 * hw, s->sv_wc, wc, hw, s->st, 0));
@@ -1764,8 +1765,9 @@ extern "C" tc_status tc_op_poisson_solve(const float *P, const float *A, const f
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const size_t n = (size_t)c * h * w;
     TmpAlloc tmp;
-    float *b, *s0, *s1, *s2, *s3;
+    float *b, *s0, *s1, *s2, *s3, *c0;
     OP_TRY(tmp.get((void **)&b, n * 4), "tc_op_poisson_solve alloc");
+    OP_TRY(tmp.get((void **)&c0, (size_t)h * w * 4), "tc_op_poisson_solve alloc");
     OP_TRY(tmp.get((void **)&s0, n * 4), "tc_op_poisson_solve alloc");
     OP_TRY(tmp.get((void **)&s1, n * 4), "tc_op_poisson_solve alloc");
     OP_TRY(tmp.get((void **)&s2, n * 4), "tc_op_poisson_solve alloc");
@@ -1773,7 +1775,7 @@ extern "C" tc_status tc_op_poisson_solve(const float *P, const float *A, const f
     if (iters == 0) {
         OP_TRY(cudaMemcpyAsync(O, A, n * 4, cudaMemcpyDeviceToDevice, st), "tc_op_poisson_solve copy");
     } else {
-        PoissonArgs pa{P, A, wc, c, h, w, iters, eta, kappa, b, s0, s1, s2, s3, O, nullptr};
+        PoissonArgs pa{P, A, wc, c, h, w, iters, eta, kappa, b, s0, s1, s2, s3, O, nullptr, c0};
         OP_TRY(launch_poisson(pa, st), "tc_op_poisson_solve launch");
     }
     OP_TRY(cudaStreamSynchronize(st), "tc_op_poisson_solve sync");

@@ -28,8 +28,10 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-// b = Lg P + wc A per channel (planar (c, h, w)).
-__global__ void poisson_rhs_kernel(const float *P, const float *A, const float *wc, int c, int h, int w, float *b) {
+// The pass-invariant coefficients, once per solve: eb = eta b, b = Lg P + wc A, per channel
+// (planar (c, h, w)), and c0 = 1 + kappa - eta (deg + wc) per pixel ((h, w)).
+__global__ void poisson_rhs_kernel(const float *P, const float *A, const float *wc, int c, int h, int w, float eta,
+                                   float kappa, float *eb, float *c0) {
     const size_t hw = (size_t)h * w;
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (size_t)c * hw) return;
@@ -42,7 +44,12 @@ __global__ void poisson_rhs_kernel(const float *P, const float *A, const float *
     if (y < h - 1) lap += v - Pc[p + w];
     if (x > 0) lap += v - Pc[p - 1];
     if (x < w - 1) lap += v - Pc[p + 1];
-    b[i] = lap + wc[p] * A[i];
+    const float b = lap + wc[p] * A[i];
+    eb[i] = eta * b;
+    if (ch == 0) {
+        const int deg = (y > 0) + (y < h - 1) + (x > 0) + (x < w - 1);
+        c0[p] = 1.f + kappa - eta * ((float)deg + wc[p]);
+    }
 }
 
 // Region of a CTA: RW x RH pixels; HALO = iterations per pass = the margin around the output
@@ -114,7 +121,7 @@ __device__ __forceinline__ void step(const float (&cu)[R][CW], float (&pv)[R][CW
 }
 
 struct SolveArgs {
-    const float *cur, *prev, *b, *wc;
+    const float *cur, *prev, *eb, *c0;  // eb = eta b per channel, c0 per pixel
     int h, w, T, tiles_x;
     float eta, kappa;
     float *cur_out, *prev_out, *cur_out2;
@@ -126,7 +133,7 @@ __device__ __forceinline__ void region(const SolveArgs &s, size_t off, int oy, i
     using G = Geo<CW, R, NW, HALO>;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int cx = ox + lane * CW, ry = oy + wp * R;
-    const float *cur = s.cur + off, *prev = s.prev + off, *b = s.b + off;
+    const float *cur = s.cur + off, *prev = s.prev + off, *ebp = s.eb + off;
     float x[R][CW], p[R][CW], c0[R][CW], eb[R][CW];
     unsigned mask = 0;
     // Interior regions load and store rows of CW floats when the host found the frame width
@@ -136,20 +143,11 @@ __device__ __forceinline__ void region(const SolveArgs &s, size_t off, int oy, i
     if (vec) {
 #pragma unroll
         for (int i = 0; i < R; ++i) {
-            const int gy = ry + i;
-            const size_t g = (size_t)gy * s.w + cx;
-            float wr[CW];
+            const size_t g = (size_t)(ry + i) * s.w + cx;
             ld_row<CW>(cur + g, x[i]);
             ld_row<CW>(prev + g, p[i]);
-            ld_row<CW>(b + g, eb[i]);
-            ld_row<CW>(s.wc + g, wr);
-#pragma unroll
-            for (int j = 0; j < CW; ++j) {
-                const int gx = cx + j;
-                const int deg = (gy > 0) + (gy < s.h - 1) + (gx > 0) + (gx < s.w - 1);
-                eb[i][j] *= s.eta;
-                c0[i][j] = 1.f + s.kappa - s.eta * ((float)deg + wr[j]);
-            }
+            ld_row<CW>(ebp + g, eb[i]);
+            ld_row<CW>(s.c0 + g, c0[i]);
         }
     } else {
 #pragma unroll
@@ -161,11 +159,10 @@ __device__ __forceinline__ void region(const SolveArgs &s, size_t off, int oy, i
                 x[i][j] = p[i][j] = c0[i][j] = eb[i][j] = 0.f;
                 if (in) {
                     const size_t g = (size_t)gy * s.w + gx;
-                    const int deg = (gy > 0) + (gy < s.h - 1) + (gx > 0) + (gx < s.w - 1);
                     x[i][j] = __ldg(cur + g);
                     p[i][j] = __ldg(prev + g);
-                    eb[i][j] = s.eta * __ldg(b + g);
-                    c0[i][j] = 1.f + s.kappa - s.eta * ((float)deg + __ldg(s.wc + g));
+                    eb[i][j] = __ldg(ebp + g);
+                    c0[i][j] = __ldg(s.c0 + g);
                     mask |= 1u << (i * CW + j);
                 }
             }
@@ -258,20 +255,21 @@ const void *copy_out_kernel_fn(int tag) {
 cudaError_t launch_poisson(const PoissonArgs &a, cudaStream_t st) {
     if (a.c < 1 || a.c > 3) return cudaErrorInvalidValue;
     const size_t n = (size_t)a.c * a.h * a.w;
-    poisson_rhs_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a.P, a.A, a.wc, a.c, a.h, a.w, a.b);
+    poisson_rhs_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a.P, a.A, a.wc, a.c, a.h, a.w, a.eta, a.kappa,
+                                                                   a.b, a.c0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || a.iters <= 0) return e;
     using G = Geo<CW, RR, NWARP, TPASS>;
     SolveArgs s{};
-    s.b = a.b;
-    s.wc = a.wc;
+    s.eb = a.b;
+    s.c0 = a.c0;
     s.h = a.h;
     s.w = a.w;
     s.tiles_x = (a.w + G::OW - 1) / G::OW;
     s.eta = a.eta;
     s.kappa = a.kappa;
     auto al = [](const void *q) { return reinterpret_cast<uintptr_t>(q) % (CW * sizeof(float)) == 0; };
-    s.vec_ok = a.w % CW == 0 && al(a.A) && al(a.wc) && al(a.b) && al(a.s0) && al(a.s1) && al(a.s2) && al(a.s3) &&
+    s.vec_ok = a.w % CW == 0 && al(a.A) && al(a.c0) && al(a.b) && al(a.s0) && al(a.s1) && al(a.s2) && al(a.s3) &&
                al(a.O) && (a.O2 == nullptr || al(a.O2));
     const dim3 grid(s.tiles_x * ((a.h + G::OH - 1) / G::OH), a.c);
     // ping-pong through (s0, s1), (s2, s3): pass k reads (cur, prev) and writes the other pair
