@@ -315,7 +315,7 @@ TC_API tc_status tc_op_warp_features(tc_precision precision, const float *f, con
 
 /* Flow upsampling by s in {2, 4}: bilinear, half-pixel centres (sample positions clamped
  * at 0 and at the last row/column), values multiplied by s.  flow (n, h, w, 2) ->
- * out (n, s h, s w, 2). */
+ * out (n, s h, s w, 2).  h * w at most INT_MAX. */
 TC_API tc_status tc_op_upsample_flow(const float *flow, int n, int h, int w, int s, float *out,
                               void *cuda_stream);
 
@@ -340,9 +340,9 @@ TC_API tc_status tc_op_downscale2(const float *src, int c, int h, int w, float *
  * h x w pixels.  It, Pt, Ip, Pp, Op: device (3, h, w) float32 (I_t, P_t, I_{t-1},
  * P_{t-1}, O_{t-1}).  Fb, Ff: device (fh, fw, 2) float32 flows at 1/scale resolution,
  * scale in {1, 2, 4, ...} (1 = full resolution, fh = h, fw = w); they are upsampled on
- * the fly as by tc_op_upsample_flow and read on the h x w crop.  Requires fh * scale >= h
- * and fw * scale >= w.  O: device (3, h, w); wc_opt (h, w) float32 or NULL; mask_opt
- * (h, w) uint8 or NULL. */
+ * the fly as by tc_op_upsample_flow and read on the h x w crop.  Requires fh * scale >= h,
+ * fw * scale >= w, and h * w and fh * fw at most INT_MAX.  O: device (3, h, w); wc_opt
+ * (h, w) float32 or NULL; mask_opt (h, w) uint8 or NULL. */
 TC_API tc_status tc_op_consistency(const float *It, const float *Pt, const float *Ip, const float *Pp,
                             const float *Op, const float *Fb, const float *Ff, int h, int w,
                             int fh, int fw, int scale, const tc_consistency *p, float *O,

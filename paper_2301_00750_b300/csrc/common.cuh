@@ -203,20 +203,22 @@ namespace tc {
 // Value at integer position (X, Y) of the s-times bilinear upsampling (half-pixel centres,
 // sample position clamped at 0 and at the last row/column) of a (fh, fw, 2) flow field,
 // multiplied by s.  s = 1 reads the field directly.  s must be a power of two, so every
-// coordinate and interpolation weight below is exact in float32.
+// coordinate and interpolation weight below is exact in float32 (the products by 1/s are
+// the quotients by s), and fh * fw must fit an int.
 __device__ __forceinline__ float2 upsampled_flow_at(const float *F, int fh, int fw, int s,
                                                     int X, int Y) {
     const float2 *f = reinterpret_cast<const float2 *>(F);
-    if (s == 1) return f[(size_t)Y * fw + X];
+    if (s == 1) return f[Y * fw + X];
     const float fs = (float)s;
-    float sy = (Y + 0.5f) / fs - 0.5f, sx = (X + 0.5f) / fs - 0.5f;
+    const float rs = __int_as_float((127 - (__ffs(s) - 1)) << 23);  // 2^-k for s = 2^k
+    float sy = (Y + 0.5f) * rs - 0.5f, sx = (X + 0.5f) * rs - 0.5f;
     sy = fmaxf(sy, 0.f);
     sx = fmaxf(sx, 0.f);
     int y0 = min((int)sy, fh - 1), x0 = min((int)sx, fw - 1);
     const int y1 = y0 < fh - 1 ? y0 + 1 : y0, x1 = x0 < fw - 1 ? x0 + 1 : x0;
     const float ly = sy - y0, lx = sx - x0;
-    const float2 a = f[(size_t)y0 * fw + x0], b = f[(size_t)y0 * fw + x1];
-    const float2 c = f[(size_t)y1 * fw + x0], d = f[(size_t)y1 * fw + x1];
+    const float2 a = f[y0 * fw + x0], b = f[y0 * fw + x1];
+    const float2 c = f[y1 * fw + x0], d = f[y1 * fw + x1];
     float u = (1.f - ly) * ((1.f - lx) * a.x + lx * b.x) + ly * ((1.f - lx) * c.x + lx * d.x);
     float v = (1.f - ly) * ((1.f - lx) * a.y + lx * b.y) + ly * ((1.f - lx) * c.y + lx * d.y);
     return make_float2(fs * u, fs * v);

@@ -1,6 +1,7 @@
 // Stream engine and C ABI (see include/tc_stream.h): per-stream device state, weight
 // loading, the per-frame launch sequence of the flow network and the consistency step,
 // and the single-stage entry points.
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -1749,7 +1750,7 @@ extern "C" tc_status tc_op_warp_features(tc_precision precision, const float *f,
 }
 
 extern "C" tc_status tc_op_upsample_flow(const float *flow, int n, int h, int w, int s, float *out, void *cuda_stream) {
-    if (!flow || !out || n < 1 || h < 1 || w < 1 || (s != 2 && s != 4))
+    if (!flow || !out || n < 1 || h < 1 || w < 1 || (s != 2 && s != 4) || (size_t)h * w > (size_t)INT_MAX)
         return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_upsample_flow: bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     UpArgs u{flow, n, h, w, s, out, nullptr, 0};
@@ -1787,7 +1788,8 @@ extern "C" tc_status tc_op_consistency(const float *It, const float *Pt, const f
                                        int fw, int scale, const tc_consistency *p, float *O, float *wc_opt,
                                        uint8_t *mask_opt, void *cuda_stream) {
     if (!It || !Pt || !Ip || !Pp || !Op || !Fb || !Ff || !p || !O || h < 1 || w < 1 || fh < 1 || fw < 1 ||
-        scale < 1 || (scale & (scale - 1)) != 0 || (size_t)fh * scale < (size_t)h || (size_t)fw * scale < (size_t)w)
+        scale < 1 || (scale & (scale - 1)) != 0 || (size_t)fh * scale < (size_t)h || (size_t)fw * scale < (size_t)w ||
+        (size_t)h * w > (size_t)INT_MAX || (size_t)fh * fw > (size_t)INT_MAX)
         return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_consistency: bad argument");
     std::string why;
     if (!valid_params(p, why)) return fail(nullptr, TC_ERR_INVALID_ARG, why);
@@ -1814,7 +1816,7 @@ extern "C" tc_status tc_op_consistency_next(const float *It, const float *Pt, co
                                             float *wc_opt, uint8_t *mask_opt, void *cuda_stream) {
     if (!It || !Pt || !Ip || !Pp || !Op || !Fb || !Ff || !In || !Pn || !Fn || !Fnb || !p || !O || h < 1 || w < 1 ||
         fh < 1 || fw < 1 || scale < 1 || (scale & (scale - 1)) != 0 || (size_t)fh * scale < (size_t)h ||
-        (size_t)fw * scale < (size_t)w)
+        (size_t)fw * scale < (size_t)w || (size_t)h * w > (size_t)INT_MAX || (size_t)fh * fw > (size_t)INT_MAX)
         return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_consistency_next: bad argument");
     std::string why;
     if (!valid_params(p, why)) return fail(nullptr, TC_ERR_INVALID_ARG, why);

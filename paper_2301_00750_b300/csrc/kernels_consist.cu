@@ -31,11 +31,12 @@ __device__ __forceinline__ Taps clamp_taps(int x, int y, float u, float v, int W
     return t;
 }
 
+// (H * W fits an int: the offsets of the taps are 32-bit.)
 __device__ __forceinline__ float gather(const float *p, int W, const Taps &t) {
-    float acc = t.w00 * __ldg(p + (size_t)t.ya * W + t.xa);
-    acc += t.w01 * __ldg(p + (size_t)t.ya * W + t.xb);
-    acc += t.w10 * __ldg(p + (size_t)t.yb * W + t.xa);
-    acc += t.w11 * __ldg(p + (size_t)t.yb * W + t.xb);
+    float acc = t.w00 * __ldg(p + (t.ya * W + t.xa));
+    acc += t.w01 * __ldg(p + (t.ya * W + t.xb));
+    acc += t.w10 * __ldg(p + (t.yb * W + t.xa));
+    acc += t.w11 * __ldg(p + (t.yb * W + t.xb));
     return acc;
 }
 
