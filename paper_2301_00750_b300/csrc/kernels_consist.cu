@@ -13,6 +13,7 @@ namespace tc {
 struct Taps {
     int xa, xb, ya, yb;
     float w00, w01, w10, w11;
+    float ax, ay;  // the fractions along x and y
 };
 
 __device__ __forceinline__ Taps clamp_taps(int x, int y, float u, float v, int W, int H) {
@@ -28,6 +29,8 @@ __device__ __forceinline__ Taps clamp_taps(int x, int y, float u, float v, int W
     t.w01 = ax * (1.f - ay);
     t.w10 = (1.f - ax) * ay;
     t.w11 = ax * ay;
+    t.ax = ax;
+    t.ay = ay;
     return t;
 }
 
@@ -38,6 +41,62 @@ __device__ __forceinline__ float gather(const float *p, int W, const Taps &t) {
     acc += t.w10 * __ldg(p + (t.yb * W + t.xa));
     acc += t.w11 * __ldg(p + (t.yb * W + t.xb));
     return acc;
+}
+
+// Weights on the low-resolution cells base, base + 1, base + 2 of one axis (base = the
+// first cell of tap a) of the bilinear combination (1 - f) up(Xa) + f up(Xb) of the
+// s-times upsampled field along that axis, s = 2^k >= 2 (1/s = rs).  Xb is Xa or Xa + 1, so
+// the first cell of Xb is base or base + 1.  Returns base; `third` says whether cell
+// base + 2 carries weight.
+__device__ __forceinline__ int axis_weights(int Xa, int Xb, float f, float rs, int n, float &c0, float &c1,
+                                            float &c2, bool &third) {
+    const float sa = fmaxf((Xa + 0.5f) * rs - 0.5f, 0.f), sb = fmaxf((Xb + 0.5f) * rs - 0.5f, 0.f);
+    const int a0 = min((int)sa, n - 1), b0 = min((int)sb, n - 1);
+    const float la = sa - a0, lb = sb - b0;
+    const float wa = 1.f - f;
+    third = b0 != a0;
+    c0 = wa * (1.f - la);
+    c1 = wa * la;
+    c2 = 0.f;
+    if (third) {
+        c1 += f * (1.f - lb);
+        c2 = f * lb;
+    } else {
+        c0 += f * (1.f - lb);
+        c1 += f * lb;
+    }
+    return a0;
+}
+
+// The opposite flow G (fh, fw, 2 at 1/s resolution, s = 2^k >= 2), upsampled and sampled
+// bilinearly at the taps t: the four upsampled values lie on one 3 x 3 block of G's cells
+// (cells past the last row/column clamp to it, as the upsampling does), so the tap weights
+// and the upsampling weights fold into one weight per cell of that block.
+__device__ __forceinline__ float2 fb_flow_at_taps(const float *G, const ConsistArgs &a, const Taps &t) {
+    const float2 *g = reinterpret_cast<const float2 *>(G);
+    const float rs = __int_as_float((127 - (__ffs(a.scale) - 1)) << 23);  // 2^-k
+    float cx[3], cy[3];
+    bool tx, ty;
+    const int x0 = axis_weights(t.xa, t.xb, t.ax, rs, a.fw, cx[0], cx[1], cx[2], tx);
+    const int y0 = axis_weights(t.ya, t.yb, t.ay, rs, a.fh, cy[0], cy[1], cy[2], ty);
+    const int xc1 = min(x0 + 1, a.fw - 1), xc2 = min(x0 + 2, a.fw - 1);
+    float su = 0.f, sv = 0.f;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        if (r == 2 && !ty) break;
+        const int row = min(y0 + r, a.fh - 1) * a.fw;
+        const float2 p0 = g[row + x0], p1 = g[row + xc1];
+        float ru = cx[0] * p0.x + cx[1] * p1.x, rv = cx[0] * p0.y + cx[1] * p1.y;
+        if (tx) {
+            const float2 p2 = g[row + xc2];
+            ru += cx[2] * p2.x;
+            rv += cx[2] * p2.y;
+        }
+        su += cy[r] * ru;
+        sv += cy[r] * rv;
+    }
+    const float fs = (float)a.scale;
+    return make_float2(fs * su, fs * sv);
 }
 
 // The warp of a neighbouring frame along F at (x, y): taps, and whether it is valid (in
@@ -54,18 +113,24 @@ __device__ __forceinline__ bool warp_sample(const float *F, const float *G, cons
     t = clamp_taps(x, y, u, v, a.W, a.H);
     bool occ = false;
     if (a.fb_check) {
-        const float2 f00 = upsampled_flow_at(G, a.fh, a.fw, a.scale, t.xa, t.ya);
-        const float2 f01 = upsampled_flow_at(G, a.fh, a.fw, a.scale, t.xb, t.ya);
-        const float2 f10 = upsampled_flow_at(G, a.fh, a.fw, a.scale, t.xa, t.yb);
-        const float2 f11 = upsampled_flow_at(G, a.fh, a.fw, a.scale, t.xb, t.yb);
-        float fu = t.w00 * f00.x;
-        fu += t.w01 * f01.x;
-        fu += t.w10 * f10.x;
-        fu += t.w11 * f11.x;
-        float fv = t.w00 * f00.y;
-        fv += t.w01 * f01.y;
-        fv += t.w10 * f10.y;
-        fv += t.w11 * f11.y;
+        float fu, fv;
+        if (a.scale > 1) {
+            const float2 f = fb_flow_at_taps(G, a, t);
+            fu = f.x;
+            fv = f.y;
+        } else {
+            const float2 *g = reinterpret_cast<const float2 *>(G);
+            const float2 f00 = g[t.ya * a.fw + t.xa], f01 = g[t.ya * a.fw + t.xb];
+            const float2 f10 = g[t.yb * a.fw + t.xa], f11 = g[t.yb * a.fw + t.xb];
+            fu = t.w00 * f00.x;
+            fu += t.w01 * f01.x;
+            fu += t.w10 * f10.x;
+            fu += t.w11 * f11.x;
+            fv = t.w00 * f00.y;
+            fv += t.w01 * f01.y;
+            fv += t.w10 * f10.y;
+            fv += t.w11 * f11.y;
+        }
         const float su = u + fu, sv = v + fv;
         const float lhs = su * su + sv * sv;
         const float rhs = a.c1 * ((u * u + v * v) + (fu * fu + fv * fv)) + a.c2;
@@ -76,8 +141,11 @@ __device__ __forceinline__ bool warp_sample(const float *F, const float *G, cons
 
 // NEXT = false: causal form (w_n = 0).  NEXT = true: frame t+1 warped along F_{t->t+1}
 // enters L_t and A^I_t with the weight w_n (Eqs. 2, 3, 6); the mask gets bit 1 for it.
+// Both forms are bound by the latency of their dependent loads (flow, then taps), so
+// occupancy comes first: the causal form runs at 40 registers (six blocks, 48 warps per
+// SM), the one with the next frame at 48 (five blocks).
 template <bool NEXT>
-__global__ void __launch_bounds__(256) consistency_kernel(ConsistArgs a) {
+__global__ void __launch_bounds__(256, NEXT ? 5 : 6) consistency_kernel(ConsistArgs a) {
     pdl_wait();
     const int x = blockIdx.x * 32 + (threadIdx.x & 31);
     const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
