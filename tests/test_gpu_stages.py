@@ -90,6 +90,8 @@ CONV_CASES = [
     # one K step and <= 32 outputs at stride 1 run the multi-row kernel (8 rows per CTA):
     # row tails of 7 and 1, a one-pixel last tile, a 24-channel input, three images
     (2, 23, 200, 64, 32, 1), (1, 1, 129, 16, 16, 1), (3, 17, 128, 24, 16, 1),
+    # a single 120-pixel tile per row over 50 rows and two images, two K steps, 96 outputs
+    (2, 50, 120, 128, 96, 1),
 ]
 
 
