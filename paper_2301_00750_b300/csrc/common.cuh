@@ -107,6 +107,10 @@ struct ConvFirstArgs {
     int cout;
     void *out;  // [Hp/2][Wp/2][cout]
     float q_out;  // outputs are multiplied by q_out before storing (1 / scale for e4m3, else 1)
+    // cout == 16: the weights [27][16] and bias by value (the kernel reads them from the
+    // parameter bank as FMA operands); set by set_first16
+    float w16[27 * 16];
+    float b16[16];
 };
 
 // Flow head: conv5 (cin -> 2, no activation) plus the residual up-flow.

@@ -38,14 +38,17 @@ using namespace ptx;
 
 constexpr int BM = 128;                    // output pixels per CTA (MMA M)
 constexpr int BK = 64;                     // bf16 channels of the widest K step (128 B); e4m3 steps hold 128
-constexpr uint32_t A_BYTES = BM * BK * 2;  // 16 KB
 
 enum : int { ERR_PRODUCER = 1, ERR_MMA = 2, ERR_EPILOGUE = 3, ERR_DRAIN = 4 };
 
 __host__ __device__ constexpr int stages_for(int bn) { return bn >= 96 ? 3 : 4; }
 __host__ __device__ constexpr int tmem_cols_for(int bn) { return bn <= 32 ? 32 : (bn <= 64 ? 64 : 128); }
-__host__ __device__ constexpr size_t smem_bytes_for(int bn) {
-    return (size_t)stages_for(bn) * (A_BYTES + (size_t)bn * BK * 2) + 1024 + 256;
+// Ring slots of the per-tap kernel hold one K step of rb bytes per row (A: BM rows, B: bn
+// rows), each rounded up to the 1024-byte swizzle atom.
+__host__ __device__ constexpr uint32_t a_slot_for(int rb) { return (uint32_t)((BM * rb + 1023) / 1024 * 1024); }
+__host__ __device__ constexpr uint32_t b_slot_for(int bn, int rb) { return (uint32_t)((bn * rb + 1023) / 1024 * 1024); }
+__host__ __device__ constexpr size_t smem_bytes_for(int bn, int rb) {
+    return (size_t)stages_for(bn) * (a_slot_for(rb) + b_slot_for(bn, rb)) + 1024 + 256;
 }
 
 struct TcLaunch {
@@ -145,8 +148,8 @@ template <int BN, bool HEAD, bool F8>
 __global__ void __launch_bounds__(128, 1)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcLaunch p) {
     constexpr int STAGES = stages_for(BN);
-    constexpr uint32_t B_BYTES = BN * BK * 2;  // slot size (128-byte rows); a step may fill less
     constexpr uint32_t TMEM_COLS = tmem_cols_for(BN);
+    const uint32_t A_BYTES = a_slot_for(p.rb), B_BYTES = b_slot_for(BN, p.rb);
     const uint32_t stage_tx = (uint32_t)(BM + BN) * (uint32_t)p.rb;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -554,13 +557,13 @@ cudaError_t launch_bn(const TcConvPlan &plan, const TcLaunch &lp, int n_img, cud
         }
         return launch_pdl(conv_tc_halo_kernel<BN, HEAD, F8>, grid, dim3(128), smem, st, plan.tmA, plan.tmB, lp);
     } else {
-        static bool attr_set = false;
-        const size_t smem = smem_bytes_for(BN);
-        if (!attr_set) {
+        static size_t attr_bytes = 0;
+        const size_t smem = smem_bytes_for(BN, plan.rb);
+        if (attr_bytes < smem) {
             cudaError_t e =
                 cudaFuncSetAttribute(conv_tc_kernel<BN, HEAD, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            attr_set = true;
+            attr_bytes = smem;
         }
         return launch_pdl(conv_tc_kernel<BN, HEAD, F8>, grid, dim3(128), smem, st, plan.tmA, plan.tmB, lp);
     }

@@ -255,6 +255,7 @@ struct tc_stream {
     std::vector<LevelBufs> lv;  // index l-1
     // pyramid weights per level (3 convs)
     std::vector<float *> pyr_w, pyr_b;
+    std::vector<float> first_w, first_b;  // host copy of the first conv ([27][cout], cout)
     TcConvPlan pyr_plan[8][3];
     // state ring: [2 slots] planar (3, H, W)
     float *sI[2] = {nullptr, nullptr}, *sP[2] = {nullptr, nullptr}, *sO[2] = {nullptr, nullptr};
@@ -582,7 +583,11 @@ static tc_status build_stream(tc_stream *s) {
             }
             if ((r = upload(s, &s->pyr_w[3 * (l - 1) + j], wk)) != TC_OK) return r;
             if ((r = upload(s, &s->pyr_b[3 * (l - 1) + j], HL.b)) != TC_OK) return r;
-            if (l == 1 && j == 0) continue;
+            if (l == 1 && j == 0) {
+                s->first_w = wk;
+                s->first_b = HL.b;
+                continue;
+            }
             // Same arguments as run_pyramid builds; the first conv of a level reads both
             // slots of the previous level's pyramid buffer.
             if (j == 0) {
@@ -787,6 +792,17 @@ static tc_status conv_layer(tc_stream *s, const ConvArgs &a, const TcConvPlan *p
     return TC_OK;
 }
 
+// The first conv's arguments for input image img (the 16-output form carries its weights).
+static ConvFirstArgs first_args(const tc_stream *s, const float *img) {
+    const LevelBufs &B = s->lv[0];
+    ConvFirstArgs f{img, s->Hn, s->Wn, s->Hp, s->Wp, s->pyr_w[0], s->pyr_b[0], B.c, B.tmpA, B.q_pyr[0], {}, {}};
+    if (B.c == 16 && s->first_w.size() == 27 * 16 && s->first_b.size() == 16) {
+        memcpy(f.w16, s->first_w.data(), sizeof f.w16);
+        memcpy(f.b16, s->first_b.data(), sizeof f.b16);
+    }
+    return f;
+}
+
 template <typename T>
 static tc_status run_pyramid(tc_stream *s, const float *img, int slot) {
     tc_status r;
@@ -799,7 +815,7 @@ static tc_status run_pyramid(tc_stream *s, const float *img, int slot) {
                 TC_LAUNCH_CAT(s, TC_PROF_PYRAMID_CONV, launch_downscale2(img, 3, s->H, s->W, s->xs, s->st));
                 img = s->xs;
             }
-            ConvFirstArgs f{img, s->Hn, s->Wn, s->Hp, s->Wp, s->pyr_w[0], s->pyr_b[0], B.c, B.tmpA, B.q_pyr[0]};
+            const ConvFirstArgs f = first_args(s, img);
             TC_LAUNCH_CAT(s, TC_PROF_PYRAMID_CONV, launch_conv_first<T>(f, s->st));
         } else {
             LevelBufs &P = s->lv[l - 2];
@@ -1139,8 +1155,7 @@ static tc_status process(tc_stream *s, const float *I, const float *P, float *O,
     if (!G.exec) {
         if ((r = capture_frame<T>(s, I, P, O, wc, mask, cur)) != TC_OK) return r;
     } else {
-        ConvFirstArgs f{I, s->Hn, s->Wn, s->Hp, s->Wp, s->pyr_w[0], s->pyr_b[0], s->lv[0].c, s->lv[0].tmpA,
-                        s->lv[0].q_pyr[0]};
+        ConvFirstArgs f = first_args(s, I);
         ConsistArgs ca = consist_args(s, I, P, O, wc, mask, cur);
         // the node that reads the caller's I_t: the first pyramid conv, or the 2x2 downscale
         int c3 = 3, hh = s->H, ww = s->W;

@@ -133,15 +133,18 @@ cudaError_t launch_conv_simt(const ConvArgs &a, cudaStream_t st) {
 // =====================================================================================
 // First pyramid conv: 3 -> cout channels, stride 2, reading the planar float image with
 // edge replication up to (Hp, Wp) (the padding to a multiple of 2^L) and zeros beyond.
-// One thread per output pixel; weights [27][cout] in shared memory.  cout % 4 == 0, <= 64.
+// One thread per output pixel; weights [27][cout] in shared memory (cout == 16: in the
+// kernel parameters).  cout % 4 == 0, <= 64.
 // =====================================================================================
 template <typename T>
 __global__ void __launch_bounds__(256) conv_first_kernel(ConvFirstArgs a) {
     __shared__ __align__(16) float ws[27 * 64];
     __shared__ __align__(16) float bs[64];
-    for (int i = threadIdx.x; i < 27 * a.cout; i += blockDim.x) ws[i] = a.wk[i];
-    for (int i = threadIdx.x; i < a.cout; i += blockDim.x) bs[i] = a.bias[i];
-    __syncthreads();
+    if (a.cout != 16) {
+        for (int i = threadIdx.x; i < 27 * a.cout; i += blockDim.x) ws[i] = a.wk[i];
+        for (int i = threadIdx.x; i < a.cout; i += blockDim.x) bs[i] = a.bias[i];
+        __syncthreads();
+    }
     pdl_wait();  // the weights above are constant; the image and the output follow the previous kernel
     const int ho = a.Hp / 2, wo = a.Wp / 2;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -162,6 +165,21 @@ __global__ void __launch_bounds__(256) conv_first_kernel(ConvFirstArgs a) {
                 v[c * 9 + ky * 3 + kx] = val;
             }
     T *out = static_cast<T *>(a.out) + (size_t)idx * a.cout;
+    if (a.cout == 16) {
+        // weights straight from the parameter bank: 432 FMAs, no weight loads
+        float acc[16];
+#pragma unroll
+        for (int o = 0; o < 16; ++o) acc[o] = a.b16[o];
+#pragma unroll
+        for (int k = 0; k < 27; ++k)
+#pragma unroll
+            for (int o = 0; o < 16; ++o) acc[o] = fmaf(a.w16[k * 16 + o], v[k], acc[o]);
+#pragma unroll
+        for (int o = 0; o < 16; o += 4)
+            st4(out + o, make_float4(lrelu(acc[o]) * a.q_out, lrelu(acc[o + 1]) * a.q_out,
+                                     lrelu(acc[o + 2]) * a.q_out, lrelu(acc[o + 3]) * a.q_out));
+        return;
+    }
     for (int o = 0; o < a.cout; o += 4) {
         float4 acc = *reinterpret_cast<const float4 *>(&bs[o]);
 #pragma unroll
