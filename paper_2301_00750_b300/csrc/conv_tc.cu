@@ -393,7 +393,7 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
 //   * warps 0-3 (epilogue): drain accumulator r % 2 into output row y0 + r while the MMAs of
 //     row r + 1 run, then hand the accumulator back.
 // Every wait is bounded as in the kernels above.
-constexpr int ROWS = 8;
+constexpr int ROWS = 4;
 constexpr int RING = 4;  // input rows held at once
 __host__ __device__ constexpr uint32_t halo_slot_for(int rb) { return (uint32_t)((HALO_ROWS * rb + 1023) / 1024 * 1024); }
 __host__ __device__ constexpr uint32_t wtile_for(int bn, int rb) { return (uint32_t)((bn * rb + 1023) / 1024 * 1024); }
@@ -531,8 +531,8 @@ cudaError_t launch_bn(const TcConvPlan &plan, const TcLaunch &lp, int n_img, cud
     dim3 grid((plan.wo + BM - 1) / BM, plan.ho, n_img);
     if constexpr (BN <= 32 && !HEAD) {
         // the multi-row form pays off where the grid stays large: measured on the 16- and
-        // 32-channel pyramid levels; the flow heads (two K steps, 173 KB of shared memory, one
-        // CTA per SM) and the coarse levels lose with 8x fewer CTAs
+        // 32-channel pyramid levels (4 rows per CTA beat 8 and 2); the flow heads (two K
+        // steps, one CTA per SM) and the coarse levels lose with ROWS times fewer CTAs
         if (plan.stride == 1 && plan.taps == 9 && plan.nch == 1) {
             const size_t smem = rows_smem_for(BN, plan.rb, 1);
             static size_t attr_bytes = 0;

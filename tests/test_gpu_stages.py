@@ -87,8 +87,8 @@ CONV_CASES = [
     (2, 3, 130, 216, 128, 1), (1, 8, 8, 48, 48, 1),
     # wide rows: two tiles with a ragged second one, a one-pixel last tile, three K steps
     (1, 20, 300, 128, 128, 1), (2, 9, 480, 120, 96, 1), (1, 6, 257, 64, 128, 1), (1, 3, 192, 192, 128, 1),
-    # one K step and <= 32 outputs at stride 1 run the multi-row kernel (8 rows per CTA):
-    # row tails of 7 and 1, a one-pixel last tile, a 24-channel input, three images
+    # one K step and <= 32 outputs at stride 1 run the multi-row kernel (4 rows per CTA):
+    # row tails of 3 and 1, a one-pixel last tile, a 24-channel input, three images
     (2, 23, 200, 64, 32, 1), (1, 1, 129, 16, 16, 1), (3, 17, 128, 24, 16, 1),
     # a single 120-pixel tile per row over 50 rows and two images, two K steps, 96 outputs
     (2, 50, 120, 128, 96, 1),
