@@ -159,7 +159,9 @@ TC_API tc_status tc_process_frame(tc_stream *s, const float *I_t, const float *P
 
 /* As tc_process_frame with HOST buffers: copies I_t, P_t to the device, runs the frame and
  * copies O_t (and the optional outputs) back, then waits for the stream.  The same
- * layouts as above; host pointers.  Pinned host memory makes the copies faster. */
+ * layouts as above; host pointers.  Pinned host memory makes the copies faster.  P_t is
+ * uploaded on a second, library-owned stream while the flow network runs (only the
+ * consistency pass reads it), so its copy overlaps the frame's kernels. */
 TC_API tc_status tc_process_frame_host(tc_stream *s, const float *I_t, const float *P_t, float *O_t,
                                 float *wc_opt, uint8_t *mask_opt);
 

@@ -296,6 +296,14 @@ struct tc_stream {
     // consistency pass, whose nodes are updated before each replay).
     bool graphs = true;
     cudaStream_t gst = nullptr;               // library stream the graphs are captured on and replayed on
+    // tc_process_frame_host uploads P_t on cst while the flow network runs and records ev_p
+    // after it; the pass that reads P_t waits on ev_p (in the host calls' graphs: an external
+    // event node on a side branch).  Device calls have P_t already and wait for nothing.
+    cudaStream_t cst = nullptr;
+    cudaEvent_t ev_p = nullptr;
+    bool p_pending = false;  // this frame's P_t arrives through the upload on cst
+    bool capturing = false;  // frame_launches is being captured into a graph
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // capture: the wait on ev_p as a side branch
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;  // fence gst to the caller's stream
     struct FrameGraph {
         cudaGraph_t g = nullptr;
@@ -303,7 +311,7 @@ struct tc_stream {
         cudaGraphNode_t n_first = nullptr, n_cons = nullptr, n_copy = nullptr, n_in = nullptr;
         cudaKernelNodeParams p_first{}, p_cons{}, p_copy{}, p_in{};
         int launches = 0;
-    } fg[2];
+    } fg[2][2];  // [host entry point][slot parity]: only host calls' graphs wait for the P_t upload
     // screened-Poisson solver (allocated when first enabled): A_t, w_c, right-hand side and
     // four iterate planes, each (3, H, W) float (w_c (H, W))
     float *sv_A = nullptr, *sv_wc = nullptr, *sv_b = nullptr, *sv_c0 = nullptr,
@@ -1024,8 +1032,19 @@ template <typename T>
 static tc_status frame_launches(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask,
                                 int cur) {
     tc_status r;
+    const bool upload = s->p_pending;  // P_t is being uploaded on cst (host entry point)
+    if (upload && s->capturing) {
+        // the wait for P_t (an external event node) on a branch forked at the frame's start
+        // and joined before the pass that reads P_t, off the chain of kernels
+        TC_TRY(s, cudaEventRecord(s->ev_fork, s->st), "cudaEventRecord");
+        TC_TRY(s, cudaStreamWaitEvent(s->cst, s->ev_fork, 0), "cudaStreamWaitEvent");
+        TC_TRY(s, cudaStreamWaitEvent(s->cst, s->ev_p, cudaEventWaitExternal), "cudaStreamWaitEvent");
+        TC_TRY(s, cudaEventRecord(s->ev_join, s->cst), "cudaEventRecord");
+    }
     if ((r = run_pyramid<T>(s, I, cur)) != TC_OK) return r;
     if (s->t > 0 && (r = run_estimators<T>(s, cur)) != TC_OK) return r;
+    // everything from here on may read P_t
+    if (upload) TC_TRY(s, cudaStreamWaitEvent(s->st, s->capturing ? s->ev_join : s->ev_p, 0), "cudaStreamWaitEvent");
     if (!s->latency) {
         const ConsistArgs ca = consist_args(s, I, P, O, wc, mask, cur);
         TC_LAUNCH_CAT(s, TC_PROF_CONSISTENCY, launch_consistency(ca, s->st));
@@ -1057,13 +1076,15 @@ static tc_status frame_launches(tc_stream *s, const float *I, const float *P, fl
 template <typename T>
 static tc_status capture_frame(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask,
                                int cur) {
-    tc_stream::FrameGraph &G = s->fg[cur];
+    tc_stream::FrameGraph &G = s->fg[s->p_pending ? 1 : 0][cur];
     // Capture on the library's own stream (capture is not allowed on the legacy default
     // stream a caller may pass); the launch helpers use s->st, so point it there meanwhile.
     cudaStream_t caller = s->st;
     TC_TRY(s, cudaStreamBeginCapture(s->gst, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
     s->st = s->gst;
+    s->capturing = true;
     const tc_status r = frame_launches<T>(s, I, P, O, wc, mask, cur);
+    s->capturing = false;
     s->st = caller;
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(s->gst, &g);
@@ -1146,7 +1167,7 @@ static tc_status process(tc_stream *s, const float *I, const float *P, float *O,
         s->last_out = out;
         return TC_OK;
     }
-    tc_stream::FrameGraph &G = s->fg[cur];
+    tc_stream::FrameGraph &G = s->fg[s->p_pending ? 1 : 0][cur];
     if (!s->gst) {
         TC_TRY(s, cudaStreamCreateWithFlags(&s->gst, cudaStreamNonBlocking), "cudaStreamCreate");
         TC_TRY(s, cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming), "cudaEventCreate");
@@ -1206,11 +1227,12 @@ static tc_status process(tc_stream *s, const float *I, const float *P, float *O,
 }
 
 static void release_graphs(tc_stream *s) {
-    for (auto &G : s->fg) {
-        if (G.exec) cudaGraphExecDestroy(G.exec);
-        if (G.g) cudaGraphDestroy(G.g);
-        G = tc_stream::FrameGraph{};
-    }
+    for (auto &GG : s->fg)
+        for (auto &G : GG) {
+            if (G.exec) cudaGraphExecDestroy(G.exec);
+            if (G.g) cudaGraphDestroy(G.g);
+            G = tc_stream::FrameGraph{};
+        }
 }
 
 static void release_graph_stream(tc_stream *s) {
@@ -1357,10 +1379,25 @@ extern "C" tc_status tc_process_frame_host(tc_stream *s, const float *I_t, const
         if ((r = dalloc_t(s, &s->hwc, plane * sizeof(float))) != TC_OK) return r;
         if ((r = dalloc_t(s, &s->hmask, plane)) != TC_OK) return r;
     }
+    if (!s->cst) TC_TRY(s, cudaStreamCreateWithFlags(&s->cst, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (!s->ev_p) {
+        TC_TRY(s, cudaEventCreateWithFlags(&s->ev_p, cudaEventDisableTiming), "cudaEventCreate");
+        TC_TRY(s, cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
+        TC_TRY(s, cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming), "cudaEventCreate");
+    }
+    // I_t first on the frame's stream; P_t, read only by the consistency pass at the end of
+    // the frame, on the copy stream while the flow network runs (the previous call has
+    // finished with hP: it waited for its stream)
     TC_TRY(s, cudaMemcpyAsync(s->hI, I_t, img, cudaMemcpyHostToDevice, s->st), "H2D I_t");
-    TC_TRY(s, cudaMemcpyAsync(s->hP, P_t, img, cudaMemcpyHostToDevice, s->st), "H2D P_t");
+    TC_TRY(s, cudaMemcpyAsync(s->hP, P_t, img, cudaMemcpyHostToDevice, s->cst), "H2D P_t");
+    TC_TRY(s, cudaEventRecord(s->ev_p, s->cst), "cudaEventRecord");
+    s->p_pending = true;
     r = tc_process_frame(s, s->hI, s->hP, s->hO, wc_opt ? s->hwc : nullptr, mask_opt ? s->hmask : nullptr);
-    if (r != TC_OK) return r;
+    s->p_pending = false;
+    if (r != TC_OK) {
+        cudaStreamSynchronize(s->cst);  // the upload into hP ends before any later call reuses it
+        return r;
+    }
     if (s->last_out < 0) {  // one frame of latency: the first call writes nothing
         TC_TRY(s, cudaStreamSynchronize(s->st), "stream synchronize");
         return check_device_error(s);
@@ -1430,6 +1467,13 @@ extern "C" tc_status tc_destroy(tc_stream *s) {
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     release_graphs(s);
     release_graph_stream(s);
+    if (s->cst) {
+        cudaStreamSynchronize(s->cst);
+        cudaStreamDestroy(s->cst);
+    }
+    if (s->ev_p) cudaEventDestroy(s->ev_p);  // after the graphs that wait on it
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
     free_all(s);
     delete s;
     return TC_OK;

@@ -134,21 +134,24 @@ def test_bf16_stream_plans_convs_on_tensor_cores(chans, radius, want):
     s.destroy()
 
 
-def test_host_entry_point_matches_device_entry_point():
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_host_entry_point_matches_device_entry_point(prec):
+    """Host buffers in and out (P_t uploaded on a second stream while the flow network runs,
+    the consistency pass waiting on it) give the device entry point's results bit for bit,
+    on the eager first frames and on the replayed graphs from the third frame on."""
     import torch
     path, _ = weights_file()
-    d = synth.pair64()
-    frames, styl = [d["I0"], d["I1"]], [d["P0"], d["P1"]]
-    dev = _run_gpu(path, frames, styl, k1=0.4)
-    s = tc.Stream(64, 64, "fp32", weights_path=path)
+    frames, styl = _pair(64, 64, seed=5, n=5)
+    dev = _run_gpu(path, frames, styl, prec=prec, k1=0.4)
+    s = tc.Stream(64, 64, prec, weights_path=path)
     s.set_consistency(k1=0.4)
-    for t in range(2):
+    for t in range(len(frames)):
         O = np.empty((3, 64, 64), np.float32)
         wc = np.empty((64, 64), np.float32)
         m = np.empty((64, 64), np.uint8)
         s.process_frame_host(np.ascontiguousarray(frames[t]), np.ascontiguousarray(styl[t]), O, wc, m)
-        assert np.array_equal(O, dev[t]["O"]) and np.array_equal(m, dev[t]["mask"])
-        assert np.array_equal(wc, dev[t]["wc"])
+        assert np.array_equal(O, dev[t]["O"]) and np.array_equal(m, dev[t]["mask"]), t
+        assert np.array_equal(wc, dev[t]["wc"]), t
     s.destroy()
     torch.cuda.synchronize()
 
