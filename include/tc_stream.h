@@ -165,6 +165,19 @@ TC_API tc_status tc_process_frame(tc_stream *s, const float *I_t, const float *P
 TC_API tc_status tc_process_frame_host(tc_stream *s, const float *I_t, const float *P_t, float *O_t,
                                 float *wc_opt, uint8_t *mask_opt);
 
+/* Pipelined form of tc_process_frame_host for a stream of frames: enqueues the upload of
+ * I_t, P_t, the frame, and the download of its outputs into O_t (and wc_opt, mask_opt),
+ * then returns without waiting.  The next call's upload and this call's download run on
+ * two library-owned copy streams while the neighbouring frames' kernels run (device
+ * staging is double-buffered), so the copies and the kernels overlap.  The host buffers
+ * must stay valid, the inputs unmodified and the outputs unread, until tc_synchronize
+ * returns; the copies overlap only from page-locked memory.  Same layouts and the same
+ * one-frame-of-latency behaviour as tc_process_frame_host (the first call of a latency-1
+ * sequence writes nothing; the last frame comes from tc_flush).  Errors as
+ * tc_process_frame; device-side failures are reported by tc_synchronize. */
+TC_API tc_status tc_process_frame_host_async(tc_stream *s, const float *I_t, const float *P_t, float *O_t,
+                                             float *wc_opt, uint8_t *mask_opt);
+
 /* One frame of latency (Sec. 1, Sec. 3.1: the local term of Eq. 2 also warps the next
  * frame).  frames = 1: each tc_process_frame call with frame t+1 returns frame t, with w_n
  * of Eq. 3 (clamped to k2) and the next frame in L_t (Eq. 2) and A^I_t (Eq. 6); the flows
@@ -225,7 +238,8 @@ TC_API tc_status tc_set_fp8_scales(tc_stream *s, const float *scales, int n);
  * Errors: TC_ERR_STATE before the second frame. */
 TC_API tc_status tc_get_flows(tc_stream *s, float *Fb, float *Ff);
 
-/* Waits for the stream's enqueued work and reports device-side failures: TC_ERR_TIMEOUT
+/* Waits for the stream's enqueued work (the copies of tc_process_frame_host_async
+ * included) and reports device-side failures: TC_ERR_TIMEOUT
  * (and a poisoned stream) if a tensor-core kernel gave up on a bounded wait, TC_ERR_CUDA on
  * a CUDA error.  tc_process_frame_host performs the same check. */
 TC_API tc_status tc_synchronize(tc_stream *s);

@@ -33,7 +33,8 @@ EXPORTED = ["tc_default_consistency", "tc_create_stream", "tc_set_consistency", 
             "tc_op_last_used_tensor_cores", "tc_op_correlation_bf16_noalloc",
             "tc_tensor_core_correlation_levels", "tc_set_graphs", "tc_activation_segments",
             "tc_set_amax_recording", "tc_get_amax", "tc_set_fp8_scales", "tc_op_poisson_solve", "tc_set_latency",
-            "tc_flush", "tc_last_output_frame", "tc_op_consistency_next", "tc_op_downscale2", "tc_op_sepconv"]
+            "tc_flush", "tc_last_output_frame", "tc_op_consistency_next", "tc_op_downscale2", "tc_op_sepconv",
+            "tc_process_frame_host_async"]
 E4M3_MAX = 448.0
 NOALLOC_SCRATCH_BYTES = 16 << 20
 PROFILE_CATEGORIES = ["pyramid_conv", "estimator_conv", "head", "correlation", "warp", "upsample", "consistency",
@@ -60,6 +61,7 @@ _lib.tc_create_stream.argtypes = [ctypes.POINTER(TcStreamDesc), _vp, ctypes.POIN
 _lib.tc_set_consistency.argtypes = [_vp, ctypes.POINTER(TcConsistency)]
 _lib.tc_process_frame.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
 _lib.tc_process_frame_host.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+_lib.tc_process_frame_host_async.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
 _lib.tc_get_flows.argtypes = [_vp, _vp, _vp]
 _lib.tc_destroy.argtypes = [_vp]
 _lib.tc_last_error.argtypes = [_vp]
@@ -92,7 +94,7 @@ _lib.tc_last_output_frame.argtypes = [_vp]
 _lib.tc_last_output_frame.restype = ctypes.c_longlong
 _lib.tc_op_consistency_next.argtypes = [_vp] * 11 + [_i] * 5 + [ctypes.POINTER(TcConsistency), _vp, _vp, _vp, _vp]
 for _n in ["tc_set_amax_recording", "tc_get_amax", "tc_set_fp8_scales", "tc_set_graphs", "tc_op_correlation_bf16_noalloc", "tc_synchronize", "tc_set_profiling", "tc_get_profile", "tc_create_stream", "tc_set_consistency", "tc_process_frame", "tc_process_frame_host", "tc_get_flows",
-           "tc_destroy", "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
+           "tc_process_frame_host_async", "tc_destroy", "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
            "tc_op_consistency", "tc_set_latency", "tc_flush", "tc_op_consistency_next", "tc_op_downscale2",
            "tc_op_sepconv"]:
     getattr(_lib, _n).restype = ctypes.c_int
@@ -107,6 +109,17 @@ class TcError(RuntimeError):
 def _check(status, handle=None):
     if status != TC_OK:
         raise TcError(status, (_lib.tc_last_error(handle) or b"").decode())
+
+
+def _hbuf(a, dt):
+    """Host address of a contiguous NumPy array or CPU torch tensor (or None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if a.dtype != dt or not a.flags.c_contiguous:
+        raise TypeError("host buffers must be contiguous " + str(dt))
+    return a.ctypes.data
 
 
 def _ptr(t, dtype=None, name="tensor"):
@@ -188,16 +201,17 @@ class Stream:
 
     def process_frame_host(self, I, P, O, wc=None, mask=None):
         """Host buffers (NumPy or CPU torch tensors, contiguous float32 / uint8)."""
-        def hp(a, dt):
-            if a is None:
-                return None
-            if hasattr(a, "data_ptr"):
-                return a.data_ptr()
-            if a.dtype != dt or not a.flags.c_contiguous:
-                raise TypeError("host buffers must be contiguous " + str(dt))
-            return a.ctypes.data
-        _check(_lib.tc_process_frame_host(self._h, hp(I, np.float32), hp(P, np.float32), hp(O, np.float32),
-                                          hp(wc, np.float32), hp(mask, np.uint8)), self._h)
+        _check(_lib.tc_process_frame_host(self._h, _hbuf(I, np.float32), _hbuf(P, np.float32),
+                                          _hbuf(O, np.float32), _hbuf(wc, np.float32), _hbuf(mask, np.uint8)),
+               self._h)
+
+    def process_frame_host_async(self, I, P, O, wc=None, mask=None):
+        """Pipelined host-buffer call: enqueues the upload, the frame and the download and
+        returns; the buffers (page-locked for the copies to overlap) must stay alive and
+        untouched until synchronize()."""
+        _check(_lib.tc_process_frame_host_async(self._h, _hbuf(I, np.float32), _hbuf(P, np.float32),
+                                                _hbuf(O, np.float32), _hbuf(wc, np.float32),
+                                                _hbuf(mask, np.uint8)), self._h)
 
     def set_latency(self, frames: int):
         """1: each process_frame with frame t+1 returns frame t blended with both neighbours

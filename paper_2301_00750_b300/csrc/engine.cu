@@ -303,6 +303,13 @@ struct tc_stream {
     cudaEvent_t ev_p = nullptr;
     bool p_pending = false;  // this frame's P_t arrives through the upload on cst
     bool capturing = false;  // frame_launches is being captured into a graph
+    // tc_process_frame_host_async: device staging per slot (call parity), the download
+    // stream, and per slot: inputs uploaded, frame done, outputs downloaded
+    float *aI[2] = {}, *aP[2] = {}, *aO[2] = {}, *awc[2] = {};
+    uint8_t *amask[2] = {};
+    cudaStream_t dst = nullptr;
+    cudaEvent_t a_in[2] = {}, a_done[2] = {}, a_out[2] = {};
+    long long a_n = 0;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // capture: the wait on ev_p as a side branch
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;  // fence gst to the caller's stream
     struct FrameGraph {
@@ -1363,7 +1370,56 @@ extern "C" tc_status tc_synchronize(tc_stream *s) {
     tc_status r = check_stream(s, "tc_synchronize");
     if (r != TC_OK) return r;
     TC_TRY(s, cudaStreamSynchronize(s->st), "stream synchronize");
+    if (s->cst) TC_TRY(s, cudaStreamSynchronize(s->cst), "upload stream synchronize");
+    if (s->dst) TC_TRY(s, cudaStreamSynchronize(s->dst), "download stream synchronize");
     return check_device_error(s);
+}
+
+extern "C" tc_status tc_process_frame_host_async(tc_stream *s, const float *I_t, const float *P_t, float *O_t,
+                                                 float *wc_opt, uint8_t *mask_opt) {
+    tc_status r = check_stream(s, "tc_process_frame_host_async");
+    if (r != TC_OK) return r;
+    if (!I_t || !P_t || !O_t) return fail(s, TC_ERR_INVALID_ARG, "tc_process_frame_host_async: NULL image pointer");
+    const size_t img = (size_t)3 * s->H * s->W * sizeof(float), plane = (size_t)s->H * s->W;
+    if (!s->aI[0]) {
+        for (int k = 0; k < 2; ++k) {
+            if ((r = dalloc_t(s, &s->aI[k], img)) != TC_OK) return r;
+            if ((r = dalloc_t(s, &s->aP[k], img)) != TC_OK) return r;
+            if ((r = dalloc_t(s, &s->aO[k], img)) != TC_OK) return r;
+            if ((r = dalloc_t(s, &s->awc[k], plane * sizeof(float))) != TC_OK) return r;
+            if ((r = dalloc_t(s, &s->amask[k], plane)) != TC_OK) return r;
+            TC_TRY(s, cudaEventCreateWithFlags(&s->a_in[k], cudaEventDisableTiming), "cudaEventCreate");
+            TC_TRY(s, cudaEventCreateWithFlags(&s->a_done[k], cudaEventDisableTiming), "cudaEventCreate");
+            TC_TRY(s, cudaEventCreateWithFlags(&s->a_out[k], cudaEventDisableTiming), "cudaEventCreate");
+        }
+        if (!s->cst) TC_TRY(s, cudaStreamCreateWithFlags(&s->cst, cudaStreamNonBlocking), "cudaStreamCreate");
+        TC_TRY(s, cudaStreamCreateWithFlags(&s->dst, cudaStreamNonBlocking), "cudaStreamCreate");
+    }
+    const int k = (int)(s->a_n & 1);
+    // Slot k was last used two calls ago: its frame read aI[k], aP[k] (a_done[k]) and its
+    // download read aO[k], awc[k], amask[k] (a_out[k]).  A wait on an event not yet
+    // recorded returns at once.
+    TC_TRY(s, cudaStreamWaitEvent(s->cst, s->a_done[k], 0), "cudaStreamWaitEvent");
+    TC_TRY(s, cudaMemcpyAsync(s->aI[k], I_t, img, cudaMemcpyHostToDevice, s->cst), "H2D I_t");
+    TC_TRY(s, cudaMemcpyAsync(s->aP[k], P_t, img, cudaMemcpyHostToDevice, s->cst), "H2D P_t");
+    TC_TRY(s, cudaEventRecord(s->a_in[k], s->cst), "cudaEventRecord");
+    TC_TRY(s, cudaStreamWaitEvent(s->st, s->a_in[k], 0), "cudaStreamWaitEvent");
+    TC_TRY(s, cudaStreamWaitEvent(s->st, s->a_out[k], 0), "cudaStreamWaitEvent");
+    r = tc_process_frame(s, s->aI[k], s->aP[k], s->aO[k], wc_opt ? s->awc[k] : nullptr,
+                         mask_opt ? s->amask[k] : nullptr);
+    if (r != TC_OK) return r;
+    TC_TRY(s, cudaEventRecord(s->a_done[k], s->st), "cudaEventRecord");
+    TC_TRY(s, cudaStreamWaitEvent(s->dst, s->a_done[k], 0), "cudaStreamWaitEvent");
+    if (s->last_out >= 0) {  // one frame of latency: the first call of a sequence writes nothing
+        TC_TRY(s, cudaMemcpyAsync(O_t, s->aO[k], img, cudaMemcpyDeviceToHost, s->dst), "D2H O_t");
+        if (wc_opt)
+            TC_TRY(s, cudaMemcpyAsync(wc_opt, s->awc[k], plane * sizeof(float), cudaMemcpyDeviceToHost, s->dst),
+                   "D2H w_c");
+        if (mask_opt) TC_TRY(s, cudaMemcpyAsync(mask_opt, s->amask[k], plane, cudaMemcpyDeviceToHost, s->dst), "D2H mask");
+    }
+    TC_TRY(s, cudaEventRecord(s->a_out[k], s->dst), "cudaEventRecord");
+    s->a_n += 1;
+    return TC_OK;
 }
 
 extern "C" tc_status tc_process_frame_host(tc_stream *s, const float *I_t, const float *P_t, float *O_t,
@@ -1474,6 +1530,15 @@ extern "C" tc_status tc_destroy(tc_stream *s) {
     if (s->ev_p) cudaEventDestroy(s->ev_p);  // after the graphs that wait on it
     if (s->ev_fork) cudaEventDestroy(s->ev_fork);
     if (s->ev_join) cudaEventDestroy(s->ev_join);
+    if (s->dst) {
+        cudaStreamSynchronize(s->dst);
+        cudaStreamDestroy(s->dst);
+    }
+    for (int k = 0; k < 2; ++k) {
+        if (s->a_in[k]) cudaEventDestroy(s->a_in[k]);
+        if (s->a_done[k]) cudaEventDestroy(s->a_done[k]);
+        if (s->a_out[k]) cudaEventDestroy(s->a_out[k]);
+    }
     free_all(s);
     delete s;
     return TC_OK;

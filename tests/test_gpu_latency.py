@@ -296,6 +296,34 @@ def test_latency_host_entry_point():
     host.destroy()
 
 
+def test_latency_pipelined_host_entry_point():
+    """One frame of latency through tc_process_frame_host_async: the first call writes
+    nothing, call t writes frame t - 1, equal to the device entry point's outputs."""
+    import torch
+    path, _ = weights_file((16, 32, 48), 3)
+    frames, styl = _frames(64, 64, seed=3, n=4)
+    dev, host = tc.Stream(64, 64, "bf16", weights_path=path), tc.Stream(64, 64, "bf16", weights_path=path)
+    for s in (dev, host):
+        s.set_latency(1)
+    want, outs, keep = [], [], []  # the host buffers live until synchronize()
+    for t, (I, P) in enumerate(zip(frames, styl)):
+        O = torch.empty((3, 64, 64), device="cuda")
+        dev.process_frame(to_dev(I), to_dev(P), O)
+        want.append(to_np(O))
+        hI = torch.from_numpy(np.ascontiguousarray(I)).pin_memory()
+        hP = torch.from_numpy(np.ascontiguousarray(P)).pin_memory()
+        hO = torch.full((3, 64, 64), -1.0).pin_memory()
+        host.process_frame_host_async(hI, hP, hO)
+        keep += [hI, hP]
+        outs.append(hO)
+    host.synchronize()
+    assert (outs[0].numpy() == -1.0).all()
+    for t in range(1, len(frames)):
+        assert np.array_equal(outs[t].numpy(), want[t]), t
+    dev.destroy()
+    host.destroy()
+
+
 def test_latency_argument_checks():
     import torch
     path, _ = weights_file((16, 32, 48), 3)

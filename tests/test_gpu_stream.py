@@ -156,6 +156,31 @@ def test_host_entry_point_matches_device_entry_point(prec):
     torch.cuda.synchronize()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_pipelined_host_entry_point_matches_device_entry_point(prec):
+    """tc_process_frame_host_async: five frames enqueued back to back from page-locked
+    buffers (uploads, frames and downloads overlapping through the double-buffered staging),
+    one synchronize at the end; every frame's outputs equal the device entry point's."""
+    import torch
+    path, _ = weights_file()
+    frames, styl = _pair(64, 64, seed=6, n=5)
+    dev = _run_gpu(path, frames, styl, prec=prec, k1=0.4)
+    s = tc.Stream(64, 64, prec, weights_path=path)
+    s.set_consistency(k1=0.4)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    hI, hP = [pin(f) for f in frames], [pin(p) for p in styl]
+    outs = [(torch.empty((3, 64, 64)).pin_memory(), torch.empty((64, 64)).pin_memory(),
+             torch.empty((64, 64), dtype=torch.uint8).pin_memory()) for _ in frames]
+    for t in range(len(frames)):
+        s.process_frame_host_async(hI[t], hP[t], *outs[t])
+    s.synchronize()
+    for t, (O, wc, m) in enumerate(outs):
+        assert np.array_equal(O.numpy(), dev[t]["O"]) and np.array_equal(m.numpy(), dev[t]["mask"]), t
+        assert np.array_equal(wc.numpy(), dev[t]["wc"]), t
+    s.destroy()
+    torch.cuda.synchronize()
+
+
 def test_stream_1080p_flows_fp32():
     """Full-size workload: the 1920x1080 5-level r=4 network, flows of one frame pair
     against the oracle over the whole frame."""
