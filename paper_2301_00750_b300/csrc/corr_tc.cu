@@ -101,8 +101,8 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
             const uint32_t fb = full0 + 8 * ch;
             mbar_expect_tx(fb, A_BYTES + (uint32_t)G::NPOS * BK * 2);
             const int c0 = ch * (F8 ? 2 * BK : BK);  // 128-byte steps: 64 bf16 or 128 e4m3 channels
-            tma_load_4d(&tmS, fb, smem_u32(sA + ch * A_BYTES), c0, x0, y0, p.img_s[b]);
-            tma_load_4d(&tmO, fb, smem_u32(sB + ch * G::B_BYTES), c0, x0 - R, y0 - R, p.img_o[b]);
+            tma_load_4d(&tmS, fb, smem_u32(sA + ch * A_BYTES), c0, x0, y0, b ? p.img_s[1] : p.img_s[0]);
+            tma_load_4d(&tmO, fb, smem_u32(sB + ch * G::B_BYTES), c0, x0 - R, y0 - R, b ? p.img_o[1] : p.img_o[0]);
         }
     } else if (threadIdx.x == 32) {
         // ---- MMA issuer: D[:, 0:NH] and D[:, NH:NP]
@@ -212,7 +212,7 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
             }
             if (p.self_copy) {
                 const size_t esz = F8 ? 1 : 2;
-                const uint4 *src = reinterpret_cast<const uint4 *>(static_cast<const uint8_t *>(p.fs[b]) +
+                const uint4 *src = reinterpret_cast<const uint4 *>(static_cast<const uint8_t *>(b ? p.fs[1] : p.fs[0]) +
                                                                    ((size_t)y * p.w + x) * p.c * esz);
                 uint4 *cp = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(p.self_copy) + pix * p.out_cs * esz);
                 for (int q = 0; q < (int)(p.c * esz / 16); ++q) cp[q] = __ldg(src + q);

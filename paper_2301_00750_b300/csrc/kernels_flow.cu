@@ -269,8 +269,12 @@ __global__ void __launch_bounds__(256) corr_kernel(CorrArgs a) {
     const int x0 = blockIdx.x * CT, y0 = blockIdx.y * CT;
     const int x = x0 + tx, y = y0 + ty;
     const bool valid = x < a.w && y < a.h;
-    const T *fs = a.fs_img ? static_cast<const T *>(a.fs[0]) + b * a.fs_img : static_cast<const T *>(a.fs[b]);
-    const T *fo = a.fo_img ? static_cast<const T *>(a.fo[0]) + b * a.fo_img : static_cast<const T *>(a.fo[b]);
+    // (selects, not a.fs[b]: a runtime index into the parameter array would copy the
+    // arguments to local memory)
+    const T *fs = a.fs_img ? static_cast<const T *>(a.fs[0]) + b * a.fs_img
+                           : static_cast<const T *>(b ? a.fs[1] : a.fs[0]);
+    const T *fo = a.fo_img ? static_cast<const T *>(a.fo[0]) + b * a.fo_img
+                           : static_cast<const T *>(b ? a.fo[1] : a.fo[0]);
     float acc[ND];
 #pragma unroll
     for (int k = 0; k < ND; ++k) acc[k] = 0.f;
@@ -380,7 +384,8 @@ __global__ void __launch_bounds__(256) warp_kernel(WarpArgs a) {
     const float fu = floorf(u), fv = floorf(v);
     const float ax = u - fu, ay = v - fv;
     const int xa = x + (int)fu, ya = y + (int)fv;
-    const T *f = a.f_img ? static_cast<const T *>(a.f[0]) + b * a.f_img : static_cast<const T *>(a.f[b]);
+    const T *f = a.f_img ? static_cast<const T *>(a.f[0]) + b * a.f_img
+                         : static_cast<const T *>(b ? a.f[1] : a.f[0]);  // no runtime index into the arguments
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy) {
