@@ -347,29 +347,28 @@ cudaError_t launch_corr(const CorrArgs &a, cudaStream_t st) {
 
 // =====================================================================================
 // Bilinear feature warp, zeros off the map: out(x) = sum of on-map taps of f at x + flow.
-// One thread per (pixel, 4 channels).  With `coarse` set, the flow is the x2 upsampling of
+// One thread per (pixel, 4Q channels).  With `coarse` set, the flow is the x2 upsampling of
 // the coarser level's flow, computed here (and stored once per pixel) instead of by a
 // separate pass.  The integer part of the sample position and the
 // interpolation weights are taken from the flow alone (floor(u), u - floor(u)), which is
 // exact in float32.
 // =====================================================================================
-template <typename T>
-__global__ void __launch_bounds__(256) warp_kernel(WarpArgs a) {
+template <typename T, int Q>
+__global__ void __launch_bounds__(256) warp_kernel(WarpArgs a, int ng, uint32_t ng_magic) {
+    // one thread per (pixel, group of Q quads of channels); block row y, image b; the
+    // pixel is i / ng by a multiply-high (exact for i < 2^21, 2 <= ng <= 64; ng = 1 has
+    // no 32-bit multiplier)
     pdl_wait();
-    const int nq = a.c / 4;
-    const size_t total = (size_t)a.n * a.h * a.w * nq;
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= total) return;
-    const int q = (int)(i % nq);
-    const size_t p = i / nq;
-    const int hwp = a.h * a.w;
-    const int b = (int)(p / hwp), rem = (int)(p - (size_t)b * hwp);
-    const int y = rem / a.w, x = rem - y * a.w;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (uint32_t)(a.w * ng)) return;
+    const int x = ng == 1 ? (int)i : (int)__umulhi(i, ng_magic), g = (int)i - x * ng;
+    const int y = blockIdx.y, b = blockIdx.z;
+    const size_t p = ((size_t)b * a.h + y) * a.w + x;
     float2 fl;
     if (a.coarse) {
         const int ch = a.h / 2, cw = a.w / 2;
         fl = upsampled_flow_at(a.coarse + (size_t)b * ch * cw * 2, ch, cw, 2, x, y);
-        if (q == 0) {
+        if (g == 0) {
             reinterpret_cast<float2 *>(a.up_out)[p] = fl;
             if (a.act) {
                 T *dst = static_cast<T *>(a.act) + p * a.act_cs;
@@ -386,7 +385,9 @@ __global__ void __launch_bounds__(256) warp_kernel(WarpArgs a) {
     const int xa = x + (int)fu, ya = y + (int)fv;
     const T *f = a.f_img ? static_cast<const T *>(a.f[0]) + b * a.f_img
                          : static_cast<const T *>(b ? a.f[1] : a.f[0]);  // no runtime index into the arguments
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 acc[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy) {
 #pragma unroll
@@ -394,20 +395,32 @@ __global__ void __launch_bounds__(256) warp_kernel(WarpArgs a) {
             const int xx = xa + dx, yy = ya + dy;
             if (xx < 0 || xx >= a.w || yy < 0 || yy >= a.h) continue;
             const float wgt = (dx ? ax : 1.f - ax) * (dy ? ay : 1.f - ay);
-            const float4 t = ld4(f + ((size_t)yy * a.w + xx) * a.f_cs + q * 4);
-            acc.x = fmaf(wgt, t.x, acc.x);
-            acc.y = fmaf(wgt, t.y, acc.y);
-            acc.z = fmaf(wgt, t.z, acc.z);
-            acc.w = fmaf(wgt, t.w, acc.w);
+            const T *t = f + ((size_t)yy * a.w + xx) * a.f_cs + g * (4 * Q);
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                const float4 tv = ld4(t + 4 * j);
+                acc[j].x = fmaf(wgt, tv.x, acc[j].x);
+                acc[j].y = fmaf(wgt, tv.y, acc[j].y);
+                acc[j].z = fmaf(wgt, tv.z, acc[j].z);
+                acc[j].w = fmaf(wgt, tv.w, acc[j].w);
+            }
         }
     }
-    st4(static_cast<T *>(a.out) + p * a.out_cs + q * 4, acc);
+    T *o = static_cast<T *>(a.out) + p * a.out_cs + g * (4 * Q);
+#pragma unroll
+    for (int j = 0; j < Q; ++j) st4(o + 4 * j, acc[j]);
 }
 
 template <typename T>
 cudaError_t launch_warp(const WarpArgs &a, cudaStream_t st) {
-    const size_t total = (size_t)a.n * a.h * a.w * (a.c / 4);
-    return launch_pdl(warp_kernel<T>, dim3((unsigned)((total + 255) / 256)), dim3(256), 0, st, a);
+    // Q quads of channels per thread (2 where c / 4 is even), so the flow sample and its
+    // taps are computed once for 4Q channels (Q = 4: 40 registers, fewer warps; slower)
+    const int nq = a.c / 4, q = nq % 2 == 0 ? 2 : 1, ng = nq / q;
+    if (ng > 64 || (size_t)a.w * ng >= (1u << 21)) return cudaErrorInvalidValue;
+    const uint32_t magic = ng > 1 ? (uint32_t)((0x100000000ull + (unsigned)ng - 1) / (unsigned)ng) : 0u;
+    const dim3 grid((unsigned)((a.w * ng + 255) / 256), (unsigned)a.h, (unsigned)a.n);
+    if (q == 2) return launch_pdl(warp_kernel<T, 2>, grid, dim3(256), 0, st, a, ng, magic);
+    return launch_pdl(warp_kernel<T, 1>, grid, dim3(256), 0, st, a, ng, magic);
 }
 
 // =====================================================================================
