@@ -93,16 +93,38 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, const TcLaunch &p, 
         const int row = warp * 32 + lane;
         const int x = x0 + row;
         const size_t pix = (size_t)(img * p.ho + y) * p.wo + x;
+        const bool vec_params = ((reinterpret_cast<uintptr_t>(p.bias) |
+                                  (F8 ? reinterpret_cast<uintptr_t>(p.wscale) : 0)) & 15) == 0;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 16) {
             uint32_t r[16];
             tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
             if (x < p.wo) {
+                // bias (and e4m3 weight scales) of the 16 columns: four 16-byte loads where
+                // the arrays allow it, else 16 scalar ones
+                float bv[16], sv[16];
+                if (vec_params) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 b4 = __ldg(reinterpret_cast<const float4 *>(p.bias + c0) + q);
+                        bv[4 * q] = b4.x; bv[4 * q + 1] = b4.y; bv[4 * q + 2] = b4.z; bv[4 * q + 3] = b4.w;
+                        if (F8) {
+                            const float4 s4 = __ldg(reinterpret_cast<const float4 *>(p.wscale + c0) + q);
+                            sv[4 * q] = s4.x; sv[4 * q + 1] = s4.y; sv[4 * q + 2] = s4.z; sv[4 * q + 3] = s4.w;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        bv[j] = __ldg(p.bias + c0 + j);
+                        if (F8) sv[j] = __ldg(p.wscale + c0 + j);
+                    }
+                }
                 float v[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const float a = __uint_as_float(r[j]);
-                    v[j] = (F8 ? a * __ldg(p.wscale + c0 + j) : a) + __ldg(p.bias + c0 + j);
+                    v[j] = (F8 ? a * sv[j] : a) + bv[j];
                     if (p.leaky) v[j] = v[j] >= 0.f ? v[j] : 0.1f * v[j];
                 }
                 if (!F8 && p.out_f32) {
