@@ -41,7 +41,9 @@ struct Geo {
     // epilogue: every thread stages the WROWS halo rows its warp reads (2 pixel rows + 2R)
     static constexpr int WROWS = 2 + 2 * R, WCOLS = WROWS * HX;         // 240 for R = 4
     static constexpr int WLOAD = (WCOLS + 15) / 16 * 16;                // tcgen05.ld x16 granularity
-    static constexpr int SSTRIDE = WLOAD + 1;                            // odd: no bank conflicts
+    // slice pitch: a whole number of 16-byte units, odd, so the 16-byte stores of 8
+    // consecutive threads hit distinct banks
+    static constexpr int SSTRIDE = (WLOAD / 4) % 2 ? WLOAD : WLOAD + 4;
     static constexpr size_t OPERANDS = (size_t)MAX_NCH * (A_BYTES + B_BYTES);
     static constexpr size_t SLICES = (size_t)128 * SSTRIDE * 4;
     static constexpr size_t SMEM = (OPERANDS > SLICES ? OPERANDS : SLICES) + 1024 + 256;
@@ -152,12 +154,24 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
         const int y = y0 + py, x = x0 + px;
         const bool valid = y < p.h && x < p.w;
         const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(2 * warp * G::HX);
+        // up to four 16-column loads in flight per wait; 16-byte shared stores
 #pragma unroll
-        for (int c0 = 0; c0 < G::WLOAD; c0 += 16) {
-            uint32_t r[16];
-            tmem_ld16(ta + (uint32_t)c0, r);
+        for (int c0 = 0; c0 < G::WLOAD; c0 += 64) {
+            constexpr int MAXK = 4;
+            uint32_t r[16 * MAXK];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) slice[c0 + i] = __uint_as_float(r[i]);
+            for (int k = 0; k < MAXK; ++k)
+                if (c0 + 16 * k < G::WLOAD) tmem_ld16_nowait(ta + (uint32_t)(c0 + 16 * k), r + 16 * k);
+            tmem_wait_ld();
+#pragma unroll
+            for (int k = 0; k < MAXK; ++k)
+                if (c0 + 16 * k < G::WLOAD) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        *reinterpret_cast<float4 *>(slice + c0 + 16 * k + 4 * q) =
+                            make_float4(__uint_as_float(r[16 * k + 4 * q]), __uint_as_float(r[16 * k + 4 * q + 1]),
+                                        __uint_as_float(r[16 * k + 4 * q + 2]), __uint_as_float(r[16 * k + 4 * q + 3]));
+                }
         }
         const int base = (py & 1) * G::HX + px;
         float res[G::ND];
