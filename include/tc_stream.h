@@ -178,6 +178,22 @@ TC_API tc_status tc_process_frame_host(tc_stream *s, const float *I_t, const flo
 TC_API tc_status tc_process_frame_host_async(tc_stream *s, const float *I_t, const float *P_t, float *O_t,
                                              float *wc_opt, uint8_t *mask_opt);
 
+/* Pipelined mode (enable != 0) for sequences whose frames are all resident before they are
+ * given: tc_process_frame then enqueues frame t on two library-owned streams without
+ * ordering it on the caller's stream, so frame t + 1's feature pyramid runs while frame t's
+ * flows are estimated (the stream keeps three pyramids instead of two).  The inputs must be
+ * valid when tc_process_frame is called and stay unmodified until the frame is done; the
+ * outputs are valid after tc_join (the caller's stream then waits for every frame given)
+ * or tc_synchronize.  tc_get_flows joins first; tc_flush runs after the frames given.  The
+ * host entry points and amax recording are not available in this mode.  Only before the
+ * first frame of a sequence; results equal those of the default mode bit for bit.
+ * Errors: TC_ERR_STATE (after the first frame of a sequence, or while recording amax). */
+TC_API tc_status tc_set_pipelined(tc_stream *s, int enable);
+
+/* Pipelined mode: makes the caller's stream wait for every frame given so far (no-op
+ * otherwise). */
+TC_API tc_status tc_join(tc_stream *s);
+
 /* One frame of latency (Sec. 1, Sec. 3.1: the local term of Eq. 2 also warps the next
  * frame).  frames = 1: each tc_process_frame call with frame t+1 returns frame t, with w_n
  * of Eq. 3 (clamped to k2) and the next frame in L_t (Eq. 2) and A^I_t (Eq. 6); the flows
@@ -201,7 +217,8 @@ TC_API long long tc_last_output_frame(const tc_stream *s);
 
 /* CUDA graphs (on by default): from the third frame on, a stream replays one captured graph
  * per slot parity -- every launch of the frame in one cudaGraphLaunch -- after updating the
- * two kernel nodes that read the caller's buffers.  enable = 0 returns to one launch per
+ * two kernel nodes that read the caller's buffers (in pipelined mode: two graphs per frame,
+ * the pyramid's and the rest's).  enable = 0 returns to one launch per
  * kernel.  Waits for the stream.  Per-stage profiling always runs without graphs. */
 TC_API tc_status tc_set_graphs(tc_stream *s, int enable);
 

@@ -34,7 +34,7 @@ EXPORTED = ["tc_default_consistency", "tc_create_stream", "tc_set_consistency", 
             "tc_tensor_core_correlation_levels", "tc_set_graphs", "tc_activation_segments",
             "tc_set_amax_recording", "tc_get_amax", "tc_set_fp8_scales", "tc_op_poisson_solve", "tc_set_latency",
             "tc_flush", "tc_last_output_frame", "tc_op_consistency_next", "tc_op_downscale2", "tc_op_sepconv",
-            "tc_process_frame_host_async"]
+            "tc_process_frame_host_async", "tc_set_pipelined", "tc_join"]
 E4M3_MAX = 448.0
 NOALLOC_SCRATCH_BYTES = 16 << 20
 PROFILE_CATEGORIES = ["pyramid_conv", "estimator_conv", "head", "correlation", "warp", "upsample", "consistency",
@@ -62,6 +62,8 @@ _lib.tc_set_consistency.argtypes = [_vp, ctypes.POINTER(TcConsistency)]
 _lib.tc_process_frame.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
 _lib.tc_process_frame_host.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
 _lib.tc_process_frame_host_async.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+_lib.tc_set_pipelined.argtypes = [_vp, _i]
+_lib.tc_join.argtypes = [_vp]
 _lib.tc_get_flows.argtypes = [_vp, _vp, _vp]
 _lib.tc_destroy.argtypes = [_vp]
 _lib.tc_last_error.argtypes = [_vp]
@@ -94,7 +96,7 @@ _lib.tc_last_output_frame.argtypes = [_vp]
 _lib.tc_last_output_frame.restype = ctypes.c_longlong
 _lib.tc_op_consistency_next.argtypes = [_vp] * 11 + [_i] * 5 + [ctypes.POINTER(TcConsistency), _vp, _vp, _vp, _vp]
 for _n in ["tc_set_amax_recording", "tc_get_amax", "tc_set_fp8_scales", "tc_set_graphs", "tc_op_correlation_bf16_noalloc", "tc_synchronize", "tc_set_profiling", "tc_get_profile", "tc_create_stream", "tc_set_consistency", "tc_process_frame", "tc_process_frame_host", "tc_get_flows",
-           "tc_process_frame_host_async", "tc_destroy", "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
+           "tc_process_frame_host_async", "tc_set_pipelined", "tc_join", "tc_destroy", "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
            "tc_op_consistency", "tc_set_latency", "tc_flush", "tc_op_consistency_next", "tc_op_downscale2",
            "tc_op_sepconv"]:
     getattr(_lib, _n).restype = ctypes.c_int
@@ -212,6 +214,17 @@ class Stream:
         _check(_lib.tc_process_frame_host_async(self._h, _hbuf(I, np.float32), _hbuf(P, np.float32),
                                                 _hbuf(O, np.float32), _hbuf(wc, np.float32),
                                                 _hbuf(mask, np.uint8)), self._h)
+
+    def set_pipelined(self, enable: bool):
+        """Pipelined mode: frames are enqueued on the library's own streams with frame t + 1's
+        pyramid overlapping frame t's flow estimation; inputs must be valid at the call and
+        stay unmodified, outputs are valid after join() or synchronize().  Only before the
+        first frame of a sequence."""
+        _check(_lib.tc_set_pipelined(self._h, int(bool(enable))), self._h)
+
+    def join(self):
+        """Pipelined mode: the caller's CUDA stream waits for every frame given so far."""
+        _check(_lib.tc_join(self._h), self._h)
 
     def set_latency(self, frames: int):
         """1: each process_frame with frame t+1 returns frame t blended with both neighbours

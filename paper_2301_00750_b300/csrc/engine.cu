@@ -147,6 +147,15 @@ static std::vector<int> iota_perm(int n, int pad_to) {
 
 static inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
+// Feature pyramids kept per stream: frame t's lives in slot t % 2 (t % NPYR in pipelined
+// mode), and the flow estimation of frame t reads the slots of t and t - 1.  With three
+// slots, frame t + 1's pyramid never overwrites one that frame t's flow estimation reads, so
+// the two can run at the same time.
+constexpr int NPYR = 3;
+// A pipelined frame's launches depend on t through the state parity (t % 2) and the pyramid
+// slots (t % 3): one captured graph of the flow estimation and blend per t % NGRAPH.
+constexpr int NGRAPH = 6;
+
 size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precision prec, int fs) {
     const int L = net.levels, D = (2 * net.radius + 1) * (2 * net.radius + 1), m = 1 << L;
     const bool f8 = prec == TC_FP8_E4M3;
@@ -165,7 +174,7 @@ size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precisi
     for (int l = 1; l <= L; ++l) {
         const size_t h = Hp >> l, w = Wp >> l, px = h * w;
         const int c = net.chans[l - 1];
-        total += al(2 * px * c * es) + 2 * al(px * c * es);
+        total += al(NPYR * px * c * es) + 2 * al(px * c * es);
         total += al((size_t)9 * prev * c * 4) + al((size_t)c * 4) + 2 * (al((size_t)9 * c * c * 4) + al((size_t)c * 4));
         if (l > 1) total += tcw(prev, c);
         total += 2 * tcw(c, c);
@@ -291,9 +300,9 @@ struct tc_stream {
     std::vector<int> ev_cat;       // category of pending pair k (events 2k, 2k+1)
     double prof_ms[TC_PROF_CATEGORIES] = {0};
     long long prof_n[TC_PROF_CATEGORIES] = {0};
-    // CUDA graphs of a whole frame, one per slot parity (the pointers of every launch depend
-    // only on the parity, except the caller's buffers read by the first pyramid conv and the
-    // consistency pass, whose nodes are updated before each replay).
+    // CUDA graphs of a whole frame, one per t % NGRAPH (the pointers of every launch depend
+    // only on the state parity and the pyramid slots, except the caller's buffers read by the
+    // first pyramid conv and the consistency pass, whose nodes are updated before each replay).
     bool graphs = true;
     cudaStream_t gst = nullptr;               // library stream the graphs are captured on and replayed on
     // tc_process_frame_host uploads P_t on cst while the flow network runs and records ev_p
@@ -318,7 +327,15 @@ struct tc_stream {
         cudaGraphNode_t n_first = nullptr, n_cons = nullptr, n_copy = nullptr, n_in = nullptr;
         cudaKernelNodeParams p_first{}, p_cons{}, p_copy{}, p_in{};
         int launches = 0;
-    } fg[2][2];  // [host entry point][slot parity]: only host calls' graphs wait for the P_t upload
+    } fg[2][2];  // [host entry point][t % 2]: only host calls' graphs wait for the P_t upload
+    // pipelined mode (tc_set_pipelined): the pyramid of frame t runs on pst, the rest of the
+    // frame on gst; pyramid t waits for the rest of frame t - 2 (ev_rest), the rest of frame
+    // t for pyramid t (ev_pyr); one graph per pyramid slot and one per t % NGRAPH
+    bool pipelined = false;
+    int last_rest = -1;  // ev_rest slot of the last frame given
+    cudaStream_t pst = nullptr;
+    cudaEvent_t ev_pyr[NPYR] = {}, ev_rest[NPYR] = {};
+    FrameGraph pg_pyr[NPYR], pg_rest[NGRAPH];
     // screened-Poisson solver (allocated when first enabled): A_t, w_c, right-hand side and
     // four iterate planes, each (3, H, W) float (w_c (H, W))
     float *sv_A = nullptr, *sv_wc = nullptr, *sv_b = nullptr, *sv_c0 = nullptr,
@@ -578,7 +595,7 @@ static tc_status build_stream(tc_stream *s) {
         B.w = s->Wp >> l;
         B.c = net.chans[l - 1];
         const size_t px = (size_t)B.h * B.w;
-        if ((r = dalloc(s, &B.pyr, 2 * px * B.c * es)) != TC_OK) return r;
+        if ((r = dalloc(s, &B.pyr, NPYR * px * B.c * es)) != TC_OK) return r;
         if ((r = dalloc(s, &B.tmpA, px * B.c * es)) != TC_OK) return r;
         if ((r = dalloc(s, &B.tmpB, px * B.c * es)) != TC_OK) return r;
         for (int j = 0; j < 3; ++j) {
@@ -603,12 +620,12 @@ static tc_status build_stream(tc_stream *s) {
                 s->first_b = HL.b;
                 continue;
             }
-            // Same arguments as run_pyramid builds; the first conv of a level reads both
-            // slots of the previous level's pyramid buffer.
+            // Same arguments as run_pyramid builds; the first conv of a level reads any
+            // slot of the previous level's pyramid buffer.
             if (j == 0) {
                 LevelBufs &P = s->lv[l - 2];
                 ConvArgs a{P.pyr, P.c, 1, P.h, P.w, P.c, 2, B.h, B.w, nullptr, nullptr, B.c, B.tmpA, B.c, 1};
-                add_layer(s, s->pyr_plan[l - 1][0], a, 2, wk, std::vector<int>(P.c, seg_pyr(s, l - 1, 2)), false);
+                add_layer(s, s->pyr_plan[l - 1][0], a, NPYR, wk, std::vector<int>(P.c, seg_pyr(s, l - 1, 2)), false);
             } else {
                 ConvArgs a{j == 1 ? B.tmpA : B.tmpB, B.c, 1, B.h, B.w, B.c, 1, B.h, B.w, nullptr, nullptr, B.c,
                            B.tmpB, B.c, 1};
@@ -663,7 +680,8 @@ static tc_status build_stream(tc_stream *s) {
             std::string why;
             // level L correlates the two pyramid slots; finer levels correlate with f2w
             const void *other = l == L ? B.pyr : B.f2w;
-            if (tc_plan_corr(B.corrplan, B.pyr, 2, B.c, other, 2, B.c, B.h, B.w, B.c, s->R, s->dev_err, why))
+            if (tc_plan_corr(B.corrplan, B.pyr, NPYR, B.c, other, l == L ? NPYR : 2, B.c, B.h, B.w, B.c, s->R,
+                             s->dev_err, why))
                 s->tc_corr_levels += 1;
         }
         {
@@ -818,6 +836,9 @@ static ConvFirstArgs first_args(const tc_stream *s, const float *img) {
     return f;
 }
 
+// The pyramid slot of frame t (see NPYR).
+static inline int pyr_slot(const tc_stream *s, long long t) { return (int)(t % (s->pipelined ? NPYR : 2)); }
+
 template <typename T>
 static tc_status run_pyramid(tc_stream *s, const float *img, int slot) {
     tc_status r;
@@ -898,14 +919,14 @@ static tc_status run_refine(tc_stream *s) {
 // Both directions at once (batch entry 0: self = frame t, other = t-1, giving F_{t->t-1};
 // entry 1: self = t-1, other = t, giving F_{t-1->t}).
 template <typename T>
-static tc_status run_estimators(tc_stream *s, int slot_cur) {
+static tc_status run_estimators(tc_stream *s, int pcur, int pprev) {
     tc_status r;
     const HostNet &net = s->net;
     for (int l = s->L; l >= 2; --l) {
         LevelBufs &B = s->lv[l - 1];
         const size_t px = (size_t)B.h * B.w;
         const T *pyr = static_cast<const T *>(B.pyr);
-        const T *self_p[2] = {pyr + (size_t)slot_cur * px * B.c, pyr + (size_t)(slot_cur ^ 1) * px * B.c};
+        const T *self_p[2] = {pyr + (size_t)pcur * px * B.c, pyr + (size_t)pprev * px * B.c};
         const T *other_p[2] = {self_p[1], self_p[0]};
         T *dec = static_cast<T *>(B.dec);
         const void *fo[2] = {other_p[0], other_p[1]};
@@ -921,8 +942,8 @@ static tc_status run_estimators(tc_stream *s, int slot_cur) {
             fo[1] = static_cast<T *>(B.f2w) + px * B.c;
         }
         if (B.corrplan.enabled) {
-            const int img_s[2] = {slot_cur, slot_cur ^ 1};
-            const int img_o[2] = {l < s->L ? 0 : slot_cur ^ 1, l < s->L ? 1 : slot_cur};
+            const int img_s[2] = {pcur, pprev};
+            const int img_o[2] = {l < s->L ? 0 : pprev, l < s->L ? 1 : pcur};
             const void *fs[2] = {self_p[0], self_p[1]};
             TC_LAUNCH_CAT(s, TC_PROF_CORRELATION,
                           launch_corr_tc(B.corrplan, 2, img_s, img_o, dec + B.c, B.ctot, fs, dec, s->st, B.s_pyr[2],
@@ -1034,22 +1055,14 @@ static tc_status solver_launches(tc_stream *s, const float *P, float *O, float *
     return TC_OK;
 }
 
-// Every launch of one frame, in order.
+// The launches of a frame after its pyramid: flow estimation (from the second frame on),
+// the blend, and the solver or the state copies.  upload: P_t arrives by the host entry
+// point's upload (waited for before the first read of P_t).
 template <typename T>
-static tc_status frame_launches(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask,
-                                int cur) {
+static tc_status rest_launches(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask,
+                               int cur, bool upload) {
     tc_status r;
-    const bool upload = s->p_pending;  // P_t is being uploaded on cst (host entry point)
-    if (upload && s->capturing) {
-        // the wait for P_t (an external event node) on a branch forked at the frame's start
-        // and joined before the pass that reads P_t, off the chain of kernels
-        TC_TRY(s, cudaEventRecord(s->ev_fork, s->st), "cudaEventRecord");
-        TC_TRY(s, cudaStreamWaitEvent(s->cst, s->ev_fork, 0), "cudaStreamWaitEvent");
-        TC_TRY(s, cudaStreamWaitEvent(s->cst, s->ev_p, cudaEventWaitExternal), "cudaStreamWaitEvent");
-        TC_TRY(s, cudaEventRecord(s->ev_join, s->cst), "cudaEventRecord");
-    }
-    if ((r = run_pyramid<T>(s, I, cur)) != TC_OK) return r;
-    if (s->t > 0 && (r = run_estimators<T>(s, cur)) != TC_OK) return r;
+    if (s->t > 0 && (r = run_estimators<T>(s, pyr_slot(s, s->t), pyr_slot(s, s->t - 1))) != TC_OK) return r;
     // everything from here on may read P_t
     if (upload) TC_TRY(s, cudaStreamWaitEvent(s->st, s->capturing ? s->ev_join : s->ev_p, 0), "cudaStreamWaitEvent");
     if (!s->latency) {
@@ -1078,23 +1091,42 @@ static tc_status frame_launches(tc_stream *s, const float *I, const float *P, fl
     return TC_OK;
 }
 
-// Captures the frame's launches for slot parity `cur` into a graph and finds the two nodes
-// whose arguments change from frame to frame.
+// Every launch of one frame, in order.
 template <typename T>
-static tc_status capture_frame(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask,
-                               int cur) {
-    tc_stream::FrameGraph &G = s->fg[s->p_pending ? 1 : 0][cur];
-    // Capture on the library's own stream (capture is not allowed on the legacy default
-    // stream a caller may pass); the launch helpers use s->st, so point it there meanwhile.
+static tc_status frame_launches(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask,
+                                int cur) {
+    tc_status r;
+    const bool upload = s->p_pending;  // P_t is being uploaded on cst (host entry point)
+    if (upload && s->capturing) {
+        // the wait for P_t (an external event node) on a branch forked at the frame's start
+        // and joined before the pass that reads P_t, off the chain of kernels
+        TC_TRY(s, cudaEventRecord(s->ev_fork, s->st), "cudaEventRecord");
+        TC_TRY(s, cudaStreamWaitEvent(s->cst, s->ev_fork, 0), "cudaStreamWaitEvent");
+        TC_TRY(s, cudaStreamWaitEvent(s->cst, s->ev_p, cudaEventWaitExternal), "cudaStreamWaitEvent");
+        TC_TRY(s, cudaEventRecord(s->ev_join, s->cst), "cudaEventRecord");
+    }
+    if ((r = run_pyramid<T>(s, I, pyr_slot(s, s->t))) != TC_OK) return r;
+    return rest_launches<T>(s, I, P, O, wc, mask, cur, upload);
+}
+
+// Captures the launches made by `launches` on stream cs into graph G and finds the kernel
+// nodes whose arguments change from frame to frame: the first pyramid conv (or the 2x2
+// downscale) when need_first, the consistency pass and the copies when need_rest.
+template <typename T, typename F>
+static tc_status capture_into(tc_stream *s, cudaStream_t cs, tc_stream::FrameGraph &G, F &&launches, bool need_first,
+                              bool need_rest) {
+    // Capture on a library-owned stream (capture is not allowed on the legacy default stream
+    // a caller may pass); the launch helpers use s->st, so point it there meanwhile.
     cudaStream_t caller = s->st;
-    TC_TRY(s, cudaStreamBeginCapture(s->gst, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
-    s->st = s->gst;
+    const int launches0 = s->launches;
+    TC_TRY(s, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    s->st = cs;
     s->capturing = true;
-    const tc_status r = frame_launches<T>(s, I, P, O, wc, mask, cur);
+    const tc_status r = launches();
     s->capturing = false;
     s->st = caller;
     cudaGraph_t g = nullptr;
-    const cudaError_t e = cudaStreamEndCapture(s->gst, &g);
+    const cudaError_t e = cudaStreamEndCapture(cs, &g);
     if (r != TC_OK) {
         if (g) cudaGraphDestroy(g);
         return r;
@@ -1116,7 +1148,8 @@ static tc_status capture_frame(tc_stream *s, const float *I, const float *P, flo
         if (kp.func == copy_out_kernel_fn(0)) { G.n_copy = node; G.p_copy = kp; }
         if (kp.func == copy_out_kernel_fn(1)) { G.n_in = node; G.p_in = kp; }
     }
-    if (!G.n_first || !G.n_cons || (s->params.solver_iters > 0 && !G.n_copy) || (s->latency && !G.n_in)) {
+    if ((need_first && !G.n_first) ||
+        (need_rest && (!G.n_cons || (s->params.solver_iters > 0 && !G.n_copy) || (s->latency && !G.n_in)))) {
         cudaGraphDestroy(g);
         return fail(s, TC_ERR_STATE, "frame graph: per-frame kernel nodes not found");
     }
@@ -1128,7 +1161,58 @@ static tc_status capture_frame(tc_stream *s, const float *I, const float *P, flo
     }
     G.g = g;
     G.exec = ex;
-    G.launches = s->launches;
+    G.launches = s->launches - launches0;
+    return TC_OK;
+}
+
+// Points the graph's node that reads the caller's I_t (the first pyramid conv, or the 2x2
+// downscale) at this frame's I_t.
+template <typename T>
+static tc_status update_first_node(tc_stream *s, tc_stream::FrameGraph &G, const float *I) {
+    ConvFirstArgs f = first_args(s, I);
+    int c3 = 3, hh = s->H, ww = s->W;
+    float *xs = s->xs;
+    void *fa[1] = {&f};
+    void *da[5] = {&I, &c3, &hh, &ww, &xs};
+    cudaKernelNodeParams pf = G.p_first;
+    pf.kernelParams = s->fs == 2 ? da : fa;
+    pf.extra = nullptr;
+    TC_TRY(s, cudaGraphExecKernelNodeSetParams(G.exec, G.n_first, &pf), "graph node update");
+    return TC_OK;
+}
+
+// Points the consistency pass and the copies of the graph at this frame's buffers and
+// consistency controls.
+static tc_status update_rest_nodes(tc_stream *s, tc_stream::FrameGraph &G, const float *I, const float *P, float *O,
+                                   float *wc, uint8_t *mask, int cur) {
+    ConsistArgs ca = consist_args(s, I, P, O, wc, mask, cur);
+    void *cargs[1] = {&ca};
+    cudaKernelNodeParams pc = G.p_cons;
+    pc.kernelParams = cargs;
+    pc.extra = nullptr;
+    TC_TRY(s, cudaGraphExecKernelNodeSetParams(G.exec, G.n_cons, &pc), "graph node update");
+    if (G.n_copy) {
+        // the solver's output copy: retarget it to this frame's O_t and w_c
+        const size_t hw = (size_t)s->H * s->W;
+        const float *src = s->sO[cur], *wsrc = s->sv_wc;
+        size_t n3 = 3 * hw, n1 = hw;
+        void *ka[6] = {&src, &O, &n3, &wsrc, &wc, &n1};
+        cudaKernelNodeParams pk = G.p_copy;
+        pk.kernelParams = ka;
+        pk.extra = nullptr;
+        TC_TRY(s, cudaGraphExecKernelNodeSetParams(G.exec, G.n_copy, &pk), "graph node update");
+    }
+    if (G.n_in) {
+        // the copy of this frame's inputs into the state (one frame of latency)
+        const size_t img = (size_t)3 * s->H * s->W;
+        float *dI = s->sI[cur], *dP = s->sP[cur];
+        size_t n3 = img;
+        void *ka[6] = {&I, &dI, &n3, &P, &dP, &n3};
+        cudaKernelNodeParams pk = G.p_in;
+        pk.kernelParams = ka;
+        pk.extra = nullptr;
+        TC_TRY(s, cudaGraphExecKernelNodeSetParams(G.exec, G.n_in, &pk), "graph node update");
+    }
     return TC_OK;
 }
 
@@ -1143,7 +1227,7 @@ static tc_status record_amax(tc_stream *s, int cur) {
         for (int l = 1; l <= s->L; ++l) {
             LevelBufs &B = s->lv[l - 1];
             const size_t px = (size_t)B.h * B.w;
-            const T *pyr = static_cast<const T *>(B.pyr) + (size_t)cur * px * B.c;
+            const T *pyr = static_cast<const T *>(B.pyr) + (size_t)pyr_slot(s, s->t) * px * B.c;
             TC_LAUNCH(s, launch_amax<T>(static_cast<const T *>(B.tmpA), px, B.c, B.c, s->amax_dev + seg_pyr(s, l, 0), s->st));
             TC_LAUNCH(s, launch_amax<T>(static_cast<const T *>(B.tmpB), px, B.c, B.c, s->amax_dev + seg_pyr(s, l, 1), s->st));
             TC_LAUNCH(s, launch_amax<T>(pyr, px, B.c, B.c, s->amax_dev + seg_pyr(s, l, 2), s->st));
@@ -1159,13 +1243,17 @@ static tc_status record_amax(tc_stream *s, int cur) {
 }
 
 template <typename T>
+static tc_status process_pipelined(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask);
+
+template <typename T>
 static tc_status process(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask) {
     tc_status r;
     s->launches = 0;
     if (s->ev_cat.size() > 4096 && (r = prof_flush(s)) != TC_OK) return r;
+    if (s->pipelined) return process_pipelined<T>(s, I, P, O, wc, mask);
     const int cur = (int)(s->t & 1);
     // The first two frames run eagerly (the first has no flow; the second sets every kernel
-    // attribute); later frames replay the graph of their parity.  Profiling runs eagerly.
+    // attribute); later frames replay the graph of their t % NGRAPH.  Profiling runs eagerly.
     const long long out = s->latency ? s->t - 1 : s->t;
     if (!s->graphs || s->prof || s->t < 2 || s->rec_amax) {
         if ((r = frame_launches<T>(s, I, P, O, wc, mask, cur)) != TC_OK) return r;
@@ -1181,45 +1269,11 @@ static tc_status process(tc_stream *s, const float *I, const float *P, float *O,
         TC_TRY(s, cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming), "cudaEventCreate");
     }
     if (!G.exec) {
-        if ((r = capture_frame<T>(s, I, P, O, wc, mask, cur)) != TC_OK) return r;
+        r = capture_into<T>(s, s->gst, G, [&] { return frame_launches<T>(s, I, P, O, wc, mask, cur); }, true, true);
+        if (r != TC_OK) return r;
     } else {
-        ConvFirstArgs f = first_args(s, I);
-        ConsistArgs ca = consist_args(s, I, P, O, wc, mask, cur);
-        // the node that reads the caller's I_t: the first pyramid conv, or the 2x2 downscale
-        int c3 = 3, hh = s->H, ww = s->W;
-        float *xs = s->xs;
-        void *fa[1] = {&f};
-        void *da[5] = {&I, &c3, &hh, &ww, &xs};
-        void *cargs[1] = {&ca};
-        cudaKernelNodeParams pf = G.p_first, pc = G.p_cons;
-        pf.kernelParams = s->fs == 2 ? da : fa;
-        pf.extra = nullptr;
-        pc.kernelParams = cargs;
-        pc.extra = nullptr;
-        TC_TRY(s, cudaGraphExecKernelNodeSetParams(G.exec, G.n_first, &pf), "graph node update");
-        TC_TRY(s, cudaGraphExecKernelNodeSetParams(G.exec, G.n_cons, &pc), "graph node update");
-        if (G.n_copy) {
-            // the solver's output copy: retarget it to this frame's O_t and w_c
-            const size_t hw = (size_t)s->H * s->W;
-            const float *src = s->sO[cur], *wsrc = s->sv_wc;
-            size_t n3 = 3 * hw, n1 = hw;
-            void *ka[6] = {&src, &O, &n3, &wsrc, &wc, &n1};
-            cudaKernelNodeParams pk = G.p_copy;
-            pk.kernelParams = ka;
-            pk.extra = nullptr;
-            TC_TRY(s, cudaGraphExecKernelNodeSetParams(G.exec, G.n_copy, &pk), "graph node update");
-        }
-        if (G.n_in) {
-            // the copy of this frame's inputs into the state (one frame of latency)
-            const size_t img = (size_t)3 * s->H * s->W;
-            float *dI = s->sI[cur], *dP = s->sP[cur];
-            size_t n3 = img;
-            void *ka[6] = {&I, &dI, &n3, &P, &dP, &n3};
-            cudaKernelNodeParams pk = G.p_in;
-            pk.kernelParams = ka;
-            pk.extra = nullptr;
-            TC_TRY(s, cudaGraphExecKernelNodeSetParams(G.exec, G.n_in, &pk), "graph node update");
-        }
+        if ((r = update_first_node<T>(s, G, I)) != TC_OK) return r;
+        if ((r = update_rest_nodes(s, G, I, P, O, wc, mask, cur)) != TC_OK) return r;
     }
     // caller's stream -> library stream -> caller's stream
     TC_TRY(s, cudaEventRecord(s->ev_in, s->st), "cudaEventRecord");
@@ -1233,16 +1287,108 @@ static tc_status process(tc_stream *s, const float *I, const float *P, float *O,
     return TC_OK;
 }
 
+// Pipelined mode: frame t's pyramid runs on pst, the rest of the frame on gst, with no
+// ordering on the caller's stream (the inputs are valid when the call is made; tc_join or
+// tc_synchronize make the results visible).  Pyramid t writes the slot that the rest of
+// frame t - 2 read last and waits for it; the rest of frame t waits for pyramid t and
+// follows the rest of frame t - 1 on gst.  So pyramid t + 1 runs while the flows of frame t
+// are estimated.
+template <typename T>
+static tc_status process_pipelined(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask) {
+    tc_status r;
+    const int cur = (int)(s->t & 1), ps = pyr_slot(s, s->t), k = (int)(s->t % NPYR);
+    const long long out = s->latency ? s->t - 1 : s->t;
+    if (!s->gst) {
+        TC_TRY(s, cudaStreamCreateWithFlags(&s->gst, cudaStreamNonBlocking), "cudaStreamCreate");
+        TC_TRY(s, cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming), "cudaEventCreate");
+        TC_TRY(s, cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming), "cudaEventCreate");
+    }
+    if (!s->pst) {
+        TC_TRY(s, cudaStreamCreateWithFlags(&s->pst, cudaStreamNonBlocking), "cudaStreamCreate");
+        for (int j = 0; j < NPYR; ++j) {
+            TC_TRY(s, cudaEventCreateWithFlags(&s->ev_pyr[j], cudaEventDisableTiming), "cudaEventCreate");
+            TC_TRY(s, cudaEventCreateWithFlags(&s->ev_rest[j], cudaEventDisableTiming), "cudaEventCreate");
+        }
+    }
+    // the slot pyramid t writes was last read by the rest of frame t - 2 (at the start of a
+    // sequence: by any earlier frame)
+    if (s->t == 0) {
+        for (int j = 0; j < NPYR; ++j) TC_TRY(s, cudaStreamWaitEvent(s->pst, s->ev_rest[j], 0), "cudaStreamWaitEvent");
+    } else {
+        TC_TRY(s, cudaStreamWaitEvent(s->pst, s->ev_rest[(s->t + 1) % NPYR], 0), "cudaStreamWaitEvent");
+    }
+    cudaStream_t caller = s->st;
+    if (!s->graphs || s->prof || s->t < 2) {
+        s->st = s->pst;
+        r = run_pyramid<T>(s, I, ps);
+        s->st = caller;
+        if (r != TC_OK) return r;
+        TC_TRY(s, cudaEventRecord(s->ev_pyr[ps], s->pst), "cudaEventRecord");
+        TC_TRY(s, cudaStreamWaitEvent(s->gst, s->ev_pyr[ps], 0), "cudaStreamWaitEvent");
+        s->st = s->gst;
+        r = rest_launches<T>(s, I, P, O, wc, mask, cur, false);
+        s->st = caller;
+        if (r != TC_OK) return r;
+    } else {
+        tc_stream::FrameGraph &Gp = s->pg_pyr[ps], &Gr = s->pg_rest[s->t % NGRAPH];
+        if (!Gp.exec) {
+            r = capture_into<T>(s, s->pst, Gp, [&] { return run_pyramid<T>(s, I, ps); }, true, false);
+            if (r != TC_OK) return r;
+        } else if ((r = update_first_node<T>(s, Gp, I)) != TC_OK) {
+            return r;
+        }
+        if (!Gr.exec) {
+            r = capture_into<T>(s, s->gst, Gr, [&] { return rest_launches<T>(s, I, P, O, wc, mask, cur, false); },
+                                false, true);
+            if (r != TC_OK) return r;
+        } else if ((r = update_rest_nodes(s, Gr, I, P, O, wc, mask, cur)) != TC_OK) {
+            return r;
+        }
+        TC_TRY(s, cudaGraphLaunch(Gp.exec, s->pst), "cudaGraphLaunch");
+        TC_TRY(s, cudaEventRecord(s->ev_pyr[ps], s->pst), "cudaEventRecord");
+        TC_TRY(s, cudaStreamWaitEvent(s->gst, s->ev_pyr[ps], 0), "cudaStreamWaitEvent");
+        TC_TRY(s, cudaGraphLaunch(Gr.exec, s->gst), "cudaGraphLaunch");
+        s->launches = Gp.launches + Gr.launches;
+    }
+    TC_TRY(s, cudaEventRecord(s->ev_rest[k], s->gst), "cudaEventRecord");
+    s->last_rest = k;
+    s->t += 1;
+    s->last_out = out;
+    return TC_OK;
+}
+
+// Pipelined mode: makes the caller's stream wait for every frame given so far.
+static tc_status join_caller(tc_stream *s) {
+    if (s->pipelined && s->last_rest >= 0)
+        TC_TRY(s, cudaStreamWaitEvent(s->st, s->ev_rest[s->last_rest], 0), "cudaStreamWaitEvent");
+    return TC_OK;
+}
+
+static void release_graph(tc_stream::FrameGraph &G) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.g) cudaGraphDestroy(G.g);
+    G = tc_stream::FrameGraph{};
+}
+
 static void release_graphs(tc_stream *s) {
     for (auto &GG : s->fg)
-        for (auto &G : GG) {
-            if (G.exec) cudaGraphExecDestroy(G.exec);
-            if (G.g) cudaGraphDestroy(G.g);
-            G = tc_stream::FrameGraph{};
-        }
+        for (auto &G : GG) release_graph(G);
+    for (auto &G : s->pg_pyr) release_graph(G);
+    for (auto &G : s->pg_rest) release_graph(G);
 }
 
 static void release_graph_stream(tc_stream *s) {
+    if (s->pst) {
+        cudaStreamSynchronize(s->pst);
+        cudaStreamDestroy(s->pst);
+        s->pst = nullptr;
+    }
+    for (int j = 0; j < NPYR; ++j) {
+        if (s->ev_pyr[j]) cudaEventDestroy(s->ev_pyr[j]);
+        if (s->ev_rest[j]) cudaEventDestroy(s->ev_rest[j]);
+        s->ev_pyr[j] = s->ev_rest[j] = nullptr;
+    }
+    s->last_rest = -1;
     if (s->gst) {
         cudaStreamSynchronize(s->gst);
         cudaStreamDestroy(s->gst);
@@ -1258,6 +1404,7 @@ extern "C" int tc_activation_segments(const tc_stream *s) { return s ? n_segment
 extern "C" tc_status tc_set_amax_recording(tc_stream *s, int enable) {
     tc_status r = check_stream(s, "tc_set_amax_recording");
     if (r != TC_OK) return r;
+    if (s->pipelined) return fail(s, TC_ERR_STATE, "tc_set_amax_recording: not available in pipelined mode");
     if (s->prec == TC_FP8_E4M3) return fail(s, TC_ERR_INVALID_ARG, "amax recording needs a TC_FP32 or TC_BF16 stream");
     TC_TRY(s, cudaMemsetAsync(s->amax_dev, 0, sizeof(unsigned) * n_segments(s), s->st), "memset");
     s->rec_amax = enable != 0;
@@ -1324,7 +1471,8 @@ extern "C" tc_status tc_set_fp8_scales(tc_stream *s, const float *scales, int n)
         LevelBufs &B = s->lv[l - 1];
         std::string why;
         const void *other = l == s->L ? B.pyr : B.f2w;
-        if (!tc_plan_corr(B.corrplan, B.pyr, 2, B.c, other, 2, B.c, B.h, B.w, B.c, s->R, s->dev_err, why, true))
+        if (!tc_plan_corr(B.corrplan, B.pyr, NPYR, B.c, other, l == s->L ? NPYR : 2, B.c, B.h, B.w, B.c, s->R,
+                          s->dev_err, why, true))
             return fail(s, TC_ERR_UNSUPPORTED, "e4m3 correlation not eligible for the tensor cores: " + why);
         s->tc_corr_levels += 1;
     }
@@ -1370,6 +1518,8 @@ extern "C" tc_status tc_synchronize(tc_stream *s) {
     tc_status r = check_stream(s, "tc_synchronize");
     if (r != TC_OK) return r;
     TC_TRY(s, cudaStreamSynchronize(s->st), "stream synchronize");
+    if (s->pst) TC_TRY(s, cudaStreamSynchronize(s->pst), "pyramid stream synchronize");
+    if (s->gst) TC_TRY(s, cudaStreamSynchronize(s->gst), "library stream synchronize");
     if (s->cst) TC_TRY(s, cudaStreamSynchronize(s->cst), "upload stream synchronize");
     if (s->dst) TC_TRY(s, cudaStreamSynchronize(s->dst), "download stream synchronize");
     return check_device_error(s);
@@ -1379,6 +1529,7 @@ extern "C" tc_status tc_process_frame_host_async(tc_stream *s, const float *I_t,
                                                  float *wc_opt, uint8_t *mask_opt) {
     tc_status r = check_stream(s, "tc_process_frame_host_async");
     if (r != TC_OK) return r;
+    if (s->pipelined) return fail(s, TC_ERR_STATE, "tc_process_frame_host_async: not available in pipelined mode");
     if (!I_t || !P_t || !O_t) return fail(s, TC_ERR_INVALID_ARG, "tc_process_frame_host_async: NULL image pointer");
     const size_t img = (size_t)3 * s->H * s->W * sizeof(float), plane = (size_t)s->H * s->W;
     if (!s->aI[0]) {
@@ -1426,6 +1577,7 @@ extern "C" tc_status tc_process_frame_host(tc_stream *s, const float *I_t, const
                                            float *wc_opt, uint8_t *mask_opt) {
     tc_status r = check_stream(s, "tc_process_frame_host");
     if (r != TC_OK) return r;
+    if (s->pipelined) return fail(s, TC_ERR_STATE, "tc_process_frame_host: not available in pipelined mode");
     if (!I_t || !P_t || !O_t) return fail(s, TC_ERR_INVALID_ARG, "tc_process_frame_host: NULL image pointer");
     const size_t img = (size_t)3 * s->H * s->W * sizeof(float), plane = (size_t)s->H * s->W;
     if (!s->hI) {
@@ -1485,6 +1637,25 @@ extern "C" tc_status tc_set_latency(tc_stream *s, int frames) {
     return TC_OK;
 }
 
+extern "C" tc_status tc_set_pipelined(tc_stream *s, int enable) {
+    tc_status r = check_stream(s, "tc_set_pipelined");
+    if (r != TC_OK) return r;
+    if (s->t != 0) return fail(s, TC_ERR_STATE, "tc_set_pipelined: only before the first frame of a sequence");
+    if (enable && s->rec_amax) return fail(s, TC_ERR_STATE, "tc_set_pipelined: not while recording amax");
+    if ((enable != 0) != s->pipelined) {
+        if ((r = tc_synchronize(s)) != TC_OK) return r;
+        release_graphs(s);
+        s->pipelined = enable != 0;
+    }
+    return TC_OK;
+}
+
+extern "C" tc_status tc_join(tc_stream *s) {
+    tc_status r = check_stream(s, "tc_join");
+    if (r != TC_OK) return r;
+    return join_caller(s);
+}
+
 extern "C" tc_status tc_flush(tc_stream *s, float *O_t, float *wc_opt, uint8_t *mask_opt) {
     tc_status r = check_stream(s, "tc_flush");
     if (r != TC_OK) return r;
@@ -1493,11 +1664,22 @@ extern "C" tc_status tc_flush(tc_stream *s, float *O_t, float *wc_opt, uint8_t *
     if (!O_t) return fail(s, TC_ERR_INVALID_ARG, "tc_flush: NULL image pointer");
     s->launches = 0;
     const int cur = (int)(s->t & 1);
-    // the last frame has no next frame: the causal blend with the kept flows
+    // the last frame has no next frame: the causal blend with the kept flows (pipelined
+    // mode: on the library stream, after the frames given)
+    cudaStream_t caller = s->st;
+    if (s->pipelined && s->gst) s->st = s->gst;
     const ConsistArgs ca = consist_args(s, nullptr, nullptr, O_t, wc_opt, mask_opt, cur, true);
-    TC_LAUNCH_CAT(s, TC_PROF_CONSISTENCY, launch_consistency(ca, s->st));
-    if (s->t > 1 && s->params.solver_iters > 0 && (r = solver_launches(s, s->sP[cur ^ 1], O_t, wc_opt, cur)) != TC_OK)
-        return r;
+    r = TC_OK;
+    const cudaError_t ce = launch_consistency(ca, s->st);
+    ++s->launches;
+    if (ce != cudaSuccess) r = cuda_fail(s, ce, "tc_flush launch");
+    if (r == TC_OK && s->t > 1 && s->params.solver_iters > 0) r = solver_launches(s, s->sP[cur ^ 1], O_t, wc_opt, cur);
+    if (r == TC_OK && s->pipelined && s->gst && s->last_rest >= 0) {
+        const cudaError_t ee = cudaEventRecord(s->ev_rest[s->last_rest], s->gst);
+        if (ee != cudaSuccess) r = cuda_fail(s, ee, "cudaEventRecord");
+    }
+    s->st = caller;
+    if (r != TC_OK) return r;
     s->last_out = s->t - 1;
     s->t = 0;
     return TC_OK;
@@ -1509,6 +1691,7 @@ extern "C" tc_status tc_get_flows(tc_stream *s, float *Fb, float *Ff) {
     tc_status r = check_stream(s, "tc_get_flows");
     if (r != TC_OK) return r;
     if (s->t < 2) return fail(s, TC_ERR_STATE, "tc_get_flows: no flow before the second frame");
+    if ((r = join_caller(s)) != TC_OK) return r;
     LevelBufs &B2 = s->lv[1];
     if (Fb) TC_LAUNCH(s, launch_flow_out(B2.flow, B2.h, B2.w, 4 * s->fs, s->H, s->W, Fb, s->st));
     if (Ff)

@@ -1,0 +1,105 @@
+"""Pipelined mode (tc_set_pipelined): frame t + 1's feature pyramid runs on a second stream
+while frame t's flows are estimated, with three pyramid slots and the frame split into two
+graphs.  The results must equal the default mode's bit for bit, frame by frame, over enough
+frames that every graph is captured and replayed (t % 6 for the flow estimation and blend,
+t % 3 for the pyramid)."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_common import to_dev, to_np, weights_file
+
+pytestmark = pytest.mark.gpu
+tc = pytest.importorskip("paper_2301_00750_b300")
+
+W, H = 200, 136
+
+
+def _frames(n, seed):
+    seq = synth.Sequence(width=W, height=H, seed=seed, side_range=(16, 34), max_vel=2.0)
+    frames = [seq.frame(t) for t in range(n)]
+    return frames, [seq.stylized(t, f) for t, f in enumerate(frames)]
+
+
+def _run(path, frames, styl, prec, pipelined, latency=0, flow_downscale=0, solver_iters=0):
+    """Every frame's outputs (O, w_c, mask) and, at the end, the last frame's flows."""
+    import torch
+    s = tc.Stream(W, H, prec, weights_path=path, flow_downscale=flow_downscale)
+    k2 = 0.4 if latency else 0.0
+    if latency:
+        s.set_consistency(k1=0.3, k2=k2, solver_iters=solver_iters)
+        s.set_latency(1)
+    s.set_pipelined(pipelined)
+    # inputs resident and unmodified, one output set per frame (pipelined frames overlap)
+    dI, dP = [to_dev(I) for I in frames], [to_dev(P) for P in styl]
+    outs = [(torch.empty((3, H, W), device="cuda"), torch.empty((H, W), device="cuda"),
+             torch.empty((H, W), device="cuda", dtype=torch.uint8)) for _ in range(len(frames) + 1)]
+    for t in range(len(frames)):
+        s.set_consistency(k1=(0.2, 0.5, 0.9)[t % 3] * (0.5 if latency else 1.0), k2=k2, solver_iters=solver_iters)
+        s.process_frame(dI[t], dP[t], *outs[t])
+    if latency:
+        s.flush(*outs[len(frames)])
+    Fb = torch.empty((2, H, W), device="cuda")
+    Ff = torch.empty((2, H, W), device="cuda")
+    if not latency:
+        s.get_flows(Fb, Ff)
+    s.join()
+    torch.cuda.synchronize()
+    res = [tuple(to_np(x) for x in o) for o in outs[:len(frames) + (1 if latency else 0)]]
+    flows = (to_np(Fb), to_np(Ff)) if not latency else None
+    s.destroy()
+    return res, flows
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_pipelined_matches_default(prec):
+    path, _ = weights_file((16, 32, 64, 96, 128), 4)
+    frames, styl = _frames(14, seed=11)
+    a, fa = _run(path, frames, styl, prec, False)
+    b, fb = _run(path, frames, styl, prec, True)
+    for t in range(len(frames)):
+        for k in range(3):
+            assert np.array_equal(a[t][k], b[t][k]), (t, k)
+    assert np.array_equal(fa[0], fb[0]) and np.array_equal(fa[1], fb[1])
+
+
+def test_pipelined_latency_and_flush():
+    path, _ = weights_file((16, 32, 64, 96, 128), 4)
+    frames, styl = _frames(9, seed=12)
+    a, _ = _run(path, frames, styl, "bf16", False, latency=1)
+    b, _ = _run(path, frames, styl, "bf16", True, latency=1)
+    for t in range(1, len(a)):  # the first call of a latency-1 sequence writes nothing
+        for k in range(3):
+            assert np.array_equal(a[t][k], b[t][k]), (t, k)
+
+
+@pytest.mark.parametrize("flow_downscale,solver_iters", [(2, 0), (1, 12)])
+def test_pipelined_fast_preset_and_solver(flow_downscale, solver_iters):
+    path, _ = weights_file((16, 32, 64, 96, 128), 4)
+    frames, styl = _frames(8, seed=13)
+    a, _ = _run(path, frames, styl, "bf16", False, flow_downscale=flow_downscale, solver_iters=solver_iters)
+    b, _ = _run(path, frames, styl, "bf16", True, flow_downscale=flow_downscale, solver_iters=solver_iters)
+    for t in range(len(frames)):
+        for k in range(3):
+            assert np.array_equal(a[t][k], b[t][k]), (t, k)
+
+
+def test_pipelined_state_errors():
+    import torch
+    path, _ = weights_file((16, 32, 64, 96, 128), 4)
+    frames, styl = _frames(2, seed=14)
+    s = tc.Stream(W, H, "bf16", weights_path=path)
+    O = torch.empty((3, H, W), device="cuda")
+    s.process_frame(to_dev(frames[0]), to_dev(styl[0]), O)
+    with pytest.raises(tc.TcError, match="TC_ERR_STATE"):
+        s.set_pipelined(True)  # after the first frame of a sequence
+    s.destroy()
+    s = tc.Stream(W, H, "bf16", weights_path=path)
+    s.set_pipelined(True)
+    with pytest.raises(tc.TcError, match="TC_ERR_STATE"):
+        s.process_frame_host(np.ascontiguousarray(frames[0]), np.ascontiguousarray(styl[0]),
+                             np.empty((3, H, W), np.float32))
+    with pytest.raises(tc.TcError, match="TC_ERR_STATE"):
+        s.set_amax_recording(True)
+    s.destroy()
+    torch.cuda.synchronize()

@@ -197,12 +197,13 @@ def test_stream_1080p_flows_fp32():
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_graph_replay_matches_eager_launches(prec):
-    """From the third frame on a stream replays one captured CUDA graph per slot parity,
-    updating only the nodes that read the caller's buffers and the consistency controls;
-    outputs and flows must be bit-identical to launching kernel by kernel."""
+    """From the third frame on a stream replays one captured CUDA graph per t % 6 (state
+    parity and pyramid slot), updating only the nodes that read the caller's buffers and the
+    consistency controls; over 14 frames every graph is captured and replayed, and outputs
+    and flows must be bit-identical to launching kernel by kernel."""
     import torch
     path, _ = weights_file((16, 32, 64, 96, 128), 4)
-    frames, styl = _pair(200, 136, seed=4, n=6)
+    frames, styl = _pair(200, 136, seed=4, n=14)
     runs = []
     for graphs in (False, True):
         s = tc.Stream(200, 136, prec, weights_path=path)
