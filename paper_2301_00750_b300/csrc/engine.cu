@@ -148,13 +148,16 @@ static std::vector<int> iota_perm(int n, int pad_to) {
 static inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
 // Feature pyramids kept per stream: frame t's lives in slot t % 2 (t % NPYR in pipelined
-// mode), and the flow estimation of frame t reads the slots of t and t - 1.  With three
-// slots, frame t + 1's pyramid never overwrites one that frame t's flow estimation reads, so
-// the two can run at the same time.
-constexpr int NPYR = 3;
-// A pipelined frame's launches depend on t through the state parity (t % 2) and the pyramid
-// slots (t % 3): one captured graph of the flow estimation and blend per t % NGRAPH.
-constexpr int NGRAPH = 6;
+// mode), and the flow estimation of frame t reads the slots of t and t - 1.  With four
+// slots, the pyramids of the next frames never overwrite one that a flow estimation still in
+// flight reads (pipelined mode runs two of them and the next pyramid at the same time).
+constexpr int NPYR = 4;
+// Estimator buffer sets (decoder activations, warped features, flows): pipelined mode
+// estimates frame t with set t % 2, so two frames' flow estimations can run at once.
+constexpr int NSET = 2;
+// A pipelined frame's flow estimation depends on t through its buffer set (t % 2) and the
+// pyramid slots (t % 4): one captured graph per t % NGRAPH.
+constexpr int NGRAPH = 4;
 
 size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precision prec, int fs) {
     const int L = net.levels, D = (2 * net.radius + 1) * (2 * net.radius + 1), m = 1 << L;
@@ -182,7 +185,7 @@ size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precisi
         if (l < 2) continue;
         const int x0p = round_up(c + D + 2, f8 ? 16 : 8);
         const int ctot = x0p + net.dec[0] + net.dec[1] + net.dec[2] + net.dec[3];
-        total += al(2 * px * ctot * es) + al(2 * px * c * es) + 2 * al(2 * px * 2 * 4);
+        total += al(NSET * 2 * px * ctot * es) + al(NSET * 2 * px * c * es) + 2 * al(NSET * 2 * px * 2 * 4);
         const int cin[5] = {x0p, net.dec[0], net.dec[1], net.dec[1] + net.dec[2], net.dec[2] + net.dec[3]};
         const int cout[5] = {net.dec[0], net.dec[1], net.dec[2], net.dec[3], 2};
         for (int j = 0; j < 5; ++j) {
@@ -224,16 +227,16 @@ struct DevBuf {
 
 struct LevelBufs {
     int h = 0, w = 0, c = 0;
-    void *pyr = nullptr;   // [2 slots][h][w][c]
+    void *pyr = nullptr;   // [NPYR slots][h][w][c]
     void *tmpA = nullptr;  // [h][w][c]
     void *tmpB = nullptr;
     // estimator (l >= 2)
     int x0p = 0, ctot = 0;
     int off_x1 = 0, off_x2 = 0, off_x3 = 0, off_x4 = 0;
-    void *dec = nullptr;   // [2 dirs][h][w][ctot]
-    void *f2w = nullptr;   // [2][h][w][c]
-    float *flow = nullptr; // [2][h][w][2]
-    float *up = nullptr;   // [2][h][w][2]
+    void *dec = nullptr;   // [NSET sets][2 dirs][h][w][ctot]
+    void *f2w = nullptr;   // [NSET][2][h][w][c]
+    float *flow = nullptr; // [NSET][2][h][w][2]
+    float *up = nullptr;   // [NSET][2][h][w][2]
     // device weights of the estimator
     float *wk[4] = {nullptr, nullptr, nullptr, nullptr};
     float *bias[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -246,6 +249,16 @@ struct LevelBufs {
     float s_est[6] = {1.f, 1.f, 1.f, 1.f, 1.f, 1.f}, q_est[6] = {1.f, 1.f, 1.f, 1.f, 1.f, 1.f};
     CorrTcPlan corrplan;   // BF16: self = pyramid slots, other = pyramid (coarsest) or f2w
 };
+
+// Buffer set `set` of a level's estimator buffers.
+template <typename T> static T *dec_of(const LevelBufs &B, int set) {
+    return static_cast<T *>(B.dec) + (size_t)set * 2 * B.h * B.w * B.ctot;
+}
+template <typename T> static T *f2w_of(const LevelBufs &B, int set) {
+    return static_cast<T *>(B.f2w) + (size_t)set * 2 * B.h * B.w * B.c;
+}
+static float *flow_of(const LevelBufs &B, int set) { return B.flow + (size_t)set * B.h * B.w * 4; }
+static float *up_of(const LevelBufs &B, int set) { return B.up + (size_t)set * B.h * B.w * 4; }
 
 }  // namespace
 
@@ -328,14 +341,15 @@ struct tc_stream {
         cudaKernelNodeParams p_first{}, p_cons{}, p_copy{}, p_in{};
         int launches = 0;
     } fg[2][2];  // [host entry point][t % 2]: only host calls' graphs wait for the P_t upload
-    // pipelined mode (tc_set_pipelined): the pyramid of frame t runs on pst, the rest of the
-    // frame on gst; pyramid t waits for the rest of frame t - 2 (ev_rest), the rest of frame
-    // t for pyramid t (ev_pyr); one graph per pyramid slot and one per t % NGRAPH
+    // pipelined mode (tc_set_pipelined): the pyramid of frame t runs on pst, its flow
+    // estimation on gst or est1 (by buffer set), its blend on bst; see process_pipelined
     bool pipelined = false;
-    int last_rest = -1;  // ev_rest slot of the last frame given
-    cudaStream_t pst = nullptr;
-    cudaEvent_t ev_pyr[NPYR] = {}, ev_rest[NPYR] = {};
-    FrameGraph pg_pyr[NPYR], pg_rest[NGRAPH];
+    int last_blend = -1;  // event ring index of the last frame's blend
+    int last_set = 0;     // estimator buffer set of the last frame given
+    cudaStream_t pst = nullptr, est1 = nullptr, bst = nullptr;  // pyramid, 2nd estimation (1st: gst), blend
+    static constexpr int NEV = 8;  // event rings, indexed by t % NEV
+    cudaEvent_t ev_pyrs[NEV] = {}, ev_ests[NEV] = {}, ev_blends[NEV] = {};  // pyramid / estimation / blend of frame t done
+    FrameGraph pg_pyr[NPYR], pg_est[NGRAPH], pg_blend[2];
     // screened-Poisson solver (allocated when first enabled): A_t, w_c, right-hand side and
     // four iterate planes, each (3, H, W) float (w_c (H, W))
     float *sv_A = nullptr, *sv_wc = nullptr, *sv_b = nullptr, *sv_c0 = nullptr,
@@ -641,12 +655,12 @@ static tc_status build_stream(tc_stream *s) {
         B.off_x3 = B.off_x2 + net.dec[1];
         B.off_x4 = B.off_x3 + net.dec[2];
         B.ctot = B.off_x4 + net.dec[3];
-        if ((r = dalloc(s, &B.dec, 2 * px * B.ctot * es)) != TC_OK) return r;
-        TC_TRY(s, cudaMemset(B.dec, 0, 2 * px * B.ctot * es), "memset");
-        if ((r = dalloc(s, &B.f2w, 2 * px * B.c * es)) != TC_OK) return r;
-        if ((r = dalloc_t(s, &B.flow, 2 * px * 2 * sizeof(float))) != TC_OK) return r;
-        if ((r = dalloc_t(s, &B.up, 2 * px * 2 * sizeof(float))) != TC_OK) return r;
-        TC_TRY(s, cudaMemset(B.up, 0, 2 * px * 2 * sizeof(float)), "memset");
+        if ((r = dalloc(s, &B.dec, NSET * 2 * px * B.ctot * es)) != TC_OK) return r;
+        TC_TRY(s, cudaMemset(B.dec, 0, NSET * 2 * px * B.ctot * es), "memset");
+        if ((r = dalloc(s, &B.f2w, NSET * 2 * px * B.c * es)) != TC_OK) return r;
+        if ((r = dalloc_t(s, &B.flow, NSET * 2 * px * 2 * sizeof(float))) != TC_OK) return r;
+        if ((r = dalloc_t(s, &B.up, NSET * 2 * px * 2 * sizeof(float))) != TC_OK) return r;
+        TC_TRY(s, cudaMemset(B.up, 0, NSET * 2 * px * 2 * sizeof(float)), "memset");
         const HostLayer *E = &net.layers[3 * L + 5 * (L - l)];
         // conv1 reads x0 (padded to x0p), conv2 x1, conv3 x2, conv4 [x2 | x3], head [x3 | x4].
         std::vector<int> p1(B.x0p, -1), g1(B.x0p, -1);
@@ -671,7 +685,7 @@ static tc_status build_stream(tc_stream *s) {
             T *dec = static_cast<T *>(B.dec);
             ConvArgs a{dec + in_off[j], B.ctot, 2, B.h, B.w, cin[j], 1, B.h, B.w, nullptr, nullptr, net.dec[j],
                        dec + B.off_x1, B.ctot, 1};
-            add_layer(s, B.tcplan[j], a, 2, wk, segs[j], false);
+            add_layer(s, B.tcplan[j], a, 2 * NSET, wk, segs[j], false);
         }
         std::vector<float> wk5 = simt_weights(E[4], p5, s->prec == TC_BF16);
         if ((r = upload(s, &B.head_w, wk5)) != TC_OK) return r;
@@ -680,15 +694,15 @@ static tc_status build_stream(tc_stream *s) {
             std::string why;
             // level L correlates the two pyramid slots; finer levels correlate with f2w
             const void *other = l == L ? B.pyr : B.f2w;
-            if (tc_plan_corr(B.corrplan, B.pyr, NPYR, B.c, other, l == L ? NPYR : 2, B.c, B.h, B.w, B.c, s->R,
-                             s->dev_err, why))
+            if (tc_plan_corr(B.corrplan, B.pyr, NPYR, B.c, other, l == L ? NPYR : 2 * NSET, B.c, B.h, B.w, B.c,
+                             s->R, s->dev_err, why))
                 s->tc_corr_levels += 1;
         }
         {
             T *dec = static_cast<T *>(B.dec);
             ConvArgs a{dec + B.off_x3, B.ctot, 2, B.h, B.w, net.dec[2] + net.dec[3], 1, B.h, B.w, nullptr, nullptr, 2,
                        nullptr, 2, 0};
-            add_layer(s, B.headplan, a, 2, wk5, g5, true);
+            add_layer(s, B.headplan, a, 2 * NSET, wk5, g5, true);
         }
     }
     if (!net.ref.empty() && (r = build_refine<T>(s)) != TC_OK) return r;
@@ -838,6 +852,11 @@ static ConvFirstArgs first_args(const tc_stream *s, const float *img) {
 
 // The pyramid slot of frame t (see NPYR).
 static inline int pyr_slot(const tc_stream *s, long long t) { return (int)(t % (s->pipelined ? NPYR : 2)); }
+// The estimator buffer set of frame t (a network with the refinement keeps one set: its own
+// buffers are single).
+static inline int est_set(const tc_stream *s, long long t) {
+    return s->pipelined && s->ref.empty() ? (int)(t % NSET) : 0;
+}
 
 template <typename T>
 static tc_status run_pyramid(tc_stream *s, const float *img, int slot) {
@@ -919,7 +938,7 @@ static tc_status run_refine(tc_stream *s) {
 // Both directions at once (batch entry 0: self = frame t, other = t-1, giving F_{t->t-1};
 // entry 1: self = t-1, other = t, giving F_{t-1->t}).
 template <typename T>
-static tc_status run_estimators(tc_stream *s, int pcur, int pprev) {
+static tc_status run_estimators(tc_stream *s, int pcur, int pprev, int set) {
     tc_status r;
     const HostNet &net = s->net;
     for (int l = s->L; l >= 2; --l) {
@@ -928,22 +947,24 @@ static tc_status run_estimators(tc_stream *s, int pcur, int pprev) {
         const T *pyr = static_cast<const T *>(B.pyr);
         const T *self_p[2] = {pyr + (size_t)pcur * px * B.c, pyr + (size_t)pprev * px * B.c};
         const T *other_p[2] = {self_p[1], self_p[0]};
-        T *dec = static_cast<T *>(B.dec);
+        T *dec = dec_of<T>(B, set);
+        T *f2w = f2w_of<T>(B, set);
+        float *flow = flow_of(B, set), *up = up_of(B, set);
         const void *fo[2] = {other_p[0], other_p[1]};
         int fo_cs = B.c;
         if (l < s->L) {
             LevelBufs &C = s->lv[l];
             // x2 upsampling of the coarser flow fused into the feature warp; the up-flow also
             // lands in B.up (residual base) and in the estimator input.
-            WarpArgs wa{{other_p[0], other_p[1]}, B.c, nullptr, 2, B.h, B.w, B.c, B.f2w, B.c,
-                        C.flow, B.up, dec + B.c + s->D, B.ctot, B.q_est[1]};
+            WarpArgs wa{{other_p[0], other_p[1]}, B.c, nullptr, 2, B.h, B.w, B.c, f2w, B.c,
+                        flow_of(C, set), up, dec + B.c + s->D, B.ctot, B.q_est[1]};
             TC_LAUNCH_CAT(s, TC_PROF_WARP, launch_warp<T>(wa, s->st));
-            fo[0] = static_cast<T *>(B.f2w);
-            fo[1] = static_cast<T *>(B.f2w) + px * B.c;
+            fo[0] = f2w;
+            fo[1] = f2w + px * B.c;
         }
         if (B.corrplan.enabled) {
             const int img_s[2] = {pcur, pprev};
-            const int img_o[2] = {l < s->L ? 0 : pprev, l < s->L ? 1 : pcur};
+            const int img_o[2] = {l < s->L ? 2 * set : pprev, l < s->L ? 2 * set + 1 : pcur};
             const void *fs[2] = {self_p[0], self_p[1]};
             TC_LAUNCH_CAT(s, TC_PROF_CORRELATION,
                           launch_corr_tc(B.corrplan, 2, img_s, img_o, dec + B.c, B.ctot, fs, dec, s->st, B.s_pyr[2],
@@ -966,12 +987,12 @@ static tc_status run_estimators(tc_stream *s, int pcur, int pprev) {
         if (B.headplan.enabled) {
             ConvArgs a5{dec + B.off_x3, B.ctot, 2, B.h, B.w, net.dec[2] + net.dec[3], 1, B.h, B.w, B.head_w, B.head_b,
                         2, nullptr, 2, 0};
-            TC_LAUNCH_CAT(s, TC_PROF_HEAD, launch_conv_tc_head(B.headplan, a5, l < s->L ? B.up : nullptr, B.flow, s->st));
+            TC_LAUNCH_CAT(s, TC_PROF_HEAD, launch_conv_tc_head(B.headplan, a5, l < s->L ? up : nullptr, flow, s->st));
         } else if constexpr (sizeof(T) == 1) {
             return fail(s, TC_ERR_UNSUPPORTED, "e4m3 flow head without a tensor-core plan");
         } else {
             HeadArgs ha{dec + B.off_x3, B.ctot, net.dec[2] + net.dec[3], 2, B.h, B.w, B.head_w, B.head_b,
-                        l < s->L ? B.up : nullptr, B.flow};
+                        l < s->L ? up : nullptr, flow};
             TC_LAUNCH_CAT(s, TC_PROF_HEAD, launch_head<T>(ha, s->st));
         }
     }
@@ -1021,14 +1042,15 @@ static ConsistArgs consist_args(tc_stream *s, const float *I, const float *P, fl
     }
     LevelBufs &B2 = s->lv[1];
     const size_t half = (size_t)B2.h * B2.w * 2;
+    float *flow2 = flow_of(B2, est_set(s, s->t));
     ca.first = 0;
     ca.Ip = lat ? s->sI[cur] : s->sI[prev];
     ca.Pp = lat ? s->sP[cur] : s->sP[prev];
     ca.Op = s->sO[prev];
     ca.fh = B2.h; ca.fw = B2.w; ca.scale = 4 * s->fs;
     if (!lat) {
-        ca.Fb = B2.flow;
-        ca.Ff = B2.flow + half;
+        ca.Fb = flow2;
+        ca.Ff = flow2 + half;
         return ca;
     }
     // the pair (t, t-1) from the previous call; the pair (t+1, t) just computed
@@ -1038,8 +1060,8 @@ static ConsistArgs consist_args(tc_stream *s, const float *I, const float *P, fl
         ca.next = 1;
         ca.In = I;
         ca.Pn = P;
-        ca.Fn = B2.flow + half;  // F_{t->t+1}
-        ca.Fnb = B2.flow;        // F_{t+1->t}
+        ca.Fn = flow2 + half;  // F_{t->t+1}
+        ca.Fnb = flow2;        // F_{t+1->t}
     }
     return ca;
 }
@@ -1055,14 +1077,20 @@ static tc_status solver_launches(tc_stream *s, const float *P, float *O, float *
     return TC_OK;
 }
 
-// The launches of a frame after its pyramid: flow estimation (from the second frame on),
-// the blend, and the solver or the state copies.  upload: P_t arrives by the host entry
-// point's upload (waited for before the first read of P_t).
+// The flow estimation of a frame (from the second frame on; with the refinement).
 template <typename T>
-static tc_status rest_launches(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask,
-                               int cur, bool upload) {
+static tc_status est_launches(tc_stream *s) {
+    if (s->t == 0) return TC_OK;
+    return run_estimators<T>(s, pyr_slot(s, s->t), pyr_slot(s, s->t - 1), est_set(s, s->t));
+}
+
+// The launches of a frame after its flow estimation: the blend, and the solver or the state
+// copies.  upload: P_t arrives by the host entry point's upload (waited for before the first
+// read of P_t).
+template <typename T>
+static tc_status blend_launches(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask,
+                                int cur, bool upload) {
     tc_status r;
-    if (s->t > 0 && (r = run_estimators<T>(s, pyr_slot(s, s->t), pyr_slot(s, s->t - 1))) != TC_OK) return r;
     // everything from here on may read P_t
     if (upload) TC_TRY(s, cudaStreamWaitEvent(s->st, s->capturing ? s->ev_join : s->ev_p, 0), "cudaStreamWaitEvent");
     if (!s->latency) {
@@ -1084,7 +1112,7 @@ static tc_status rest_launches(tc_stream *s, const float *I, const float *P, flo
     TC_LAUNCH_CAT(s, TC_PROF_CONSISTENCY, launch_copy_out(I, s->sI[cur], img, P, s->sP[cur], img, s->st, 1));
     if (s->t > 0) {
         LevelBufs &B2 = s->lv[1];
-        TC_TRY(s, cudaMemcpyAsync(s->Fprev, B2.flow, (size_t)B2.h * B2.w * 4 * sizeof(float),
+        TC_TRY(s, cudaMemcpyAsync(s->Fprev, flow_of(B2, est_set(s, s->t)), (size_t)B2.h * B2.w * 4 * sizeof(float),
                                   cudaMemcpyDeviceToDevice, s->st),
                "flow copy");
     }
@@ -1106,7 +1134,8 @@ static tc_status frame_launches(tc_stream *s, const float *I, const float *P, fl
         TC_TRY(s, cudaEventRecord(s->ev_join, s->cst), "cudaEventRecord");
     }
     if ((r = run_pyramid<T>(s, I, pyr_slot(s, s->t))) != TC_OK) return r;
-    return rest_launches<T>(s, I, P, O, wc, mask, cur, upload);
+    if ((r = est_launches<T>(s)) != TC_OK) return r;
+    return blend_launches<T>(s, I, P, O, wc, mask, cur, upload);
 }
 
 // Captures the launches made by `launches` on stream cs into graph G and finds the kernel
@@ -1282,22 +1311,30 @@ static tc_status process(tc_stream *s, const float *I, const float *P, float *O,
     TC_TRY(s, cudaEventRecord(s->ev_out, s->gst), "cudaEventRecord");
     TC_TRY(s, cudaStreamWaitEvent(s->st, s->ev_out, 0), "cudaStreamWaitEvent");
     s->launches = G.launches;
+    s->last_set = 0;
     s->t += 1;
     s->last_out = out;
     return TC_OK;
 }
 
-// Pipelined mode: frame t's pyramid runs on pst, the rest of the frame on gst, with no
-// ordering on the caller's stream (the inputs are valid when the call is made; tc_join or
-// tc_synchronize make the results visible).  Pyramid t writes the slot that the rest of
-// frame t - 2 read last and waits for it; the rest of frame t waits for pyramid t and
-// follows the rest of frame t - 1 on gst.  So pyramid t + 1 runs while the flows of frame t
-// are estimated.
+// Pipelined mode: frame t's pyramid runs on pst, its flow estimation on gst or est1 (its
+// buffer set, t % 2), its blend on bst, with no ordering on the caller's stream (the inputs
+// are valid when the call is made; tc_join or tc_synchronize make the results visible).
+//   * pyramid t writes slot t % 4, last read by the flow estimations of frames t - 4 and
+//     t - 3, and waits for both;
+//   * the flow estimation of frame t waits for pyramid t (pyramid t - 1 came before it on
+//     pst) and for the blend that last read its buffer set's flows (frame t - 2, or t - 1
+//     with one set), and follows frame t - 2's estimation on its stream;
+//   * the blend of frame t waits for its flow estimation and follows frame t - 1's blend.
+// So the next frame's pyramid and two frames' flow estimations run at the same time.
 template <typename T>
 static tc_status process_pipelined(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask) {
+    constexpr int NEV = tc_stream::NEV;
     tc_status r;
-    const int cur = (int)(s->t & 1), ps = pyr_slot(s, s->t), k = (int)(s->t % NPYR);
-    const long long out = s->latency ? s->t - 1 : s->t;
+    const long long t = s->t;
+    const int cur = (int)(t & 1), ps = pyr_slot(s, t), set = est_set(s, t), e = (int)(t % NEV);
+    const int nsets = s->ref.empty() ? NSET : 1;
+    const long long out = s->latency ? t - 1 : t;
     if (!s->gst) {
         TC_TRY(s, cudaStreamCreateWithFlags(&s->gst, cudaStreamNonBlocking), "cudaStreamCreate");
         TC_TRY(s, cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming), "cudaEventCreate");
@@ -1305,62 +1342,84 @@ static tc_status process_pipelined(tc_stream *s, const float *I, const float *P,
     }
     if (!s->pst) {
         TC_TRY(s, cudaStreamCreateWithFlags(&s->pst, cudaStreamNonBlocking), "cudaStreamCreate");
-        for (int j = 0; j < NPYR; ++j) {
-            TC_TRY(s, cudaEventCreateWithFlags(&s->ev_pyr[j], cudaEventDisableTiming), "cudaEventCreate");
-            TC_TRY(s, cudaEventCreateWithFlags(&s->ev_rest[j], cudaEventDisableTiming), "cudaEventCreate");
+        TC_TRY(s, cudaStreamCreateWithFlags(&s->est1, cudaStreamNonBlocking), "cudaStreamCreate");
+        TC_TRY(s, cudaStreamCreateWithFlags(&s->bst, cudaStreamNonBlocking), "cudaStreamCreate");
+        for (int j = 0; j < NEV; ++j) {
+            TC_TRY(s, cudaEventCreateWithFlags(&s->ev_pyrs[j], cudaEventDisableTiming), "cudaEventCreate");
+            TC_TRY(s, cudaEventCreateWithFlags(&s->ev_ests[j], cudaEventDisableTiming), "cudaEventCreate");
+            TC_TRY(s, cudaEventCreateWithFlags(&s->ev_blends[j], cudaEventDisableTiming), "cudaEventCreate");
         }
     }
-    // the slot pyramid t writes was last read by the rest of frame t - 2 (at the start of a
-    // sequence: by any earlier frame)
-    if (s->t == 0) {
-        for (int j = 0; j < NPYR; ++j) TC_TRY(s, cudaStreamWaitEvent(s->pst, s->ev_rest[j], 0), "cudaStreamWaitEvent");
+    cudaStream_t es = set == 1 ? s->est1 : s->gst;
+    // pyramid t: after everything before the sequence, or after the estimations of t-4, t-3
+    if (t == 0) {
+        if (s->last_blend >= 0)
+            TC_TRY(s, cudaStreamWaitEvent(s->pst, s->ev_blends[s->last_blend], 0), "cudaStreamWaitEvent");
     } else {
-        TC_TRY(s, cudaStreamWaitEvent(s->pst, s->ev_rest[(s->t + 1) % NPYR], 0), "cudaStreamWaitEvent");
+        for (int j = 3; j <= 4; ++j)
+            if (t - j >= 0) TC_TRY(s, cudaStreamWaitEvent(s->pst, s->ev_ests[(t - j) % NEV], 0), "cudaStreamWaitEvent");
     }
+    // estimation t: after the blend that last read this buffer set's flows
+    if (t >= nsets) TC_TRY(s, cudaStreamWaitEvent(es, s->ev_blends[(t - nsets) % NEV], 0), "cudaStreamWaitEvent");
     cudaStream_t caller = s->st;
-    if (!s->graphs || s->prof || s->t < 2) {
+    if (!s->graphs || s->prof || t < 2) {
         s->st = s->pst;
         r = run_pyramid<T>(s, I, ps);
         s->st = caller;
         if (r != TC_OK) return r;
-        TC_TRY(s, cudaEventRecord(s->ev_pyr[ps], s->pst), "cudaEventRecord");
-        TC_TRY(s, cudaStreamWaitEvent(s->gst, s->ev_pyr[ps], 0), "cudaStreamWaitEvent");
-        s->st = s->gst;
-        r = rest_launches<T>(s, I, P, O, wc, mask, cur, false);
+        TC_TRY(s, cudaEventRecord(s->ev_pyrs[e], s->pst), "cudaEventRecord");
+        TC_TRY(s, cudaStreamWaitEvent(es, s->ev_pyrs[e], 0), "cudaStreamWaitEvent");
+        s->st = es;
+        r = est_launches<T>(s);
+        s->st = caller;
+        if (r != TC_OK) return r;
+        TC_TRY(s, cudaEventRecord(s->ev_ests[e], es), "cudaEventRecord");
+        TC_TRY(s, cudaStreamWaitEvent(s->bst, s->ev_ests[e], 0), "cudaStreamWaitEvent");
+        s->st = s->bst;
+        r = blend_launches<T>(s, I, P, O, wc, mask, cur, false);
         s->st = caller;
         if (r != TC_OK) return r;
     } else {
-        tc_stream::FrameGraph &Gp = s->pg_pyr[ps], &Gr = s->pg_rest[s->t % NGRAPH];
+        tc_stream::FrameGraph &Gp = s->pg_pyr[ps], &Ge = s->pg_est[t % NGRAPH], &Gb = s->pg_blend[cur];
         if (!Gp.exec) {
             r = capture_into<T>(s, s->pst, Gp, [&] { return run_pyramid<T>(s, I, ps); }, true, false);
             if (r != TC_OK) return r;
         } else if ((r = update_first_node<T>(s, Gp, I)) != TC_OK) {
             return r;
         }
-        if (!Gr.exec) {
-            r = capture_into<T>(s, s->gst, Gr, [&] { return rest_launches<T>(s, I, P, O, wc, mask, cur, false); },
+        if (!Ge.exec) {
+            r = capture_into<T>(s, es, Ge, [&] { return est_launches<T>(s); }, false, false);
+            if (r != TC_OK) return r;
+        }
+        if (!Gb.exec) {
+            r = capture_into<T>(s, s->bst, Gb, [&] { return blend_launches<T>(s, I, P, O, wc, mask, cur, false); },
                                 false, true);
             if (r != TC_OK) return r;
-        } else if ((r = update_rest_nodes(s, Gr, I, P, O, wc, mask, cur)) != TC_OK) {
+        } else if ((r = update_rest_nodes(s, Gb, I, P, O, wc, mask, cur)) != TC_OK) {
             return r;
         }
         TC_TRY(s, cudaGraphLaunch(Gp.exec, s->pst), "cudaGraphLaunch");
-        TC_TRY(s, cudaEventRecord(s->ev_pyr[ps], s->pst), "cudaEventRecord");
-        TC_TRY(s, cudaStreamWaitEvent(s->gst, s->ev_pyr[ps], 0), "cudaStreamWaitEvent");
-        TC_TRY(s, cudaGraphLaunch(Gr.exec, s->gst), "cudaGraphLaunch");
-        s->launches = Gp.launches + Gr.launches;
+        TC_TRY(s, cudaEventRecord(s->ev_pyrs[e], s->pst), "cudaEventRecord");
+        TC_TRY(s, cudaStreamWaitEvent(es, s->ev_pyrs[e], 0), "cudaStreamWaitEvent");
+        TC_TRY(s, cudaGraphLaunch(Ge.exec, es), "cudaGraphLaunch");
+        TC_TRY(s, cudaEventRecord(s->ev_ests[e], es), "cudaEventRecord");
+        TC_TRY(s, cudaStreamWaitEvent(s->bst, s->ev_ests[e], 0), "cudaStreamWaitEvent");
+        TC_TRY(s, cudaGraphLaunch(Gb.exec, s->bst), "cudaGraphLaunch");
+        s->launches = Gp.launches + Ge.launches + Gb.launches;
     }
-    TC_TRY(s, cudaEventRecord(s->ev_rest[k], s->gst), "cudaEventRecord");
-    s->last_rest = k;
+    TC_TRY(s, cudaEventRecord(s->ev_blends[e], s->bst), "cudaEventRecord");
+    s->last_blend = e;
+    s->last_set = set;
     s->t += 1;
     s->last_out = out;
     return TC_OK;
 }
 
-// Pipelined mode: makes the caller's stream wait for every frame given so far.
+// Pipelined mode: makes the caller's stream wait for every frame given so far (the last
+// blend follows every earlier blend, each after its frame's estimation and pyramid).
 static tc_status join_caller(tc_stream *s) {
-    if (s->pipelined && s->last_rest >= 0)
-        TC_TRY(s, cudaStreamWaitEvent(s->st, s->ev_rest[s->last_rest], 0), "cudaStreamWaitEvent");
+    if (s->pipelined && s->last_blend >= 0)
+        TC_TRY(s, cudaStreamWaitEvent(s->st, s->ev_blends[s->last_blend], 0), "cudaStreamWaitEvent");
     return TC_OK;
 }
 
@@ -1374,21 +1433,24 @@ static void release_graphs(tc_stream *s) {
     for (auto &GG : s->fg)
         for (auto &G : GG) release_graph(G);
     for (auto &G : s->pg_pyr) release_graph(G);
-    for (auto &G : s->pg_rest) release_graph(G);
+    for (auto &G : s->pg_est) release_graph(G);
+    for (auto &G : s->pg_blend) release_graph(G);
 }
 
 static void release_graph_stream(tc_stream *s) {
-    if (s->pst) {
-        cudaStreamSynchronize(s->pst);
-        cudaStreamDestroy(s->pst);
-        s->pst = nullptr;
+    for (cudaStream_t *q : {&s->pst, &s->est1, &s->bst})
+        if (*q) {
+            cudaStreamSynchronize(*q);
+            cudaStreamDestroy(*q);
+            *q = nullptr;
+        }
+    for (int j = 0; j < tc_stream::NEV; ++j) {
+        if (s->ev_pyrs[j]) cudaEventDestroy(s->ev_pyrs[j]);
+        if (s->ev_ests[j]) cudaEventDestroy(s->ev_ests[j]);
+        if (s->ev_blends[j]) cudaEventDestroy(s->ev_blends[j]);
+        s->ev_pyrs[j] = s->ev_ests[j] = s->ev_blends[j] = nullptr;
     }
-    for (int j = 0; j < NPYR; ++j) {
-        if (s->ev_pyr[j]) cudaEventDestroy(s->ev_pyr[j]);
-        if (s->ev_rest[j]) cudaEventDestroy(s->ev_rest[j]);
-        s->ev_pyr[j] = s->ev_rest[j] = nullptr;
-    }
-    s->last_rest = -1;
+    s->last_blend = -1;
     if (s->gst) {
         cudaStreamSynchronize(s->gst);
         cudaStreamDestroy(s->gst);
@@ -1471,8 +1533,8 @@ extern "C" tc_status tc_set_fp8_scales(tc_stream *s, const float *scales, int n)
         LevelBufs &B = s->lv[l - 1];
         std::string why;
         const void *other = l == s->L ? B.pyr : B.f2w;
-        if (!tc_plan_corr(B.corrplan, B.pyr, NPYR, B.c, other, l == s->L ? NPYR : 2, B.c, B.h, B.w, B.c, s->R,
-                          s->dev_err, why, true))
+        if (!tc_plan_corr(B.corrplan, B.pyr, NPYR, B.c, other, l == s->L ? NPYR : 2 * NSET, B.c, B.h, B.w, B.c,
+                          s->R, s->dev_err, why, true))
             return fail(s, TC_ERR_UNSUPPORTED, "e4m3 correlation not eligible for the tensor cores: " + why);
         s->tc_corr_levels += 1;
     }
@@ -1518,7 +1580,8 @@ extern "C" tc_status tc_synchronize(tc_stream *s) {
     tc_status r = check_stream(s, "tc_synchronize");
     if (r != TC_OK) return r;
     TC_TRY(s, cudaStreamSynchronize(s->st), "stream synchronize");
-    if (s->pst) TC_TRY(s, cudaStreamSynchronize(s->pst), "pyramid stream synchronize");
+    for (cudaStream_t q : {s->pst, s->est1, s->bst})
+        if (q) TC_TRY(s, cudaStreamSynchronize(q), "pipeline stream synchronize");
     if (s->gst) TC_TRY(s, cudaStreamSynchronize(s->gst), "library stream synchronize");
     if (s->cst) TC_TRY(s, cudaStreamSynchronize(s->cst), "upload stream synchronize");
     if (s->dst) TC_TRY(s, cudaStreamSynchronize(s->dst), "download stream synchronize");
@@ -1667,15 +1730,15 @@ extern "C" tc_status tc_flush(tc_stream *s, float *O_t, float *wc_opt, uint8_t *
     // the last frame has no next frame: the causal blend with the kept flows (pipelined
     // mode: on the library stream, after the frames given)
     cudaStream_t caller = s->st;
-    if (s->pipelined && s->gst) s->st = s->gst;
+    if (s->pipelined && s->bst) s->st = s->bst;
     const ConsistArgs ca = consist_args(s, nullptr, nullptr, O_t, wc_opt, mask_opt, cur, true);
     r = TC_OK;
     const cudaError_t ce = launch_consistency(ca, s->st);
     ++s->launches;
     if (ce != cudaSuccess) r = cuda_fail(s, ce, "tc_flush launch");
     if (r == TC_OK && s->t > 1 && s->params.solver_iters > 0) r = solver_launches(s, s->sP[cur ^ 1], O_t, wc_opt, cur);
-    if (r == TC_OK && s->pipelined && s->gst && s->last_rest >= 0) {
-        const cudaError_t ee = cudaEventRecord(s->ev_rest[s->last_rest], s->gst);
+    if (r == TC_OK && s->pipelined && s->bst && s->last_blend >= 0) {
+        const cudaError_t ee = cudaEventRecord(s->ev_blends[s->last_blend], s->bst);
         if (ee != cudaSuccess) r = cuda_fail(s, ee, "cudaEventRecord");
     }
     s->st = caller;
@@ -1693,9 +1756,10 @@ extern "C" tc_status tc_get_flows(tc_stream *s, float *Fb, float *Ff) {
     if (s->t < 2) return fail(s, TC_ERR_STATE, "tc_get_flows: no flow before the second frame");
     if ((r = join_caller(s)) != TC_OK) return r;
     LevelBufs &B2 = s->lv[1];
-    if (Fb) TC_LAUNCH(s, launch_flow_out(B2.flow, B2.h, B2.w, 4 * s->fs, s->H, s->W, Fb, s->st));
+    float *flow2 = flow_of(B2, s->last_set);
+    if (Fb) TC_LAUNCH(s, launch_flow_out(flow2, B2.h, B2.w, 4 * s->fs, s->H, s->W, Fb, s->st));
     if (Ff)
-        TC_LAUNCH(s, launch_flow_out(B2.flow + (size_t)B2.h * B2.w * 2, B2.h, B2.w, 4 * s->fs, s->H, s->W, Ff, s->st));
+        TC_LAUNCH(s, launch_flow_out(flow2 + (size_t)B2.h * B2.w * 2, B2.h, B2.w, 4 * s->fs, s->H, s->W, Ff, s->st));
     return TC_OK;
 }
 
