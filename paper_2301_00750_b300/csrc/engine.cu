@@ -342,14 +342,15 @@ struct tc_stream {
         int launches = 0;
     } fg[2][2];  // [host entry point][t % 2]: only host calls' graphs wait for the P_t upload
     // pipelined mode (tc_set_pipelined): the pyramid of frame t runs on pst, its flow
-    // estimation on gst or est1 (by buffer set), its blend on bst; see process_pipelined
+    // estimation on the stream of its buffer set, its blend on bst; see process_pipelined
     bool pipelined = false;
     int last_blend = -1;  // event ring index of the last frame's blend
     int last_set = 0;     // estimator buffer set of the last frame given
-    cudaStream_t pst = nullptr, est1 = nullptr, bst = nullptr;  // pyramid, 2nd estimation (1st: gst), blend
+    cudaStream_t pst = nullptr, bst = nullptr;  // pyramid, blend
+    cudaStream_t estx[NSET - 1] = {};           // estimation of sets 1.. (set 0: gst)
     static constexpr int NEV = 8;  // event rings, indexed by t % NEV
     cudaEvent_t ev_pyrs[NEV] = {}, ev_ests[NEV] = {}, ev_blends[NEV] = {};  // pyramid / estimation / blend of frame t done
-    FrameGraph pg_pyr[NPYR], pg_est[NGRAPH], pg_blend[2];
+    FrameGraph pg_pyr[NPYR], pg_est[NGRAPH], pg_blend[NGRAPH];
     // screened-Poisson solver (allocated when first enabled): A_t, w_c, right-hand side and
     // four iterate planes, each (3, H, W) float (w_c (H, W))
     float *sv_A = nullptr, *sv_wc = nullptr, *sv_b = nullptr, *sv_c0 = nullptr,
@@ -1317,16 +1318,16 @@ static tc_status process(tc_stream *s, const float *I, const float *P, float *O,
     return TC_OK;
 }
 
-// Pipelined mode: frame t's pyramid runs on pst, its flow estimation on gst or est1 (its
-// buffer set, t % 2), its blend on bst, with no ordering on the caller's stream (the inputs
+// Pipelined mode: frame t's pyramid runs on pst, its flow estimation on the stream of its
+// buffer set (t % NSET: gst, estx[...]), its blend on bst, with no ordering on the caller's stream (the inputs
 // are valid when the call is made; tc_join or tc_synchronize make the results visible).
-//   * pyramid t writes slot t % 4, last read by the flow estimations of frames t - 4 and
-//     t - 3, and waits for both;
+//   * pyramid t writes slot t % NPYR, last read by the flow estimations of frames t - NPYR
+//     and t - NPYR + 1, and waits for both;
 //   * the flow estimation of frame t waits for pyramid t (pyramid t - 1 came before it on
-//     pst) and for the blend that last read its buffer set's flows (frame t - 2, or t - 1
-//     with one set), and follows frame t - 2's estimation on its stream;
+//     pst) and for the blend that last read its buffer set's flows (frame t - NSET, or t - 1
+//     with one set), and follows frame t - NSET's estimation on its stream;
 //   * the blend of frame t waits for its flow estimation and follows frame t - 1's blend.
-// So the next frame's pyramid and two frames' flow estimations run at the same time.
+// So the next frame's pyramid and NSET frames' flow estimations run at the same time.
 template <typename T>
 static tc_status process_pipelined(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask) {
     constexpr int NEV = tc_stream::NEV;
@@ -1342,7 +1343,7 @@ static tc_status process_pipelined(tc_stream *s, const float *I, const float *P,
     }
     if (!s->pst) {
         TC_TRY(s, cudaStreamCreateWithFlags(&s->pst, cudaStreamNonBlocking), "cudaStreamCreate");
-        TC_TRY(s, cudaStreamCreateWithFlags(&s->est1, cudaStreamNonBlocking), "cudaStreamCreate");
+        for (cudaStream_t &q : s->estx) TC_TRY(s, cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking), "cudaStreamCreate");
         TC_TRY(s, cudaStreamCreateWithFlags(&s->bst, cudaStreamNonBlocking), "cudaStreamCreate");
         for (int j = 0; j < NEV; ++j) {
             TC_TRY(s, cudaEventCreateWithFlags(&s->ev_pyrs[j], cudaEventDisableTiming), "cudaEventCreate");
@@ -1350,13 +1351,14 @@ static tc_status process_pipelined(tc_stream *s, const float *I, const float *P,
             TC_TRY(s, cudaEventCreateWithFlags(&s->ev_blends[j], cudaEventDisableTiming), "cudaEventCreate");
         }
     }
-    cudaStream_t es = set == 1 ? s->est1 : s->gst;
-    // pyramid t: after everything before the sequence, or after the estimations of t-4, t-3
+    cudaStream_t es = set == 0 ? s->gst : s->estx[set - 1];
+    // pyramid t: after everything before the sequence, or after the estimations that read
+    // its slot last (frames t - NPYR and t - NPYR + 1)
     if (t == 0) {
         if (s->last_blend >= 0)
             TC_TRY(s, cudaStreamWaitEvent(s->pst, s->ev_blends[s->last_blend], 0), "cudaStreamWaitEvent");
     } else {
-        for (int j = 3; j <= 4; ++j)
+        for (int j = NPYR - 1; j <= NPYR; ++j)
             if (t - j >= 0) TC_TRY(s, cudaStreamWaitEvent(s->pst, s->ev_ests[(t - j) % NEV], 0), "cudaStreamWaitEvent");
     }
     // estimation t: after the blend that last read this buffer set's flows
@@ -1380,7 +1382,7 @@ static tc_status process_pipelined(tc_stream *s, const float *I, const float *P,
         s->st = caller;
         if (r != TC_OK) return r;
     } else {
-        tc_stream::FrameGraph &Gp = s->pg_pyr[ps], &Ge = s->pg_est[t % NGRAPH], &Gb = s->pg_blend[cur];
+        tc_stream::FrameGraph &Gp = s->pg_pyr[ps], &Ge = s->pg_est[t % NGRAPH], &Gb = s->pg_blend[t % NGRAPH];
         if (!Gp.exec) {
             r = capture_into<T>(s, s->pst, Gp, [&] { return run_pyramid<T>(s, I, ps); }, true, false);
             if (r != TC_OK) return r;
@@ -1438,7 +1440,9 @@ static void release_graphs(tc_stream *s) {
 }
 
 static void release_graph_stream(tc_stream *s) {
-    for (cudaStream_t *q : {&s->pst, &s->est1, &s->bst})
+    std::vector<cudaStream_t *> qs = {&s->pst, &s->bst};
+    for (cudaStream_t &q : s->estx) qs.push_back(&q);
+    for (cudaStream_t *q : qs)
         if (*q) {
             cudaStreamSynchronize(*q);
             cudaStreamDestroy(*q);
@@ -1580,7 +1584,9 @@ extern "C" tc_status tc_synchronize(tc_stream *s) {
     tc_status r = check_stream(s, "tc_synchronize");
     if (r != TC_OK) return r;
     TC_TRY(s, cudaStreamSynchronize(s->st), "stream synchronize");
-    for (cudaStream_t q : {s->pst, s->est1, s->bst})
+    for (cudaStream_t q : {s->pst, s->bst})
+        if (q) TC_TRY(s, cudaStreamSynchronize(q), "pipeline stream synchronize");
+    for (cudaStream_t q : s->estx)
         if (q) TC_TRY(s, cudaStreamSynchronize(q), "pipeline stream synchronize");
     if (s->gst) TC_TRY(s, cudaStreamSynchronize(s->gst), "library stream synchronize");
     if (s->cst) TC_TRY(s, cudaStreamSynchronize(s->cst), "upload stream synchronize");
