@@ -69,6 +69,7 @@ struct TcLaunch {
     int out_f32;          // bf16 operands only: write float32 (out_cs in floats) instead of bf16
     int accumulate;       // with out_f32: add to the output instead of overwriting it
     int taps;             // 9: 3x3 conv; 1: pointwise 1x1 conv (the centre tap only)
+    int tail;             // halo kernel: the last channel step is a 32-channel (64-byte) tail
 };
 
 // Epilogue shared by the conv kernels: thread r of the CTA owns accumulator row r, i.e.
@@ -285,7 +286,8 @@ __host__ __device__ constexpr size_t halo_smem_for(int bn) {
 
 template <int BN, bool HEAD, bool F8>
 __global__ void __launch_bounds__(128, 1)
-conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcLaunch p) {
+conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2, const TcLaunch p) {
     constexpr int SB = halo_sb(BN);
     constexpr uint32_t B_BYTES = BN * BK * 2;
     constexpr uint32_t TMEM_COLS = tmem_cols_for(BN);
@@ -336,9 +338,10 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
             const int ky = g / p.nch, ch = g - ky * p.nch;
             const int sa = g % HALO_SA;
             if (!mbar_wait(emptyA + 8 * sa, ((uint32_t)(g / HALO_SA) & 1u) ^ 1u, p.err, ERR_PRODUCER)) break;
-            mbar_expect_tx(fullA + 8 * sa, halo_tx);
-            tma_load_4d(&tmA, fullA + 8 * sa, smem_u32(sA + sa * HALO_SLOT), ch * p.kc, x0 - 1, y + ky - 1,
-                        img + p.img_off);
+            const bool tl = p.tail && ch == p.nch - 1;  // the 32-channel tail step
+            mbar_expect_tx(fullA + 8 * sa, tl ? HALO_ROWS * 64u : halo_tx);
+            tma_load_4d(tl ? &tmA2 : &tmA, fullA + 8 * sa, smem_u32(sA + sa * HALO_SLOT), ch * p.kc, x0 - 1,
+                        y + ky - 1, img + p.img_off);
             ga = g + 1;
             for (int kx = 0; kx < 3; ++kx) {
                 const int kb = 3 * g + kx, sb = kb % SB;
@@ -346,8 +349,8 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                     fine = false;
                     break;
                 }
-                mbar_expect_tx(fullB + 8 * sb, b_tx);
-                tma_load_3d(&tmB, fullB + 8 * sb, smem_u32(sB + sb * B_BYTES), ch * p.kc, 0, ky * 3 + kx);
+                mbar_expect_tx(fullB + 8 * sb, tl ? (uint32_t)BN * 64u : b_tx);
+                tma_load_3d(tl ? &tmB2 : &tmB, fullB + 8 * sb, smem_u32(sB + sb * B_BYTES), ch * p.kc, 0, ky * 3 + kx);
                 gb = kb + 1;
             }
         }
@@ -369,6 +372,8 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
             const int sa = g % HALO_SA;
             if (!mbar_wait(fullA + 8 * sa, (uint32_t)(g / HALO_SA) & 1u, p.err, ERR_MMA)) break;
             const uint32_t a0 = smem_u32(sA + sa * HALO_SLOT);
+            const int ch = g % p.nch;
+            const uint32_t rb = p.tail && ch == p.nch - 1 ? 64u : (uint32_t)p.rb;  // bytes of this K step
             for (int kx = 0; kx < 3; ++kx) {
                 const int kb = 3 * g + kx, sb = kb % SB;
                 if (!mbar_wait(fullB + 8 * sb, (uint32_t)(kb / SB) & 1u, p.err, ERR_MMA)) {
@@ -376,9 +381,9 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint64_t da = sw_desc(a0 + (uint32_t)p.rb * (uint32_t)kx, (uint32_t)p.rb);
-                const uint64_t db = sw_desc(smem_u32(sB + sb * B_BYTES), (uint32_t)p.rb);
-                for (int kk = 0; kk < p.rb / 32; ++kk)
+                const uint64_t da = sw_desc(a0 + rb * (uint32_t)kx, rb);
+                const uint64_t db = sw_desc(smem_u32(sB + sb * B_BYTES), rb);
+                for (int kk = 0; kk < (int)rb / 32; ++kk)
                     umma<F8>(tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
                               (g | kx | kk) != 0 ? 1u : 0u);
                 umma_commit(emptyB + 8 * sb);
@@ -577,7 +582,10 @@ cudaError_t launch_bn(const TcConvPlan &plan, const TcLaunch &lp, int n_img, cud
             if (e != cudaSuccess) return e;
             attr_set = true;
         }
-        return launch_pdl(conv_tc_halo_kernel<BN, HEAD, F8>, grid, dim3(128), smem, st, plan.tmA, plan.tmB, lp);
+        TcLaunch lt = lp;
+        lt.tail = plan.tail ? 1 : 0;
+        return launch_pdl(conv_tc_halo_kernel<BN, HEAD, F8>, grid, dim3(128), smem, st, plan.tmA, plan.tmB,
+                          plan.tail ? plan.tmA2 : plan.tmA, plan.tail ? plan.tmB2 : plan.tmB, lt);
     } else {
         static size_t attr_bytes = 0;
         const size_t smem = smem_bytes_for(BN, plan.rb);
@@ -706,6 +714,23 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
         const cuuint32_t box[3] = {(cuuint32_t)kc, (cuuint32_t)bn, 1};
         r = enc(&plan.tmB, dt, 3, wdev, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    // A stride-1 3x3 BF16 layer whose last 64-channel step holds at most 32 channels takes
+    // that step as 32 channels (64-byte rows and swizzle): the same tensors, boxes of 32.
+    plan.tail = !f8 && taps == 9 && a.stride == 1 && rb == 128 && nch >= 2 && a.cin - (nch - 1) * kc <= 32;
+    if (r == CUDA_SUCCESS && plan.tail) {
+        const cuuint64_t dims[4] = {(cuuint64_t)a.cin, (cuuint64_t)a.w, (cuuint64_t)a.h, (cuuint64_t)n_in};
+        const cuuint64_t strides[3] = {a.in_cs * esz, (cuuint64_t)a.w * a.in_cs * esz, (cuuint64_t)a.h * a.w * a.in_cs * esz};
+        const cuuint32_t box[4] = {32, HALO_ROWS, 1, 1};
+        r = enc(&plan.tmA2, dt, 4, const_cast<void *>(a.in), dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r == CUDA_SUCCESS) {
+            const cuuint64_t wdims[3] = {(cuuint64_t)cinp, (cuuint64_t)bn, (cuuint64_t)taps};
+            const cuuint64_t wstrides[2] = {(cuuint64_t)cinp * esz, (cuuint64_t)bn * cinp * esz};
+            const cuuint32_t wbox[3] = {32, (cuuint32_t)bn, 1};
+            r = enc(&plan.tmB2, dt, 3, wdev, wdims, wstrides, wbox, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        }
     }
     if (r != CUDA_SUCCESS) {
         cudaFree(wdev);

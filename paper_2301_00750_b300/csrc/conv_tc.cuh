@@ -19,6 +19,11 @@ struct TcConvPlan {
     bool f8 = false;    // e4m3 operands (kind::f8f6f4) instead of bf16
     CUtensorMap tmA;  // 64-byte aligned type
     CUtensorMap tmB;
+    // stride-1 3x3 BF16 layers whose last 64-channel step holds at most 32 channels: that
+    // step (the tail) is taken as 32 channels with the 64-byte swizzle, through these maps
+    CUtensorMap tmA2;
+    CUtensorMap tmB2;
+    bool tail = false;
     int bn = 0, nch = 0, stride = 1, h = 0, w = 0, ho = 0, wo = 0, n_in = 0, cout = 0;
     int kc = 0, rb = 0;  // channels and bytes of one K step (rb = 32, 64 or 128: the swizzle span)
     int taps = 9;        // 9: 3x3 conv; 1: pointwise 1x1 conv
