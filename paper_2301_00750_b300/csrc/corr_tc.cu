@@ -63,6 +63,7 @@ struct CorrTcLaunch {
     float scale;  // dot product -> cost: 1/C (bf16), s_f^2 / C (e4m3 features with scale s_f)
     float q_out;  // e4m3: 1 / scale of the stored cost volume
     int *err;
+    int rb;       // bytes of channels per step (128, or 64: 32 bf16 channels with the 64-byte swizzle)
 };
 
 template <int R, bool F8>
@@ -101,8 +102,8 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
         // ---- producer: every channel step at once (the whole block fits in shared memory)
         for (int ch = 0; ch < p.nch; ++ch) {
             const uint32_t fb = full0 + 8 * ch;
-            mbar_expect_tx(fb, A_BYTES + (uint32_t)G::NPOS * BK * 2);
-            const int c0 = ch * (F8 ? 2 * BK : BK);  // 128-byte steps: 64 bf16 or 128 e4m3 channels
+            mbar_expect_tx(fb, (uint32_t)(BX * BY + G::NPOS) * (uint32_t)p.rb);
+            const int c0 = ch * (F8 ? p.rb : p.rb / 2);  // a step: rb bytes of e4m3 or bf16 channels
             tma_load_4d(&tmS, fb, smem_u32(sA + ch * A_BYTES), c0, x0, y0, b ? p.img_s[1] : p.img_s[0]);
             tma_load_4d(&tmO, fb, smem_u32(sB + ch * G::B_BYTES), c0, x0 - R, y0 - R, b ? p.img_o[1] : p.img_o[0]);
         }
@@ -116,11 +117,12 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint64_t da = sw128_desc(smem_u32(sA + ch * A_BYTES));
-            const uint64_t db0 = sw128_desc(smem_u32(sB + ch * G::B_BYTES));
-            const uint64_t db1 = sw128_desc(smem_u32(sB + ch * G::B_BYTES + (uint32_t)G::NH * BK * 2));
+            const uint32_t rb = (uint32_t)p.rb;
+            const uint64_t da = sw_desc(smem_u32(sA + ch * A_BYTES), rb);
+            const uint64_t db0 = sw_desc(smem_u32(sB + ch * G::B_BYTES), rb);
+            const uint64_t db1 = sw_desc(smem_u32(sB + ch * G::B_BYTES + (uint32_t)G::NH * rb), rb);
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
+            for (int kk = 0; kk < p.rb / 32; ++kk) {  // 32 bytes of K per MMA
                 const uint32_t acc = (ch | kk) != 0 ? 1u : 0u;
                 umma<F8>(tmem, da + (uint64_t)(kk * 2), db0 + (uint64_t)(kk * 2), idesc, acc);
                 umma<F8>(tmem + (uint32_t)G::NH, da + (uint64_t)(kk * 2), db1 + (uint64_t)(kk * 2), idesc, acc);
@@ -242,16 +244,17 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
 }
 
 bool encode_features(CUtensorMap *map, const void *base, int n, int cs, int h, int w, int c, int box_x, int box_y,
-                     bool f8) {
+                     bool f8, int rb) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return false;
     const cuuint64_t es = f8 ? 1 : 2;
     const cuuint64_t dims[4] = {(cuuint64_t)c, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
     const cuuint64_t strides[3] = {(cuuint64_t)cs * es, (cuuint64_t)w * cs * es, (cuuint64_t)h * w * cs * es};
-    const cuuint32_t box[4] = {(cuuint32_t)(128 / es), (cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+    const cuuint32_t box[4] = {(cuuint32_t)(rb / es), (cuuint32_t)box_x, (cuuint32_t)box_y, 1};
     const cuuint32_t ones[4] = {1, 1, 1, 1};
     return enc(map, f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims, strides, box, ones,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, rb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -279,8 +282,10 @@ bool tc_plan_corr(CorrTcPlan &plan, const void *self, int n_self, int self_cs, c
     if (r < 1 || r > 4) { why = "radius must be 1..4"; return false; }
     if (self_cs % al != 0 || other_cs % al != 0) { why = "pixel strides must be multiples of 16 bytes"; return false; }
     if (reinterpret_cast<uintptr_t>(self) % 16 || reinterpret_cast<uintptr_t>(other) % 16) { why = "misaligned"; return false; }
-    if (!encode_features(&plan.tmS, self, n_self, self_cs, h, w, c, BX, BY, f8) ||
-        !encode_features(&plan.tmO, other, n_other, other_cs, h, w, c, BX + 2 * r, BY + 2 * r, f8)) {
+    // BF16 features of at most 32 channels: 64-byte steps, so no step multiplies zero padding
+    const int rb = !f8 && c <= 32 ? 64 : 128;
+    if (!encode_features(&plan.tmS, self, n_self, self_cs, h, w, c, BX, BY, f8, rb) ||
+        !encode_features(&plan.tmO, other, n_other, other_cs, h, w, c, BX + 2 * r, BY + 2 * r, f8, rb)) {
         why = "tensor map encoding failed";
         return false;
     }
@@ -288,7 +293,8 @@ bool tc_plan_corr(CorrTcPlan &plan, const void *self, int n_self, int self_cs, c
     plan.w = w;
     plan.c = c;
     plan.r = r;
-    plan.nch = f8 ? 1 : (c + BK - 1) / BK;
+    plan.rb = rb;
+    plan.nch = f8 ? 1 : (c + rb / 2 - 1) / (rb / 2);
     plan.f8 = f8;
     plan.err = err;
     plan.enabled = true;
@@ -307,6 +313,7 @@ cudaError_t launch_corr_tc(const CorrTcPlan &plan, int nb, const int img_self[2]
     lp.h = plan.h;
     lp.w = plan.w;
     lp.nch = plan.nch;
+    lp.rb = plan.rb;
     for (int b = 0; b < 2; ++b) {
         lp.img_s[b] = img_self[b < nb ? b : 0];
         lp.img_o[b] = img_other[b < nb ? b : 0];

@@ -17,6 +17,7 @@ struct CorrTcPlan {
     CUtensorMap tmS;
     CUtensorMap tmO;
     int h = 0, w = 0, c = 0, r = 0, nch = 0;
+    int rb = 128;     // bytes of channels per step: 128, or 64 for BF16 features of <= 32 channels
     bool f8 = false;  // e4m3 features (kind::f8f6f4)
     int *err = nullptr;  // device error word (not owned)
 };
