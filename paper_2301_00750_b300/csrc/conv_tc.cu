@@ -69,7 +69,7 @@ struct TcLaunch {
     int out_f32;          // bf16 operands only: write float32 (out_cs in floats) instead of bf16
     int accumulate;       // with out_f32: add to the output instead of overwriting it
     int taps;             // 9: 3x3 conv; 1: pointwise 1x1 conv (the centre tap only)
-    int tail;             // halo kernel: the last channel step is a 32-channel (64-byte) tail
+    int tail;             // halo kernel: the last channel step is a 64-byte tail
 };
 
 // Epilogue shared by the conv kernels: thread r of the CTA owns accumulator row r, i.e.
@@ -715,19 +715,21 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
         r = enc(&plan.tmB, dt, 3, wdev, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     }
-    // A stride-1 3x3 BF16 layer whose last 64-channel step holds at most 32 channels takes
-    // that step as 32 channels (64-byte rows and swizzle): the same tensors, boxes of 32.
-    plan.tail = !f8 && taps == 9 && a.stride == 1 && rb == 128 && nch >= 2 && a.cin - (nch - 1) * kc <= 32;
+    // A stride-1 3x3 layer whose last 128-byte channel step holds at most 64 bytes of
+    // channels (32 bf16, 64 e4m3) takes that step as 64-byte rows with the 64-byte swizzle:
+    // the same tensors, boxes of 64 bytes.
+    plan.tail = taps == 9 && a.stride == 1 && rb == 128 && nch >= 2 && (a.cin - (nch - 1) * kc) * (int)esz <= 64;
+    const cuuint32_t tail_ch = (cuuint32_t)(64 / esz);
     if (r == CUDA_SUCCESS && plan.tail) {
         const cuuint64_t dims[4] = {(cuuint64_t)a.cin, (cuuint64_t)a.w, (cuuint64_t)a.h, (cuuint64_t)n_in};
         const cuuint64_t strides[3] = {a.in_cs * esz, (cuuint64_t)a.w * a.in_cs * esz, (cuuint64_t)a.h * a.w * a.in_cs * esz};
-        const cuuint32_t box[4] = {32, HALO_ROWS, 1, 1};
+        const cuuint32_t box[4] = {tail_ch, HALO_ROWS, 1, 1};
         r = enc(&plan.tmA2, dt, 4, const_cast<void *>(a.in), dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r == CUDA_SUCCESS) {
             const cuuint64_t wdims[3] = {(cuuint64_t)cinp, (cuuint64_t)bn, (cuuint64_t)taps};
             const cuuint64_t wstrides[2] = {(cuuint64_t)cinp * esz, (cuuint64_t)bn * cinp * esz};
-            const cuuint32_t wbox[3] = {32, (cuuint32_t)bn, 1};
+            const cuuint32_t wbox[3] = {tail_ch, (cuuint32_t)bn, 1};
             r = enc(&plan.tmB2, dt, 3, wdev, wdims, wstrides, wbox, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         }

@@ -19,8 +19,8 @@ struct TcConvPlan {
     bool f8 = false;    // e4m3 operands (kind::f8f6f4) instead of bf16
     CUtensorMap tmA;  // 64-byte aligned type
     CUtensorMap tmB;
-    // stride-1 3x3 BF16 layers whose last 64-channel step holds at most 32 channels: that
-    // step (the tail) is taken as 32 channels with the 64-byte swizzle, through these maps
+    // stride-1 3x3 layers whose last 128-byte channel step holds at most 64 bytes: that step
+    // (the tail) is taken as 64-byte rows with the 64-byte swizzle, through these maps
     CUtensorMap tmA2;
     CUtensorMap tmB2;
     bool tail = false;
