@@ -40,7 +40,7 @@ K1_SWEEP = (0.0, 0.25, 0.5, 0.75, 1.0)
 SOLVER_ITERS = 150  # Eq. 8 iterations per frame in the paper's full method
 # DRAM bytes (read + write) of one frame's estimator convs at 1080p BF16, one ncu capture
 # (profiles/estimator_traffic_1080p_bf16.md); valid for the kernels as of that capture
-ESTIMATOR_TRAFFIC_BYTES_BF16 = 678.4e6
+ESTIMATOR_TRAFFIC_BYTES_BF16 = 675.6e6
 SOLVER_FLOPS_PER_PX_ITER = 9  # per channel: neighbour sum (3 adds) and 3 FMAs
 WIDTH, HEIGHT = 1920, 1080
 SPEC = dict(chans=(16, 32, 64, 96, 128), radius=4)
