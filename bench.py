@@ -275,6 +275,12 @@ def time_stream(tc, torch, path, dev_frames, dev_styl, precision, steps, warmup,
                 tc_corr=tc_corr)
 
 
+def pipelined_value(entry, res, n):
+    """Adds the pipelined-mode frames/s of a side configuration (the value is the default mode's)."""
+    if res is not None:
+        entry["pipelined"] = round(n / (res["total_ms"] / 1e3), 3)
+
+
 def e2e_host(tc, torch, path, frames, styl, precision, steps, warmup, scales=None, solver_iters=0, latency=0,
              flow_downscale=1, pipelined=False):
     """End-to-end through the host-buffer entry points: pinned host I_t, P_t in, O_t out per
@@ -385,14 +391,20 @@ def run_ours(args):
         solver = (time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 3, solver_iters=SOLVER_ITERS,
                               scales=scales),
                   time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 2, profile=True,
-                              solver_iters=SOLVER_ITERS, scales=scales))
+                              solver_iters=SOLVER_ITERS, scales=scales),
+                  None if args.sequential else
+                  time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 3, solver_iters=SOLVER_ITERS,
+                              scales=scales, pipelined=True))
     latency = None
     if not args.skip_latency and args.latency == 0:
         # the paper's one-frame-latency form (next frame in Eqs. 2, 3, 6; k1 0.3, k2 0.5)
         n = max(3, args.steps // 4)
         latency = (time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 3, scales=scales, latency=1),
                    time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 3, profile=True,
-                               scales=scales, latency=1))
+                               scales=scales, latency=1),
+                   None if args.sequential else
+                   time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 3, scales=scales, latency=1,
+                               pipelined=True))
     refined = None
     if not args.skip_refine and args.precision != "fp8":
         # the network with the depthwise-separable refinement after the level-2 estimator
@@ -402,7 +414,10 @@ def run_ours(args):
         refined = (time_stream(tc, torch, rpath, dev_frames, dev_styl, args.precision, n, 3,
                                flow_downscale=args.flow_downscale),
                    time_stream(tc, torch, rpath, dev_frames, dev_styl, args.precision, n, 3, profile=True,
-                               flow_downscale=args.flow_downscale))
+                               flow_downscale=args.flow_downscale),
+                   None if args.sequential else
+                   time_stream(tc, torch, rpath, dev_frames, dev_styl, args.precision, n, 3,
+                               flow_downscale=args.flow_downscale, pipelined=True))
     fast = None
     if not args.skip_fast and args.flow_downscale == 1:
         # the paper's fast preset (Table 3): flow on half-size frames, 50 solver iterations
@@ -411,7 +426,10 @@ def run_ours(args):
         fast = (time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 3, scales=fscales,
                             solver_iters=50, flow_downscale=2),
                 time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 3, profile=True,
-                            scales=fscales, solver_iters=50, flow_downscale=2))
+                            scales=fscales, solver_iters=50, flow_downscale=2),
+                None if args.sequential else
+                time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, n, 3, scales=fscales,
+                            solver_iters=50, flow_downscale=2, pipelined=True))
     e2e = e2e_host(tc, torch, path, frames, styl, args.precision, max(3, min(args.steps, 100)), 3, scales=scales,
                    solver_iters=args.solver_iters, latency=args.latency, flow_downscale=args.flow_downscale,
                    pipelined=True)
@@ -513,7 +531,7 @@ def run_ours(args):
         if fp8_pipe is not None:
             line["fp8_e4m3"]["pipelined"] = round(args.steps / (fp8_pipe["total_ms"] / 1e3), 3)
     if solver is not None:
-        sv, svp = solver
+        sv, svp, svq = solver
         n = len(sv["per_frame_ms"])
         ms = svp["profile"]["solver"][0] / n
         line["with_solver"] = {
@@ -528,16 +546,18 @@ def run_ours(args):
                                        / FP32_SIMT_PEAK_TFLOPS, 4),
                          "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2032 MHz"},
             "note": "Eq. 1 by Eq. 8 (eta 0.15, kappa 0.2) after the blend, time-blocked 8 iterations per launch"}
+        pipelined_value(line["with_solver"], svq, n)
     if refined is not None:
-        rt, rtp = refined
+        rt, rtp, rtq = refined
         n = len(rt["per_frame_ms"])
         line["with_refinement"] = {
             "value": round(n / (rt["total_ms"] / 1e3), 3), "unit": UNIT,
             "refine_ms_per_frame": round(rtp["profile"]["refine"][0] / n, 4),
             "note": "network + depthwise-separable refinement (7 layers 128/128/128/96/64/32/2, dilations "
                     "1/2/4/8/16/1/1) on the level-2 flows of both directions"}
+        pipelined_value(line["with_refinement"], rtq, n)
     if fast is not None:
-        ft, ftp = fast
+        ft, ftp, ftq = fast
         n = len(ft["per_frame_ms"])
         pf = sorted(ft["per_frame_ms"])
         line["fast_preset"] = {
@@ -546,13 +566,15 @@ def run_ours(args):
             "stage_ms_per_frame": {k: round(v[0] / n, 4) for k, v in ftp["profile"].items() if v[1]},
             "note": "Table 3's fast preset: flow network on 960x540 2x2-mean frames (flow upsampled x8), "
                     "50 Eq. 8 iterations"}
+        pipelined_value(line["fast_preset"], ftq, n)
     if latency is not None:
-        lt, ltp = latency
+        lt, ltp, ltq = latency
         n = len(lt["per_frame_ms"])
         line["with_next_frame"] = {
             "value": round(n / (lt["total_ms"] / 1e3), 3), "unit": UNIT, "latency_frames": 1,
             "consistency_ms_per_frame": round(ltp["profile"]["consistency"][0] / n, 4),
             "note": "frame t returned with frame t+1: w_n of Eq. 3 (k2 0.5) in Eqs. 2 and 6, k1 0.3"}
+        pipelined_value(line["with_next_frame"], ltq, n)
     if world == 1 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline_oracle()
     print(json.dumps(line), flush=True)
