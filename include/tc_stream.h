@@ -182,8 +182,7 @@ TC_API tc_status tc_process_frame_host_async(tc_stream *s, const float *I_t, con
  * given: tc_process_frame then enqueues frame t on library-owned streams without ordering it
  * on the caller's stream, so the next frame's feature pyramid and two frames' flow
  * estimations run at the same time (the flow network estimates each frame pair on its own;
- * the stream keeps four pyramid slots and two sets of estimator buffers; a network with the
- * refinement estimates one frame at a time).  The inputs must be
+ * the stream keeps four pyramid slots and two sets of estimator and refinement buffers).  The inputs must be
  * valid when tc_process_frame is called and stay unmodified until the frame is done; the
  * outputs are valid after tc_join (the caller's stream then waits for every frame given)
  * or tc_synchronize.  tc_get_flows joins first; tc_flush runs after the frames given.  The

@@ -207,7 +207,7 @@ size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precisi
             total += al(9 * cp * 4) + al(cp * 4) + al(cp * net.ref[k].cout * 4) + al(net.ref[k].cout * 4);
             if (bf) total += al(cp * std::max(16, net.ref[k].cout) * 2);
         }
-        total += al(2 * px2 * dcs * es) + al(2 * px2 * pcs * es);
+        total += al(NSET * 2 * px2 * dcs * es) + al(NSET * 2 * px2 * pcs * es);
     }
     return total;
 }
@@ -363,7 +363,7 @@ struct tc_stream {
     // refinement network (TCW2): per layer the depthwise taps and bias and the pointwise
     // weights in buffer channel order, its tensor-core plan (BF16) or none (CUDA cores);
     // refD holds the depthwise outputs, refP the pointwise ones, both for the two flow
-    // directions at level 2
+    // directions at level 2, one copy per estimator buffer set
     struct RefLayer {
         int cin_p = 0, nin = 0, cout = 0, dil = 1, leaky = 1;
         float *dw = nullptr, *db = nullptr, *pw = nullptr, *pb = nullptr;
@@ -546,10 +546,10 @@ static tc_status build_refine(tc_stream *s) {
     s->refD_cs = dcs;
     s->refP_cs = pcs;
     tc_status r;
-    if ((r = dalloc(s, &s->refD, 2 * px * dcs * sizeof(T))) != TC_OK) return r;
-    if ((r = dalloc(s, &s->refP, 2 * px * pcs * sizeof(T))) != TC_OK) return r;
-    TC_TRY(s, cudaMemset(s->refD, 0, 2 * px * dcs * sizeof(T)), "memset");
-    TC_TRY(s, cudaMemset(s->refP, 0, 2 * px * pcs * sizeof(T)), "memset");
+    if ((r = dalloc(s, &s->refD, NSET * 2 * px * dcs * sizeof(T))) != TC_OK) return r;
+    if ((r = dalloc(s, &s->refP, NSET * 2 * px * pcs * sizeof(T))) != TC_OK) return r;
+    TC_TRY(s, cudaMemset(s->refD, 0, NSET * 2 * px * dcs * sizeof(T)), "memset");
+    TC_TRY(s, cudaMemset(s->refP, 0, NSET * 2 * px * pcs * sizeof(T)), "memset");
     for (int k = 0; k < nl; ++k) {
         const HostSep &H = net.ref[k];
         tc_stream::RefLayer &R = s->ref[k];
@@ -581,8 +581,8 @@ static tc_status build_refine(tc_stream *s) {
             ConvArgs a{s->refD, dcs, 1, B.h, B.w, R.cin_p, 1, B.h, B.w, nullptr, nullptr, last ? 2 : H.cout,
                        last ? nullptr : s->refP, last ? 16 : pcs, H.leaky};
             std::string why;
-            const bool ok = last ? tc_plan_head(R.plan, a, 2, pw, s->dev_err, why, false, 1)
-                                 : tc_plan_conv(R.plan, a, 2, pw, s->dev_err, why, false, 1);
+            const bool ok = last ? tc_plan_head(R.plan, a, 2 * NSET, pw, s->dev_err, why, false, 1)
+                                 : tc_plan_conv(R.plan, a, 2 * NSET, pw, s->dev_err, why, false, 1);
             if (ok) s->tc_layers += 1;
         }
     }
@@ -853,11 +853,8 @@ static ConvFirstArgs first_args(const tc_stream *s, const float *img) {
 
 // The pyramid slot of frame t (see NPYR).
 static inline int pyr_slot(const tc_stream *s, long long t) { return (int)(t % (s->pipelined ? NPYR : 2)); }
-// The estimator buffer set of frame t (a network with the refinement keeps one set: its own
-// buffers are single).
-static inline int est_set(const tc_stream *s, long long t) {
-    return s->pipelined && s->ref.empty() ? (int)(t % NSET) : 0;
-}
+// The estimator buffer set of frame t.
+static inline int est_set(const tc_stream *s, long long t) { return s->pipelined ? (int)(t % NSET) : 0; }
 
 template <typename T>
 static tc_status run_pyramid(tc_stream *s, const float *img, int slot) {
@@ -895,39 +892,42 @@ static tc_status run_pyramid(tc_stream *s, const float *img, int slot) {
 // first reads [x3 | x4 | flow] (the buffer order of cat(flow, x4, x3)), the last adds its
 // two outputs to the flow in place.
 template <typename T>
-static tc_status run_refine(tc_stream *s) {
+static tc_status run_refine(tc_stream *s, int set) {
     if constexpr (sizeof(T) == 1) {
         return fail(s, TC_ERR_UNSUPPORTED, "the refinement network runs in TC_FP32 or TC_BF16 streams");
     } else {
     LevelBufs &B = s->lv[1];
-    T *dec = static_cast<T *>(B.dec);
+    T *dec = dec_of<T>(B, set);
+    float *flow = flow_of(B, set);
     const size_t px = (size_t)B.h * B.w;
+    T *refD = static_cast<T *>(s->refD) + (size_t)set * 2 * px * s->refD_cs;
+    T *refP = static_cast<T *>(s->refP) + (size_t)set * 2 * px * s->refP_cs;
     const int nl = (int)s->ref.size();
     for (int k = 0; k < nl; ++k) {
         tc_stream::RefLayer &R = s->ref[k];
         DwArgs d{};
-        d.in = k == 0 ? static_cast<const void *>(dec + B.off_x3) : s->refP;
+        d.in = k == 0 ? static_cast<const void *>(dec + B.off_x3) : static_cast<const void *>(refP);
         d.in_cs = k == 0 ? B.ctot : s->refP_cs;
         d.nin = R.nin;
-        d.flow = k == 0 ? B.flow : nullptr;
+        d.flow = k == 0 ? flow : nullptr;
         d.n = 2; d.h = B.h; d.w = B.w;
         d.dw = R.dw; d.db = R.db; d.dil = R.dil;
-        d.out = s->refD; d.out_cs = s->refD_cs; d.cp = R.cin_p;
+        d.out = refD; d.out_cs = s->refD_cs; d.cp = R.cin_p;
         TC_LAUNCH_CAT(s, TC_PROF_REFINE, launch_depthwise<T>(d, s->st));
         const bool last = k == nl - 1;
         if (R.plan.enabled) {
-            ConvArgs a{s->refD, s->refD_cs, 2, B.h, B.w, R.cin_p, 1, B.h, B.w, nullptr, R.pb, last ? 2 : R.cout,
-                       last ? nullptr : s->refP, last ? 16 : s->refP_cs, R.leaky};
+            ConvArgs a{refD, s->refD_cs, 2, B.h, B.w, R.cin_p, 1, B.h, B.w, nullptr, R.pb, last ? 2 : R.cout,
+                       last ? nullptr : refP, last ? 16 : s->refP_cs, R.leaky};
             if (last)
-                TC_LAUNCH_CAT(s, TC_PROF_REFINE, launch_conv_tc_head(R.plan, a, B.flow, B.flow, s->st));
+                TC_LAUNCH_CAT(s, TC_PROF_REFINE, launch_conv_tc_head(R.plan, a, flow, flow, s->st));
             else
                 TC_LAUNCH_CAT(s, TC_PROF_REFINE, launch_conv_tc(R.plan, a, s->st));
         } else {
             PwArgs pa{};
-            pa.in = s->refD; pa.in_cs = s->refD_cs; pa.cin = R.cin_p;
+            pa.in = refD; pa.in_cs = s->refD_cs; pa.cin = R.cin_p;
             pa.w = R.pw; pa.b = R.pb; pa.cout = R.cout; pa.leaky = R.leaky;
-            pa.out = last ? nullptr : s->refP; pa.out_cs = s->refP_cs;
-            pa.flow = last ? B.flow : nullptr;
+            pa.out = last ? nullptr : refP; pa.out_cs = s->refP_cs;
+            pa.flow = last ? flow : nullptr;
             pa.npx = 2 * px;
             TC_LAUNCH_CAT(s, TC_PROF_REFINE, launch_pointwise<T>(pa, s->st));
         }
@@ -997,7 +997,7 @@ static tc_status run_estimators(tc_stream *s, int pcur, int pprev, int set) {
             TC_LAUNCH_CAT(s, TC_PROF_HEAD, launch_head<T>(ha, s->st));
         }
     }
-    return s->ref.empty() ? TC_OK : run_refine<T>(s);
+    return s->ref.empty() ? TC_OK : run_refine<T>(s, set);
 }
 
 static tc_status check_stream(tc_stream *s, const char *fn) {
@@ -1324,8 +1324,8 @@ static tc_status process(tc_stream *s, const float *I, const float *P, float *O,
 //   * pyramid t writes slot t % NPYR, last read by the flow estimations of frames t - NPYR
 //     and t - NPYR + 1, and waits for both;
 //   * the flow estimation of frame t waits for pyramid t (pyramid t - 1 came before it on
-//     pst) and for the blend that last read its buffer set's flows (frame t - NSET, or t - 1
-//     with one set), and follows frame t - NSET's estimation on its stream;
+//     pst) and for the blend that last read its buffer set's flows (frame t - NSET), and
+//     follows frame t - NSET's estimation on its stream;
 //   * the blend of frame t waits for its flow estimation and follows frame t - 1's blend.
 // So the next frame's pyramid and NSET frames' flow estimations run at the same time.
 template <typename T>
@@ -1334,7 +1334,7 @@ static tc_status process_pipelined(tc_stream *s, const float *I, const float *P,
     tc_status r;
     const long long t = s->t;
     const int cur = (int)(t & 1), ps = pyr_slot(s, t), set = est_set(s, t), e = (int)(t % NEV);
-    const int nsets = s->ref.empty() ? NSET : 1;
+    const int nsets = NSET;
     const long long out = s->latency ? t - 1 : t;
     if (!s->gst) {
         TC_TRY(s, cudaStreamCreateWithFlags(&s->gst, cudaStreamNonBlocking), "cudaStreamCreate");

@@ -84,6 +84,18 @@ def test_pipelined_fast_preset_and_solver(flow_downscale, solver_iters):
             assert np.array_equal(a[t][k], b[t][k]), (t, k)
 
 
+def test_pipelined_refinement():
+    """The network with the depthwise-separable refinement: its buffers are per set too."""
+    path, _ = weights_file((16, 32, 64, 96, 128), 4, refine=True)
+    frames, styl = _frames(8, seed=15)
+    a, fa = _run(path, frames, styl, "bf16", False)
+    b, fb = _run(path, frames, styl, "bf16", True)
+    for t in range(len(frames)):
+        for k in range(3):
+            assert np.array_equal(a[t][k], b[t][k]), (t, k)
+    assert np.array_equal(fa[0], fb[0]) and np.array_equal(fa[1], fb[1])
+
+
 def test_pipelined_state_errors():
     import torch
     path, _ = weights_file((16, 32, 64, 96, 128), 4)
