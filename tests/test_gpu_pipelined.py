@@ -1,8 +1,8 @@
-"""Pipelined mode (tc_set_pipelined): frame t + 1's feature pyramid runs on a second stream
-while frame t's flows are estimated, with three pyramid slots and the frame split into two
+"""Pipelined mode (tc_set_pipelined): frame t + 1's feature pyramid runs on its own stream
+while earlier frames' flows are estimated, with four pyramid slots, two sets of estimator
+buffers (two estimations in flight) and the frame split into pyramid, estimation and blend
 graphs.  The results must equal the default mode's bit for bit, frame by frame, over enough
-frames that every graph is captured and replayed (t % 6 for the flow estimation and blend,
-t % 3 for the pyramid)."""
+frames that every graph is captured and replayed (t % 4 for each of the three graph kinds)."""
 import numpy as np
 import pytest
 
