@@ -227,7 +227,8 @@ def consistency_controls(step, solver_iters, latency):
 def time_stream(tc, torch, path, dev_frames, dev_styl, precision, steps, warmup, profile=False, scales=None,
                 solver_iters=0, latency=0, flow_downscale=1, pipelined=False):
     """Runs warmup + steps frames through one stream; returns timings (device events).
-    pipelined: tc_set_pipelined (frame t+1's pyramid overlaps frame t's flow estimation);
+    pipelined: tc_set_pipelined (frame t+1's pyramid overlaps the flow estimation of frames t
+    and t-1, each with its own buffer set);
     the timed region then ends with tc_join, and there are no per-frame times."""
     H, W = dev_frames[0].shape[1:]
     s = open_stream(tc, path, W, H, precision, scales, flow_downscale)
@@ -495,8 +496,9 @@ def run_ours(args):
                    "frames_resident": N_FRAMES, "streams_per_gpu": 1,
                    "precision": args.precision, "l2": "per-frame working set > 126 MB L2 (no flush needed)"},
         "mode": ("sequential: each frame ordered on the caller's stream" if args.sequential else
-                 "pipelined (tc_set_pipelined): frame t+1's feature pyramid runs on a second stream during "
-                 "frame t's flow estimation; inputs resident, one tc_join at the end of the timed region"),
+                 "pipelined (tc_set_pipelined): frame t+1's feature pyramid runs on its own stream while "
+                 "two frames' flow estimations run on two more; inputs resident, one tc_join at the end "
+                 "of the timed region"),
         "sequential": {"value": round(args.steps / (seq["total_ms"] / 1e3), 3), "unit": UNIT,
                        "ms_per_step": round(seq["total_ms"] / args.steps, 4)},
         "latency_ms": {"p50": round(per[len(per) // 2], 4), "p99": round(per[min(len(per) - 1, int(0.99 * len(per)))], 4),
