@@ -218,9 +218,9 @@ TC_API long long tc_last_output_frame(const tc_stream *s);
 
 /* CUDA graphs (on by default): from the third frame on, a stream replays one captured graph
  * per slot parity -- every launch of the frame in one cudaGraphLaunch -- after updating the
- * two kernel nodes that read the caller's buffers (in pipelined mode: two graphs per frame,
- * the pyramid's and the rest's).  enable = 0 returns to one launch per
- * kernel.  Waits for the stream.  Per-stage profiling always runs without graphs. */
+ * two kernel nodes that read the caller's buffers (in pipelined mode: three graphs per
+ * frame, its pyramid's, its flow estimation's and its blend's).  enable = 0 returns to one
+ * launch per kernel.  Waits for the stream.  Per-stage profiling always runs without graphs. */
 TC_API tc_status tc_set_graphs(tc_stream *s, int enable);
 
 /* ---- E4M3 calibration --------------------------------------------------------------

@@ -1283,7 +1283,8 @@ static tc_status process(tc_stream *s, const float *I, const float *P, float *O,
     if (s->pipelined) return process_pipelined<T>(s, I, P, O, wc, mask);
     const int cur = (int)(s->t & 1);
     // The first two frames run eagerly (the first has no flow; the second sets every kernel
-    // attribute); later frames replay the graph of their t % NGRAPH.  Profiling runs eagerly.
+    // attribute); later frames replay the graph of their t % 2 (state parity and pyramid
+    // slot), one set for host calls and one for device calls.  Profiling runs eagerly.
     const long long out = s->latency ? s->t - 1 : s->t;
     if (!s->graphs || s->prof || s->t < 2 || s->rec_amax) {
         if ((r = frame_launches<T>(s, I, P, O, wc, mask, cur)) != TC_OK) return r;
