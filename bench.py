@@ -318,6 +318,13 @@ def e2e_host(tc, torch, path, frames, styl, precision, steps, warmup, scales=Non
     return dict(value=steps / dt, h2d=2 * img, d2h=img)
 
 
+def oracle_threads():
+    """Threads of the oracle's OpenMP loops: OMP_NUM_THREADS when set, else (the OpenMP
+    default) the CPUs this process may run on."""
+    v = os.environ.get("OMP_NUM_THREADS", "").split(",")[0].strip()
+    return int(v) if v.isdigit() and int(v) > 0 else len(os.sched_getaffinity(0))
+
+
 def cpu_baseline_oracle(seed=0):
     """The FP64 oracle timed on this host's cores on a bounded sample: one full 1080p frame
     step (pyramid of frame t, both flow directions, consistency) after frame t-1."""
@@ -333,7 +340,7 @@ def cpu_baseline_oracle(seed=0):
     t0 = time.perf_counter()
     st.step(f1, p1)
     dt = time.perf_counter() - t0
-    return dict(value=1.0 / dt, unit=UNIT, cores=os.cpu_count(), kind="oracle",
+    return dict(value=1.0 / dt, unit=UNIT, cores=oracle_threads(), kind="oracle",
                 sample=f"one 1920x1080 frame step of the FP64 oracle (pyramid, both flow directions, "
                        f"consistency), {dt:.1f} s")
 
@@ -487,14 +494,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp8": "e4m3", "fp32": "f32"}.get(args.precision, args.precision),
         "data": "synthetic (seeded 1080p sequence, He-init weights)",
-        "config": {"workload": "1920x1080 RGB stream, lite flow net 5 levels 16/32/64/96/128, radius 4, "
-                               "decoder 128/96/64/32/2, both flow directions + fused consistency, "
-                               + ("k1 swept {0,.25,.5,.75,1}" if not args.latency else
-                                  "k1 0.3 and k2 0.5 with the next frame (one frame of latency)")
-                               + (f", then {args.solver_iters} Eq. 8 solver iterations" if args.solver_iters else "")
-                               + (", flow network on 2x2-mean half-size frames" if args.flow_downscale == 2 else ""),
-                   "frames_resident": N_FRAMES, "streams_per_gpu": 1,
-                   "precision": args.precision, "l2": "per-frame working set > 126 MB L2 (no flush needed)"},
+        "config": workload_config(args),
         "mode": ("sequential: each frame ordered on the caller's stream" if args.sequential else
                  "pipelined (tc_set_pipelined): frame t+1's feature pyramid runs on its own stream while "
                  "two frames' flow estimations run on two more; inputs resident, one tc_join at the end "
@@ -594,11 +594,26 @@ def measured_peaks():
 
 # ----------------------------------------------------------------------------- reference arm
 
+def workload_config(args):
+    """The line's `config`: the workload, named by what it is and its sizes."""
+    return {"workload": "1920x1080 RGB stream, lite flow net 5 levels 16/32/64/96/128, radius 4, "
+                        "decoder 128/96/64/32/2, both flow directions + fused consistency, "
+                        + ("k1 swept {0,.25,.5,.75,1}" if not args.latency else
+                           "k1 0.3 and k2 0.5 with the next frame (one frame of latency)")
+                        + (f", then {args.solver_iters} Eq. 8 solver iterations" if args.solver_iters else "")
+                        + (", flow network on 2x2-mean half-size frames" if args.flow_downscale == 2 else ""),
+            "frames_resident": N_FRAMES, "streams_per_gpu": 1,
+            "precision": args.precision, "l2": "per-frame working set > 126 MB L2 (no flush needed)"}
+
+
 def run_reference(args):
-    """The FP64 oracle on this host's cores, same workload family; each step is a bounded
-    sample: a 1920x128 band of the sequence (two frames, pyramid + both flows +
-    consistency), reported as 1080p-frame equivalents per second."""
+    """The FP64 oracle on this host's cores, with the main arm's workload and settings (the
+    k1 sweep or one frame of latency, solver iterations, the flow downscale).  Each step is a
+    bounded sample: one frame step of a 1920x128 band of the sequence (pyramid, both flows,
+    consistency, the solver when on), reported as 1080p-frame equivalents per second.  Under
+    torchrun rank 0 alone runs it."""
     rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
     import oracle
@@ -607,30 +622,37 @@ def run_reference(args):
     net = oracle.net_from_layers(spec.levels, spec.radius, spec.chans, spec.decoder, layers)
     bh = 128
     seq = synth.Sequence(width=WIDTH, height=bh, seed=0)
-    frames = [seq.frame(t) for t in range(2)]
+    nf = 3 if args.latency else 2
+    frames = [seq.frame(t) for t in range(nf)]
     styl = [seq.stylized(t, f) for t, f in enumerate(frames)]
 
-    def one_step():
-        st = oracle.Stream(net, k1=0.5)
-        st.step(frames[0], styl[0])
+    def one_step(i):
+        # the timed call computes one output frame: the flows of its pair and the blend
+        c = consistency_controls(i, args.solver_iters, args.latency)
+        st = oracle.Stream(net, k1=c["k1"], k2=c.get("k2", 0.5), solver_iters=c["solver_iters"],
+                           latency=args.latency, flow_downscale=args.flow_downscale)
+        for t in range(nf - 1):
+            st.step(frames[t], styl[t])
         t0 = time.perf_counter()
-        st.step(frames[1], styl[1])
+        st.step(frames[nf - 1], styl[nf - 1])
         return time.perf_counter() - t0
 
-    for _ in range(args.warmup):
-        one_step()
-    times = [one_step() for _ in range(args.steps)]
+    for i in range(args.warmup):
+        one_step(i)
+    times = [one_step(i) for i in range(args.steps)]
     frac = (WIDTH * bh) / (WIDTH * HEIGHT)
     total = sum(times)
     value = args.steps * frac / total
     sample = f"per step: one frame step of a 1920x{bh} band ({frac:.4f} of a 1080p frame), FP64 oracle"
+    config = workload_config(args)
+    config["precision"] = "f64 (oracle)"
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": 1,
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total * 1e3 / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": "1920x1080 stream (1920x128 bands), same network"},
-        "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": sample},
+        "data": "synthetic (seeded sequence, He-init weights)", "config": config,
+        "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+                         "sample": sample + "; one host process (rank 0)"},
         "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
