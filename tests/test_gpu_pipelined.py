@@ -96,6 +96,48 @@ def test_pipelined_refinement():
     assert np.array_equal(fa[0], fb[0]) and np.array_equal(fa[1], fb[1])
 
 
+def test_pipelined_1080p_bf16_matches_default_and_oracle():
+    """The configuration the benchmark times: 1920x1080, the 5-level r = 4 network, BF16,
+    pipelined mode with CUDA graphs (frame 2 is captured and replayed).  Every frame's outputs
+    equal the default mode's bit for bit, and the flows of the last pair match the FP64
+    oracle within the BF16 bound of the stream tests: 0.05 px or 2 u sqrt(layers) of the mean
+    flow (u = 2^-9, 35 conv layers on the path to the flow)."""
+    import oracle
+    import torch
+    path, net = weights_file((16, 32, 64, 96, 128), 4)
+    seq = synth.Sequence(seed=0)
+    frames = [seq.frame(t) for t in range(3)]
+    styl = [seq.stylized(t, f) for t, f in enumerate(frames)]
+    _, h, w = frames[0].shape
+    dI, dP = [to_dev(I) for I in frames], [to_dev(P) for P in styl]
+    res = []
+    for pipelined in (False, True):
+        s = tc.Stream(w, h, "bf16", weights_path=path)
+        s.set_pipelined(pipelined)
+        outs = [(torch.empty((3, h, w), device="cuda"), torch.empty((h, w), device="cuda"),
+                 torch.empty((h, w), device="cuda", dtype=torch.uint8)) for _ in frames]
+        for t in range(len(frames)):
+            s.set_consistency(k1=(0.0, 0.5, 1.0)[t])
+            s.process_frame(dI[t], dP[t], *outs[t])
+        Fb, Ff = torch.empty((2, h, w), device="cuda"), torch.empty((2, h, w), device="cuda")
+        s.get_flows(Fb, Ff)
+        s.join()
+        torch.cuda.synchronize()
+        res.append(([tuple(to_np(x) for x in o) for o in outs], (to_np(Fb), to_np(Ff))))
+        s.destroy()
+    (a, fa), (b, fb) = res
+    for t in range(len(frames)):
+        for k in range(3):
+            assert np.array_equal(a[t][k], b[t][k]), (t, k)
+    assert np.array_equal(fa[0], fb[0]) and np.array_equal(fa[1], fb[1])
+    ref_b, ref_f = oracle.flow_pair(net, frames[2], frames[1])
+    eb, ef = oracle.epe(fb[0], ref_b), oracle.epe(fb[1], ref_f)
+    mag = float(np.sqrt((ref_b ** 2).sum(0)).mean())
+    bound = max(0.05, 2 * 2.0 ** -9 * np.sqrt(35) * mag)
+    print(f"1080p BF16 pipelined EPE vs FP64 oracle: Fb {eb:.4f} px, Ff {ef:.4f} px (bound {bound:.4f})")
+    assert eb <= bound and ef <= bound, (eb, ef, bound)
+
+
 def test_pipelined_state_errors():
     import torch
     path, _ = weights_file((16, 32, 64, 96, 128), 4)
