@@ -30,6 +30,10 @@
  * Precision: TC_FP32 runs every stage in float32.  TC_BF16 runs the convolutions and the
  * correlation with bfloat16 operands and float32 accumulation; flow coordinates, feature
  * warp interpolation weights, the mask thresholds and the consistency step stay float32.
+ * TC_FP16 is TC_BF16 with IEEE half (11 significant bits instead of 8) for the weights and
+ * the stored activations: the same tensor-core kernels and rate, about a quarter of
+ * TC_BF16's deviation from the float32 flows.  Activations must stay below 65504 in
+ * magnitude (the network's are O(10)); tiny ones lose relative precision below 6.1e-5.
  * TC_FP8_E4M3 stores every network activation as e4m3 with one float scale per activation
  * segment (see tc_set_fp8_scales) and every weight as e4m3 with one scale per output
  * channel; the products accumulate in float32 on the tensor cores.  The flows, the
@@ -66,7 +70,7 @@ typedef enum {
     TC_ERR_UNSUPPORTED = 8    /* the request is valid but not built in this library */
 } tc_status;
 
-typedef enum { TC_FP32 = 0, TC_BF16 = 1, TC_FP8_E4M3 = 2 } tc_precision;
+typedef enum { TC_FP32 = 0, TC_BF16 = 1, TC_FP8_E4M3 = 2, TC_FP16 = 3 } tc_precision;
 
 /* Consistency controls (Sec. 3.1 "Consistency Control Modes", values of Sec. 4.2).
  *   k1      upper clamp of w_p (Eq. 3); the global/local proportion of A_t.  [0, 1]
@@ -96,8 +100,8 @@ typedef struct {
 
 /* Stream description.
  *   width, height   frame size in pixels, each >= 2^levels of the network.
- *   precision       TC_FP32, TC_BF16 or TC_FP8_E4M3 (the latter processes frames only
- *                   after tc_set_fp8_scales).
+ *   precision       TC_FP32, TC_BF16, TC_FP16 or TC_FP8_E4M3 (the latter processes frames
+ *                   only after tc_set_fp8_scales).
  *   weights_path    path of a 'TCW1' weight file, or NULL to use weights_blob.
  *   weights_blob    host pointer to the same bytes as such a file (copied at creation).
  * The weight file fixes the number of pyramid levels, the channel counts and the
@@ -111,7 +115,8 @@ typedef struct {
  * depthwise 3x3 conv with that dilation (zero padding, bias, no activation) and a pointwise
  * 1x1 conv (bias, LeakyReLU if leaky); the first reads cat(flow, x4, x3) of the level-2
  * estimator (cin = 2 + decoder[3] + decoder[2]), the last has cout = 2, no activation, and
- * is added to the level-2 flow.  Refinement networks run in TC_FP32 and TC_BF16 streams.
+ * is added to the level-2 flow.  Refinement networks run in TC_FP32, TC_BF16 and TC_FP16
+ * streams.
  *   flow_downscale  0 or 1: the flow network runs on the frames as given.  2: it runs on the
  *                   frames downscaled by 2 (the mean of each 2 x 2 block, the last row and
  *                   column replicated for odd sizes) and its final flow is upsampled x8
@@ -231,7 +236,7 @@ TC_API tc_status tc_set_graphs(tc_stream *s, int enable);
  * tc_activation_segments(s) = 3L + 6(L-1); 0 for s == NULL. */
 TC_API int tc_activation_segments(const tc_stream *s);
 
-/* TC_FP32 / TC_BF16 streams: enable != 0 clears the record and from then on folds the
+/* TC_FP32 / TC_BF16 / TC_FP16 streams: enable != 0 clears the record and from then on folds the
  * largest |value| of every activation segment of every processed frame into it (frames run
  * without graphs while recording).  enable = 0 stops recording and keeps the record.
  * Errors: TC_ERR_INVALID_ARG for a TC_FP8_E4M3 stream. */
@@ -308,8 +313,9 @@ TC_API tc_status tc_get_profile(tc_stream *s, double *ms, long long *launches, i
  * Single-stage entry points.  Each runs one stage of the path on caller-owned device
  * buffers, enqueued on cuda_stream, and returns without waiting.  Feature maps are NHWC
  * float32 (n, h, w, c) contiguous; flows are (n, h, w, 2) float32 (u, v interleaved).
- * `precision` selects the arithmetic: TC_FP32, or TC_BF16 (inputs rounded to bfloat16
- * on load, float32 accumulation, float32 outputs).  These allocate temporary device
+ * `precision` selects the arithmetic: TC_FP32, or TC_BF16 / TC_FP16 (inputs rounded to
+ * bfloat16 / half on load, float32 accumulation, outputs rounded to the same type and
+ * returned as float32).  These allocate temporary device
  * memory for reformatted weights where noted and free it before returning.
  * ---------------------------------------------------------------------------------- */
 
@@ -317,7 +323,8 @@ TC_API tc_status tc_get_profile(tc_stream *s, double *ms, long long *launches, i
  * (Sec. 3.2 pyramid and estimator layers).  in (n, h, w, cin); w_oihw, bias: HOST float32
  * (cout, cin, 3, 3) and (cout); out (n, (h-1)/stride+1, (w-1)/stride+1, cout).
  * Allocates temporary device memory for the weights, waits for completion.  cin, cout >= 1.
- * With TC_BF16 eligible layers run on the tensor cores (see tc_op_last_used_tensor_cores).
+ * With TC_BF16 or TC_FP16 eligible layers run on the tensor cores (see
+ * tc_op_last_used_tensor_cores).
  * TC_FP8_E4M3 (tensor cores only; cout <= 128, else TC_ERR_UNSUPPORTED): the input is
  * rounded to e4m3 as given (activation scale 1), each output channel's weights to e4m3
  * after dividing by s_o = max |w[o]| / 448, the products accumulate in float32, and
@@ -327,9 +334,9 @@ TC_API tc_status tc_op_conv3x3(tc_precision precision, const float *in, int n, i
                         float *out, void *cuda_stream);
 
 /* 1 if the last successful tc_op_conv3x3 or tc_op_correlation in this process ran on the
- * tensor cores, else 0.  TC_BF16 convs with cin a multiple of 8 and cout a multiple of 16 up
- * to 128, and TC_BF16 correlations with c a multiple of 8 up to 128, do; TC_FP8_E4M3 ones
- * always do. */
+ * tensor cores, else 0.  TC_BF16 / TC_FP16 convs with cin a multiple of 8 and cout a
+ * multiple of 16 up to 128, and TC_BF16 / TC_FP16 correlations with c a multiple of 8 up to
+ * 128, do; TC_FP8_E4M3 ones always do. */
 TC_API int tc_op_last_used_tensor_cores(void);
 
 /* Cost volume (Sec. 3.2): out[n][y][x][k] = LeakyReLU((1/c) sum_ch f1[n][y][x][ch] *
@@ -359,8 +366,8 @@ TC_API tc_status tc_op_upsample_flow(const float *flow, int n, int h, int w, int
  * conv.  in: device (n, h, w, cin) float32 NHWC, cin a multiple of 8 (<= 256); dw (cin, 3, 3),
  * db (cin), pw (cout, cin), pb (cout): host float32; cout a multiple of 8 (<= 256) written to
  * out (n, h, w, cout), or cout = 2 (the refinement's last layer, no activation) written as
- * float pairs.  precision TC_FP32 (CUDA cores) or TC_BF16 (activations rounded to bfloat16,
- * pointwise conv on the tensor cores when eligible).  Allocates temporaries and waits. */
+ * float pairs.  precision TC_FP32 (CUDA cores) or TC_BF16 / TC_FP16 (activations rounded
+ * to bfloat16 / half, pointwise conv on the tensor cores when eligible).  Allocates temporaries and waits. */
 TC_API tc_status tc_op_sepconv(tc_precision precision, const float *in, int n, int h, int w, int cin,
                                const float *dw, const float *db, const float *pw, const float *pb, int cout,
                                int dil, int leaky, float *out, void *cuda_stream);
@@ -419,7 +426,7 @@ TC_API size_t tc_stream_device_bytes(const tc_stream *s);
 typedef struct tc_server tc_server;
 
 typedef struct {
-    tc_precision precision;          /* TC_FP32 or TC_BF16 for every stream */
+    tc_precision precision;          /* TC_FP32, TC_BF16 or TC_FP16 for every stream */
     const char *weights_path;        /* TCW1 file, or NULL and weights_blob (copied) */
     const void *weights_blob;
     size_t weights_bytes;

@@ -18,6 +18,12 @@ reading implemented here, and checked against the library's E4M3 path by the tes
 * The feature warp and the cost volume requantise their outputs: the warped features with
   the scale of the features they warp, the cost volume with its own scale.
 
+The 16-bit operand formats are modelled too (``round16``, ``flow_pair_16``): the weights
+and/or every stored activation (pyramid outputs, warped features, cost volume, up-flow,
+x1..x4) rounded to bfloat16 or IEEE half, the rest in FP64.  This is an attribution tool
+for the precision variants (which rounding moves the flows how far), not a model of a
+kernel's exact arithmetic.
+
 Everything else is the network of ``oracle.flow_from_pyramids`` (Sec. 3.2), composed here
 in Python from the same C primitives; with ``scales=None`` the composition reproduces
 ``oracle.flow_from_pyramids`` (a test pins that), and it can record the amax of every
@@ -168,3 +174,70 @@ def scales_from_amax(amax):
     """E4M3 scales amax / 448 (1 for a segment that stayed zero)."""
     amax = np.asarray(amax, np.float64)
     return np.where(amax > 0, amax / E4M3_MAX, 1.0)
+
+
+# ----------------------------------------------------------------------------- 16-bit formats
+
+def round16(a, fmt):
+    """Nearest value of the 16-bit format ("bf16": 8 significant bits, "fp16": IEEE half with
+    subnormals), ties to even, as float64.  Values are first rounded to float32 (the
+    library's storage of a float), then to the format."""
+    a32 = np.ascontiguousarray(a, np.float32)
+    if fmt == "fp16":
+        with np.errstate(over="ignore"):  # beyond 65504 -> inf, as the conversion defines
+            return a32.astype(np.float16).astype(np.float64)
+    if fmt != "bf16":
+        raise ValueError(fmt)
+    u = a32.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+class _R16(_Q):
+    """Rounds weights and/or activations to a 16-bit format (see round16)."""
+
+    def __init__(self, fmt, weights=True, activations=True):
+        super().__init__()
+        self.fmt, self.w, self.a = fmt, weights, activations
+
+    def act(self, x, seg):
+        return round16(x, self.fmt) if self.a else x
+
+    def conv(self, x, L, segs, stride=1):
+        w = round16(L["w"], self.fmt) if self.w else L["w"]
+        return conv3x3(x, w, L["b"], stride=stride, leaky=bool(L["leaky"]))
+
+
+def _flow_r16(net: Net, feat_self, feat_other, hp, wp, q: _R16):
+    """flow_q with the warped features, cost volume and up-flow rounded by q as well."""
+    prev = None
+    for l in range(net.levels, 1, -1):
+        lh, lw = hp >> l, wp >> l
+        E = net.layers[3 * net.levels + 5 * (net.levels - l):][:5]
+        fs, fo = feat_self[l - 1], feat_other[l - 1]
+        if prev is None:
+            up = np.zeros((2, lh, lw))
+            f2w = fo
+        else:
+            up = upsample_flow(prev, 2)
+            f2w = q.act(warp(fo, up, zero_outside=True)[0], None)
+        x0 = np.concatenate([q.act(correlation(fs, f2w, net.radius), None), fs, q.act(up, None)], 0)
+        x1 = q.act(q.conv(x0, E[0], None), None)
+        x2 = q.act(q.conv(x1, E[1], None), None)
+        x3 = q.act(q.conv(x2, E[2], None), None)
+        x4 = q.act(q.conv(np.concatenate([x3, x2], 0), E[3], None), None)
+        prev = up + q.conv(np.concatenate([x4, x3], 0), E[4], None)
+    return upsample_flow(prev, 4)
+
+
+def flow_pair_16(net: Net, I_a, I_b, fmt, weights=True, activations=True):
+    """F_{a->b} and F_{b->a} with the weights and/or the stored activations rounded to the
+    16-bit format fmt; flows, the residual base and the head's output stay FP64."""
+    _, h, w = I_a.shape
+    hp, wp = padded_size(h, w, net.levels)
+    q = _R16(fmt, weights, activations)
+    pa = pyramid_q(net, pad_replicate(I_a, hp, wp), q)
+    pb = pyramid_q(net, pad_replicate(I_b, hp, wp), q)
+    fab = _flow_r16(net, pa, pb, hp, wp, q)[:, :h, :w]
+    fba = _flow_r16(net, pb, pa, hp, wp, q)[:, :h, :w]
+    return np.ascontiguousarray(fab), np.ascontiguousarray(fba)

@@ -24,7 +24,7 @@ TC_OK, TC_ERR_INVALID_ARG, TC_ERR_OOM, TC_ERR_CUDA, TC_ERR_BUSY, TC_ERR_TIMEOUT,
     TC_ERR_UNSUPPORTED = range(9)
 _STATUS = ["TC_OK", "TC_ERR_INVALID_ARG", "TC_ERR_OOM", "TC_ERR_CUDA", "TC_ERR_BUSY", "TC_ERR_TIMEOUT",
            "TC_ERR_STATE", "TC_ERR_IO", "TC_ERR_UNSUPPORTED"]
-PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2}
+PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2, "fp16": 3}
 
 EXPORTED = ["tc_default_consistency", "tc_create_stream", "tc_set_consistency", "tc_process_frame",
             "tc_process_frame_host", "tc_get_flows", "tc_destroy", "tc_last_error", "tc_last_launch_count",
@@ -271,7 +271,7 @@ class Stream:
         return _lib.tc_activation_segments(self._h)
 
     def set_amax_recording(self, enable: bool):
-        """FP32/BF16 streams: record the largest |activation| of every segment from now on."""
+        """FP32/BF16/FP16 streams: record the largest |activation| of every segment from now on."""
         _check(_lib.tc_set_amax_recording(self._h, int(bool(enable))), self._h)
 
     def get_amax(self) -> np.ndarray:

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -33,14 +34,16 @@ inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t
     return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
-// Activation storage types: float (TC_FP32) and bfloat16 (TC_BF16).
+// Activation storage types: float (TC_FP32), bfloat16 (TC_BF16) and IEEE half (TC_FP16).
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 template <typename T> __device__ __forceinline__ T from_f(float v);
 template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
 template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) {
     return __float2bfloat16_rn(v);
 }
+template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
 
 // E4M3 activations hold the value divided by a per-tensor scale; the kernels here move the
 // scaled codes (warps interpolate them, copies copy them) and the scale is applied where the
@@ -57,6 +60,12 @@ __device__ __forceinline__ float4 ld4(const __nv_bfloat16 *p) {
     float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
     return make_float4(fa.x, fa.y, fb.x, fb.y);
 }
+__device__ __forceinline__ float4 ld4(const __half *p) {
+    uint2 u = *reinterpret_cast<const uint2 *>(p);
+    const float2 fa = __half22float2(*reinterpret_cast<__half2 *>(&u.x));
+    const float2 fb = __half22float2(*reinterpret_cast<__half2 *>(&u.y));
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
 __device__ __forceinline__ float4 ld4(const __nv_fp8_e4m3 *p) {
     const __nv_fp8x4_e4m3 q = *reinterpret_cast<const __nv_fp8x4_e4m3 *>(p);
     return float4(q);
@@ -67,6 +76,14 @@ __device__ __forceinline__ void st4(__nv_fp8_e4m3 *p, float4 v) {
 __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 __device__ __forceinline__ void st4(__nv_bfloat16 *p, float4 v) {
     __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    uint2 u;
+    u.x = *reinterpret_cast<uint32_t *>(&a);
+    u.y = *reinterpret_cast<uint32_t *>(&b);
+    *reinterpret_cast<uint2 *>(p) = u;
+}
+
+__device__ __forceinline__ void st4(__half *p, float4 v) {
+    __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
     uint2 u;
     u.x = *reinterpret_cast<uint32_t *>(&a);
     u.y = *reinterpret_cast<uint32_t *>(&b);

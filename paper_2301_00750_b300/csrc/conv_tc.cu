@@ -70,6 +70,7 @@ struct TcLaunch {
     int accumulate;       // with out_f32: add to the output instead of overwriting it
     int taps;             // 9: 3x3 conv; 1: pointwise 1x1 conv (the centre tap only)
     int tail;             // halo kernel: the last channel step is a 64-byte tail
+    int f16;              // 16-bit operands and outputs are IEEE half instead of bfloat16
 };
 
 // Epilogue shared by the conv kernels: thread r of the CTA owns accumulator row r, i.e.
@@ -147,16 +148,16 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, const TcLaunch &p, 
                     q.w = pack_e4m3x4(v[12] * p.q_out, v[13] * p.q_out, v[14] * p.q_out, v[15] * p.q_out);
                     *reinterpret_cast<uint4 *>(static_cast<uint8_t *>(p.out) + pix * p.out_cs + c0) = q;
                 } else {
-                    __nv_bfloat16 *dst = static_cast<__nv_bfloat16 *>(p.out) + pix * p.out_cs;
+                    uint16_t *dst = static_cast<uint16_t *>(p.out) + pix * p.out_cs;  // bf16 or half
                     uint4 lo, hi;
-                    lo.x = pack_bf16x2(v[0], v[1]);
-                    lo.y = pack_bf16x2(v[2], v[3]);
-                    lo.z = pack_bf16x2(v[4], v[5]);
-                    lo.w = pack_bf16x2(v[6], v[7]);
-                    hi.x = pack_bf16x2(v[8], v[9]);
-                    hi.y = pack_bf16x2(v[10], v[11]);
-                    hi.z = pack_bf16x2(v[12], v[13]);
-                    hi.w = pack_bf16x2(v[14], v[15]);
+                    lo.x = pack16x2(p.f16, v[0], v[1]);
+                    lo.y = pack16x2(p.f16, v[2], v[3]);
+                    lo.z = pack16x2(p.f16, v[4], v[5]);
+                    lo.w = pack16x2(p.f16, v[6], v[7]);
+                    hi.x = pack16x2(p.f16, v[8], v[9]);
+                    hi.y = pack16x2(p.f16, v[10], v[11]);
+                    hi.z = pack16x2(p.f16, v[12], v[13]);
+                    hi.w = pack16x2(p.f16, v[14], v[15]);
                     *reinterpret_cast<uint4 *>(dst + c0) = lo;
                     *reinterpret_cast<uint4 *>(dst + c0 + 8) = hi;
                 }
@@ -241,7 +242,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
     } else if (threadIdx.x == 32) {
         // ---- MMA issuer
-        constexpr uint32_t idesc = F8 ? idesc_e4m3(BM, BN) : idesc_bf16(BM, BN);
+        const uint32_t idesc = F8 ? idesc_e4m3(BM, BN) : (p.f16 ? idesc_f16(BM, BN) : idesc_bf16(BM, BN));
         for (int ks = 0; ks < nk; ++ks) {
             const int s = ks % STAGES;
             if (!mbar_wait(full0 + 8 * s, (uint32_t)(ks / STAGES) & 1u, p.err, ERR_MMA)) break;
@@ -366,7 +367,7 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
         }
     } else if (threadIdx.x == 32) {
         // ---- MMA issuer
-        constexpr uint32_t idesc = F8 ? idesc_e4m3(BM, BN) : idesc_bf16(BM, BN);
+        const uint32_t idesc = F8 ? idesc_e4m3(BM, BN) : (p.f16 ? idesc_f16(BM, BN) : idesc_bf16(BM, BN));
         bool fine = true;
         for (int g = 0; g < ng && fine; ++g) {
             const int sa = g % HALO_SA;
@@ -499,7 +500,7 @@ conv_tc_rows_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
         }
     } else if (warp == 5 && lane == 0) {
         // ---- MMA issuer
-        constexpr uint32_t idesc = F8 ? idesc_e4m3(BM, BN) : idesc_bf16(BM, BN);
+        const uint32_t idesc = F8 ? idesc_e4m3(BM, BN) : (p.f16 ? idesc_f16(BM, BN) : idesc_bf16(BM, BN));
         bool fine = mbar_wait(wfull, 0, p.err, ERR_MMA);
         for (int r = 0; r < nrows && fine; ++r) {
             const int b = r & 1;
@@ -627,7 +628,8 @@ void TcConvPlan::release() {
 }
 
 bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vector<float> &wk_simt, int *err,
-                  std::string &why, bool f8, int taps) {
+                  std::string &why, bool f8, int taps, bool f16) {
+    if (f8) f16 = false;
     plan.enabled = false;
     plan.head = false;
     if (taps != 9 && (taps != 1 || a.stride != 1)) { why = "taps must be 9, or 1 at stride 1"; return false; }
@@ -651,8 +653,8 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
     const int nch = (a.cin + kc - 1) / kc, cinp = nch * kc;
     const CUtensorMapSwizzle swz = rb == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
                                             : (rb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);
-    // Packed weights [taps][cout][cinp] (zero beyond cin): bfloat16, or e4m3 with one scale
-    // per output channel (amax / 448 over its taps x cin weights).
+    // Packed weights [taps][cout][cinp] (zero beyond cin): bfloat16 or half, or e4m3 with
+    // one scale per output channel (amax / 448 over its taps x cin weights).
     std::vector<uint8_t> pk((size_t)taps * bn * cinp * esz, 0);
     std::vector<float> ws(bn, 1.f);
     if (f8) {
@@ -669,6 +671,9 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
                 const size_t idx = ((size_t)tap * bn + o) * cinp + c;
                 if (f8) {
                     pk[idx] = (uint8_t)__nv_cvt_float_to_fp8(v / ws[o], __NV_SATFINITE, __NV_E4M3);
+                } else if (f16) {
+                    const __half b = __float2half_rn(v);
+                    memcpy(&pk[2 * idx], &b, 2);
                 } else {
                     const __nv_bfloat16 b = __float2bfloat16_rn(v);
                     memcpy(&pk[2 * idx], &b, 2);
@@ -690,7 +695,8 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
         why = "weight upload failed";
         return false;
     }
-    const CUtensorMapDataType dt = f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const CUtensorMapDataType dt = f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                      : (f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
     const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
     CUresult r;
     if (a.stride == 1) {
@@ -747,6 +753,7 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
     plan.kc = kc;
     plan.rb = rb;
     plan.f8 = f8;
+    plan.f16 = f16;
     plan.stride = a.stride;
     plan.h = a.h;
     plan.w = a.w;
@@ -764,7 +771,7 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
 }
 
 bool tc_plan_head(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vector<float> &wk_simt, int *err,
-                  std::string &why, bool f8, int taps) {
+                  std::string &why, bool f8, int taps, bool f16) {
     if (a.cout > 16) { why = "head has more than 16 outputs"; return false; }
     std::vector<float> wk16((size_t)taps * a.cin * 16, 0.f);
     for (size_t k = 0; k < (size_t)taps * a.cin; ++k)
@@ -772,7 +779,7 @@ bool tc_plan_head(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
     ConvArgs a16 = a;
     a16.cout = 16;
     a16.out_cs = 16;  // not used by the head epilogue
-    if (!tc_plan_conv(plan, a16, n_in, wk16, err, why, f8, taps)) return false;
+    if (!tc_plan_conv(plan, a16, n_in, wk16, err, why, f8, taps, f16)) return false;
     plan.head = true;
     plan.cout = a.cout;
     return true;
@@ -790,7 +797,7 @@ cudaError_t launch_conv_tc_head(const TcConvPlan &plan, const ConvArgs &a, const
     int img_off = 0;
     if (!plan.enabled || !plan.head || !image_offset(plan, a, &img_off)) return cudaErrorInvalidValue;
     TcLaunch lp{plan.nch, plan.kc, plan.rb, plan.stride, plan.ho, plan.wo, img_off, nullptr, 0, a.bias, 0, plan.err,
-                flow, up, plan.wscale, 1.f, 0, 0, plan.taps};
+                flow, up, plan.wscale, 1.f, 0, 0, plan.taps, 0, plan.f16 ? 1 : 0};
     return plan.f8 ? launch_bn<16, true, true>(plan, lp, a.n, st) : launch_bn<16, true, false>(plan, lp, a.n, st);
 }
 
@@ -814,7 +821,7 @@ cudaError_t launch_conv_tc(const TcConvPlan &plan, const ConvArgs &a, cudaStream
     if (!plan.enabled || plan.head || !image_offset(plan, a, &img_off)) return cudaErrorInvalidValue;
     if (reinterpret_cast<uintptr_t>(a.out) % 16 != 0 || a.out_cs % (plan.f8 ? 16 : 8) != 0) return cudaErrorInvalidValue;
     TcLaunch lp{plan.nch, plan.kc, plan.rb, plan.stride, plan.ho, plan.wo, img_off, a.out, a.out_cs, a.bias, a.leaky,
-                plan.err, nullptr, nullptr, plan.wscale, a.q_out, 0, 0, plan.taps};
+                plan.err, nullptr, nullptr, plan.wscale, a.q_out, 0, 0, plan.taps, 0, plan.f16 ? 1 : 0};
     return plan.f8 ? launch_any_bn<true>(plan, lp, a.n, st) : launch_any_bn<false>(plan, lp, a.n, st);
 }
 
@@ -823,7 +830,7 @@ cudaError_t launch_conv_tc_f32(const TcConvPlan &plan, const ConvArgs &a, bool a
     if (!plan.enabled || plan.head || plan.f8 || !image_offset(plan, a, &img_off)) return cudaErrorInvalidValue;
     if (reinterpret_cast<uintptr_t>(a.out) % 16 != 0 || a.out_cs % 4 != 0) return cudaErrorInvalidValue;
     TcLaunch lp{plan.nch, plan.kc, plan.rb, plan.stride, plan.ho, plan.wo, img_off, a.out, a.out_cs, a.bias, a.leaky,
-                plan.err, nullptr, nullptr, plan.wscale, 1.f, 1, accumulate ? 1 : 0, plan.taps};
+                plan.err, nullptr, nullptr, plan.wscale, 1.f, 1, accumulate ? 1 : 0, plan.taps, 0, plan.f16 ? 1 : 0};
     return launch_any_bn<false>(plan, lp, a.n, st);
 }
 

@@ -10,13 +10,14 @@
 
 namespace tc {
 
-// A planned tensor-core conv for one layer.  Planning packs the weights to bfloat16
-// [9][cout][nch * 64] on the device and encodes the TMA descriptors of the input
+// A planned tensor-core conv for one layer.  Planning packs the weights to bfloat16, half
+// or e4m3 [9][cout][nch * kc] on the device and encodes the TMA descriptors of the input
 // activations (covering all n_in images of the buffer) and of the weights.
 struct TcConvPlan {
     bool enabled = false;
     bool head = false;  // flow-head plan (float flow output, see tc_plan_head)
     bool f8 = false;    // e4m3 operands (kind::f8f6f4) instead of bf16
+    bool f16 = false;   // IEEE half operands and outputs instead of bf16 (kind::f16, same rate)
     CUtensorMap tmA;  // 64-byte aligned type
     CUtensorMap tmB;
     // stride-1 3x3 layers whose last 128-byte channel step holds at most 64 bytes: that step
@@ -45,20 +46,23 @@ struct TcConvPlan {
 // already folded in (w[o][c] * s_in[c]); the epilogue multiplies by the per-output-channel
 // weight scale and quantizes with a.q_out.
 // taps = 1 plans a pointwise 1x1 conv (stride 1; wk_simt then holds [a.cin][a.cout]).
+// f16: half operands (weights packed to half, activations read and written as half)
+// instead of bfloat16; ignored with f8.
 bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vector<float> &wk_simt, int *err,
-                  std::string &why, bool f8 = false, int taps = 9);
+                  std::string &why, bool f8 = false, int taps = 9, bool f16 = false);
 
 // Plans the flow head (cout <= 16, no activation; in practice 2) on the tensor cores: the
 // weights are zero-padded to 16 outputs for the MMA.
 bool tc_plan_head(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vector<float> &wk_simt, int *err,
-                  std::string &why, bool f8 = false, int taps = 9);
+                  std::string &why, bool f8 = false, int taps = 9, bool f16 = false);
 
 // Launches a planned head: flow[i] = up[i] (if up) + bias + conv(a.in)[i][0..1], float (n, ho, wo, 2).
 cudaError_t launch_conv_tc_head(const TcConvPlan &plan, const ConvArgs &a, const float *up, float *flow,
                                 cudaStream_t st);
 
 // Launches a planned conv for a.n images starting at a.in (which must lie inside the
-// planned buffer, on an image boundary), writing bfloat16 to a.out with a.out_cs stride.
+// planned buffer, on an image boundary), writing the plan's 16-bit type (bfloat16 or half)
+// or e4m3 to a.out with a.out_cs stride.
 cudaError_t launch_conv_tc(const TcConvPlan &plan, const ConvArgs &a, cudaStream_t st);
 
 // The same for a bf16 plan writing float32 to a.out (pixel stride a.out_cs floats, a

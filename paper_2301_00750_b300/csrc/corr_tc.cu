@@ -6,12 +6,13 @@
 // entry D[m][q = m + d] (81 of the 384 columns of its row for R = 4).  One TMA load brings
 // the block's self features [8][16][64 ch] and one the halo of the other map
 // [8+2R][16+2R][64 ch] (zero outside the map, which gives the zero product the definition
-// asks for), 128-byte swizzled; one lane issues tcgen05.mma kind::f16 (BF16 x BF16 -> FP32)
-// for the two halves of N into TMEM; the four warps then read, per displacement row dy, the
-// two halo rows their 32 pixels need (tcgen05.ld), pick each pixel's 2R+1 entries through a
-// per-thread shared-memory slice, scale by 1/C, apply LeakyReLU, and store the (2R+1)^2
-// values in bfloat16.  The self features of the pixel are copied into the estimator input in
-// the same pass.  Waits are bounded like those of the convolution kernel.
+// asks for), 128-byte swizzled; one lane issues tcgen05.mma kind::f16 (BF16 x BF16 or
+// F16 x F16 -> FP32) for the two halves of N into TMEM; the four warps then read, per
+// displacement row dy, the two halo rows their 32 pixels need (tcgen05.ld), pick each
+// pixel's 2R+1 entries through a per-thread shared-memory slice, scale by 1/C, apply
+// LeakyReLU, and store the (2R+1)^2 values in the features' type.  The self features of
+// the pixel are copied into the estimator input in the same pass.  Waits are bounded like
+// those of the convolution kernel.
 #include <mutex>
 
 #include "corr_tc.cuh"
@@ -64,6 +65,7 @@ struct CorrTcLaunch {
     float q_out;  // e4m3: 1 / scale of the stored cost volume
     int *err;
     int rb;       // bytes of channels per step (128, or 64: 32 bf16 channels with the 64-byte swizzle)
+    int f16;      // 16-bit features and cost volume are IEEE half instead of bfloat16
 };
 
 template <int R, bool F8>
@@ -109,7 +111,7 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
         }
     } else if (threadIdx.x == 32) {
         // ---- MMA issuer: D[:, 0:NH] and D[:, NH:NP]
-        constexpr uint32_t idesc = F8 ? idesc_e4m3(128, G::NH) : idesc_bf16(128, G::NH);
+        const uint32_t idesc = F8 ? idesc_e4m3(128, G::NH) : (p.f16 ? idesc_f16(128, G::NH) : idesc_bf16(128, G::NH));
         bool ok = true;
         for (int ch = 0; ch < p.nch && ok; ++ch) {
             if (!mbar_wait(full0 + 8 * ch, 0, p.err, ERR_CORR_MMA)) {
@@ -208,22 +210,23 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
                         dst[k] = (uint8_t)__nv_cvt_float_to_fp8(res[k] * p.q_out, __NV_SATFINITE, __NV_E4M3);
                 }
             } else {
-                __nv_bfloat16 *dst = static_cast<__nv_bfloat16 *>(p.out) + pix * p.out_cs;
+                uint16_t *dst = static_cast<uint16_t *>(p.out) + pix * p.out_cs;  // bf16 or half
+                const bool f16 = p.f16 != 0;
                 if (p.vec_out) {
 #pragma unroll
                     for (int k = 0; k + 8 <= G::ND; k += 8) {
                         uint4 v;
-                        v.x = pack_bf16x2(res[k], res[k + 1]);
-                        v.y = pack_bf16x2(res[k + 2], res[k + 3]);
-                        v.z = pack_bf16x2(res[k + 4], res[k + 5]);
-                        v.w = pack_bf16x2(res[k + 6], res[k + 7]);
+                        v.x = pack16x2(f16, res[k], res[k + 1]);
+                        v.y = pack16x2(f16, res[k + 2], res[k + 3]);
+                        v.z = pack16x2(f16, res[k + 4], res[k + 5]);
+                        v.w = pack16x2(f16, res[k + 6], res[k + 7]);
                         *reinterpret_cast<uint4 *>(dst + k) = v;
                     }
 #pragma unroll
-                    for (int k = G::ND / 8 * 8; k < G::ND; ++k) dst[k] = __float2bfloat16_rn(res[k]);
+                    for (int k = G::ND / 8 * 8; k < G::ND; ++k) dst[k] = (uint16_t)pack16x2(f16, res[k], 0.f);
                 } else {
 #pragma unroll
-                    for (int k = 0; k < G::ND; ++k) dst[k] = __float2bfloat16_rn(res[k]);
+                    for (int k = 0; k < G::ND; ++k) dst[k] = (uint16_t)pack16x2(f16, res[k], 0.f);
                 }
             }
             if (p.self_copy) {
@@ -244,7 +247,7 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
 }
 
 bool encode_features(CUtensorMap *map, const void *base, int n, int cs, int h, int w, int c, int box_x, int box_y,
-                     bool f8, int rb) {
+                     bool f8, int rb, bool f16) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return false;
     const cuuint64_t es = f8 ? 1 : 2;
@@ -252,7 +255,9 @@ bool encode_features(CUtensorMap *map, const void *base, int n, int cs, int h, i
     const cuuint64_t strides[3] = {(cuuint64_t)cs * es, (cuuint64_t)w * cs * es, (cuuint64_t)h * w * cs * es};
     const cuuint32_t box[4] = {(cuuint32_t)(rb / es), (cuuint32_t)box_x, (cuuint32_t)box_y, 1};
     const cuuint32_t ones[4] = {1, 1, 1, 1};
-    return enc(map, f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims, strides, box, ones,
+    const CUtensorMapDataType dt = f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                      : (f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+    return enc(map, dt, 4, const_cast<void *>(base), dims, strides, box, ones,
                CU_TENSOR_MAP_INTERLEAVE_NONE, rb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -275,8 +280,9 @@ cudaError_t launch_r(const CorrTcPlan &plan, const CorrTcLaunch &lp, int nb, cud
 }  // namespace
 
 bool tc_plan_corr(CorrTcPlan &plan, const void *self, int n_self, int self_cs, const void *other, int n_other,
-                  int other_cs, int h, int w, int c, int r, int *err, std::string &why, bool f8) {
+                  int other_cs, int h, int w, int c, int r, int *err, std::string &why, bool f8, bool f16) {
     plan.enabled = false;
+    if (f8) f16 = false;
     const int al = f8 ? 16 : 8;  // 16-byte strides
     if (c % al != 0 || c < al || c > BK * MAX_NCH) { why = "channels must be a multiple of 16 bytes, up to 128"; return false; }
     if (r < 1 || r > 4) { why = "radius must be 1..4"; return false; }
@@ -284,8 +290,8 @@ bool tc_plan_corr(CorrTcPlan &plan, const void *self, int n_self, int self_cs, c
     if (reinterpret_cast<uintptr_t>(self) % 16 || reinterpret_cast<uintptr_t>(other) % 16) { why = "misaligned"; return false; }
     // BF16 features of at most 32 channels: 64-byte steps, so no step multiplies zero padding
     const int rb = !f8 && c <= 32 ? 64 : 128;
-    if (!encode_features(&plan.tmS, self, n_self, self_cs, h, w, c, BX, BY, f8, rb) ||
-        !encode_features(&plan.tmO, other, n_other, other_cs, h, w, c, BX + 2 * r, BY + 2 * r, f8, rb)) {
+    if (!encode_features(&plan.tmS, self, n_self, self_cs, h, w, c, BX, BY, f8, rb, f16) ||
+        !encode_features(&plan.tmO, other, n_other, other_cs, h, w, c, BX + 2 * r, BY + 2 * r, f8, rb, f16)) {
         why = "tensor map encoding failed";
         return false;
     }
@@ -296,6 +302,7 @@ bool tc_plan_corr(CorrTcPlan &plan, const void *self, int n_self, int self_cs, c
     plan.rb = rb;
     plan.nch = f8 ? 1 : (c + rb / 2 - 1) / (rb / 2);
     plan.f8 = f8;
+    plan.f16 = f16;
     plan.err = err;
     plan.enabled = true;
     return true;
@@ -327,6 +334,7 @@ cudaError_t launch_corr_tc(const CorrTcPlan &plan, int nb, const int img_self[2]
     lp.scale = feat_scale * feat_scale / (float)plan.c;
     lp.q_out = q_out;
     lp.err = plan.err;
+    lp.f16 = plan.f16 ? 1 : 0;
     if (plan.f8) {
         switch (plan.r) {
             case 1: return launch_r<1, true>(plan, lp, nb, st);

@@ -9,9 +9,9 @@
 
 namespace tc {
 
-// A planned tensor-core correlation over bfloat16 NHWC feature buffers.  tmS covers the
-// "self" buffer, tmO the "other" buffer (they may be the same buffer); both hold n_img
-// images of h x w pixels with c channels at pixel stride cs.
+// A planned tensor-core correlation over bfloat16 (or half, or e4m3) NHWC feature buffers.
+// tmS covers the "self" buffer, tmO the "other" buffer (they may be the same buffer); both
+// hold n_img images of h x w pixels with c channels at pixel stride cs.
 struct CorrTcPlan {
     bool enabled = false;
     CUtensorMap tmS;
@@ -19,6 +19,7 @@ struct CorrTcPlan {
     int h = 0, w = 0, c = 0, r = 0, nch = 0;
     int rb = 128;     // bytes of channels per step: 128, or 64 for BF16 features of <= 32 channels
     bool f8 = false;  // e4m3 features (kind::f8f6f4)
+    bool f16 = false; // IEEE half features and cost volume instead of bfloat16
     int *err = nullptr;  // device error word (not owned)
 };
 
@@ -26,11 +27,12 @@ struct CorrTcPlan {
 // self_cs) and of `other` (n_other images, pixel stride other_cs).  Returns false with `why`
 // when not eligible (c % 8 != 0, c > 128, r > 4, misaligned buffers).
 bool tc_plan_corr(CorrTcPlan &plan, const void *self, int n_self, int self_cs, const void *other, int n_other,
-                  int other_cs, int h, int w, int c, int r, int *err, std::string &why, bool f8 = false);
+                  int other_cs, int h, int w, int c, int r, int *err, std::string &why, bool f8 = false,
+                  bool f16 = false);
 
 // Launches the planned correlation for nb <= 2 batch entries: entry b correlates image
 // img_self[b] of the self buffer with image img_other[b] of the other buffer and writes
-// LeakyReLU(mean over channels) for the (2r+1)^2 displacements, bfloat16 or e4m3, to
+// LeakyReLU(mean over channels) for the (2r+1)^2 displacements, in the features' type, to
 // out + ((b h + y) w + x) out_cs + k.  If self_copy is set, it also copies the c self
 // features of pixel (b, y, x) (read from fs[b], [h][w][c]) to self_copy + ((b h + y) w + x)
 // out_cs.

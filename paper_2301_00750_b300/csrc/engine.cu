@@ -10,6 +10,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/tc_stream.h"
@@ -120,10 +121,22 @@ bool parse_weights(const uint8_t *p, size_t n, HostNet &net, std::string &err) {
     return true;
 }
 
+// 16-bit tensor-core precisions: bfloat16 (TC_BF16) or IEEE half (TC_FP16) operands.
+static inline bool is16(tc_precision p) { return p == TC_BF16 || p == TC_FP16; }
+
+// The value a float weight takes as an operand of precision p: rounded to bfloat16 or half
+// for the 16-bit paths; unchanged otherwise (float, and e4m3, which quantises per channel
+// when it plans its layers).
+static inline float operand_value(float v, tc_precision p) {
+    if (p == TC_BF16) return __bfloat162float(__float2bfloat16_rn(v));
+    if (p == TC_FP16) return __half2float(__float2half_rn(v));
+    return v;
+}
+
 // [9 * cin_pad][cout] layout for the SIMT conv; input channel ci of the buffer maps to
-// channel perm[ci] of the file's layer (-1 = zero padding).  bf16 = round weights to
-// bfloat16 values (the BF16 path's operands).
-static std::vector<float> simt_weights(const HostLayer &L, const std::vector<int> &perm, bool bf16) {
+// channel perm[ci] of the file's layer (-1 = zero padding).  The weights take their operand
+// values for precision p (see operand_value).
+static std::vector<float> simt_weights(const HostLayer &L, const std::vector<int> &perm, tc_precision p) {
     const int cp = (int)perm.size();
     std::vector<float> out((size_t)9 * cp * L.cout, 0.f);
     for (int tap = 0; tap < 9; ++tap)
@@ -132,8 +145,7 @@ static std::vector<float> simt_weights(const HostLayer &L, const std::vector<int
             if (c < 0) continue;
             for (int o = 0; o < L.cout; ++o) {
                 float v = L.w[(((size_t)o * L.cin + c) * 3 + tap / 3) * 3 + tap % 3];
-                if (bf16) v = __bfloat162float(__float2bfloat16_rn(v));
-                out[((size_t)tap * cp + ci) * L.cout + o] = v;
+                out[((size_t)tap * cp + ci) * L.cout + o] = operand_value(v, p);
             }
         }
     return out;
@@ -510,14 +522,16 @@ static int seg_est(const tc_stream *s, int l, int k) { return 3 * s->L + 6 * (s-
 static int n_segments(const tc_stream *s) { return 3 * s->L + 6 * (s->L - 1); }
 
 // Records a tensor-core layer; BF16 layers are planned at once (layers that are not
-// eligible keep the CUDA-core kernel), E4M3 layers when the scales are set.
+// eligible keep the CUDA-core kernel), and so are FP16 layers; E4M3 layers when the scales
+// are set.
 static void add_layer(tc_stream *s, TcConvPlan &plan, const ConvArgs &a, int n_in, std::vector<float> wk,
                       std::vector<int> in_seg, bool head) {
     if (s->prec == TC_FP32) return;
-    if (s->prec == TC_BF16) {
+    if (is16(s->prec)) {
         std::string why;
-        const bool ok = head ? tc_plan_head(plan, a, n_in, wk, s->dev_err, why)
-                             : tc_plan_conv(plan, a, n_in, wk, s->dev_err, why);
+        const bool f16 = s->prec == TC_FP16;
+        const bool ok = head ? tc_plan_head(plan, a, n_in, wk, s->dev_err, why, false, 9, f16)
+                             : tc_plan_conv(plan, a, n_in, wk, s->dev_err, why, false, 9, f16);
         if (ok) s->tc_layers += 1;
         return;
     }
@@ -531,7 +545,7 @@ template <typename T>
 static tc_status build_refine(tc_stream *s) {
     const HostNet &net = s->net;
     if (s->prec == TC_FP8_E4M3)
-        return fail(s, TC_ERR_UNSUPPORTED, "the refinement network runs in TC_FP32 or TC_BF16 streams");
+        return fail(s, TC_ERR_UNSUPPORTED, "the refinement network runs in TC_FP32, TC_BF16 or TC_FP16 streams");
     const LevelBufs &B = s->lv[1];
     const size_t px = (size_t)B.h * B.w;
     const int c3 = net.dec[2], c4 = net.dec[3];
@@ -576,13 +590,14 @@ static tc_status build_refine(tc_stream *s) {
         if ((r = upload(s, &R.dw, dw)) != TC_OK || (r = upload(s, &R.db, db)) != TC_OK ||
             (r = upload(s, &R.pw, pw)) != TC_OK || (r = upload(s, &R.pb, H.pb)) != TC_OK)
             return r;
-        if (s->prec == TC_BF16) {
+        if (is16(s->prec)) {
             const bool last = k == nl - 1;
+            const bool f16 = s->prec == TC_FP16;
             ConvArgs a{s->refD, dcs, 1, B.h, B.w, R.cin_p, 1, B.h, B.w, nullptr, nullptr, last ? 2 : H.cout,
                        last ? nullptr : s->refP, last ? 16 : pcs, H.leaky};
             std::string why;
-            const bool ok = last ? tc_plan_head(R.plan, a, 2 * NSET, pw, s->dev_err, why, false, 1)
-                                 : tc_plan_conv(R.plan, a, 2 * NSET, pw, s->dev_err, why, false, 1);
+            const bool ok = last ? tc_plan_head(R.plan, a, 2 * NSET, pw, s->dev_err, why, false, 1, f16)
+                                 : tc_plan_conv(R.plan, a, 2 * NSET, pw, s->dev_err, why, false, 1, f16);
             if (ok) s->tc_layers += 1;
         }
     }
@@ -622,11 +637,13 @@ static tc_status build_stream(tc_stream *s) {
                 for (int o = 0; o < HL.cout; ++o)
                     for (int k = 0; k < 27; ++k) {
                         float v = HL.w[(size_t)o * 27 + k];
-                        if (bf) v = __bfloat162float(__float2bfloat16_rn(v));
+                        // the first conv reads the float image: its weights take the 16-bit
+                        // operand values (bfloat16 also for e4m3 streams)
+                        if (bf) v = operand_value(v, s->prec == TC_FP16 ? TC_FP16 : TC_BF16);
                         wk[(size_t)k * HL.cout + o] = v;
                     }
             } else {
-                wk = simt_weights(HL, iota_perm(HL.cin, HL.cin), s->prec == TC_BF16);
+                wk = simt_weights(HL, iota_perm(HL.cin, HL.cin), s->prec);
             }
             if ((r = upload(s, &s->pyr_w[3 * (l - 1) + j], wk)) != TC_OK) return r;
             if ((r = upload(s, &s->pyr_b[3 * (l - 1) + j], HL.b)) != TC_OK) return r;
@@ -680,7 +697,7 @@ static tc_status build_stream(tc_stream *s) {
         const int in_off[4] = {0, B.off_x1, B.off_x2, B.off_x2};
         const int cin[4] = {B.x0p, net.dec[0], net.dec[1], net.dec[1] + net.dec[2]};
         for (int j = 0; j < 4; ++j) {
-            std::vector<float> wk = simt_weights(E[j], perms[j], s->prec == TC_BF16);
+            std::vector<float> wk = simt_weights(E[j], perms[j], s->prec);
             if ((r = upload(s, &B.wk[j], wk)) != TC_OK) return r;
             if ((r = upload(s, &B.bias[j], E[j].b)) != TC_OK) return r;
             T *dec = static_cast<T *>(B.dec);
@@ -688,15 +705,15 @@ static tc_status build_stream(tc_stream *s) {
                        dec + B.off_x1, B.ctot, 1};
             add_layer(s, B.tcplan[j], a, 2 * NSET, wk, segs[j], false);
         }
-        std::vector<float> wk5 = simt_weights(E[4], p5, s->prec == TC_BF16);
+        std::vector<float> wk5 = simt_weights(E[4], p5, s->prec);
         if ((r = upload(s, &B.head_w, wk5)) != TC_OK) return r;
         if ((r = upload(s, &B.head_b, E[4].b)) != TC_OK) return r;
-        if (s->prec == TC_BF16) {
+        if (is16(s->prec)) {
             std::string why;
             // level L correlates the two pyramid slots; finer levels correlate with f2w
             const void *other = l == L ? B.pyr : B.f2w;
             if (tc_plan_corr(B.corrplan, B.pyr, NPYR, B.c, other, l == L ? NPYR : 2 * NSET, B.c, B.h, B.w, B.c,
-                             s->R, s->dev_err, why))
+                             s->R, s->dev_err, why, false, s->prec == TC_FP16))
                 s->tc_corr_levels += 1;
         }
         {
@@ -720,8 +737,10 @@ static tc_status build_stream(tc_stream *s) {
 extern "C" tc_status tc_create_stream(const tc_stream_desc *desc, void *cuda_stream, tc_stream **out) {
     if (out) *out = nullptr;
     if (!desc || !out) return fail(nullptr, TC_ERR_INVALID_ARG, "tc_create_stream: NULL argument");
-    if (desc->precision != TC_FP32 && desc->precision != TC_BF16 && desc->precision != TC_FP8_E4M3)
-        return fail(nullptr, TC_ERR_INVALID_ARG, "tc_create_stream: precision must be TC_FP32, TC_BF16 or TC_FP8_E4M3");
+    if (desc->precision != TC_FP32 && desc->precision != TC_BF16 && desc->precision != TC_FP8_E4M3 &&
+        desc->precision != TC_FP16)
+        return fail(nullptr, TC_ERR_INVALID_ARG,
+                    "tc_create_stream: precision must be TC_FP32, TC_BF16, TC_FP16 or TC_FP8_E4M3");
     std::unique_ptr<tc_stream> s(new (std::nothrow) tc_stream());
     if (!s) return fail(nullptr, TC_ERR_OOM, "tc_create_stream: host allocation failed");
     std::vector<uint8_t> blob;
@@ -765,6 +784,7 @@ extern "C" tc_status tc_create_stream(const tc_stream_desc *desc, void *cuda_str
     tc_default_consistency(&s->params);
     tc_status r = s->prec == TC_FP32   ? build_stream<float>(s.get())
                   : s->prec == TC_BF16 ? build_stream<__nv_bfloat16>(s.get())
+                  : s->prec == TC_FP16 ? build_stream<__half>(s.get())
                                        : build_stream<__nv_fp8_e4m3>(s.get());
     if (r != TC_OK) {
         std::string msg = s->err;
@@ -894,7 +914,7 @@ static tc_status run_pyramid(tc_stream *s, const float *img, int slot) {
 template <typename T>
 static tc_status run_refine(tc_stream *s, int set) {
     if constexpr (sizeof(T) == 1) {
-        return fail(s, TC_ERR_UNSUPPORTED, "the refinement network runs in TC_FP32 or TC_BF16 streams");
+        return fail(s, TC_ERR_UNSUPPORTED, "the refinement network runs in TC_FP32, TC_BF16 or TC_FP16 streams");
     } else {
     LevelBufs &B = s->lv[1];
     T *dec = dec_of<T>(B, set);
@@ -1252,7 +1272,7 @@ static void release_graphs(tc_stream *s);
 template <typename T>
 static tc_status record_amax(tc_stream *s, int cur) {
     if constexpr (sizeof(T) == 1) {
-        return fail(s, TC_ERR_INVALID_ARG, "amax recording needs a TC_FP32 or TC_BF16 stream");
+        return fail(s, TC_ERR_INVALID_ARG, "amax recording needs a TC_FP32, TC_BF16 or TC_FP16 stream");
     } else {
         for (int l = 1; l <= s->L; ++l) {
             LevelBufs &B = s->lv[l - 1];
@@ -1472,7 +1492,7 @@ extern "C" tc_status tc_set_amax_recording(tc_stream *s, int enable) {
     tc_status r = check_stream(s, "tc_set_amax_recording");
     if (r != TC_OK) return r;
     if (s->pipelined) return fail(s, TC_ERR_STATE, "tc_set_amax_recording: not available in pipelined mode");
-    if (s->prec == TC_FP8_E4M3) return fail(s, TC_ERR_INVALID_ARG, "amax recording needs a TC_FP32 or TC_BF16 stream");
+    if (s->prec == TC_FP8_E4M3) return fail(s, TC_ERR_INVALID_ARG, "amax recording needs a TC_FP32, TC_BF16 or TC_FP16 stream");
     TC_TRY(s, cudaMemsetAsync(s->amax_dev, 0, sizeof(unsigned) * n_segments(s), s->st), "memset");
     s->rec_amax = enable != 0;
     return TC_OK;
@@ -1563,6 +1583,7 @@ extern "C" tc_status tc_process_frame(tc_stream *s, const float *I_t, const floa
     if (!I_t || !P_t || !O_t) return fail(s, TC_ERR_INVALID_ARG, "tc_process_frame: NULL image pointer");
     if (s->prec == TC_FP32) return process<float>(s, I_t, P_t, O_t, wc_opt, mask_opt);
     if (s->prec == TC_BF16) return process<__nv_bfloat16>(s, I_t, P_t, O_t, wc_opt, mask_opt);
+    if (s->prec == TC_FP16) return process<__half>(s, I_t, P_t, O_t, wc_opt, mask_opt);
     if (!s->fp8_ready)
         return fail(s, TC_ERR_STATE, "tc_process_frame: an e4m3 stream needs tc_set_fp8_scales before its first frame");
     return process<__nv_fp8_e4m3>(s, I_t, P_t, O_t, wc_opt, mask_opt);
@@ -1876,11 +1897,13 @@ static tc_status op_conv(const float *in, int n, int h, int w, int cin, const fl
     L.cout = cout; L.cin = cin; L.stride = stride; L.leaky = leaky;
     L.w.assign(w_oihw, w_oihw + (size_t)cout * cin * 9);
     L.b.assign(bias, bias + cout);
-    const bool bf = sizeof(T) == 2;
+    const bool bf = sizeof(T) == 2;      // bfloat16 or half operands
+    constexpr bool f16 = std::is_same<T, __half>::value;
     constexpr bool f8 = sizeof(T) == 1;  // e4m3 activations with scale 1; tensor cores only
     const int cin_p = round_up(cin, f8 ? 16 : (bf ? 8 : 4)), cout_p = round_up(cout, f8 ? 16 : 4);
     const int ho = (h - 1) / stride + 1, wo = (w - 1) / stride + 1;
-    std::vector<float> wk = simt_weights(L, iota_perm(cin, cin_p), bf);
+    std::vector<float> wk =
+        simt_weights(L, iota_perm(cin, cin_p), !bf ? TC_FP32 : (f16 ? TC_FP16 : TC_BF16));
     // pad cout to a multiple of 4 (16 for e4m3)
     std::vector<float> wkp((size_t)9 * cin_p * cout_p, 0.f), bp(cout_p, 0.f);
     for (size_t k = 0; k < (size_t)9 * cin_p; ++k)
@@ -1914,7 +1937,7 @@ static tc_status op_conv(const float *in, int n, int h, int w, int cin, const fl
     OP_TRY(tmp.get((void **)&derr, sizeof(int)), "tc_op_conv3x3 alloc");
     OP_TRY(cudaMemsetAsync(derr, 0, sizeof(int), st), "tc_op_conv3x3 memset");
     std::string why;
-    const bool use_tc = (bf || f8) && tc_plan_conv(plan, a, n, wkp, derr, why, f8);
+    const bool use_tc = (bf || f8) && tc_plan_conv(plan, a, n, wkp, derr, why, f8, 9, f16);
     if (use_tc) {
         cudaError_t e = launch_conv_tc(plan, a, st);
         if (e != cudaSuccess) {
@@ -1956,6 +1979,7 @@ extern "C" tc_status tc_op_conv3x3(tc_precision precision, const float *in, int 
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (precision == TC_FP32) return op_conv<float>(in, n, h, w, cin, w_oihw, bias, cout, stride, leaky, out, st);
     if (precision == TC_BF16) return op_conv<__nv_bfloat16>(in, n, h, w, cin, w_oihw, bias, cout, stride, leaky, out, st);
+    if (precision == TC_FP16) return op_conv<__half>(in, n, h, w, cin, w_oihw, bias, cout, stride, leaky, out, st);
     if (precision == TC_FP8_E4M3)
         return op_conv<__nv_fp8_e4m3>(in, n, h, w, cin, w_oihw, bias, cout, stride, leaky, out, st);
     return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_conv3x3: precision");
@@ -2003,8 +2027,9 @@ static tc_status op_sepconv(const float *in, int n, int h, int w, int cin, const
     OP_TRY(cudaMemsetAsync(derr, 0, sizeof(int), st), "tc_op_sepconv memset");
     ConvArgs a{d, cin, n, h, w, cin, 1, h, w, nullptr, dpb, cout, o, head ? 16 : cout, leaky};
     std::string why;
-    const bool use_tc = bf && (head ? tc_plan_head(plan, a, n, pwk, derr, why, false, 1)
-                                    : tc_plan_conv(plan, a, n, pwk, derr, why, false, 1));
+    constexpr bool f16 = std::is_same<T, __half>::value;
+    const bool use_tc = bf && (head ? tc_plan_head(plan, a, n, pwk, derr, why, false, 1, f16)
+                                    : tc_plan_conv(plan, a, n, pwk, derr, why, false, 1, f16));
     if (use_tc) {
         const cudaError_t e = head ? launch_conv_tc_head(plan, a, flow, flow, st) : launch_conv_tc(plan, a, st);
         if (e != cudaSuccess) {
@@ -2039,7 +2064,8 @@ extern "C" tc_status tc_op_sepconv(tc_precision precision, const float *in, int 
     if (precision == TC_FP32) return op_sepconv<float>(in, n, h, w, cin, dw, db, pw, pb, cout, dil, leaky, out, st);
     if (precision == TC_BF16)
         return op_sepconv<__nv_bfloat16>(in, n, h, w, cin, dw, db, pw, pb, cout, dil, leaky, out, st);
-    return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_sepconv: precision must be TC_FP32 or TC_BF16");
+    if (precision == TC_FP16) return op_sepconv<__half>(in, n, h, w, cin, dw, db, pw, pb, cout, dil, leaky, out, st);
+    return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_sepconv: precision must be TC_FP32, TC_BF16 or TC_FP16");
 }
 
 template <typename T>
@@ -2061,7 +2087,8 @@ static tc_status op_corr(const float *f1, const float *f2, int n, int h, int w, 
     OP_TRY(cudaMemsetAsync(derr, 0, sizeof(int), st), "tc_op_correlation memset");
     std::string why;
     constexpr bool f8 = sizeof(T) == 1;  // e4m3 features and cost volume with scale 1
-    const bool use_tc = (sizeof(T) == 2 || f8) && tc_plan_corr(plan, a, n, c, b, n, c, h, w, c, r, derr, why, f8);
+    const bool use_tc = (sizeof(T) == 2 || f8) &&
+                        tc_plan_corr(plan, a, n, c, b, n, c, h, w, c, r, derr, why, f8, std::is_same<T, __half>::value);
     if (f8 && !use_tc)
         return fail(nullptr, TC_ERR_UNSUPPORTED, "tc_op_correlation: e4m3 runs on the tensor cores only: " + why);
     for (int i = 0; i < n; i += 2) {
@@ -2092,6 +2119,7 @@ extern "C" tc_status tc_op_correlation(tc_precision precision, const float *f1, 
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (precision == TC_FP32) return op_corr<float>(f1, f2, n, h, w, c, r, out, st);
     if (precision == TC_BF16) return op_corr<__nv_bfloat16>(f1, f2, n, h, w, c, r, out, st);
+    if (precision == TC_FP16) return op_corr<__half>(f1, f2, n, h, w, c, r, out, st);
     if (precision == TC_FP8_E4M3) return op_corr<__nv_fp8_e4m3>(f1, f2, n, h, w, c, r, out, st);
     return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_correlation: precision");
 }
@@ -2123,6 +2151,7 @@ extern "C" tc_status tc_op_warp_features(tc_precision precision, const float *f,
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (precision == TC_FP32) return op_warp<float>(f, flow, n, h, w, c, out, st);
     if (precision == TC_BF16) return op_warp<__nv_bfloat16>(f, flow, n, h, w, c, out, st);
+    if (precision == TC_FP16) return op_warp<__half>(f, flow, n, h, w, c, out, st);
     if (precision == TC_FP8_E4M3) return op_warp<__nv_fp8_e4m3>(f, flow, n, h, w, c, out, st);
     return fail(nullptr, TC_ERR_INVALID_ARG, "tc_op_warp_features: precision");
 }

@@ -1,7 +1,7 @@
 // SIMT kernels of the lite flow network (Sec. 3.2): implicit-GEMM 3x3 convolution, the
 // first (3-channel, stride-2) pyramid conv, the flow head with its residual, the
 // shared-memory-tiled correlation, the bilinear feature warp and flow upsampling.
-// Activations are NHWC in float (TC_FP32) or bfloat16 (TC_BF16); every accumulation is
+// Activations are NHWC in float (TC_FP32), bfloat16 (TC_BF16) or half (TC_FP16); every accumulation is
 // float32.
 #include "common.cuh"
 
@@ -490,6 +490,7 @@ cudaError_t launch_from_act(const T *in, size_t n, float *out, cudaStream_t st) 
     template cudaError_t launch_from_act<T>(const T *, size_t, float *, cudaStream_t);
 TC_INST(float)
 TC_INST(__nv_bfloat16)
+TC_INST(__half)
 #undef TC_INST
 
 // =====================================================================================
@@ -520,6 +521,7 @@ cudaError_t launch_amax(const T *base, size_t npix, int cs, int nc, unsigned *sl
 }
 template cudaError_t launch_amax<float>(const float *, size_t, int, int, unsigned *, cudaStream_t);
 template cudaError_t launch_amax<__nv_bfloat16>(const __nv_bfloat16 *, size_t, int, int, unsigned *, cudaStream_t);
+template cudaError_t launch_amax<__half>(const __half *, size_t, int, int, unsigned *, cudaStream_t);
 
 // E4M3 activations: only the kernels an E4M3 stream runs outside the tensor cores.
 template cudaError_t launch_conv_first<__nv_fp8_e4m3>(const ConvFirstArgs &, cudaStream_t);

@@ -10,7 +10,7 @@ namespace {
 constexpr int DW_THREADS = 128;  // threads per block: channel groups x pixel lanes
 constexpr int DW_PIX = 8;        // pixels per thread, one lane count apart along the row
 
-// 8 consecutive activations as raw bits (one 16-byte load for bf16, two for float) and
+// 8 consecutive activations as raw bits (one 16-byte load for bf16 and half, two for float) and
 // their float values.
 template <typename T> struct Raw8;
 template <> struct Raw8<__nv_bfloat16> {
@@ -21,6 +21,19 @@ template <> struct Raw8<__nv_bfloat16> {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const float2 f = __bfloat1622float2(h[k]);
+            v[2 * k] = f.x;
+            v[2 * k + 1] = f.y;
+        }
+    }
+};
+template <> struct Raw8<__half> {
+    uint4 u;
+    __device__ __forceinline__ void load(const __half *p) { u = __ldg(reinterpret_cast<const uint4 *>(p)); }
+    __device__ __forceinline__ void get(float (&v)[8]) const {
+        const __half2 *h = reinterpret_cast<const __half2 *>(&u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 f = __half22float2(h[k]);
             v[2 * k] = f.x;
             v[2 * k + 1] = f.y;
         }
@@ -199,7 +212,9 @@ cudaError_t launch_pointwise(const PwArgs &a, cudaStream_t st) {
 
 template cudaError_t launch_depthwise<float>(const DwArgs &, cudaStream_t);
 template cudaError_t launch_depthwise<__nv_bfloat16>(const DwArgs &, cudaStream_t);
+template cudaError_t launch_depthwise<__half>(const DwArgs &, cudaStream_t);
 template cudaError_t launch_pointwise<float>(const PwArgs &, cudaStream_t);
 template cudaError_t launch_pointwise<__nv_bfloat16>(const PwArgs &, cudaStream_t);
+template cudaError_t launch_pointwise<__half>(const PwArgs &, cudaStream_t);
 
 }  // namespace tc

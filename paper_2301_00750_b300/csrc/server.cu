@@ -121,8 +121,8 @@ static tc_status srv_fail(tc_status code, const std::string &msg) { return tc_re
 extern "C" tc_status tc_server_create(const tc_server_desc *desc, tc_server **out) {
     if (out) *out = nullptr;
     if (!desc || !out) return srv_fail(TC_ERR_INVALID_ARG, "tc_server_create: NULL argument");
-    if (desc->precision != TC_FP32 && desc->precision != TC_BF16)
-        return srv_fail(TC_ERR_INVALID_ARG, "tc_server_create: precision must be TC_FP32 or TC_BF16");
+    if (desc->precision != TC_FP32 && desc->precision != TC_BF16 && desc->precision != TC_FP16)
+        return srv_fail(TC_ERR_INVALID_ARG, "tc_server_create: precision must be TC_FP32, TC_BF16 or TC_FP16");
     if (desc->workers < 1 || desc->workers > 64 || desc->max_streams < 1)
         return srv_fail(TC_ERR_INVALID_ARG, "tc_server_create: workers must lie in [1, 64], max_streams >= 1");
     tc_server *srv = new (std::nothrow) tc_server();

@@ -128,6 +128,12 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
+// Instruction descriptor of kind::f16 with A and B IEEE half (format code 0): D f32,
+// both K-major, M x N.  The MMA instruction is the one of the bf16 form.
+__host__ __device__ constexpr uint32_t idesc_f16(int m, int n) {
+    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
 // Instruction descriptor of kind::f8f6f4: D f32, A and B E4M3 (format code 0), K-major.
 __host__ __device__ constexpr uint32_t idesc_e4m3(int m, int n) {
     return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
@@ -193,6 +199,16 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ uint32_t pack_f16x2(float a, float b) {
+    __half2 v = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// Two 16-bit activations of a 16-bit tensor-core operand type: half when f16, else bf16.
+__device__ __forceinline__ uint32_t pack16x2(bool f16, float a, float b) {
+    return f16 ? pack_f16x2(a, b) : pack_bf16x2(a, b);
 }
 
 }  // namespace ptx

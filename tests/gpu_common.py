@@ -56,6 +56,22 @@ def bf16_round(a):
     return r.astype(np.uint32).view(np.float32)
 
 
+def f16_round(a):
+    """Round float32 values to the nearest IEEE half (ties to even, subnormals kept), as
+    float32."""
+    return np.asarray(a, np.float32).astype(np.float16).astype(np.float32)
+
+
+def round16(prec, a):
+    """The operand values of a 16-bit precision ("bf16" or "fp16"); float32 unchanged."""
+    return bf16_round(a) if prec == "bf16" else f16_round(a) if prec == "fp16" else np.asarray(a, np.float32)
+
+
+# Relative step of a 16-bit precision's stored values (8 significant bits for bfloat16,
+# 11 for half): outputs rounded to it differ from float32 by at most half of it.
+REL16 = {"bf16": 2.0 ** -8, "fp16": 2.0 ** -10}
+
+
 def weight_scales_e4m3(w):
     """Per-output-channel E4M3 weight scales amax / 448 computed in float32, as a layer's
     planning does (w: (cout, cin, 3, 3) float32)."""

@@ -51,7 +51,7 @@ def _run(path, frames, styl, prec, pipelined, latency=0, flow_downscale=0, solve
     return res, flows
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 def test_pipelined_matches_default(prec):
     path, _ = weights_file((16, 32, 64, 96, 128), 4)
     frames, styl = _frames(14, seed=11)
@@ -96,23 +96,57 @@ def test_pipelined_refinement():
     assert np.array_equal(fa[0], fb[0]) and np.array_equal(fa[1], fb[1])
 
 
-def test_pipelined_1080p_bf16_matches_default_and_oracle():
-    """The configuration the benchmark times: 1920x1080, the 5-level r = 4 network, BF16,
-    pipelined mode with CUDA graphs (frame 2 is captured and replayed).  Every frame's outputs
-    equal the default mode's bit for bit, and the flows of the last pair match the FP64
-    oracle within the BF16 bound of the stream tests: 0.05 px or 2 u sqrt(layers) of the mean
-    flow (u = 2^-9, 35 conv layers on the path to the flow)."""
+_REF_1080 = {}
+
+
+def _ref_1080p():
+    """Frames 0-2 of the seeded 1920x1080 sequence, the FP64 oracle's flows of the pair
+    (2, 1), and the FP32 path's flows of the same pair (computed once per process)."""
     import oracle
     import torch
-    path, net = weights_file((16, 32, 64, 96, 128), 4)
-    seq = synth.Sequence(seed=0)
-    frames = [seq.frame(t) for t in range(3)]
-    styl = [seq.stylized(t, f) for t, f in enumerate(frames)]
+    if not _REF_1080:
+        path, net = weights_file((16, 32, 64, 96, 128), 4)
+        seq = synth.Sequence(seed=0)
+        frames = [seq.frame(t) for t in range(3)]
+        styl = [seq.stylized(t, f) for t, f in enumerate(frames)]
+        _, h, w = frames[0].shape
+        s = tc.Stream(w, h, "fp32", weights_path=path)
+        O = torch.empty((3, h, w), device="cuda")
+        for t in (1, 2):
+            s.process_frame(to_dev(frames[t]), to_dev(styl[t]), O)
+        Fb, Ff = torch.empty((2, h, w), device="cuda"), torch.empty((2, h, w), device="cuda")
+        s.get_flows(Fb, Ff)
+        torch.cuda.synchronize()
+        fp32 = (to_np(Fb), to_np(Ff))
+        s.destroy()
+        _REF_1080.update(path=path, frames=frames, styl=styl, oracle=oracle.flow_pair(net, frames[2], frames[1]),
+                         fp32=fp32)
+    return _REF_1080
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_pipelined_1080p_matches_default_and_fixed_epe(prec):
+    """The configuration the benchmark times: 1920x1080, the 5-level r = 4 network, pipelined
+    mode with CUDA graphs (frame 2 is captured and replayed).  Every frame's outputs equal the
+    default mode's bit for bit.  The flows of the last pair are compared with the FP32 path's
+    flows and with the FP64 oracle's.
+
+    FP16 is held to the fixed-EPE bar of the precision variants: EPE <= 0.05 px per direction
+    against the FP32 result, and against the FP64 oracle (measured ~0.02 px at a 21 px mean
+    flow).  BF16 cannot meet that bar with these weights: rounding the He-init weights alone
+    to bfloat16, with every activation exact, moves the flows by ~0.12 px (the FP64
+    attribution in test_precision_cpu.py), so BF16 is held to its representation bound
+    2 u sqrt(n) of the mean flow (u = 2^-9, n = 35 conv layers on the path to the flow) and
+    reported as not at fixed EPE."""
+    import oracle
+    import torch
+    R = _ref_1080p()
+    frames, styl = R["frames"], R["styl"]
     _, h, w = frames[0].shape
     dI, dP = [to_dev(I) for I in frames], [to_dev(P) for P in styl]
     res = []
     for pipelined in (False, True):
-        s = tc.Stream(w, h, "bf16", weights_path=path)
+        s = tc.Stream(w, h, prec, weights_path=R["path"])
         s.set_pipelined(pipelined)
         outs = [(torch.empty((3, h, w), device="cuda"), torch.empty((h, w), device="cuda"),
                  torch.empty((h, w), device="cuda", dtype=torch.uint8)) for _ in frames]
@@ -130,12 +164,21 @@ def test_pipelined_1080p_bf16_matches_default_and_oracle():
         for k in range(3):
             assert np.array_equal(a[t][k], b[t][k]), (t, k)
     assert np.array_equal(fa[0], fb[0]) and np.array_equal(fa[1], fb[1])
-    ref_b, ref_f = oracle.flow_pair(net, frames[2], frames[1])
+    ref_b, ref_f = R["oracle"]
+    f32_b, f32_f = R["fp32"]
     eb, ef = oracle.epe(fb[0], ref_b), oracle.epe(fb[1], ref_f)
+    qb, qf = oracle.epe(fb[0], f32_b), oracle.epe(fb[1], f32_f)
     mag = float(np.sqrt((ref_b ** 2).sum(0)).mean())
-    bound = max(0.05, 2 * 2.0 ** -9 * np.sqrt(35) * mag)
-    print(f"1080p BF16 pipelined EPE vs FP64 oracle: Fb {eb:.4f} px, Ff {ef:.4f} px (bound {bound:.4f})")
-    assert eb <= bound and ef <= bound, (eb, ef, bound)
+    print(f"1080p {prec} pipelined EPE vs FP32 path: Fb {qb:.4f} px, Ff {qf:.4f} px; vs FP64 oracle: "
+          f"Fb {eb:.4f} px, Ff {ef:.4f} px (mean |F| {mag:.2f} px)")
+    # the FP32 path itself is within 1e-3 px of the oracle at this size
+    assert oracle.epe(f32_b, ref_b) <= 1e-3 and oracle.epe(f32_f, ref_f) <= 1e-3
+    if prec == "fp16":
+        assert max(qb, qf) <= 0.05, (qb, qf)
+        assert max(eb, ef) <= 0.05, (eb, ef)
+    else:
+        bound = 2 * 2.0 ** -9 * np.sqrt(35) * mag
+        assert max(qb, qf, eb, ef) <= bound, (qb, qf, eb, ef, bound)
 
 
 def test_pipelined_state_errors():

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_common import bf16_round, nchw_to_nhwc, nhwc_to_nchw, to_dev, to_np, weights_file
+from gpu_common import REL16, nchw_to_nhwc, nhwc_to_nchw, round16, to_dev, to_np, weights_file
 
 pytestmark = pytest.mark.gpu
 tc = pytest.importorskip("paper_2301_00750_b300")
@@ -41,24 +41,27 @@ def test_sepconv_fp32_matches_oracle(n, h, w, cin, cout, dil, leaky):
         assert (err <= 1e-5 * (scale + 1.0)).all(), err.max()
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("n,h,w,cin,cout,dil,leaky", LAYER_CASES)
-def test_sepconv_bf16_matches_oracle(n, h, w, cin, cout, dil, leaky):
-    """BF16: the input is rounded on the host, the depthwise output is stored as bfloat16 and
-    the pointwise weights are bfloat16; the oracle follows the same roundings in FP64, so a
-    difference is at most one bf16 step of each depthwise output it sums over (where FP32
-    and FP64 round a value on either side of a midpoint) plus the output's own rounding."""
+def test_sepconv_16bit_matches_oracle(prec, n, h, w, cin, cout, dil, leaky):
+    """BF16 / FP16: the input is rounded on the host, the depthwise output is stored in the
+    16-bit type and so are the pointwise weights; the oracle follows the same roundings in
+    FP64, so a difference is at most one 16-bit step of each depthwise output it sums over
+    (where FP32 and FP64 round a value on either side of a midpoint) plus the output's own
+    rounding."""
     g = synth.rng(140 + cin)
-    x = bf16_round(g.normal(size=(n, cin, h, w)).astype(np.float32))
+    x = round16(prec, g.normal(size=(n, cin, h, w)).astype(np.float32))
     dw, db, pw, pb = _layer(g, cin, cout)
-    got = nhwc_to_nchw(to_np(tc.op_sepconv(to_dev(nchw_to_nhwc(x)), dw, db, pw, pb, dil, leaky, "bf16")))
+    got = nhwc_to_nchw(to_np(tc.op_sepconv(to_dev(nchw_to_nhwc(x)), dw, db, pw, pb, dil, leaky, prec)))
     assert tc.op_last_used_tensor_cores()
-    pw16 = bf16_round(pw.astype(np.float32))
+    pw16 = round16(prec, pw.astype(np.float32))
+    step = REL16[prec]
     for i in range(n):
-        d = bf16_round(oracle.depthwise3x3(x[i], dw.astype(np.float32), db.astype(np.float32), dil).astype(np.float32))
+        d = round16(prec, oracle.depthwise3x3(x[i], dw.astype(np.float32), db.astype(np.float32), dil).astype(np.float32))
         want = oracle.pointwise(d, pw16, pb.astype(np.float32), leaky)
         scale = np.abs(pw16) @ np.abs(d).reshape(cin, -1)
         err = np.abs(got[i] - want).reshape(cout, -1)
-        bound = 2.0 ** -8 * scale + (2.0 ** -8 * np.abs(want).reshape(cout, -1) if cout != 2 else 0) + 1e-6
+        bound = step * scale + (step * np.abs(want).reshape(cout, -1) if cout != 2 else 0) + 1e-6
         assert (err <= bound).all(), (err - bound).max()
 
 
@@ -106,19 +109,22 @@ def test_refined_stream_flows_fp32(chans, radius, W, H):
         assert eb <= 1e-3 and ef <= 1e-3, (eb, ef)
 
 
-def test_refined_stream_flows_bf16():
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_refined_stream_flows_16bit(prec):
+    """FP16 meets the fixed 0.05 px bar; BF16 its representation bound 2 u sqrt(n) of the mean
+    flow (u = 2^-9, with the 14 refinement convs counted in n)."""
     chans, radius = (16, 32, 64, 96, 128), 4
     path, net = weights_file(chans, radius, refine=True)
     frames, styl = _frames(200, 136, seed=3, n=2)
-    got, layers = _stream_flows(path, frames, styl, "bf16")
+    got, layers = _stream_flows(path, frames, styl, prec)
     assert layers == 34 + 7  # every pointwise refinement conv on the tensor cores too
     ref = oracle.Stream(net)
     r = [ref.step(I, P) for I, P in zip(frames, styl)][1]
     mag = float(np.sqrt((r["Fb"] ** 2).sum(0)).mean())
     n_layers = 3 * len(chans) + 5 * (len(chans) - 1) + 2 * 7
-    bound = max(0.05, 2 * 2.0 ** -9 * np.sqrt(n_layers) * mag)
+    bound = 0.05 if prec == "fp16" else max(0.05, 2 * 2.0 ** -9 * np.sqrt(n_layers) * mag)
     eb, ef = oracle.epe(got[0][0], r["Fb"]), oracle.epe(got[0][1], r["Ff"])
-    print(f"refined bf16 EPE vs FP64: Fb {eb:.4f} Ff {ef:.4f} (mean |F| {mag:.2f}, bound {bound:.4f})")
+    print(f"refined {prec} EPE vs FP64: Fb {eb:.4f} Ff {ef:.4f} (mean |F| {mag:.2f}, bound {bound:.4f})")
     assert eb <= bound and ef <= bound
 
 

@@ -4,15 +4,16 @@ Inputs are seeded (synth); expected values come from the oracle only.  Tolerance
 from float32 arithmetic: a sum of K products of O(1) terms carries an error of about
 K * 2^-24 relative to the sum of magnitudes, so conv outputs (K <= 9 * 211) are held to
 2e-5 of the output scale, the correlation (a mean over <= 128 channels) to 1e-5, the
-bilinear warps (4 taps) to 2e-6.  BF16 operands are rounded on the host first, so both
-sides see the same values; BF16 outputs are rounded to 8 significant bits (2^-9).
+bilinear warps (4 taps) to 2e-6.  BF16 / FP16 operands are rounded on the host first, so
+both sides see the same values; BF16 outputs are rounded to 8 significant bits (2^-9
+relative), FP16 outputs to 11 (2^-11).
 """
 import numpy as np
 import pytest
 
 import oracle
 import synth
-from gpu_common import bf16_round, nchw_to_nhwc, nhwc_to_nchw, planar_to_hw2, to_dev, to_np
+from gpu_common import REL16, nchw_to_nhwc, nhwc_to_nchw, planar_to_hw2, round16, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 tc = pytest.importorskip("paper_2301_00750_b300")
@@ -27,40 +28,37 @@ def test_upsample_flow(n, h, w, s):
         np.testing.assert_allclose(np.moveaxis(got[i], -1, 0), ref, rtol=1e-6, atol=1e-5)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 @pytest.mark.parametrize("n,h,w,c,mag", [(2, 17, 23, 8, 3.0), (1, 34, 60, 128, 6.0), (2, 136, 240, 64, 2.0)])
 def test_warp_features(prec, n, h, w, c, mag):
     g = synth.rng(21)
-    f = g.normal(size=(n, c, h, w)).astype(np.float32)
-    if prec == "bf16":
-        f = bf16_round(f)
+    f = round16(prec, g.normal(size=(n, c, h, w)).astype(np.float32))
     flow = g.uniform(-mag, mag, (n, 2, h, w)).astype(np.float32)
     got = to_np(tc.op_warp_features(to_dev(nchw_to_nhwc(f)), to_dev(np.moveaxis(flow, 1, -1)), precision=prec))
-    tol = 2e-6 if prec == "fp32" else 2 ** -8
+    tol = 2e-6 if prec == "fp32" else REL16[prec]
     for i in range(n):
         ref, _ = oracle.warp(f[i], flow[i], 1)
         np.testing.assert_allclose(nhwc_to_nchw(got[i:i + 1])[0], ref, rtol=tol, atol=tol * 4)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 @pytest.mark.parametrize("n,h,w,c,r", [(2, 19, 21, 32, 4), (1, 34, 60, 128, 4), (2, 8, 8, 48, 3), (2, 33, 47, 16, 2),
                                        (1, 21, 37, 24, 1), (3, 68, 120, 96, 4), (2, 136, 240, 64, 4)])
 def test_correlation(prec, n, h, w, c, r):
     g = synth.rng(22)
-    f1 = g.normal(size=(n, c, h, w)).astype(np.float32)
-    f2 = g.normal(size=(n, c, h, w)).astype(np.float32)
-    if prec == "bf16":
-        f1, f2 = bf16_round(f1), bf16_round(f2)
+    f1 = round16(prec, g.normal(size=(n, c, h, w)).astype(np.float32))
+    f2 = round16(prec, g.normal(size=(n, c, h, w)).astype(np.float32))
     got = to_np(tc.op_correlation(to_dev(nchw_to_nhwc(f1)), to_dev(nchw_to_nhwc(f2)), r, precision=prec))
-    # BF16 cost volumes with c a multiple of 8 up to 128 run on the tensor cores (banded GEMM)
-    assert tc.op_last_used_tensor_cores() == (prec == "bf16" and c % 8 == 0 and c <= 128)
+    # BF16 / FP16 cost volumes with c a multiple of 8 up to 128 run on the tensor cores
+    # (banded GEMM)
+    assert tc.op_last_used_tensor_cores() == (prec != "fp32" and c % 8 == 0 and c <= 128)
     for i in range(n):
         ref = oracle.correlation(f1[i], f2[i], r)
         g_ = nhwc_to_nchw(got[i:i + 1])[0]
         if prec == "fp32":
             np.testing.assert_allclose(g_, ref, rtol=1e-5, atol=1e-5)
         else:
-            np.testing.assert_allclose(g_, ref, rtol=2 ** -8, atol=1e-4)
+            np.testing.assert_allclose(g_, ref, rtol=REL16[prec], atol=1e-4)
 
 
 def test_correlation_finds_integer_shift():
@@ -95,17 +93,16 @@ CONV_CASES = [
 ]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 @pytest.mark.parametrize("n,h,w,cin,cout,stride", CONV_CASES)
 def test_conv3x3(prec, n, h, w, cin, cout, stride):
     g = synth.rng(24)
     x = g.normal(size=(n, cin, h, w)).astype(np.float32)
     wt = (g.normal(size=(cout, cin, 3, 3)) / np.sqrt(9 * cin)).astype(np.float32)
     b = g.normal(0, 0.1, cout).astype(np.float32)
-    if prec == "bf16":
-        x, wt = bf16_round(x), bf16_round(wt)
+    x, wt = round16(prec, x), round16(prec, wt)
     got = to_np(tc.op_conv3x3(to_dev(nchw_to_nhwc(x)), wt, b, stride=stride, leaky=True, precision=prec))
-    eligible = prec == "bf16" and cin % 8 == 0 and cout % 16 == 0 and cout <= 128
+    eligible = prec != "fp32" and cin % 8 == 0 and cout % 16 == 0 and cout <= 128
     assert tc.op_last_used_tensor_cores() == eligible
     for i in range(n):
         ref = oracle.conv3x3(x[i], wt, b, stride=stride, leaky=True)
@@ -114,7 +111,8 @@ def test_conv3x3(prec, n, h, w, cin, cout, stride):
         if prec == "fp32":
             np.testing.assert_allclose(g_, ref, rtol=0, atol=2e-5 * scale)
         else:
-            np.testing.assert_allclose(g_, ref, rtol=2 ** -8, atol=1e-3 * scale)
+            # the output's own rounding (relative) plus float32 accumulation order
+            np.testing.assert_allclose(g_, ref, rtol=REL16[prec], atol=(1e-3 if prec == "bf16" else 2.5e-4) * scale)
 
 
 # --------------------------------------------------------------------- consistency (K7)

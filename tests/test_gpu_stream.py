@@ -2,8 +2,10 @@
 against the oracle's stream.
 
 Staging of the tolerances (float32 vs the FP64 oracle):
-  * flows: average end-point error (Eq. 10) <= 1e-3 px per direction for the FP32 path and
-    <= 0.05 px (or 2 u sqrt(layers) of the mean flow, u = 2^-9) for the BF16 path;
+  * flows: average end-point error (Eq. 10) <= 1e-3 px per direction for the FP32 path,
+    <= 0.05 px for the FP16 path (the fixed-EPE bar of the 16-bit variants), and 2 u
+    sqrt(layers) of the mean flow (u = 2^-9) for the BF16 path, whose rounding of the
+    weights alone exceeds 0.05 px on the He-init networks (test_precision_cpu.py);
   * outputs: with alpha = 6.5e3 the photometric weight amplifies a flow difference of
     1e-4 px into weight differences of ~1e-2, so O_t is compared bit-for-bit only through
     the staged tests (identical flows, test_gpu_stages) and end to end with alpha = 0
@@ -98,34 +100,41 @@ def test_stream_flows_fp32(name, chans, radius, W, H):
         assert err[ok].max() <= max(1e-4, 1.0 * fmax), (err[ok].max(), fmax)
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("name,chans,radius,W,H", CASES)
-def test_stream_flows_bf16(name, chans, radius, W, H):
+def test_stream_flows_16bit(prec, name, chans, radius, W, H):
     path, net = weights_file(chans, radius)
     frames, styl = _pair(W, H, seed=1, n=2) if W != 64 else (
         [synth.pair64()["I0"], synth.pair64()["I1"]], [synth.pair64()["P0"], synth.pair64()["P1"]])
-    got = _run_gpu(path, frames, styl, prec="bf16", k1=0.5)
+    got = _run_gpu(path, frames, styl, prec=prec, k1=0.5)
     ref = _oracle_run(net, frames, styl, k1=0.5)
     eb = oracle.epe(got[1]["flows"][0], ref[1]["Fb"])
     ef = oracle.epe(got[1]["flows"][1], ref[1]["Ff"])
     mag = float(np.sqrt((ref[1]["Fb"] ** 2).sum(0)).mean())
-    print(f"{name}: bf16 EPE vs FP64 oracle: Fb {eb:.4f} px, Ff {ef:.4f} px (mean |F| {mag:.2f} px)")
-    # BF16 operands carry 8 significant bits (unit roundoff u = 2^-9).  Each of the n conv
-    # layers on the path to the flow adds an independent relative error of about u, so the
-    # flow's relative error is about u sqrt(n); the bound allows twice that: 0.05 px, or
-    # 2 u sqrt(n) of the mean flow magnitude where the He-init network's random flows are
-    # large (~10 px; about 2.3% for the 5-level net's n = 35 layers).
-    n_layers = 3 * len(chans) + 5 * (len(chans) - 1)
-    bound = max(0.05, 2 * 2.0 ** -9 * np.sqrt(n_layers) * mag)
-    assert eb <= bound and ef <= bound, (eb, ef, bound)
+    print(f"{name}: {prec} EPE vs FP64 oracle: Fb {eb:.4f} px, Ff {ef:.4f} px (mean |F| {mag:.2f} px)")
+    if prec == "fp16":
+        # the fixed-EPE bar, unwidened (measured <= 0.02 px)
+        assert eb <= 0.05 and ef <= 0.05, (eb, ef)
+    else:
+        # BF16 operands carry 8 significant bits (unit roundoff u = 2^-9).  Each of the n
+        # conv layers on the path to the flow adds an independent relative error of about u,
+        # so the flow's relative error is about u sqrt(n); the bound allows twice that of
+        # the mean flow magnitude (~10 px for the He-init networks; about 2.3% for the
+        # 5-level net's n = 35 layers).  It is above the 0.05 px bar: weight rounding alone
+        # moves these flows by more than 0.05 px.
+        n_layers = 3 * len(chans) + 5 * (len(chans) - 1)
+        bound = max(0.05, 2 * 2.0 ** -9 * np.sqrt(n_layers) * mag)
+        assert eb <= bound and ef <= bound, (eb, ef, bound)
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("chans,radius,want", [((16, 32, 48), 3, 18), ((16, 32, 64, 96, 128), 4, 34)])
-def test_bf16_stream_plans_convs_on_tensor_cores(chans, radius, want):
+def test_16bit_stream_plans_convs_on_tensor_cores(prec, chans, radius, want):
     """Every pyramid conv but the first (3 input channels), every estimator conv1..conv4 and
-    every flow head runs on the tensor cores in a BF16 stream, and so does the correlation of
-    every estimator level; an FP32 stream uses none."""
+    every flow head runs on the tensor cores in a BF16 or FP16 stream, and so does the
+    correlation of every estimator level; an FP32 stream uses none."""
     path, _ = weights_file(chans, radius)
-    s = tc.Stream(64, 64, "bf16", weights_path=path)
+    s = tc.Stream(64, 64, prec, weights_path=path)
     assert s.tensor_core_layers == want
     assert s.tensor_core_correlation_levels == len(chans) - 1
     s.destroy()
@@ -134,7 +143,7 @@ def test_bf16_stream_plans_convs_on_tensor_cores(chans, radius, want):
     s.destroy()
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 def test_host_entry_point_matches_device_entry_point(prec):
     """Host buffers in and out (P_t uploaded on a second stream while the flow network runs,
     the consistency pass waiting on it) give the device entry point's results bit for bit,
@@ -195,7 +204,7 @@ def test_stream_1080p_flows_fp32():
     assert eb <= 1e-3 and ef <= 1e-3
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 def test_graph_replay_matches_eager_launches(prec):
     """From the third frame on a stream replays one captured CUDA graph per t % 2 (state
     parity and pyramid slot), updating only the nodes that read the caller's buffers and the
