@@ -259,3 +259,29 @@ def test_blend_decomposes_into_eq2_and_eq5_weights():
     np.testing.assert_allclose(oracle.consistency(It, one, Ip, zero, zero, z, z, **kw)["O"], (1 - wp) ** 2, atol=1e-15)
     np.testing.assert_allclose(oracle.consistency(It, zero, Ip, one, zero, z, z, **kw)["O"], wp * (1 - wp), atol=1e-15)
     assert 0.05 < wp.mean() < 0.8
+
+
+@pytest.mark.parametrize("fb_u,ff_cols,ff_u,want_valid", [
+    # integer F_b = (+2, 0): F_f~(x) = F_f(x + 2); F_f = -2 on columns 3..5, so exactly the
+    # columns x with x + 2 in 3..5 pass the test (|F_b + F_f~|^2 = 0); elsewhere
+    # |2 + 0|^2 = 4 > 0.01 * 4 + 0.5.  Sampling F_f at x would give 3..5, at x - 2 5..7.
+    (2.0, (3, 4, 5), -2.0, (1, 2, 3)),
+    # fractional F_b = (+1.5, 0): F_f~(x) = (F_f(x + 1) + F_f(x + 2)) / 2; F_f = -1.5 on
+    # columns 4..6: x = 3, 4 see -1.5 (lhs 0, valid); x = 2, 5 see -0.75 (lhs 0.5625 >
+    # 0.01 * (2.25 + 0.5625) + 0.5 = 0.528, occluded); the rest see 0 (lhs 2.25, occluded).
+    (1.5, (4, 5, 6), -1.5, (3, 4)),
+])
+def test_fb_test_samples_forward_flow_at_backward_target(fb_u, ff_cols, ff_u, want_valid):
+    """The forward-backward test reads F_f where F_b points (F_f~ = Gamma_{F_b}(F_f), C6),
+    on a spatially varying F_f whose decision changes if it is read anywhere else; the mask
+    is hand-computed (columns past W - 1 - u are out of bounds either way)."""
+    h, w = 4, 10
+    It, Pt, Ip, Pp, Op = [np.full((3, h, w), 0.5) for _ in range(5)]
+    Fb = np.zeros((2, h, w))
+    Fb[0] = fb_u
+    Ff = np.zeros((2, h, w))
+    Ff[0][:, list(ff_cols)] = ff_u
+    r = oracle.consistency(It, Pt, Ip, Pp, Op, Fb, Ff, k1=0.5)
+    want = np.zeros((h, w), np.uint8)
+    want[:, list(want_valid)] = 1
+    assert np.array_equal(r["mask"], want), r["mask"][0]

@@ -168,3 +168,22 @@ def test_epe_definition():
     g[0] = 3.0
     g[1] = 4.0
     assert oracle.epe(f, g) == 5.0
+
+
+@pytest.mark.parametrize("r", [1, 2, 3])
+def test_bruteforce_tie_rule_smallest_norm_then_smallest_index(r):
+    """C12: a's vertical stripes are b's shifted by one column, so every odd horizontal
+    displacement (and any vertical one) gives SSD 0 in the interior.  The smallest |d| among
+    them is 1, at d = (-1, 0) and (+1, 0); the smaller index k = (dy + r)(2r + 1) + (dx + r)
+    wins, i.e. d = (-1, 0).  A rule by index alone, by the largest index, or by |d| then the
+    largest index each gives another k."""
+    h, w = 16, 18
+    cols = np.arange(w) % 2
+    b = np.broadcast_to(cols.astype(np.float64), (3, h, w)).copy()
+    a = 1.0 - b
+    k = oracle.bruteforce_flow(a, b, r)
+    want = r * (2 * r + 1) + (r - 1)
+    assert (k[r + 1:-(r + 1), r + 1:-(r + 1)] == want).all()
+    # flat images: every displacement ties at SSD 0 and the zero displacement wins
+    flat = np.full((1, h, w), 0.3)
+    assert (oracle.bruteforce_flow(flat, flat, r) == r * (2 * r + 1) + r).all()
