@@ -256,6 +256,15 @@ TC_API tc_status tc_get_amax(tc_stream *s, float *amax, int n);
  * cin and cout multiples of 16, cout <= 128). */
 TC_API tc_status tc_set_fp8_scales(tc_stream *s, const float *scales, int n);
 
+/* Static E4M3 activation scales from a calibration record (the reading of the supplement's
+ * 8-bit linear quantisation used here): scales[i] = margin * amax[i] / 448, so the largest
+ * calibrated |activation| of segment i, times margin, maps to the largest finite e4m3 value;
+ * a segment whose amax is 0 gets scale 0 (tc_set_fp8_scales takes it as 1).  amax and
+ * scales are host arrays of n floats (they may be the same array); margin > 0 and finite.
+ * Pure host arithmetic: needs no device and no stream.  Errors: TC_ERR_INVALID_ARG (NULL
+ * array, n < 1, margin not positive and finite, an amax negative or not finite). */
+TC_API tc_status tc_fp8_scales_from_amax(const float *amax, int n, float margin, float *scales);
+
 /* Writes the flows of the last processed frame at full resolution: Fb = F_{t->t-1} and
  * Ff = F_{t-1->t}, each device (2, H, W) float32 (planar u then v).  Either may be NULL.
  * Errors: TC_ERR_STATE before the second frame. */

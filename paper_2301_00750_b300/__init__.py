@@ -35,7 +35,6 @@ EXPORTED = ["tc_default_consistency", "tc_create_stream", "tc_set_consistency", 
             "tc_set_amax_recording", "tc_get_amax", "tc_set_fp8_scales", "tc_op_poisson_solve", "tc_set_latency",
             "tc_flush", "tc_last_output_frame", "tc_op_consistency_next", "tc_op_downscale2", "tc_op_sepconv",
             "tc_process_frame_host_async", "tc_set_pipelined", "tc_join"]
-E4M3_MAX = 448.0
 NOALLOC_SCRATCH_BYTES = 16 << 20
 PROFILE_CATEGORIES = ["pyramid_conv", "estimator_conv", "head", "correlation", "warp", "upsample", "consistency",
                       "other", "solver", "refine"]
@@ -87,6 +86,7 @@ _lib.tc_activation_segments.argtypes = [_vp]
 _lib.tc_set_amax_recording.argtypes = [_vp, _i]
 _lib.tc_get_amax.argtypes = [_vp, ctypes.POINTER(_f), _i]
 _lib.tc_set_fp8_scales.argtypes = [_vp, ctypes.POINTER(_f), _i]
+_lib.tc_fp8_scales_from_amax.argtypes = [ctypes.POINTER(_f), _i, _f, ctypes.POINTER(_f)]
 _lib.tc_get_profile.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), _i]
 _lib.tc_set_latency.argtypes = [_vp, _i]
 _lib.tc_op_downscale2.argtypes = [_vp, _i, _i, _i, _vp, _vp]
@@ -95,7 +95,7 @@ _lib.tc_flush.argtypes = [_vp, _vp, _vp, _vp]
 _lib.tc_last_output_frame.argtypes = [_vp]
 _lib.tc_last_output_frame.restype = ctypes.c_longlong
 _lib.tc_op_consistency_next.argtypes = [_vp] * 11 + [_i] * 5 + [ctypes.POINTER(TcConsistency), _vp, _vp, _vp, _vp]
-for _n in ["tc_set_amax_recording", "tc_get_amax", "tc_set_fp8_scales", "tc_set_graphs", "tc_op_correlation_bf16_noalloc", "tc_synchronize", "tc_set_profiling", "tc_get_profile", "tc_create_stream", "tc_set_consistency", "tc_process_frame", "tc_process_frame_host", "tc_get_flows",
+for _n in ["tc_set_amax_recording", "tc_get_amax", "tc_set_fp8_scales", "tc_fp8_scales_from_amax", "tc_set_graphs", "tc_op_correlation_bf16_noalloc", "tc_synchronize", "tc_set_profiling", "tc_get_profile", "tc_create_stream", "tc_set_consistency", "tc_process_frame", "tc_process_frame_host", "tc_get_flows",
            "tc_process_frame_host_async", "tc_set_pipelined", "tc_join", "tc_destroy", "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
            "tc_op_consistency", "tc_set_latency", "tc_flush", "tc_op_consistency_next", "tc_op_downscale2",
            "tc_op_sepconv"]:
@@ -309,10 +309,20 @@ class Stream:
             pass
 
 
+def fp8_scales_from_amax(amax, margin=1.0):
+    """tc_fp8_scales_from_amax: the static E4M3 activation scales of a calibration record."""
+    a = np.ascontiguousarray(amax, np.float32)
+    out = np.empty_like(a)
+    _check(_lib.tc_fp8_scales_from_amax(a.ctypes.data_as(ctypes.POINTER(_f)), int(a.size), float(margin),
+                                        out.ctypes.data_as(ctypes.POINTER(_f))))
+    return out
+
+
 def calibrate_fp8(width, height, frames, weights_path=None, weights_blob=None, margin=1.0, flow_downscale=1):
     """E4M3 scales from a BF16 pass: runs `frames` (a list of (I, P) CUDA (3, H, W) float32
     pairs) through a BF16 stream recording the amax of every activation segment, and returns
-    margin * amax / 448 per segment (the scales tc_set_fp8_scales takes)."""
+    the scales tc_fp8_scales_from_amax derives from that record (what tc_set_fp8_scales
+    takes)."""
     import torch
     s = Stream(width, height, "bf16", weights_path=weights_path, weights_blob=weights_blob,
                flow_downscale=flow_downscale)
@@ -324,7 +334,7 @@ def calibrate_fp8(width, height, frames, weights_path=None, weights_blob=None, m
         amax = s.get_amax()
     finally:
         s.destroy()
-    return (margin * amax / E4M3_MAX).astype(np.float32)
+    return fp8_scales_from_amax(amax, margin)
 
 
 # ----------------------------------------------------------------------------- stage ops

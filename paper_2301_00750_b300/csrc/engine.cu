@@ -1509,6 +1509,18 @@ extern "C" tc_status tc_get_amax(tc_stream *s, float *amax, int n) {
     return TC_OK;
 }
 
+extern "C" tc_status tc_fp8_scales_from_amax(const float *amax, int n, float margin, float *scales) {
+    if (!amax || !scales || n < 1) return fail(nullptr, TC_ERR_INVALID_ARG, "tc_fp8_scales_from_amax: NULL array or n < 1");
+    if (!std::isfinite(margin) || margin <= 0.f)
+        return fail(nullptr, TC_ERR_INVALID_ARG, "tc_fp8_scales_from_amax: margin must be positive and finite");
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(amax[i]) || amax[i] < 0.f)
+            return fail(nullptr, TC_ERR_INVALID_ARG, "tc_fp8_scales_from_amax: amax must be finite and >= 0");
+    // 448: the largest finite e4m3 value (4 exponent bits, bias 7, 3 mantissa bits)
+    for (int i = 0; i < n; ++i) scales[i] = margin * amax[i] / 448.f;
+    return TC_OK;
+}
+
 extern "C" tc_status tc_set_fp8_scales(tc_stream *s, const float *scales, int n) {
     tc_status r = check_stream(s, "tc_set_fp8_scales");
     if (r != TC_OK) return r;

@@ -155,3 +155,19 @@ def test_training_pairs_carry_their_flow():
         back = synth.resample(b, yy + f[1], xx + f[0])
         ok = np.abs(back - a).max(0) < 1e-3
         assert ok.mean() > 0.85, (seed, ok.mean())
+
+
+def test_fp8_scales_from_amax_is_host_arithmetic(lib):
+    """The static E4M3 activation scales are computed behind the C ABI (no device needed):
+    margin * amax / 448, zero for an all-zero segment; bad records are rejected."""
+    import numpy as np
+    amax = np.array([448.0, 1.0, 0.0, 3.5, 1e-3], np.float32)
+    got = lib.fp8_scales_from_amax(amax)
+    assert np.array_equal(got, (amax / np.float32(448)).astype(np.float32))
+    assert got[0] == 1.0 and got[2] == 0.0
+    got2 = lib.fp8_scales_from_amax(amax, margin=1.25)
+    np.testing.assert_allclose(got2, 1.25 * amax / 448, rtol=1e-6)
+    for bad_amax, margin in [([1.0, -1.0], 1.0), ([1.0, float("nan")], 1.0), ([1.0], 0.0), ([1.0], float("inf"))]:
+        with pytest.raises(lib.TcError) as e:
+            lib.fp8_scales_from_amax(np.array(bad_amax, np.float32), margin)
+        assert e.value.status == lib.TC_ERR_INVALID_ARG
