@@ -490,6 +490,26 @@ TC_API tc_status tc_server_close(tc_server *srv, int stream_id);
 TC_API tc_status tc_server_destroy(tc_server *srv);
 
 /* ------------------------------------------------------------------------------------
+ * Failure injection, for tests of the error paths only (process-wide; not for use in
+ * production).  Neither faults nor hangs the device: the failures are made on the host, or
+ * are a kernel that issues no work and whose bounded waits then run out.
+ * ---------------------------------------------------------------------------------- */
+
+/* The next `count` stride-1 tensor-core convolution launches made eagerly (not while the
+ * launching stream is being captured into a CUDA graph; a stream with graphs replays its
+ * captured launches from the third frame on, see tc_set_graphs) issue none of their loads:
+ * every CTA's MMA issuer waits for operands that never arrive until the wait limit (2 s),
+ * records a code in the stream's device error word, and the CTA frees its tensor memory
+ * and exits.  The stream then reports TC_ERR_TIMEOUT at tc_synchronize and is poisoned
+ * (later calls: TC_ERR_STATE).  count <= 0 disarms. */
+TC_API void tc_test_stall_next_convs(int count);
+
+/* The nth stream device allocation from now (nth >= 1; allocations of tc_create_stream and
+ * of the host-buffer entry points) fails as an out-of-memory cudaMalloc would, so the call
+ * returns TC_ERR_OOM after freeing what it had allocated.  nth <= 0 disarms. */
+TC_API void tc_test_fail_device_allocation(long long nth);
+
+/* ------------------------------------------------------------------------------------
  * Allocation-free variant.  The paper has no counterpart: this entry point exists for hosts
  * that cannot let the library allocate device memory -- an application whose memory pool
  * has reserved the device memory up front and passes only pre-allocated buffers, or a
@@ -501,21 +521,25 @@ TC_API tc_status tc_server_destroy(tc_server *srv);
 #define TC_NOALLOC_SCRATCH_BYTES (16u << 20)
 
 /* Same result as tc_op_correlation(TC_BF16, f1, f2, n, h, w, c, r, out, cuda_stream) -- the
- * bfloat16 cost volume returned as float32 -- but it allocates nothing: the bfloat16 copies
- * of f1, f2 and of the cost volume are staged in a fixed array of TC_NOALLOC_SCRATCH_BYTES in
- * device memory instead of temporary buffers.  Same arguments, layouts and limits as
- * tc_op_correlation (device NHWC float32 inputs, output (n, h, w, (2r+1)^2) float32).
- *   - Sizes: requires 2 * align256(2 n h w c) + align256(2 n h w (2r+1)^2) <=
+ * bfloat16 cost volume returned as float32, bit for bit: the same kernels run (the
+ * tensor-core correlation when c is a multiple of 8 up to 128, else the CUDA-core one, as
+ * tc_op_last_used_tensor_cores then reports) -- but it allocates nothing: the bfloat16
+ * copies of f1, f2 and of the cost volume, and the tensor-core kernel's error word, live in
+ * a fixed array of TC_NOALLOC_SCRATCH_BYTES in device memory instead of temporary buffers.
+ * Same arguments, layouts and limits as tc_op_correlation (device NHWC float32 inputs,
+ * output (n, h, w, (2r+1)^2) float32).
+ *   - Sizes: requires 2 * align256(2 n h w c) + align256(2 n h w (2r+1)^2) + 256 <=
  *     TC_NOALLOC_SCRATCH_BYTES, else TC_ERR_INVALID_ARG with the needed size in
  *     tc_last_error(NULL).
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call before any
- *     stream capture.
+ *     stream capture (a first call on a capturing stream returns TC_ERR_UNSUPPORTED).
  *   - Every call on a device shares the one array, which keeps the last call's contents
- *     (each call writes every byte it reads, so nothing needs clearing).  Calls whose work
- *     overlaps on the GPU (other streams, other host threads) race on it: order them on one
- *     stream or synchronise between them.
- *   - Enqueued on cuda_stream; returns without waiting. */
+ *     (each call writes every staged byte it reads and clears the error word first).  Calls
+ *     whose work overlaps on the GPU (other streams, other host threads) race on it: order
+ *     them on one stream or synchronise between them.
+ *   - Enqueued on cuda_stream; like tc_op_correlation it waits for completion, and returns
+ *     TC_ERR_TIMEOUT if a bounded tensor-core wait gave up. */
 TC_API tc_status tc_op_correlation_bf16_noalloc(const float *f1, const float *f2, int n, int h, int w, int c,
                                                int r, float *out, void *cuda_stream);
 

@@ -34,7 +34,8 @@ EXPORTED = ["tc_default_consistency", "tc_create_stream", "tc_set_consistency", 
             "tc_tensor_core_correlation_levels", "tc_set_graphs", "tc_activation_segments",
             "tc_set_amax_recording", "tc_get_amax", "tc_set_fp8_scales", "tc_op_poisson_solve", "tc_set_latency",
             "tc_flush", "tc_last_output_frame", "tc_op_consistency_next", "tc_op_downscale2", "tc_op_sepconv",
-            "tc_process_frame_host_async", "tc_set_pipelined", "tc_join"]
+            "tc_process_frame_host_async", "tc_set_pipelined", "tc_join", "tc_fp8_scales_from_amax",
+            "tc_test_stall_next_convs", "tc_test_fail_device_allocation"]
 NOALLOC_SCRATCH_BYTES = 16 << 20
 PROFILE_CATEGORIES = ["pyramid_conv", "estimator_conv", "head", "correlation", "warp", "upsample", "consistency",
                       "other", "solver", "refine"]
@@ -87,6 +88,10 @@ _lib.tc_set_amax_recording.argtypes = [_vp, _i]
 _lib.tc_get_amax.argtypes = [_vp, ctypes.POINTER(_f), _i]
 _lib.tc_set_fp8_scales.argtypes = [_vp, ctypes.POINTER(_f), _i]
 _lib.tc_fp8_scales_from_amax.argtypes = [ctypes.POINTER(_f), _i, _f, ctypes.POINTER(_f)]
+_lib.tc_test_stall_next_convs.argtypes = [_i]
+_lib.tc_test_stall_next_convs.restype = None
+_lib.tc_test_fail_device_allocation.argtypes = [ctypes.c_longlong]
+_lib.tc_test_fail_device_allocation.restype = None
 _lib.tc_get_profile.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), _i]
 _lib.tc_set_latency.argtypes = [_vp, _i]
 _lib.tc_op_downscale2.argtypes = [_vp, _i, _i, _i, _vp, _vp]
@@ -309,6 +314,16 @@ class Stream:
             pass
 
 
+def inject_stall_next_convs(count):
+    """tc_test_stall_next_convs (failure injection for tests of the timeout path)."""
+    _lib.tc_test_stall_next_convs(int(count))
+
+
+def inject_device_allocation_failure(nth):
+    """tc_test_fail_device_allocation (failure injection for tests of the OOM path)."""
+    _lib.tc_test_fail_device_allocation(int(nth))
+
+
 def fp8_scales_from_amax(amax, margin=1.0):
     """tc_fp8_scales_from_amax: the static E4M3 activation scales of a calibration record."""
     a = np.ascontiguousarray(amax, np.float32)
@@ -339,14 +354,26 @@ def calibrate_fp8(width, height, frames, weights_path=None, weights_blob=None, m
 
 # ----------------------------------------------------------------------------- stage ops
 
-def op_conv3x3(x, w, b, stride=1, leaky=True, precision="fp32", cuda_stream=None):
+def _out(out, shape, like, dtype=None):
+    """The caller's output buffer (checked: CUDA, contiguous, the op's shape and dtype), or a
+    new one."""
+    import torch
+    dtype = dtype or torch.float32
+    if out is None:
+        return torch.empty(shape, device=like.device, dtype=dtype)
+    if tuple(out.shape) != tuple(shape) or out.dtype != dtype or not out.is_cuda or not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous CUDA {dtype} tensor of shape {tuple(shape)}")
+    return out
+
+
+def op_conv3x3(x, w, b, stride=1, leaky=True, precision="fp32", cuda_stream=None, out=None):
     """x: CUDA (n, h, w, cin) float32; w: (cout, cin, 3, 3), b: (cout) on the host."""
     import torch
     n, h, wd, cin = x.shape
     w = np.ascontiguousarray(w, np.float32)
     b = np.ascontiguousarray(b, np.float32)
     cout = w.shape[0]
-    out = torch.empty((n, (h - 1) // stride + 1, (wd - 1) // stride + 1, cout), device=x.device, dtype=torch.float32)
+    out = _out(out, (n, (h - 1) // stride + 1, (wd - 1) // stride + 1, cout), x)
     _check(_lib.tc_op_conv3x3(PRECISION[precision], _ptr(x, torch.float32), n, h, wd, cin, w.ctypes.data,
                               b.ctypes.data, cout, stride, int(leaky), out.data_ptr(), _stream_handle(cuda_stream)))
     return out
@@ -356,10 +383,10 @@ def op_last_used_tensor_cores() -> bool:
     return bool(_lib.tc_op_last_used_tensor_cores())
 
 
-def op_correlation(f1, f2, r, precision="fp32", cuda_stream=None):
+def op_correlation(f1, f2, r, precision="fp32", cuda_stream=None, out=None):
     import torch
     n, h, w, c = f1.shape
-    out = torch.empty((n, h, w, (2 * r + 1) ** 2), device=f1.device, dtype=torch.float32)
+    out = _out(out, (n, h, w, (2 * r + 1) ** 2), f1)
     _check(_lib.tc_op_correlation(PRECISION[precision], _ptr(f1, torch.float32), _ptr(f2, torch.float32), n, h, w,
                                   c, r, out.data_ptr(), _stream_handle(cuda_stream)))
     return out
@@ -379,42 +406,42 @@ def op_correlation_bf16_noalloc(f1, f2, r, out=None, cuda_stream=None):
     return out
 
 
-def op_warp_features(f, flow, precision="fp32", cuda_stream=None):
+def op_warp_features(f, flow, precision="fp32", cuda_stream=None, out=None):
     import torch
     n, h, w, c = f.shape
-    out = torch.empty_like(f)
+    out = _out(out, (n, h, w, c), f)
     _check(_lib.tc_op_warp_features(PRECISION[precision], _ptr(f, torch.float32), _ptr(flow, torch.float32), n, h,
                                     w, c, out.data_ptr(), _stream_handle(cuda_stream)))
     return out
 
 
-def op_upsample_flow(flow, s, cuda_stream=None):
+def op_upsample_flow(flow, s, cuda_stream=None, out=None):
     import torch
     n, h, w, _ = flow.shape
-    out = torch.empty((n, s * h, s * w, 2), device=flow.device, dtype=torch.float32)
+    out = _out(out, (n, s * h, s * w, 2), flow)
     _check(_lib.tc_op_upsample_flow(_ptr(flow, torch.float32), n, h, w, s, out.data_ptr(),
                                     _stream_handle(cuda_stream)))
     return out
 
 
-def op_poisson_solve(P, A, wc, iters=150, eta=0.15, kappa=0.2, cuda_stream=None):
+def op_poisson_solve(P, A, wc, iters=150, eta=0.15, kappa=0.2, cuda_stream=None, out=None):
     """Eq. 1 by Eq. 8 from O = A: P, A (c, h, w), wc (h, w) float32 CUDA tensors."""
     import torch
     c, h, w = P.shape
-    O = torch.empty_like(P)
+    O = _out(out, (c, h, w), P)
     _check(_lib.tc_op_poisson_solve(_ptr(P, torch.float32, "P"), _ptr(A, torch.float32, "A"),
                                     _ptr(wc, torch.float32, "wc"), c, h, w, int(iters), float(eta), float(kappa),
                                     O.data_ptr(), _stream_handle(cuda_stream)))
     return O
 
 
-def op_sepconv(x, dw, db, pw, pb, dil=1, leaky=True, precision="fp32", cuda_stream=None):
+def op_sepconv(x, dw, db, pw, pb, dil=1, leaky=True, precision="fp32", cuda_stream=None, out=None):
     """One depthwise-separable refinement layer: x CUDA (n, h, w, cin) float32; dw (cin, 3, 3),
     db (cin), pw (cout, cin), pb (cout) on the host.  Returns (n, h, w, cout) float32."""
     import torch
     n, h, w, cin = x.shape
     cout = pw.shape[0]
-    out = torch.empty((n, h, w, cout), device=x.device, dtype=torch.float32)
+    out = _out(out, (n, h, w, cout), x)
     arr = [np.ascontiguousarray(a, np.float32) for a in (dw, db, pw, pb)]
     _check(_lib.tc_op_sepconv(PRECISION[precision], _ptr(x, torch.float32, "x"), n, h, w, cin,
                               *[a.ctypes.data for a in arr], cout, int(dil), int(bool(leaky)), out.data_ptr(),
@@ -422,11 +449,11 @@ def op_sepconv(x, dw, db, pw, pb, dil=1, leaky=True, precision="fp32", cuda_stre
     return out
 
 
-def op_downscale2(src, cuda_stream=None):
+def op_downscale2(src, cuda_stream=None, out=None):
     """(c, h, w) float32 CUDA -> (c, ceil(h/2), ceil(w/2)): 2x2 block means, edges replicated."""
     import torch
     c, h, w = src.shape
-    dst = torch.empty((c, (h + 1) // 2, (w + 1) // 2), device=src.device, dtype=torch.float32)
+    dst = _out(out, (c, (h + 1) // 2, (w + 1) // 2), src)
     _check(_lib.tc_op_downscale2(_ptr(src, torch.float32, "src"), c, h, w, dst.data_ptr(), _stream_handle(cuda_stream)))
     return dst
 

@@ -24,9 +24,11 @@
 #include <cudaTypedefs.h>
 #include <cuda_fp8.h>
 
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
+#include "../../include/tc_stream.h"
 #include "conv_tc.cuh"
 #include "tc_ptx.cuh"
 
@@ -71,6 +73,7 @@ struct TcLaunch {
     int taps;             // 9: 3x3 conv; 1: pointwise 1x1 conv (the centre tap only)
     int tail;             // halo kernel: the last channel step is a 64-byte tail
     int f16;              // 16-bit operands and outputs are IEEE half instead of bfloat16
+    int stall;            // halo kernel, test hook: the producer issues no loads (see tc_test_stall_next_convs)
 };
 
 // Epilogue shared by the conv kernels: thread r of the CTA owns accumulator row r, i.e.
@@ -334,7 +337,7 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     if (threadIdx.x == 0) {
         // ---- producer
         int ga = 0, gb = 0;  // halo loads and weight loads issued
-        bool fine = true;
+        bool fine = !p.stall;  // stalled (test hook): nothing is issued, so the MMA warp's waits run out
         for (int g = 0; g < ng && fine; ++g) {
             const int ky = g / p.nch, ch = g - ky * p.nch;
             const int sa = g % HALO_SA;
@@ -356,7 +359,8 @@ conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
             }
         }
         if (ga < ng || gb < 3 * ng) {
-            // Error path: let the loads already issued land before the CTA exits.
+            // Error path: let the loads already issued land before the CTA exits (none when
+            // stalled).
             const unsigned long long t0 = global_ns();
             for (int g = ga - HALO_SA < 0 ? 0 : ga - HALO_SA; g < ga; ++g)
                 while (!mbar_try(fullA + 8 * (g % HALO_SA), (uint32_t)(g / HALO_SA) & 1u))
@@ -554,6 +558,25 @@ conv_tc_rows_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     }
 }
 
+// Test hook: stride-1 conv launches still to stall (tc_test_stall_next_convs).
+std::atomic<int> g_stall_next{0};
+
+// 1 if this launch takes one of the armed stalls: never while st is being captured into a
+// graph, so no graph ever bakes a stall in.
+int take_stall(cudaStream_t st) {
+    if (g_stall_next.load() <= 0) return 0;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return 0;
+    int k = g_stall_next.load();
+    while (k > 0 && !g_stall_next.compare_exchange_weak(k, k - 1)) {
+    }
+    return k > 0 ? 1 : 0;
+}
+
 template <int BN, bool HEAD = false, bool F8 = false>
 cudaError_t launch_bn(const TcConvPlan &plan, const TcLaunch &lp, int n_img, cudaStream_t st) {
     dim3 grid((plan.wo + BM - 1) / BM, plan.ho, n_img);
@@ -585,6 +608,7 @@ cudaError_t launch_bn(const TcConvPlan &plan, const TcLaunch &lp, int n_img, cud
         }
         TcLaunch lt = lp;
         lt.tail = plan.tail ? 1 : 0;
+        lt.stall = take_stall(st);
         return launch_pdl(conv_tc_halo_kernel<BN, HEAD, F8>, grid, dim3(128), smem, st, plan.tmA, plan.tmB,
                           plan.tail ? plan.tmA2 : plan.tmA, plan.tail ? plan.tmB2 : plan.tmB, lt);
     } else {
@@ -835,3 +859,5 @@ cudaError_t launch_conv_tc_f32(const TcConvPlan &plan, const ConvArgs &a, bool a
 }
 
 }  // namespace tc
+
+extern "C" void tc_test_stall_next_convs(int count) { tc::g_stall_next.store(count > 0 ? count : 0); }

@@ -1,6 +1,7 @@
 // Stream engine and C ABI (see include/tc_stream.h): per-stream device state, weight
 // loading, the per-frame launch sequence of the flow network and the consistency step,
 // and the single-stage entry points.
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -413,10 +414,16 @@ static tc_status cuda_fail(tc_stream *s, cudaError_t e, const char *what) {
         if (_e != cudaSuccess) return cuda_fail(stream, _e, what);  \
     } while (0)
 
+// Test hook (tc_test_fail_device_allocation): the stream device allocation that brings
+// this countdown from 1 to 0 fails as an out-of-memory cudaMalloc would.
+static std::atomic<long long> g_alloc_fail_countdown{0};
+
 static tc_status dalloc(tc_stream *s, void **p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(p, bytes);
+    bool inject = false;
+    if (g_alloc_fail_countdown.load() > 0) inject = g_alloc_fail_countdown.fetch_sub(1) == 1;
+    cudaError_t e = inject ? cudaErrorMemoryAllocation : cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -1981,6 +1988,10 @@ static tc_status op_conv(const float *in, int n, int h, int w, int cin, const fl
 }
 
 extern "C" int tc_op_last_used_tensor_cores(void) { return g_last_op_tc; }
+
+extern "C" void tc_test_fail_device_allocation(long long nth) { g_alloc_fail_countdown.store(nth > 0 ? nth : 0); }
+
+void tc_set_last_op_tensor_cores(int used) { g_last_op_tc = used ? 1 : 0; }
 
 extern "C" tc_status tc_op_conv3x3(tc_precision precision, const float *in, int n, int h, int w, int cin,
                                    const float *w_oihw, const float *bias, int cout, int stride, int leaky,

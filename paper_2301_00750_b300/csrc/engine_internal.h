@@ -45,3 +45,7 @@ size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precisi
 
 // Records the error of a stream-less call (read back with tc_last_error(NULL)).
 tc_status tc_record_error(tc_status code, const std::string &msg);
+
+// Sets what tc_op_last_used_tensor_cores() reports (1: the last stage op ran on the tensor
+// cores, 0: on the CUDA cores).
+void tc_set_last_op_tensor_cores(int used);

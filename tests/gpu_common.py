@@ -77,3 +77,41 @@ def weight_scales_e4m3(w):
     planning does (w: (cout, cin, 3, 3) float32)."""
     a = np.abs(np.asarray(w, np.float32)).reshape(w.shape[0], -1).max(1)
     return np.where(a > 0, a / np.float32(448), np.float32(1)).astype(np.float32)
+
+
+# Canary padding (the stand-in for a memory checker): an output buffer with guard elements
+# on both sides, all set to a marker no kernel writes (a NaN with payload 0xDEAD for float32,
+# 0xA5 for bytes).  After a call the guards must be intact (no out-of-bounds write) and the
+# output region free of markers (every element written).
+CANARY = 4096
+_MARK = {"float32": 0x7FC0DEAD, "uint8": 0xA5}
+
+
+def guarded(shape, dtype="float32"):
+    """(buffer, view): a CUDA buffer of CANARY + prod(shape) + CANARY elements, all set to the
+    marker, and the contiguous view of the middle (16 KiB-aligned for float32)."""
+    import torch
+    n = int(np.prod(shape))
+    tdt = {"float32": torch.float32, "uint8": torch.uint8}[dtype]
+    buf = torch.empty(2 * CANARY + n, dtype=tdt, device="cuda")
+    if dtype == "float32":
+        buf.view(torch.int32).fill_(_MARK[dtype])
+    else:
+        buf.fill_(_MARK[dtype])
+    return buf, buf[CANARY:CANARY + n].view(*shape)
+
+
+def check_guarded(buf, shape, dtype="float32", written=True):
+    """Asserts the guards are intact and, with written, that no marker is left inside."""
+    import torch
+    n = int(np.prod(shape))
+    raw = buf.view(torch.int32) if dtype == "float32" else buf
+    m = _MARK[dtype]
+    a = raw.cpu().numpy()
+    if dtype == "float32":
+        a = a.view(np.uint32)
+        m = np.uint32(m)
+    assert (a[:CANARY] == m).all(), "write before the output buffer"
+    assert (a[CANARY + n:] == m).all(), "write past the output buffer"
+    if written:
+        assert not (a[CANARY:CANARY + n] == m).any(), "output elements left unwritten"
