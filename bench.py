@@ -506,6 +506,10 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
+    gemm_peaks = measure_gemm_peaks(torch) if not args.skip_peaks else {}
+    fp32_peak = gemm_peaks.get("fp32_tflops") or FP32_SIMT_PEAK_TFLOPS
+    fp32_peak_source = ("of measured fp32 SGEMM (this run, TF32 off)" if gemm_peaks.get("fp32_tflops")
+                        else "derived: 148 SM x 128 FP32 lanes x 2 x 2032 MHz")
     flops = conv_flops_per_frame(net_spec())
     p = prof["profile"]
     steps = args.steps
@@ -518,23 +522,25 @@ def run_ours(args):
     peaks = measured_peaks()
     if dom == "solver":
         achieved = SOLVER_FLOPS_PER_PX_ITER * 3 * WIDTH * HEIGHT * args.solver_iters * steps / (p[dom][0] / 1e3) / 1e12
-        peak, unit, bound = FP32_SIMT_PEAK_TFLOPS, "TFLOP/s", "alu"
+        peak, unit, bound = fp32_peak, "TFLOP/s", "alu"
     elif dom in ("estimator_conv", "pyramid_conv", "head", "correlation"):
         achieved = flops[dom] * steps / (p[dom][0] / 1e3) / 1e12
         if tensor_path and args.precision == "fp8":
-            # no measured e4m3 peak: the bf16 one x the nominal dense fp8 : bf16 ratio (4.5 : 2.25)
-            peak, unit, bound = 2 * peaks.get("bf16_tflops"), "TFLOP/s", "tensor"
+            # the e4m3 GEMM peak measured in this run, else the bf16 one x the nominal dense
+            # fp8 : bf16 ratio (4.5 : 2.25)
+            peak, unit, bound = gemm_peaks.get("e4m3_tflops") or 2 * peaks.get("bf16_tflops"), "TFLOP/s", "tensor"
         elif tensor_path:
             peak, unit, bound = peaks.get("bf16_tflops"), "TFLOP/s", "tensor"
         else:
-            peak, unit, bound = FP32_SIMT_PEAK_TFLOPS, "TFLOP/s", "alu"
+            peak, unit, bound = fp32_peak, "TFLOP/s", "alu"
     else:
         achieved = CONSISTENCY_BYTES_PER_PX * WIDTH * HEIGHT * steps / (p[dom][0] / 1e3) / 1e9
         peak, unit, bound = peaks.get("hbm_gbs"), "GB/s", "hbm"
     if bound == "alu":
-        peak_source = "derived: 148 SM x 128 FP32 lanes x 2 x 2032 MHz"
+        peak_source = fp32_peak_source
     elif bound == "tensor" and args.precision == "fp8":
-        peak_source = "of measured bf16 burst x 2 (nominal dense fp8:bf16), MEASURED_PEAKS.json"
+        peak_source = ("of measured e4m3 cuBLAS GEMM (this run)" if gemm_peaks.get("e4m3_tflops") else
+                       "of measured bf16 burst x 2 (nominal dense fp8:bf16), MEASURED_PEAKS.json")
     elif bound == "tensor":
         peak_source = ("of measured bf16 burst (MEASURED_PEAKS.json; fp16 and bf16 have the same nominal "
                        "dense rate)" if args.precision == "fp16" else "of measured bf16 burst (MEASURED_PEAKS.json)")
@@ -574,6 +580,8 @@ def run_ours(args):
                      "api": "tc_process_frame_host, which waits for each frame (its P_t upload overlaps the "
                             "flow network)"},
     }
+    if gemm_peaks:
+        line["measured_gemm_peaks"] = gemm_peaks
     if variants:
         line["variants"] = variants
         if args.precision in variants:
@@ -599,10 +607,10 @@ def run_ours(args):
             # 9 flops (3 adds, 3 FMAs) per pixel, channel and iteration, on the CUDA cores
             "roofline": {"kernel": "solver", "bound": "alu",
                          "achieved": round(SOLVER_FLOPS_PER_PX_ITER * 3 * WIDTH * HEIGHT * SOLVER_ITERS / (ms / 1e3) / 1e12, 3),
-                         "peak": round(FP32_SIMT_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
+                         "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
                          "frac": round(SOLVER_FLOPS_PER_PX_ITER * 3 * WIDTH * HEIGHT * SOLVER_ITERS / (ms / 1e3) / 1e12
-                                       / FP32_SIMT_PEAK_TFLOPS, 4),
-                         "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2032 MHz"},
+                                       / fp32_peak, 4),
+                         "peak_source": fp32_peak_source},
             "note": "Eq. 1 by Eq. 8 (eta 0.15, kappa 0.2) after the blend, time-blocked 8 iterations per launch"}
         pipelined_value(line["with_solver"], svq, n)
     if refined is not None:
@@ -646,6 +654,49 @@ def measured_peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "_fallback": True}
+
+
+def measure_gemm_peaks(torch, n=8192, reps=8):
+    """Dense peaks the way the bf16 one is measured: the best of `reps` cuBLAS GEMMs of
+    n^3 (2 n^3 flop each, CUDA events) -- e4m3 x e4m3 -> bf16 through torch._scaled_mm
+    (unit scales) and float32 x float32 with TF32 off (the CUDA cores' FMA path)."""
+    out = {}
+
+    def best(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        return 2.0 * n ** 3 / min(ts) / 1e12
+
+    try:
+        a8 = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+        b8 = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn).t()  # column-major operand
+        one = torch.ones((), device="cuda")
+        out["e4m3_tflops"] = round(best(lambda: torch._scaled_mm(a8, b8, one, one, out_dtype=torch.bfloat16)), 1)
+        del a8, b8
+    except Exception as e:  # noqa: BLE001 (reported, not fatal)
+        out["e4m3_error"] = str(e)[:200]
+    tf32 = torch.backends.cuda.matmul.allow_tf32
+    try:
+        torch.backends.cuda.matmul.allow_tf32 = False
+        a = torch.randn(n, n, device="cuda")
+        b = torch.randn(n, n, device="cuda")
+        out["fp32_tflops"] = round(best(lambda: torch.matmul(a, b)), 2)
+        del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+    torch.cuda.empty_cache()
+    out["how"] = (f"best of {reps} cuBLAS GEMMs of {n}^3 (2 n^3 flop): torch._scaled_mm e4m3 x e4m3 -> bf16, "
+                  f"and torch.matmul float32 with TF32 off (CUDA-core FMA)")
+    return out
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -911,6 +962,7 @@ def main():
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-fp8", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-peaks", action="store_true", help="skip measuring the e4m3 and fp32 GEMM peaks")
     ap.add_argument("--skip-solver", action="store_true")
     ap.add_argument("--skip-latency", action="store_true")
     ap.add_argument("--sequential", action="store_true",
