@@ -490,6 +490,48 @@ TC_API tc_status tc_server_close(tc_server *srv, int stream_id);
 TC_API tc_status tc_server_destroy(tc_server *srv);
 
 /* ------------------------------------------------------------------------------------
+ * Batches: `lanes` independent streams of one size whose networks run in shared launches.
+ * The serving problem of Sec. 3.1 (many streams, each with its own per-frame state) at a
+ * load where several streams have a frame ready at once: their feature pyramids and flow
+ * estimations run as one launch per layer over every lane's images (both directions of
+ * every lane in the estimators) instead of one launch per stream.  Each lane is a causal
+ * stream of its own (O_1 = P_1, then Eqs. 2-7 with w_n = 0 and O_t := A_t): its own frame
+ * count, state (I, P, O of its previous frame) and consistency controls; a lane's results
+ * are those of a tc_create_stream stream given the same frames, bit for bit, whichever other
+ * lanes run in the same step.  TC_FP32, TC_BF16 or TC_FP16; no solver, one frame of
+ * latency, fast preset or refinement network (TC_ERR_UNSUPPORTED), and the stream-only
+ * calls (tc_process_frame*, tc_get_flows, tc_set_pipelined, ...) answer TC_ERR_STATE.
+ * ---------------------------------------------------------------------------------- */
+
+/* Creates a batch of 1 <= lanes <= 64 lanes (desc as for tc_create_stream; flow_downscale
+ * 0 or 1).  Every lane starts at its first frame with the default controls.  Device memory:
+ * about `lanes` times a stream's, without the host-entry staging. */
+TC_API tc_status tc_create_batch(const tc_stream_desc *desc, int lanes, void *cuda_stream, tc_stream **out);
+
+/* One frame for each of n distinct lanes (lanes[k] in [0, lanes)): device planar (3, H, W)
+ * float32 I_t[k], P_t[k] in, O_t[k] out (caller-owned, as tc_process_frame), w_c and mask
+ * optional (wc_opt / mask_opt NULL, or arrays whose entries may be NULL).  The pyramids and
+ * flow estimations of lanes min(lanes) .. max(lanes) run in shared launches (the range's
+ * launches are captured into a CUDA graph on its second use and replayed from then on);
+ * lanes inside that range without a frame in this step are computed too, but keep their
+ * state.  Enqueued on the batch's CUDA stream; returns without waiting. */
+TC_API tc_status tc_process_lanes(tc_stream *s, int n, const int *lanes, const float *const *I_t,
+                                  const float *const *P_t, float *const *O_t, float *const *wc_opt,
+                                  uint8_t *const *mask_opt);
+
+/* Consistency controls of one lane (tc_set_consistency on a batch sets every lane's).
+ * solver_iters must be 0. */
+TC_API tc_status tc_set_lane_consistency(tc_stream *s, int lane, const tc_consistency *p);
+
+/* The lane's next frame is a first frame (a new stream takes the lane); its controls go
+ * back to the defaults. */
+TC_API tc_status tc_reset_lane(tc_stream *s, int lane);
+
+/* The lane's flows of its last frame pair, as tc_get_flows (device (2, H, W) float32 each,
+ * NULL to skip); TC_ERR_STATE before its second frame. */
+TC_API tc_status tc_get_lane_flows(tc_stream *s, int lane, float *Fb, float *Ff);
+
+/* ------------------------------------------------------------------------------------
  * Failure injection, for tests of the error paths only (process-wide; not for use in
  * production).  Neither faults nor hangs the device: the failures are made on the host, or
  * are a kernel that issues no work and whose bounded waits then run out.

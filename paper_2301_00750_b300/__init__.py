@@ -35,7 +35,8 @@ EXPORTED = ["tc_default_consistency", "tc_create_stream", "tc_set_consistency", 
             "tc_set_amax_recording", "tc_get_amax", "tc_set_fp8_scales", "tc_op_poisson_solve", "tc_set_latency",
             "tc_flush", "tc_last_output_frame", "tc_op_consistency_next", "tc_op_downscale2", "tc_op_sepconv",
             "tc_process_frame_host_async", "tc_set_pipelined", "tc_join", "tc_fp8_scales_from_amax",
-            "tc_test_stall_next_convs", "tc_test_fail_device_allocation"]
+            "tc_test_stall_next_convs", "tc_test_fail_device_allocation", "tc_create_batch", "tc_process_lanes",
+            "tc_set_lane_consistency", "tc_reset_lane", "tc_get_lane_flows"]
 NOALLOC_SCRATCH_BYTES = 16 << 20
 PROFILE_CATEGORIES = ["pyramid_conv", "estimator_conv", "head", "correlation", "warp", "upsample", "consistency",
                       "other", "solver", "refine"]
@@ -88,6 +89,14 @@ _lib.tc_set_amax_recording.argtypes = [_vp, _i]
 _lib.tc_get_amax.argtypes = [_vp, ctypes.POINTER(_f), _i]
 _lib.tc_set_fp8_scales.argtypes = [_vp, ctypes.POINTER(_f), _i]
 _lib.tc_fp8_scales_from_amax.argtypes = [ctypes.POINTER(_f), _i, _f, ctypes.POINTER(_f)]
+_lib.tc_create_batch.argtypes = [ctypes.POINTER(TcStreamDesc), _i, _vp, ctypes.POINTER(_vp)]
+_lib.tc_process_lanes.argtypes = [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                  ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp)]
+_lib.tc_set_lane_consistency.argtypes = [_vp, _i, ctypes.POINTER(TcConsistency)]
+_lib.tc_reset_lane.argtypes = [_vp, _i]
+_lib.tc_get_lane_flows.argtypes = [_vp, _i, _vp, _vp]
+for _n in ("tc_create_batch", "tc_process_lanes", "tc_set_lane_consistency", "tc_reset_lane", "tc_get_lane_flows"):
+    getattr(_lib, _n).restype = ctypes.c_int
 _lib.tc_test_stall_next_convs.argtypes = [_i]
 _lib.tc_test_stall_next_convs.restype = None
 _lib.tc_test_fail_device_allocation.argtypes = [ctypes.c_longlong]
@@ -331,6 +340,54 @@ def fp8_scales_from_amax(amax, margin=1.0):
     _check(_lib.tc_fp8_scales_from_amax(a.ctypes.data_as(ctypes.POINTER(_f)), int(a.size), float(margin),
                                         out.ctypes.data_as(ctypes.POINTER(_f))))
     return out
+
+
+class Batch(Stream):
+    """tc_create_batch: `lanes` independent causal streams of one size whose pyramids and
+    flow estimations run in shared launches; process() takes one frame for each of several
+    lanes.  The single-stream calls of Stream answer TC_ERR_STATE on a batch."""
+
+    def __init__(self, width, height, lanes, precision="fp16", weights_path=None, weights_blob=None,
+                 cuda_stream=None):
+        desc = TcStreamDesc()
+        desc.width, desc.height = int(width), int(height)
+        desc.flow_downscale = 1
+        desc.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        self._blob = None
+        if weights_path is not None:
+            desc.weights_path = os.fsencode(weights_path)
+        elif weights_blob is not None:
+            self._blob = ctypes.create_string_buffer(bytes(weights_blob), len(weights_blob))
+            desc.weights_blob = ctypes.cast(self._blob, ctypes.c_void_p)
+            desc.weights_bytes = len(weights_blob)
+        h = _vp()
+        self.cuda_stream = _stream_handle(cuda_stream)
+        _check(_lib.tc_create_batch(ctypes.byref(desc), int(lanes), self.cuda_stream, ctypes.byref(h)))
+        self._h = h
+        self.width, self.height, self.lanes = int(width), int(height), int(lanes)
+
+    def process(self, lanes, I, P, O, wc=None, mask=None):
+        """One frame for each lane in `lanes`: lists of CUDA (3, H, W) float32 tensors I, P, O
+        (and optional (H, W) float32 wc, uint8 mask lists) in the order of `lanes`."""
+        import torch
+        n = len(lanes)
+        ln = (_i * n)(*[int(x) for x in lanes])
+        arr = lambda xs, dt, nm: (_vp * n)(*[_ptr(x, dt, nm) for x in xs]) if xs is not None else None
+        _check(_lib.tc_process_lanes(self._h, n, ln, arr(I, torch.float32, "I_t"), arr(P, torch.float32, "P_t"),
+                                     arr(O, torch.float32, "O_t"), arr(wc, torch.float32, "wc"),
+                                     arr(mask, torch.uint8, "mask")), self._h)
+
+    def set_lane_consistency(self, lane, **kw):
+        c = _consistency_struct(**kw)
+        _check(_lib.tc_set_lane_consistency(self._h, int(lane), ctypes.byref(c)), self._h)
+
+    def reset_lane(self, lane):
+        _check(_lib.tc_reset_lane(self._h, int(lane)), self._h)
+
+    def get_lane_flows(self, lane, Fb=None, Ff=None):
+        import torch
+        _check(_lib.tc_get_lane_flows(self._h, int(lane), _ptr(Fb, torch.float32, "Fb"), _ptr(Ff, torch.float32, "Ff")),
+               self._h)
 
 
 def calibrate_fp8(width, height, frames, weights_path=None, weights_blob=None, margin=1.0, flow_downscale=1):

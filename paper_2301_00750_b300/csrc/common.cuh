@@ -152,6 +152,13 @@ struct CorrArgs {
     // CUDA-core kernel only: when set, batch entry b reads fs[0] + b * fs_img and
     // fo[0] + b * fo_img (elements) instead of the per-entry pointers (any n)
     size_t fs_img, fo_img;
+    // Lane pairs (batched streams, pair_lanes > 0; with fs_img and fo_img set): entry b is
+    // direction b & 1 of lane q = b >> 1, and the feature maps are two slots of pair_lanes
+    // images (slot 0: the lanes' current frames, slot 1: their previous ones).  self =
+    // fs[0] + (q + (b & 1) pair_lanes) fs_img; other = fo[0] + (q + (1 - (b & 1))
+    // pair_lanes) fo_img when pair_other (both from the slots), else fo[0] + b fo_img.
+    int pair_lanes;
+    int pair_other;
 };
 
 struct WarpArgs {
@@ -170,6 +177,10 @@ struct WarpArgs {
     int act_cs;
     float act_q;  // the up-flow is multiplied by act_q before the activation store (1 unless e4m3)
     size_t f_img;  // when set, batch entry b reads f[0] + b * f_img (elements; any n)
+    // Lane pairs (batched streams, pair_lanes > 0; with f_img set): entry b is direction
+    // b & 1 of lane q = b >> 1 and reads the other frame's features, f[0] + (q + (1 - (b & 1))
+    // pair_lanes) f_img (slot 0: the lanes' current frames, slot 1: their previous ones).
+    int pair_lanes;
 };
 
 struct UpArgs {

@@ -66,6 +66,11 @@ struct CorrTcLaunch {
     int *err;
     int rb;       // bytes of channels per step (128, or 64: 32 bf16 channels with the 64-byte swizzle)
     int f16;      // 16-bit features and cost volume are IEEE half instead of bfloat16
+    // Lane pairs (pair_lanes > 0, any number of entries): entry z is direction d = z & 1 of
+    // lane q = z >> 1; self image s0 + q + d pair_lanes, other image o0 + q oq + d od; the
+    // self copy reads fs[0] + (q + d pair_lanes) fs_img_bytes.
+    int pair_lanes, s0, o0, oq, od;
+    size_t fs_img_bytes;
 };
 
 template <int R, bool F8>
@@ -82,6 +87,11 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.z, x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    // images of this entry in the self and other tensor maps (selects, not a runtime index
+    // into the argument arrays)
+    const int pq = b >> 1, pd = b & 1;
+    const int img_self = p.pair_lanes ? p.s0 + pq + pd * p.pair_lanes : (b ? p.img_s[1] : p.img_s[0]);
+    const int img_other = p.pair_lanes ? p.o0 + pq * p.oq + pd * p.od : (b ? p.img_o[1] : p.img_o[0]);
 
     if (threadIdx.x == 0) {
         for (int ch = 0; ch < MAX_NCH; ++ch) mbar_init(full0 + 8 * ch, 1);
@@ -106,8 +116,8 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
             const uint32_t fb = full0 + 8 * ch;
             mbar_expect_tx(fb, (uint32_t)(BX * BY + G::NPOS) * (uint32_t)p.rb);
             const int c0 = ch * (F8 ? p.rb : p.rb / 2);  // a step: rb bytes of e4m3 or bf16 channels
-            tma_load_4d(&tmS, fb, smem_u32(sA + ch * A_BYTES), c0, x0, y0, b ? p.img_s[1] : p.img_s[0]);
-            tma_load_4d(&tmO, fb, smem_u32(sB + ch * G::B_BYTES), c0, x0 - R, y0 - R, b ? p.img_o[1] : p.img_o[0]);
+            tma_load_4d(&tmS, fb, smem_u32(sA + ch * A_BYTES), c0, x0, y0, img_self);
+            tma_load_4d(&tmO, fb, smem_u32(sB + ch * G::B_BYTES), c0, x0 - R, y0 - R, img_other);
         }
     } else if (threadIdx.x == 32) {
         // ---- MMA issuer: D[:, 0:NH] and D[:, NH:NP]
@@ -231,8 +241,10 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
             }
             if (p.self_copy) {
                 const size_t esz = F8 ? 1 : 2;
-                const uint4 *src = reinterpret_cast<const uint4 *>(static_cast<const uint8_t *>(b ? p.fs[1] : p.fs[0]) +
-                                                                   ((size_t)y * p.w + x) * p.c * esz);
+                const uint8_t *fsb = p.pair_lanes ? static_cast<const uint8_t *>(p.fs[0]) +
+                                                        (size_t)(pq + pd * p.pair_lanes) * p.fs_img_bytes
+                                                  : static_cast<const uint8_t *>(b ? p.fs[1] : p.fs[0]);
+                const uint4 *src = reinterpret_cast<const uint4 *>(fsb + ((size_t)y * p.w + x) * p.c * esz);
                 uint4 *cp = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(p.self_copy) + pix * p.out_cs * esz);
                 for (int q = 0; q < (int)(p.c * esz / 16); ++q) cp[q] = __ldg(src + q);
             }
@@ -308,6 +320,57 @@ bool tc_plan_corr(CorrTcPlan &plan, const void *self, int n_self, int self_cs, c
     return true;
 }
 
+static cudaError_t launch_plan(const CorrTcPlan &plan, const CorrTcLaunch &lp, int nb, cudaStream_t st) {
+    if (plan.f8) {
+        switch (plan.r) {
+            case 1: return launch_r<1, true>(plan, lp, nb, st);
+            case 2: return launch_r<2, true>(plan, lp, nb, st);
+            case 3: return launch_r<3, true>(plan, lp, nb, st);
+            case 4: return launch_r<4, true>(plan, lp, nb, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (plan.r) {
+        case 1: return launch_r<1, false>(plan, lp, nb, st);
+        case 2: return launch_r<2, false>(plan, lp, nb, st);
+        case 3: return launch_r<3, false>(plan, lp, nb, st);
+        case 4: return launch_r<4, false>(plan, lp, nb, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_corr_tc_pairs(const CorrTcPlan &plan, int lanes, int pair_lanes, int s0, int o0, int oq, int od,
+                                 void *out, int out_cs, const void *fs0, size_t fs_img_bytes, void *self_copy,
+                                 cudaStream_t st) {
+    if (!plan.enabled || plan.f8 || lanes < 1 || pair_lanes < 1 || 2 * lanes > 65535) return cudaErrorInvalidValue;
+    const int esz = 2;
+    if (self_copy && ((out_cs * esz) % 16 != 0 || reinterpret_cast<uintptr_t>(self_copy) % 16 != 0 || !fs0 ||
+                      reinterpret_cast<uintptr_t>(fs0) % 16 != 0 || fs_img_bytes % 16 != 0))
+        return cudaErrorInvalidValue;
+    CorrTcLaunch lp{};
+    lp.h = plan.h;
+    lp.w = plan.w;
+    lp.nch = plan.nch;
+    lp.rb = plan.rb;
+    lp.out = out;
+    lp.out_cs = out_cs;
+    lp.vec_out = ((out_cs * esz) % 16 == 0 && reinterpret_cast<uintptr_t>(out) % 16 == 0) ? 1 : 0;
+    lp.c = plan.c;
+    lp.fs[0] = lp.fs[1] = fs0;
+    lp.self_copy = self_copy;
+    lp.scale = 1.f / (float)plan.c;
+    lp.q_out = 1.f;
+    lp.err = plan.err;
+    lp.f16 = plan.f16 ? 1 : 0;
+    lp.pair_lanes = pair_lanes;
+    lp.s0 = s0;
+    lp.o0 = o0;
+    lp.oq = oq;
+    lp.od = od;
+    lp.fs_img_bytes = fs_img_bytes;
+    return launch_plan(plan, lp, 2 * lanes, st);
+}
+
 cudaError_t launch_corr_tc(const CorrTcPlan &plan, int nb, const int img_self[2], const int img_other[2], void *out,
                            int out_cs, const void *const fs[2], void *self_copy, cudaStream_t st, float feat_scale,
                            float q_out) {
@@ -335,22 +398,7 @@ cudaError_t launch_corr_tc(const CorrTcPlan &plan, int nb, const int img_self[2]
     lp.q_out = q_out;
     lp.err = plan.err;
     lp.f16 = plan.f16 ? 1 : 0;
-    if (plan.f8) {
-        switch (plan.r) {
-            case 1: return launch_r<1, true>(plan, lp, nb, st);
-            case 2: return launch_r<2, true>(plan, lp, nb, st);
-            case 3: return launch_r<3, true>(plan, lp, nb, st);
-            case 4: return launch_r<4, true>(plan, lp, nb, st);
-            default: return cudaErrorInvalidValue;
-        }
-    }
-    switch (plan.r) {
-        case 1: return launch_r<1, false>(plan, lp, nb, st);
-        case 2: return launch_r<2, false>(plan, lp, nb, st);
-        case 3: return launch_r<3, false>(plan, lp, nb, st);
-        case 4: return launch_r<4, false>(plan, lp, nb, st);
-        default: return cudaErrorInvalidValue;
-    }
+    return launch_plan(plan, lp, nb, st);
 }
 
 }  // namespace tc

@@ -42,4 +42,12 @@ cudaError_t launch_corr_tc(const CorrTcPlan &plan, int nb, const int img_self[2]
                            int out_cs, const void *const fs[2], void *self_copy, cudaStream_t st,
                            float feat_scale = 1.f, float q_out = 1.f);
 
+// Lane pairs (batched streams): 2 lanes entries, entry z = direction d = z & 1 of lane
+// q = z >> 1, correlates image s0 + q + d pair_lanes of the self buffer with image
+// o0 + q oq + d od of the other buffer and writes to out + ((z h + y) w + x) out_cs; the
+// self copy (if set) reads fs0 + (q + d pair_lanes) fs_img_bytes.  16-bit features only.
+cudaError_t launch_corr_tc_pairs(const CorrTcPlan &plan, int lanes, int pair_lanes, int s0, int o0, int oq, int od,
+                                 void *out, int out_cs, const void *fs0, size_t fs_img_bytes, void *self_copy,
+                                 cudaStream_t st);
+
 }  // namespace tc

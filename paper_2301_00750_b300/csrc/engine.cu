@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -172,7 +173,11 @@ constexpr int NSET = 2;
 // pyramid slots (t % 4): one captured graph per t % NGRAPH.
 constexpr int NGRAPH = 4;
 
-size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precision prec, int fs) {
+size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precision prec, int fs, int lanes) {
+    // a single stream (lanes = 0) keeps NPYR pyramid slots and NSET estimator sets; a batch
+    // of `lanes` lanes keeps two slots (current, previous) and one set per lane
+    const size_t npyr = lanes ? 2 * (size_t)lanes : NPYR, nest = lanes ? 2 * (size_t)lanes : 2 * NSET;
+    const size_t nl = lanes ? (size_t)lanes : 1;
     const int L = net.levels, D = (2 * net.radius + 1) * (2 * net.radius + 1), m = 1 << L;
     const bool f8 = prec == TC_FP8_E4M3;
     const size_t es = prec == TC_FP32 ? 4 : (f8 ? 1 : 2);
@@ -190,7 +195,7 @@ size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precisi
     for (int l = 1; l <= L; ++l) {
         const size_t h = Hp >> l, w = Wp >> l, px = h * w;
         const int c = net.chans[l - 1];
-        total += al(NPYR * px * c * es) + 2 * al(px * c * es);
+        total += al(npyr * px * c * es) + 2 * al(nl * px * c * es);
         total += al((size_t)9 * prev * c * 4) + al((size_t)c * 4) + 2 * (al((size_t)9 * c * c * 4) + al((size_t)c * 4));
         if (l > 1) total += tcw(prev, c);
         total += 2 * tcw(c, c);
@@ -198,7 +203,7 @@ size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precisi
         if (l < 2) continue;
         const int x0p = round_up(c + D + 2, f8 ? 16 : 8);
         const int ctot = x0p + net.dec[0] + net.dec[1] + net.dec[2] + net.dec[3];
-        total += al(NSET * 2 * px * ctot * es) + al(NSET * 2 * px * c * es) + 2 * al(NSET * 2 * px * 2 * 4);
+        total += al(nest * px * ctot * es) + al(nest * px * c * es) + 2 * al(nest * px * 2 * 4);
         const int cin[5] = {x0p, net.dec[0], net.dec[1], net.dec[1] + net.dec[2], net.dec[2] + net.dec[3]};
         const int cout[5] = {net.dec[0], net.dec[1], net.dec[2], net.dec[3], 2};
         for (int j = 0; j < 5; ++j) {
@@ -207,6 +212,7 @@ size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precisi
         }
     }
     const size_t img = al((size_t)3 * height * width * 4), plane = (size_t)height * width;
+    if (lanes) return total + 6 * al((size_t)3 * height * width * 4 * nl);  // state I, P, O x 2 slots per lane
     total += 6 * img;                                        // state I, P, O x 2 slots
     total += 3 * img + al(plane * 4) + al(plane);            // host-entry staging
     if (fs > 1) total += al((size_t)3 * hn * wn * 4);        // the downscaled frame
@@ -385,6 +391,22 @@ struct tc_stream {
     std::vector<RefLayer> ref;
     void *refD = nullptr, *refP = nullptr;
     int refD_cs = 0, refP_cs = 0;
+    // batch (tc_create_batch): `lanes` independent causal streams of one size whose feature
+    // pyramids and flow estimations run in shared launches (the lanes are the images of
+    // every buffer); per lane its frame count, its state slot and its consistency controls.
+    // The pyramid buffers hold two slots of `lanes` images: slot 0 the current frames, slot
+    // 1 every lane's previous frame (copied from slot 0 after each step of the lane).
+    bool batch = false;
+    int lanes = 1;
+    int npyr = NPYR;       // images of a level's pyramid buffer
+    int n_est = 2 * NSET;  // images of a level's estimator buffers
+    std::vector<long long> lane_t;
+    std::vector<int> lane_cur;  // state slot the lane's next frame writes
+    std::vector<tc_consistency> lane_params;
+    // the shared launches of lanes [lo, lo + n), key lo * 4096 + n: uses so far, and the
+    // graph captured on the second use
+    std::map<int, int> range_uses;
+    std::map<int, FrameGraph> range_graphs;
 };
 
 static std::mutex g_err_mu;
@@ -499,6 +521,13 @@ extern "C" tc_status tc_set_consistency(tc_stream *s, const tc_consistency *p) {
     if (!s || !p) return fail(s, TC_ERR_INVALID_ARG, "tc_set_consistency: NULL argument");
     std::string why;
     if (!valid_params(p, why)) return fail(s, TC_ERR_INVALID_ARG, why);
+    if (s->batch) {
+        // a batch: every lane's controls (tc_set_lane_consistency sets one lane's)
+        if (p->solver_iters != 0) return fail(s, TC_ERR_UNSUPPORTED, "tc_set_consistency: a batch runs without the solver");
+        for (auto &lp : s->lane_params) lp = *p;
+        s->params = *p;
+        return TC_OK;
+    }
     if (s->latency && !(p->k1 + p->k2 < 1.f))
         return fail(s, TC_ERR_INVALID_ARG, "with the next-frame term k1 + k2 must be < 1");
     if (p->solver_iters > 0 && !s->sv_A) {
@@ -632,9 +661,9 @@ static tc_status build_stream(tc_stream *s) {
         B.w = s->Wp >> l;
         B.c = net.chans[l - 1];
         const size_t px = (size_t)B.h * B.w;
-        if ((r = dalloc(s, &B.pyr, NPYR * px * B.c * es)) != TC_OK) return r;
-        if ((r = dalloc(s, &B.tmpA, px * B.c * es)) != TC_OK) return r;
-        if ((r = dalloc(s, &B.tmpB, px * B.c * es)) != TC_OK) return r;
+        if ((r = dalloc(s, &B.pyr, s->npyr * px * B.c * es)) != TC_OK) return r;
+        if ((r = dalloc(s, &B.tmpA, s->lanes * px * B.c * es)) != TC_OK) return r;
+        if ((r = dalloc(s, &B.tmpB, s->lanes * px * B.c * es)) != TC_OK) return r;
         for (int j = 0; j < 3; ++j) {
             const HostLayer &HL = net.layers[3 * (l - 1) + j];
             std::vector<float> wk;
@@ -664,11 +693,11 @@ static tc_status build_stream(tc_stream *s) {
             if (j == 0) {
                 LevelBufs &P = s->lv[l - 2];
                 ConvArgs a{P.pyr, P.c, 1, P.h, P.w, P.c, 2, B.h, B.w, nullptr, nullptr, B.c, B.tmpA, B.c, 1};
-                add_layer(s, s->pyr_plan[l - 1][0], a, NPYR, wk, std::vector<int>(P.c, seg_pyr(s, l - 1, 2)), false);
+                add_layer(s, s->pyr_plan[l - 1][0], a, s->npyr, wk, std::vector<int>(P.c, seg_pyr(s, l - 1, 2)), false);
             } else {
                 ConvArgs a{j == 1 ? B.tmpA : B.tmpB, B.c, 1, B.h, B.w, B.c, 1, B.h, B.w, nullptr, nullptr, B.c,
                            B.tmpB, B.c, 1};
-                add_layer(s, s->pyr_plan[l - 1][j], a, 1, wk, std::vector<int>(B.c, seg_pyr(s, l, j - 1)), false);
+                add_layer(s, s->pyr_plan[l - 1][j], a, s->lanes, wk, std::vector<int>(B.c, seg_pyr(s, l, j - 1)), false);
             }
         }
         if (l < 2) continue;
@@ -680,12 +709,13 @@ static tc_status build_stream(tc_stream *s) {
         B.off_x3 = B.off_x2 + net.dec[1];
         B.off_x4 = B.off_x3 + net.dec[2];
         B.ctot = B.off_x4 + net.dec[3];
-        if ((r = dalloc(s, &B.dec, NSET * 2 * px * B.ctot * es)) != TC_OK) return r;
-        TC_TRY(s, cudaMemset(B.dec, 0, NSET * 2 * px * B.ctot * es), "memset");
-        if ((r = dalloc(s, &B.f2w, NSET * 2 * px * B.c * es)) != TC_OK) return r;
-        if ((r = dalloc_t(s, &B.flow, NSET * 2 * px * 2 * sizeof(float))) != TC_OK) return r;
-        if ((r = dalloc_t(s, &B.up, NSET * 2 * px * 2 * sizeof(float))) != TC_OK) return r;
-        TC_TRY(s, cudaMemset(B.up, 0, NSET * 2 * px * 2 * sizeof(float)), "memset");
+        const size_t ne = (size_t)s->n_est;
+        if ((r = dalloc(s, &B.dec, ne * px * B.ctot * es)) != TC_OK) return r;
+        TC_TRY(s, cudaMemset(B.dec, 0, ne * px * B.ctot * es), "memset");
+        if ((r = dalloc(s, &B.f2w, ne * px * B.c * es)) != TC_OK) return r;
+        if ((r = dalloc_t(s, &B.flow, ne * px * 2 * sizeof(float))) != TC_OK) return r;
+        if ((r = dalloc_t(s, &B.up, ne * px * 2 * sizeof(float))) != TC_OK) return r;
+        TC_TRY(s, cudaMemset(B.up, 0, ne * px * 2 * sizeof(float)), "memset");
         const HostLayer *E = &net.layers[3 * L + 5 * (L - l)];
         // conv1 reads x0 (padded to x0p), conv2 x1, conv3 x2, conv4 [x2 | x3], head [x3 | x4].
         std::vector<int> p1(B.x0p, -1), g1(B.x0p, -1);
@@ -710,7 +740,7 @@ static tc_status build_stream(tc_stream *s) {
             T *dec = static_cast<T *>(B.dec);
             ConvArgs a{dec + in_off[j], B.ctot, 2, B.h, B.w, cin[j], 1, B.h, B.w, nullptr, nullptr, net.dec[j],
                        dec + B.off_x1, B.ctot, 1};
-            add_layer(s, B.tcplan[j], a, 2 * NSET, wk, segs[j], false);
+            add_layer(s, B.tcplan[j], a, s->n_est, wk, segs[j], false);
         }
         std::vector<float> wk5 = simt_weights(E[4], p5, s->prec);
         if ((r = upload(s, &B.head_w, wk5)) != TC_OK) return r;
@@ -719,7 +749,7 @@ static tc_status build_stream(tc_stream *s) {
             std::string why;
             // level L correlates the two pyramid slots; finer levels correlate with f2w
             const void *other = l == L ? B.pyr : B.f2w;
-            if (tc_plan_corr(B.corrplan, B.pyr, NPYR, B.c, other, l == L ? NPYR : 2 * NSET, B.c, B.h, B.w, B.c,
+            if (tc_plan_corr(B.corrplan, B.pyr, s->npyr, B.c, other, l == L ? s->npyr : s->n_est, B.c, B.h, B.w, B.c,
                              s->R, s->dev_err, why, false, s->prec == TC_FP16))
                 s->tc_corr_levels += 1;
         }
@@ -727,11 +757,11 @@ static tc_status build_stream(tc_stream *s) {
             T *dec = static_cast<T *>(B.dec);
             ConvArgs a{dec + B.off_x3, B.ctot, 2, B.h, B.w, net.dec[2] + net.dec[3], 1, B.h, B.w, nullptr, nullptr, 2,
                        nullptr, 2, 0};
-            add_layer(s, B.headplan, a, 2 * NSET, wk5, g5, true);
+            add_layer(s, B.headplan, a, s->n_est, wk5, g5, true);
         }
     }
     if (!net.ref.empty() && (r = build_refine<T>(s)) != TC_OK) return r;
-    const size_t img = (size_t)3 * s->H * s->W * sizeof(float);
+    const size_t img = (size_t)3 * s->H * s->W * sizeof(float) * s->lanes;
     for (int k = 0; k < 2; ++k) {
         if ((r = dalloc_t(s, &s->sI[k], img)) != TC_OK) return r;
         if ((r = dalloc_t(s, &s->sP[k], img)) != TC_OK) return r;
@@ -741,7 +771,8 @@ static tc_status build_stream(tc_stream *s) {
     return TC_OK;
 }
 
-extern "C" tc_status tc_create_stream(const tc_stream_desc *desc, void *cuda_stream, tc_stream **out) {
+// A stream (lanes = 0) or a batch of `lanes` lanes (tc_create_batch).
+static tc_status create_impl(const tc_stream_desc *desc, void *cuda_stream, tc_stream **out, int lanes) {
     if (out) *out = nullptr;
     if (!desc || !out) return fail(nullptr, TC_ERR_INVALID_ARG, "tc_create_stream: NULL argument");
     if (desc->precision != TC_FP32 && desc->precision != TC_BF16 && desc->precision != TC_FP8_E4M3 &&
@@ -768,6 +799,21 @@ extern "C" tc_status tc_create_stream(const tc_stream_desc *desc, void *cuda_str
     }
     std::string err;
     if (!parse_weights(blob.data(), blob.size(), s->net, err)) return fail(nullptr, TC_ERR_IO, err);
+    if (lanes) {
+        if (desc->precision == TC_FP8_E4M3)
+            return fail(nullptr, TC_ERR_UNSUPPORTED, "tc_create_batch: a batch runs in TC_FP32, TC_BF16 or TC_FP16");
+        if (desc->flow_downscale == 2 || !s->net.ref.empty())
+            return fail(nullptr, TC_ERR_UNSUPPORTED,
+                        "tc_create_batch: a batch runs the causal path without the fast preset or the refinement");
+        s->batch = true;
+        s->lanes = lanes;
+        s->npyr = 2 * lanes;
+        s->n_est = 2 * lanes;
+        s->lane_t.assign(lanes, 0);
+        s->lane_cur.assign(lanes, 0);
+        s->lane_params.resize(lanes);
+        for (auto &lp : s->lane_params) tc_default_consistency(&lp);
+    }
     s->L = s->net.levels;
     s->R = s->net.radius;
     s->D = (2 * s->R + 1) * (2 * s->R + 1);
@@ -805,6 +851,18 @@ extern "C" tc_status tc_create_stream(const tc_stream_desc *desc, void *cuda_str
     }
     *out = s.release();
     return TC_OK;
+}
+
+extern "C" tc_status tc_create_stream(const tc_stream_desc *desc, void *cuda_stream, tc_stream **out) {
+    return create_impl(desc, cuda_stream, out, 0);
+}
+
+extern "C" tc_status tc_create_batch(const tc_stream_desc *desc, int lanes, void *cuda_stream, tc_stream **out) {
+    if (lanes < 1 || lanes > 64) {
+        if (out) *out = nullptr;
+        return fail(nullptr, TC_ERR_INVALID_ARG, "tc_create_batch: lanes must lie in [1, 64]");
+    }
+    return create_impl(desc, cuda_stream, out, lanes);
 }
 
 // Folds the pending profiling events of s into its per-category totals.
@@ -1030,6 +1088,14 @@ static tc_status run_estimators(tc_stream *s, int pcur, int pprev, int set) {
 static tc_status check_stream(tc_stream *s, const char *fn) {
     if (!s) return fail(nullptr, TC_ERR_INVALID_ARG, std::string(fn) + ": NULL stream");
     if (s->poisoned) return fail(s, TC_ERR_STATE, std::string(fn) + ": stream is poisoned by an earlier CUDA error: " + s->err);
+    return TC_OK;
+}
+
+// The entry points of a single stream refuse a batch.
+static tc_status single_only(tc_stream *s, const char *fn) {
+    tc_status r = check_stream(s, fn);
+    if (r != TC_OK) return r;
+    if (s->batch) return fail(s, TC_ERR_STATE, std::string(fn) + ": not available on a batch (tc_create_batch)");
     return TC_OK;
 }
 
@@ -1465,6 +1531,9 @@ static void release_graphs(tc_stream *s) {
     for (auto &G : s->pg_pyr) release_graph(G);
     for (auto &G : s->pg_est) release_graph(G);
     for (auto &G : s->pg_blend) release_graph(G);
+    for (auto &kv : s->range_graphs) release_graph(kv.second);
+    s->range_graphs.clear();
+    s->range_uses.clear();
 }
 
 static void release_graph_stream(tc_stream *s) {
@@ -1496,7 +1565,7 @@ static void release_graph_stream(tc_stream *s) {
 extern "C" int tc_activation_segments(const tc_stream *s) { return s ? n_segments(s) : 0; }
 
 extern "C" tc_status tc_set_amax_recording(tc_stream *s, int enable) {
-    tc_status r = check_stream(s, "tc_set_amax_recording");
+    tc_status r = single_only(s, "tc_set_amax_recording");
     if (r != TC_OK) return r;
     if (s->pipelined) return fail(s, TC_ERR_STATE, "tc_set_amax_recording: not available in pipelined mode");
     if (s->prec == TC_FP8_E4M3) return fail(s, TC_ERR_INVALID_ARG, "amax recording needs a TC_FP32, TC_BF16 or TC_FP16 stream");
@@ -1529,7 +1598,7 @@ extern "C" tc_status tc_fp8_scales_from_amax(const float *amax, int n, float mar
 }
 
 extern "C" tc_status tc_set_fp8_scales(tc_stream *s, const float *scales, int n) {
-    tc_status r = check_stream(s, "tc_set_fp8_scales");
+    tc_status r = single_only(s, "tc_set_fp8_scales");
     if (r != TC_OK) return r;
     if (s->prec != TC_FP8_E4M3) return fail(s, TC_ERR_INVALID_ARG, "tc_set_fp8_scales: not a TC_FP8_E4M3 stream");
     if (!scales || n != n_segments(s)) return fail(s, TC_ERR_INVALID_ARG, "tc_set_fp8_scales: need tc_activation_segments() scales");
@@ -1577,7 +1646,7 @@ extern "C" tc_status tc_set_fp8_scales(tc_stream *s, const float *scales, int n)
         LevelBufs &B = s->lv[l - 1];
         std::string why;
         const void *other = l == s->L ? B.pyr : B.f2w;
-        if (!tc_plan_corr(B.corrplan, B.pyr, NPYR, B.c, other, l == s->L ? NPYR : 2 * NSET, B.c, B.h, B.w, B.c,
+        if (!tc_plan_corr(B.corrplan, B.pyr, s->npyr, B.c, other, l == s->L ? s->npyr : s->n_est, B.c, B.h, B.w, B.c,
                           s->R, s->dev_err, why, true))
             return fail(s, TC_ERR_UNSUPPORTED, "e4m3 correlation not eligible for the tensor cores: " + why);
         s->tc_corr_levels += 1;
@@ -1595,9 +1664,238 @@ extern "C" tc_status tc_set_graphs(tc_stream *s, int enable) {
     return TC_OK;
 }
 
+// ------------------------------------------------------------------------------- batch
+
+// The first pyramid conv of one lane: its frame I -> the lane's image of the level-1
+// scratch buffer.
+template <typename T>
+static tc_status lane_first(tc_stream *s, int lane, const float *I) {
+    const LevelBufs &B = s->lv[0];
+    ConvFirstArgs f = first_args(s, I);
+    f.out = static_cast<T *>(B.tmpA) + (size_t)lane * B.h * B.w * B.c;
+    TC_LAUNCH_CAT(s, TC_PROF_PYRAMID_CONV, launch_conv_first<T>(f, s->st));
+    return TC_OK;
+}
+
+// The shared launches of lanes [lo, lo + n): the feature pyramids of their current frames
+// (after each lane's first conv) into pyramid slot 0, then both flow directions of every
+// lane, entry 2q + d of the estimator buffers being direction d of lane lo + q (d = 0: the
+// current frame against the previous one, F_{t->t-1}; d = 1: F_{t-1->t}).  Every launch
+// covers all 2n (pyramid: n) images; the warp and the correlation find each entry's frames
+// in the two pyramid slots (lane pairs).
+template <typename T>
+static tc_status lanes_network(tc_stream *s, int lo, int n) {
+    tc_status r;
+    const HostNet &net = s->net;
+    const int NL = s->lanes;
+    for (int l = 1; l <= s->L; ++l) {
+        LevelBufs &B = s->lv[l - 1];
+        const size_t img = (size_t)B.h * B.w * B.c;
+        T *tA = static_cast<T *>(B.tmpA) + lo * img, *tB = static_cast<T *>(B.tmpB) + lo * img;
+        T *cur = static_cast<T *>(B.pyr) + lo * img;
+        if (l > 1) {
+            LevelBufs &P = s->lv[l - 2];
+            const T *src = static_cast<const T *>(P.pyr) + (size_t)lo * P.h * P.w * P.c;
+            ConvArgs a{src, P.c, n, P.h, P.w, P.c, 2, B.h, B.w, s->pyr_w[3 * (l - 1)], s->pyr_b[3 * (l - 1)],
+                       B.c, tA, B.c, 1, 1.f};
+            if ((r = conv_layer<T>(s, a, &s->pyr_plan[l - 1][0], TC_PROF_PYRAMID_CONV)) != TC_OK) return r;
+        }
+        ConvArgs b{tA, B.c, n, B.h, B.w, B.c, 1, B.h, B.w, s->pyr_w[3 * (l - 1) + 1], s->pyr_b[3 * (l - 1) + 1],
+                   B.c, tB, B.c, 1, 1.f};
+        if ((r = conv_layer<T>(s, b, &s->pyr_plan[l - 1][1], TC_PROF_PYRAMID_CONV)) != TC_OK) return r;
+        ConvArgs c{tB, B.c, n, B.h, B.w, B.c, 1, B.h, B.w, s->pyr_w[3 * (l - 1) + 2], s->pyr_b[3 * (l - 1) + 2],
+                   B.c, cur, B.c, 1, 1.f};
+        if ((r = conv_layer<T>(s, c, &s->pyr_plan[l - 1][2], TC_PROF_PYRAMID_CONV)) != TC_OK) return r;
+    }
+    const int ne = 2 * n;
+    for (int l = s->L; l >= 2; --l) {
+        LevelBufs &B = s->lv[l - 1];
+        const size_t px = (size_t)B.h * B.w, img = px * B.c;
+        const T *pyr0 = static_cast<const T *>(B.pyr) + lo * img;  // slot 0, lane lo (slot 1: + NL images)
+        T *dec = static_cast<T *>(B.dec) + (size_t)2 * lo * px * B.ctot;
+        T *f2w = static_cast<T *>(B.f2w) + (size_t)2 * lo * img;
+        float *flow = B.flow + (size_t)2 * lo * px * 2, *up = B.up + (size_t)2 * lo * px * 2;
+        if (l < s->L) {
+            const LevelBufs &C = s->lv[l];
+            const float *cflow = C.flow + (size_t)2 * lo * C.h * C.w * 2;
+            WarpArgs wa{{pyr0, pyr0}, B.c, nullptr, ne, B.h, B.w, B.c, f2w, B.c, cflow, up, dec + B.c + s->D, B.ctot,
+                        1.f, img, NL};
+            TC_LAUNCH_CAT(s, TC_PROF_WARP, launch_warp<T>(wa, s->st));
+        }
+        if (B.corrplan.enabled) {
+            // self: image d NL + lo + q of the pyramid; other: the pyramid's other slot at
+            // the coarsest level, else entry 2 (lo + q) + d of the warped features
+            const bool top = l == s->L;
+            TC_LAUNCH_CAT(s, TC_PROF_CORRELATION,
+                          launch_corr_tc_pairs(B.corrplan, n, NL, lo, top ? lo + NL : 2 * lo, top ? 1 : 2,
+                                               top ? -NL : 1, dec + B.c, B.ctot, pyr0, img * sizeof(T), dec, s->st));
+        } else {
+            const T *fo0 = l == s->L ? pyr0 : f2w;
+            CorrArgs ca{{pyr0, pyr0}, {fo0, fo0}, B.c, B.c, ne, B.h, B.w, B.c, s->R, dec + B.c, B.ctot, dec, img, img,
+                        NL, l == s->L ? 1 : 0};
+            TC_LAUNCH_CAT(s, TC_PROF_CORRELATION, launch_corr<T>(ca, s->st));
+        }
+        ConvArgs c1{dec, B.ctot, ne, B.h, B.w, B.x0p, 1, B.h, B.w, B.wk[0], B.bias[0], net.dec[0], dec + B.off_x1, B.ctot, 1, 1.f};
+        if ((r = conv_layer<T>(s, c1, &B.tcplan[0], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
+        ConvArgs c2{dec + B.off_x1, B.ctot, ne, B.h, B.w, net.dec[0], 1, B.h, B.w, B.wk[1], B.bias[1], net.dec[1], dec + B.off_x2, B.ctot, 1, 1.f};
+        if ((r = conv_layer<T>(s, c2, &B.tcplan[1], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
+        ConvArgs c3{dec + B.off_x2, B.ctot, ne, B.h, B.w, net.dec[1], 1, B.h, B.w, B.wk[2], B.bias[2], net.dec[2], dec + B.off_x3, B.ctot, 1, 1.f};
+        if ((r = conv_layer<T>(s, c3, &B.tcplan[2], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
+        ConvArgs c4{dec + B.off_x2, B.ctot, ne, B.h, B.w, net.dec[1] + net.dec[2], 1, B.h, B.w, B.wk[3], B.bias[3], net.dec[3], dec + B.off_x4, B.ctot, 1, 1.f};
+        if ((r = conv_layer<T>(s, c4, &B.tcplan[3], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
+        if (B.headplan.enabled) {
+            ConvArgs a5{dec + B.off_x3, B.ctot, ne, B.h, B.w, net.dec[2] + net.dec[3], 1, B.h, B.w, B.head_w, B.head_b,
+                        2, nullptr, 2, 0};
+            TC_LAUNCH_CAT(s, TC_PROF_HEAD, launch_conv_tc_head(B.headplan, a5, l < s->L ? up : nullptr, flow, s->st));
+        } else {
+            HeadArgs ha{dec + B.off_x3, B.ctot, net.dec[2] + net.dec[3], ne, B.h, B.w, B.head_w, B.head_b,
+                        l < s->L ? up : nullptr, flow};
+            TC_LAUNCH_CAT(s, TC_PROF_HEAD, launch_head<T>(ha, s->st));
+        }
+    }
+    return TC_OK;
+}
+
+// The causal consistency pass of one lane (its own controls and state slots; a lane's
+// first frame returns P), then its current pyramid becomes its previous one.
+template <typename T>
+static tc_status lane_blend(tc_stream *s, int lane, const float *I, const float *P, float *O, float *wc,
+                            uint8_t *mask) {
+    const tc_consistency &pr = s->lane_params[lane];
+    const int cur = s->lane_cur[lane], prev = cur ^ 1;
+    const size_t off = (size_t)3 * s->H * s->W * lane;
+    ConsistArgs ca{};
+    ca.It = I; ca.Pt = P;
+    ca.H = s->H; ca.W = s->W;
+    ca.k1 = pr.k1; ca.alpha = pr.alpha; ca.lambda = pr.lambda;
+    ca.c1 = pr.fb_c1; ca.c2 = pr.fb_c2; ca.fb_check = pr.fb_check; ca.k2 = pr.k2;
+    ca.O = O; ca.wc = wc; ca.mask = mask;
+    ca.sI = s->sI[cur] + off; ca.sP = s->sP[cur] + off; ca.sO = s->sO[cur] + off;
+    if (s->lane_t[lane] == 0) {
+        ca.first = 1;
+        ca.fh = ca.fw = 1; ca.scale = 1;
+    } else {
+        const LevelBufs &B2 = s->lv[1];
+        const size_t fimg = (size_t)B2.h * B2.w * 2;
+        ca.Ip = s->sI[prev] + off; ca.Pp = s->sP[prev] + off; ca.Op = s->sO[prev] + off;
+        ca.Fb = B2.flow + (size_t)2 * lane * fimg;
+        ca.Ff = ca.Fb + fimg;
+        ca.fh = B2.h; ca.fw = B2.w; ca.scale = 4;
+    }
+    TC_LAUNCH_CAT(s, TC_PROF_CONSISTENCY, launch_consistency(ca, s->st));
+    for (int l = 1; l <= s->L; ++l) {
+        const LevelBufs &B = s->lv[l - 1];
+        const size_t bytes = (size_t)B.h * B.w * B.c * sizeof(T);
+        char *base = static_cast<char *>(B.pyr);
+        TC_TRY(s, cudaMemcpyAsync(base + (size_t)(s->lanes + lane) * bytes, base + (size_t)lane * bytes, bytes,
+                                  cudaMemcpyDeviceToDevice, s->st),
+               "pyramid copy");
+    }
+    return TC_OK;
+}
+
+template <typename T>
+static tc_status process_lanes(tc_stream *s, int n, const int *lanes, const float *const *I, const float *const *P,
+                               float *const *O, float *const *wc, uint8_t *const *mask) {
+    tc_status r;
+    s->launches = 0;
+    int lo = lanes[0], hi = lanes[0];
+    for (int k = 1; k < n; ++k) {
+        lo = std::min(lo, lanes[k]);
+        hi = std::max(hi, lanes[k]);
+    }
+    const int nr = hi - lo + 1;
+    for (int k = 0; k < n; ++k)
+        if ((r = lane_first<T>(s, lanes[k], I[k])) != TC_OK) return r;
+    // The shared launches: eager on a range's first use (which also sets every kernel's
+    // attributes), then captured once and replayed as one graph.
+    const int key = lo * 4096 + nr;
+    int &uses = s->range_uses[key];
+    if (s->graphs && !s->prof && uses >= 1) {
+        tc_stream::FrameGraph &G = s->range_graphs[key];
+        if (!G.exec) {
+            if (!s->gst) TC_TRY(s, cudaStreamCreateWithFlags(&s->gst, cudaStreamNonBlocking), "cudaStreamCreate");
+            const int before = s->launches;
+            r = capture_into<T>(s, s->gst, G, [&] { return lanes_network<T>(s, lo, nr); }, false, false);
+            if (r != TC_OK) return r;
+            s->launches = before;
+        }
+        TC_TRY(s, cudaGraphLaunch(G.exec, s->st), "cudaGraphLaunch");
+        s->launches += G.launches;
+    } else if ((r = lanes_network<T>(s, lo, nr)) != TC_OK) {
+        return r;
+    }
+    uses += 1;
+    for (int k = 0; k < n; ++k)
+        if ((r = lane_blend<T>(s, lanes[k], I[k], P[k], O[k], wc ? wc[k] : nullptr, mask ? mask[k] : nullptr)) != TC_OK)
+            return r;
+    for (int k = 0; k < n; ++k) {
+        s->lane_t[lanes[k]] += 1;
+        s->lane_cur[lanes[k]] ^= 1;
+    }
+    return TC_OK;
+}
+
+extern "C" tc_status tc_process_lanes(tc_stream *s, int n, const int *lanes, const float *const *I_t,
+                                      const float *const *P_t, float *const *O_t, float *const *wc_opt,
+                                      uint8_t *const *mask_opt) {
+    tc_status r = check_stream(s, "tc_process_lanes");
+    if (r != TC_OK) return r;
+    if (!s->batch) return fail(s, TC_ERR_STATE, "tc_process_lanes: not a batch (tc_create_batch)");
+    if (n < 1 || n > s->lanes || !lanes || !I_t || !P_t || !O_t)
+        return fail(s, TC_ERR_INVALID_ARG, "tc_process_lanes: n must lie in [1, lanes] with non-NULL arrays");
+    std::vector<char> seen(s->lanes, 0);
+    for (int k = 0; k < n; ++k) {
+        if (lanes[k] < 0 || lanes[k] >= s->lanes || seen[lanes[k]])
+            return fail(s, TC_ERR_INVALID_ARG, "tc_process_lanes: lanes must be distinct and in [0, lanes)");
+        seen[lanes[k]] = 1;
+        if (!I_t[k] || !P_t[k] || !O_t[k]) return fail(s, TC_ERR_INVALID_ARG, "tc_process_lanes: NULL image pointer");
+    }
+    if (s->prec == TC_FP32) return process_lanes<float>(s, n, lanes, I_t, P_t, O_t, wc_opt, mask_opt);
+    if (s->prec == TC_BF16) return process_lanes<__nv_bfloat16>(s, n, lanes, I_t, P_t, O_t, wc_opt, mask_opt);
+    return process_lanes<__half>(s, n, lanes, I_t, P_t, O_t, wc_opt, mask_opt);
+}
+
+extern "C" tc_status tc_set_lane_consistency(tc_stream *s, int lane, const tc_consistency *p) {
+    tc_status r = check_stream(s, "tc_set_lane_consistency");
+    if (r != TC_OK) return r;
+    if (!s->batch) return fail(s, TC_ERR_STATE, "tc_set_lane_consistency: not a batch (tc_create_batch)");
+    if (lane < 0 || lane >= s->lanes || !p) return fail(s, TC_ERR_INVALID_ARG, "tc_set_lane_consistency: bad lane");
+    if (p->solver_iters != 0) return fail(s, TC_ERR_UNSUPPORTED, "tc_set_lane_consistency: a batch runs without the solver");
+    std::string why;
+    if (!valid_params(p, why)) return fail(s, TC_ERR_INVALID_ARG, why);
+    s->lane_params[lane] = *p;
+    return TC_OK;
+}
+
+extern "C" tc_status tc_reset_lane(tc_stream *s, int lane) {
+    tc_status r = check_stream(s, "tc_reset_lane");
+    if (r != TC_OK) return r;
+    if (!s->batch) return fail(s, TC_ERR_STATE, "tc_reset_lane: not a batch (tc_create_batch)");
+    if (lane < 0 || lane >= s->lanes) return fail(s, TC_ERR_INVALID_ARG, "tc_reset_lane: bad lane");
+    s->lane_t[lane] = 0;
+    s->lane_cur[lane] = 0;
+    tc_default_consistency(&s->lane_params[lane]);
+    return TC_OK;
+}
+
+extern "C" tc_status tc_get_lane_flows(tc_stream *s, int lane, float *Fb, float *Ff) {
+    tc_status r = check_stream(s, "tc_get_lane_flows");
+    if (r != TC_OK) return r;
+    if (!s->batch) return fail(s, TC_ERR_STATE, "tc_get_lane_flows: not a batch (tc_create_batch)");
+    if (lane < 0 || lane >= s->lanes) return fail(s, TC_ERR_INVALID_ARG, "tc_get_lane_flows: bad lane");
+    if (s->lane_t[lane] < 2) return fail(s, TC_ERR_STATE, "tc_get_lane_flows: the lane has no flows yet");
+    const LevelBufs &B2 = s->lv[1];
+    const size_t fimg = (size_t)B2.h * B2.w * 2;
+    const float *fb = B2.flow + (size_t)2 * lane * fimg;
+    if (Fb) TC_LAUNCH(s, launch_flow_out(fb, B2.h, B2.w, 4, s->H, s->W, Fb, s->st));
+    if (Ff) TC_LAUNCH(s, launch_flow_out(fb + fimg, B2.h, B2.w, 4, s->H, s->W, Ff, s->st));
+    return TC_OK;
+}
+
 extern "C" tc_status tc_process_frame(tc_stream *s, const float *I_t, const float *P_t, float *O_t,
                                       float *wc_opt, uint8_t *mask_opt) {
-    tc_status r = check_stream(s, "tc_process_frame");
+    tc_status r = single_only(s, "tc_process_frame");
     if (r != TC_OK) return r;
     if (!I_t || !P_t || !O_t) return fail(s, TC_ERR_INVALID_ARG, "tc_process_frame: NULL image pointer");
     if (s->prec == TC_FP32) return process<float>(s, I_t, P_t, O_t, wc_opt, mask_opt);
@@ -1637,7 +1935,7 @@ extern "C" tc_status tc_synchronize(tc_stream *s) {
 
 extern "C" tc_status tc_process_frame_host_async(tc_stream *s, const float *I_t, const float *P_t, float *O_t,
                                                  float *wc_opt, uint8_t *mask_opt) {
-    tc_status r = check_stream(s, "tc_process_frame_host_async");
+    tc_status r = single_only(s, "tc_process_frame_host_async");
     if (r != TC_OK) return r;
     if (s->pipelined) return fail(s, TC_ERR_STATE, "tc_process_frame_host_async: not available in pipelined mode");
     if (!I_t || !P_t || !O_t) return fail(s, TC_ERR_INVALID_ARG, "tc_process_frame_host_async: NULL image pointer");
@@ -1685,7 +1983,7 @@ extern "C" tc_status tc_process_frame_host_async(tc_stream *s, const float *I_t,
 
 extern "C" tc_status tc_process_frame_host(tc_stream *s, const float *I_t, const float *P_t, float *O_t,
                                            float *wc_opt, uint8_t *mask_opt) {
-    tc_status r = check_stream(s, "tc_process_frame_host");
+    tc_status r = single_only(s, "tc_process_frame_host");
     if (r != TC_OK) return r;
     if (s->pipelined) return fail(s, TC_ERR_STATE, "tc_process_frame_host: not available in pipelined mode");
     if (!I_t || !P_t || !O_t) return fail(s, TC_ERR_INVALID_ARG, "tc_process_frame_host: NULL image pointer");
@@ -1728,7 +2026,7 @@ extern "C" tc_status tc_process_frame_host(tc_stream *s, const float *I_t, const
 }
 
 extern "C" tc_status tc_set_latency(tc_stream *s, int frames) {
-    tc_status r = check_stream(s, "tc_set_latency");
+    tc_status r = single_only(s, "tc_set_latency");
     if (r != TC_OK) return r;
     if (frames != 0 && frames != 1) return fail(s, TC_ERR_INVALID_ARG, "tc_set_latency: frames must be 0 or 1");
     if (s->t != 0) return fail(s, TC_ERR_STATE, "tc_set_latency: only before the first frame of a sequence");
@@ -1748,7 +2046,7 @@ extern "C" tc_status tc_set_latency(tc_stream *s, int frames) {
 }
 
 extern "C" tc_status tc_set_pipelined(tc_stream *s, int enable) {
-    tc_status r = check_stream(s, "tc_set_pipelined");
+    tc_status r = single_only(s, "tc_set_pipelined");
     if (r != TC_OK) return r;
     if (s->t != 0) return fail(s, TC_ERR_STATE, "tc_set_pipelined: only before the first frame of a sequence");
     if (enable && s->rec_amax) return fail(s, TC_ERR_STATE, "tc_set_pipelined: not while recording amax");
@@ -1767,7 +2065,7 @@ extern "C" tc_status tc_join(tc_stream *s) {
 }
 
 extern "C" tc_status tc_flush(tc_stream *s, float *O_t, float *wc_opt, uint8_t *mask_opt) {
-    tc_status r = check_stream(s, "tc_flush");
+    tc_status r = single_only(s, "tc_flush");
     if (r != TC_OK) return r;
     if (!s->latency) return fail(s, TC_ERR_STATE, "tc_flush: the stream has no frame of latency");
     if (s->t == 0) return fail(s, TC_ERR_STATE, "tc_flush: no frame pending");
@@ -1798,7 +2096,7 @@ extern "C" tc_status tc_flush(tc_stream *s, float *O_t, float *wc_opt, uint8_t *
 extern "C" long long tc_last_output_frame(const tc_stream *s) { return s ? s->last_out : -1; }
 
 extern "C" tc_status tc_get_flows(tc_stream *s, float *Fb, float *Ff) {
-    tc_status r = check_stream(s, "tc_get_flows");
+    tc_status r = single_only(s, "tc_get_flows");
     if (r != TC_OK) return r;
     if (s->t < 2) return fail(s, TC_ERR_STATE, "tc_get_flows: no flow before the second frame");
     if ((r = join_caller(s)) != TC_OK) return r;

@@ -38,8 +38,9 @@ struct HostNet {
 bool parse_weights(const uint8_t *p, size_t n, HostNet &net, std::string &err);
 
 // Device memory a stream of width x height holds (feature pyramids, estimator buffers,
-// flows, state, weights, host-entry staging), from the same sizes the stream allocates.
-size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precision prec, int fs = 1);
+// flows, state, weights, host-entry staging), from the same sizes the stream allocates;
+// lanes > 0: a batch of that many lanes (tc_create_batch; no host-entry staging).
+size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precision prec, int fs = 1, int lanes = 0);
 
 }  // namespace tc
 

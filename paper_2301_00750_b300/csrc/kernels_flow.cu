@@ -271,10 +271,14 @@ __global__ void __launch_bounds__(256) corr_kernel(CorrArgs a) {
     const bool valid = x < a.w && y < a.h;
     // (selects, not a.fs[b]: a runtime index into the parameter array would copy the
     // arguments to local memory)
-    const T *fs = a.fs_img ? static_cast<const T *>(a.fs[0]) + b * a.fs_img
-                           : static_cast<const T *>(b ? a.fs[1] : a.fs[0]);
-    const T *fo = a.fo_img ? static_cast<const T *>(a.fo[0]) + b * a.fo_img
-                           : static_cast<const T *>(b ? a.fo[1] : a.fo[0]);
+    const int lq = b >> 1, ld = b & 1;  // lane pairs: lane and direction of entry b
+    const T *fs = a.pair_lanes ? static_cast<const T *>(a.fs[0]) + (size_t)(lq + ld * a.pair_lanes) * a.fs_img
+                  : a.fs_img   ? static_cast<const T *>(a.fs[0]) + b * a.fs_img
+                               : static_cast<const T *>(b ? a.fs[1] : a.fs[0]);
+    const T *fo = a.pair_lanes && a.pair_other
+                      ? static_cast<const T *>(a.fo[0]) + (size_t)(lq + (1 - ld) * a.pair_lanes) * a.fo_img
+                  : a.fo_img ? static_cast<const T *>(a.fo[0]) + b * a.fo_img
+                             : static_cast<const T *>(b ? a.fo[1] : a.fo[0]);
     float acc[ND];
 #pragma unroll
     for (int k = 0; k < ND; ++k) acc[k] = 0.f;
@@ -383,8 +387,9 @@ __global__ void __launch_bounds__(256) warp_kernel(WarpArgs a, int ng, uint32_t 
     const float fu = floorf(u), fv = floorf(v);
     const float ax = u - fu, ay = v - fv;
     const int xa = x + (int)fu, ya = y + (int)fv;
-    const T *f = a.f_img ? static_cast<const T *>(a.f[0]) + b * a.f_img
-                         : static_cast<const T *>(b ? a.f[1] : a.f[0]);  // no runtime index into the arguments
+    const T *f = a.pair_lanes ? static_cast<const T *>(a.f[0]) + (size_t)((b >> 1) + (1 - (b & 1)) * a.pair_lanes) * a.f_img
+                 : a.f_img    ? static_cast<const T *>(a.f[0]) + b * a.f_img
+                              : static_cast<const T *>(b ? a.f[1] : a.f[0]);  // no runtime index into the arguments
     float4 acc[Q];
 #pragma unroll
     for (int j = 0; j < Q; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
