@@ -769,18 +769,66 @@ def run_reference(args):
 SERVE_MIX = [(640, 360, 4), (1280, 720, 4), (1920, 1080, 6), (2560, 1440, 2)]
 
 
+def serve_load(srv, streams, frames_by_size, rate, seconds, seed, warm=1.0):
+    """Poisson frame arrivals at `rate` frames/s per stream for warm + seconds; returns served
+    frames/s over the measured window, latency percentiles, batch sizes and drops."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    latencies, batches, done_n, dropped = [], [], 0, 0
+    tag_slot = {}
+    for s_ in streams:
+        s_["free"] = list(range(len(s_["outs"])))
+        s_["next"] = g.exponential(1.0 / rate)
+    t0 = time.perf_counter()
+    n_tag = 0
+    while True:
+        now = time.perf_counter() - t0
+        if now > seconds + warm:
+            break
+        for s_ in streams:
+            while s_["next"] <= now:
+                if not s_["free"]:
+                    dropped += s_["next"] >= warm  # client found no free output slot: frame skipped
+                else:
+                    slot = s_["free"].pop()
+                    fr, st = frames_by_size[(s_["W"], s_["H"])]
+                    k = s_["n"] % len(fr)
+                    n_tag += 1
+                    tag_slot[n_tag] = (s_, slot, s_["next"])
+                    srv.submit(s_["id"], fr[k], st[k], s_["outs"][slot], tag=n_tag)
+                    s_["n"] += 1
+                s_["next"] += g.exponential(1.0 / rate)
+        for c in srv.poll(timeout_ms=1):
+            s_, slot, t_sub = tag_slot.pop(c["tag"])
+            s_["free"].append(slot)
+            if c["status"] == 0 and t_sub >= warm:
+                latencies.append(c["total_us"] / 1e3)
+                batches.append(c["batch"])
+                done_n += 1
+    end = time.perf_counter() - t0
+    while tag_slot:  # drain what is in flight before the next load
+        for c in srv.poll(max_n=4096, timeout_ms=200):
+            s_, slot, _ = tag_slot.pop(c["tag"])
+            s_["free"].append(slot)
+    lat = sorted(latencies)
+    pct = lambda q: round(lat[min(len(lat) - 1, int(q * len(lat)))], 3) if lat else None
+    return {"offered_frames_per_s": round(rate * len(streams), 1), "served_frames_per_s": round(done_n / (end - warm), 2),
+            "p50_ms": pct(0.5), "p99_ms": pct(0.99), "mean_batch": round(float(np.mean(batches)), 2) if batches else None,
+            "max_batch": int(max(batches)) if batches else None, "dropped_no_slot": int(dropped)}
+
+
 def run_serve(args):
     """16 concurrent streams at mixed resolutions through tc_server_*: Poisson frame arrivals
-    at 30 fps per stream, host buffers in and out, HBM-budget admission, continuous batching;
-    reports aggregate frames/s and p50/p99 submit-to-done latency."""
+    per stream, host buffers in and out, HBM-budget admission, streams of one size sharing a
+    batch (their ready frames run as one step of shared launches, CUDA graphs per lane
+    range).  The line reports the load of 30 frames/s per stream and a curve of higher loads
+    up to saturation (served frames/s, p50/p99 submit-to-done latency, mean frames per step)."""
     import torch
     import paper_2301_00750_b300 as tc
 
     tmp = tempfile.mkdtemp(prefix="tcserve")
     path = os.path.join(tmp, "net.tcw")
     write_weights(path)
-    g = np.random.Generator(np.random.PCG64(7))
-    srv = tc.Server(path, precision=args.precision, workers=args.workers,
+    srv = tc.Server(path, precision=args.precision, workers=args.workers, batch_lanes=args.batch_lanes,
                     hbm_budget_bytes=int(args.budget_gb * (1 << 30)) if args.budget_gb else 0)
     streams = []
     frames_by_size = {}
@@ -793,53 +841,26 @@ def run_serve(args):
             sid = srv.open(W, H)
             srv.set_consistency(sid, k1=0.5)
             outs = [torch.empty((3, H, W), dtype=torch.float32).pin_memory() for _ in range(args.ring)]
-            streams.append(dict(id=sid, W=W, H=H, outs=outs, free=list(range(args.ring)), next=0.0, n=0))
-    rate = 30.0
-    duration = args.seconds
-    latencies, done_n, dropped = [], 0, 0
-    tag_slot = {}
-    t0 = time.perf_counter()
-    for s_ in streams:
-        s_["next"] = g.exponential(1.0 / rate)
-    warm = 1.0  # seconds excluded from the statistics
-    while True:
-        now = time.perf_counter() - t0
-        if now > duration + warm:
-            break
-        for s_ in streams:
-            while s_["next"] <= now:
-                if not s_["free"]:
-                    dropped += 1  # client found no free output slot: frame skipped
-                else:
-                    slot = s_["free"].pop()
-                    fr, st = frames_by_size[(s_["W"], s_["H"])]
-                    k = s_["n"] % len(fr)
-                    tag = (s_["id"] << 32) | s_["n"]
-                    tag_slot[tag] = (s_, slot, s_["next"])
-                    srv.submit(s_["id"], fr[k], st[k], s_["outs"][slot], tag=tag)
-                    s_["n"] += 1
-                s_["next"] += g.exponential(1.0 / rate)
-        for c in srv.poll(timeout_ms=1):
-            s_, slot, t_sub = tag_slot.pop(c["tag"])
-            s_["free"].append(slot)
-            if c["status"] == 0 and t_sub >= warm:
-                latencies.append(c["total_us"] / 1e3)
-                done_n += 1
-    end = time.perf_counter() - t0
-    for c in srv.poll(max_n=4096, timeout_ms=2000):
-        pass
+            streams.append(dict(id=sid, W=W, H=H, outs=outs, n=0))
+    base = serve_load(srv, streams, frames_by_size, 30.0, args.seconds, 7)
+    curve = [base]
+    if not args.skip_curve:
+        for k, rate in enumerate((60.0, 120.0, 240.0, 1000.0)):
+            curve.append(serve_load(srv, streams, frames_by_size, rate, max(3.0, args.seconds / 2), 8 + k))
     srv.destroy()
-    lat = sorted(latencies)
     px = sum(W * H * c for W, H, c in SERVE_MIX)
+    cap = max(c["served_frames_per_s"] for c in curve)
     print(json.dumps({
         "metric": "serving: aggregate frames/s and p50/p99 frame latency, 16 mixed-resolution streams, Poisson 30 fps",
-        "value": round(done_n / (end - warm), 2), "unit": "frames/s", "higher_is_better": True,
-        "p50_ms": round(lat[len(lat) // 2], 3) if lat else None,
-        "p99_ms": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3) if lat else None,
-        "offered_frames_per_s": rate * len(streams), "dropped_no_slot": dropped,
-        "dtype": args.precision, "data": "synthetic", "workers": args.workers,
-        "config": {"workload": "4x640x360, 4x1280x720, 6x1920x1080, 2x2560x1440; host buffers in/out per frame",
-                   "megapixels_per_round": round(px / 1e6, 2), "seconds": duration},
+        "value": base["served_frames_per_s"], "unit": "frames/s", "higher_is_better": True,
+        "p50_ms": base["p50_ms"], "p99_ms": base["p99_ms"], "mean_batch": base["mean_batch"],
+        "offered_frames_per_s": base["offered_frames_per_s"], "dropped_no_slot": base["dropped_no_slot"],
+        "capacity_frames_per_s": cap, "load_curve": curve,
+        "dtype": {"fp16": "f16", "fp32": "f32"}.get(args.precision, args.precision), "data": "synthetic",
+        "workers": args.workers, "batch_lanes": args.batch_lanes,
+        "config": {"workload": "4x640x360, 4x1280x720, 6x1920x1080, 2x2560x1440; host buffers in/out per frame; "
+                               f"{args.ring} output buffers per stream (a frame arriving with none free is skipped)",
+                   "megapixels_per_round": round(px / 1e6, 2), "seconds": args.seconds},
     }), flush=True)
 
 
@@ -980,6 +1001,8 @@ def main():
     ap.add_argument("--ring", type=int, default=4, help="output buffers per stream (frames in flight)")
     ap.add_argument("--seconds", type=float, default=10.0)
     ap.add_argument("--budget-gb", type=float, default=0.0)
+    ap.add_argument("--batch-lanes", type=int, default=4, help="serving: streams of one size per shared batch")
+    ap.add_argument("--skip-curve", action="store_true", help="serving: only the 30 frames/s per stream load")
     ap.add_argument("--train", action="store_true", help="run the training-throughput benchmark instead")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -426,11 +426,15 @@ TC_API size_t tc_stream_device_bytes(const tc_stream *s);
 /* ------------------------------------------------------------------------------------
  * Multi-stream server.  Many concurrent streams (each with its own state on the device, as
  * Sec. 3.1 requires: I_{t-1}, P_{t-1}, O_{t-1} and the cached pyramid) of mixed
- * resolutions share one GPU.  Admission reserves a stream's device memory against an HBM
- * budget; frames are submitted with host buffers and run, in order per stream, by a pool of
- * worker threads as soon as a worker is free and the stream's previous frame has finished
- * (continuous batching: work of different streams overlaps on the device, each frame on its
- * stream's own CUDA stream as one CUDA-graph replay).
+ * resolutions share one GPU.  Streams of one resolution are lanes of a shared batch
+ * (tc_create_batch) of batch_lanes lanes; admission reserves a batch's device memory
+ * against an HBM budget when a stream finds no free lane of its size.  Frames are
+ * submitted with host buffers and run, in order per stream, by a pool of worker threads:
+ * a free worker takes the batch with the oldest queued frame and runs the next frame of
+ * every lane of it that has one as one batched step (their pyramids and flow estimations
+ * in shared launches, replayed as CUDA graphs); frames that arrive meanwhile join the next
+ * step (continuous batching), and different batches run at the same time on their own CUDA
+ * streams.  A stream's results are the same whichever other streams share its steps.
  * ---------------------------------------------------------------------------------- */
 typedef struct tc_server tc_server;
 
@@ -440,8 +444,9 @@ typedef struct {
     const void *weights_blob;
     size_t weights_bytes;
     size_t hbm_budget_bytes;         /* device bytes the streams may hold together; 0 = unlimited */
-    int workers;                     /* frames in flight at once, 1..64 */
+    int workers;                     /* batched steps in flight at once, 1..64 */
     int max_streams;                 /* stream slots, >= 1 */
+    int batch_lanes;                 /* streams per shared batch, 0..64 (0 or 1: a batch per stream) */
 } tc_server_desc;
 
 typedef struct {
@@ -450,12 +455,14 @@ typedef struct {
     unsigned long long tag;          /* as passed to tc_server_submit */
     tc_status status;                /* TC_OK, TC_ERR_STATE if cancelled, or the frame's error */
     double queued_us, gpu_us, total_us;  /* submit -> start, start -> done, submit -> done */
+    int batch;                       /* frames run by the step that ran this one */
 } tc_completion;
 
 /* Creates a server and its worker threads on the current device. */
 TC_API tc_status tc_server_create(const tc_server_desc *desc, tc_server **out);
 
-/* Device bytes a stream of width x height would hold (the admission charge). */
+/* Device bytes a batch of width x height (batch_lanes lanes and its staging) holds: the
+ * admission charge of a stream that finds no free lane of its size. */
 TC_API size_t tc_server_stream_bytes(const tc_server *srv, int width, int height);
 
 /* Device bytes currently reserved by admitted streams. */

@@ -554,13 +554,13 @@ def op_consistency(It, Pt, Ip, Pp, Op, Fb, Ff, scale=1, O=None, wc=None, mask=No
 class TcServerDesc(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("weights_path", ctypes.c_char_p), ("weights_blob", ctypes.c_void_p),
                 ("weights_bytes", ctypes.c_size_t), ("hbm_budget_bytes", ctypes.c_size_t), ("workers", ctypes.c_int),
-                ("max_streams", ctypes.c_int)]
+                ("max_streams", ctypes.c_int), ("batch_lanes", ctypes.c_int)]
 
 
 class TcCompletion(ctypes.Structure):
     _fields_ = [("stream_id", ctypes.c_int), ("frame", ctypes.c_longlong), ("tag", ctypes.c_ulonglong),
                 ("status", ctypes.c_int), ("queued_us", ctypes.c_double), ("gpu_us", ctypes.c_double),
-                ("total_us", ctypes.c_double)]
+                ("total_us", ctypes.c_double), ("batch", ctypes.c_int)]
 
 
 _lib.tc_server_create.argtypes = [ctypes.POINTER(TcServerDesc), ctypes.POINTER(_vp)]
@@ -599,13 +599,16 @@ class Server:
     and continuous batching.  Host buffers passed to submit() must stay alive until their
     completion is polled."""
 
-    def __init__(self, weights_path, precision="bf16", hbm_budget_bytes=0, workers=4, max_streams=64):
+    def __init__(self, weights_path, precision="bf16", hbm_budget_bytes=0, workers=4, max_streams=64, batch_lanes=1):
+        """batch_lanes: streams of one resolution per shared batch (their frames run in
+        shared launches when ready together); 1: a batch per stream."""
         d = TcServerDesc()
         d.precision = PRECISION[precision]
         d.weights_path = os.fsencode(weights_path)
         d.hbm_budget_bytes = int(hbm_budget_bytes)
         d.workers = int(workers)
         d.max_streams = int(max_streams)
+        d.batch_lanes = int(batch_lanes)
         h = _vp()
         _check(_lib.tc_server_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h
@@ -638,7 +641,7 @@ class Server:
         for c in buf[:n]:
             self._keep.pop((c.stream_id, c.tag), None)
             out.append(dict(stream_id=c.stream_id, frame=c.frame, tag=c.tag, status=c.status, queued_us=c.queued_us,
-                            gpu_us=c.gpu_us, total_us=c.total_us))
+                            gpu_us=c.gpu_us, total_us=c.total_us, batch=c.batch))
         return out
 
     def cancel(self, stream_id):

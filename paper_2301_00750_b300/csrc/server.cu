@@ -1,17 +1,22 @@
 // Multi-stream server: many concurrent video streams (Sec. 3.1: one state per stream, O(1)
 // in the stream length) of mixed resolutions on one GPU.
 //
-//   * Admission: tc_server_open reserves a stream slot and the device memory the stream will
-//     hold (computed from the same buffer sizes the stream allocates); it answers
-//     TC_ERR_BUSY when the slots or the HBM budget are used up, and succeeds again once a
-//     stream has been closed.
+//   * Groups: streams of the same resolution share a batch (tc_create_batch) of
+//     desc.batch_lanes lanes, one lane per stream; a group is created (device memory
+//     reserved against the HBM budget) when a stream finds no free lane of its size, and
+//     destroyed when its last stream closes.  tc_server_open answers TC_ERR_BUSY when the
+//     slots or the budget are used up, and succeeds again once streams have closed.
 //   * Continuous batching: a pool of worker threads takes, whenever a worker is free, the
-//     oldest submitted frame of any stream whose previous frame has finished, and runs it
-//     through tc_process_frame_host on that stream's own CUDA stream (one CUDA-graph replay
-//     per frame from its third frame on).  Frames that arrive while others are on the GPU
-//     start as soon as a worker frees up, and the work of different streams overlaps on the
-//     device; a stream's own frames stay in order.
-//   * Completions carry the time spent queued, on the GPU and in total (submit to done).
+//     group holding the oldest submitted frame among idle groups, and runs the oldest queued
+//     frame of every lane of that group that has one as one batched step: uploads to the
+//     group's device staging, tc_process_lanes (the pyramids and flow estimations of those
+//     lanes in shared launches, one CUDA graph per lane range), downloads.  Lanes far apart
+//     run as separate runs of the step so that idle lanes between them are not computed.
+//     Frames that arrive while a group is on the GPU join its next step; different groups
+//     run at the same time on their own CUDA streams; a stream's frames stay in order.
+//   * Completions carry the time spent queued, on the GPU and in total (submit to done), and
+//     how many frames their step ran.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -38,16 +43,33 @@ struct Request {
     double t_submit;
 };
 
+struct Group;
+
 struct Slot {
     int id = 0, W = 0, H = 0;
-    size_t bytes = 0;
-    tc_stream *s = nullptr;      // NULL while the stream is being created
-    cudaStream_t cs = nullptr;
+    Group *g = nullptr;
+    int lane = -1;
     std::deque<Request> q;
     bool busy = false, closing = false;
     long long next_frame = 0;
     tc_consistency params{};
-    bool params_dirty = false;
+    bool params_dirty = true;  // applied by the worker before the lane's next frame
+    bool reset = true;         // the lane starts a new stream at its next frame
+};
+
+struct Group {
+    int W = 0, H = 0, lanes = 0;
+    size_t bytes = 0;
+    tc_stream *b = nullptr;  // NULL while being created
+    cudaStream_t cs = nullptr;
+    float *stage = nullptr;  // device staging [3][lanes][3][H][W]: I, P, O
+    std::vector<Slot *> lane_slot;  // NULL = free lane
+    bool busy = false;
+    int open_slots() const {
+        int n = 0;
+        for (Slot *s : lane_slot) n += s != nullptr;
+        return n;
+    }
 };
 
 }  // namespace
@@ -57,9 +79,11 @@ struct tc_server {
     std::vector<uint8_t> blob;
     tc::HostNet net;
     int device = 0;
+    int lanes = 1;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::map<int, Slot *> slots;
+    std::vector<Group *> groups;
     int next_id = 1;
     size_t bytes_used = 0;
     std::deque<tc_completion> done;
@@ -69,13 +93,22 @@ struct tc_server {
 
     double now_us() const { return std::chrono::duration<double, std::micro>(Clock::now() - t0).count(); }
 
-    // Oldest pending frame among the streams that are idle (FIFO across streams).
-    Slot *pick_ready() {
-        Slot *best = nullptr;
-        for (auto &kv : slots) {
-            Slot *sl = kv.second;
-            if (!sl->s || sl->busy || sl->q.empty()) continue;
-            if (!best || sl->q.front().t_submit < best->q.front().t_submit) best = sl;
+    size_t group_bytes(int W, int H) const {
+        const size_t img = (size_t)3 * W * H * sizeof(float);
+        return tc::stream_device_bytes(net, W, H, desc.precision, 1, lanes) + ((3 * lanes * img + 511) & ~(size_t)511);
+    }
+
+    // The idle group holding the oldest queued frame (FIFO across groups).
+    Group *pick_ready() {
+        Group *best = nullptr;
+        double best_t = 0;
+        for (Group *g : groups) {
+            if (!g->b || g->busy) continue;
+            for (Slot *s : g->lane_slot)
+                if (s && !s->q.empty() && (!best || s->q.front().t_submit < best_t)) {
+                    best = g;
+                    best_t = s->q.front().t_submit;
+                }
         }
         return best;
     }
@@ -84,50 +117,120 @@ struct tc_server {
         cudaSetDevice(device);
         std::unique_lock<std::mutex> lk(mu);
         for (;;) {
-            Slot *sl = nullptr;
-            cv_work.wait(lk, [&] { return stop || (sl = pick_ready()) != nullptr; });
-            if (!sl) break;  // stopping and nothing runnable
-            Request rq = sl->q.front();
-            sl->q.pop_front();
-            sl->busy = true;
-            const bool dirty = sl->params_dirty;
-            const tc_consistency prm = sl->params;
-            sl->params_dirty = false;
+            Group *g = nullptr;
+            cv_work.wait(lk, [&] { return stop || (g = pick_ready()) != nullptr; });
+            if (!g) break;  // stopping and nothing runnable
+            struct Item {
+                Slot *s;
+                Request rq;
+                bool reset, dirty;
+                tc_consistency prm;
+            };
+            std::vector<Item> items;
+            for (int l = 0; l < g->lanes; ++l) {
+                Slot *s = g->lane_slot[l];
+                if (!s || s->q.empty()) continue;
+                items.push_back(Item{s, s->q.front(), s->reset, s->params_dirty, s->params});
+                s->q.pop_front();
+                s->busy = true;
+                s->reset = false;
+                s->params_dirty = false;
+            }
+            g->busy = true;
             lk.unlock();
             const double t_start = now_us();
-            tc_status st = TC_OK;
-            if (dirty) st = tc_set_consistency(sl->s, &prm);
-            if (st == TC_OK) st = tc_process_frame_host(sl->s, rq.I, rq.P, rq.O, nullptr, nullptr);
+            const tc_status st = run_step(g, items);
             const double t_end = now_us();
             lk.lock();
-            sl->busy = false;
-            tc_completion c{};
-            c.stream_id = sl->id;
-            c.frame = rq.frame;
-            c.tag = rq.tag;
-            c.status = st;
-            c.queued_us = t_start - rq.t_submit;
-            c.gpu_us = t_end - t_start;
-            c.total_us = t_end - rq.t_submit;
-            done.push_back(c);
+            g->busy = false;
+            for (const Item &it : items) {
+                it.s->busy = false;
+                tc_completion c{};
+                c.stream_id = it.s->id;
+                c.frame = it.rq.frame;
+                c.tag = it.rq.tag;
+                c.status = st;
+                c.queued_us = t_start - it.rq.t_submit;
+                c.gpu_us = t_end - t_start;
+                c.total_us = t_end - it.rq.t_submit;
+                c.batch = (int)items.size();
+                done.push_back(c);
+            }
             cv_done.notify_all();
             cv_work.notify_all();
         }
     }
+
+    // One batched step of a group (no lock held): every item's lane gets its frame.
+    template <typename Item>
+    tc_status run_step(Group *g, const std::vector<Item> &items) {
+        const size_t img = (size_t)3 * g->W * g->H;
+        float *dI = g->stage, *dP = g->stage + g->lanes * img, *dO = g->stage + 2 * g->lanes * img;
+        tc_status st = TC_OK;
+        for (const Item &it : items) {
+            const int l = it.s->lane;
+            if (st == TC_OK && it.reset) st = tc_reset_lane(g->b, l);
+            if (st == TC_OK && it.dirty) st = tc_set_lane_consistency(g->b, l, &it.prm);
+            if (st == TC_OK && (cudaMemcpyAsync(dI + l * img, it.rq.I, img * sizeof(float), cudaMemcpyHostToDevice,
+                                                g->cs) != cudaSuccess ||
+                                cudaMemcpyAsync(dP + l * img, it.rq.P, img * sizeof(float), cudaMemcpyHostToDevice,
+                                                g->cs) != cudaSuccess)) {
+                cudaGetLastError();
+                st = tc_record_error(TC_ERR_CUDA, "server: upload failed");
+            }
+        }
+        // Lanes in ascending order, split into runs that skip more than one idle lane: each
+        // run is one tc_process_lanes call, whose shared launches cover lanes lo .. hi.
+        std::vector<int> ls;
+        for (const Item &it : items) ls.push_back(it.s->lane);
+        std::sort(ls.begin(), ls.end());
+        size_t k0 = 0;
+        while (st == TC_OK && k0 < ls.size()) {
+            size_t k1 = k0 + 1;
+            while (k1 < ls.size() && ls[k1] - ls[k1 - 1] <= 2) ++k1;
+            std::vector<const float *> I, P;
+            std::vector<float *> O;
+            for (size_t k = k0; k < k1; ++k) {
+                I.push_back(dI + ls[k] * img);
+                P.push_back(dP + ls[k] * img);
+                O.push_back(dO + ls[k] * img);
+            }
+            st = tc_process_lanes(g->b, (int)(k1 - k0), ls.data() + k0, I.data(), P.data(), O.data(), nullptr, nullptr);
+            k0 = k1;
+        }
+        for (const Item &it : items)
+            if (st == TC_OK && cudaMemcpyAsync(it.rq.O, dO + it.s->lane * img, img * sizeof(float),
+                                               cudaMemcpyDeviceToHost, g->cs) != cudaSuccess) {
+                cudaGetLastError();
+                st = tc_record_error(TC_ERR_CUDA, "server: download failed");
+            }
+        const tc_status ss = tc_synchronize(g->b);
+        return st != TC_OK ? st : ss;
+    }
 };
 
 static tc_status srv_fail(tc_status code, const std::string &msg) { return tc_record_error(code, msg); }
+
+static void destroy_group(Group *g) {
+    if (g->b) tc_destroy(g->b);
+    if (g->stage) cudaFree(g->stage);
+    if (g->cs) cudaStreamDestroy(g->cs);
+    delete g;
+}
 
 extern "C" tc_status tc_server_create(const tc_server_desc *desc, tc_server **out) {
     if (out) *out = nullptr;
     if (!desc || !out) return srv_fail(TC_ERR_INVALID_ARG, "tc_server_create: NULL argument");
     if (desc->precision != TC_FP32 && desc->precision != TC_BF16 && desc->precision != TC_FP16)
         return srv_fail(TC_ERR_INVALID_ARG, "tc_server_create: precision must be TC_FP32, TC_BF16 or TC_FP16");
-    if (desc->workers < 1 || desc->workers > 64 || desc->max_streams < 1)
-        return srv_fail(TC_ERR_INVALID_ARG, "tc_server_create: workers must lie in [1, 64], max_streams >= 1");
+    if (desc->workers < 1 || desc->workers > 64 || desc->max_streams < 1 || desc->batch_lanes < 0 ||
+        desc->batch_lanes > 64)
+        return srv_fail(TC_ERR_INVALID_ARG,
+                        "tc_server_create: workers must lie in [1, 64], max_streams >= 1, batch_lanes in [0, 64]");
     tc_server *srv = new (std::nothrow) tc_server();
     if (!srv) return srv_fail(TC_ERR_OOM, "tc_server_create: host allocation failed");
     srv->desc = *desc;
+    srv->lanes = desc->batch_lanes > 1 ? desc->batch_lanes : 1;
     if (desc->weights_path) {
         FILE *f = fopen(desc->weights_path, "rb");
         if (!f) {
@@ -156,6 +259,10 @@ extern "C" tc_status tc_server_create(const tc_server_desc *desc, tc_server **ou
         delete srv;
         return srv_fail(TC_ERR_IO, err);
     }
+    if (!srv->net.ref.empty()) {
+        delete srv;
+        return srv_fail(TC_ERR_UNSUPPORTED, "tc_server_create: served streams run without the refinement network");
+    }
     srv->desc.weights_path = nullptr;
     srv->desc.weights_blob = nullptr;
     if (cudaGetDevice(&srv->device) != cudaSuccess) {
@@ -169,7 +276,7 @@ extern "C" tc_status tc_server_create(const tc_server_desc *desc, tc_server **ou
 
 extern "C" size_t tc_server_stream_bytes(const tc_server *srv, int width, int height) {
     if (!srv || width < 1 || height < 1) return 0;
-    return tc::stream_device_bytes(srv->net, width, height, srv->desc.precision);
+    return srv->group_bytes(width, height);
 }
 
 extern "C" tc_status tc_server_open(tc_server *srv, int width, int height, int *stream_id) {
@@ -178,51 +285,87 @@ extern "C" tc_status tc_server_open(tc_server *srv, int width, int height, int *
     const int m = 1 << srv->net.levels;
     if (width < m || height < m || width > 16384 || height > 16384)
         return srv_fail(TC_ERR_INVALID_ARG, "tc_server_open: width and height must lie in [2^levels, 16384]");
-    const size_t need = tc::stream_device_bytes(srv->net, width, height, srv->desc.precision);
     Slot *sl = nullptr;
+    Group *fresh = nullptr;
     {
         std::lock_guard<std::mutex> lk(srv->mu);
         if ((int)srv->slots.size() >= srv->desc.max_streams)
             return srv_fail(TC_ERR_BUSY, "tc_server_open: all stream slots are in use");
-        if (srv->desc.hbm_budget_bytes && srv->bytes_used + need > srv->desc.hbm_budget_bytes)
-            return srv_fail(TC_ERR_BUSY, "tc_server_open: the stream would exceed the HBM budget (" +
-                                             std::to_string(srv->bytes_used + need) + " > " +
-                                             std::to_string(srv->desc.hbm_budget_bytes) + " bytes)");
+        Group *g = nullptr;
+        int lane = -1;
+        for (Group *c : srv->groups) {
+            if (c->W != width || c->H != height || !c->b) continue;  // (a group being created is skipped)
+            for (int l = 0; l < c->lanes && lane < 0; ++l)
+                if (!c->lane_slot[l]) lane = l;
+            if (lane >= 0) {
+                g = c;
+                break;
+            }
+        }
+        if (!g) {
+            const size_t need = srv->group_bytes(width, height);
+            if (srv->desc.hbm_budget_bytes && srv->bytes_used + need > srv->desc.hbm_budget_bytes)
+                return srv_fail(TC_ERR_BUSY, "tc_server_open: the stream would exceed the HBM budget (" +
+                                                 std::to_string(srv->bytes_used + need) + " > " +
+                                                 std::to_string(srv->desc.hbm_budget_bytes) + " bytes)");
+            g = fresh = new Group();
+            g->W = width;
+            g->H = height;
+            g->lanes = srv->lanes;
+            g->bytes = need;
+            g->lane_slot.assign(g->lanes, nullptr);
+            srv->groups.push_back(g);
+            srv->bytes_used += need;
+            lane = 0;
+        }
         sl = new Slot();
         sl->id = srv->next_id++;
         sl->W = width;
         sl->H = height;
-        sl->bytes = need;
+        sl->g = g;
+        sl->lane = lane;
         tc_default_consistency(&sl->params);
+        g->lane_slot[lane] = sl;
         srv->slots[sl->id] = sl;
-        srv->bytes_used += need;
     }
-    // Create the stream outside the lock (allocation and weight upload take time).
-    tc_status st = TC_OK;
-    cudaSetDevice(srv->device);
-    if (cudaStreamCreateWithFlags(&sl->cs, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        st = srv_fail(TC_ERR_CUDA, "tc_server_open: cudaStreamCreate failed");
-    }
-    tc_stream *s = nullptr;
-    if (st == TC_OK) {
-        tc_stream_desc d{};
-        d.width = width;
-        d.height = height;
-        d.precision = srv->desc.precision;
-        d.weights_blob = srv->blob.data();
-        d.weights_bytes = srv->blob.size();
-        st = tc_create_stream(&d, sl->cs, &s);
+    if (fresh) {
+        // Create the batch outside the lock (allocation and weight upload take time); until
+        // then the group is not picked (b == NULL).
+        tc_status st = TC_OK;
+        cudaSetDevice(srv->device);
+        if (cudaStreamCreateWithFlags(&fresh->cs, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            st = srv_fail(TC_ERR_CUDA, "tc_server_open: cudaStreamCreate failed");
+        }
+        const size_t img = (size_t)3 * width * height * sizeof(float);
+        if (st == TC_OK && cudaMalloc(&fresh->stage, 3 * fresh->lanes * img) != cudaSuccess) {
+            cudaGetLastError();
+            fresh->stage = nullptr;
+            st = srv_fail(TC_ERR_OOM, "tc_server_open: staging allocation failed");
+        }
+        tc_stream *b = nullptr;
+        if (st == TC_OK) {
+            tc_stream_desc d{};
+            d.width = width;
+            d.height = height;
+            d.precision = srv->desc.precision;
+            d.weights_blob = srv->blob.data();
+            d.weights_bytes = srv->blob.size();
+            st = tc_create_batch(&d, fresh->lanes, fresh->cs, &b);
+        }
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (st != TC_OK) {
+            // no other stream joins a group being created, so only this slot goes with it
+            srv->slots.erase(sl->id);
+            delete sl;
+            srv->groups.erase(std::find(srv->groups.begin(), srv->groups.end(), fresh));
+            srv->bytes_used -= fresh->bytes;
+            destroy_group(fresh);
+            return st;
+        }
+        fresh->b = b;
     }
     std::lock_guard<std::mutex> lk(srv->mu);
-    if (st != TC_OK) {
-        srv->slots.erase(sl->id);
-        srv->bytes_used -= need;
-        if (sl->cs) cudaStreamDestroy(sl->cs);
-        delete sl;
-        return st;
-    }
-    sl->s = s;
     *stream_id = sl->id;
     srv->cv_work.notify_all();
     return TC_OK;
@@ -246,7 +389,7 @@ extern "C" tc_status tc_server_submit(tc_server *srv, int stream_id, const float
     if (!srv || !I_host || !P_host || !O_host) return srv_fail(TC_ERR_INVALID_ARG, "tc_server_submit: NULL argument");
     std::lock_guard<std::mutex> lk(srv->mu);
     auto it = srv->slots.find(stream_id);
-    if (it == srv->slots.end() || !it->second->s)
+    if (it == srv->slots.end() || !it->second->g->b)
         return srv_fail(TC_ERR_INVALID_ARG, "tc_server_submit: unknown stream");
     Slot *sl = it->second;
     if (sl->closing) return srv_fail(TC_ERR_STATE, "tc_server_submit: stream is closing");
@@ -295,23 +438,31 @@ extern "C" tc_status tc_server_cancel(tc_server *srv, int stream_id) {
 
 extern "C" tc_status tc_server_close(tc_server *srv, int stream_id) {
     if (!srv) return srv_fail(TC_ERR_INVALID_ARG, "tc_server_close: NULL server");
-    Slot *sl = nullptr;
+    Group *dead = nullptr;
     {
         std::unique_lock<std::mutex> lk(srv->mu);
         auto it = srv->slots.find(stream_id);
-        if (it == srv->slots.end() || !it->second->s) return srv_fail(TC_ERR_INVALID_ARG, "tc_server_close: unknown stream");
-        sl = it->second;
+        if (it == srv->slots.end() || !it->second->g->b)
+            return srv_fail(TC_ERR_INVALID_ARG, "tc_server_close: unknown stream");
+        Slot *sl = it->second;
         sl->closing = true;
         srv->cv_done.wait(lk, [&] { return sl->q.empty() && !sl->busy; });
-        srv->slots.erase(it);
-        srv->bytes_used -= sl->bytes;
+        Group *g = sl->g;
+        srv->slots.erase(sl->id);
+        g->lane_slot[sl->lane] = nullptr;
+        delete sl;
+        if (g->open_slots() == 0) {
+            // the group's last stream: free its memory (no step of it can be running: every
+            // lane's frames are done)
+            srv->cv_done.wait(lk, [&] { return !g->busy; });
+            srv->groups.erase(std::find(srv->groups.begin(), srv->groups.end(), g));
+            srv->bytes_used -= g->bytes;
+            dead = g;
+        }
+        srv->cv_work.notify_all();
     }
-    tc_status st = tc_destroy(sl->s);
-    cudaStreamDestroy(sl->cs);
-    delete sl;
-    std::lock_guard<std::mutex> lk(srv->mu);
-    srv->cv_work.notify_all();
-    return st;
+    if (dead) destroy_group(dead);
+    return TC_OK;
 }
 
 extern "C" size_t tc_server_bytes_in_use(const tc_server *srv) {
@@ -329,11 +480,8 @@ extern "C" tc_status tc_server_destroy(tc_server *srv) {
         srv->cv_work.notify_all();
     }
     for (auto &t : srv->workers) t.join();
-    for (auto &kv : srv->slots) {
-        if (kv.second->s) tc_destroy(kv.second->s);
-        if (kv.second->cs) cudaStreamDestroy(kv.second->cs);
-        delete kv.second;
-    }
+    for (auto &kv : srv->slots) delete kv.second;
+    for (Group *g : srv->groups) destroy_group(g);
     delete srv;
     return TC_OK;
 }

@@ -1,5 +1,7 @@
-"""The multi-stream server (tc_server_*): results of a stream are the same alone and in a
-mix with other streams running concurrently, HBM-budget admission, and cancellation."""
+"""The multi-stream server (tc_server_*): results of a stream are the same alone, in a mix
+with other streams running concurrently, and batched with streams of its size (frames of
+several streams in one step's shared launches), and equal a plain stream's; HBM-budget
+admission of shared batches, and cancellation."""
 import numpy as np
 import pytest
 
@@ -31,12 +33,24 @@ STREAMS = [(320, 200, 11), (256, 160, 12), (320, 200, 13), (200, 136, 14)]
 N_FRAMES = 4
 
 
-def test_each_stream_alone_equals_in_the_mix():
+@pytest.mark.parametrize("batch_lanes", [1, 4])
+def test_each_stream_alone_equals_in_the_mix(batch_lanes):
+    import torch
     path, _ = weights_file(*NET)
     data = {k: _frames(W, H, seed, N_FRAMES) for k, (W, H, seed) in enumerate(STREAMS)}
+    # a plain stream (tc_create_stream) per sequence
+    plain = {}
+    for k, (W, H, _) in enumerate(STREAMS):
+        s = tc.Stream(W, H, "bf16", weights_path=path)
+        O = torch.empty((3, H, W), device="cuda")
+        plain[k] = []
+        for t in range(N_FRAMES):
+            s.process_frame(torch.from_numpy(data[k][0][t]).cuda(), torch.from_numpy(data[k][1][t]).cuda(), O)
+            plain[k].append(O.cpu().numpy())
+        s.destroy()
     # alone: one worker, one stream at a time
     alone = {}
-    srv = tc.Server(path, precision="bf16", workers=1)
+    srv = tc.Server(path, precision="bf16", workers=1, batch_lanes=batch_lanes)
     for k, (W, H, _) in enumerate(STREAMS):
         sid = srv.open(W, H)
         outs = [np.zeros((3, H, W), np.float32) for _ in range(N_FRAMES)]
@@ -48,8 +62,9 @@ def test_each_stream_alone_equals_in_the_mix():
         alone[k] = outs
         srv.close(sid)
     srv.destroy()
-    # mix: four workers, all streams open, frames submitted interleaved
-    srv = tc.Server(path, precision="bf16", workers=4)
+    # mix: four workers, all streams open, frames submitted interleaved (with batch_lanes 4
+    # the two 320x200 streams share a batch, and their queued frames share steps)
+    srv = tc.Server(path, precision="bf16", workers=4, batch_lanes=batch_lanes)
     sids = {k: srv.open(W, H) for k, (W, H, _) in enumerate(STREAMS)}
     mixed = {k: [np.zeros((3, H, W), np.float32) for _ in range(N_FRAMES)] for k, (W, H, _) in enumerate(STREAMS)}
     for t in range(N_FRAMES):
@@ -60,11 +75,16 @@ def test_each_stream_alone_equals_in_the_mix():
     for k in range(len(STREAMS)):
         frames = [c["frame"] for c in done if c["stream_id"] == sids[k]]
         assert frames == sorted(frames)            # per-stream order kept
+    if batch_lanes > 1:
+        assert max(c["batch"] for c in done) >= 2  # frames of two streams ran in one step
+    else:
+        assert all(c["batch"] == 1 for c in done)
     srv.destroy()
     for k in range(len(STREAMS)):
         for t in range(N_FRAMES):
             # same kernels, same inputs: bit-identical whatever else runs on the GPU
             assert np.array_equal(alone[k][t], mixed[k][t]), (k, t)
+            assert np.array_equal(alone[k][t], plain[k][t]), (k, t)
 
 
 def test_budget_admission_and_release():
@@ -83,19 +103,33 @@ def test_budget_admission_and_release():
     c = srv.open(320, 200)                          # the freed memory admits a new stream
     assert c not in (a, b) and srv.bytes_in_use == 2 * per
     srv.destroy()
+    # shared batches: two streams of a size take two lanes of one batch, a third a new one
+    srv = tc.Server(path, precision="bf16", workers=2, batch_lanes=2)
+    per2 = srv.stream_bytes(320, 200)
+    assert per < per2 < 2 * per
+    a, b = srv.open(320, 200), srv.open(320, 200)
+    assert srv.bytes_in_use == per2
+    c = srv.open(320, 200)
+    assert srv.bytes_in_use == 2 * per2
+    srv.close(a)
+    assert srv.bytes_in_use == 2 * per2             # its batch still holds b
+    srv.close(b)
+    assert srv.bytes_in_use == per2                 # the batch's last stream closed
+    srv.close(c)
+    assert srv.bytes_in_use == 0
+    srv.destroy()
 
 
-def test_admission_charge_covers_what_a_stream_allocates():
+@pytest.mark.parametrize("lanes", [1, 3])
+def test_admission_charge_covers_what_a_batch_allocates(lanes):
     path, _ = weights_file(*NET)
-    for prec in ("bf16", "fp32"):
-        srv = tc.Server(path, precision=prec, workers=1)
+    for prec in ("bf16", "fp32", "fp16"):
+        srv = tc.Server(path, precision=prec, workers=1, batch_lanes=lanes)
         want = srv.stream_bytes(320, 200)
         srv.destroy()
-        s = tc.Stream(320, 200, prec, weights_path=path)
-        I = np.zeros((3, 200, 320), np.float32)
-        s.process_frame_host(I, I, np.zeros_like(I))   # allocates the host-entry staging too
-        got = tc.stream_device_bytes(s)
-        s.destroy()
+        b = tc.Batch(320, 200, lanes, prec, weights_path=path)
+        got = tc.stream_device_bytes(b) + 3 * lanes * 3 * 200 * 320 * 4  # + the server's I, P, O staging
+        b.destroy()
         assert got <= want <= 1.05 * got + (1 << 20), (prec, got, want)
 
 
