@@ -227,7 +227,7 @@ def consistency_controls(step, solver_iters, latency):
 
 
 def time_stream(tc, torch, path, dev_frames, dev_styl, precision, steps, warmup, profile=False, scales=None,
-                solver_iters=0, latency=0, flow_downscale=1, pipelined=False):
+                solver_iters=0, latency=0, flow_downscale=1, pipelined=False, frame_timing=False):
     """Runs warmup + steps frames through one stream; returns timings (device events).
     pipelined: tc_set_pipelined (frame t+1's pyramid overlaps the flow estimation of frames t
     and t-1, each with its own buffer set);
@@ -252,6 +252,8 @@ def time_stream(tc, torch, path, dev_frames, dev_styl, precision, steps, warmup,
     torch.cuda.synchronize()
     if profile:
         s.set_profiling(True)
+    if frame_timing:
+        s.set_frame_timing(True)  # pipelined: per-frame device latency (pyramid may start -> blend done)
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     launches = 0
@@ -272,10 +274,11 @@ def time_stream(tc, torch, path, dev_frames, dev_styl, precision, steps, warmup,
     per = None if pipelined else [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
     total = ev[0].elapsed_time(ev[steps])
     prof = s.get_profile() if profile else None
+    frame_ms = [float(v) for v in s.get_frame_times(steps)] if frame_timing else None
     tc_layers, tc_corr = s.tensor_core_layers, s.tensor_core_correlation_levels
     s.destroy()
     return dict(total_ms=total, per_frame_ms=per, launches=launches, profile=prof, tc_layers=tc_layers,
-                tc_corr=tc_corr)
+                tc_corr=tc_corr, frame_ms=frame_ms)
 
 
 def pair_flows(tc, torch, path, dev_frames, dev_styl, precision, scales=None):
@@ -400,6 +403,11 @@ def run_ours(args):
         tc, torch, path, dev_frames, dev_styl, args.precision, args.steps, args.warmup, scales=scales,
         solver_iters=args.solver_iters, latency=args.latency, flow_downscale=args.flow_downscale)
 
+    # Pipelined mode's per-frame latency, in a pass of its own (two timing events per frame)
+    plat = None if args.sequential else time_stream(
+        tc, torch, path, dev_frames, dev_styl, args.precision, args.steps, args.warmup, scales=scales,
+        solver_iters=args.solver_iters, latency=args.latency, flow_downscale=args.flow_downscale, pipelined=True,
+        frame_timing=True)
     # Per-stage device times over the same number of steps (events around every launch).
     prof = time_stream(tc, torch, path, dev_frames, dev_styl, args.precision, args.steps, 2, profile=True,
                        scales=scales, solver_iters=args.solver_iters, latency=args.latency,
@@ -562,6 +570,11 @@ def run_ours(args):
                        "ms_per_step": round(seq["total_ms"] / args.steps, 4)},
         "latency_ms": {"p50": round(per[len(per) // 2], 4), "p99": round(per[min(len(per) - 1, int(0.99 * len(per)))], 4),
                        "mode": "sequential (per-frame device time)"},
+        "latency_ms_pipelined": (None if plat is None else {
+            "p50": round(sorted(plat["frame_ms"])[len(plat["frame_ms"]) // 2], 4),
+            "p99": round(sorted(plat["frame_ms"])[min(len(plat["frame_ms"]) - 1, int(0.99 * len(plat["frame_ms"])))], 4),
+            "frames_per_s_while_timed": round(args.steps / (plat["total_ms"] / 1e3), 3),
+            "mode": "pipelined: device time from the moment a frame's pyramid may start to the end of its blend"}),
         "stage_ms_per_frame": {k: round(v[0] / steps, 4) for k, v in p.items() if v[1]},
         "roofline": {"kernel": dom, "bound": bound, "achieved": round(achieved, 2), "peak": peak, "unit": unit,
                      "frac": round(achieved / peak, 4) if peak else None,

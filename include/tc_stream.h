@@ -496,6 +496,17 @@ TC_API tc_status tc_server_close(tc_server *srv, int stream_id);
 /* Cancels every queued frame, stops the workers and frees everything. */
 TC_API tc_status tc_server_destroy(tc_server *srv);
 
+/* Per-frame latency in pipelined mode (tc_set_pipelined), where frames overlap and the
+ * caller's stream sees no per-frame order: enable != 0 starts a record (cleared) of, for
+ * every frame given from now on, the device time from the moment its feature pyramid may
+ * start (its own stream past the waits for the frames it depends on) to the end of its
+ * blend.  Two timing events per frame; 0 stops recording. */
+TC_API tc_status tc_set_frame_timing(tc_stream *s, int enable);
+
+/* Waits for the last recorded frame, then copies the first min(n, recorded) latencies (ms,
+ * host floats) to ms and the number recorded to *count. */
+TC_API tc_status tc_get_frame_times(tc_stream *s, float *ms, int n, int *count);
+
 /* ------------------------------------------------------------------------------------
  * Batches: `lanes` independent streams of one size whose networks run in shared launches.
  * The serving problem of Sec. 3.1 (many streams, each with its own per-frame state) at a

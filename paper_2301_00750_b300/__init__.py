@@ -36,7 +36,8 @@ EXPORTED = ["tc_default_consistency", "tc_create_stream", "tc_set_consistency", 
             "tc_flush", "tc_last_output_frame", "tc_op_consistency_next", "tc_op_downscale2", "tc_op_sepconv",
             "tc_process_frame_host_async", "tc_set_pipelined", "tc_join", "tc_fp8_scales_from_amax",
             "tc_test_stall_next_convs", "tc_test_fail_device_allocation", "tc_create_batch", "tc_process_lanes",
-            "tc_set_lane_consistency", "tc_reset_lane", "tc_get_lane_flows"]
+            "tc_set_lane_consistency", "tc_reset_lane", "tc_get_lane_flows", "tc_set_frame_timing",
+            "tc_get_frame_times"]
 NOALLOC_SCRATCH_BYTES = 16 << 20
 PROFILE_CATEGORIES = ["pyramid_conv", "estimator_conv", "head", "correlation", "warp", "upsample", "consistency",
                       "other", "solver", "refine"]
@@ -89,6 +90,10 @@ _lib.tc_set_amax_recording.argtypes = [_vp, _i]
 _lib.tc_get_amax.argtypes = [_vp, ctypes.POINTER(_f), _i]
 _lib.tc_set_fp8_scales.argtypes = [_vp, ctypes.POINTER(_f), _i]
 _lib.tc_fp8_scales_from_amax.argtypes = [ctypes.POINTER(_f), _i, _f, ctypes.POINTER(_f)]
+_lib.tc_set_frame_timing.argtypes = [_vp, _i]
+_lib.tc_get_frame_times.argtypes = [_vp, ctypes.POINTER(_f), _i, ctypes.POINTER(_i)]
+_lib.tc_set_frame_timing.restype = ctypes.c_int
+_lib.tc_get_frame_times.restype = ctypes.c_int
 _lib.tc_create_batch.argtypes = [ctypes.POINTER(TcStreamDesc), _i, _vp, ctypes.POINTER(_vp)]
 _lib.tc_process_lanes.argtypes = [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                   ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp)]
@@ -260,6 +265,17 @@ class Stream:
     def get_flows(self, Fb=None, Ff=None):
         import torch
         _check(_lib.tc_get_flows(self._h, _ptr(Fb, torch.float32, "Fb"), _ptr(Ff, torch.float32, "Ff")), self._h)
+
+    def set_frame_timing(self, enable: bool):
+        """Pipelined mode: record every frame's device latency (pyramid may start -> blend done)."""
+        _check(_lib.tc_set_frame_timing(self._h, int(bool(enable))), self._h)
+
+    def get_frame_times(self, n=100000) -> np.ndarray:
+        """The recorded per-frame latencies in milliseconds (waits for the last frame)."""
+        buf = (_f * n)()
+        cnt = _i()
+        _check(_lib.tc_get_frame_times(self._h, buf, n, ctypes.byref(cnt)), self._h)
+        return np.array(buf[:min(n, cnt.value)], np.float32)
 
     def set_graphs(self, enable: bool):
         """Replay each frame as one CUDA graph launch (default) or launch kernel by kernel."""

@@ -407,6 +407,11 @@ struct tc_stream {
     // graph captured on the second use
     std::map<int, int> range_uses;
     std::map<int, FrameGraph> range_graphs;
+    // per-frame latency in pipelined mode (tc_set_frame_timing): a timing event when a
+    // frame's pyramid may start (its stream past its waits) and one when its blend ends
+    bool frame_timing = false;
+    std::vector<cudaEvent_t> ft_start, ft_done;
+    size_t ft_n = 0;
 };
 
 static std::mutex g_err_mu;
@@ -472,6 +477,10 @@ static tc_status upload(tc_stream *s, float **dst, const std::vector<float> &v) 
 }
 
 static void free_all(tc_stream *s) {
+    for (cudaEvent_t e : s->ft_start) cudaEventDestroy(e);
+    for (cudaEvent_t e : s->ft_done) cudaEventDestroy(e);
+    s->ft_start.clear();
+    s->ft_done.clear();
     for (auto &B : s->lv) {
         for (auto &pl : B.tcplan) pl.release();
         B.headplan.release();
@@ -1457,6 +1466,16 @@ static tc_status process_pipelined(tc_stream *s, const float *I, const float *P,
     }
     // estimation t: after the blend that last read this buffer set's flows
     if (t >= nsets) TC_TRY(s, cudaStreamWaitEvent(es, s->ev_blends[(t - nsets) % NEV], 0), "cudaStreamWaitEvent");
+    if (s->frame_timing) {
+        if (s->ft_n == s->ft_start.size()) {
+            cudaEvent_t a = nullptr, b = nullptr;
+            TC_TRY(s, cudaEventCreate(&a), "cudaEventCreate");
+            TC_TRY(s, cudaEventCreate(&b), "cudaEventCreate");
+            s->ft_start.push_back(a);
+            s->ft_done.push_back(b);
+        }
+        TC_TRY(s, cudaEventRecord(s->ft_start[s->ft_n], s->pst), "cudaEventRecord");
+    }
     cudaStream_t caller = s->st;
     if (!s->graphs || s->prof || t < 2) {
         s->st = s->pst;
@@ -1504,6 +1523,7 @@ static tc_status process_pipelined(tc_stream *s, const float *I, const float *P,
         s->launches = Gp.launches + Ge.launches + Gb.launches;
     }
     TC_TRY(s, cudaEventRecord(s->ev_blends[e], s->bst), "cudaEventRecord");
+    if (s->frame_timing) TC_TRY(s, cudaEventRecord(s->ft_done[s->ft_n++], s->bst), "cudaEventRecord");
     s->last_blend = e;
     s->last_set = set;
     s->t += 1;
@@ -2062,6 +2082,26 @@ extern "C" tc_status tc_join(tc_stream *s) {
     tc_status r = check_stream(s, "tc_join");
     if (r != TC_OK) return r;
     return join_caller(s);
+}
+
+extern "C" tc_status tc_set_frame_timing(tc_stream *s, int enable) {
+    tc_status r = single_only(s, "tc_set_frame_timing");
+    if (r != TC_OK) return r;
+    s->frame_timing = enable != 0;
+    s->ft_n = 0;
+    return TC_OK;
+}
+
+extern "C" tc_status tc_get_frame_times(tc_stream *s, float *ms, int n, int *count) {
+    tc_status r = single_only(s, "tc_get_frame_times");
+    if (r != TC_OK) return r;
+    if (!count || (n > 0 && !ms)) return fail(s, TC_ERR_INVALID_ARG, "tc_get_frame_times: NULL argument");
+    const int k = (int)std::min<size_t>(s->ft_n, n > 0 ? (size_t)n : 0);
+    if (s->ft_n > 0) TC_TRY(s, cudaEventSynchronize(s->ft_done[s->ft_n - 1]), "cudaEventSynchronize");
+    for (int i = 0; i < k; ++i)
+        TC_TRY(s, cudaEventElapsedTime(&ms[i], s->ft_start[i], s->ft_done[i]), "cudaEventElapsedTime");
+    *count = (int)s->ft_n;
+    return TC_OK;
 }
 
 extern "C" tc_status tc_flush(tc_stream *s, float *O_t, float *wc_opt, uint8_t *mask_opt) {

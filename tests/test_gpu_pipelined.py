@@ -200,3 +200,28 @@ def test_pipelined_state_errors():
         s.set_amax_recording(True)
     s.destroy()
     torch.cuda.synchronize()
+
+
+def test_pipelined_frame_timing_records_every_frame():
+    """tc_set_frame_timing: one latency per frame given in pipelined mode (device time from
+    the moment its pyramid may start to the end of its blend), positive and finite; the
+    recording changes no result."""
+    path, _ = weights_file((16, 32, 64, 96, 128), 4)
+    frames, styl = _frames(10, seed=16)
+    a, _ = _run(path, frames, styl, "fp16", True)
+    import torch
+    s = tc.Stream(W, H, "fp16", weights_path=path)
+    s.set_pipelined(True)
+    s.set_frame_timing(True)
+    dI, dP = [to_dev(I) for I in frames], [to_dev(P) for P in styl]
+    outs = [torch.empty((3, H, W), device="cuda") for _ in frames]
+    for t in range(len(frames)):
+        s.set_consistency(k1=(0.2, 0.5, 0.9)[t % 3])
+        s.process_frame(dI[t], dP[t], outs[t])
+    times = s.get_frame_times()
+    s.join()
+    torch.cuda.synchronize()
+    assert len(times) == len(frames) and np.isfinite(times).all() and (times > 0).all()
+    for t in range(len(frames)):
+        assert np.array_equal(to_np(outs[t]), a[t][0]), t
+    s.destroy()
