@@ -428,6 +428,8 @@ def run_ours(args):
     if not args.skip_variants and args.flow_downscale == 1 and args.latency == 0 and args.solver_iters == 0:
         ref = pair_flows(tc, torch, path, dev_frames, dev_styl, "fp32")
         for prec in ("fp16", "bf16", "fp8"):
+            if prec == "fp8" and scales is None:
+                continue  # E4M3 not calibrated in this run (--skip-fp8)
             Fb, Ff = pair_flows(tc, torch, path, dev_frames, dev_styl, prec, scales if prec == "fp8" else None)
             eb, ef = epe_px(Fb, ref[0]), epe_px(Ff, ref[1])
             if prec == args.precision:

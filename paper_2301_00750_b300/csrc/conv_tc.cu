@@ -4,10 +4,11 @@
 // one swizzle span: 64 bf16 (128 e4m3) channels with the 128-byte swizzle, or 32 / 16 bf16
 // channels with the 64- / 32-byte swizzle for layers that have no more input channels than
 // that (the 16- and 32-channel pyramid levels), so no step multiplies zero padding
-// wider than the layer.  The descriptions below use the 128-byte case.  Stride-1 layers use
-// conv_tc_halo_kernel (below), which loads each activation tile once per kernel row and
-// reuses it for the three horizontal taps; the description here is of the per-tap kernel,
-// which serves the stride-2 layers.  One CTA computes a
+// wider than the layer.  The descriptions below use the 128-byte case.  Stride-1 3x3 layers
+// run conv_tc_tiles_kernel (below), a persistent kernel that reuses each loaded halo row for
+// the three horizontal taps and up to three output rows and each loaded kernel row of
+// weights for several output rows; the description here is of the per-tap kernel, which
+// serves the stride-2 layers and the pointwise (1x1) convs.  One CTA computes a
 // tile of 128 consecutive output pixels of one row (M = 128) and all cout (N = BN, a
 // multiple of 16 up to 128):
 //   * warp 0, lane 0 (producer): for every (tap, 64-channel chunk) step, one TMA tiled load
@@ -27,6 +28,7 @@
 #include <atomic>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "../../include/tc_stream.h"
 #include "conv_tc.cuh"
@@ -39,7 +41,6 @@ namespace {
 using namespace ptx;
 
 constexpr int BM = 128;                    // output pixels per CTA (MMA M)
-constexpr int BK = 64;                     // bf16 channels of the widest K step (128 B); e4m3 steps hold 128
 
 enum : int { ERR_PRODUCER = 1, ERR_MMA = 2, ERR_EPILOGUE = 3, ERR_DRAIN = 4 };
 
@@ -73,19 +74,26 @@ struct TcLaunch {
     int taps;             // 9: 3x3 conv; 1: pointwise 1x1 conv (the centre tap only)
     int tail;             // halo kernel: the last channel step is a 64-byte tail
     int f16;              // 16-bit operands and outputs are IEEE half instead of bfloat16
-    int stall;            // halo kernel, test hook: the producer issues no loads (see tc_test_stall_next_convs)
+    int stall;            // stride-1 kernels, test hook: the producer issues no loads (see tc_test_stall_next_convs)
+    // persistent tile kernel (conv_tc_tiles_kernel): its tiling, chosen by the launcher
+    int R;                // output rows per tile (1..TILE_RMAX), each a 128-pixel accumulator
+    int acc_cols;         // TMEM columns per accumulator (two sets of R accumulators)
+    int tmem_cols;        // TMEM columns allocated (a power of two >= 2 * R * acc_cols)
+    int sa, sb;           // halo ring units (a channel step's R + 2 rows each); weight ring slots, a
+                          // kernel row each (0: resident weights)
+    int ntx, nrg, ntiles; // tiles: 128-pixel column tiles x groups of R rows x images
 };
 
 // Epilogue shared by the conv kernels: thread r of the CTA owns accumulator row r, i.e.
-// output pixel (img, y, x0 + r).
+// output pixel (img, y, x0 + r), stored for r < tw.
 template <int BN, bool HEAD, bool F8>
 __device__ __forceinline__ void conv_epilogue(uint32_t tmem, const TcLaunch &p, int warp, int lane, int x0, int y,
-                                              int img) {
+                                              int img, int tw = BM) {
     if (HEAD) {
         const int x = x0 + warp * 32 + lane;
         uint32_t r[16];
         tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), r);
-        if (x < p.wo) {
+        if (warp * 32 + lane < tw && x < p.wo) {
             const size_t pix = (size_t)(img * p.ho + y) * p.wo + x;
             float2 up = make_float2(0.f, 0.f);
             if (p.up) up = reinterpret_cast<const float2 *>(p.up)[pix];
@@ -104,7 +112,7 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, const TcLaunch &p, 
         for (int c0 = 0; c0 < BN; c0 += 16) {
             uint32_t r[16];
             tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-            if (x < p.wo) {
+            if (row < tw && x < p.wo) {
                 // bias (and e4m3 weight scales) of the 16 columns: four 16-byte loads where
                 // the arrays allow it, else 16 scalar ones
                 float bv[16], sv[16];
@@ -275,200 +283,112 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
 }
 
-// Stride-1 variant that fetches each activation tile once per (kernel row ky, channel
-// step): a TMA load of the 130-pixel halo row [x0 - 1, x0 + 129) x 64 channels, reused by
-// the three horizontal taps through descriptors whose start is shifted by kx rows of the
-// 128-byte-swizzled tile.  Activation halos and weight tiles travel in two separate rings
-// (2 halo slots, SB weight slots), so a halo stays resident while its three taps run.
-constexpr uint32_t HALO_ROWS = BM + 2;
-constexpr uint32_t HALO_SLOT = 17408;             // rounded up to the 1024-byte swizzle atom
-constexpr int HALO_SA = 2;
-__host__ __device__ constexpr int halo_sb(int bn) { return bn >= 96 ? 3 : 4; }
-__host__ __device__ constexpr size_t halo_smem_for(int bn) {
-    return (size_t)HALO_SA * HALO_SLOT + (size_t)halo_sb(bn) * bn * BK * 2 + 1024 + 256;
+// Persistent stride-1 3x3 conv.  A tile is R output rows of TW = 126 consecutive pixels; the
+// grid holds one CTA per SM and each CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x,
+// ...  A halo row is the 128 input pixels [x0 - 1, x0 + 127) of one channel step, so the
+// MMA's M = 128 rows read halo rows m + kx for output m: outputs 126 and 127 read the two
+// rows past the slot and are discarded (no tile count changes at the pyramid sizes used, and
+// a slot is exactly 128 x 128 bytes).  Per tile and channel step c the R + 2 halo rows form
+// one unit of a ring (one barrier), and the weights of each kernel row (c, ky, kx = 0..2, one
+// TMA box of three taps) are multiplied into all R row accumulators while resident, so an
+// output row costs (R + 2) / R halo rows and 1 / R of the layer's weights.  Layers whose
+// packed weights fit beside the ring keep them resident for the whole kernel (loaded once
+// per CTA, before the previous kernel has finished); wider layers stream them through a
+// second ring, a kernel row per slot, in the order the MMAs consume them.
+//   * warp 8, lane 0 (halo producer): per tile and channel step, the unit of halo rows
+//     0 .. R + 1;
+//   * warp 9, lane 0 (weight producer): the resident weights once, or per tile, channel step
+//     and kernel row the three taps of that row;
+//   * warps 10 and 11, lane 0 (MMA issuers): issuer j owns the output rows r = j, j + 2, ...
+//     of every tile.  Per channel step it waits for the halo unit, per kernel row for the
+//     weight slot; it issues the K steps of its rows for the three taps (halo row r + ky
+//     shifted by kx pixels: a row offset of the swizzled slot) and releases the weight slot,
+//     then the halo unit after ky = 2.  Every release barrier counts both issuers.  A thread
+//     issues MMAs only as fast as its instruction stream allows (a barrier wait or a commit
+//     costs ~100-160 cycles of issue), so two issuers overlap one's synchronisation with the
+//     other's MMAs; each accumulator still receives its MMAs in the same order;
+//   * warps 0-7 (epilogue): warp w drains TMEM lanes 32 (w % 4) .. of rows r = w / 4,
+//     w / 4 + 2, ... of the finished set, then returns the set to the issuers.  The two sets
+//     let the epilogue of tile j run under the MMAs of tile j + 1.
+// Every wait is bounded as in the kernel above; on an error each role stops, the producers
+// wait for their loads in flight and the issuers for their MMAs before TMEM is freed.
+constexpr int TW = BM - 2;  // output pixels per tile
+constexpr int TILE_RMAX = 8;
+constexpr int TILE_EPI_WARPS = 8;
+constexpr int TILE_ISSUERS = 2;
+constexpr int TILE_THREADS = 32 * (TILE_EPI_WARPS + 2 + TILE_ISSUERS);
+__host__ __device__ constexpr uint32_t round1k(uint32_t b) { return (b + 1023u) / 1024u * 1024u; }
+__host__ __device__ constexpr int tile_issuers(int r) { return r >= 2 ? TILE_ISSUERS : 1; }
+
+// Waits for the last loads issued into a ring to land (error path of the producers).
+__device__ __forceinline__ void drain_ring(uint32_t full0, int slots, uint32_t issued, int *err) {
+    const unsigned long long t0 = global_ns();
+    for (uint32_t u = issued > (uint32_t)slots ? issued - (uint32_t)slots : 0; u < issued; ++u)
+        while (!mbar_try(full0 + 8 * (u % (uint32_t)slots), (u / (uint32_t)slots) & 1u))
+            if (global_ns() - t0 > WAIT_NS) { atomicCAS(err, 0, ERR_DRAIN); return; }
 }
 
-template <int BN, bool HEAD, bool F8>
-__global__ void __launch_bounds__(128, 1)
-conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                    const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2, const TcLaunch p) {
-    constexpr int SB = halo_sb(BN);
-    constexpr uint32_t B_BYTES = BN * BK * 2;
-    constexpr uint32_t TMEM_COLS = tmem_cols_for(BN);
+// The K steps of one tap into an issuer's accumulators: its m-th row reads halo slot
+// descriptor dA[m] advanced by the kx shift.  NK = 4, 2 or 1 (128-, 64- or 32-byte channel
+// steps); f0 = 0 for the first MMA of a tile (clears the accumulators).
+template <bool F8, int M, int NK>
+__device__ __forceinline__ void tap_mmas(uint32_t acc0, uint32_t acc_step, const uint64_t (&dA)[M], uint32_t ashift,
+                                         uint64_t db, uint32_t idesc, int nmine, uint32_t f0) {
+#pragma unroll
+    for (int kk = 0; kk < NK; ++kk)
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+            if (m < nmine)
+                umma<F8>(acc0 + (uint32_t)m * acc_step, dA[m] + (uint64_t)(ashift + 2 * kk), db + (uint64_t)(2 * kk),
+                         idesc, kk == 0 ? f0 : 1u);
+}
+
+template <int BN, bool HEAD, bool F8, int R>
+__global__ void __launch_bounds__(TILE_THREADS, 1)
+conv_tc_tiles_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
+                     const TcLaunch p) {
+    constexpr int NI = tile_issuers(R);  // MMA issuers
+    constexpr int MR = R / NI;           // accumulator rows per issuer
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t *sA = smem;
-    uint8_t *sB = smem + HALO_SA * HALO_SLOT;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + SB * B_BYTES);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * HALO_SA + 2 * SB + 1);
-    const uint32_t fullA = smem_u32(bars), emptyA = fullA + 8 * HALO_SA;
-    const uint32_t fullB = emptyA + 8 * HALO_SA, emptyB = fullB + 8 * SB;
-    const uint32_t accum = emptyB + 8 * SB;
+    const int nch = p.nch, UA = p.sa, SB = p.sb;
+    const bool resident = SB == 0;
+    // a kernel row of weights (three taps): bytes in a full channel step and in the 64-byte tail step
+    const uint32_t ufull = round1k(3u * BN * (uint32_t)p.rb), utail = round1k(3u * BN * 64u);
+    const uint32_t wbytes = resident ? 3u * (uint32_t)(nch - p.tail) * ufull + (p.tail ? 3u * utail : 0u)
+                                     : (uint32_t)SB * ufull;
+    const uint32_t aslot = (uint32_t)BM * (uint32_t)p.rb, aunit = (uint32_t)(R + 2) * aslot;
+    uint8_t *sW = smem;
+    uint8_t *sA = smem + wbytes;
+    // 256 bytes after the halo ring: the two rows past a slot that outputs 126, 127 read
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sA + (size_t)UA * aunit + 256);
+    const uint32_t fullA = smem_u32(bars), emptyA = fullA + 8 * UA;
+    const uint32_t fullB = emptyA + 8 * UA, emptyB = fullB + 8 * SB;
+    const uint32_t wfull = emptyB + 8 * SB, accf0 = wfull + 8, acce0 = accf0 + 16, done0 = acce0 + 16;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * UA + 2 * SB + 7);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int x0 = blockIdx.x * BM, y = blockIdx.y, img = blockIdx.z;
-    const int ng = 3 * p.nch;  // (ky, channel step) groups
-    const uint32_t halo_tx = HALO_ROWS * (uint32_t)p.rb, b_tx = (uint32_t)BN * (uint32_t)p.rb;
-
     if (threadIdx.x == 0) {
-        for (int s = 0; s < HALO_SA; ++s) {
+        for (int s = 0; s < UA; ++s) {
             mbar_init(fullA + 8 * s, 1);
-            mbar_init(emptyA + 8 * s, 1);
+            mbar_init(emptyA + 8 * s, NI);
         }
         for (int s = 0; s < SB; ++s) {
             mbar_init(fullB + 8 * s, 1);
-            mbar_init(emptyB + 8 * s, 1);
-        }
-        mbar_init(accum, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tmem_slot;
-    pdl_wait();  // every global access below follows the previous kernel
-
-    if (threadIdx.x == 0) {
-        // ---- producer
-        int ga = 0, gb = 0;  // halo loads and weight loads issued
-        bool fine = !p.stall;  // stalled (test hook): nothing is issued, so the MMA warp's waits run out
-        for (int g = 0; g < ng && fine; ++g) {
-            const int ky = g / p.nch, ch = g - ky * p.nch;
-            const int sa = g % HALO_SA;
-            if (!mbar_wait(emptyA + 8 * sa, ((uint32_t)(g / HALO_SA) & 1u) ^ 1u, p.err, ERR_PRODUCER)) break;
-            const bool tl = p.tail && ch == p.nch - 1;  // the 32-channel tail step
-            mbar_expect_tx(fullA + 8 * sa, tl ? HALO_ROWS * 64u : halo_tx);
-            tma_load_4d(tl ? &tmA2 : &tmA, fullA + 8 * sa, smem_u32(sA + sa * HALO_SLOT), ch * p.kc, x0 - 1,
-                        y + ky - 1, img + p.img_off);
-            ga = g + 1;
-            for (int kx = 0; kx < 3; ++kx) {
-                const int kb = 3 * g + kx, sb = kb % SB;
-                if (!mbar_wait(emptyB + 8 * sb, ((uint32_t)(kb / SB) & 1u) ^ 1u, p.err, ERR_PRODUCER)) {
-                    fine = false;
-                    break;
-                }
-                mbar_expect_tx(fullB + 8 * sb, tl ? (uint32_t)BN * 64u : b_tx);
-                tma_load_3d(tl ? &tmB2 : &tmB, fullB + 8 * sb, smem_u32(sB + sb * B_BYTES), ch * p.kc, 0, ky * 3 + kx);
-                gb = kb + 1;
-            }
-        }
-        if (ga < ng || gb < 3 * ng) {
-            // Error path: let the loads already issued land before the CTA exits (none when
-            // stalled).
-            const unsigned long long t0 = global_ns();
-            for (int g = ga - HALO_SA < 0 ? 0 : ga - HALO_SA; g < ga; ++g)
-                while (!mbar_try(fullA + 8 * (g % HALO_SA), (uint32_t)(g / HALO_SA) & 1u))
-                    if (global_ns() - t0 > WAIT_NS) { atomicCAS(p.err, 0, ERR_DRAIN); break; }
-            for (int kb = gb - SB < 0 ? 0 : gb - SB; kb < gb; ++kb)
-                while (!mbar_try(fullB + 8 * (kb % SB), (uint32_t)(kb / SB) & 1u))
-                    if (global_ns() - t0 > WAIT_NS) { atomicCAS(p.err, 0, ERR_DRAIN); break; }
-        }
-    } else if (threadIdx.x == 32) {
-        // ---- MMA issuer
-        const uint32_t idesc = F8 ? idesc_e4m3(BM, BN) : (p.f16 ? idesc_f16(BM, BN) : idesc_bf16(BM, BN));
-        bool fine = true;
-        for (int g = 0; g < ng && fine; ++g) {
-            const int sa = g % HALO_SA;
-            if (!mbar_wait(fullA + 8 * sa, (uint32_t)(g / HALO_SA) & 1u, p.err, ERR_MMA)) break;
-            const uint32_t a0 = smem_u32(sA + sa * HALO_SLOT);
-            const int ch = g % p.nch;
-            const uint32_t rb = p.tail && ch == p.nch - 1 ? 64u : (uint32_t)p.rb;  // bytes of this K step
-            for (int kx = 0; kx < 3; ++kx) {
-                const int kb = 3 * g + kx, sb = kb % SB;
-                if (!mbar_wait(fullB + 8 * sb, (uint32_t)(kb / SB) & 1u, p.err, ERR_MMA)) {
-                    fine = false;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint64_t da = sw_desc(a0 + rb * (uint32_t)kx, rb);
-                const uint64_t db = sw_desc(smem_u32(sB + sb * B_BYTES), rb);
-                for (int kk = 0; kk < (int)rb / 32; ++kk)
-                    umma<F8>(tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
-                              (g | kx | kk) != 0 ? 1u : 0u);
-                umma_commit(emptyB + 8 * sb);
-            }
-            if (fine) umma_commit(emptyA + 8 * sa);  // the halo's three taps are done
-        }
-        umma_commit(accum);
-    }
-
-    int ok = 1;
-    if (lane == 0) ok = mbar_wait(accum, 0, p.err, ERR_EPILOGUE) && *(volatile int *)p.err == 0;
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) conv_epilogue<BN, HEAD, F8>(tmem, p, warp, lane, x0, y, img);
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
-    }
-}
-
-// Multi-row stride-1 variant for narrow layers (at most 32 outputs) whose input channels
-// fit one or two K steps (the launcher takes it for one): there the per-CTA
-// set-up (TMEM allocation, barriers, pipeline fill) outweighs the few MMAs of one row.  A
-// CTA computes ROWS output rows of one 128-pixel column tile:
-//   * warp 4, lane 0 (producer): the 9 x nch weight tiles once, then the halo units
-//     (input row, channel step) of the ROWS + 2 input rows [x0 - 1, x0 + 129) in order
-//     through a ring of RING x nch slots; each input row is loaded once for the three
-//     output rows that read it;
-//   * warp 5, lane 0 (MMA issuer): for output row r the nine taps of every channel step
-//     from input rows r, r + 1, r + 2 into TMEM accumulator r % 2; then it frees the units
-//     of input row r (their last reader) and signals the accumulator;
-//   * warps 0-3 (epilogue): drain accumulator r % 2 into output row y0 + r while the MMAs of
-//     row r + 1 run, then hand the accumulator back.
-// Every wait is bounded as in the kernels above.
-constexpr int ROWS = 4;
-constexpr int RING = 4;  // input rows held at once
-__host__ __device__ constexpr uint32_t halo_slot_for(int rb) { return (uint32_t)((HALO_ROWS * rb + 1023) / 1024 * 1024); }
-__host__ __device__ constexpr uint32_t wtile_for(int bn, int rb) { return (uint32_t)((bn * rb + 1023) / 1024 * 1024); }
-__host__ __device__ constexpr size_t rows_smem_for(int bn, int rb, int nch) {
-    return (size_t)RING * nch * halo_slot_for(rb) + 9 * (size_t)nch * wtile_for(bn, rb) + 1024 + 256;
-}
-
-template <int BN, bool HEAD, bool F8, int NCH>
-__global__ void __launch_bounds__(192, 1)
-conv_tc_rows_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcLaunch p) {
-    constexpr uint32_t ACC_COLS = tmem_cols_for(BN);
-    constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    constexpr int nch = NCH, ru = RING * NCH;  // channel steps (p.nch), ring units
-    const uint32_t hslot = halo_slot_for(p.rb), wtile = wtile_for(BN, p.rb);
-    uint8_t *sA = smem;
-    uint8_t *sW = smem + ru * hslot;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sW + 9 * nch * wtile);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * ru + 5);
-    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * ru, wfull = empty0 + 8 * ru;
-    const uint32_t accf0 = wfull + 8, acce0 = accf0 + 16;
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int x0 = blockIdx.x * BM, y0 = blockIdx.y * ROWS, img = blockIdx.z;
-    const int nrows = p.ho - y0 < ROWS ? p.ho - y0 : ROWS;
-    const int nunits = (nrows + 2) * nch;  // input rows y0 - 1 .. y0 + nrows, every channel step
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < ru; ++s) {
-            mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
+            mbar_init(emptyB + 8 * s, NI);
         }
         mbar_init(wfull, 1);
         for (int b = 0; b < 2; ++b) {
-            mbar_init(accf0 + 8 * b, 1);
-            mbar_init(acce0 + 8 * b, 4);  // one arrival per epilogue warp
+            mbar_init(accf0 + 8 * b, NI);
+            mbar_init(acce0 + 8 * b, TILE_EPI_WARPS);
+            mbar_init(done0 + 8 * b, 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS)
+                     "r"((uint32_t)p.tmem_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -476,75 +396,157 @@ conv_tc_rows_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    pdl_wait();  // every global access below follows the previous kernel
 
-    if (warp == 4 && lane == 0) {
-        // ---- producer
-        mbar_expect_tx(wfull, 9u * (uint32_t)nch * BN * (uint32_t)p.rb);
-        for (int t = 0; t < 9; ++t)
-            for (int ch = 0; ch < nch; ++ch)
-                tma_load_3d(&tmB, wfull, smem_u32(sW + (t * nch + ch) * wtile), ch * p.kc, 0, t);
-        int issued = 0;
-        for (int u = 0; u < nunits; ++u) {
-            const int s = u % ru, i = u / nch, ch = u - i * nch;
-            if (!mbar_wait(empty0 + 8 * s, ((uint32_t)(u / ru) & 1u) ^ 1u, p.err, ERR_PRODUCER)) break;
-            mbar_expect_tx(full0 + 8 * s, HALO_ROWS * (uint32_t)p.rb);
-            tma_load_4d(&tmA, full0 + 8 * s, smem_u32(sA + s * hslot), ch * p.kc, x0 - 1, y0 - 1 + i,
-                        img + p.img_off);
-            issued = u + 1;
+    // offset of the resident kernel row (c, ky): full steps first, the tail step last
+    auto woff = [&](int c, int ky) -> uint32_t {
+        return (uint32_t)(c * 3) * ufull + (uint32_t)ky * (p.tail && c == nch - 1 ? utail : ufull);
+    };
+
+    if (warp == TILE_EPI_WARPS && lane == 0) {
+        // ---- halo producer
+        pdl_wait();  // the activations follow the previous kernel
+        bool fine = !p.stall;  // stalled (test hook): nothing is issued, so the issuers' waits run out
+        uint32_t ua = 0, u = 0, q = 0;  // units issued; unit and phase of the next one
+        for (int ts = blockIdx.x; ts < p.ntiles && fine; ts += gridDim.x) {
+            const int xt = ts % p.ntx, rg = (ts / p.ntx) % p.nrg, img = ts / (p.ntx * p.nrg);
+            const int x0 = xt * TW, y0 = rg * R;
+            const int nrows = p.ho - y0 < R ? p.ho - y0 : R;
+            for (int c = 0; c < nch; ++c) {
+                const bool tl = p.tail && c == nch - 1;
+                if (!mbar_wait(emptyA + 8 * u, q ^ 1u, p.err, ERR_PRODUCER)) {
+                    fine = false;
+                    break;
+                }
+                mbar_expect_tx(fullA + 8 * u, (uint32_t)(nrows + 2) * BM * (tl ? 64u : (uint32_t)p.rb));
+                const uint32_t dst = smem_u32(sA + u * aunit);
+                for (int i = 0; i < nrows + 2; ++i)
+                    tma_load_4d(tl ? &tmA2 : &tmA, fullA + 8 * u, dst + (uint32_t)i * aslot, c * p.kc, x0 - 1,
+                                y0 - 1 + i, img + p.img_off);
+                ++ua;
+                if (++u == (uint32_t)UA) { u = 0; q ^= 1u; }
+            }
         }
-        if (issued < nunits) {
-            // Error path: let the loads already issued land before the CTA exits.
-            const unsigned long long t0 = global_ns();
-            while (!mbar_try(wfull, 0))
-                if (global_ns() - t0 > WAIT_NS) { atomicCAS(p.err, 0, ERR_DRAIN); break; }
-            for (int u = issued - ru < 0 ? 0 : issued - ru; u < issued; ++u)
-                while (!mbar_try(full0 + 8 * (u % ru), (uint32_t)(u / ru) & 1u))
+        if (!fine) drain_ring(fullA, UA, ua, p.err);  // let the loads already issued land
+    } else if (warp == TILE_EPI_WARPS + 1 && lane == 0) {
+        // ---- weight producer
+        bool fine = !p.stall;
+        if (resident) {
+            // the packed weights are constant: loaded before the previous kernel has finished
+            if (fine) {
+                mbar_expect_tx(wfull, (uint32_t)(9 * (nch - p.tail) * BN * p.rb + (p.tail ? 9 * BN * 64 : 0)));
+                for (int c = 0; c < nch; ++c) {
+                    const bool tl = p.tail && c == nch - 1;
+                    for (int ky = 0; ky < 3; ++ky)
+                        tma_load_3d(tl ? &tmB2 : &tmB, wfull, smem_u32(sW + woff(c, ky)), c * p.kc, 0, 3 * ky);
+                }
+                const unsigned long long t0 = global_ns();
+                while (!mbar_try(wfull, 0))  // before this thread may leave
                     if (global_ns() - t0 > WAIT_NS) { atomicCAS(p.err, 0, ERR_DRAIN); break; }
-        }
-    } else if (warp == 5 && lane == 0) {
-        // ---- MMA issuer
-        const uint32_t idesc = F8 ? idesc_e4m3(BM, BN) : (p.f16 ? idesc_f16(BM, BN) : idesc_bf16(BM, BN));
-        bool fine = mbar_wait(wfull, 0, p.err, ERR_MMA);
-        for (int r = 0; r < nrows && fine; ++r) {
-            const int b = r & 1;
-            // accumulator b was last drained for row r - 2
-            if (r >= 2 && !mbar_wait(acce0 + 8 * b, (uint32_t)((r >> 1) - 1) & 1u, p.err, ERR_MMA)) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t acc = tmem + (uint32_t)b * ACC_COLS;
-            for (int ky = 0; ky < 3 && fine; ++ky) {
-                for (int ch = 0; ch < nch; ++ch) {
-                    const int u = (r + ky) * nch + ch, s = u % ru;
-                    if (!mbar_wait(full0 + 8 * s, (uint32_t)(u / ru) & 1u, p.err, ERR_MMA)) {
-                        fine = false;
-                        break;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t a0 = smem_u32(sA + s * hslot);
-                    for (int kx = 0; kx < 3; ++kx) {
-                        const uint64_t da = sw_desc(a0 + (uint32_t)p.rb * (uint32_t)kx, (uint32_t)p.rb);
-                        const uint64_t db = sw_desc(smem_u32(sW + ((ky * 3 + kx) * nch + ch) * wtile), (uint32_t)p.rb);
-                        for (int kk = 0; kk < p.rb / 32; ++kk)
-                            umma<F8>(acc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
-                                     (ky | ch | kx | kk) != 0 ? 1u : 0u);
+            }
+        } else {
+            uint32_t ub = 0, s = 0, q = 0;
+            for (int ts = blockIdx.x; ts < p.ntiles && fine; ts += gridDim.x) {
+                for (int c = 0; c < nch && fine; ++c) {
+                    const bool tl = p.tail && c == nch - 1;
+                    const uint32_t tx = 3u * BN * (tl ? 64u : (uint32_t)p.rb);
+                    for (int ky = 0; ky < 3; ++ky) {
+                        if (!mbar_wait(emptyB + 8 * s, q ^ 1u, p.err, ERR_PRODUCER)) {
+                            fine = false;
+                            break;
+                        }
+                        mbar_expect_tx(fullB + 8 * s, tx);
+                        tma_load_3d(tl ? &tmB2 : &tmB, fullB + 8 * s, smem_u32(sW + s * ufull), c * p.kc, 0, 3 * ky);
+                        ++ub;
+                        if (++s == (uint32_t)SB) { s = 0; q ^= 1u; }
                     }
                 }
             }
-            if (!fine) break;
-            for (int ch = 0; ch < nch; ++ch) umma_commit(empty0 + 8 * ((r * nch + ch) % ru));  // input row r is done
-            umma_commit(accf0 + 8 * b);
+            if (!fine) drain_ring(fullB, SB, ub, p.err);
         }
-    } else if (warp < 4) {
-        // ---- epilogue (thread r of warps 0-3 owns accumulator row r = pixel x0 + r)
-        for (int r = 0; r < nrows; ++r) {
-            const int b = r & 1;
+    } else if (warp >= TILE_EPI_WARPS + 2 && warp < TILE_EPI_WARPS + 2 + NI && lane == 0) {
+        // ---- MMA issuer j
+        const int j = warp - (TILE_EPI_WARPS + 2);
+        const uint32_t idesc = F8 ? idesc_e4m3(BM, BN) : (p.f16 ? idesc_f16(BM, BN) : idesc_bf16(BM, BN));
+        const uint32_t acc_step = (uint32_t)p.acc_cols, unit16 = ufull >> 4;
+        bool fine = !resident || mbar_wait(wfull, 0, p.err, ERR_MMA);
+        uint32_t ua = 0, qa = 0;  // halo ring: unit and phase of the next step
+        uint32_t sb = 0, qb = 0;  // weight ring
+        int k = 0;
+        for (int ts = blockIdx.x; ts < p.ntiles && fine; ts += gridDim.x, ++k) {
+            const int b = k & 1, use = k >> 1;
+            if (use >= 1) {
+                if (!mbar_wait(acce0 + 8 * b, (uint32_t)(use - 1) & 1u, p.err, ERR_MMA)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");  // the epilogue's TMEM reads are done
+            }
+            const int y0 = ((ts / p.ntx) % p.nrg) * R;
+            const int nrows = p.ho - y0 < R ? p.ho - y0 : R;
+            const int nmine = (nrows - j + NI - 1) / NI;  // rows j, j + NI, ... below nrows
+            const uint32_t acc0 = tmem + (uint32_t)(b * R + j) * acc_step;
+            for (int c = 0; c < nch && fine; ++c) {
+                const bool tl = p.tail && c == nch - 1;
+                const uint32_t rbc = tl ? 64u : (uint32_t)p.rb;
+                if (!mbar_wait(fullA + 8 * ua, qa, p.err, ERR_MMA)) { fine = false; break; }
+                const uint64_t dA0 = sw_desc(smem_u32(sA + ua * aunit), rbc), dW0 = sw_desc(smem_u32(sW), rbc);
+                const uint32_t sh = rbc >> 4;                    // one pixel row of a halo slot, 16-byte units
+                const uint32_t slot16 = aslot >> 4;
+                const uint32_t tap16 = (uint32_t)BN * rbc >> 4;  // one tap of a weight row
+                for (int ky = 0; ky < 3 && fine; ++ky) {
+                    uint64_t dB;
+                    if (resident) {
+                        dB = dW0 + (uint64_t)(woff(c, ky) >> 4);
+                    } else {
+                        if (!mbar_wait(fullB + 8 * sb, qb, p.err, ERR_MMA)) { fine = false; break; }
+                        dB = dW0 + (uint64_t)(sb * unit16);
+                    }
+                    // this issuer's rows r = j + m NI read halo row r + ky of the unit
+                    uint64_t dA[MR];
+#pragma unroll
+                    for (int m = 0; m < MR; ++m) dA[m] = dA0 + (uint64_t)((uint32_t)(j + m * NI + ky) * slot16);
+                    for (int kx = 0; kx < 3; ++kx) {
+                        const uint32_t f = (c | ky | kx) != 0 ? 1u : 0u;
+                        const uint64_t db = dB + (uint64_t)(kx * tap16);
+                        if (rbc == 128u)
+                            tap_mmas<F8, MR, 4>(acc0, NI * acc_step, dA, sh * (uint32_t)kx, db, idesc, nmine, f);
+                        else if (rbc == 64u)
+                            tap_mmas<F8, MR, 2>(acc0, NI * acc_step, dA, sh * (uint32_t)kx, db, idesc, nmine, f);
+                        else
+                            tap_mmas<F8, MR, 1>(acc0, NI * acc_step, dA, sh * (uint32_t)kx, db, idesc, nmine, f);
+                    }
+                    if (!resident) {
+                        umma_commit(emptyB + 8 * sb);
+                        if (++sb == (uint32_t)SB) { sb = 0; qb ^= 1u; }
+                    }
+                }
+                if (!fine) break;
+                umma_commit(emptyA + 8 * ua);  // the step's halo rows are read
+                if (++ua == (uint32_t)UA) { ua = 0; qa ^= 1u; }
+            }
+            if (fine) umma_commit(accf0 + 8 * b);
+        }
+        // every MMA this issuer issued has completed once its `done` fires
+        umma_commit(done0 + 8 * j);
+        const unsigned long long t0 = global_ns();
+        while (!mbar_try(done0 + 8 * j, 0))
+            if (global_ns() - t0 > WAIT_NS) { atomicCAS(p.err, 0, ERR_DRAIN); break; }
+    } else if (warp < TILE_EPI_WARPS) {
+        // ---- epilogue
+        pdl_wait();  // the outputs may still be read by the previous kernel
+        const int q = warp & 3;
+        int k = 0;
+        for (int ts = blockIdx.x; ts < p.ntiles; ts += gridDim.x, ++k) {
+            const int b = k & 1, use = k >> 1;
+            // the issuers hand a set over only when all of their MMAs were issued
             int ok = 1;
-            if (lane == 0) ok = mbar_wait(accf0 + 8 * b, (uint32_t)(r >> 1) & 1u, p.err, ERR_EPILOGUE) &&
-                                *(volatile int *)p.err == 0;
+            if (lane == 0) ok = mbar_wait(accf0 + 8 * b, (uint32_t)use & 1u, p.err, ERR_EPILOGUE);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            conv_epilogue<BN, HEAD, F8>(tmem + (uint32_t)b * ACC_COLS, p, warp, lane, x0, y0 + r, img);
+            const int xt = ts % p.ntx, rg = (ts / p.ntx) % p.nrg, img = ts / (p.ntx * p.nrg);
+            const int y0 = rg * R, nrows = p.ho - y0 < R ? p.ho - y0 : R;
+            const uint32_t acc0 = tmem + (uint32_t)(b * R) * (uint32_t)p.acc_cols;
+            for (int r = warp >> 2; r < nrows; r += TILE_EPI_WARPS / 4)
+                conv_epilogue<BN, HEAD, F8>(acc0 + (uint32_t)r * (uint32_t)p.acc_cols, p, q, lane, xt * TW, y0 + r, img,
+                                            TW);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(acce0 + 8 * b);
@@ -554,11 +556,12 @@ conv_tc_rows_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)p.tmem_cols)
+                     : "memory");
     }
 }
 
-// Test hook: stride-1 conv launches still to stall (tc_test_stall_next_convs).
+// Test hook: stride-1 3x3 conv launches still to stall (tc_test_stall_next_convs).
 std::atomic<int> g_stall_next{0};
 
 // 1 if this launch takes one of the armed stalls: never while st is being captured into a
@@ -577,51 +580,109 @@ int take_stall(cudaStream_t st) {
     return k > 0 ? 1 : 0;
 }
 
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int d = 0;
+        if (cudaGetDevice(&d) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess) {
+            cudaGetLastError();
+            n = 148;
+        }
+    }
+    return n;
+}
+
+// Tiling of conv_tc_tiles_kernel for a planned stride-1 3x3 layer over n_img images:
+// rows per tile, halo units (at least two, so the next channel step loads under the current
+// one), resident or streamed weights.  Returns the dynamic shared memory it needs.
+size_t plan_tiles(const TcConvPlan &plan, int bn, int n_img, TcLaunch &lp, int *grid) {
+    constexpr uint32_t SMEM_MAX = 232448;                  // opt-in maximum per CTA
+    const uint32_t budget = SMEM_MAX - 1024 - 256 - 512;    // alignment slack, slot overrun guard, barriers
+    const int acc = tmem_cols_for(bn);
+    const uint32_t aslot = (uint32_t)BM * (uint32_t)plan.rb;
+    const uint32_t ufull = round1k(3u * (uint32_t)bn * (uint32_t)plan.rb), utail = round1k(3u * (uint32_t)bn * 64u);
+    const int tail = plan.tail ? 1 : 0;
+    const uint32_t wres = 3u * (uint32_t)(plan.nch - tail) * ufull + (tail ? 3u * utail : 0u);
+    const int ntx = (plan.wo + TW - 1) / TW;
+    const int nsm = sm_count();
+    // rows per tile: as many as two accumulator sets of TMEM hold, fewer where the tiles
+    // would not cover the SMs or two halo units would not fit beside the weights
+    int R = 512 / (2 * acc);
+    if (R > TILE_RMAX) R = TILE_RMAX;
+    while (R > 1 && (long)ntx * ((plan.ho + R - 1) / R) * n_img < nsm) R /= 2;
+    int SB = 0;
+    uint32_t wbytes = 0, aunit = 0;
+    for (;; R /= 2) {
+        aunit = (uint32_t)(R + 2) * aslot;
+        if (wres + 2 * aunit <= budget) { SB = 0; wbytes = wres; break; }
+        if (3 * ufull + 2 * aunit <= budget) { SB = 3; wbytes = 3 * ufull; break; }
+        if (2 * ufull + 2 * aunit <= budget) { SB = 2; wbytes = 2 * ufull; break; }
+        if (R == 1) return 0;  // no tiling fits
+    }
+    int UA = (int)((budget - wbytes) / aunit);
+    if (UA > 4) UA = 4;
+    lp.R = R;
+    lp.acc_cols = acc;
+    int cols = 32;
+    while (cols < 2 * R * acc) cols *= 2;
+    lp.tmem_cols = cols;
+    lp.sa = UA;
+    lp.sb = SB;
+    lp.tail = tail;
+    lp.ntx = ntx;
+    lp.nrg = (plan.ho + R - 1) / R;
+    lp.ntiles = ntx * lp.nrg * n_img;
+    const size_t smem = 1024 + wbytes + (size_t)UA * aunit + 256 + 512;
+    // resident CTAs per SM: TMEM columns and the SM's 228 KB of shared memory (1 KB of it
+    // reserved per CTA)
+    int per_sm = 512 / cols;
+    const int by_smem = (int)(233472 / (smem + 1024));
+    if (by_smem < per_sm) per_sm = by_smem;
+    *grid = lp.ntiles < nsm * per_sm ? lp.ntiles : nsm * per_sm;
+    return smem;
+}
+
+template <int BN, bool HEAD, bool F8, int R>
+cudaError_t launch_tiles(const TcConvPlan &plan, const TcLaunch &lt, int grid, size_t smem, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(conv_tc_tiles_kernel<BN, HEAD, F8, R>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    return launch_pdl(conv_tc_tiles_kernel<BN, HEAD, F8, R>, dim3(grid), dim3(TILE_THREADS), smem, st, plan.tmA, plan.tmB,
+                      plan.tail ? plan.tmA2 : plan.tmA, plan.tail ? plan.tmB2 : plan.tmB, lt);
+}
+
 template <int BN, bool HEAD = false, bool F8 = false>
 cudaError_t launch_bn(const TcConvPlan &plan, const TcLaunch &lp, int n_img, cudaStream_t st) {
-    dim3 grid((plan.wo + BM - 1) / BM, plan.ho, n_img);
-    if constexpr (BN <= 32 && !HEAD) {
-        // the multi-row form pays off where the grid stays large: measured on the 16- and
-        // 32-channel pyramid levels (4 rows per CTA beat 8 and 2); the flow heads (two K
-        // steps, one CTA per SM) and the coarse levels lose with ROWS times fewer CTAs
-        if (plan.stride == 1 && plan.taps == 9 && plan.nch == 1) {
-            const size_t smem = rows_smem_for(BN, plan.rb, 1);
-            static size_t attr_bytes = 0;
-            if (attr_bytes < smem) {
-                cudaError_t e = cudaFuncSetAttribute(conv_tc_rows_kernel<BN, HEAD, F8, 1>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                if (e != cudaSuccess) return e;
-                attr_bytes = smem;
-            }
-            const dim3 rgrid((plan.wo + BM - 1) / BM, (plan.ho + ROWS - 1) / ROWS, n_img);
-            return launch_pdl(conv_tc_rows_kernel<BN, HEAD, F8, 1>, rgrid, dim3(192), smem, st, plan.tmA, plan.tmB, lp);
-        }
-    }
     if (plan.stride == 1 && plan.taps == 9) {
-        static bool attr_set = false;
-        const size_t smem = halo_smem_for(BN);
-        if (!attr_set) {
-            cudaError_t e = cudaFuncSetAttribute(conv_tc_halo_kernel<BN, HEAD, F8>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            attr_set = true;
-        }
         TcLaunch lt = lp;
-        lt.tail = plan.tail ? 1 : 0;
+        int g = 0;
+        const size_t smem = plan_tiles(plan, BN, n_img, lt, &g);
+        if (smem == 0 || lt.sa < 2) return cudaErrorInvalidConfiguration;
         lt.stall = take_stall(st);
-        return launch_pdl(conv_tc_halo_kernel<BN, HEAD, F8>, grid, dim3(128), smem, st, plan.tmA, plan.tmB,
-                          plan.tail ? plan.tmA2 : plan.tmA, plan.tail ? plan.tmB2 : plan.tmB, lt);
-    } else {
-        static size_t attr_bytes = 0;
-        const size_t smem = smem_bytes_for(BN, plan.rb);
-        if (attr_bytes < smem) {
-            cudaError_t e =
-                cudaFuncSetAttribute(conv_tc_kernel<BN, HEAD, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            attr_bytes = smem;
+        constexpr int ACC = tmem_cols_for(BN);
+        switch (lt.R) {
+            case 1: return launch_tiles<BN, HEAD, F8, 1>(plan, lt, g, smem, st);
+            case 2: return launch_tiles<BN, HEAD, F8, 2>(plan, lt, g, smem, st);
+            case 4: if constexpr (ACC <= 64) return launch_tiles<BN, HEAD, F8, 4>(plan, lt, g, smem, st); break;
+            case 8: if constexpr (ACC <= 32) return launch_tiles<BN, HEAD, F8, 8>(plan, lt, g, smem, st); break;
+            default: break;
         }
-        return launch_pdl(conv_tc_kernel<BN, HEAD, F8>, grid, dim3(128), smem, st, plan.tmA, plan.tmB, lp);
+        return cudaErrorInvalidConfiguration;
     }
+    const dim3 grid((plan.wo + BM - 1) / BM, plan.ho, n_img);
+    static size_t attr_bytes = 0;
+    const size_t smem = smem_bytes_for(BN, plan.rb);
+    if (attr_bytes < smem) {
+        cudaError_t e =
+            cudaFuncSetAttribute(conv_tc_kernel<BN, HEAD, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_bytes = smem;
+    }
+    return launch_pdl(conv_tc_kernel<BN, HEAD, F8>, grid, dim3(128), smem, st, plan.tmA, plan.tmB, lp);
 }
 
 }  // namespace
@@ -726,8 +787,8 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
     if (a.stride == 1) {
         const cuuint64_t dims[4] = {(cuuint64_t)a.cin, (cuuint64_t)a.w, (cuuint64_t)a.h, (cuuint64_t)n_in};
         const cuuint64_t strides[3] = {a.in_cs * esz, (cuuint64_t)a.w * a.in_cs * esz, (cuuint64_t)a.h * a.w * a.in_cs * esz};
-        // the 3x3 stride-1 kernel loads halo rows; the pointwise one tiles of BM pixels
-        const cuuint32_t box[4] = {(cuuint32_t)kc, taps == 9 ? HALO_ROWS : (cuuint32_t)BM, 1, 1};
+        // halo rows of the 3x3 kernel and pixel tiles of the pointwise one: BM pixels
+        const cuuint32_t box[4] = {(cuuint32_t)kc, (cuuint32_t)BM, 1, 1};
         r = enc(&plan.tmA, dt, 4, const_cast<void *>(a.in), dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     } else {
@@ -741,7 +802,8 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
     if (r == CUDA_SUCCESS) {
         const cuuint64_t dims[3] = {(cuuint64_t)cinp, (cuuint64_t)bn, (cuuint64_t)taps};
         const cuuint64_t strides[2] = {(cuuint64_t)cinp * esz, (cuuint64_t)bn * cinp * esz};
-        const cuuint32_t box[3] = {(cuuint32_t)kc, (cuuint32_t)bn, 1};
+        // the stride-1 3x3 kernel loads a kernel row (three taps) at a time, the others one tap
+        const cuuint32_t box[3] = {(cuuint32_t)kc, (cuuint32_t)bn, taps == 9 && a.stride == 1 ? 3u : 1u};
         r = enc(&plan.tmB, dt, 3, wdev, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     }
@@ -753,13 +815,13 @@ bool tc_plan_conv(TcConvPlan &plan, const ConvArgs &a, int n_in, const std::vect
     if (r == CUDA_SUCCESS && plan.tail) {
         const cuuint64_t dims[4] = {(cuuint64_t)a.cin, (cuuint64_t)a.w, (cuuint64_t)a.h, (cuuint64_t)n_in};
         const cuuint64_t strides[3] = {a.in_cs * esz, (cuuint64_t)a.w * a.in_cs * esz, (cuuint64_t)a.h * a.w * a.in_cs * esz};
-        const cuuint32_t box[4] = {tail_ch, HALO_ROWS, 1, 1};
+        const cuuint32_t box[4] = {tail_ch, (cuuint32_t)BM, 1, 1};
         r = enc(&plan.tmA2, dt, 4, const_cast<void *>(a.in), dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r == CUDA_SUCCESS) {
             const cuuint64_t wdims[3] = {(cuuint64_t)cinp, (cuuint64_t)bn, (cuuint64_t)taps};
             const cuuint64_t wstrides[2] = {(cuuint64_t)cinp * esz, (cuuint64_t)bn * cinp * esz};
-            const cuuint32_t wbox[3] = {tail_ch, (cuuint32_t)bn, 1};
+            const cuuint32_t wbox[3] = {tail_ch, (cuuint32_t)bn, 3};
             r = enc(&plan.tmB2, dt, 3, wdev, wdims, wstrides, wbox, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         }

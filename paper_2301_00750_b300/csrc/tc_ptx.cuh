@@ -47,19 +47,27 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Waits for the phase of `bar` with the given parity; gives up after WAIT_NS or as soon as
-// another role of this CTA (or another CTA) has recorded an error.
+// A wait that has lasted this long also looks at the device error word (a global load of
+// several hundred cycles, kept off the path of the waits that complete in time).
+constexpr unsigned long long SLOW_WAIT_NS = 100000ull;
+
+// Waits for the phase of `bar` with the given parity; gives up after WAIT_NS, or once the
+// wait has lasted SLOW_WAIT_NS and another role of this CTA (or another CTA) has recorded an
+// error.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, int code) {
     unsigned long long t0 = 0;
     for (uint32_t i = 0;; ++i) {
         if (mbar_try(bar, parity)) return true;
         if ((i & 63) == 63) {
-            if (*(volatile int *)err != 0) return false;
             const unsigned long long t = global_ns();
-            if (t0 == 0) t0 = t;
-            else if (t - t0 > WAIT_NS) {
-                atomicCAS(err, 0, code);
-                return false;
+            if (t0 == 0) {
+                t0 = t;
+            } else if (t - t0 > SLOW_WAIT_NS) {
+                if (*(volatile int *)err != 0) return false;
+                if (t - t0 > WAIT_NS) {
+                    atomicCAS(err, 0, code);
+                    return false;
+                }
             }
         }
     }

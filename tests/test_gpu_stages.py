@@ -85,11 +85,17 @@ CONV_CASES = [
     (2, 3, 130, 216, 128, 1), (1, 8, 8, 48, 48, 1),
     # wide rows: two tiles with a ragged second one, a one-pixel last tile, three K steps
     (1, 20, 300, 128, 128, 1), (2, 9, 480, 120, 96, 1), (1, 6, 257, 64, 128, 1), (1, 3, 192, 192, 128, 1),
-    # one K step and <= 32 outputs at stride 1 run the multi-row kernel (4 rows per CTA):
-    # row tails of 3 and 1, a one-pixel last tile, a 24-channel input, three images
+    # one K step and <= 32 outputs: row tails of 3 and 1, a one-pixel last tile, a
+    # 24-channel input, three images
     (2, 23, 200, 64, 32, 1), (1, 1, 129, 16, 16, 1), (3, 17, 128, 24, 16, 1),
     # a single 120-pixel tile per row over 50 rows and two images, two K steps, 96 outputs
     (2, 50, 120, 128, 96, 1),
+    # enough tiles for the persistent stride-1 kernel to take several rows per tile: 2 rows
+    # of 128 outputs with streamed weights (odd row count: a one-row last group), rows of 64
+    # outputs behind a 32-channel tail step, rows of 32 outputs over three K steps
+    (1, 299, 130, 120, 128, 1), (2, 150, 260, 96, 64, 1), (2, 300, 130, 160, 32, 1),
+    # rows of exactly one and two 126-pixel tiles of that kernel
+    (1, 5, 126, 64, 64, 1), (2, 4, 252, 128, 128, 1),
 ]
 
 
