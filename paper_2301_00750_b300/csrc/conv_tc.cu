@@ -81,7 +81,8 @@ struct TcLaunch {
     int tmem_cols;        // TMEM columns allocated (a power of two >= 2 * R * acc_cols)
     int sa, sb;           // halo ring units (a channel step's R + 2 rows each); weight ring slots, a
                           // kernel row each (0: resident weights)
-    int ntx, nrg, ntiles; // tiles: 128-pixel column tiles x groups of R rows x images
+    int ntx, nrg, ntiles; // tiles: 126-pixel column tiles x groups of R rows x images
+    int tailunit;         // halo unit 1 holds the 64-byte tail step (two channel steps per tile)
 };
 
 // Epilogue shared by the conv kernels: thread r of the CTA owns accumulator row r, i.e.
@@ -358,11 +359,17 @@ conv_tc_tiles_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
     const uint32_t ufull = round1k(3u * BN * (uint32_t)p.rb), utail = round1k(3u * BN * 64u);
     const uint32_t wbytes = resident ? 3u * (uint32_t)(nch - p.tail) * ufull + (p.tail ? 3u * utail : 0u)
                                      : (uint32_t)SB * ufull;
+    // halo units: (R + 2) slots of a channel step; with p.tailunit (two steps per tile, the
+    // second a 64-byte tail) unit 0 always holds the full step and unit 1 the tail step, in
+    // slots of their own widths
     const uint32_t aslot = (uint32_t)BM * (uint32_t)p.rb, aunit = (uint32_t)(R + 2) * aslot;
+    const uint32_t aslot_t = p.tailunit ? (uint32_t)BM * 64u : aslot;
+    auto unit_base = [&](uint32_t u) -> uint32_t { return p.tailunit ? (u ? aunit : 0u) : u * aunit; };
+    const uint32_t abytes = p.tailunit ? aunit + (uint32_t)(R + 2) * aslot_t : (uint32_t)UA * aunit;
     uint8_t *sW = smem;
     uint8_t *sA = smem + wbytes;
     // 256 bytes after the halo ring: the two rows past a slot that outputs 126, 127 read
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sA + (size_t)UA * aunit + 256);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sA + abytes + 256);
     const uint32_t fullA = smem_u32(bars), emptyA = fullA + 8 * UA;
     const uint32_t fullB = emptyA + 8 * UA, emptyB = fullB + 8 * SB;
     const uint32_t wfull = emptyB + 8 * SB, accf0 = wfull + 8, acce0 = accf0 + 16, done0 = acce0 + 16;
@@ -418,9 +425,9 @@ conv_tc_tiles_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                     break;
                 }
                 mbar_expect_tx(fullA + 8 * u, (uint32_t)(nrows + 2) * BM * (tl ? 64u : (uint32_t)p.rb));
-                const uint32_t dst = smem_u32(sA + u * aunit);
+                const uint32_t dst = smem_u32(sA + unit_base(u)), pitch = p.tailunit && u ? aslot_t : aslot;
                 for (int i = 0; i < nrows + 2; ++i)
-                    tma_load_4d(tl ? &tmA2 : &tmA, fullA + 8 * u, dst + (uint32_t)i * aslot, c * p.kc, x0 - 1,
+                    tma_load_4d(tl ? &tmA2 : &tmA, fullA + 8 * u, dst + (uint32_t)i * pitch, c * p.kc, x0 - 1,
                                 y0 - 1 + i, img + p.img_off);
                 ++ua;
                 if (++u == (uint32_t)UA) { u = 0; q ^= 1u; }
@@ -486,9 +493,9 @@ conv_tc_tiles_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                 const bool tl = p.tail && c == nch - 1;
                 const uint32_t rbc = tl ? 64u : (uint32_t)p.rb;
                 if (!mbar_wait(fullA + 8 * ua, qa, p.err, ERR_MMA)) { fine = false; break; }
-                const uint64_t dA0 = sw_desc(smem_u32(sA + ua * aunit), rbc), dW0 = sw_desc(smem_u32(sW), rbc);
+                const uint64_t dA0 = sw_desc(smem_u32(sA + unit_base(ua)), rbc), dW0 = sw_desc(smem_u32(sW), rbc);
                 const uint32_t sh = rbc >> 4;                    // one pixel row of a halo slot, 16-byte units
-                const uint32_t slot16 = aslot >> 4;
+                const uint32_t slot16 = (p.tailunit && ua ? aslot_t : aslot) >> 4;
                 const uint32_t tap16 = (uint32_t)BN * rbc >> 4;  // one tap of a weight row
                 for (int ky = 0; ky < 3 && fine; ++ky) {
                     uint64_t dB;
@@ -610,17 +617,22 @@ size_t plan_tiles(const TcConvPlan &plan, int bn, int n_img, TcLaunch &lp, int *
     int R = 512 / (2 * acc);
     if (R > TILE_RMAX) R = TILE_RMAX;
     while (R > 1 && (long)ntx * ((plan.ho + R - 1) / R) * n_img < nsm) R /= 2;
+    // two channel steps, the second a 64-byte tail: the two halo units alternate between
+    // them, so unit 1 takes tail-width slots
+    const bool split = tail && plan.nch == 2 && plan.rb == 128;
     int SB = 0;
-    uint32_t wbytes = 0, aunit = 0;
+    uint32_t wbytes = 0, aunit = 0, a2 = 0;  // a2: bytes of two halo units
     for (;; R /= 2) {
         aunit = (uint32_t)(R + 2) * aslot;
-        if (wres + 2 * aunit <= budget) { SB = 0; wbytes = wres; break; }
-        if (3 * ufull + 2 * aunit <= budget) { SB = 3; wbytes = 3 * ufull; break; }
-        if (2 * ufull + 2 * aunit <= budget) { SB = 2; wbytes = 2 * ufull; break; }
+        a2 = split ? aunit + (uint32_t)(R + 2) * BM * 64u : 2 * aunit;
+        if (wres + a2 <= budget) { SB = 0; wbytes = wres; break; }
+        if (3 * ufull + a2 <= budget) { SB = 3; wbytes = 3 * ufull; break; }
+        if (2 * ufull + a2 <= budget) { SB = 2; wbytes = 2 * ufull; break; }
         if (R == 1) return 0;  // no tiling fits
     }
-    int UA = (int)((budget - wbytes) / aunit);
+    int UA = split ? 2 : (int)((budget - wbytes) / aunit);
     if (UA > 4) UA = 4;
+    lp.tailunit = split ? 1 : 0;
     lp.R = R;
     lp.acc_cols = acc;
     int cols = 32;
@@ -632,7 +644,7 @@ size_t plan_tiles(const TcConvPlan &plan, int bn, int n_img, TcLaunch &lp, int *
     lp.ntx = ntx;
     lp.nrg = (plan.ho + R - 1) / R;
     lp.ntiles = ntx * lp.nrg * n_img;
-    const size_t smem = 1024 + wbytes + (size_t)UA * aunit + 256 + 512;
+    const size_t smem = 1024 + wbytes + (split ? (size_t)a2 : (size_t)UA * aunit) + 256 + 512;
     // resident CTAs per SM: TMEM columns and the SM's 228 KB of shared memory (1 KB of it
     // reserved per CTA)
     int per_sm = 512 / cols;

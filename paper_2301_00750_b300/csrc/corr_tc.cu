@@ -27,30 +27,9 @@ using namespace ptx;
 constexpr int BX = 16, BY = 8;  // output pixel block: M = 128 rows, row m = py * 16 + px
 constexpr int BK = 64;          // channels per TMA step (128 B of bf16)
 constexpr int MAX_NCH = 2;      // channels <= 128
-constexpr uint32_t A_BYTES = BX * BY * BK * 2;
+constexpr int TILE_CORR_EPI = 8;  // epilogue warps: two halves of the displacements per pixel
 
-
-enum : int { ERR_CORR_MMA = 5, ERR_CORR_EPILOGUE = 6, ERR_CORR_DRAIN = 7 };
-
-template <int R>
-struct Geo {
-    static constexpr int HX = BX + 2 * R, HY = BY + 2 * R, NPOS = HX * HY;
-    static constexpr int NP = (NPOS + 31) / 32 * 32, NH = NP / 2;
-    static constexpr uint32_t B_BYTES = (uint32_t)NP * BK * 2;
-    static constexpr int ND = (2 * R + 1) * (2 * R + 1);
-    static constexpr uint32_t TMEM_COLS = NP <= 256 ? 256 : 512;
-    // epilogue: every thread stages the WROWS halo rows its warp reads (2 pixel rows + 2R)
-    static constexpr int WROWS = 2 + 2 * R, WCOLS = WROWS * HX;         // 240 for R = 4
-    static constexpr int WLOAD = (WCOLS + 15) / 16 * 16;                // tcgen05.ld x16 granularity
-    // slice pitch: a whole number of 16-byte units, odd, so the 16-byte stores of 8
-    // consecutive threads hit distinct banks
-    static constexpr int SSTRIDE = (WLOAD / 4) % 2 ? WLOAD : WLOAD + 4;
-    static constexpr size_t OPERANDS = (size_t)MAX_NCH * (A_BYTES + B_BYTES);
-    static constexpr size_t SLICES = (size_t)128 * SSTRIDE * 4;
-    static constexpr size_t SMEM = (OPERANDS > SLICES ? OPERANDS : SLICES) + 1024 + 256;
-    static_assert(NH % 16 == 0 && NH <= 256, "MMA N");
-    static_assert(2 * (BY / 2 - 1) * HX + WLOAD <= (int)TMEM_COLS, "epilogue column window inside TMEM");
-};
+enum : int { ERR_CORR_MMA = 5, ERR_CORR_EPILOGUE = 6, ERR_CORR_DRAIN = 7, ERR_CORR_PRODUCER = 8 };
 
 struct CorrTcLaunch {
     int h, w, nch;
@@ -71,31 +50,230 @@ struct CorrTcLaunch {
     // self copy reads fs[0] + (q + d pair_lanes) fs_img_bytes.
     int pair_lanes, s0, o0, oq, od;
     size_t fs_img_bytes;
+    int nb;       // batch entries (blocks run over nbx x nby x nb)
+    int nstages;  // operand stages in shared memory
 };
 
+template <int R>
+struct Geo {
+    static constexpr int HX = BX + 2 * R, HY = BY + 2 * R, NPOS = HX * HY;
+    static constexpr int NP = (NPOS + 31) / 32 * 32, NH = NP / 2;
+    static constexpr uint32_t TMEM_COLS = NP <= 256 ? 256 : 512;
+    // epilogue: per displacement row dy a warp reads the two halo rows of its two pixel rows
+    static constexpr int WIN = (2 * HX + 15) / 16 * 16;  // columns loaded (tcgen05.ld x16 granularity)
+    // per-thread staging slice: a whole number of 16-byte units, odd, so the 16-byte stores
+    // of 8 consecutive threads hit distinct banks
+    static constexpr int SSTRIDE = (WIN / 4) % 2 ? WIN : WIN + 4;
+    static constexpr size_t SLICES = (size_t)TILE_CORR_EPI * 32 * SSTRIDE * 4;
+    static_assert(NH % 16 == 0 && NH <= 256, "MMA N");
+    static_assert(2 * (BY / 2 - 1) + 2 * R + 2 <= HY && (HY - 2) * HX + WIN <= (int)TMEM_COLS,
+                  "epilogue column window inside TMEM");
+};
+
+// Operand bytes of one block: per channel step the self block [8][16][rb] and the other
+// map's halo [HY][HX][rb], each rounded to the 1024-byte swizzle atom.
+__host__ __device__ constexpr uint32_t corr_a_bytes(int rb) { return (uint32_t)(BX * BY * rb + 1023) / 1024u * 1024u; }
+__host__ __device__ constexpr uint32_t corr_b_bytes(int np, int rb) { return (uint32_t)(np * rb + 1023) / 1024u * 1024u; }
+
+// Displacements k in [K0, K1) of one pixel (k = dy (2R+1) + dx): the epilogue half G of the
+// CTA computes K0 = 0 .. KS or KS .. ND, split on a 16-byte boundary of the stored vector.
+template <int R, bool F8, int G>
+struct Half {
+    static constexpr int ND = (2 * R + 1) * (2 * R + 1);
+    static constexpr int VEC = F8 ? 16 : 8;
+    static constexpr int KS = ND / 2 / VEC * VEC;
+    static constexpr int K0 = G == 0 ? 0 : KS, K1 = G == 0 ? KS : ND;
+    static constexpr int N = K1 - K0;
+    static constexpr int DY0 = K0 / (2 * R + 1), DY1 = N > 0 ? (K1 - 1) / (2 * R + 1) : -1;
+    static_assert(N == 0 || (DY0 <= DY1 && DY1 <= 2 * R), "displacement rows of the half");
+    // whole-window staging: halo rows 2q + DY0 .. 2q + DY1 + 1 of warp quarter q
+    static constexpr int WROWS = N > 0 ? DY1 - DY0 + 2 : 0;
+    static constexpr int WLOAD = (WROWS * (BX + 2 * R) + 15) / 16 * 16;
+    static_assert(WROWS <= 2 * R + 3, "window rows");
+};
+
+// Whole-window staging (the epilogue copies every halo row its half reads, then frees TMEM
+// for the next block): slices of the larger of the two halves' windows, pitch as above.
 template <int R, bool F8>
-__global__ void __launch_bounds__(128, 1)
+struct Whole {
+    static constexpr int W0 = Half<R, F8, 0>::WLOAD, W1 = Half<R, F8, 1>::WLOAD;
+    static constexpr int SSW0 = W0 > W1 ? W0 : W1;
+    static constexpr int SSW = (SSW0 / 4) % 2 ? SSW0 : SSW0 + 4;
+    static constexpr size_t SLICES = (size_t)TILE_CORR_EPI * 32 * SSW * 4;
+};
+
+// Whole-window staging of half G: the warp's halo rows into the thread's slice (row i of the
+// window at slice + i HX), two 16-column loads per wait.
+template <int R, bool F8, int G>
+__device__ __forceinline__ void corr_stage_window(uint32_t ta, float *slice, int q) {
+    using Gm = Geo<R>;
+    using H = Half<R, F8, G>;
+    static_assert((2 * 3 + H::DY0) * Gm::HX + H::WLOAD <= (int)Gm::TMEM_COLS && H::WLOAD <= Whole<R, F8>::SSW,
+                  "window inside TMEM and the slice");
+    if constexpr (H::N > 0) {
+        const uint32_t col = (uint32_t)((2 * q + H::DY0) * Gm::HX);
+#pragma unroll
+        for (int c0 = 0; c0 < H::WLOAD; c0 += 32) {
+            uint32_t r[32];
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                if (c0 + 16 * k < H::WLOAD) tmem_ld16_nowait(ta + col + (uint32_t)(c0 + 16 * k), r + 16 * k);
+            tmem_wait_ld();
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (c0 + 4 * k < H::WLOAD)
+                    *reinterpret_cast<float4 *>(slice + c0 + 4 * k) = make_float4(
+                        __uint_as_float(r[4 * k]), __uint_as_float(r[4 * k + 1]), __uint_as_float(r[4 * k + 2]),
+                        __uint_as_float(r[4 * k + 3]));
+        }
+    }
+}
+
+// The half's entries of the pixel from its staged window (after corr_stage_window).
+template <int R, bool F8, int G>
+__device__ __forceinline__ void corr_pick_window(const float *slice, int py, int px, float scale,
+                                                 float (&res)[Half<R, F8, G>::N > 0 ? Half<R, F8, G>::N : 1]) {
+    using H = Half<R, F8, G>;
+    constexpr int HX = BX + 2 * R;
+    const int base = (py & 1) * HX + px;
+#pragma unroll
+    for (int dy = H::DY0; dy <= H::DY1; ++dy)
+#pragma unroll
+        for (int dx = 0; dx <= 2 * R; ++dx) {
+            const int kk = dy * (2 * R + 1) + dx;
+            if (kk >= H::K0 && kk < H::K1) {
+                const float v = slice[base + (dy - H::DY0) * HX + dx] * scale;
+                res[kk - H::K0] = v >= 0.f ? v : 0.1f * v;
+            }
+        }
+}
+
+// Store of half G's entries (scaled, LeakyReLU) of pixel pix: 16-byte vectors where the
+// buffer allows, in the features' type.
+template <int R, bool F8, int G>
+__device__ __forceinline__ void corr_store_half(const CorrTcLaunch &p,
+                                                const float (&res)[Half<R, F8, G>::N > 0 ? Half<R, F8, G>::N : 1],
+                                                size_t pix) {
+    using H = Half<R, F8, G>;
+    if constexpr (H::N > 0) {
+        if constexpr (F8) {
+            uint8_t *dst = static_cast<uint8_t *>(p.out) + pix * p.out_cs + H::K0;
+            if (p.vec_out) {
+#pragma unroll
+                for (int k = 0; k + 16 <= H::N; k += 16) {
+                    uint4 v;
+                    v.x = pack_e4m3x4(res[k] * p.q_out, res[k + 1] * p.q_out, res[k + 2] * p.q_out, res[k + 3] * p.q_out);
+                    v.y = pack_e4m3x4(res[k + 4] * p.q_out, res[k + 5] * p.q_out, res[k + 6] * p.q_out, res[k + 7] * p.q_out);
+                    v.z = pack_e4m3x4(res[k + 8] * p.q_out, res[k + 9] * p.q_out, res[k + 10] * p.q_out, res[k + 11] * p.q_out);
+                    v.w = pack_e4m3x4(res[k + 12] * p.q_out, res[k + 13] * p.q_out, res[k + 14] * p.q_out, res[k + 15] * p.q_out);
+                    *reinterpret_cast<uint4 *>(dst + k) = v;
+                }
+#pragma unroll
+                for (int k = H::N / 16 * 16; k < H::N; ++k)
+                    dst[k] = (uint8_t)__nv_cvt_float_to_fp8(res[k] * p.q_out, __NV_SATFINITE, __NV_E4M3);
+            } else {
+#pragma unroll
+                for (int k = 0; k < H::N; ++k)
+                    dst[k] = (uint8_t)__nv_cvt_float_to_fp8(res[k] * p.q_out, __NV_SATFINITE, __NV_E4M3);
+            }
+        } else {
+            uint16_t *dst = static_cast<uint16_t *>(p.out) + pix * p.out_cs + H::K0;  // bf16 or half
+            const bool f16 = p.f16 != 0;
+            if (p.vec_out) {
+#pragma unroll
+                for (int k = 0; k + 8 <= H::N; k += 8) {
+                    uint4 v;
+                    v.x = pack16x2(f16, res[k], res[k + 1]);
+                    v.y = pack16x2(f16, res[k + 2], res[k + 3]);
+                    v.z = pack16x2(f16, res[k + 4], res[k + 5]);
+                    v.w = pack16x2(f16, res[k + 6], res[k + 7]);
+                    *reinterpret_cast<uint4 *>(dst + k) = v;
+                }
+#pragma unroll
+                for (int k = H::N / 8 * 8; k < H::N; ++k) dst[k] = (uint16_t)pack16x2(f16, res[k], 0.f);
+            } else {
+#pragma unroll
+                for (int k = 0; k < H::N; ++k) dst[k] = (uint16_t)pack16x2(f16, res[k], 0.f);
+            }
+        }
+    }
+}
+
+// One epilogue half: for displacement rows DY0 .. DY1, load the warp's two halo rows from
+// TMEM, stage the thread's own values in its slice, pick the pixel's 2R+1 entries, then scale,
+// LeakyReLU and store the half's (k0 .. k1) cost-volume entries of the pixel.
+template <int R, bool F8, int G>
+__device__ __forceinline__ void corr_epilogue_half(const CorrTcLaunch &p, uint32_t ta, float *slice, int py, int px,
+                                                   int q, bool valid, size_t pix) {
+    using Gm = Geo<R>;
+    using H = Half<R, F8, G>;
+    if constexpr (H::N > 0) {
+        float res[H::N > 0 ? H::N : 1];
+        const int base = (py & 1) * Gm::HX + px;
+#pragma unroll
+        for (int dy = H::DY0; dy <= H::DY1; ++dy) {
+            uint32_t r[Gm::WIN];
+            const uint32_t col = (uint32_t)((2 * q + dy) * Gm::HX);
+#pragma unroll
+            for (int k = 0; k < Gm::WIN / 16; ++k) tmem_ld16_nowait(ta + col + (uint32_t)(16 * k), r + 16 * k);
+            tmem_wait_ld();
+#pragma unroll
+            for (int k = 0; k < Gm::WIN / 4; ++k)
+                *reinterpret_cast<float4 *>(slice + 4 * k) = make_float4(
+                    __uint_as_float(r[4 * k]), __uint_as_float(r[4 * k + 1]), __uint_as_float(r[4 * k + 2]),
+                    __uint_as_float(r[4 * k + 3]));
+#pragma unroll
+            for (int dx = 0; dx <= 2 * R; ++dx) {
+                const int kk = dy * (2 * R + 1) + dx;
+                if (kk >= H::K0 && kk < H::K1) {
+                    const float v = slice[base + dx] * p.scale;
+                    res[kk - H::K0] = v >= 0.f ? v : 0.1f * v;
+                }
+            }
+        }
+        if (valid) corr_store_half<R, F8, G>(p, res, pix);
+    }
+}
+
+// Persistent correlation: one CTA per SM walks the blocks blockIdx.x, blockIdx.x + gridDim.x,
+// ...; the operands of the next block load while the current one is in TMEM.
+//   * warp 8, lane 0 (producer): per block, the self block and the other map's halo of every
+//     channel step into an operand stage (NS stages, one barrier each);
+//   * warp 9, lane 0 (MMA issuer): per block, after the epilogue has released TMEM, the MMAs
+//     of both N halves over the channel steps; the commit frees the operand stage and hands
+//     TMEM to the epilogue;
+//   * warps 0-7 (epilogue): warp w reads TMEM lanes 32 (w % 4) .. (pixel rows 2 (w % 4) and
+//     2 (w % 4) + 1 of the block) and computes half of each pixel's displacements (w / 4
+//     selects the half): per displacement row it loads the two halo rows its pixels read,
+//     stages its own values in a per-thread slice and picks each pixel's 2R+1 entries.  Each
+//     half also copies half of the pixel's self features into the estimator input.
+template <int R, bool F8, bool WHOLE>
+__global__ void __launch_bounds__(32 * (TILE_CORR_EPI + 2), 1)
 corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmO, const CorrTcLaunch p) {
     using G = Geo<R>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t *sA = smem;
-    uint8_t *sB = smem + MAX_NCH * A_BYTES;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + MAX_NCH * (A_BYTES + G::B_BYTES));
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + MAX_NCH + 1);
-    const uint32_t full0 = smem_u32(bars), accum = smem_u32(bars + MAX_NCH);
+    const uint32_t abytes = corr_a_bytes(p.rb), bbytes = corr_b_bytes(G::NP, p.rb);
+    const uint32_t stage = (uint32_t)p.nch * (abytes + bbytes);
+    const int NS = p.nstages;
+    float *slices = reinterpret_cast<float *>(smem + (size_t)NS * stage);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(slices) +
+                                                  (WHOLE ? Whole<R, F8>::SLICES : G::SLICES));
+    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * NS;
+    const uint32_t tfull = empty0 + 8 * NS, tempty = tfull + 8, done = tempty + 8;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NS + 3);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int b = blockIdx.z, x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
-    // images of this entry in the self and other tensor maps (selects, not a runtime index
-    // into the argument arrays)
-    const int pq = b >> 1, pd = b & 1;
-    const int img_self = p.pair_lanes ? p.s0 + pq + pd * p.pair_lanes : (b ? p.img_s[1] : p.img_s[0]);
-    const int img_other = p.pair_lanes ? p.o0 + pq * p.oq + pd * p.od : (b ? p.img_o[1] : p.img_o[0]);
-
+    const int nbx = (p.w + BX - 1) / BX, nby = (p.h + BY - 1) / BY;
+    const int nblocks = nbx * nby * p.nb;
     if (threadIdx.x == 0) {
-        for (int ch = 0; ch < MAX_NCH; ++ch) mbar_init(full0 + 8 * ch, 1);
-        mbar_init(accum, 1);
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(tfull, 1);
+        mbar_init(tempty, TILE_CORR_EPI);
+        mbar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -108,145 +286,134 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    pdl_wait();  // every global access below follows the previous kernel
 
-    if (threadIdx.x == 0) {
-        // ---- producer: every channel step at once (the whole block fits in shared memory)
-        for (int ch = 0; ch < p.nch; ++ch) {
-            const uint32_t fb = full0 + 8 * ch;
-            mbar_expect_tx(fb, (uint32_t)(BX * BY + G::NPOS) * (uint32_t)p.rb);
-            const int c0 = ch * (F8 ? p.rb : p.rb / 2);  // a step: rb bytes of e4m3 or bf16 channels
-            tma_load_4d(&tmS, fb, smem_u32(sA + ch * A_BYTES), c0, x0, y0, img_self);
-            tma_load_4d(&tmO, fb, smem_u32(sB + ch * G::B_BYTES), c0, x0 - R, y0 - R, img_other);
-        }
-    } else if (threadIdx.x == 32) {
-        // ---- MMA issuer: D[:, 0:NH] and D[:, NH:NP]
-        const uint32_t idesc = F8 ? idesc_e4m3(128, G::NH) : (p.f16 ? idesc_f16(128, G::NH) : idesc_bf16(128, G::NH));
-        bool ok = true;
-        for (int ch = 0; ch < p.nch && ok; ++ch) {
-            if (!mbar_wait(full0 + 8 * ch, 0, p.err, ERR_CORR_MMA)) {
-                ok = false;
+    // images of block entry z in the self and other tensor maps
+    auto images = [&](int z, int &img_self, int &img_other) {
+        const int pq = z >> 1, pd = z & 1;
+        img_self = p.pair_lanes ? p.s0 + pq + pd * p.pair_lanes : (z ? p.img_s[1] : p.img_s[0]);
+        img_other = p.pair_lanes ? p.o0 + pq * p.oq + pd * p.od : (z ? p.img_o[1] : p.img_o[0]);
+    };
+
+    if (warp == TILE_CORR_EPI && lane == 0) {
+        // ---- producer
+        pdl_wait();  // the features follow the previous kernel
+        uint32_t s = 0, ph = 0, issued = 0;
+        bool fine = true;
+        for (int t = blockIdx.x; t < nblocks && fine; t += gridDim.x) {
+            const int bx = t % nbx, by = (t / nbx) % nby, z = t / (nbx * nby);
+            int is, io;
+            images(z, is, io);
+            if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, p.err, ERR_CORR_PRODUCER)) {
+                fine = false;
                 break;
             }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t rb = (uint32_t)p.rb;
-            const uint64_t da = sw_desc(smem_u32(sA + ch * A_BYTES), rb);
-            const uint64_t db0 = sw_desc(smem_u32(sB + ch * G::B_BYTES), rb);
-            const uint64_t db1 = sw_desc(smem_u32(sB + ch * G::B_BYTES + (uint32_t)G::NH * rb), rb);
-#pragma unroll
-            for (int kk = 0; kk < p.rb / 32; ++kk) {  // 32 bytes of K per MMA
-                const uint32_t acc = (ch | kk) != 0 ? 1u : 0u;
-                umma<F8>(tmem, da + (uint64_t)(kk * 2), db0 + (uint64_t)(kk * 2), idesc, acc);
-                umma<F8>(tmem + (uint32_t)G::NH, da + (uint64_t)(kk * 2), db1 + (uint64_t)(kk * 2), idesc, acc);
-            }
-        }
-        umma_commit(accum);
-        if (!ok) {
-            // Error path: let every issued load land before the CTA exits.
+            const uint32_t fb = full0 + 8 * s;
+            mbar_expect_tx(fb, (uint32_t)p.nch * (uint32_t)(BX * BY + G::NPOS) * (uint32_t)p.rb);
+            const uint32_t dst = smem_u32(smem + s * stage);
             for (int ch = 0; ch < p.nch; ++ch) {
-                const unsigned long long t0 = global_ns();
-                while (!mbar_try(full0 + 8 * ch, 0))
-                    if (global_ns() - t0 > WAIT_NS) {
-                        atomicCAS(p.err, 0, ERR_CORR_DRAIN);
-                        break;
-                    }
+                const int c0 = ch * (F8 ? p.rb : p.rb / 2);  // a step: rb bytes of e4m3 or 16-bit channels
+                const uint32_t d = dst + (uint32_t)ch * (abytes + bbytes);
+                tma_load_4d(&tmS, fb, d, c0, bx * BX, by * BY, is);
+                tma_load_4d(&tmO, fb, d + abytes, c0, bx * BX - R, by * BY - R, io);
             }
+            ++issued;
+            if (++s == (uint32_t)NS) { s = 0; ph ^= 1u; }
         }
-    }
-
-    int ok = 1;
-    if (lane == 0) ok = mbar_wait(accum, 0, p.err, ERR_CORR_EPILOGUE) && *(volatile int *)p.err == 0;
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
-        // The MMAs have completed, so the operand buffers are free: reuse them as per-thread
-        // slices.  Warp w's pixel rows 2w, 2w + 1 read halo rows 2w .. 2w + 2R + 1: those
-        // WCOLS contiguous TMEM columns are staged once, then each pixel picks its (2R+1)^2
-        // entries (row dy + (py & 1), columns px + dx of the staged window).
-        float *slice = reinterpret_cast<float *>(smem) + threadIdx.x * G::SSTRIDE;
-        const int py = threadIdx.x >> 4, px = threadIdx.x & 15;
-        const int y = y0 + py, x = x0 + px;
-        const bool valid = y < p.h && x < p.w;
-        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(2 * warp * G::HX);
-        // up to four 16-column loads in flight per wait; 16-byte shared stores
-#pragma unroll
-        for (int c0 = 0; c0 < G::WLOAD; c0 += 64) {
-            constexpr int MAXK = 4;
-            uint32_t r[16 * MAXK];
-#pragma unroll
-            for (int k = 0; k < MAXK; ++k)
-                if (c0 + 16 * k < G::WLOAD) tmem_ld16_nowait(ta + (uint32_t)(c0 + 16 * k), r + 16 * k);
-            tmem_wait_ld();
-#pragma unroll
-            for (int k = 0; k < MAXK; ++k)
-                if (c0 + 16 * k < G::WLOAD) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        *reinterpret_cast<float4 *>(slice + c0 + 16 * k + 4 * q) =
-                            make_float4(__uint_as_float(r[16 * k + 4 * q]), __uint_as_float(r[16 * k + 4 * q + 1]),
-                                        __uint_as_float(r[16 * k + 4 * q + 2]), __uint_as_float(r[16 * k + 4 * q + 3]));
-                }
+        if (!fine) {
+            // Error path: let the loads already issued land before the CTA exits.
+            const unsigned long long t0 = global_ns();
+            for (uint32_t u = issued > (uint32_t)NS ? issued - NS : 0; u < issued; ++u)
+                while (!mbar_try(full0 + 8 * (u % NS), (u / NS) & 1u))
+                    if (global_ns() - t0 > WAIT_NS) { atomicCAS(p.err, 0, ERR_CORR_DRAIN); break; }
         }
-        const int base = (py & 1) * G::HX + px;
-        float res[G::ND];
-#pragma unroll
-        for (int j = 0; j <= 2 * R; ++j) {
-#pragma unroll
-            for (int i = 0; i <= 2 * R; ++i) {
-                const float v = slice[base + j * G::HX + i] * p.scale;
-                res[j * (2 * R + 1) + i] = v >= 0.f ? v : 0.1f * v;
-            }
-        }
-        if (valid) {
-            const size_t pix = ((size_t)b * p.h + y) * p.w + x;
-            if (F8) {
-                uint8_t *dst = static_cast<uint8_t *>(p.out) + pix * p.out_cs;
-                if (p.vec_out) {
-#pragma unroll
-                    for (int k = 0; k + 16 <= G::ND; k += 16) {
-                        uint4 v;
-                        v.x = pack_e4m3x4(res[k] * p.q_out, res[k + 1] * p.q_out, res[k + 2] * p.q_out, res[k + 3] * p.q_out);
-                        v.y = pack_e4m3x4(res[k + 4] * p.q_out, res[k + 5] * p.q_out, res[k + 6] * p.q_out, res[k + 7] * p.q_out);
-                        v.z = pack_e4m3x4(res[k + 8] * p.q_out, res[k + 9] * p.q_out, res[k + 10] * p.q_out, res[k + 11] * p.q_out);
-                        v.w = pack_e4m3x4(res[k + 12] * p.q_out, res[k + 13] * p.q_out, res[k + 14] * p.q_out, res[k + 15] * p.q_out);
-                        *reinterpret_cast<uint4 *>(dst + k) = v;
-                    }
-#pragma unroll
-                    for (int k = G::ND / 16 * 16; k < G::ND; ++k)
-                        dst[k] = (uint8_t)__nv_cvt_float_to_fp8(res[k] * p.q_out, __NV_SATFINITE, __NV_E4M3);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < G::ND; ++k)
-                        dst[k] = (uint8_t)__nv_cvt_float_to_fp8(res[k] * p.q_out, __NV_SATFINITE, __NV_E4M3);
-                }
-            } else {
-                uint16_t *dst = static_cast<uint16_t *>(p.out) + pix * p.out_cs;  // bf16 or half
-                const bool f16 = p.f16 != 0;
-                if (p.vec_out) {
-#pragma unroll
-                    for (int k = 0; k + 8 <= G::ND; k += 8) {
-                        uint4 v;
-                        v.x = pack16x2(f16, res[k], res[k + 1]);
-                        v.y = pack16x2(f16, res[k + 2], res[k + 3]);
-                        v.z = pack16x2(f16, res[k + 4], res[k + 5]);
-                        v.w = pack16x2(f16, res[k + 6], res[k + 7]);
-                        *reinterpret_cast<uint4 *>(dst + k) = v;
-                    }
-#pragma unroll
-                    for (int k = G::ND / 8 * 8; k < G::ND; ++k) dst[k] = (uint16_t)pack16x2(f16, res[k], 0.f);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < G::ND; ++k) dst[k] = (uint16_t)pack16x2(f16, res[k], 0.f);
+    } else if (warp == TILE_CORR_EPI + 1 && lane == 0) {
+        // ---- MMA issuer: D[:, 0:NH] and D[:, NH:NP] per block
+        const uint32_t idesc = F8 ? idesc_e4m3(128, G::NH) : (p.f16 ? idesc_f16(128, G::NH) : idesc_bf16(128, G::NH));
+        const uint32_t rb = (uint32_t)p.rb;
+        uint32_t s = 0, ph = 0;
+        int k = 0;
+        for (int t = blockIdx.x; t < nblocks; t += gridDim.x, ++k) {
+            if (k >= 1 && !mbar_wait(tempty, (uint32_t)(k - 1) & 1u, p.err, ERR_CORR_MMA)) break;
+            if (!mbar_wait(full0 + 8 * s, ph, p.err, ERR_CORR_MMA)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t base = smem_u32(smem + s * stage);
+            for (int ch = 0; ch < p.nch; ++ch) {
+                const uint32_t a = base + (uint32_t)ch * (abytes + bbytes);
+                const uint64_t da = sw_desc(a, rb), db0 = sw_desc(a + abytes, rb);
+                const uint64_t db1 = sw_desc(a + abytes + (uint32_t)G::NH * rb, rb);
+                for (int kk = 0; kk < p.rb / 32; ++kk) {  // 32 bytes of K per MMA
+                    const uint32_t acc = (ch | kk) != 0 ? 1u : 0u;
+                    umma<F8>(tmem, da + (uint64_t)(kk * 2), db0 + (uint64_t)(kk * 2), idesc, acc);
+                    umma<F8>(tmem + (uint32_t)G::NH, da + (uint64_t)(kk * 2), db1 + (uint64_t)(kk * 2), idesc, acc);
                 }
             }
-            if (p.self_copy) {
-                const size_t esz = F8 ? 1 : 2;
+            umma_commit(empty0 + 8 * s);  // the operand stage is read
+            umma_commit(tfull);           // the block is in TMEM
+            if (++s == (uint32_t)NS) { s = 0; ph ^= 1u; }
+        }
+        umma_commit(done);  // every MMA issued above has completed once it fires
+        const unsigned long long t0 = global_ns();
+        while (!mbar_try(done, 0))
+            if (global_ns() - t0 > WAIT_NS) { atomicCAS(p.err, 0, ERR_CORR_DRAIN); break; }
+    } else if (warp < TILE_CORR_EPI) {
+        // ---- epilogue
+        pdl_wait();  // the outputs may still be read by the previous kernel
+        const int q = warp & 3, half = warp >> 2;
+        const int m = q * 32 + lane, py = m >> 4, px = m & 15;
+        float *slice = slices + (size_t)threadIdx.x * (WHOLE ? Whole<R, F8>::SSW : G::SSTRIDE);
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16);
+        const size_t esz = F8 ? 1 : 2;
+        const int nq = p.self_copy ? (int)(p.c * esz / 16) : 0;  // 16-byte units of a pixel's self features
+        const int q0 = half ? nq / 2 : 0, q1 = half ? nq : nq / 2;  // this half's share of them
+        int k = 0;
+        for (int t = blockIdx.x; t < nblocks; t += gridDim.x, ++k) {
+            const int bx = t % nbx, by = (t / nbx) % nby, z = t / (nbx * nby);
+            const int y = by * BY + py, x = bx * BX + px;
+            const bool valid = y < p.h && x < p.w;
+            const size_t pix = ((size_t)z * p.h + y) * p.w + x;
+            // the pixel's self features, copied into the estimator input below
+            const uint4 *src = nullptr;
+            if (valid && nq > 0) {
+                const int pq = z >> 1, pd = z & 1;
                 const uint8_t *fsb = p.pair_lanes ? static_cast<const uint8_t *>(p.fs[0]) +
                                                         (size_t)(pq + pd * p.pair_lanes) * p.fs_img_bytes
-                                                  : static_cast<const uint8_t *>(b ? p.fs[1] : p.fs[0]);
-                const uint4 *src = reinterpret_cast<const uint4 *>(fsb + ((size_t)y * p.w + x) * p.c * esz);
+                                                  : static_cast<const uint8_t *>(z ? p.fs[1] : p.fs[0]);
+                src = reinterpret_cast<const uint4 *>(fsb + ((size_t)y * p.w + x) * p.c * esz);
+            }
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(tfull, (uint32_t)k & 1u, p.err, ERR_CORR_EPILOGUE);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if constexpr (WHOLE) {
+                // copy the window out of TMEM, hand TMEM to the next block's MMAs, then pick
+                if (half == 0) corr_stage_window<R, F8, 0>(ta, slice, q);
+                else corr_stage_window<R, F8, 1>(ta, slice, q);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty);
+                if (half == 0) {
+                    float res[Half<R, F8, 0>::N > 0 ? Half<R, F8, 0>::N : 1];
+                    corr_pick_window<R, F8, 0>(slice, py, px, p.scale, res);
+                    if (valid) corr_store_half<R, F8, 0>(p, res, pix);
+                } else {
+                    float res[Half<R, F8, 1>::N > 0 ? Half<R, F8, 1>::N : 1];
+                    corr_pick_window<R, F8, 1>(slice, py, px, p.scale, res);
+                    if (valid) corr_store_half<R, F8, 1>(p, res, pix);
+                }
+            } else if (half == 0) {
+                corr_epilogue_half<R, F8, 0>(p, ta, slice, py, px, q, valid, pix);
+            } else {
+                corr_epilogue_half<R, F8, 1>(p, ta, slice, py, px, q, valid, pix);
+            }
+            if (src) {
                 uint4 *cp = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(p.self_copy) + pix * p.out_cs * esz);
-                for (int q = 0; q < (int)(p.c * esz / 16); ++q) cp[q] = __ldg(src + q);
+                for (int qq = q0; qq < q1; ++qq) cp[qq] = __ldg(src + qq);
+            }
+            if constexpr (!WHOLE) {
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty);
             }
         }
     }
@@ -275,18 +442,51 @@ bool encode_features(CUtensorMap *map, const void *base, int n, int cs, int h, i
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int R, bool F8>
-cudaError_t launch_r(const CorrTcPlan &plan, const CorrTcLaunch &lp, int nb, cudaStream_t st) {
-    using G = Geo<R>;
+int corr_sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int d = 0;
+        if (cudaGetDevice(&d) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess) {
+            cudaGetLastError();
+            n = 148;
+        }
+    }
+    return n;
+}
+
+template <int R, bool F8, bool WHOLE>
+cudaError_t launch_rw(const CorrTcPlan &plan, const CorrTcLaunch &lp, int grid, size_t smem, cudaStream_t st) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e =
-            cudaFuncSetAttribute(corr_tc_kernel<R, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+            cudaFuncSetAttribute(corr_tc_kernel<R, F8, WHOLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    dim3 grid((plan.w + BX - 1) / BX, (plan.h + BY - 1) / BY, nb);
-    return launch_pdl(corr_tc_kernel<R, F8>, grid, dim3(128), G::SMEM, st, plan.tmS, plan.tmO, lp);
+    return launch_pdl(corr_tc_kernel<R, F8, WHOLE>, dim3(grid), dim3(32 * (TILE_CORR_EPI + 2)), smem, st, plan.tmS,
+                      plan.tmO, lp);
+}
+
+// Whole-window staging where its slices fit beside one operand stage (the narrow levels),
+// else staging per displacement row; as many operand stages as fit, up to four.
+template <int R, bool F8>
+cudaError_t launch_r(const CorrTcPlan &plan, const CorrTcLaunch &lp0, int nb, cudaStream_t st) {
+    using G = Geo<R>;
+    CorrTcLaunch lp = lp0;
+    lp.nb = nb;
+    const size_t budget = 232448 - 1024 - 256;
+    const size_t stage = (size_t)plan.nch * (corr_a_bytes(plan.rb) + corr_b_bytes(G::NP, plan.rb));
+    const bool whole = stage + Whole<R, F8>::SLICES <= budget;
+    const size_t slices = whole ? Whole<R, F8>::SLICES : G::SLICES;
+    int ns = stage + slices <= budget ? (int)((budget - slices) / stage) : 0;
+    if (ns > 4) ns = 4;
+    if (ns < 1) return cudaErrorInvalidConfiguration;
+    lp.nstages = ns;
+    const long nblocks = (long)((plan.w + BX - 1) / BX) * ((plan.h + BY - 1) / BY) * nb;
+    const int nsm = corr_sm_count();
+    const int grid = nblocks < nsm ? (int)nblocks : nsm;
+    const size_t smem = 1024 + (size_t)ns * stage + slices + 256;
+    return whole ? launch_rw<R, F8, true>(plan, lp, grid, smem, st) : launch_rw<R, F8, false>(plan, lp, grid, smem, st);
 }
 
 }  // namespace
