@@ -47,6 +47,9 @@ SOLVER_FLOPS_PER_PX_ITER = 9  # per channel: neighbour sum (3 adds) and 3 FMAs
 WIDTH, HEIGHT = 1920, 1080
 SPEC = dict(chans=(16, 32, 64, 96, 128), radius=4)
 N_FRAMES = 8
+# DRAM read + write bytes of the FP16 estimator convs (conv1-conv4, levels 5-2, both flow
+# directions) for one 1080p frame, from an ncu capture of the current persistent conv kernel.
+ESTIMATOR_DRAM_BYTES_PER_FRAME = 661.6e6
 # Peak of plain float32 FMA issue: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz.
 FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
@@ -557,6 +560,14 @@ def run_ours(args):
     else:
         peak_source = "of measured HBM copy (MEASURED_PEAKS.json)"
     per = sorted(seq["per_frame_ms"])
+    # DRAM bytes of the dominant class per frame, from one ncu capture of the current kernels
+    # (cold reads, writes partly still in L2); known for the default FP16 workload only
+    traffic, traffic_note = None, "no ncu capture of this configuration"
+    if (dom == "estimator_conv" and args.precision == "fp16" and args.flow_downscale == 1 and
+            args.solver_iters == 0 and args.latency == 0):
+        traffic = ESTIMATOR_DRAM_BYTES_PER_FRAME
+        traffic_note = ("conv1-conv4 of levels 5-2, both directions, one frame: dram__bytes_read.sum + "
+                        "dram__bytes_write.sum over the 16 launches (ncu capture of the current kernels)")
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": steps, "warmup": args.warmup, "ms_per_step": round(total_s * 1e3 / steps, 4),
@@ -580,8 +591,8 @@ def run_ours(args):
         "stage_ms_per_frame": {k: round(v[0] / steps, 4) for k, v in p.items() if v[1]},
         "roofline": {"kernel": dom, "bound": bound, "achieved": round(achieved, 2), "peak": peak, "unit": unit,
                      "frac": round(achieved / peak, 4) if peak else None,
-                     "traffic": None,
-                     "traffic_note": "no ncu capture of the current kernels yet",
+                     "traffic": traffic,
+                     "traffic_note": traffic_note,
                      "peak_source": peak_source},
         "gpu_launches": main["launches"],
         "clocks": clk,

@@ -129,23 +129,55 @@ __device__ __forceinline__ void corr_stage_window(uint32_t ta, float *slice, int
     }
 }
 
-// The half's entries of the pixel from its staged window (after corr_stage_window).
+// The half's entries of the pixel from its staged window (after corr_stage_window), stored
+// as they are computed, a 16-byte vector (8 16-bit or 16 e4m3 values) at a time, so only one
+// vector's values are live.
 template <int R, bool F8, int G>
-__device__ __forceinline__ void corr_pick_window(const float *slice, int py, int px, float scale,
-                                                 float (&res)[Half<R, F8, G>::N > 0 ? Half<R, F8, G>::N : 1]) {
+__device__ __forceinline__ void corr_pick_store_window(const CorrTcLaunch &p, const float *slice, int py, int px,
+                                                       bool valid, size_t pix) {
     using H = Half<R, F8, G>;
-    constexpr int HX = BX + 2 * R;
-    const int base = (py & 1) * HX + px;
+    constexpr int HX = BX + 2 * R, W = 2 * R + 1, VEC = H::VEC;
+    if constexpr (H::N > 0) {
+        const int base = (py & 1) * HX + px;
+        const bool f16 = p.f16 != 0;
+        auto value = [&](int kk) -> float {  // entry kk of the pixel (LeakyReLU of the scaled mean)
+            const int dy = kk / W, dx = kk - dy * W;
+            const float v = slice[base + (dy - H::DY0) * HX + dx] * p.scale;
+            return v >= 0.f ? v : 0.1f * v;
+        };
+        uint8_t *dst8 = static_cast<uint8_t *>(p.out) + pix * p.out_cs * (F8 ? 1 : 2) + (size_t)H::K0 * (F8 ? 1 : 2);
 #pragma unroll
-    for (int dy = H::DY0; dy <= H::DY1; ++dy)
+        for (int k0 = H::K0; k0 < H::K1; k0 += VEC) {
+            if (k0 + VEC <= H::K1 && p.vec_out) {
+                float v[VEC];
 #pragma unroll
-        for (int dx = 0; dx <= 2 * R; ++dx) {
-            const int kk = dy * (2 * R + 1) + dx;
-            if (kk >= H::K0 && kk < H::K1) {
-                const float v = slice[base + (dy - H::DY0) * HX + dx] * scale;
-                res[kk - H::K0] = v >= 0.f ? v : 0.1f * v;
+                for (int j = 0; j < VEC; ++j) v[j] = value(k0 + j);
+                uint4 o;
+                if constexpr (F8) {
+                    o.x = pack_e4m3x4(v[0] * p.q_out, v[1] * p.q_out, v[2] * p.q_out, v[3] * p.q_out);
+                    o.y = pack_e4m3x4(v[4] * p.q_out, v[5] * p.q_out, v[6] * p.q_out, v[7] * p.q_out);
+                    o.z = pack_e4m3x4(v[8] * p.q_out, v[9] * p.q_out, v[10] * p.q_out, v[11] * p.q_out);
+                    o.w = pack_e4m3x4(v[12] * p.q_out, v[13] * p.q_out, v[14] * p.q_out, v[15] * p.q_out);
+                } else {
+                    o.x = pack16x2(f16, v[0], v[1]);
+                    o.y = pack16x2(f16, v[2], v[3]);
+                    o.z = pack16x2(f16, v[4], v[5]);
+                    o.w = pack16x2(f16, v[6], v[7]);
+                }
+                if (valid) *reinterpret_cast<uint4 *>(dst8 + (size_t)(k0 - H::K0) * (F8 ? 1 : 2)) = o;
+            } else if (valid) {
+#pragma unroll
+                for (int j = 0; j < VEC; ++j)
+                    if (k0 + j < H::K1) {
+                        const float v = value(k0 + j);
+                        if constexpr (F8)
+                            dst8[k0 + j - H::K0] = (uint8_t)__nv_cvt_float_to_fp8(v * p.q_out, __NV_SATFINITE, __NV_E4M3);
+                        else
+                            reinterpret_cast<uint16_t *>(dst8)[k0 + j - H::K0] = (uint16_t)pack16x2(f16, v, 0.f);
+                    }
             }
         }
+    }
 }
 
 // Store of half G's entries (scaled, LeakyReLU) of pixel pix: 16-byte vectors where the
@@ -380,6 +412,11 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
                                                   : static_cast<const uint8_t *>(z ? p.fs[1] : p.fs[0]);
                 src = reinterpret_cast<const uint4 *>(fsb + ((size_t)y * p.w + x) * p.c * esz);
             }
+            // up to four 16-byte units of them in flight under the MMAs and the staging
+            uint4 sf[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (src && q0 + i < q1) sf[i] = __ldg(src + q0 + i);
             int ok = 1;
             if (lane == 0) ok = mbar_wait(tfull, (uint32_t)k & 1u, p.err, ERR_CORR_EPILOGUE);
             ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -392,15 +429,8 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(tempty);
-                if (half == 0) {
-                    float res[Half<R, F8, 0>::N > 0 ? Half<R, F8, 0>::N : 1];
-                    corr_pick_window<R, F8, 0>(slice, py, px, p.scale, res);
-                    if (valid) corr_store_half<R, F8, 0>(p, res, pix);
-                } else {
-                    float res[Half<R, F8, 1>::N > 0 ? Half<R, F8, 1>::N : 1];
-                    corr_pick_window<R, F8, 1>(slice, py, px, p.scale, res);
-                    if (valid) corr_store_half<R, F8, 1>(p, res, pix);
-                }
+                if (half == 0) corr_pick_store_window<R, F8, 0>(p, slice, py, px, valid, pix);
+                else corr_pick_store_window<R, F8, 1>(p, slice, py, px, valid, pix);
             } else if (half == 0) {
                 corr_epilogue_half<R, F8, 0>(p, ta, slice, py, px, q, valid, pix);
             } else {
@@ -408,7 +438,10 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
             }
             if (src) {
                 uint4 *cp = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(p.self_copy) + pix * p.out_cs * esz);
-                for (int qq = q0; qq < q1; ++qq) cp[qq] = __ldg(src + qq);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (q0 + i < q1) cp[q0 + i] = sf[i];
+                for (int qq = q0 + 4; qq < q1; ++qq) cp[qq] = __ldg(src + qq);
             }
             if constexpr (!WHOLE) {
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
