@@ -86,10 +86,12 @@ struct TcLaunch {
 };
 
 // Epilogue shared by the conv kernels: thread r of the CTA owns accumulator row r, i.e.
-// output pixel (img, y, x0 + r), stored for r < tw.
+// output pixel (img, y, x0 + r), stored for r < tw; columns [c_lo, c_hi) (multiples of 16);
+// bias and e4m3 weight scales from global or shared memory.
 template <int BN, bool HEAD, bool F8>
 __device__ __forceinline__ void conv_epilogue(uint32_t tmem, const TcLaunch &p, int warp, int lane, int x0, int y,
-                                              int img, int tw = BM) {
+                                              int img, int tw, const float *bias, const float *wscale, int c_lo,
+                                              int c_hi) {
     if (HEAD) {
         const int x = x0 + warp * 32 + lane;
         uint32_t r[16];
@@ -98,19 +100,18 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, const TcLaunch &p, 
             const size_t pix = (size_t)(img * p.ho + y) * p.wo + x;
             float2 up = make_float2(0.f, 0.f);
             if (p.up) up = reinterpret_cast<const float2 *>(p.up)[pix];
-            const float s0 = F8 ? __ldg(p.wscale) : 1.f, s1 = F8 ? __ldg(p.wscale + 1) : 1.f;
+            const float s0 = F8 ? wscale[0] : 1.f, s1 = F8 ? wscale[1] : 1.f;
             reinterpret_cast<float2 *>(p.flow)[pix] =
-                make_float2(up.x + (__uint_as_float(r[0]) * s0 + __ldg(p.bias)),
-                            up.y + (__uint_as_float(r[1]) * s1 + __ldg(p.bias + 1)));
+                make_float2(up.x + (__uint_as_float(r[0]) * s0 + bias[0]), up.y + (__uint_as_float(r[1]) * s1 + bias[1]));
         }
     } else {
         const int row = warp * 32 + lane;
         const int x = x0 + row;
         const size_t pix = (size_t)(img * p.ho + y) * p.wo + x;
-        const bool vec_params = ((reinterpret_cast<uintptr_t>(p.bias) |
-                                  (F8 ? reinterpret_cast<uintptr_t>(p.wscale) : 0)) & 15) == 0;
+        const bool vec_params = ((reinterpret_cast<uintptr_t>(bias) |
+                                  (F8 ? reinterpret_cast<uintptr_t>(wscale) : 0)) & 15) == 0;
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
+        for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
             uint32_t r[16];
             tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
             if (row < tw && x < p.wo) {
@@ -120,18 +121,18 @@ __device__ __forceinline__ void conv_epilogue(uint32_t tmem, const TcLaunch &p, 
                 if (vec_params) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float4 b4 = __ldg(reinterpret_cast<const float4 *>(p.bias + c0) + q);
+                        const float4 b4 = reinterpret_cast<const float4 *>(bias + c0)[q];
                         bv[4 * q] = b4.x; bv[4 * q + 1] = b4.y; bv[4 * q + 2] = b4.z; bv[4 * q + 3] = b4.w;
                         if (F8) {
-                            const float4 s4 = __ldg(reinterpret_cast<const float4 *>(p.wscale + c0) + q);
+                            const float4 s4 = reinterpret_cast<const float4 *>(wscale + c0)[q];
                             sv[4 * q] = s4.x; sv[4 * q + 1] = s4.y; sv[4 * q + 2] = s4.z; sv[4 * q + 3] = s4.w;
                         }
                     }
                 } else {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        bv[j] = __ldg(p.bias + c0 + j);
-                        if (F8) sv[j] = __ldg(p.wscale + c0 + j);
+                        bv[j] = bias[c0 + j];
+                        if (F8) sv[j] = wscale[c0 + j];
                     }
                 }
                 float v[16];
@@ -275,7 +276,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (lane == 0) ok = mbar_wait(accum, 0, p.err, ERR_EPILOGUE) && *(volatile int *)p.err == 0;
     ok = __shfl_sync(0xffffffffu, ok, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) conv_epilogue<BN, HEAD, F8>(tmem, p, warp, lane, x0, y, img);
+    if (ok) conv_epilogue<BN, HEAD, F8>(tmem, p, warp, lane, x0, y, img, BM, p.bias, p.wscale, 0, BN);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -370,6 +371,8 @@ conv_tc_tiles_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
     uint8_t *sA = smem + wbytes;
     // 256 bytes after the halo ring: the two rows past a slot that outputs 126, 127 read
     uint64_t *bars = reinterpret_cast<uint64_t *>(sA + abytes + 256);
+    // bias and e4m3 weight scales, staged once for the epilogue (512 bytes after the barriers)
+    float *sbias = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(bars) + 512), *sscale = sbias + 128;
     const uint32_t fullA = smem_u32(bars), emptyA = fullA + 8 * UA;
     const uint32_t fullB = emptyA + 8 * UA, emptyB = fullB + 8 * SB;
     const uint32_t wfull = emptyB + 8 * SB, accf0 = wfull + 8, acce0 = accf0 + 16, done0 = acce0 + 16;
@@ -537,8 +540,16 @@ conv_tc_tiles_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
             if (global_ns() - t0 > WAIT_NS) { atomicCAS(p.err, 0, ERR_DRAIN); break; }
     } else if (warp < TILE_EPI_WARPS) {
         // ---- epilogue
+        for (int i = threadIdx.x; i < BN; i += 32 * TILE_EPI_WARPS) {
+            if (i < (HEAD ? 2 : BN)) sbias[i] = p.bias[i];  // a flow head's bias has its 2 outputs only
+            if (F8) sscale[i] = p.wscale[i];
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * TILE_EPI_WARPS) : "memory");  // the epilogue warps only
         pdl_wait();  // the outputs may still be read by the previous kernel
-        const int q = warp & 3;
+        const int q = warp & 3, g = warp >> 2;
+        // one-row tiles: the two warp groups take half of the columns each; else alternate rows
+        constexpr bool COLS = !HEAD && BN >= 32 && R == 1;
+        constexpr int CH = (BN / 2 + 15) / 16 * 16;
         int k = 0;
         for (int ts = blockIdx.x; ts < p.ntiles; ts += gridDim.x, ++k) {
             const int b = k & 1, use = k >> 1;
@@ -551,9 +562,14 @@ conv_tc_tiles_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
             const int xt = ts % p.ntx, rg = (ts / p.ntx) % p.nrg, img = ts / (p.ntx * p.nrg);
             const int y0 = rg * R, nrows = p.ho - y0 < R ? p.ho - y0 : R;
             const uint32_t acc0 = tmem + (uint32_t)(b * R) * (uint32_t)p.acc_cols;
-            for (int r = warp >> 2; r < nrows; r += TILE_EPI_WARPS / 4)
-                conv_epilogue<BN, HEAD, F8>(acc0 + (uint32_t)r * (uint32_t)p.acc_cols, p, q, lane, xt * TW, y0 + r, img,
-                                            TW);
+            if (COLS) {
+                conv_epilogue<BN, HEAD, F8>(acc0, p, q, lane, xt * TW, y0, img, TW, sbias, sscale, g ? CH : 0,
+                                            g ? BN : CH);
+            } else {
+                for (int r = g; r < nrows; r += TILE_EPI_WARPS / 4)
+                    conv_epilogue<BN, HEAD, F8>(acc0 + (uint32_t)r * (uint32_t)p.acc_cols, p, q, lane, xt * TW, y0 + r,
+                                                img, TW, sbias, sscale, 0, BN);
+            }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(acce0 + 8 * b);
@@ -604,7 +620,7 @@ int sm_count() {
 // one), resident or streamed weights.  Returns the dynamic shared memory it needs.
 size_t plan_tiles(const TcConvPlan &plan, int bn, int n_img, TcLaunch &lp, int *grid) {
     constexpr uint32_t SMEM_MAX = 232448;                  // opt-in maximum per CTA
-    const uint32_t budget = SMEM_MAX - 1024 - 256 - 512;    // alignment slack, slot overrun guard, barriers
+    const uint32_t budget = SMEM_MAX - 1024 - 256 - 1536;   // alignment slack, slot overrun guard, barriers and epilogue parameters
     const int acc = tmem_cols_for(bn);
     const uint32_t aslot = (uint32_t)BM * (uint32_t)plan.rb;
     const uint32_t ufull = round1k(3u * (uint32_t)bn * (uint32_t)plan.rb), utail = round1k(3u * (uint32_t)bn * 64u);
@@ -630,8 +646,9 @@ size_t plan_tiles(const TcConvPlan &plan, int bn, int n_img, TcLaunch &lp, int *
         if (2 * ufull + a2 <= budget) { SB = 2; wbytes = 2 * ufull; break; }
         if (R == 1) return 0;  // no tiling fits
     }
-    int UA = split ? 2 : (int)((budget - wbytes) / aunit);
-    if (UA > 4) UA = 4;
+    // two halo units: the next channel step loads under the current one (deeper rings
+    // measured no faster, and the smaller footprint leaves room for other streams' CTAs)
+    const int UA = 2;
     lp.tailunit = split ? 1 : 0;
     lp.R = R;
     lp.acc_cols = acc;
@@ -644,7 +661,7 @@ size_t plan_tiles(const TcConvPlan &plan, int bn, int n_img, TcLaunch &lp, int *
     lp.ntx = ntx;
     lp.nrg = (plan.ho + R - 1) / R;
     lp.ntiles = ntx * lp.nrg * n_img;
-    const size_t smem = 1024 + wbytes + (split ? (size_t)a2 : (size_t)UA * aunit) + 256 + 512;
+    const size_t smem = 1024 + wbytes + (size_t)a2 + 256 + 1536;
     // resident CTAs per SM: TMEM columns and the SM's 228 KB of shared memory (1 KB of it
     // reserved per CTA)
     int per_sm = 512 / cols;
