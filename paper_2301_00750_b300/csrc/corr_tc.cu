@@ -52,6 +52,7 @@ struct CorrTcLaunch {
     size_t fs_img_bytes;
     int nb;       // batch entries (blocks run over nbx x nby x nb)
     int nstages;  // operand stages in shared memory
+    int tma_self; // the self copy is a TMA store of the block's self operand (tmC), not per thread
 };
 
 template <int R>
@@ -281,7 +282,8 @@ __device__ __forceinline__ void corr_epilogue_half(const CorrTcLaunch &p, uint32
 //     half also copies half of the pixel's self features into the estimator input.
 template <int R, bool F8, bool WHOLE>
 __global__ void __launch_bounds__(32 * (TILE_CORR_EPI + 2), 1)
-corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmO, const CorrTcLaunch p) {
+corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmO,
+               const __grid_constant__ CUtensorMap tmC, const CorrTcLaunch p) {
     using G = Geo<R>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -301,7 +303,7 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, p.tma_self ? 2 : 1);  // the MMAs, and the self store's reads
         }
         mbar_init(tfull, 1);
         mbar_init(tempty, TILE_CORR_EPI);
@@ -364,11 +366,20 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
         const uint32_t rb = (uint32_t)p.rb;
         uint32_t s = 0, ph = 0;
         int k = 0;
+        if (p.tma_self) pdl_wait();  // the self store writes the estimator input
         for (int t = blockIdx.x; t < nblocks; t += gridDim.x, ++k) {
             if (k >= 1 && !mbar_wait(tempty, (uint32_t)(k - 1) & 1u, p.err, ERR_CORR_MMA)) break;
             if (!mbar_wait(full0 + 8 * s, ph, p.err, ERR_CORR_MMA)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t base = smem_u32(smem + s * stage);
+            if (p.tma_self) {
+                // the block's self features, already in the stage, into the estimator input
+                const int bx = t % nbx, by = (t / nbx) % nby, z = t / (nbx * nby);
+                for (int ch = 0; ch < p.nch; ++ch)
+                    tma_store_4d(&tmC, base + (uint32_t)ch * (abytes + bbytes), ch * (F8 ? p.rb : p.rb / 2), bx * BX,
+                                 by * BY, z);
+                tma_store_commit();
+            }
             for (int ch = 0; ch < p.nch; ++ch) {
                 const uint32_t a = base + (uint32_t)ch * (abytes + bbytes);
                 const uint64_t da = sw_desc(a, rb), db0 = sw_desc(a + abytes, rb);
@@ -381,8 +392,13 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
             }
             umma_commit(empty0 + 8 * s);  // the operand stage is read
             umma_commit(tfull);           // the block is in TMEM
+            if (p.tma_self) {
+                tma_store_wait_read();  // the self store has read the stage as well
+                mbar_arrive(empty0 + 8 * s);
+            }
             if (++s == (uint32_t)NS) { s = 0; ph ^= 1u; }
         }
+        if (p.tma_self) tma_store_wait_all();
         umma_commit(done);  // every MMA issued above has completed once it fires
         const unsigned long long t0 = global_ns();
         while (!mbar_try(done, 0))
@@ -395,7 +411,7 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
         float *slice = slices + (size_t)threadIdx.x * (WHOLE ? Whole<R, F8>::SSW : G::SSTRIDE);
         const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16);
         const size_t esz = F8 ? 1 : 2;
-        const int nq = p.self_copy ? (int)(p.c * esz / 16) : 0;  // 16-byte units of a pixel's self features
+        const int nq = p.self_copy && !p.tma_self ? (int)(p.c * esz / 16) : 0;  // 16-byte units of a pixel's self features
         const int q0 = half ? nq / 2 : 0, q1 = half ? nq : nq / 2;  // this half's share of them
         int k = 0;
         for (int t = blockIdx.x; t < nblocks; t += gridDim.x, ++k) {
@@ -488,7 +504,8 @@ int corr_sm_count() {
 }
 
 template <int R, bool F8, bool WHOLE>
-cudaError_t launch_rw(const CorrTcPlan &plan, const CorrTcLaunch &lp, int grid, size_t smem, cudaStream_t st) {
+cudaError_t launch_rw(const CorrTcPlan &plan, const CorrTcLaunch &lp, const CUtensorMap &tmC, int grid, size_t smem,
+                      cudaStream_t st) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e =
@@ -497,7 +514,7 @@ cudaError_t launch_rw(const CorrTcPlan &plan, const CorrTcLaunch &lp, int grid, 
         attr_set = true;
     }
     return launch_pdl(corr_tc_kernel<R, F8, WHOLE>, dim3(grid), dim3(32 * (TILE_CORR_EPI + 2)), smem, st, plan.tmS,
-                      plan.tmO, lp);
+                      plan.tmO, tmC, lp);
 }
 
 // Whole-window staging where its slices fit beside one operand stage (the narrow levels),
@@ -519,7 +536,16 @@ cudaError_t launch_r(const CorrTcPlan &plan, const CorrTcLaunch &lp0, int nb, cu
     const int nsm = corr_sm_count();
     const int grid = nblocks < nsm ? (int)nblocks : nsm;
     const size_t smem = 1024 + (size_t)ns * stage + slices + 256;
-    return whole ? launch_rw<R, F8, true>(plan, lp, grid, smem, st) : launch_rw<R, F8, false>(plan, lp, grid, smem, st);
+    // the self copy as a TMA store of each block's self operand: a map over the destination
+    // (channels [0, c) of nb images at pixel stride out_cs), boxed and swizzled like the self
+    // map; the per-thread copy where the encoding fails
+    CUtensorMap tmC = plan.tmS;
+    lp.tma_self = 0;
+    if (lp.self_copy && encode_features(&tmC, lp.self_copy, nb, lp.out_cs, plan.h, plan.w, plan.c, BX, BY, plan.f8,
+                                        plan.rb, plan.f16))
+        lp.tma_self = 1;
+    return whole ? launch_rw<R, F8, true>(plan, lp, tmC, grid, smem, st)
+                 : launch_rw<R, F8, false>(plan, lp, tmC, grid, smem, st);
 }
 
 }  // namespace

@@ -103,6 +103,19 @@ __device__ __forceinline__ void tma_load_5d(const CUtensorMap *map, uint32_t bar
         : "memory");
 }
 
+// TMA tiled store of a 4-d box from shared memory (bulk-group completion: commit, then wait
+// for the reads of the shared-memory source with tma_store_wait_read before reusing it, and
+// for the writes with tma_store_wait_all before the thread exits).
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap *map, uint32_t src, int c0, int c1, int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];"
+        ::"l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(src)
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void tma_store_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void tma_store_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // Shared-memory matrix descriptor: K-major operand in the 128-byte swizzled layout written
 // by TMA (rows of 128 B, 8-row groups 1024 B apart), version 1 (tcgen05).
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
