@@ -130,12 +130,16 @@ __device__ __forceinline__ void corr_stage_window(uint32_t ta, float *slice, int
     }
 }
 
-// The half's entries of the pixel from its staged window (after corr_stage_window), stored
-// as they are computed, a 16-byte vector (8 16-bit or 16 e4m3 values) at a time, so only one
-// vector's values are live.
+// The half's entries of the pixel from its staged window (after corr_stage_window).  16-bit
+// cost volumes where 16-byte stores are allowed go through the warp: every thread packs its
+// pixel's entries into its slice, then the warp writes the 32 pixels' rows chunk by chunk, so
+// consecutive lanes write consecutive 16-byte chunks of one pixel (the pixels are a whole
+// estimator-input row apart) instead of 32 different lines per store; else (and for e4m3)
+// each thread stores its own vectors as they are computed.
 template <int R, bool F8, int G>
-__device__ __forceinline__ void corr_pick_store_window(const CorrTcLaunch &p, const float *slice, int py, int px,
-                                                       bool valid, size_t pix) {
+__device__ __forceinline__ void corr_pick_store_window(const CorrTcLaunch &p, float *slice, int py, int px, bool valid,
+                                                       size_t pix, float *slices, int sstride, int q, int lane, int bx,
+                                                       int by, int z) {
     using H = Half<R, F8, G>;
     constexpr int HX = BX + 2 * R, W = 2 * R + 1, VEC = H::VEC;
     if constexpr (H::N > 0) {
@@ -146,6 +150,38 @@ __device__ __forceinline__ void corr_pick_store_window(const CorrTcLaunch &p, co
             const float v = slice[base + (dy - H::DY0) * HX + dx] * p.scale;
             return v >= 0.f ? v : 0.1f * v;
         };
+        if constexpr (!F8) {
+            if (p.vec_out) {
+                constexpr int NV = H::N / 8;  // whole 16-byte chunks of the half
+                uint32_t pk[NV * 4];
+#pragma unroll
+                for (int k = 0; k < NV * 8; k += 2) pk[k / 2] = pack16x2(f16, value(H::K0 + k), value(H::K0 + k + 1));
+                uint16_t tail[H::N - NV * 8 > 0 ? H::N - NV * 8 : 1];
+#pragma unroll
+                for (int k = NV * 8; k < H::N; ++k) tail[k - NV * 8] = (uint16_t)pack16x2(f16, value(H::K0 + k), 0.f);
+                __syncwarp();  // every lane has read its window
+                uint4 *own = reinterpret_cast<uint4 *>(slice);
+#pragma unroll
+                for (int j = 0; j < NV; ++j) own[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                __syncwarp();
+                const int w0 = q * 32;  // first pixel (and slice) of this warp
+                for (int j = lane; j < 32 * NV; j += 32) {
+                    const int l = j / NV, part = j - l * NV, m = w0 + l;
+                    const int yy = by * BY + (m >> 4), xx = bx * BX + (m & 15);
+                    if (yy < p.h && xx < p.w) {
+                        const size_t pp = ((size_t)z * p.h + yy) * p.w + xx;
+                        const uint4 v = reinterpret_cast<const uint4 *>(slices + (size_t)(threadIdx.x - lane + l) * sstride)[part];
+                        *reinterpret_cast<uint4 *>(static_cast<uint16_t *>(p.out) + pp * p.out_cs + H::K0 + 8 * part) = v;
+                    }
+                }
+                if (valid) {
+                    uint16_t *dst = static_cast<uint16_t *>(p.out) + pix * p.out_cs + H::K0 + NV * 8;
+#pragma unroll
+                    for (int k = NV * 8; k < H::N; ++k) dst[k - NV * 8] = tail[k - NV * 8];
+                }
+                return;
+            }
+        }
         uint8_t *dst8 = static_cast<uint8_t *>(p.out) + pix * p.out_cs * (F8 ? 1 : 2) + (size_t)H::K0 * (F8 ? 1 : 2);
 #pragma unroll
         for (int k0 = H::K0; k0 < H::K1; k0 += VEC) {
@@ -445,8 +481,12 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(tempty);
-                if (half == 0) corr_pick_store_window<R, F8, 0>(p, slice, py, px, valid, pix);
-                else corr_pick_store_window<R, F8, 1>(p, slice, py, px, valid, pix);
+                if (half == 0)
+                    corr_pick_store_window<R, F8, 0>(p, slice, py, px, valid, pix, slices, Whole<R, F8>::SSW, q, lane, bx,
+                                                     by, z);
+                else
+                    corr_pick_store_window<R, F8, 1>(p, slice, py, px, valid, pix, slices, Whole<R, F8>::SSW, q, lane, bx,
+                                                     by, z);
             } else if (half == 0) {
                 corr_epilogue_half<R, F8, 0>(p, ta, slice, py, px, q, valid, pix);
             } else {

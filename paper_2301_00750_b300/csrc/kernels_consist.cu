@@ -155,8 +155,8 @@ __global__ void __launch_bounds__(256, NEXT ? 5 : 6) consistency_kernel(ConsistA
     float It[3], Pt[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        It[c] = __ldg(a.It + c * hw + i);
-        Pt[c] = __ldg(a.Pt + c * hw + i);
+        It[c] = __ldcs(a.It + c * hw + i);  // read once: streaming
+        Pt[c] = __ldcs(a.Pt + c * hw + i);
     }
     if (!NEXT && a.first) {
 #pragma unroll
@@ -206,10 +206,10 @@ __global__ void __launch_bounds__(256, NEXT ? 5 : 6) consistency_kernel(ConsistA
             const float AI = wl * It[c] + wp * gI[c] + wn * gIn[c];
             const float e = It[c] - AI;
             dI += e * e;
-            a.O[c * hw + i] = A;
-            if (a.sI) a.sI[c * hw + i] = It[c];
-            if (a.sP) a.sP[c * hw + i] = Pt[c];
-            if (a.sO) a.sO[c * hw + i] = A;
+            __stcs(a.O + c * hw + i, A);  // written once: streaming
+            if (a.sI) __stcs(a.sI + c * hw + i, It[c]);
+            if (a.sP) __stcs(a.sP + c * hw + i, Pt[c]);
+            if (a.sO) __stcs(a.sO + c * hw + i, A);
         }
     } else {
 #pragma unroll
@@ -219,13 +219,13 @@ __global__ void __launch_bounds__(256, NEXT ? 5 : 6) consistency_kernel(ConsistA
             const float AI = (1.f - wp) * It[c] + wp * gI[c];
             const float e = It[c] - AI;
             dI += e * e;
-            a.O[c * hw + i] = A;
-            if (a.sI) a.sI[c * hw + i] = It[c];
-            if (a.sP) a.sP[c * hw + i] = Pt[c];
-            if (a.sO) a.sO[c * hw + i] = A;
+            __stcs(a.O + c * hw + i, A);  // written once: streaming
+            if (a.sI) __stcs(a.sI + c * hw + i, It[c]);
+            if (a.sP) __stcs(a.sP + c * hw + i, Pt[c]);
+            if (a.sO) __stcs(a.sO + c * hw + i, A);
         }
     }
-    if (a.wc) a.wc[i] = a.lambda * expf(-a.alpha * dI);
+    if (a.wc) __stcs(a.wc + i, a.lambda * expf(-a.alpha * dI));
     if (a.mask) a.mask[i] = (m ? 1 : 0) | (mn ? 2 : 0);
 }
 
