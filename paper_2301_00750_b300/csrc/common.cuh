@@ -112,6 +112,9 @@ struct ConvArgs {
     int leaky;
     float q_out;  // e4m3 outputs: 1 / output activation scale (unused otherwise)
     int accumulate;  // CUDA-core kernel only: add to the output instead of overwriting it
+    // persistent tensor-core kernel only: walk the tiles from the last to the first, so a layer
+    // first reads the rows its producer wrote last (still in L2); alternate layers of a chain
+    int rev;
 };
 
 // First pyramid conv: planar float image (3, H, W), edge-replicated to (Hp, Wp) and

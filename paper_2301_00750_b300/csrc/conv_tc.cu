@@ -83,6 +83,7 @@ struct TcLaunch {
                           // kernel row each (0: resident weights)
     int ntx, nrg, ntiles; // tiles: 126-pixel column tiles x groups of R rows x images
     int tailunit;         // halo unit 1 holds the 64-byte tail step (two channel steps per tile)
+    int rev;              // tiles in reverse order (tile ts is ntiles - 1 - ts)
 };
 
 // Epilogue shared by the conv kernels: thread r of the CTA owns accumulator row r, i.e.
@@ -418,7 +419,8 @@ conv_tc_tiles_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
         bool fine = !p.stall;  // stalled (test hook): nothing is issued, so the issuers' waits run out
         uint32_t ua = 0, u = 0, q = 0;  // units issued; unit and phase of the next one
         for (int ts = blockIdx.x; ts < p.ntiles && fine; ts += gridDim.x) {
-            const int xt = ts % p.ntx, rg = (ts / p.ntx) % p.nrg, img = ts / (p.ntx * p.nrg);
+            const int tt = p.rev ? p.ntiles - 1 - ts : ts;
+            const int xt = tt % p.ntx, rg = (tt / p.ntx) % p.nrg, img = tt / (p.ntx * p.nrg);
             const int x0 = xt * TW, y0 = rg * R;
             const int nrows = p.ho - y0 < R ? p.ho - y0 : R;
             for (int c = 0; c < nch; ++c) {
@@ -488,7 +490,7 @@ conv_tc_tiles_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                 if (!mbar_wait(acce0 + 8 * b, (uint32_t)(use - 1) & 1u, p.err, ERR_MMA)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");  // the epilogue's TMEM reads are done
             }
-            const int y0 = ((ts / p.ntx) % p.nrg) * R;
+            const int y0 = (((p.rev ? p.ntiles - 1 - ts : ts) / p.ntx) % p.nrg) * R;
             const int nrows = p.ho - y0 < R ? p.ho - y0 : R;
             const int nmine = (nrows - j + NI - 1) / NI;  // rows j, j + NI, ... below nrows
             const uint32_t acc0 = tmem + (uint32_t)(b * R + j) * acc_step;
@@ -559,7 +561,8 @@ conv_tc_tiles_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int xt = ts % p.ntx, rg = (ts / p.ntx) % p.nrg, img = ts / (p.ntx * p.nrg);
+            const int tt = p.rev ? p.ntiles - 1 - ts : ts;
+            const int xt = tt % p.ntx, rg = (tt / p.ntx) % p.nrg, img = tt / (p.ntx * p.nrg);
             const int y0 = rg * R, nrows = p.ho - y0 < R ? p.ho - y0 : R;
             const uint32_t acc0 = tmem + (uint32_t)(b * R) * (uint32_t)p.acc_cols;
             if (COLS) {
@@ -937,6 +940,7 @@ cudaError_t launch_conv_tc(const TcConvPlan &plan, const ConvArgs &a, cudaStream
     if (reinterpret_cast<uintptr_t>(a.out) % 16 != 0 || a.out_cs % (plan.f8 ? 16 : 8) != 0) return cudaErrorInvalidValue;
     TcLaunch lp{plan.nch, plan.kc, plan.rb, plan.stride, plan.ho, plan.wo, img_off, a.out, a.out_cs, a.bias, a.leaky,
                 plan.err, nullptr, nullptr, plan.wscale, a.q_out, 0, 0, plan.taps, 0, plan.f16 ? 1 : 0};
+    lp.rev = a.rev;
     return plan.f8 ? launch_any_bn<true>(plan, lp, a.n, st) : launch_any_bn<false>(plan, lp, a.n, st);
 }
 

@@ -973,6 +973,7 @@ static tc_status run_pyramid(tc_stream *s, const float *img, int slot) {
         }
         ConvArgs b{B.tmpA, B.c, 1, B.h, B.w, B.c, 1, B.h, B.w, s->pyr_w[3 * (l - 1) + 1], s->pyr_b[3 * (l - 1) + 1],
                    B.c, B.tmpB, B.c, 1, B.q_pyr[1]};
+        b.rev = 1;  // reads the rows conv a wrote last first
         if ((r = conv_layer<T>(s, b, &s->pyr_plan[l - 1][1], TC_PROF_PYRAMID_CONV)) != TC_OK) return r;
         ConvArgs c{B.tmpB, B.c, 1, B.h, B.w, B.c, 1, B.h, B.w, s->pyr_w[3 * (l - 1) + 2], s->pyr_b[3 * (l - 1) + 2],
                    B.c, dst, B.c, 1, B.q_pyr[2]};
@@ -1074,10 +1075,12 @@ static tc_status run_estimators(tc_stream *s, int pcur, int pprev, int set) {
         ConvArgs c1{dec, B.ctot, 2, B.h, B.w, B.x0p, 1, B.h, B.w, B.wk[0], B.bias[0], net.dec[0], dec + B.off_x1, B.ctot, 1, B.q_est[2]};
         if ((r = conv_layer<T>(s, c1, &B.tcplan[0], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
         ConvArgs c2{dec + B.off_x1, B.ctot, 2, B.h, B.w, net.dec[0], 1, B.h, B.w, B.wk[1], B.bias[1], net.dec[1], dec + B.off_x2, B.ctot, 1, B.q_est[3]};
+        c2.rev = 1;  // conv2 and conv4 walk their tiles backwards (see ConvArgs::rev)
         if ((r = conv_layer<T>(s, c2, &B.tcplan[1], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
         ConvArgs c3{dec + B.off_x2, B.ctot, 2, B.h, B.w, net.dec[1], 1, B.h, B.w, B.wk[2], B.bias[2], net.dec[2], dec + B.off_x3, B.ctot, 1, B.q_est[4]};
         if ((r = conv_layer<T>(s, c3, &B.tcplan[2], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
         ConvArgs c4{dec + B.off_x2, B.ctot, 2, B.h, B.w, net.dec[1] + net.dec[2], 1, B.h, B.w, B.wk[3], B.bias[3], net.dec[3], dec + B.off_x4, B.ctot, 1, B.q_est[5]};
+        c4.rev = 1;
         if ((r = conv_layer<T>(s, c4, &B.tcplan[3], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
         if (B.headplan.enabled) {
             ConvArgs a5{dec + B.off_x3, B.ctot, 2, B.h, B.w, net.dec[2] + net.dec[3], 1, B.h, B.w, B.head_w, B.head_b,
@@ -1722,6 +1725,7 @@ static tc_status lanes_network(tc_stream *s, int lo, int n) {
         }
         ConvArgs b{tA, B.c, n, B.h, B.w, B.c, 1, B.h, B.w, s->pyr_w[3 * (l - 1) + 1], s->pyr_b[3 * (l - 1) + 1],
                    B.c, tB, B.c, 1, 1.f};
+        b.rev = 1;
         if ((r = conv_layer<T>(s, b, &s->pyr_plan[l - 1][1], TC_PROF_PYRAMID_CONV)) != TC_OK) return r;
         ConvArgs c{tB, B.c, n, B.h, B.w, B.c, 1, B.h, B.w, s->pyr_w[3 * (l - 1) + 2], s->pyr_b[3 * (l - 1) + 2],
                    B.c, cur, B.c, 1, 1.f};
@@ -1758,10 +1762,12 @@ static tc_status lanes_network(tc_stream *s, int lo, int n) {
         ConvArgs c1{dec, B.ctot, ne, B.h, B.w, B.x0p, 1, B.h, B.w, B.wk[0], B.bias[0], net.dec[0], dec + B.off_x1, B.ctot, 1, 1.f};
         if ((r = conv_layer<T>(s, c1, &B.tcplan[0], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
         ConvArgs c2{dec + B.off_x1, B.ctot, ne, B.h, B.w, net.dec[0], 1, B.h, B.w, B.wk[1], B.bias[1], net.dec[1], dec + B.off_x2, B.ctot, 1, 1.f};
+        c2.rev = 1;
         if ((r = conv_layer<T>(s, c2, &B.tcplan[1], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
         ConvArgs c3{dec + B.off_x2, B.ctot, ne, B.h, B.w, net.dec[1], 1, B.h, B.w, B.wk[2], B.bias[2], net.dec[2], dec + B.off_x3, B.ctot, 1, 1.f};
         if ((r = conv_layer<T>(s, c3, &B.tcplan[2], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
         ConvArgs c4{dec + B.off_x2, B.ctot, ne, B.h, B.w, net.dec[1] + net.dec[2], 1, B.h, B.w, B.wk[3], B.bias[3], net.dec[3], dec + B.off_x4, B.ctot, 1, 1.f};
+        c4.rev = 1;
         if ((r = conv_layer<T>(s, c4, &B.tcplan[3], TC_PROF_ESTIMATOR_CONV)) != TC_OK) return r;
         if (B.headplan.enabled) {
             ConvArgs a5{dec + B.off_x3, B.ctot, ne, B.h, B.w, net.dec[2] + net.dec[3], 1, B.h, B.w, B.head_w, B.head_b,
