@@ -115,6 +115,10 @@ struct ConvArgs {
     // persistent tensor-core kernel only: walk the tiles from the last to the first, so a layer
     // first reads the rows its producer wrote last (still in L2); alternate layers of a chain
     int rev;
+    // persistent tensor-core kernel only: the launch overlaps another stream's kernels (the
+    // pipelined mode), so its tiles keep the rows TMEM allows instead of being cut down to
+    // cover every SM: fewer CTAs, each fuller, leave SMs to the other stream
+    int overlap;
 };
 
 // First pyramid conv: planar float image (3, H, W), edge-replicated to (Hp, Wp) and

@@ -84,6 +84,7 @@ struct TcLaunch {
     int ntx, nrg, ntiles; // tiles: 126-pixel column tiles x groups of R rows x images
     int tailunit;         // halo unit 1 holds the 64-byte tail step (two channel steps per tile)
     int rev;              // tiles in reverse order (tile ts is ntiles - 1 - ts)
+    int overlap;          // launcher only: keep the full rows per tile (see ConvArgs::overlap)
 };
 
 // Epilogue shared by the conv kernels: thread r of the CTA owns accumulator row r, i.e.
@@ -621,7 +622,12 @@ int sm_count() {
 // Tiling of conv_tc_tiles_kernel for a planned stride-1 3x3 layer over n_img images:
 // rows per tile, halo units (at least two, so the next channel step loads under the current
 // one), resident or streamed weights.  Returns the dynamic shared memory it needs.
-size_t plan_tiles(const TcConvPlan &plan, int bn, int n_img, TcLaunch &lp, int *grid) {
+// overlap: the launch shares the GPU with another stream's kernels; the rows per tile are
+// not cut down to cover the SMs (measured at 1080p: sequential 1201 vs 1269 frames/s, so
+// off there; pipelined 1633 vs 1575).
+constexpr int kOverlapGrid = 120;
+
+size_t plan_tiles(const TcConvPlan &plan, int bn, int n_img, TcLaunch &lp, int *grid, bool overlap) {
     constexpr uint32_t SMEM_MAX = 232448;                  // opt-in maximum per CTA
     const uint32_t budget = SMEM_MAX - 1024 - 256 - 1536;   // alignment slack, slot overrun guard, barriers and epilogue parameters
     const int acc = tmem_cols_for(bn);
@@ -635,7 +641,7 @@ size_t plan_tiles(const TcConvPlan &plan, int bn, int n_img, TcLaunch &lp, int *
     // would not cover the SMs or two halo units would not fit beside the weights
     int R = 512 / (2 * acc);
     if (R > TILE_RMAX) R = TILE_RMAX;
-    while (R > 1 && (long)ntx * ((plan.ho + R - 1) / R) * n_img < nsm) R /= 2;
+    while (!overlap && R > 1 && (long)ntx * ((plan.ho + R - 1) / R) * n_img < nsm) R /= 2;
     // two channel steps, the second a 64-byte tail: the two halo units alternate between
     // them, so unit 1 takes tail-width slots
     const bool split = tail && plan.nch == 2 && plan.rb == 128;
@@ -671,6 +677,10 @@ size_t plan_tiles(const TcConvPlan &plan, int bn, int n_img, TcLaunch &lp, int *
     const int by_smem = (int)(233472 / (smem + 1024));
     if (by_smem < per_sm) per_sm = by_smem;
     *grid = lp.ntiles < nsm * per_sm ? lp.ntiles : nsm * per_sm;
+    // overlapped launches also leave SMs to the other streams' kernels: a persistent grid of at
+    // most kOverlapGrid CTAs (its tiles are spread over fewer SMs, so none starts late behind
+    // another stream's CTAs and holds up the launch's end)
+    if (overlap && *grid > kOverlapGrid) *grid = kOverlapGrid;
     return smem;
 }
 
@@ -692,7 +702,7 @@ cudaError_t launch_bn(const TcConvPlan &plan, const TcLaunch &lp, int n_img, cud
     if (plan.stride == 1 && plan.taps == 9) {
         TcLaunch lt = lp;
         int g = 0;
-        const size_t smem = plan_tiles(plan, BN, n_img, lt, &g);
+        const size_t smem = plan_tiles(plan, BN, n_img, lt, &g, lp.overlap != 0);
         if (smem == 0 || lt.sa < 2) return cudaErrorInvalidConfiguration;
         lt.stall = take_stall(st);
         constexpr int ACC = tmem_cols_for(BN);
@@ -916,6 +926,7 @@ cudaError_t launch_conv_tc_head(const TcConvPlan &plan, const ConvArgs &a, const
     if (!plan.enabled || !plan.head || !image_offset(plan, a, &img_off)) return cudaErrorInvalidValue;
     TcLaunch lp{plan.nch, plan.kc, plan.rb, plan.stride, plan.ho, plan.wo, img_off, nullptr, 0, a.bias, 0, plan.err,
                 flow, up, plan.wscale, 1.f, 0, 0, plan.taps, 0, plan.f16 ? 1 : 0};
+    lp.overlap = a.overlap;
     return plan.f8 ? launch_bn<16, true, true>(plan, lp, a.n, st) : launch_bn<16, true, false>(plan, lp, a.n, st);
 }
 
@@ -941,6 +952,7 @@ cudaError_t launch_conv_tc(const TcConvPlan &plan, const ConvArgs &a, cudaStream
     TcLaunch lp{plan.nch, plan.kc, plan.rb, plan.stride, plan.ho, plan.wo, img_off, a.out, a.out_cs, a.bias, a.leaky,
                 plan.err, nullptr, nullptr, plan.wscale, a.q_out, 0, 0, plan.taps, 0, plan.f16 ? 1 : 0};
     lp.rev = a.rev;
+    lp.overlap = a.overlap;
     return plan.f8 ? launch_any_bn<true>(plan, lp, a.n, st) : launch_any_bn<false>(plan, lp, a.n, st);
 }
 

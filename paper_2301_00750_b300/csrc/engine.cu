@@ -925,7 +925,9 @@ static tc_status prof_end(tc_stream *s) {
 template <typename T>
 static tc_status conv_layer(tc_stream *s, const ConvArgs &a, const TcConvPlan *plan, int cat) {
     if (plan && plan->enabled) {
-        TC_LAUNCH_CAT(s, cat, launch_conv_tc(*plan, a, s->st));
+        ConvArgs b = a;
+        b.overlap = s->pipelined ? 1 : 0;  // pipelined mode: the launches overlap the other streams'
+        TC_LAUNCH_CAT(s, cat, launch_conv_tc(*plan, b, s->st));
     } else if constexpr (sizeof(T) == 1) {
         return fail(s, TC_ERR_UNSUPPORTED, "e4m3 layer without a tensor-core plan");
     } else {
@@ -1085,6 +1087,7 @@ static tc_status run_estimators(tc_stream *s, int pcur, int pprev, int set) {
         if (B.headplan.enabled) {
             ConvArgs a5{dec + B.off_x3, B.ctot, 2, B.h, B.w, net.dec[2] + net.dec[3], 1, B.h, B.w, B.head_w, B.head_b,
                         2, nullptr, 2, 0};
+            a5.overlap = s->pipelined ? 1 : 0;
             TC_LAUNCH_CAT(s, TC_PROF_HEAD, launch_conv_tc_head(B.headplan, a5, l < s->L ? up : nullptr, flow, s->st));
         } else if constexpr (sizeof(T) == 1) {
             return fail(s, TC_ERR_UNSUPPORTED, "e4m3 flow head without a tensor-core plan");
@@ -1772,6 +1775,7 @@ static tc_status lanes_network(tc_stream *s, int lo, int n) {
         if (B.headplan.enabled) {
             ConvArgs a5{dec + B.off_x3, B.ctot, ne, B.h, B.w, net.dec[2] + net.dec[3], 1, B.h, B.w, B.head_w, B.head_b,
                         2, nullptr, 2, 0};
+            a5.overlap = s->pipelined ? 1 : 0;
             TC_LAUNCH_CAT(s, TC_PROF_HEAD, launch_conv_tc_head(B.headplan, a5, l < s->L ? up : nullptr, flow, s->st));
         } else {
             HeadArgs ha{dec + B.off_x3, B.ctot, net.dec[2] + net.dec[3], ne, B.h, B.w, B.head_w, B.head_b,
