@@ -346,6 +346,40 @@ def e2e_host(tc, torch, path, frames, styl, precision, steps, warmup, scales=Non
     return dict(value=steps / dt, h2d=2 * img, d2h=img)
 
 
+def host_link(torch, img_bytes, reps=10):
+    """The host link's throughput for the end-to-end copy pattern of one frame, measured with
+    pinned buffers: H2D of I_t and P_t (2 x img_bytes) alone, D2H of O_t (img_bytes) alone, and
+    both at once on two streams.  The link roofline takes the two directions as independent
+    (full duplex): 1 / max(H2D time, D2H time) frames/s; the concurrent time is reported beside
+    it (it came out above the pipelined entry point's own per-frame time, which overlaps the
+    copies of neighbouring frames better than back-to-back bursts do)."""
+    n = img_bytes // 4
+    hin = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in range(2)]
+    hout = torch.empty(n, dtype=torch.float32).pin_memory()
+    din = [torch.empty(n, device="cuda") for _ in range(2)]
+    dout = torch.empty(n, device="cuda")
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(h2d, d2h):
+        for it in range(reps + 2):
+            if it == 2:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            if h2d:
+                with torch.cuda.stream(up):
+                    for k in range(2):
+                        din[k].copy_(hin[k], non_blocking=True)
+            if d2h:
+                with torch.cuda.stream(down):
+                    hout.copy_(dout, non_blocking=True)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps
+
+    t_up, t_down, t_both = timed(True, False), timed(False, True), timed(True, True)
+    return dict(h2d_gbs=round(2 * img_bytes / t_up / 1e9, 1), d2h_gbs=round(img_bytes / t_down / 1e9, 1),
+                both_ms_per_frame=round(t_both * 1e3, 4), frames_per_s_bound=round(1.0 / max(t_up, t_down), 1))
+
+
 def oracle_threads():
     """Threads of the oracle's OpenMP loops: OMP_NUM_THREADS when set, else (the OpenMP
     default) the CPUs this process may run on."""
@@ -509,6 +543,8 @@ def run_ours(args):
                         scales=scales, solver_iters=args.solver_iters, latency=args.latency,
                         flow_downscale=args.flow_downscale)
     e2e_v, e2e_sync_v = e2e["value"], e2e_sync["value"]
+    H, W = frames[0].shape[1:]
+    link = host_link(torch, 3 * H * W * 4)
     if world > 1:
         e2e_v = world / max_over_ranks(1.0 / e2e["value"], world)
         e2e_sync_v = world / max_over_ranks(1.0 / e2e_sync["value"], world)
@@ -600,7 +636,11 @@ def run_ours(args):
                 "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
                 "api": "tc_process_frame_host_async for every frame from pinned host memory, one "
                        "tc_synchronize at the end of the timed region (uploads and downloads overlap the "
-                       "neighbouring frames' kernels)"},
+                       "neighbouring frames' kernels)",
+                "link": dict(link, frac=round(e2e["value"] / link["frames_per_s_bound"], 4),
+                             note="host link roofline of this copy pattern, measured in this run with pinned "
+                                  "buffers: 1 / max(H2D time of I_t + P_t, D2H time of O_t), the two directions "
+                                  "taken as independent; frac = e2e / that bound")},
         "e2e_sync": {"value": round(e2e_sync_v * (world if world > 1 else 1), 3), "unit": UNIT,
                      "h2d_bytes_per_step": e2e_sync["h2d"], "d2h_bytes_per_step": e2e_sync["d2h"],
                      "api": "tc_process_frame_host, which waits for each frame (its P_t upload overlaps the "
@@ -997,6 +1037,93 @@ def run_train(args):
     print(json.dumps(line), flush=True)
 
 
+def _kernel_short(name):
+    n = name.replace("void ", "").replace("tc::(anonymous namespace)::", "").replace("tc::", "")
+    i = n.find(">(")
+    return n[: i + 1] if i >= 0 else n.split("(")[0]
+
+
+def run_timeline(args):
+    """Kernel timeline of the 1080p stream (CUPTI through torch.profiler): K frames after the
+    warm-up in pipelined and in sequential mode.  Reports per mode the time span per frame,
+    the time the GPU had at least one kernel running, the sum of kernel durations (above the
+    span when kernels of different frames overlap), each kernel's launches and time per frame,
+    and the kernels of one sequential frame in order with their start offsets."""
+    import torch
+    from torch.profiler import profile, ProfilerActivity
+    import paper_2301_00750_b300 as tc
+
+    torch.cuda.set_device(0)
+    tmp = tempfile.mkdtemp(prefix="tctl")
+    path = os.path.join(tmp, "net.tcw")
+    write_weights(path)
+    frames, styl = make_frames(seed=0)
+    dev_f = [torch.from_numpy(f).cuda() for f in frames]
+    dev_s = [torch.from_numpy(p).cuda() for p in styl]
+    scales = fp8_scales(tc, path, dev_f, dev_s) if args.precision == "fp8" else None
+    H, W = dev_f[0].shape[1:]
+    k = max(4, min(args.steps, 24))
+    report = {}
+    for mode in ("pipelined", "sequential"):
+        s = open_stream(tc, path, W, H, args.precision, scales)
+        if mode == "pipelined":
+            s.set_pipelined(True)
+        O = torch.empty((3, H, W), device="cuda")
+        wc = torch.empty((H, W), device="cuda")
+        m = torch.empty((H, W), device="cuda", dtype=torch.uint8)
+        step = 0
+        for _ in range(max(args.warmup, 8)):
+            s.set_consistency(**consistency_controls(step, 0, 0))
+            i = frame_order(step)
+            s.process_frame(dev_f[i], dev_s[i], O, wc, m)
+            step += 1
+        s.synchronize()
+        torch.cuda.synchronize()
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            for _ in range(k):
+                s.set_consistency(**consistency_controls(step, 0, 0))
+                i = frame_order(step)
+                s.process_frame(dev_f[i], dev_s[i], O, wc, m)
+                step += 1
+            s.synchronize()
+            torch.cuda.synchronize()
+        s.destroy()
+        ev = sorted([(e.time_range.start, e.time_range.end - e.time_range.start, _kernel_short(e.name))
+                     for e in prof.events() if e.device_type == torch.autograd.DeviceType.CUDA
+                     and not e.name.startswith("Memcpy") and not e.name.startswith("Memset")])
+        t0, t1 = ev[0][0], max(a + d for a, d, _ in ev)
+        busy, cs, ce = 0.0, None, None
+        for a, d, _ in ev:
+            if ce is None or a > ce:
+                if ce is not None:
+                    busy += ce - cs
+                cs, ce = a, a + d
+            else:
+                ce = max(ce, a + d)
+        busy += ce - cs
+        agg = {}
+        for a, d, n in ev:
+            c, t = agg.get(n, (0, 0.0))
+            agg[n] = (c + 1, t + d)
+        report[mode] = dict(
+            us_per_frame=round((t1 - t0) / k, 1), busy_us_per_frame=round(busy / k, 1),
+            kernel_us_per_frame=round(sum(d for _, d, _ in ev) / k, 1), launches_per_frame=round(len(ev) / k, 2),
+            kernels={n: [round(c / k, 2), round(t / k, 1)] for n, (c, t) in sorted(agg.items(), key=lambda x: -x[1][1])})
+        if mode == "sequential":
+            per = len(ev) // k
+            fr = ev[per * (k // 2): per * (k // 2 + 1)]
+            report[mode]["one_frame"] = [[round(a - fr[0][0], 1), round(d, 1), n] for a, d, n in fr]
+    for mode, r in report.items():
+        print(f"== {mode}: {r['us_per_frame']} us per frame, GPU busy {r['busy_us_per_frame']} us, "
+              f"kernel time {r['kernel_us_per_frame']} us, {r['launches_per_frame']} launches per frame")
+        for n, (c, t) in r["kernels"].items():
+            print(f"   {t:8.1f} us/frame  {c:5.2f}/frame  {n}")
+        for a, d, n in r.get("one_frame", []):
+            print(f"   one frame: start {a:8.1f}  {d:7.1f} us  {n}")
+    print(json.dumps({"timeline": report, "precision": args.precision, "frames": k,
+                      "config": workload_config(args)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1030,6 +1157,8 @@ def main():
     ap.add_argument("--batch-lanes", type=int, default=4, help="serving: streams of one size per shared batch")
     ap.add_argument("--skip-curve", action="store_true", help="serving: only the 30 frames/s per stream load")
     ap.add_argument("--train", action="store_true", help="run the training-throughput benchmark instead")
+    ap.add_argument("--timeline", action="store_true",
+                    help="record the kernel timeline (CUPTI) of the 1080p stream in pipelined and sequential mode")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -1037,6 +1166,8 @@ def main():
         run_serve(args)
     elif args.train:
         run_train(args)
+    elif args.timeline:
+        run_timeline(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
