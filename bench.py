@@ -346,6 +346,36 @@ def e2e_host(tc, torch, path, frames, styl, precision, steps, warmup, scales=Non
     return dict(value=steps / dt, h2d=2 * img, d2h=img)
 
 
+def e2e_host_rgb8(tc, torch, path, frames, styl, precision, steps, warmup, scales=None):
+    """End-to-end with 8-bit video frames (tc_process_frame_host_rgb8_async): the synthetic
+    frames clipped to [0, 1] and rounded to interleaved RGB8 codes, uploaded, decoded on the
+    device, run, and O_t quantised and downloaded as RGB8; one tc_synchronize inside the timed
+    region, as the float32 `e2e`."""
+    H, W = frames[0].shape[1:]
+    q8 = lambda a: torch.from_numpy(np.ascontiguousarray(np.moveaxis(
+        np.floor(np.clip(a, 0.0, 1.0) * 255.0 + 0.5).astype(np.uint8), 0, -1))).pin_memory()
+    hI, hP = [q8(f) for f in frames], [q8(p) for p in styl]
+    hO = [torch.empty((H, W, 3), dtype=torch.uint8).pin_memory() for _ in range(4)]
+    s = open_stream(tc, path, W, H, precision, scales)
+    step = 0
+    for _ in range(warmup):
+        i = frame_order(step)
+        s.set_consistency(**consistency_controls(step, 0, 0))
+        s.process_frame_host_rgb8_async(hI[i], hP[i], hO[step % 4])
+        step += 1
+    s.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        i = frame_order(step)
+        s.set_consistency(**consistency_controls(step, 0, 0))
+        s.process_frame_host_rgb8_async(hI[i], hP[i], hO[step % 4])
+        step += 1
+    s.synchronize()
+    dt = time.perf_counter() - t0
+    s.destroy()
+    return dict(value=steps / dt, h2d=2 * 3 * H * W, d2h=3 * H * W)
+
+
 def host_link(torch, img_bytes, reps=10):
     """The host link's throughput for the end-to-end copy pattern of one frame, measured with
     pinned buffers: H2D of I_t and P_t (2 x img_bytes) alone, D2H of O_t (img_bytes) alone, and
@@ -545,6 +575,10 @@ def run_ours(args):
     e2e_v, e2e_sync_v = e2e["value"], e2e_sync["value"]
     H, W = frames[0].shape[1:]
     link = host_link(torch, 3 * H * W * 4)
+    e2e8 = None
+    if not args.latency and not args.solver_iters and args.flow_downscale == 1:
+        e2e8 = e2e_host_rgb8(tc, torch, path, frames, styl, args.precision, max(3, min(args.steps, 100)), 3,
+                             scales=scales)
     if world > 1:
         e2e_v = world / max_over_ranks(1.0 / e2e["value"], world)
         e2e_sync_v = world / max_over_ranks(1.0 / e2e_sync["value"], world)
@@ -646,6 +680,12 @@ def run_ours(args):
                      "api": "tc_process_frame_host, which waits for each frame (its P_t upload overlaps the "
                             "flow network)"},
     }
+    if e2e8 is not None:
+        line["e2e_rgb8"] = {"value": round(e2e8["value"] * (world if world > 1 else 1), 3), "unit": UNIT,
+                            "h2d_bytes_per_step": e2e8["h2d"], "d2h_bytes_per_step": e2e8["d2h"],
+                            "api": "tc_process_frame_host_rgb8_async: 8-bit interleaved RGB frames in and out "
+                                   "(the synthetic frames clipped to [0, 1] and rounded to codes), decoded and "
+                                   "quantised on the device, one tc_synchronize at the end of the timed region"}
     if gemm_peaks:
         line["measured_gemm_peaks"] = gemm_peaks
     if variants:

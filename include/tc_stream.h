@@ -183,6 +183,21 @@ TC_API tc_status tc_process_frame_host(tc_stream *s, const float *I_t, const flo
 TC_API tc_status tc_process_frame_host_async(tc_stream *s, const float *I_t, const float *P_t, float *O_t,
                                              float *wc_opt, uint8_t *mask_opt);
 
+/* tc_process_frame_host_async for 8-bit video frames, the form decoders produce and displays
+ * take (Sec. 3.1: the method reads frames I_t, P_t and returns O_t; the paper fixes no pixel
+ * format, this one moves a quarter of the float32 bytes over the host link).
+ * I_t, P_t: HOST (H, W, 3) interleaved RGB, one byte per channel, row-major; code q stands
+ * for the value q / 255 (IEEE float32 division).  O_t: HOST (H, W, 3) interleaved RGB bytes,
+ * O quantised as floor(255 clamp(O, 0, 1) + 0.5) in float32 (product and sum rounded
+ * separately).  wc_opt, mask_opt: HOST (H, W) float w_c and uint8 mask, or NULL.  Between
+ * the conversions the frame is the one tc_process_frame computes from the decoded values,
+ * so O_t equals the quantised float32 output of tc_process_frame_host_async given the
+ * decoded frames.  Ordering, buffer lifetimes (valid and unmodified until tc_synchronize),
+ * one frame of latency and errors as tc_process_frame_host_async, whose device staging
+ * slots this call shares (the two may be interleaved in one sequence). */
+TC_API tc_status tc_process_frame_host_rgb8_async(tc_stream *s, const uint8_t *I_t, const uint8_t *P_t,
+                                                  uint8_t *O_t, float *wc_opt, uint8_t *mask_opt);
+
 /* Pipelined mode (enable != 0) for sequences whose frames are all resident before they are
  * given: tc_process_frame then enqueues frame t on library-owned streams without ordering it
  * on the caller's stream, so the next frame's feature pyramid and two frames' flow

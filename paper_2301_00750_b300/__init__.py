@@ -37,7 +37,7 @@ EXPORTED = ["tc_default_consistency", "tc_create_stream", "tc_set_consistency", 
             "tc_process_frame_host_async", "tc_set_pipelined", "tc_join", "tc_fp8_scales_from_amax",
             "tc_test_stall_next_convs", "tc_test_fail_device_allocation", "tc_create_batch", "tc_process_lanes",
             "tc_set_lane_consistency", "tc_reset_lane", "tc_get_lane_flows", "tc_set_frame_timing",
-            "tc_get_frame_times"]
+            "tc_get_frame_times", "tc_process_frame_host_rgb8_async"]
 NOALLOC_SCRATCH_BYTES = 16 << 20
 PROFILE_CATEGORIES = ["pyramid_conv", "estimator_conv", "head", "correlation", "warp", "upsample", "consistency",
                       "other", "solver", "refine"]
@@ -64,6 +64,7 @@ _lib.tc_set_consistency.argtypes = [_vp, ctypes.POINTER(TcConsistency)]
 _lib.tc_process_frame.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
 _lib.tc_process_frame_host.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
 _lib.tc_process_frame_host_async.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+_lib.tc_process_frame_host_rgb8_async.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
 _lib.tc_set_pipelined.argtypes = [_vp, _i]
 _lib.tc_join.argtypes = [_vp]
 _lib.tc_get_flows.argtypes = [_vp, _vp, _vp]
@@ -115,7 +116,7 @@ _lib.tc_last_output_frame.argtypes = [_vp]
 _lib.tc_last_output_frame.restype = ctypes.c_longlong
 _lib.tc_op_consistency_next.argtypes = [_vp] * 11 + [_i] * 5 + [ctypes.POINTER(TcConsistency), _vp, _vp, _vp, _vp]
 for _n in ["tc_set_amax_recording", "tc_get_amax", "tc_set_fp8_scales", "tc_fp8_scales_from_amax", "tc_set_graphs", "tc_op_correlation_bf16_noalloc", "tc_synchronize", "tc_set_profiling", "tc_get_profile", "tc_create_stream", "tc_set_consistency", "tc_process_frame", "tc_process_frame_host", "tc_get_flows",
-           "tc_process_frame_host_async", "tc_set_pipelined", "tc_join", "tc_destroy", "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
+           "tc_process_frame_host_async", "tc_process_frame_host_rgb8_async", "tc_set_pipelined", "tc_join", "tc_destroy", "tc_op_conv3x3", "tc_op_correlation", "tc_op_warp_features", "tc_op_upsample_flow",
            "tc_op_consistency", "tc_set_latency", "tc_flush", "tc_op_consistency_next", "tc_op_downscale2",
            "tc_op_sepconv"]:
     getattr(_lib, _n).restype = ctypes.c_int
@@ -233,6 +234,15 @@ class Stream:
         _check(_lib.tc_process_frame_host_async(self._h, _hbuf(I, np.float32), _hbuf(P, np.float32),
                                                 _hbuf(O, np.float32), _hbuf(wc, np.float32),
                                                 _hbuf(mask, np.uint8)), self._h)
+
+    def process_frame_host_rgb8_async(self, I, P, O, wc=None, mask=None):
+        """As process_frame_host_async for 8-bit frames: I, P, O host (H, W, 3) uint8
+        interleaved RGB (code q = value q / 255; O quantised as floor(255 clamp(O, 0, 1) + 0.5)).
+        The buffers (page-locked for the copies to overlap) must stay alive and untouched
+        until synchronize()."""
+        _check(_lib.tc_process_frame_host_rgb8_async(self._h, _hbuf(I, np.uint8), _hbuf(P, np.uint8),
+                                                     _hbuf(O, np.uint8), _hbuf(wc, np.float32),
+                                                     _hbuf(mask, np.uint8)), self._h)
 
     def set_pipelined(self, enable: bool):
         """Pipelined mode: frames are enqueued on the library's own streams with frame t + 1's

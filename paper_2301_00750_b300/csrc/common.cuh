@@ -230,6 +230,10 @@ cudaError_t launch_downscale2(const float *src, int c, int h, int w, float *dst,
 const void *downscale2_kernel_fn();
 cudaError_t launch_flow_out(const float *flow, int fh, int fw, int scale, int H, int W,
                             float *out, cudaStream_t st);
+// Interleaved RGB8 (hw pixels x 3 bytes) -> planar float (3, hw) as q / 255, and back as
+// floor(255 clamp(v, 0, 1) + 0.5).
+cudaError_t launch_unpack_rgb8(const uint8_t *src, size_t hw, float *dst, cudaStream_t st);
+cudaError_t launch_pack_rgb8(const float *src, size_t hw, uint8_t *dst, cudaStream_t st);
 template <typename T>
 cudaError_t launch_amax(const T *base, size_t npix, int cs, int nc, unsigned *slot, cudaStream_t st);
 template <typename T> cudaError_t launch_to_act(const float *in, size_t n, T *out, cudaStream_t st);

@@ -348,6 +348,7 @@ struct tc_stream {
     // stream, and per slot: inputs uploaded, frame done, outputs downloaded
     float *aI[2] = {}, *aP[2] = {}, *aO[2] = {}, *awc[2] = {};
     uint8_t *amask[2] = {};
+    uint8_t *a8I[2] = {}, *a8P[2] = {}, *a8O[2] = {};  // tc_process_frame_host_rgb8_async: 8-bit staging
     cudaStream_t dst = nullptr;
     cudaEvent_t a_in[2] = {}, a_done[2] = {}, a_out[2] = {};
     long long a_n = 0;
@@ -2001,6 +2002,64 @@ extern "C" tc_status tc_process_frame_host_async(tc_stream *s, const float *I_t,
     TC_TRY(s, cudaStreamWaitEvent(s->dst, s->a_done[k], 0), "cudaStreamWaitEvent");
     if (s->last_out >= 0) {  // one frame of latency: the first call of a sequence writes nothing
         TC_TRY(s, cudaMemcpyAsync(O_t, s->aO[k], img, cudaMemcpyDeviceToHost, s->dst), "D2H O_t");
+        if (wc_opt)
+            TC_TRY(s, cudaMemcpyAsync(wc_opt, s->awc[k], plane * sizeof(float), cudaMemcpyDeviceToHost, s->dst),
+                   "D2H w_c");
+        if (mask_opt) TC_TRY(s, cudaMemcpyAsync(mask_opt, s->amask[k], plane, cudaMemcpyDeviceToHost, s->dst), "D2H mask");
+    }
+    TC_TRY(s, cudaEventRecord(s->a_out[k], s->dst), "cudaEventRecord");
+    s->a_n += 1;
+    return TC_OK;
+}
+
+extern "C" tc_status tc_process_frame_host_rgb8_async(tc_stream *s, const uint8_t *I_t, const uint8_t *P_t,
+                                                      uint8_t *O_t, float *wc_opt, uint8_t *mask_opt) {
+    tc_status r = single_only(s, "tc_process_frame_host_rgb8_async");
+    if (r != TC_OK) return r;
+    if (s->pipelined) return fail(s, TC_ERR_STATE, "tc_process_frame_host_rgb8_async: not available in pipelined mode");
+    if (!I_t || !P_t || !O_t)
+        return fail(s, TC_ERR_INVALID_ARG, "tc_process_frame_host_rgb8_async: NULL image pointer");
+    const size_t plane = (size_t)s->H * s->W, img = 3 * plane * sizeof(float), img8 = 3 * plane;
+    if (!s->a8I[0]) {
+        for (int k = 0; k < 2; ++k) {
+            if (!s->aI[k] && (r = dalloc_t(s, &s->aI[k], img)) != TC_OK) return r;
+            if (!s->aP[k] && (r = dalloc_t(s, &s->aP[k], img)) != TC_OK) return r;
+            if (!s->aO[k] && (r = dalloc_t(s, &s->aO[k], img)) != TC_OK) return r;
+            if (!s->awc[k] && (r = dalloc_t(s, &s->awc[k], plane * sizeof(float))) != TC_OK) return r;
+            if (!s->amask[k] && (r = dalloc_t(s, &s->amask[k], plane)) != TC_OK) return r;
+            if ((r = dalloc_t(s, &s->a8I[k], img8)) != TC_OK) return r;
+            if ((r = dalloc_t(s, &s->a8P[k], img8)) != TC_OK) return r;
+            if ((r = dalloc_t(s, &s->a8O[k], img8)) != TC_OK) return r;
+            if (!s->a_in[k]) {
+                TC_TRY(s, cudaEventCreateWithFlags(&s->a_in[k], cudaEventDisableTiming), "cudaEventCreate");
+                TC_TRY(s, cudaEventCreateWithFlags(&s->a_done[k], cudaEventDisableTiming), "cudaEventCreate");
+                TC_TRY(s, cudaEventCreateWithFlags(&s->a_out[k], cudaEventDisableTiming), "cudaEventCreate");
+            }
+        }
+        if (!s->cst) TC_TRY(s, cudaStreamCreateWithFlags(&s->cst, cudaStreamNonBlocking), "cudaStreamCreate");
+        if (!s->dst) TC_TRY(s, cudaStreamCreateWithFlags(&s->dst, cudaStreamNonBlocking), "cudaStreamCreate");
+    }
+    // The same slot rotation as tc_process_frame_host_async (the two share the slots and
+    // their events): 8-bit uploads on cst, the unpack, the frame and the pack on the
+    // stream's CUDA stream, 8-bit downloads on dst.
+    const int k = (int)(s->a_n & 1);
+    TC_TRY(s, cudaStreamWaitEvent(s->cst, s->a_done[k], 0), "cudaStreamWaitEvent");
+    TC_TRY(s, cudaMemcpyAsync(s->a8I[k], I_t, img8, cudaMemcpyHostToDevice, s->cst), "H2D I_t");
+    TC_TRY(s, cudaMemcpyAsync(s->a8P[k], P_t, img8, cudaMemcpyHostToDevice, s->cst), "H2D P_t");
+    TC_TRY(s, cudaEventRecord(s->a_in[k], s->cst), "cudaEventRecord");
+    TC_TRY(s, cudaStreamWaitEvent(s->st, s->a_in[k], 0), "cudaStreamWaitEvent");
+    TC_TRY(s, cudaStreamWaitEvent(s->st, s->a_out[k], 0), "cudaStreamWaitEvent");
+    TC_LAUNCH(s, launch_unpack_rgb8(s->a8I[k], plane, s->aI[k], s->st));
+    TC_LAUNCH(s, launch_unpack_rgb8(s->a8P[k], plane, s->aP[k], s->st));
+    r = tc_process_frame(s, s->aI[k], s->aP[k], s->aO[k], wc_opt ? s->awc[k] : nullptr,
+                         mask_opt ? s->amask[k] : nullptr);
+    if (r != TC_OK) return r;
+    const bool wrote = s->last_out >= 0;  // one frame of latency: the first call writes nothing
+    if (wrote) TC_LAUNCH(s, launch_pack_rgb8(s->aO[k], plane, s->a8O[k], s->st));
+    TC_TRY(s, cudaEventRecord(s->a_done[k], s->st), "cudaEventRecord");
+    TC_TRY(s, cudaStreamWaitEvent(s->dst, s->a_done[k], 0), "cudaStreamWaitEvent");
+    if (wrote) {
+        TC_TRY(s, cudaMemcpyAsync(O_t, s->a8O[k], img8, cudaMemcpyDeviceToHost, s->dst), "D2H O_t");
         if (wc_opt)
             TC_TRY(s, cudaMemcpyAsync(wc_opt, s->awc[k], plane * sizeof(float), cudaMemcpyDeviceToHost, s->dst),
                    "D2H w_c");

@@ -264,6 +264,39 @@ cudaError_t launch_downscale2(const float *src, int c, int h, int w, float *dst,
     return cudaGetLastError();
 }
 
+// 8-bit video frames: interleaved RGB8 (H, W, 3) <-> planar float (3, H, W).  A code q stands
+// for q / 255 (an IEEE division, so host and device agree bit for bit); an output value v
+// is stored as floor(255 clamp(v, 0, 1) + 0.5), with the multiply and the add rounded
+// separately (no contraction), so the host can reproduce it exactly in float32.
+__global__ void unpack_rgb8_kernel(const uint8_t *__restrict__ src, size_t hw, float *__restrict__ dst) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= hw) return;
+    const uint8_t *p = src + 3 * i;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dst[c * hw + i] = __fdiv_rn((float)p[c], 255.f);
+}
+
+__global__ void pack_rgb8_kernel(const float *__restrict__ src, size_t hw, uint8_t *__restrict__ dst) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= hw) return;
+    uint8_t *p = dst + 3 * i;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float v = fminf(fmaxf(src[c * hw + i], 0.f), 1.f);  // NaN -> 0
+        p[c] = (uint8_t)(int)floorf(__fadd_rn(__fmul_rn(v, 255.f), 0.5f));
+    }
+}
+
+cudaError_t launch_unpack_rgb8(const uint8_t *src, size_t hw, float *dst, cudaStream_t st) {
+    unpack_rgb8_kernel<<<(unsigned)((hw + 255) / 256), 256, 0, st>>>(src, hw, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_rgb8(const float *src, size_t hw, uint8_t *dst, cudaStream_t st) {
+    pack_rgb8_kernel<<<(unsigned)((hw + 255) / 256), 256, 0, st>>>(src, hw, dst);
+    return cudaGetLastError();
+}
+
 // Full-resolution flow, cropped to (H, W), planar (2, H, W), from a (fh, fw, 2) field.
 __global__ void flow_out_kernel(const float *F, int fh, int fw, int s, int H, int W, float *out) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
