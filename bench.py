@@ -900,7 +900,8 @@ def serve_load(srv, streams, frames_by_size, rate, seconds, seed, warm=1.0):
                     k = s_["n"] % len(fr)
                     n_tag += 1
                     tag_slot[n_tag] = (s_, slot, s_["next"])
-                    srv.submit(s_["id"], fr[k], st[k], s_["outs"][slot], tag=n_tag)
+                    (srv.submit_rgb8 if s_.get("rgb8") else srv.submit)(s_["id"], fr[k], st[k], s_["outs"][slot],
+                                                                       tag=n_tag)
                     s_["n"] += 1
                 s_["next"] += g.exponential(1.0 / rate)
         for c in srv.poll(timeout_ms=1):
@@ -938,16 +939,24 @@ def run_serve(args):
                     hbm_budget_bytes=int(args.budget_gb * (1 << 30)) if args.budget_gb else 0)
     streams = []
     frames_by_size = {}
+    q8 = lambda a: torch.from_numpy(np.ascontiguousarray(np.moveaxis(
+        np.floor(np.clip(a, 0.0, 1.0) * 255.0 + 0.5).astype(np.uint8), 0, -1))).pin_memory()
     for W, H, count in SERVE_MIX:
         if (W, H) not in frames_by_size:
             fr, st = make_frames(seed=W, n=3, width=W, height=H)
-            frames_by_size[(W, H)] = ([torch.from_numpy(f).pin_memory() for f in fr],
-                                      [torch.from_numpy(p).pin_memory() for p in st])
+            if args.rgb8:  # 8-bit interleaved RGB frames (the synthetic frames clipped and rounded)
+                frames_by_size[(W, H)] = ([q8(f) for f in fr], [q8(p) for p in st])
+            else:
+                frames_by_size[(W, H)] = ([torch.from_numpy(f).pin_memory() for f in fr],
+                                          [torch.from_numpy(p).pin_memory() for p in st])
         for _ in range(count):
             sid = srv.open(W, H)
             srv.set_consistency(sid, k1=0.5)
-            outs = [torch.empty((3, H, W), dtype=torch.float32).pin_memory() for _ in range(args.ring)]
-            streams.append(dict(id=sid, W=W, H=H, outs=outs, n=0))
+            if args.rgb8:
+                outs = [torch.empty((H, W, 3), dtype=torch.uint8).pin_memory() for _ in range(args.ring)]
+            else:
+                outs = [torch.empty((3, H, W), dtype=torch.float32).pin_memory() for _ in range(args.ring)]
+            streams.append(dict(id=sid, W=W, H=H, outs=outs, n=0, rgb8=args.rgb8))
     base = serve_load(srv, streams, frames_by_size, 30.0, args.seconds, 7)
     curve = [base]
     if not args.skip_curve:
@@ -964,8 +973,10 @@ def run_serve(args):
         "capacity_frames_per_s": cap, "load_curve": curve,
         "dtype": {"fp16": "f16", "fp32": "f32"}.get(args.precision, args.precision), "data": "synthetic",
         "workers": args.workers, "batch_lanes": args.batch_lanes,
-        "config": {"workload": "4x640x360, 4x1280x720, 6x1920x1080, 2x2560x1440; host buffers in/out per frame; "
-                               f"{args.ring} output buffers per stream (a frame arriving with none free is skipped)",
+        "config": {"workload": "4x640x360, 4x1280x720, 6x1920x1080, 2x2560x1440; host buffers in/out per frame "
+                               + ("(8-bit interleaved RGB, tc_server_submit_rgb8); " if args.rgb8 else
+                                  "(float32 planar); ")
+                               + f"{args.ring} output buffers per stream (a frame arriving with none free is skipped)",
                    "megapixels_per_round": round(px / 1e6, 2), "seconds": args.seconds},
     }), flush=True)
 
@@ -1196,6 +1207,7 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=0.0)
     ap.add_argument("--batch-lanes", type=int, default=4, help="serving: streams of one size per shared batch")
     ap.add_argument("--skip-curve", action="store_true", help="serving: only the 30 frames/s per stream load")
+    ap.add_argument("--rgb8", action="store_true", help="serving: submit 8-bit interleaved RGB frames")
     ap.add_argument("--train", action="store_true", help="run the training-throughput benchmark instead")
     ap.add_argument("--timeline", action="store_true",
                     help="record the kernel timeline (CUPTI) of the 1080p stream in pipelined and sequential mode")

@@ -476,8 +476,8 @@ typedef struct {
 /* Creates a server and its worker threads on the current device. */
 TC_API tc_status tc_server_create(const tc_server_desc *desc, tc_server **out);
 
-/* Device bytes a batch of width x height (batch_lanes lanes and its staging) holds: the
- * admission charge of a stream that finds no free lane of its size. */
+/* Device bytes a batch of width x height (batch_lanes lanes and its float and 8-bit staging)
+ * holds: the admission charge of a stream that finds no free lane of its size. */
 TC_API size_t tc_server_stream_bytes(const tc_server *srv, int width, int height);
 
 /* Device bytes currently reserved by admitted streams. */
@@ -497,6 +497,13 @@ TC_API tc_status tc_server_set_consistency(tc_server *srv, int stream_id, const 
  * alive and unchanged until then (pinned memory makes the copies faster). */
 TC_API tc_status tc_server_submit(tc_server *srv, int stream_id, const float *I_host, const float *P_host,
                                  float *O_host, unsigned long long tag);
+
+/* tc_server_submit for 8-bit frames: I_host, P_host, O_host are host (H, W, 3) interleaved
+ * RGB bytes, decoded and quantised on the device exactly as tc_process_frame_host_rgb8_async
+ * does (Sec. 3.1 fixes no pixel format; this one moves a quarter of the bytes over the host
+ * link).  A stream may mix both forms of submission.  Same lifetimes and errors. */
+TC_API tc_status tc_server_submit_rgb8(tc_server *srv, int stream_id, const uint8_t *I_host, const uint8_t *P_host,
+                                      uint8_t *O_host, unsigned long long tag);
 
 /* Copies up to max finished frames into out, waiting up to timeout_ms for the first one;
  * returns how many. */

@@ -597,6 +597,7 @@ _lib.tc_server_bytes_in_use.restype = ctypes.c_size_t
 _lib.tc_server_open.argtypes = [_vp, _i, _i, ctypes.POINTER(_i)]
 _lib.tc_server_set_consistency.argtypes = [_vp, _i, ctypes.POINTER(TcConsistency)]
 _lib.tc_server_submit.argtypes = [_vp, _i, _vp, _vp, _vp, ctypes.c_ulonglong]
+_lib.tc_server_submit_rgb8.argtypes = [_vp, _i, _vp, _vp, _vp, ctypes.c_ulonglong]
 _lib.tc_server_poll.argtypes = [_vp, ctypes.POINTER(TcCompletion), _i, _i]
 _lib.tc_server_poll.restype = ctypes.c_int
 _lib.tc_server_cancel.argtypes = [_vp, _i]
@@ -604,11 +605,13 @@ _lib.tc_server_close.argtypes = [_vp, _i]
 _lib.tc_server_destroy.argtypes = [_vp]
 _lib.tc_stream_device_bytes.argtypes = [_vp]
 _lib.tc_stream_device_bytes.restype = ctypes.c_size_t
-for _n in ["tc_server_create", "tc_server_open", "tc_server_set_consistency", "tc_server_submit", "tc_server_cancel",
+for _n in ["tc_server_create", "tc_server_open", "tc_server_set_consistency", "tc_server_submit",
+           "tc_server_submit_rgb8", "tc_server_cancel",
            "tc_server_close", "tc_server_destroy"]:
     getattr(_lib, _n).restype = ctypes.c_int
 EXPORTED += ["tc_server_create", "tc_server_stream_bytes", "tc_server_bytes_in_use", "tc_server_open",
-             "tc_server_set_consistency", "tc_server_submit", "tc_server_poll", "tc_server_cancel",
+             "tc_server_set_consistency", "tc_server_submit", "tc_server_submit_rgb8", "tc_server_poll",
+             "tc_server_cancel",
              "tc_server_close", "tc_server_destroy", "tc_stream_device_bytes"]
 
 
@@ -659,6 +662,13 @@ class Server:
     def submit(self, stream_id, I, P, O, tag=0):
         self._keep[(stream_id, tag)] = (I, P, O)
         _check(_lib.tc_server_submit(self._h, stream_id, _host_ptr(I), _host_ptr(P), _host_ptr(O), tag))
+
+    def submit_rgb8(self, stream_id, I, P, O, tag=0):
+        """The next frame as 8-bit interleaved RGB: I, P, O host (H, W, 3) uint8 (as
+        Stream.process_frame_host_rgb8_async)."""
+        self._keep[(stream_id, tag)] = (I, P, O)
+        _check(_lib.tc_server_submit_rgb8(self._h, stream_id, _hbuf(I, np.uint8), _hbuf(P, np.uint8),
+                                          _hbuf(O, np.uint8), tag))
 
     def poll(self, max_n=256, timeout_ms=100):
         buf = (TcCompletion * max_n)()

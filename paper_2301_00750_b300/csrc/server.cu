@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/tc_stream.h"
+#include "common.cuh"
 #include "engine_internal.h"
 
 namespace {
@@ -35,12 +36,13 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 struct Request {
-    const float *I;
-    const float *P;
-    float *O;
+    const void *I;  // float32 planar, or RGB8 interleaved when rgb8
+    const void *P;
+    void *O;
     unsigned long long tag;
     long long frame;
     double t_submit;
+    bool rgb8 = false;
 };
 
 struct Group;
@@ -63,6 +65,7 @@ struct Group {
     tc_stream *b = nullptr;  // NULL while being created
     cudaStream_t cs = nullptr;
     float *stage = nullptr;  // device staging [3][lanes][3][H][W]: I, P, O
+    uint8_t *stage8 = nullptr;  // 8-bit frames: [3][lanes][H][W][3] RGB8 I, P, O
     std::vector<Slot *> lane_slot;  // NULL = free lane
     bool busy = false;
     int open_slots() const {
@@ -94,8 +97,9 @@ struct tc_server {
     double now_us() const { return std::chrono::duration<double, std::micro>(Clock::now() - t0).count(); }
 
     size_t group_bytes(int W, int H) const {
-        const size_t img = (size_t)3 * W * H * sizeof(float);
-        return tc::stream_device_bytes(net, W, H, desc.precision, 1, lanes) + ((3 * lanes * img + 511) & ~(size_t)511);
+        const size_t img = (size_t)3 * W * H * sizeof(float), img8 = (size_t)3 * W * H;
+        return tc::stream_device_bytes(net, W, H, desc.precision, 1, lanes) + ((3 * lanes * img + 511) & ~(size_t)511) +
+               ((3 * lanes * img8 + 511) & ~(size_t)511);
     }
 
     // The idle group holding the oldest queued frame (FIFO across groups).
@@ -164,17 +168,28 @@ struct tc_server {
     // One batched step of a group (no lock held): every item's lane gets its frame.
     template <typename Item>
     tc_status run_step(Group *g, const std::vector<Item> &items) {
-        const size_t img = (size_t)3 * g->W * g->H;
+        const size_t img = (size_t)3 * g->W * g->H, plane = (size_t)g->W * g->H;
         float *dI = g->stage, *dP = g->stage + g->lanes * img, *dO = g->stage + 2 * g->lanes * img;
+        uint8_t *bI = g->stage8, *bP = g->stage8 + g->lanes * img, *bO = g->stage8 + 2 * g->lanes * img;
         tc_status st = TC_OK;
         for (const Item &it : items) {
             const int l = it.s->lane;
             if (st == TC_OK && it.reset) st = tc_reset_lane(g->b, l);
             if (st == TC_OK && it.dirty) st = tc_set_lane_consistency(g->b, l, &it.prm);
-            if (st == TC_OK && (cudaMemcpyAsync(dI + l * img, it.rq.I, img * sizeof(float), cudaMemcpyHostToDevice,
-                                                g->cs) != cudaSuccess ||
-                                cudaMemcpyAsync(dP + l * img, it.rq.P, img * sizeof(float), cudaMemcpyHostToDevice,
-                                                g->cs) != cudaSuccess)) {
+            if (st != TC_OK) continue;
+            cudaError_t e;
+            if (it.rq.rgb8) {
+                // 8-bit frames: upload the codes, decode them into the lane's float staging
+                e = cudaMemcpyAsync(bI + l * img, it.rq.I, img, cudaMemcpyHostToDevice, g->cs);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(bP + l * img, it.rq.P, img, cudaMemcpyHostToDevice, g->cs);
+                if (e == cudaSuccess) e = tc::launch_unpack_rgb8(bI + l * img, plane, dI + l * img, g->cs);
+                if (e == cudaSuccess) e = tc::launch_unpack_rgb8(bP + l * img, plane, dP + l * img, g->cs);
+            } else {
+                e = cudaMemcpyAsync(dI + l * img, it.rq.I, img * sizeof(float), cudaMemcpyHostToDevice, g->cs);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(dP + l * img, it.rq.P, img * sizeof(float), cudaMemcpyHostToDevice, g->cs);
+            }
+            if (e != cudaSuccess) {
                 cudaGetLastError();
                 st = tc_record_error(TC_ERR_CUDA, "server: upload failed");
             }
@@ -198,12 +213,21 @@ struct tc_server {
             st = tc_process_lanes(g->b, (int)(k1 - k0), ls.data() + k0, I.data(), P.data(), O.data(), nullptr, nullptr);
             k0 = k1;
         }
-        for (const Item &it : items)
-            if (st == TC_OK && cudaMemcpyAsync(it.rq.O, dO + it.s->lane * img, img * sizeof(float),
-                                               cudaMemcpyDeviceToHost, g->cs) != cudaSuccess) {
+        for (const Item &it : items) {
+            if (st != TC_OK) break;
+            const int l = it.s->lane;
+            cudaError_t e;
+            if (it.rq.rgb8) {
+                e = tc::launch_pack_rgb8(dO + l * img, plane, bO + l * img, g->cs);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(it.rq.O, bO + l * img, img, cudaMemcpyDeviceToHost, g->cs);
+            } else {
+                e = cudaMemcpyAsync(it.rq.O, dO + l * img, img * sizeof(float), cudaMemcpyDeviceToHost, g->cs);
+            }
+            if (e != cudaSuccess) {
                 cudaGetLastError();
                 st = tc_record_error(TC_ERR_CUDA, "server: download failed");
             }
+        }
         const tc_status ss = tc_synchronize(g->b);
         return st != TC_OK ? st : ss;
     }
@@ -214,6 +238,7 @@ static tc_status srv_fail(tc_status code, const std::string &msg) { return tc_re
 static void destroy_group(Group *g) {
     if (g->b) tc_destroy(g->b);
     if (g->stage) cudaFree(g->stage);
+    if (g->stage8) cudaFree(g->stage8);
     if (g->cs) cudaStreamDestroy(g->cs);
     delete g;
 }
@@ -343,6 +368,11 @@ extern "C" tc_status tc_server_open(tc_server *srv, int width, int height, int *
             fresh->stage = nullptr;
             st = srv_fail(TC_ERR_OOM, "tc_server_open: staging allocation failed");
         }
+        if (st == TC_OK && cudaMalloc(&fresh->stage8, 3 * fresh->lanes * (img / sizeof(float))) != cudaSuccess) {
+            cudaGetLastError();
+            fresh->stage8 = nullptr;
+            st = srv_fail(TC_ERR_OOM, "tc_server_open: staging allocation failed");
+        }
         tc_stream *b = nullptr;
         if (st == TC_OK) {
             tc_stream_desc d{};
@@ -384,18 +414,28 @@ extern "C" tc_status tc_server_set_consistency(tc_server *srv, int stream_id, co
     return TC_OK;
 }
 
-extern "C" tc_status tc_server_submit(tc_server *srv, int stream_id, const float *I_host, const float *P_host,
-                                      float *O_host, unsigned long long tag) {
-    if (!srv || !I_host || !P_host || !O_host) return srv_fail(TC_ERR_INVALID_ARG, "tc_server_submit: NULL argument");
+static tc_status submit(tc_server *srv, int stream_id, const void *I_host, const void *P_host, void *O_host,
+                        unsigned long long tag, bool rgb8, const char *fn) {
+    if (!srv || !I_host || !P_host || !O_host) return srv_fail(TC_ERR_INVALID_ARG, std::string(fn) + ": NULL argument");
     std::lock_guard<std::mutex> lk(srv->mu);
     auto it = srv->slots.find(stream_id);
     if (it == srv->slots.end() || !it->second->g->b)
-        return srv_fail(TC_ERR_INVALID_ARG, "tc_server_submit: unknown stream");
+        return srv_fail(TC_ERR_INVALID_ARG, std::string(fn) + ": unknown stream");
     Slot *sl = it->second;
-    if (sl->closing) return srv_fail(TC_ERR_STATE, "tc_server_submit: stream is closing");
-    sl->q.push_back(Request{I_host, P_host, O_host, tag, sl->next_frame++, srv->now_us()});
+    if (sl->closing) return srv_fail(TC_ERR_STATE, std::string(fn) + ": stream is closing");
+    sl->q.push_back(Request{I_host, P_host, O_host, tag, sl->next_frame++, srv->now_us(), rgb8});
     srv->cv_work.notify_one();
     return TC_OK;
+}
+
+extern "C" tc_status tc_server_submit(tc_server *srv, int stream_id, const float *I_host, const float *P_host,
+                                      float *O_host, unsigned long long tag) {
+    return submit(srv, stream_id, I_host, P_host, O_host, tag, false, "tc_server_submit");
+}
+
+extern "C" tc_status tc_server_submit_rgb8(tc_server *srv, int stream_id, const uint8_t *I_host, const uint8_t *P_host,
+                                           uint8_t *O_host, unsigned long long tag) {
+    return submit(srv, stream_id, I_host, P_host, O_host, tag, true, "tc_server_submit_rgb8");
 }
 
 extern "C" int tc_server_poll(tc_server *srv, tc_completion *out, int max, int timeout_ms) {

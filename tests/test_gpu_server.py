@@ -152,3 +152,49 @@ def test_cancel_drops_queued_frames_in_order():
     assert sorted(c["frame"] for c in dropped) == list(range(len(ok), 12))
     srv.close(sid)
     srv.destroy()
+
+
+def test_rgb8_submissions_equal_a_plain_stream_quantised():
+    """8-bit submissions (tc_server_submit_rgb8), batched with a stream of the same size that
+    submits float32 frames: each 8-bit stream's outputs equal a plain stream's float32
+    outputs on the decoded frames, quantised (floor(255 clamp(O, 0, 1) + 0.5) in float32), and
+    the float32 stream in the same batch is unchanged."""
+    import torch
+    path, _ = weights_file(*NET)
+    W, H = 320, 200
+    q8 = lambda a: np.ascontiguousarray(np.moveaxis(
+        np.floor(np.clip(np.asarray(a, np.float64), 0.0, 1.0) * 255.0 + 0.5).astype(np.uint8), 0, -1))
+    dec = lambda q: np.ascontiguousarray(np.moveaxis(q, -1, 0).astype(np.float32) / np.float32(255.0))
+    quant = lambda O: np.ascontiguousarray(np.moveaxis(np.floor(
+        np.clip(O, np.float32(0), np.float32(1)) * np.float32(255.0) + np.float32(0.5)).astype(np.uint8), 0, -1))
+    seqs = {k: _frames(W, H, 40 + k, N_FRAMES) for k in range(3)}
+    rgb = {k: ([q8(a) for a in seqs[k][0]], [q8(a) for a in seqs[k][1]]) for k in (0, 1)}
+
+    def plain(I, P):
+        s = tc.Stream(W, H, "bf16", weights_path=path)
+        O = torch.empty((3, H, W), device="cuda")
+        out = []
+        for a, b in zip(I, P):
+            s.process_frame(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), O)
+            out.append(O.cpu().numpy())
+        s.destroy()
+        return out
+
+    want8 = {k: [quant(O) for O in plain([dec(q) for q in rgb[k][0]], [dec(q) for q in rgb[k][1]])] for k in (0, 1)}
+    want32 = plain(*seqs[2])
+    srv = tc.Server(path, precision="bf16", workers=2, batch_lanes=4)
+    sids = {k: srv.open(W, H) for k in range(3)}
+    got8 = {k: [np.zeros((H, W, 3), np.uint8) for _ in range(N_FRAMES)] for k in (0, 1)}
+    got32 = [np.zeros((3, H, W), np.float32) for _ in range(N_FRAMES)]
+    for t in range(N_FRAMES):
+        for k in (0, 1):
+            srv.submit_rgb8(sids[k], rgb[k][0][t], rgb[k][1][t], got8[k][t], tag=10 * k + t)
+        srv.submit(sids[2], seqs[2][0][t], seqs[2][1][t], got32[t], tag=100 + t)
+    done = _drain(srv, 3 * N_FRAMES)
+    srv.destroy()
+    assert len(done) == 3 * N_FRAMES and all(c["status"] == 0 for c in done)
+    for k in (0, 1):
+        for t in range(N_FRAMES):
+            assert np.array_equal(got8[k][t], want8[k][t]), (k, t)
+    for t in range(N_FRAMES):
+        assert np.array_equal(got32[t], want32[t]), t
