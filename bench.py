@@ -311,17 +311,20 @@ def pipelined_value(entry, res, n):
 
 
 def e2e_host(tc, torch, path, frames, styl, precision, steps, warmup, scales=None, solver_iters=0, latency=0,
-             flow_downscale=1, pipelined=False):
+             flow_downscale=1, pipelined=False, pipe_mode=False):
     """End-to-end through the host-buffer entry points: pinned host I_t, P_t in, O_t out per
     frame.  pipelined: tc_process_frame_host_async for every frame (uploads, kernels and
     downloads of neighbouring frames overlap; four output buffers in rotation) and one
     tc_synchronize inside the timed region; else tc_process_frame_host, which waits for
-    each frame."""
+    each frame.  pipe_mode: the stream in pipelined mode (tc_set_pipelined), with the async
+    call only."""
     H, W = frames[0].shape[1:]
     s = open_stream(tc, path, W, H, precision, scales, flow_downscale)
     if latency:
         s.set_consistency(**consistency_controls(0, solver_iters, latency))
         s.set_latency(latency)
+    if pipe_mode:
+        s.set_pipelined(True)
     hI = [torch.from_numpy(f).pin_memory() for f in frames]
     hP = [torch.from_numpy(p).pin_memory() for p in styl]
     hO = [torch.empty((3, H, W), dtype=torch.float32).pin_memory() for _ in range(4 if pipelined else 1)]
@@ -346,7 +349,7 @@ def e2e_host(tc, torch, path, frames, styl, precision, steps, warmup, scales=Non
     return dict(value=steps / dt, h2d=2 * img, d2h=img)
 
 
-def e2e_host_rgb8(tc, torch, path, frames, styl, precision, steps, warmup, scales=None):
+def e2e_host_rgb8(tc, torch, path, frames, styl, precision, steps, warmup, scales=None, pipe_mode=False):
     """End-to-end with 8-bit video frames (tc_process_frame_host_rgb8_async): the synthetic
     frames clipped to [0, 1] and rounded to interleaved RGB8 codes, uploaded, decoded on the
     device, run, and O_t quantised and downloaded as RGB8; one tc_synchronize inside the timed
@@ -357,6 +360,8 @@ def e2e_host_rgb8(tc, torch, path, frames, styl, precision, steps, warmup, scale
     hI, hP = [q8(f) for f in frames], [q8(p) for p in styl]
     hO = [torch.empty((H, W, 3), dtype=torch.uint8).pin_memory() for _ in range(4)]
     s = open_stream(tc, path, W, H, precision, scales)
+    if pipe_mode:
+        s.set_pipelined(True)
     step = 0
     for _ in range(warmup):
         i = frame_order(step)
@@ -568,7 +573,7 @@ def run_ours(args):
                             solver_iters=50, flow_downscale=2, pipelined=True))
     e2e = e2e_host(tc, torch, path, frames, styl, args.precision, max(3, min(args.steps, 100)), 3, scales=scales,
                    solver_iters=args.solver_iters, latency=args.latency, flow_downscale=args.flow_downscale,
-                   pipelined=True)
+                   pipelined=True, pipe_mode=not args.sequential)
     e2e_sync = e2e_host(tc, torch, path, frames, styl, args.precision, max(3, min(args.steps, 50)), 2,
                         scales=scales, solver_iters=args.solver_iters, latency=args.latency,
                         flow_downscale=args.flow_downscale)
@@ -578,7 +583,7 @@ def run_ours(args):
     e2e8 = None
     if not args.latency and not args.solver_iters and args.flow_downscale == 1:
         e2e8 = e2e_host_rgb8(tc, torch, path, frames, styl, args.precision, max(3, min(args.steps, 100)), 3,
-                             scales=scales)
+                             scales=scales, pipe_mode=not args.sequential)
     if world > 1:
         e2e_v = world / max_over_ranks(1.0 / e2e["value"], world)
         e2e_sync_v = world / max_over_ranks(1.0 / e2e_sync["value"], world)
@@ -670,7 +675,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
                 "api": "tc_process_frame_host_async for every frame from pinned host memory, one "
                        "tc_synchronize at the end of the timed region (uploads and downloads overlap the "
-                       "neighbouring frames' kernels)",
+                       "neighbouring frames' kernels)" + ("" if args.sequential else "; the stream in pipelined mode"),
                 "link": dict(link, frac=round(e2e["value"] / link["frames_per_s_bound"], 4),
                              note="host link roofline of this copy pattern, measured in this run with pinned "
                                   "buffers: 1 / max(H2D time of I_t + P_t, D2H time of O_t), the two directions "
@@ -685,7 +690,8 @@ def run_ours(args):
                             "h2d_bytes_per_step": e2e8["h2d"], "d2h_bytes_per_step": e2e8["d2h"],
                             "api": "tc_process_frame_host_rgb8_async: 8-bit interleaved RGB frames in and out "
                                    "(the synthetic frames clipped to [0, 1] and rounded to codes), decoded and "
-                                   "quantised on the device, one tc_synchronize at the end of the timed region"}
+                                   "quantised on the device, one tc_synchronize at the end of the timed region"
+                                   + ("" if args.sequential else "; the stream in pipelined mode")}
     if gemm_peaks:
         line["measured_gemm_peaks"] = gemm_peaks
     if variants:

@@ -205,9 +205,12 @@ TC_API tc_status tc_process_frame_host_rgb8_async(tc_stream *s, const uint8_t *I
  * the stream keeps four pyramid slots and two sets of estimator and refinement buffers).  The inputs must be
  * valid when tc_process_frame is called and stay unmodified until the frame is done; the
  * outputs are valid after tc_join (the caller's stream then waits for every frame given)
- * or tc_synchronize.  tc_get_flows joins first; tc_flush runs after the frames given.  The
- * host entry points and amax recording are not available in this mode.  Only before the
- * first frame of a sequence; results equal those of the default mode bit for bit.
+ * or tc_synchronize.  tc_get_flows joins first; tc_flush runs after the frames given.
+ * tc_process_frame_host_async and tc_process_frame_host_rgb8_async work in this mode too
+ * (four device staging slots; each call's upload is fenced to the frame's pyramid and blend
+ * streams and its download to the blend); tc_process_frame_host and amax recording do not.
+ * Only before the first frame of a sequence; results equal those of the default mode bit
+ * for bit.
  * Errors: TC_ERR_STATE (after the first frame of a sequence, or while recording amax). */
 TC_API tc_status tc_set_pipelined(tc_stream *s, int enable);
 

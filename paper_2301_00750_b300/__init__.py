@@ -248,8 +248,8 @@ class Stream:
         """Pipelined mode: frames are enqueued on the library's own streams with frame t + 1's
         pyramid overlapping the flow estimation of frames t and t - 1 (two estimator buffer
         sets); inputs must be valid at the call and
-        stay unmodified, outputs are valid after join() or synchronize().  Only before the
-        first frame of a sequence."""
+        stay unmodified, outputs are valid after join() or synchronize().  The asynchronous
+        host-buffer calls work in this mode too.  Only before the first frame of a sequence."""
         _check(_lib.tc_set_pipelined(self._h, int(bool(enable))), self._h)
 
     def join(self):

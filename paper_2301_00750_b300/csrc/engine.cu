@@ -346,11 +346,14 @@ struct tc_stream {
     bool capturing = false;  // frame_launches is being captured into a graph
     // tc_process_frame_host_async: device staging per slot (call parity), the download
     // stream, and per slot: inputs uploaded, frame done, outputs downloaded
-    float *aI[2] = {}, *aP[2] = {}, *aO[2] = {}, *awc[2] = {};
-    uint8_t *amask[2] = {};
-    uint8_t *a8I[2] = {}, *a8P[2] = {}, *a8O[2] = {};  // tc_process_frame_host_rgb8_async: 8-bit staging
+    // (two slots in the default mode, four in pipelined mode, where the inputs of the next
+    // frames' pyramids and of the frames still blending are alive at once)
+    static constexpr int NSLOT = 4;
+    float *aI[NSLOT] = {}, *aP[NSLOT] = {}, *aO[NSLOT] = {}, *awc[NSLOT] = {};
+    uint8_t *amask[NSLOT] = {};
+    uint8_t *a8I[NSLOT] = {}, *a8P[NSLOT] = {}, *a8O[NSLOT] = {};  // tc_process_frame_host_rgb8_async: 8-bit staging
     cudaStream_t dst = nullptr;
-    cudaEvent_t a_in[2] = {}, a_done[2] = {}, a_out[2] = {};
+    cudaEvent_t a_in[NSLOT] = {}, a_done[NSLOT] = {}, a_out[NSLOT] = {};
     long long a_n = 0;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // capture: the wait on ev_p as a side branch
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;  // fence gst to the caller's stream
@@ -1438,14 +1441,9 @@ static tc_status process(tc_stream *s, const float *I, const float *P, float *O,
 //     follows frame t - NSET's estimation on its stream;
 //   * the blend of frame t waits for its flow estimation and follows frame t - 1's blend.
 // So the next frame's pyramid and NSET frames' flow estimations run at the same time.
-template <typename T>
-static tc_status process_pipelined(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask) {
+// The library streams and event rings of the pipelined mode, created on first use.
+static tc_status ensure_pipeline_streams(tc_stream *s) {
     constexpr int NEV = tc_stream::NEV;
-    tc_status r;
-    const long long t = s->t;
-    const int cur = (int)(t & 1), ps = pyr_slot(s, t), set = est_set(s, t), e = (int)(t % NEV);
-    const int nsets = NSET;
-    const long long out = s->latency ? t - 1 : t;
     if (!s->gst) {
         TC_TRY(s, cudaStreamCreateWithFlags(&s->gst, cudaStreamNonBlocking), "cudaStreamCreate");
         TC_TRY(s, cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming), "cudaEventCreate");
@@ -1461,6 +1459,18 @@ static tc_status process_pipelined(tc_stream *s, const float *I, const float *P,
             TC_TRY(s, cudaEventCreateWithFlags(&s->ev_blends[j], cudaEventDisableTiming), "cudaEventCreate");
         }
     }
+    return TC_OK;
+}
+
+template <typename T>
+static tc_status process_pipelined(tc_stream *s, const float *I, const float *P, float *O, float *wc, uint8_t *mask) {
+    constexpr int NEV = tc_stream::NEV;
+    tc_status r;
+    const long long t = s->t;
+    const int cur = (int)(t & 1), ps = pyr_slot(s, t), set = est_set(s, t), e = (int)(t % NEV);
+    const int nsets = NSET;
+    const long long out = s->latency ? t - 1 : t;
+    if ((r = ensure_pipeline_streams(s)) != TC_OK) return r;
     cudaStream_t es = set == 0 ? s->gst : s->estx[set - 1];
     // pyramid t: after everything before the sequence, or after the estimations that read
     // its slot last (frames t - NPYR and t - NPYR + 1)
@@ -1964,15 +1974,22 @@ extern "C" tc_status tc_synchronize(tc_stream *s) {
     return check_device_error(s);
 }
 
-extern "C" tc_status tc_process_frame_host_async(tc_stream *s, const float *I_t, const float *P_t, float *O_t,
-                                                 float *wc_opt, uint8_t *mask_opt) {
-    tc_status r = single_only(s, "tc_process_frame_host_async");
+// tc_process_frame_host_async and its 8-bit form.  Slot k of the device staging holds one
+// call's inputs and outputs: two slots used in turn in the default mode, four in pipelined
+// mode.  Copies run on two library streams: uploads on cst (with the 8-bit decode), downloads
+// on dst.  Default mode: the frame runs on the stream's CUDA stream after the upload.
+// Pipelined mode: the frame's pyramid (pst) and blend (bst) wait for the upload, and the
+// blend also for the download that last read the slot's outputs; the slot's next upload waits
+// for the blend (its last reader).  Either way the download follows the frame's last step.
+static tc_status host_async(tc_stream *s, const void *I_t, const void *P_t, void *O_t, float *wc_opt,
+                            uint8_t *mask_opt, bool rgb8, const char *fn) {
+    tc_status r = single_only(s, fn);
     if (r != TC_OK) return r;
-    if (s->pipelined) return fail(s, TC_ERR_STATE, "tc_process_frame_host_async: not available in pipelined mode");
-    if (!I_t || !P_t || !O_t) return fail(s, TC_ERR_INVALID_ARG, "tc_process_frame_host_async: NULL image pointer");
-    const size_t img = (size_t)3 * s->H * s->W * sizeof(float), plane = (size_t)s->H * s->W;
-    if (!s->aI[0]) {
-        for (int k = 0; k < 2; ++k) {
+    if (!I_t || !P_t || !O_t) return fail(s, TC_ERR_INVALID_ARG, std::string(fn) + ": NULL image pointer");
+    const size_t plane = (size_t)s->H * s->W, img = 3 * plane * sizeof(float), img8 = 3 * plane;
+    const int nslot = s->pipelined ? tc_stream::NSLOT : 2;
+    for (int k = 0; k < nslot; ++k) {
+        if (!s->aI[k]) {
             if ((r = dalloc_t(s, &s->aI[k], img)) != TC_OK) return r;
             if ((r = dalloc_t(s, &s->aP[k], img)) != TC_OK) return r;
             if ((r = dalloc_t(s, &s->aO[k], img)) != TC_OK) return r;
@@ -1982,26 +1999,60 @@ extern "C" tc_status tc_process_frame_host_async(tc_stream *s, const float *I_t,
             TC_TRY(s, cudaEventCreateWithFlags(&s->a_done[k], cudaEventDisableTiming), "cudaEventCreate");
             TC_TRY(s, cudaEventCreateWithFlags(&s->a_out[k], cudaEventDisableTiming), "cudaEventCreate");
         }
-        if (!s->cst) TC_TRY(s, cudaStreamCreateWithFlags(&s->cst, cudaStreamNonBlocking), "cudaStreamCreate");
-        TC_TRY(s, cudaStreamCreateWithFlags(&s->dst, cudaStreamNonBlocking), "cudaStreamCreate");
+        if (rgb8 && !s->a8I[k]) {
+            if ((r = dalloc_t(s, &s->a8I[k], img8)) != TC_OK) return r;
+            if ((r = dalloc_t(s, &s->a8P[k], img8)) != TC_OK) return r;
+            if ((r = dalloc_t(s, &s->a8O[k], img8)) != TC_OK) return r;
+        }
     }
-    const int k = (int)(s->a_n & 1);
-    // Slot k was last used two calls ago: its frame read aI[k], aP[k] (a_done[k]) and its
-    // download read aO[k], awc[k], amask[k] (a_out[k]).  A wait on an event not yet
-    // recorded returns at once.
+    if (!s->cst) TC_TRY(s, cudaStreamCreateWithFlags(&s->cst, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (!s->dst) TC_TRY(s, cudaStreamCreateWithFlags(&s->dst, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (s->pipelined && (r = ensure_pipeline_streams(s)) != TC_OK) return r;
+    const int k = (int)(s->a_n % nslot);
+    // Slot k was last used nslot calls ago: a_done[k] marks the end of that frame's last step
+    // (the last reader of aI[k], aP[k]), a_out[k] the end of its download (the last reader of
+    // aO[k], awc[k], amask[k]).  A wait on an event not yet recorded returns at once.
     TC_TRY(s, cudaStreamWaitEvent(s->cst, s->a_done[k], 0), "cudaStreamWaitEvent");
-    TC_TRY(s, cudaMemcpyAsync(s->aI[k], I_t, img, cudaMemcpyHostToDevice, s->cst), "H2D I_t");
-    TC_TRY(s, cudaMemcpyAsync(s->aP[k], P_t, img, cudaMemcpyHostToDevice, s->cst), "H2D P_t");
+    if (rgb8) {
+        TC_TRY(s, cudaMemcpyAsync(s->a8I[k], I_t, img8, cudaMemcpyHostToDevice, s->cst), "H2D I_t");
+        TC_TRY(s, cudaMemcpyAsync(s->a8P[k], P_t, img8, cudaMemcpyHostToDevice, s->cst), "H2D P_t");
+        cudaStream_t st = s->st;
+        s->st = s->cst;
+        TC_LAUNCH(s, launch_unpack_rgb8(s->a8I[k], plane, s->aI[k], s->cst));
+        TC_LAUNCH(s, launch_unpack_rgb8(s->a8P[k], plane, s->aP[k], s->cst));
+        s->st = st;
+    } else {
+        TC_TRY(s, cudaMemcpyAsync(s->aI[k], I_t, img, cudaMemcpyHostToDevice, s->cst), "H2D I_t");
+        TC_TRY(s, cudaMemcpyAsync(s->aP[k], P_t, img, cudaMemcpyHostToDevice, s->cst), "H2D P_t");
+    }
     TC_TRY(s, cudaEventRecord(s->a_in[k], s->cst), "cudaEventRecord");
-    TC_TRY(s, cudaStreamWaitEvent(s->st, s->a_in[k], 0), "cudaStreamWaitEvent");
-    TC_TRY(s, cudaStreamWaitEvent(s->st, s->a_out[k], 0), "cudaStreamWaitEvent");
+    // the streams that read the slot: the frame's stream, or the pyramid and blend streams
+    cudaStream_t last = s->pipelined ? s->bst : s->st;
+    if (s->pipelined) {
+        TC_TRY(s, cudaStreamWaitEvent(s->pst, s->a_in[k], 0), "cudaStreamWaitEvent");
+        TC_TRY(s, cudaStreamWaitEvent(s->bst, s->a_in[k], 0), "cudaStreamWaitEvent");
+        TC_TRY(s, cudaStreamWaitEvent(s->bst, s->a_out[k], 0), "cudaStreamWaitEvent");
+    } else {
+        TC_TRY(s, cudaStreamWaitEvent(s->st, s->a_in[k], 0), "cudaStreamWaitEvent");
+        TC_TRY(s, cudaStreamWaitEvent(s->st, s->a_out[k], 0), "cudaStreamWaitEvent");
+    }
     r = tc_process_frame(s, s->aI[k], s->aP[k], s->aO[k], wc_opt ? s->awc[k] : nullptr,
                          mask_opt ? s->amask[k] : nullptr);
     if (r != TC_OK) return r;
-    TC_TRY(s, cudaEventRecord(s->a_done[k], s->st), "cudaEventRecord");
+    const bool wrote = s->last_out >= 0;  // one frame of latency: the first call of a sequence writes nothing
+    if (rgb8 && wrote) {
+        cudaStream_t st = s->st;
+        s->st = last;
+        TC_LAUNCH(s, launch_pack_rgb8(s->aO[k], plane, s->a8O[k], last));
+        s->st = st;
+    }
+    TC_TRY(s, cudaEventRecord(s->a_done[k], last), "cudaEventRecord");
     TC_TRY(s, cudaStreamWaitEvent(s->dst, s->a_done[k], 0), "cudaStreamWaitEvent");
-    if (s->last_out >= 0) {  // one frame of latency: the first call of a sequence writes nothing
-        TC_TRY(s, cudaMemcpyAsync(O_t, s->aO[k], img, cudaMemcpyDeviceToHost, s->dst), "D2H O_t");
+    if (wrote) {
+        if (rgb8)
+            TC_TRY(s, cudaMemcpyAsync(O_t, s->a8O[k], img8, cudaMemcpyDeviceToHost, s->dst), "D2H O_t");
+        else
+            TC_TRY(s, cudaMemcpyAsync(O_t, s->aO[k], img, cudaMemcpyDeviceToHost, s->dst), "D2H O_t");
         if (wc_opt)
             TC_TRY(s, cudaMemcpyAsync(wc_opt, s->awc[k], plane * sizeof(float), cudaMemcpyDeviceToHost, s->dst),
                    "D2H w_c");
@@ -2012,62 +2063,14 @@ extern "C" tc_status tc_process_frame_host_async(tc_stream *s, const float *I_t,
     return TC_OK;
 }
 
+extern "C" tc_status tc_process_frame_host_async(tc_stream *s, const float *I_t, const float *P_t, float *O_t,
+                                                 float *wc_opt, uint8_t *mask_opt) {
+    return host_async(s, I_t, P_t, O_t, wc_opt, mask_opt, false, "tc_process_frame_host_async");
+}
+
 extern "C" tc_status tc_process_frame_host_rgb8_async(tc_stream *s, const uint8_t *I_t, const uint8_t *P_t,
                                                       uint8_t *O_t, float *wc_opt, uint8_t *mask_opt) {
-    tc_status r = single_only(s, "tc_process_frame_host_rgb8_async");
-    if (r != TC_OK) return r;
-    if (s->pipelined) return fail(s, TC_ERR_STATE, "tc_process_frame_host_rgb8_async: not available in pipelined mode");
-    if (!I_t || !P_t || !O_t)
-        return fail(s, TC_ERR_INVALID_ARG, "tc_process_frame_host_rgb8_async: NULL image pointer");
-    const size_t plane = (size_t)s->H * s->W, img = 3 * plane * sizeof(float), img8 = 3 * plane;
-    if (!s->a8I[0]) {
-        for (int k = 0; k < 2; ++k) {
-            if (!s->aI[k] && (r = dalloc_t(s, &s->aI[k], img)) != TC_OK) return r;
-            if (!s->aP[k] && (r = dalloc_t(s, &s->aP[k], img)) != TC_OK) return r;
-            if (!s->aO[k] && (r = dalloc_t(s, &s->aO[k], img)) != TC_OK) return r;
-            if (!s->awc[k] && (r = dalloc_t(s, &s->awc[k], plane * sizeof(float))) != TC_OK) return r;
-            if (!s->amask[k] && (r = dalloc_t(s, &s->amask[k], plane)) != TC_OK) return r;
-            if ((r = dalloc_t(s, &s->a8I[k], img8)) != TC_OK) return r;
-            if ((r = dalloc_t(s, &s->a8P[k], img8)) != TC_OK) return r;
-            if ((r = dalloc_t(s, &s->a8O[k], img8)) != TC_OK) return r;
-            if (!s->a_in[k]) {
-                TC_TRY(s, cudaEventCreateWithFlags(&s->a_in[k], cudaEventDisableTiming), "cudaEventCreate");
-                TC_TRY(s, cudaEventCreateWithFlags(&s->a_done[k], cudaEventDisableTiming), "cudaEventCreate");
-                TC_TRY(s, cudaEventCreateWithFlags(&s->a_out[k], cudaEventDisableTiming), "cudaEventCreate");
-            }
-        }
-        if (!s->cst) TC_TRY(s, cudaStreamCreateWithFlags(&s->cst, cudaStreamNonBlocking), "cudaStreamCreate");
-        if (!s->dst) TC_TRY(s, cudaStreamCreateWithFlags(&s->dst, cudaStreamNonBlocking), "cudaStreamCreate");
-    }
-    // The same slot rotation as tc_process_frame_host_async (the two share the slots and
-    // their events): 8-bit uploads on cst, the unpack, the frame and the pack on the
-    // stream's CUDA stream, 8-bit downloads on dst.
-    const int k = (int)(s->a_n & 1);
-    TC_TRY(s, cudaStreamWaitEvent(s->cst, s->a_done[k], 0), "cudaStreamWaitEvent");
-    TC_TRY(s, cudaMemcpyAsync(s->a8I[k], I_t, img8, cudaMemcpyHostToDevice, s->cst), "H2D I_t");
-    TC_TRY(s, cudaMemcpyAsync(s->a8P[k], P_t, img8, cudaMemcpyHostToDevice, s->cst), "H2D P_t");
-    TC_TRY(s, cudaEventRecord(s->a_in[k], s->cst), "cudaEventRecord");
-    TC_TRY(s, cudaStreamWaitEvent(s->st, s->a_in[k], 0), "cudaStreamWaitEvent");
-    TC_TRY(s, cudaStreamWaitEvent(s->st, s->a_out[k], 0), "cudaStreamWaitEvent");
-    TC_LAUNCH(s, launch_unpack_rgb8(s->a8I[k], plane, s->aI[k], s->st));
-    TC_LAUNCH(s, launch_unpack_rgb8(s->a8P[k], plane, s->aP[k], s->st));
-    r = tc_process_frame(s, s->aI[k], s->aP[k], s->aO[k], wc_opt ? s->awc[k] : nullptr,
-                         mask_opt ? s->amask[k] : nullptr);
-    if (r != TC_OK) return r;
-    const bool wrote = s->last_out >= 0;  // one frame of latency: the first call writes nothing
-    if (wrote) TC_LAUNCH(s, launch_pack_rgb8(s->aO[k], plane, s->a8O[k], s->st));
-    TC_TRY(s, cudaEventRecord(s->a_done[k], s->st), "cudaEventRecord");
-    TC_TRY(s, cudaStreamWaitEvent(s->dst, s->a_done[k], 0), "cudaStreamWaitEvent");
-    if (wrote) {
-        TC_TRY(s, cudaMemcpyAsync(O_t, s->a8O[k], img8, cudaMemcpyDeviceToHost, s->dst), "D2H O_t");
-        if (wc_opt)
-            TC_TRY(s, cudaMemcpyAsync(wc_opt, s->awc[k], plane * sizeof(float), cudaMemcpyDeviceToHost, s->dst),
-                   "D2H w_c");
-        if (mask_opt) TC_TRY(s, cudaMemcpyAsync(mask_opt, s->amask[k], plane, cudaMemcpyDeviceToHost, s->dst), "D2H mask");
-    }
-    TC_TRY(s, cudaEventRecord(s->a_out[k], s->dst), "cudaEventRecord");
-    s->a_n += 1;
-    return TC_OK;
+    return host_async(s, I_t, P_t, O_t, wc_opt, mask_opt, true, "tc_process_frame_host_rgb8_async");
 }
 
 extern "C" tc_status tc_process_frame_host(tc_stream *s, const float *I_t, const float *P_t, float *O_t,

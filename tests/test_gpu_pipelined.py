@@ -181,6 +181,45 @@ def test_pipelined_1080p_matches_default_and_fixed_epe(prec):
         assert max(qb, qf, eb, ef) <= bound, (qb, qf, eb, ef, bound)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_pipelined_host_async_matches_default(prec):
+    """tc_process_frame_host_async and its 8-bit form in pipelined mode (four staging slots,
+    each upload fenced to the frame's pyramid and blend streams, each download to its blend):
+    14 frames enqueued back to back from page-locked buffers give the default mode's outputs
+    bit for bit (the 8-bit form: the default mode on the decoded frames, quantised)."""
+    import torch
+    path, _ = weights_file((16, 32, 64, 96, 128), 4)
+    frames, styl = _frames(14, seed=21)
+    q8 = lambda a: np.ascontiguousarray(np.moveaxis(
+        np.floor(np.clip(np.asarray(a, np.float64), 0.0, 1.0) * 255.0 + 0.5).astype(np.uint8), 0, -1))
+    dec = lambda q: np.ascontiguousarray(np.moveaxis(q, -1, 0).astype(np.float32) / np.float32(255.0))
+    quant = lambda O: np.ascontiguousarray(np.moveaxis(np.floor(
+        np.clip(O, np.float32(0), np.float32(1)) * np.float32(255.0) + np.float32(0.5)).astype(np.uint8), 0, -1))
+    f8, s8 = [q8(a) for a in frames], [q8(a) for a in styl]
+    want32, _ = _run(path, frames, styl, prec, False)
+    want8, _ = _run(path, [dec(a) for a in f8], [dec(a) for a in s8], prec, False)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    for rgb8 in (False, True):
+        s = tc.Stream(W, H, prec, weights_path=path)
+        s.set_pipelined(True)
+        hI = [pin(a) for a in (f8 if rgb8 else frames)]
+        hP = [pin(a) for a in (s8 if rgb8 else styl)]
+        outs = [((torch.empty((H, W, 3), dtype=torch.uint8) if rgb8 else torch.empty((3, H, W))).pin_memory(),
+                 torch.empty((H, W)).pin_memory(), torch.empty((H, W), dtype=torch.uint8).pin_memory())
+                for _ in frames]
+        call = s.process_frame_host_rgb8_async if rgb8 else s.process_frame_host_async
+        for t in range(len(frames)):
+            s.set_consistency(k1=(0.2, 0.5, 0.9)[t % 3])
+            call(hI[t], hP[t], *outs[t])
+        s.synchronize()
+        s.destroy()
+        for t in range(len(frames)):
+            O, wc, m = (o.numpy() for o in outs[t])
+            want = want8[t] if rgb8 else want32[t]
+            assert np.array_equal(O, quant(want[0]) if rgb8 else want[0]), (rgb8, t)
+            assert np.array_equal(wc, want[1]) and np.array_equal(m, want[2]), (rgb8, t)
+
+
 def test_pipelined_state_errors():
     import torch
     path, _ = weights_file((16, 32, 64, 96, 128), 4)
