@@ -642,12 +642,12 @@ size_t plan_tiles(const TcConvPlan &plan, int bn, int n_img, TcLaunch &lp, int *
     int R = 512 / (2 * acc);
     if (R > TILE_RMAX) R = TILE_RMAX;
     while (!overlap && R > 1 && (long)ntx * ((plan.ho + R - 1) / R) * n_img < nsm) R /= 2;
-    // one-step layers (all input channels in one K step: the 16- and 32-channel pyramid
-    // levels) get few tiles per CTA, too few to overlap one tile's loads, MMAs and epilogue
-    // with the next; in a launch alone on the GPU, rows such that two CTAs share each SM let
-    // one CTA's latency hide under the other's work (sequential 1264 vs 1252 frames/s; with
-    // overlapped launches it cost 0.5%, so not there)
-    if (!overlap && plan.nch == 1 && R >= 2 && 2 * R * acc > 256) R /= 2;
+    // one-step layers with narrow K steps (the 16- and 32-channel pyramid levels) get few
+    // tiles per CTA, too few to overlap one tile's loads, MMAs and epilogue with the next; in
+    // a launch alone on the GPU, rows such that two CTAs share each SM let one CTA's latency
+    // hide under the other's work (sequential 1264 vs 1252 frames/s; with overlapped launches
+    // it cost 0.5%, and on E4M3 layers, whose 128-byte step holds up to 128 channels, 4%)
+    if (!overlap && plan.nch == 1 && plan.rb <= 64 && R >= 2 && 2 * R * acc > 256) R /= 2;
     // two channel steps, the second a 64-byte tail: the two halo units alternate between
     // them, so unit 1 takes tail-width slots
     const bool split = tail && plan.nch == 2 && plan.rb == 128;
