@@ -173,8 +173,9 @@ TC_API tc_status tc_process_frame_host(tc_stream *s, const float *I_t, const flo
 /* Pipelined form of tc_process_frame_host for a stream of frames: enqueues the upload of
  * I_t, P_t, the frame, and the download of its outputs into O_t (and wc_opt, mask_opt),
  * then returns without waiting.  The next call's upload and this call's download run on
- * two library-owned copy streams while the neighbouring frames' kernels run (device
- * staging is double-buffered), so the copies and the kernels overlap.  The host buffers
+ * two library-owned copy streams while the neighbouring frames' kernels run (device staging
+ * has two slots, four in pipelined mode, where the call works too: see tc_set_pipelined),
+ * so the copies and the kernels overlap.  The host buffers
  * must stay valid, the inputs unmodified and the outputs unread, until tc_synchronize
  * returns; the copies overlap only from page-locked memory.  Same layouts and the same
  * one-frame-of-latency behaviour as tc_process_frame_host (the first call of a latency-1
