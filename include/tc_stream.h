@@ -411,7 +411,9 @@ TC_API tc_status tc_op_downscale2(const float *src, int c, int h, int w, float *
  * scale in {1, 2, 4, ...} (1 = full resolution, fh = h, fw = w); they are upsampled on
  * the fly as by tc_op_upsample_flow and read on the h x w crop.  Requires fh * scale >= h,
  * fw * scale >= w, and h * w and fh * fw at most INT_MAX.  O: device (3, h, w); wc_opt
- * (h, w) float32 or NULL; mask_opt (h, w) uint8 or NULL. */
+ * (h, w) float32 or NULL; mask_opt (h, w) uint8 or NULL.  Ip, Pp, Op are first packed into
+ * the interleaved per-pixel layout a stream keeps of its previous frame (temporary device
+ * memory), and the call waits for completion. */
 TC_API tc_status tc_op_consistency(const float *It, const float *Pt, const float *Ip, const float *Pp,
                             const float *Op, const float *Fb, const float *Ff, int h, int w,
                             int fh, int fw, int scale, const tc_consistency *p, float *O,

@@ -198,8 +198,16 @@ struct UpArgs {
     int act_cs;
 };
 
+// The state a stream keeps of a frame (its I, P and O, read back by the next frame's
+// bilinear taps) is interleaved per pixel: A = (I0, I1, I2, P0) and B = (P1, P2, O0, O1) as
+// 16-byte words and C = O2, so a tap is three loads instead of nine.
 struct ConsistArgs {
-    const float *It, *Pt, *Ip, *Pp, *Op;  // planar (3, H, W)
+    const float *It, *Pt;                 // planar (3, H, W) frame t, or NULL: its I, P from tA, tB
+    const float4 *tA, *tB;                // frame t in the kept-state layout (when It is NULL)
+    // frame t - 1 in the kept-state layout: I, P from pA and pB.xy, O from oB.zw and pC
+    // (oB == pB when they are one frame's state)
+    const float4 *pA, *pB, *oB;
+    const float *pC;
     const float *Fb, *Ff;                 // (fh, fw, 2): F_{t->t-1}, F_{t-1->t}
     int H, W, fh, fw, scale;
     float k1, alpha, lambda, c1, c2;
@@ -207,7 +215,12 @@ struct ConsistArgs {
     int first;
     float *O, *wc;
     uint8_t *mask;
-    float *sI, *sP, *sO;  // state copies (nullable)
+    // the state kept of frame t (kA NULL: none): I, P into kA and kB.xy when keep_io, O into
+    // kB.zw and kC when keep_o
+    float4 *kA, *kB;
+    float *kC;
+    int keep_io, keep_o;
+    float *Pcopy;  // planar copy of P_t (the solver's input), or NULL
     // next-frame term (next != 0): frame t+1 and the flows F_{t->t+1}, F_{t+1->t} (fh, fw, 2)
     int next;
     const float *In, *Pn, *Fn, *Fnb;
@@ -230,6 +243,19 @@ cudaError_t launch_downscale2(const float *src, int c, int h, int w, float *dst,
 const void *downscale2_kernel_fn();
 cudaError_t launch_flow_out(const float *flow, int fh, int fw, int scale, int H, int W,
                             float *out, cudaStream_t st);
+// Planar (3, hw) I, P, O -> the kept-state layout (A, B, C of ConsistArgs).
+cudaError_t launch_pack_state(const float *I, const float *P, const float *O, size_t hw, float4 *A, float4 *B,
+                              float *C, cudaStream_t st);
+// Planar I, P of a frame into the I, P part of a kept state (A, B.xy): the inputs a stream
+// with one frame of latency keeps.  A kernel, so that a captured graph can retarget it.
+cudaError_t launch_keep_inputs(const float *I, const float *P, size_t hw, float4 *A, float4 *B, cudaStream_t st);
+const void *keep_inputs_kernel_fn();
+// The solver's result: planar src copied to O (and wsrc to wc, when wc is not NULL), and
+// into the O part of a kept state (B.zw, C).
+cudaError_t launch_solver_out(const float *src, float *O, const float *wsrc, float *wc, size_t hw, float4 *B,
+                              float *C, cudaStream_t st);
+const void *solver_out_kernel_fn();
+
 // Interleaved RGB8 (hw pixels x 3 bytes) -> planar float (3, hw) as q / 255, and back as
 // floor(255 clamp(v, 0, 1) + 0.5).
 cudaError_t launch_unpack_rgb8(const uint8_t *src, size_t hw, float *dst, cudaStream_t st);

@@ -212,8 +212,11 @@ size_t stream_device_bytes(const HostNet &net, int width, int height, tc_precisi
         }
     }
     const size_t img = al((size_t)3 * height * width * 4), plane = (size_t)height * width;
-    if (lanes) return total + 6 * al((size_t)3 * height * width * 4 * nl);  // state I, P, O x 2 slots per lane
-    total += 6 * img;                                        // state I, P, O x 2 slots
+    // kept state, 2 slots: two 16-byte words and one float per pixel (per lane)
+    const size_t px_all = (size_t)height * width * (lanes ? nl : 1);
+    const size_t kept = 2 * (2 * al(px_all * 16) + al(px_all * 4));
+    if (lanes) return total + kept;
+    total += kept;
     total += 3 * img + al(plane * 4) + al(plane);            // host-entry staging
     if (fs > 1) total += al((size_t)3 * hn * wn * 4);        // the downscaled frame
     if (!net.ref.empty()) {                                  // refinement buffers and weights
@@ -298,8 +301,10 @@ struct tc_stream {
     std::vector<float *> pyr_w, pyr_b;
     std::vector<float> first_w, first_b;  // host copy of the first conv ([27][cout], cout)
     TcConvPlan pyr_plan[8][3];
-    // state ring: [2 slots] planar (3, H, W)
-    float *sI[2] = {nullptr, nullptr}, *sP[2] = {nullptr, nullptr}, *sO[2] = {nullptr, nullptr};
+    // kept state ring: [2 slots] of the interleaved layout of ConsistArgs, (H, W) pixels per
+    // lane: kA = (I0, I1, I2, P0), kB = (P1, P2, O0, O1), kC = O2
+    float4 *kA[2] = {nullptr, nullptr}, *kB[2] = {nullptr, nullptr};
+    float *kC[2] = {nullptr, nullptr};
     // staging for the host entry point
     float *hI = nullptr, *hP = nullptr, *hO = nullptr, *hwc = nullptr;
     uint8_t *hmask = nullptr;
@@ -376,7 +381,8 @@ struct tc_stream {
     FrameGraph pg_pyr[NPYR], pg_est[NGRAPH], pg_blend[NGRAPH];
     // screened-Poisson solver (allocated when first enabled): A_t, w_c, right-hand side and
     // four iterate planes, each (3, H, W) float (w_c (H, W))
-    float *sv_A = nullptr, *sv_wc = nullptr, *sv_b = nullptr, *sv_c0 = nullptr,
+    // solver: A_t and w_c from the blend, its result, the planar P_t copy, coefficients, scratch
+    float *sv_A = nullptr, *sv_wc = nullptr, *sv_O = nullptr, *sv_P = nullptr, *sv_b = nullptr, *sv_c0 = nullptr,
           *sv_s[4] = {nullptr, nullptr, nullptr, nullptr};
     // one frame of latency (tc_set_latency): frame t is blended when frame t+1 arrives, with
     // the final flows of the pair (t, t-1) kept from the previous call ((2, h_2, w_2, 2) float)
@@ -547,6 +553,7 @@ extern "C" tc_status tc_set_consistency(tc_stream *s, const tc_consistency *p) {
         const size_t img = (size_t)3 * s->H * s->W * sizeof(float), plane = (size_t)s->H * s->W * sizeof(float);
         tc_status r;
         if ((r = dalloc_t(s, &s->sv_A, img)) != TC_OK || (r = dalloc_t(s, &s->sv_wc, plane)) != TC_OK ||
+            (r = dalloc_t(s, &s->sv_O, img)) != TC_OK || (r = dalloc_t(s, &s->sv_P, img)) != TC_OK ||
             (r = dalloc_t(s, &s->sv_b, img)) != TC_OK || (r = dalloc_t(s, &s->sv_c0, plane)) != TC_OK)
             return r;
         for (int k = 0; k < 4; ++k)
@@ -774,11 +781,11 @@ static tc_status build_stream(tc_stream *s) {
         }
     }
     if (!net.ref.empty() && (r = build_refine<T>(s)) != TC_OK) return r;
-    const size_t img = (size_t)3 * s->H * s->W * sizeof(float) * s->lanes;
+    const size_t npx = (size_t)s->H * s->W * s->lanes;
     for (int k = 0; k < 2; ++k) {
-        if ((r = dalloc_t(s, &s->sI[k], img)) != TC_OK) return r;
-        if ((r = dalloc_t(s, &s->sP[k], img)) != TC_OK) return r;
-        if ((r = dalloc_t(s, &s->sO[k], img)) != TC_OK) return r;
+        if ((r = dalloc_t(s, &s->kA[k], npx * sizeof(float4))) != TC_OK) return r;
+        if ((r = dalloc_t(s, &s->kB[k], npx * sizeof(float4))) != TC_OK) return r;
+        if ((r = dalloc_t(s, &s->kC[k], npx * sizeof(float))) != TC_OK) return r;
     }
     if (s->fs == 2 && (r = dalloc_t(s, &s->xs, (size_t)3 * s->Hn * s->Wn * sizeof(float))) != TC_OK) return r;
     return TC_OK;
@@ -1128,38 +1135,45 @@ static ConsistArgs consist_args(tc_stream *s, const float *I, const float *P, fl
     const int prev = cur ^ 1;
     const bool lat = s->latency != 0;
     const long long n = s->t;  // frames given before this call
-    ca.It = lat ? s->sI[prev] : I;
-    ca.Pt = lat ? s->sP[prev] : P;
+    // latency: frame t's I, P are the previous call's inputs, kept in slot prev
+    ca.It = lat ? nullptr : I;
+    ca.Pt = lat ? nullptr : P;
+    ca.tA = lat ? s->kA[prev] : nullptr;
+    ca.tB = lat ? s->kB[prev] : nullptr;
     ca.H = s->H; ca.W = s->W;
     ca.k1 = s->params.k1; ca.alpha = s->params.alpha; ca.lambda = s->params.lambda;
     ca.c1 = s->params.fb_c1; ca.c2 = s->params.fb_c2; ca.fb_check = s->params.fb_check;
     ca.k2 = s->params.k2;
     ca.O = O; ca.wc = wc; ca.mask = mask;
-    // latency: the caller's inputs are copied into the state after this pass
-    ca.sI = lat ? nullptr : s->sI[cur];
-    ca.sP = lat ? nullptr : s->sP[cur];
-    ca.sO = s->sO[cur];
+    // the state kept in slot cur: O_t, and I_t, P_t in the causal form (with latency the
+    // caller's inputs are kept after this pass)
+    ca.kA = s->kA[cur]; ca.kB = s->kB[cur]; ca.kC = s->kC[cur];
+    ca.keep_io = lat ? 0 : 1;
+    ca.keep_o = 1;
     const bool first = lat ? n == 1 : n == 0;
     if (!first && s->params.solver_iters > 0) {
-        // A_t and w_c go to the solver's buffers; the solver writes O_t and the kept copy
+        // A_t and w_c go to the solver's buffers, P_t as its planar input; the solver writes
+        // O_t and the kept O
         ca.O = s->sv_A;
         ca.wc = s->sv_wc;
-        ca.sO = nullptr;
+        ca.keep_o = 0;
+        ca.Pcopy = s->sv_P;
     }
     if (first) {
         ca.first = 1;
         ca.Fb = ca.Ff = nullptr;
         ca.fh = ca.fw = 1; ca.scale = 1;
-        ca.Ip = ca.Pp = ca.Op = nullptr;
         return ca;
     }
     LevelBufs &B2 = s->lv[1];
     const size_t half = (size_t)B2.h * B2.w * 2;
     float *flow2 = flow_of(B2, est_set(s, s->t));
     ca.first = 0;
-    ca.Ip = lat ? s->sI[cur] : s->sI[prev];
-    ca.Pp = lat ? s->sP[cur] : s->sP[prev];
-    ca.Op = s->sO[prev];
+    // frame t - 1: its I, P in slot cur with latency (prev otherwise), its O in slot prev
+    ca.pA = lat ? s->kA[cur] : s->kA[prev];
+    ca.pB = lat ? s->kB[cur] : s->kB[prev];
+    ca.oB = s->kB[prev];
+    ca.pC = s->kC[prev];
     ca.fh = B2.h; ca.fw = B2.w; ca.scale = 4 * s->fs;
     if (!lat) {
         ca.Fb = flow2;
@@ -1179,14 +1193,14 @@ static ConsistArgs consist_args(tc_stream *s, const float *I, const float *P, fl
     return ca;
 }
 
-// The solver after the consistency pass (A_t, w_c in its buffers), then the copy of O_t and
-// w_c to the caller.  P is P_t.
-static tc_status solver_launches(tc_stream *s, const float *P, float *O, float *wc, int cur) {
-    PoissonArgs pa{P, s->sv_A, s->sv_wc, 3, s->H, s->W, s->params.solver_iters, s->params.eta, s->params.kappa,
-                   s->sv_b, s->sv_s[0], s->sv_s[1], s->sv_s[2], s->sv_s[3], s->sO[cur], nullptr, s->sv_c0};
+// The solver after the consistency pass (A_t, w_c and the planar P_t in its buffers), then
+// its result to the caller (O_t, w_c) and into the kept state of slot cur.
+static tc_status solver_launches(tc_stream *s, float *O, float *wc, int cur) {
+    PoissonArgs pa{s->sv_P, s->sv_A, s->sv_wc, 3, s->H, s->W, s->params.solver_iters, s->params.eta, s->params.kappa,
+                   s->sv_b, s->sv_s[0], s->sv_s[1], s->sv_s[2], s->sv_s[3], s->sv_O, nullptr, s->sv_c0};
     TC_LAUNCH_CAT(s, TC_PROF_SOLVER, launch_poisson(pa, s->st));
     const size_t hw = (size_t)s->H * s->W;
-    TC_LAUNCH_CAT(s, TC_PROF_SOLVER, launch_copy_out(s->sO[cur], O, 3 * hw, s->sv_wc, wc, hw, s->st, 0));
+    TC_LAUNCH_CAT(s, TC_PROF_SOLVER, launch_solver_out(s->sv_O, O, s->sv_wc, wc, hw, s->kB[cur], s->kC[cur], s->st));
     return TC_OK;
 }
 
@@ -1209,20 +1223,18 @@ static tc_status blend_launches(tc_stream *s, const float *I, const float *P, fl
     if (!s->latency) {
         const ConsistArgs ca = consist_args(s, I, P, O, wc, mask, cur);
         TC_LAUNCH_CAT(s, TC_PROF_CONSISTENCY, launch_consistency(ca, s->st));
-        // Eq. 1 by Eq. 8 from A_t; P_t is read from the stream's own copy (written above)
-        if (s->t > 0 && s->params.solver_iters > 0 && (r = solver_launches(s, s->sP[cur], O, wc, cur)) != TC_OK)
-            return r;
+        // Eq. 1 by Eq. 8 from A_t; P_t is read from the planar copy written above
+        if (s->t > 0 && s->params.solver_iters > 0 && (r = solver_launches(s, O, wc, cur)) != TC_OK) return r;
         return TC_OK;
     }
     // one frame of latency: frame t = (frames given before) - 1 is blended now
     if (s->t > 0) {
         const ConsistArgs ca = consist_args(s, I, P, O, wc, mask, cur);
         TC_LAUNCH_CAT(s, TC_PROF_CONSISTENCY, launch_consistency(ca, s->st));
-        if (s->t > 1 && s->params.solver_iters > 0 && (r = solver_launches(s, s->sP[cur ^ 1], O, wc, cur)) != TC_OK)
-            return r;
+        if (s->t > 1 && s->params.solver_iters > 0 && (r = solver_launches(s, O, wc, cur)) != TC_OK) return r;
     }
-    const size_t img = (size_t)3 * s->H * s->W;
-    TC_LAUNCH_CAT(s, TC_PROF_CONSISTENCY, launch_copy_out(I, s->sI[cur], img, P, s->sP[cur], img, s->st, 1));
+    TC_LAUNCH_CAT(s, TC_PROF_CONSISTENCY,
+                  launch_keep_inputs(I, P, (size_t)s->H * s->W, s->kA[cur], s->kB[cur], s->st));
     if (s->t > 0) {
         LevelBufs &B2 = s->lv[1];
         TC_TRY(s, cudaMemcpyAsync(s->Fprev, flow_of(B2, est_set(s, s->t)), (size_t)B2.h * B2.w * 4 * sizeof(float),
@@ -1287,8 +1299,8 @@ static tc_status capture_into(tc_stream *s, cudaStream_t cs, tc_stream::FrameGra
         if (s->fs == 1 && kp.func == conv_first_kernel_fn<T>()) { G.n_first = node; G.p_first = kp; }
         if (s->fs == 2 && kp.func == downscale2_kernel_fn()) { G.n_first = node; G.p_first = kp; }
         if (kp.func == consistency_kernel_fn(s->latency != 0)) { G.n_cons = node; G.p_cons = kp; }
-        if (kp.func == copy_out_kernel_fn(0)) { G.n_copy = node; G.p_copy = kp; }
-        if (kp.func == copy_out_kernel_fn(1)) { G.n_in = node; G.p_in = kp; }
+        if (kp.func == solver_out_kernel_fn()) { G.n_copy = node; G.p_copy = kp; }
+        if (kp.func == keep_inputs_kernel_fn()) { G.n_in = node; G.p_in = kp; }
     }
     if ((need_first && !G.n_first) ||
         (need_rest && (!G.n_cons || (s->params.solver_iters > 0 && !G.n_copy) || (s->latency && !G.n_in)))) {
@@ -1334,22 +1346,22 @@ static tc_status update_rest_nodes(tc_stream *s, tc_stream::FrameGraph &G, const
     pc.extra = nullptr;
     TC_TRY(s, cudaGraphExecKernelNodeSetParams(G.exec, G.n_cons, &pc), "graph node update");
     if (G.n_copy) {
-        // the solver's output copy: retarget it to this frame's O_t and w_c
-        const size_t hw = (size_t)s->H * s->W;
-        const float *src = s->sO[cur], *wsrc = s->sv_wc;
-        size_t n3 = 3 * hw, n1 = hw;
-        void *ka[6] = {&src, &O, &n3, &wsrc, &wc, &n1};
+        // the solver's result: retarget it to this frame's O_t, w_c and kept-state slot
+        size_t hw = (size_t)s->H * s->W;
+        const float *src = s->sv_O, *wsrc = s->sv_wc;
+        float4 *kb = s->kB[cur];
+        float *kc = s->kC[cur];
+        void *ka[7] = {&src, &O, &wsrc, &wc, &hw, &kb, &kc};
         cudaKernelNodeParams pk = G.p_copy;
         pk.kernelParams = ka;
         pk.extra = nullptr;
         TC_TRY(s, cudaGraphExecKernelNodeSetParams(G.exec, G.n_copy, &pk), "graph node update");
     }
     if (G.n_in) {
-        // the copy of this frame's inputs into the state (one frame of latency)
-        const size_t img = (size_t)3 * s->H * s->W;
-        float *dI = s->sI[cur], *dP = s->sP[cur];
-        size_t n3 = img;
-        void *ka[6] = {&I, &dI, &n3, &P, &dP, &n3};
+        // the copy of this frame's inputs into the kept state (one frame of latency)
+        size_t hw = (size_t)s->H * s->W;
+        float4 *da = s->kA[cur], *db = s->kB[cur];
+        void *ka[5] = {&I, &P, &hw, &da, &db};
         cudaKernelNodeParams pk = G.p_in;
         pk.kernelParams = ka;
         pk.extra = nullptr;
@@ -1804,21 +1816,22 @@ static tc_status lane_blend(tc_stream *s, int lane, const float *I, const float 
                             uint8_t *mask) {
     const tc_consistency &pr = s->lane_params[lane];
     const int cur = s->lane_cur[lane], prev = cur ^ 1;
-    const size_t off = (size_t)3 * s->H * s->W * lane;
+    const size_t off = (size_t)s->H * s->W * lane;  // the lane's pixels in the kept state
     ConsistArgs ca{};
     ca.It = I; ca.Pt = P;
     ca.H = s->H; ca.W = s->W;
     ca.k1 = pr.k1; ca.alpha = pr.alpha; ca.lambda = pr.lambda;
     ca.c1 = pr.fb_c1; ca.c2 = pr.fb_c2; ca.fb_check = pr.fb_check; ca.k2 = pr.k2;
     ca.O = O; ca.wc = wc; ca.mask = mask;
-    ca.sI = s->sI[cur] + off; ca.sP = s->sP[cur] + off; ca.sO = s->sO[cur] + off;
+    ca.kA = s->kA[cur] + off; ca.kB = s->kB[cur] + off; ca.kC = s->kC[cur] + off;
+    ca.keep_io = ca.keep_o = 1;
     if (s->lane_t[lane] == 0) {
         ca.first = 1;
         ca.fh = ca.fw = 1; ca.scale = 1;
     } else {
         const LevelBufs &B2 = s->lv[1];
         const size_t fimg = (size_t)B2.h * B2.w * 2;
-        ca.Ip = s->sI[prev] + off; ca.Pp = s->sP[prev] + off; ca.Op = s->sO[prev] + off;
+        ca.pA = s->kA[prev] + off; ca.pB = ca.oB = s->kB[prev] + off; ca.pC = s->kC[prev] + off;
         ca.Fb = B2.flow + (size_t)2 * lane * fimg;
         ca.Ff = ca.Fb + fimg;
         ca.fh = B2.h; ca.fw = B2.w; ca.scale = 4;
@@ -2193,7 +2206,7 @@ extern "C" tc_status tc_flush(tc_stream *s, float *O_t, float *wc_opt, uint8_t *
     const cudaError_t ce = launch_consistency(ca, s->st);
     ++s->launches;
     if (ce != cudaSuccess) r = cuda_fail(s, ce, "tc_flush launch");
-    if (r == TC_OK && s->t > 1 && s->params.solver_iters > 0) r = solver_launches(s, s->sP[cur ^ 1], O_t, wc_opt, cur);
+    if (r == TC_OK && s->t > 1 && s->params.solver_iters > 0) r = solver_launches(s, O_t, wc_opt, cur);
     if (r == TC_OK && s->pipelined && s->bst && s->last_blend >= 0) {
         const cudaError_t ee = cudaEventRecord(s->ev_blends[s->last_blend], s->bst);
         if (ee != cudaSuccess) r = cuda_fail(s, ee, "cudaEventRecord");
@@ -2634,12 +2647,23 @@ extern "C" tc_status tc_op_consistency(const float *It, const float *Pt, const f
     std::string why;
     if (!valid_params(p, why)) return fail(nullptr, TC_ERR_INVALID_ARG, why);
     ConsistArgs ca{};
-    ca.It = It; ca.Pt = Pt; ca.Ip = Ip; ca.Pp = Pp; ca.Op = Op; ca.Fb = Fb; ca.Ff = Ff;
+    const cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    TmpAlloc tmp;
+    const size_t hw = (size_t)h * w;
+    float4 *A, *B;
+    float *C;
+    // frame t - 1 into the layout a stream keeps (the pass reads it there)
+    OP_TRY(tmp.get((void **)&A, hw * sizeof(float4)), "tc_op_consistency alloc");
+    OP_TRY(tmp.get((void **)&B, hw * sizeof(float4)), "tc_op_consistency alloc");
+    OP_TRY(tmp.get((void **)&C, hw * sizeof(float)), "tc_op_consistency alloc");
+    OP_TRY(launch_pack_state(Ip, Pp, Op, hw, A, B, C, st), "tc_op_consistency pack");
+    ca.It = It; ca.Pt = Pt; ca.pA = A; ca.pB = ca.oB = B; ca.pC = C; ca.Fb = Fb; ca.Ff = Ff;
     ca.H = h; ca.W = w; ca.fh = fh; ca.fw = fw; ca.scale = scale;
     ca.k1 = p->k1; ca.alpha = p->alpha; ca.lambda = p->lambda; ca.c1 = p->fb_c1; ca.c2 = p->fb_c2;
     ca.fb_check = p->fb_check; ca.first = 0;
     ca.O = O; ca.wc = wc_opt; ca.mask = mask_opt;
-    OP_TRY(launch_consistency(ca, static_cast<cudaStream_t>(cuda_stream)), "tc_op_consistency launch");
+    OP_TRY(launch_consistency(ca, st), "tc_op_consistency launch");
+    OP_TRY(cudaStreamSynchronize(st), "tc_op_consistency synchronize");  // before the temporaries go
     return TC_OK;
 }
 
@@ -2662,12 +2686,22 @@ extern "C" tc_status tc_op_consistency_next(const float *It, const float *Pt, co
     if (!valid_params(p, why)) return fail(nullptr, TC_ERR_INVALID_ARG, why);
     if (!(p->k1 + p->k2 < 1.f)) return fail(nullptr, TC_ERR_INVALID_ARG, "with the next-frame term k1 + k2 must be < 1");
     ConsistArgs ca{};
-    ca.It = It; ca.Pt = Pt; ca.Ip = Ip; ca.Pp = Pp; ca.Op = Op; ca.Fb = Fb; ca.Ff = Ff;
+    const cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    TmpAlloc tmp;
+    const size_t hw = (size_t)h * w;
+    float4 *A, *B;
+    float *C;
+    OP_TRY(tmp.get((void **)&A, hw * sizeof(float4)), "tc_op_consistency_next alloc");
+    OP_TRY(tmp.get((void **)&B, hw * sizeof(float4)), "tc_op_consistency_next alloc");
+    OP_TRY(tmp.get((void **)&C, hw * sizeof(float)), "tc_op_consistency_next alloc");
+    OP_TRY(launch_pack_state(Ip, Pp, Op, hw, A, B, C, st), "tc_op_consistency_next pack");
+    ca.It = It; ca.Pt = Pt; ca.pA = A; ca.pB = ca.oB = B; ca.pC = C; ca.Fb = Fb; ca.Ff = Ff;
     ca.In = In; ca.Pn = Pn; ca.Fn = Fn; ca.Fnb = Fnb; ca.next = 1; ca.k2 = p->k2;
     ca.H = h; ca.W = w; ca.fh = fh; ca.fw = fw; ca.scale = scale;
     ca.k1 = p->k1; ca.alpha = p->alpha; ca.lambda = p->lambda; ca.c1 = p->fb_c1; ca.c2 = p->fb_c2;
     ca.fb_check = p->fb_check; ca.first = 0;
     ca.O = O; ca.wc = wc_opt; ca.mask = mask_opt;
-    OP_TRY(launch_consistency(ca, static_cast<cudaStream_t>(cuda_stream)), "tc_op_consistency_next launch");
+    OP_TRY(launch_consistency(ca, st), "tc_op_consistency_next launch");
+    OP_TRY(cudaStreamSynchronize(st), "tc_op_consistency_next synchronize");  // before the temporaries go
     return TC_OK;
 }

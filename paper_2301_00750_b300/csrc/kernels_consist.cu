@@ -139,13 +139,125 @@ __device__ __forceinline__ bool warp_sample(const float *F, const float *G, cons
     return inb && !occ;
 }
 
+// Frame t - 1's I, P, O at the taps t, from the kept-state layout (see ConsistArgs): I, P from
+// pA and pB.xy, O from oB.zw and pC.  When oB is pB (one frame's state) one 16-byte load of B
+// serves both; otherwise (one frame of latency, where I, P and O of frame t - 1 sit in
+// different slots) B's halves are loaded from their own slots, 8 bytes each.  The sum of each
+// tap's weight times its value runs in the order of gather() above.
+template <bool SPLIT>
+__device__ __forceinline__ void gather_state(const ConsistArgs &a, const Taps &t, float (&gI)[3], float (&gP)[3],
+                                             float (&gO)[3]) {
+    const int o[4] = {t.ya * a.W + t.xa, t.ya * a.W + t.xb, t.yb * a.W + t.xa, t.yb * a.W + t.xb};
+    const float w[4] = {t.w00, t.w01, t.w10, t.w11};
+    float4 A[4], B[4];
+    float C[4];
+    if constexpr (!SPLIT) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            A[k] = __ldg(a.pA + o[k]);
+            B[k] = __ldg(a.pB + o[k]);
+            C[k] = __ldg(a.pC + o[k]);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            A[k] = __ldg(a.pA + o[k]);
+            const float2 ip = __ldg(reinterpret_cast<const float2 *>(a.pB + o[k]));
+            const float2 op = __ldg(reinterpret_cast<const float2 *>(a.oB + o[k]) + 1);
+            B[k] = make_float4(ip.x, ip.y, op.x, op.y);
+            C[k] = __ldg(a.pC + o[k]);
+        }
+    }
+    float v[9];
+#define TC_TAPSUM(dst, f)                         \
+    do {                                          \
+        float acc_ = w[0] * (f(0));               \
+        acc_ += w[1] * (f(1));                    \
+        acc_ += w[2] * (f(2));                    \
+        acc_ += w[3] * (f(3));                    \
+        dst = acc_;                               \
+    } while (0)
+#define TC_AX(k) A[k].x
+#define TC_AY(k) A[k].y
+#define TC_AZ(k) A[k].z
+#define TC_AW(k) A[k].w
+#define TC_BX(k) B[k].x
+#define TC_BY(k) B[k].y
+#define TC_BZ(k) B[k].z
+#define TC_BW(k) B[k].w
+#define TC_C(k) C[k]
+    TC_TAPSUM(v[0], TC_AX);
+    TC_TAPSUM(v[1], TC_AY);
+    TC_TAPSUM(v[2], TC_AZ);
+    TC_TAPSUM(v[3], TC_AW);
+    TC_TAPSUM(v[4], TC_BX);
+    TC_TAPSUM(v[5], TC_BY);
+    TC_TAPSUM(v[6], TC_BZ);
+    TC_TAPSUM(v[7], TC_BW);
+    TC_TAPSUM(v[8], TC_C);
+#undef TC_TAPSUM
+#undef TC_AX
+#undef TC_AY
+#undef TC_AZ
+#undef TC_AW
+#undef TC_BX
+#undef TC_BY
+#undef TC_BZ
+#undef TC_BW
+#undef TC_C
+    gI[0] = v[0]; gI[1] = v[1]; gI[2] = v[2];
+    gP[0] = v[3]; gP[1] = v[4]; gP[2] = v[5];
+    gO[0] = v[6]; gO[1] = v[7]; gO[2] = v[8];
+}
+
+// Frame t's I, P (planar inputs, or its kept state when It is NULL).
+__device__ __forceinline__ void frame_inputs(const ConsistArgs &a, size_t i, size_t hw, float (&It)[3],
+                                             float (&Pt)[3]) {
+    if (a.It) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            It[c] = __ldcs(a.It + c * hw + i);  // read once: streaming
+            Pt[c] = __ldcs(a.Pt + c * hw + i);
+        }
+    } else {
+        const float4 A = a.tA[i], B = a.tB[i];
+        It[0] = A.x; It[1] = A.y; It[2] = A.z;
+        Pt[0] = A.w; Pt[1] = B.x; Pt[2] = B.y;
+    }
+}
+
+// The state kept of frame t (written once: streaming stores), and the planar P_t copy.
+__device__ __forceinline__ void keep_state(const ConsistArgs &a, size_t i, size_t hw, const float (&It)[3],
+                                           const float (&Pt)[3], const float (&Ot)[3]) {
+    if (a.Pcopy)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) __stcs(a.Pcopy + c * hw + i, Pt[c]);
+    if (!a.kA) return;
+    if (a.keep_io && a.keep_o) {
+        __stcs(a.kA + i, make_float4(It[0], It[1], It[2], Pt[0]));
+        __stcs(a.kB + i, make_float4(Pt[1], Pt[2], Ot[0], Ot[1]));
+        __stcs(a.kC + i, Ot[2]);
+    } else if (a.keep_io) {
+        __stcs(a.kA + i, make_float4(It[0], It[1], It[2], Pt[0]));
+        __stcs(reinterpret_cast<float2 *>(a.kB + i), make_float2(Pt[1], Pt[2]));
+    } else if (a.keep_o) {
+        __stcs(reinterpret_cast<float2 *>(a.kB + i) + 1, make_float2(Ot[0], Ot[1]));
+        __stcs(a.kC + i, Ot[2]);
+    }
+}
+
 // NEXT = false: causal form (w_n = 0).  NEXT = true: frame t+1 warped along F_{t->t+1}
 // enters L_t and A^I_t with the weight w_n (Eqs. 2, 3, 6); the mask gets bit 1 for it.
+// GEN: the causal form for frame t from the kept state and frame t - 1's state split over
+// two slots (the last frame of a stream with one frame of latency, tc_flush); without it
+// (causal streams, lanes and the stage op) frame t is planar and frame t - 1 one slot.
 // Both forms are bound by the latency of their dependent loads (flow, then taps), so
-// occupancy comes first: the causal form runs at 40 registers (six blocks, 48 warps per
-// SM), the one with the next frame at 48 (five blocks).
-template <bool NEXT>
-__global__ void __launch_bounds__(256, NEXT ? 5 : 6) consistency_kernel(ConsistArgs a) {
+// occupancy matters: five blocks (40 warps) per SM and 48 registers, which the twelve tap
+// loads of the interleaved state need without spilling (at six blocks they spilled: 57.5 vs
+// 55.4 us for the causal pass at 1080p; the planar state's 36 scalar tap loads: 61.6 us).
+template <bool NEXT, bool GEN = false>
+__global__ void __launch_bounds__(256, 5) consistency_kernel(ConsistArgs a) {
+    constexpr bool RT = NEXT || GEN;  // frame t's source and frame t - 1's slots chosen at run time
     pdl_wait();
     const int x = blockIdx.x * 32 + (threadIdx.x & 31);
     const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
@@ -153,31 +265,33 @@ __global__ void __launch_bounds__(256, NEXT ? 5 : 6) consistency_kernel(ConsistA
     const size_t hw = (size_t)a.H * a.W;
     const size_t i = (size_t)y * a.W + x;
     float It[3], Pt[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        It[c] = __ldcs(a.It + c * hw + i);  // read once: streaming
-        Pt[c] = __ldcs(a.Pt + c * hw + i);
-    }
     if (!NEXT && a.first) {
+        frame_inputs(a, i, hw, It, Pt);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            a.O[c * hw + i] = Pt[c];
-            if (a.sI) a.sI[c * hw + i] = It[c];
-            if (a.sP) a.sP[c * hw + i] = Pt[c];
-            if (a.sO) a.sO[c * hw + i] = Pt[c];
-        }
+        for (int c = 0; c < 3; ++c) a.O[c * hw + i] = Pt[c];
+        keep_state(a, i, hw, It, Pt, Pt);
         if (a.wc) a.wc[i] = 0.f;
         if (a.mask) a.mask[i] = 0;
         return;
     }
+    if (!RT) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            It[c] = __ldcs(a.It + c * hw + i);
+            Pt[c] = __ldcs(a.Pt + c * hw + i);
+        }
+    } else {
+        frame_inputs(a, i, hw, It, Pt);
+    }
     Taps t;
     const bool m = warp_sample(a.Fb, a.Ff, a, x, y, t);
     float gI[3], gP[3], gO[3], d = 0.f;
+    if (RT && a.oB != a.pB)
+        gather_state<true>(a, t, gI, gP, gO);
+    else
+        gather_state<false>(a, t, gI, gP, gO);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        gI[c] = gather(a.Ip + c * hw, a.W, t);
-        gP[c] = gather(a.Pp + c * hw, a.W, t);
-        gO[c] = gather(a.Op + c * hw, a.W, t);
         const float e = It[c] - gI[c];
         d += e * e;
     }
@@ -185,6 +299,7 @@ __global__ void __launch_bounds__(256, NEXT ? 5 : 6) consistency_kernel(ConsistA
     if (m) wp = fminf(a.k1, expf(-a.alpha * d));
     float dI = 0.f;
     bool mn = false;
+    float Ot[3];
     if constexpr (NEXT) {
         Taps tn;
         mn = warp_sample(a.Fn, a.Fnb, a, x, y, tn);
@@ -207,9 +322,7 @@ __global__ void __launch_bounds__(256, NEXT ? 5 : 6) consistency_kernel(ConsistA
             const float e = It[c] - AI;
             dI += e * e;
             __stcs(a.O + c * hw + i, A);  // written once: streaming
-            if (a.sI) __stcs(a.sI + c * hw + i, It[c]);
-            if (a.sP) __stcs(a.sP + c * hw + i, Pt[c]);
-            if (a.sO) __stcs(a.sO + c * hw + i, A);
+            Ot[c] = A;
         }
     } else {
 #pragma unroll
@@ -220,14 +333,67 @@ __global__ void __launch_bounds__(256, NEXT ? 5 : 6) consistency_kernel(ConsistA
             const float e = It[c] - AI;
             dI += e * e;
             __stcs(a.O + c * hw + i, A);  // written once: streaming
-            if (a.sI) __stcs(a.sI + c * hw + i, It[c]);
-            if (a.sP) __stcs(a.sP + c * hw + i, Pt[c]);
-            if (a.sO) __stcs(a.sO + c * hw + i, A);
+            Ot[c] = A;
         }
     }
+    keep_state(a, i, hw, It, Pt, Ot);
     if (a.wc) __stcs(a.wc + i, a.lambda * expf(-a.alpha * dI));
     if (a.mask) a.mask[i] = (m ? 1 : 0) | (mn ? 2 : 0);
 }
+
+// Planar (3, hw) I, P, O -> kept-state layout.
+__global__ void pack_state_kernel(const float *I, const float *P, const float *O, size_t hw, float4 *A, float4 *B,
+                                  float *C) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= hw) return;
+    A[i] = make_float4(I[i], I[hw + i], I[2 * hw + i], P[i]);
+    B[i] = make_float4(P[hw + i], P[2 * hw + i], O[i], O[hw + i]);
+    C[i] = O[2 * hw + i];
+}
+
+cudaError_t launch_pack_state(const float *I, const float *P, const float *O, size_t hw, float4 *A, float4 *B,
+                              float *C, cudaStream_t st) {
+    pack_state_kernel<<<(unsigned)((hw + 255) / 256), 256, 0, st>>>(I, P, O, hw, A, B, C);
+    return cudaGetLastError();
+}
+
+// A frame's planar I, P -> the I, P part of a kept state (the O part is left as it is).
+__global__ void keep_inputs_kernel(const float *I, const float *P, size_t hw, float4 *A, float4 *B) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= hw) return;
+    A[i] = make_float4(I[i], I[hw + i], I[2 * hw + i], P[i]);
+    reinterpret_cast<float2 *>(B + i)[0] = make_float2(P[hw + i], P[2 * hw + i]);
+}
+
+cudaError_t launch_keep_inputs(const float *I, const float *P, size_t hw, float4 *A, float4 *B, cudaStream_t st) {
+    keep_inputs_kernel<<<(unsigned)((hw + 255) / 256), 256, 0, st>>>(I, P, hw, A, B);
+    return cudaGetLastError();
+}
+
+const void *keep_inputs_kernel_fn() { return reinterpret_cast<const void *>(keep_inputs_kernel); }
+
+// The solver's result to the caller (O, and w_c when wc is not NULL) and into the O part of
+// the kept state.
+__global__ void solver_out_kernel(const float *src, float *O, const float *wsrc, float *wc, size_t hw, float4 *B,
+                                  float *C) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= hw) return;
+    const float o0 = src[i], o1 = src[hw + i], o2 = src[2 * hw + i];
+    O[i] = o0;
+    O[hw + i] = o1;
+    O[2 * hw + i] = o2;
+    if (wc) wc[i] = wsrc[i];
+    reinterpret_cast<float2 *>(B + i)[1] = make_float2(o0, o1);
+    C[i] = o2;
+}
+
+cudaError_t launch_solver_out(const float *src, float *O, const float *wsrc, float *wc, size_t hw, float4 *B,
+                              float *C, cudaStream_t st) {
+    solver_out_kernel<<<(unsigned)((hw + 255) / 256), 256, 0, st>>>(src, O, wsrc, wc, hw, B, C);
+    return cudaGetLastError();
+}
+
+const void *solver_out_kernel_fn() { return reinterpret_cast<const void *>(solver_out_kernel); }
 
 const void *consistency_kernel_fn(bool next) {
     return next ? reinterpret_cast<const void *>(consistency_kernel<true>)
@@ -237,6 +403,7 @@ const void *consistency_kernel_fn(bool next) {
 cudaError_t launch_consistency(const ConsistArgs &a, cudaStream_t st) {
     dim3 grid((a.W + 31) / 32, (a.H + 7) / 8);
     if (a.next) return launch_pdl(consistency_kernel<true>, grid, dim3(256), 0, st, a);
+    if (!a.It || a.oB != a.pB) return launch_pdl(consistency_kernel<false, true>, grid, dim3(256), 0, st, a);
     return launch_pdl(consistency_kernel<false>, grid, dim3(256), 0, st, a);
 }
 

@@ -226,31 +226,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) poisson_solve_kernel(const Solv
 // pass, 48 x 48 output; two CTAs per SM.
 constexpr int CW = 2, RR = 8, NWARP = 8, TPASS = 8, MINB = 2;
 
-// TAG only tells the copies of a frame apart in a captured graph (0: the solver's output to
-// the caller, 1: the caller's inputs into the stream's state).
-template <int TAG>
-__global__ void copy_out_kernel(const float *src, float *dst, size_t n, const float *wsrc, float *wdst, size_t nw) {
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
-    if (wdst)
-        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += stride) wdst[i] = wsrc[i];
-}
-
 }  // namespace
-
-cudaError_t launch_copy_out(const float *src, float *dst, size_t n, const float *wsrc, float *wdst, size_t nw,
-                            cudaStream_t st, int tag) {
-    if (tag == 1)
-        copy_out_kernel<1><<<4 * 148, 256, 0, st>>>(src, dst, n, wsrc, wdst, nw);
-    else
-        copy_out_kernel<0><<<4 * 148, 256, 0, st>>>(src, dst, n, wsrc, wdst, nw);
-    return cudaGetLastError();
-}
-
-const void *copy_out_kernel_fn(int tag) {
-    return tag == 1 ? reinterpret_cast<const void *>(copy_out_kernel<1>)
-                    : reinterpret_cast<const void *>(copy_out_kernel<0>);
-}
 
 cudaError_t launch_poisson(const PoissonArgs &a, cudaStream_t st) {
     if (a.c < 1 || a.c > 3) return cudaErrorInvalidValue;

@@ -21,12 +21,4 @@ struct PoissonArgs {
 
 cudaError_t launch_poisson(const PoissonArgs &a, cudaStream_t st);
 
-// dst[i] = src[i] for i < n and wdst[i] = wsrc[i] for i < nw (wdst may be NULL): the
-// solver's output and weights copied to the caller's buffers (tag 0), or the caller's
-// inputs copied into the stream's state (tag 1).  A kernel, so that a captured frame graph
-// can retarget it; the tag tells the two apart in the graph.
-cudaError_t launch_copy_out(const float *src, float *dst, size_t n, const float *wsrc, float *wdst, size_t nw,
-                            cudaStream_t st, int tag = 0);
-const void *copy_out_kernel_fn(int tag);
-
 }  // namespace tc
