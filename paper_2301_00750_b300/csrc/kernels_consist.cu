@@ -265,23 +265,23 @@ __global__ void __launch_bounds__(256, 5) consistency_kernel(ConsistArgs a) {
     const size_t hw = (size_t)a.H * a.W;
     const size_t i = (size_t)y * a.W + x;
     float It[3], Pt[3];
-    if (!NEXT && a.first) {
+    // frame t's inputs first: their loads overlap everything up to the blend
+    if (!RT) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            It[c] = __ldcs(a.It + c * hw + i);  // read once: streaming
+            Pt[c] = __ldcs(a.Pt + c * hw + i);
+        }
+    } else {
         frame_inputs(a, i, hw, It, Pt);
+    }
+    if (!NEXT && a.first) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) a.O[c * hw + i] = Pt[c];
         keep_state(a, i, hw, It, Pt, Pt);
         if (a.wc) a.wc[i] = 0.f;
         if (a.mask) a.mask[i] = 0;
         return;
-    }
-    if (!RT) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            It[c] = __ldcs(a.It + c * hw + i);
-            Pt[c] = __ldcs(a.Pt + c * hw + i);
-        }
-    } else {
-        frame_inputs(a, i, hw, It, Pt);
     }
     Taps t;
     const bool m = warp_sample(a.Fb, a.Ff, a, x, y, t);
