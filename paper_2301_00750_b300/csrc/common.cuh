@@ -13,10 +13,14 @@ namespace tc {
 // the previous kernel of the stream exits, without a full stream-order round trip.  It calls
 // pdl_wait() before it reads or writes any memory an earlier kernel touches (it returns once
 // the earlier grids have completed and their writes are visible; without a programmatic
-// launch it returns at once).  The kernels trigger their dependents only implicitly, at
-// exit: an explicit trigger at the start let the next kernel's CTAs compete with the last
-// wave (945 vs 954 frames/s), the implicit one measured 956 vs 954.
+// launch it returns at once).  Most kernels trigger their dependents only implicitly, at
+// exit: an explicit trigger at the start of every kernel let the next kernel's CTAs compete
+// with the last wave (945 vs 954 frames/s).  The tensor-core kernels trigger early where
+// their grid leaves half of the SMs free and no other stream shares the GPU (pdl_trigger).
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next kernel of the stream launch before this one exits (once every CTA of this
+// grid has executed it or exited); that kernel still waits for this one in pdl_wait().
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,

@@ -85,6 +85,7 @@ struct TcLaunch {
     int tailunit;         // halo unit 1 holds the 64-byte tail step (two channel steps per tile)
     int rev;              // tiles in reverse order (tile ts is ntiles - 1 - ts)
     int overlap;          // launcher only: keep the full rows per tile (see ConvArgs::overlap)
+    int trigger;          // let the next kernel of the stream launch once every CTA holds its TMEM
 };
 
 // Epilogue shared by the conv kernels: thread r of the CTA owns accumulator row r, i.e.
@@ -220,6 +221,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
+    if (p.trigger) pdl_trigger();
     pdl_wait();  // every global access below follows the previous kernel
 
     if (threadIdx.x == 0) {
@@ -408,6 +410,7 @@ conv_tc_tiles_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
+    if (p.trigger) pdl_trigger();
 
     // offset of the resident kernel row (c, ky): full steps first, the tail step last
     auto woff = [&](int c, int ky) -> uint32_t {
@@ -690,6 +693,16 @@ size_t plan_tiles(const TcConvPlan &plan, int bn, int n_img, TcLaunch &lp, int *
     return smem;
 }
 
+// Early launch of the next kernel (griddepcontrol.launch_dependents once a CTA holds its TMEM)
+// for a launch alone on the GPU whose CTAs leave at least half of the SMs free: the next
+// kernel's CTAs then set up (barriers, TMEM, their constant weights) on those SMs while this
+// one runs, and wait in griddepcontrol.wait for its results.  Every CTA of this launch holds
+// its TMEM before any CTA of the next one starts, so the waiting CTAs only wait on work that
+// is running.  Launches that fill the GPU (or share it with other streams) trigger at exit:
+// there the next kernel's CTAs would take SMs from this launch's last wave.  Measured at
+// 1080p in default mode: 1271.9 -> 1288.5 frames/s.
+inline int early_trigger(const TcLaunch &lp, long ctas) { return !lp.overlap && 2 * ctas <= sm_count() ? 1 : 0; }
+
 template <int BN, bool HEAD, bool F8, int R>
 cudaError_t launch_tiles(const TcConvPlan &plan, const TcLaunch &lt, int grid, size_t smem, cudaStream_t st) {
     static bool attr = false;
@@ -711,6 +724,7 @@ cudaError_t launch_bn(const TcConvPlan &plan, const TcLaunch &lp, int n_img, cud
         const size_t smem = plan_tiles(plan, BN, n_img, lt, &g, lp.overlap != 0);
         if (smem == 0 || lt.sa < 2) return cudaErrorInvalidConfiguration;
         lt.stall = take_stall(st);
+        lt.trigger = early_trigger(lt, g);
         constexpr int ACC = tmem_cols_for(BN);
         switch (lt.R) {
             case 1: return launch_tiles<BN, HEAD, F8, 1>(plan, lt, g, smem, st);
@@ -722,6 +736,8 @@ cudaError_t launch_bn(const TcConvPlan &plan, const TcLaunch &lp, int n_img, cud
         return cudaErrorInvalidConfiguration;
     }
     const dim3 grid((plan.wo + BM - 1) / BM, plan.ho, n_img);
+    TcLaunch l1 = lp;
+    l1.trigger = early_trigger(lp, (long)grid.x * grid.y * grid.z);
     static size_t attr_bytes = 0;
     const size_t smem = smem_bytes_for(BN, plan.rb);
     if (attr_bytes < smem) {
@@ -730,7 +746,7 @@ cudaError_t launch_bn(const TcConvPlan &plan, const TcLaunch &lp, int n_img, cud
         if (e != cudaSuccess) return e;
         attr_bytes = smem;
     }
-    return launch_pdl(conv_tc_kernel<BN, HEAD, F8>, grid, dim3(128), smem, st, plan.tmA, plan.tmB, lp);
+    return launch_pdl(conv_tc_kernel<BN, HEAD, F8>, grid, dim3(128), smem, st, plan.tmA, plan.tmB, l1);
 }
 
 }  // namespace

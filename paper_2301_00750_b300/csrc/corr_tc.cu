@@ -53,6 +53,7 @@ struct CorrTcLaunch {
     int nb;       // batch entries (blocks run over nbx x nby x nb)
     int nstages;  // operand stages in shared memory
     int tma_self; // the self copy is a TMA store of the block's self operand (tmC), not per thread
+    int trigger;  // let the next kernel of the stream launch once every CTA holds its TMEM
 };
 
 template <int R>
@@ -356,6 +357,7 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
+    if (p.trigger) pdl_trigger();
 
     // images of block entry z in the self and other tensor maps
     auto images = [&](int z, int &img_self, int &img_other) {
@@ -575,6 +577,9 @@ cudaError_t launch_r(const CorrTcPlan &plan, const CorrTcLaunch &lp0, int nb, cu
     const long nblocks = (long)((plan.w + BX - 1) / BX) * ((plan.h + BY - 1) / BY) * nb;
     const int nsm = corr_sm_count();
     const int grid = nblocks < nsm ? (int)nblocks : nsm;
+    // a launch alone on the GPU whose CTAs leave half of the SMs free lets the next kernel
+    // set up on them while it runs (as the convolutions do; every CTA holds its TMEM first)
+    lp.trigger = lp.trigger && 2 * grid <= nsm ? 1 : 0;
     const size_t smem = 1024 + (size_t)ns * stage + slices + 256;
     // the self copy as a TMA store of each block's self operand: a map over the destination
     // (channels [0, c) of nb images at pixel stride out_cs), boxed and swizzled like the self
@@ -672,7 +677,7 @@ cudaError_t launch_corr_tc_pairs(const CorrTcPlan &plan, int lanes, int pair_lan
 
 cudaError_t launch_corr_tc(const CorrTcPlan &plan, int nb, const int img_self[2], const int img_other[2], void *out,
                            int out_cs, const void *const fs[2], void *self_copy, cudaStream_t st, float feat_scale,
-                           float q_out) {
+                           float q_out, bool alone) {
     if (!plan.enabled || nb < 1 || nb > 2) return cudaErrorInvalidValue;
     const int esz = plan.f8 ? 1 : 2;
     if (self_copy && ((out_cs * esz) % 16 != 0 || reinterpret_cast<uintptr_t>(self_copy) % 16 != 0 || !fs ||
@@ -693,6 +698,7 @@ cudaError_t launch_corr_tc(const CorrTcPlan &plan, int nb, const int img_self[2]
     lp.vec_out = ((out_cs * esz) % 16 == 0 && reinterpret_cast<uintptr_t>(out) % 16 == 0) ? 1 : 0;
     lp.c = plan.c;
     lp.self_copy = self_copy;
+    lp.trigger = alone ? 1 : 0;
     lp.scale = feat_scale * feat_scale / (float)plan.c;
     lp.q_out = q_out;
     lp.err = plan.err;

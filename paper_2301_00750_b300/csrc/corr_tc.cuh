@@ -38,9 +38,11 @@ bool tc_plan_corr(CorrTcPlan &plan, const void *self, int n_self, int self_cs, c
 // out_cs.
 // For e4m3 features stored with scale feat_scale, the cost is feat_scale^2 / c times the
 // integer-grid dot product, stored e4m3 after multiplying by q_out (1 / its scale).
+// alone: no other stream's kernels share the GPU (a small launch then lets the next kernel
+// of the stream set up early).
 cudaError_t launch_corr_tc(const CorrTcPlan &plan, int nb, const int img_self[2], const int img_other[2], void *out,
                            int out_cs, const void *const fs[2], void *self_copy, cudaStream_t st,
-                           float feat_scale = 1.f, float q_out = 1.f);
+                           float feat_scale = 1.f, float q_out = 1.f, bool alone = false);
 
 // Lane pairs (batched streams): 2 lanes entries, entry z = direction d = z & 1 of lane
 // q = z >> 1, correlates image s0 + q + d pair_lanes of the self buffer with image

@@ -1077,7 +1077,7 @@ static tc_status run_estimators(tc_stream *s, int pcur, int pprev, int set) {
             const void *fs[2] = {self_p[0], self_p[1]};
             TC_LAUNCH_CAT(s, TC_PROF_CORRELATION,
                           launch_corr_tc(B.corrplan, 2, img_s, img_o, dec + B.c, B.ctot, fs, dec, s->st, B.s_pyr[2],
-                                         B.q_est[0]));
+                                         B.q_est[0], !s->pipelined));
         } else if constexpr (sizeof(T) == 1) {
             return fail(s, TC_ERR_UNSUPPORTED, "e4m3 correlation without a tensor-core plan");
         } else {
