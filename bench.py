@@ -150,9 +150,15 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self._t.join(timeout=2)
+        return self.summarize(self.lines)
+
+    @staticmethod
+    def summarize(lines):
+        """Median SM clock, maximum SM clock, the throttle reasons seen active at least once,
+        and the number of parsed samples, from nvidia-smi's CSV lines (FIELDS, no units)."""
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue

@@ -1,6 +1,8 @@
 """bench.py's host-side contract on CPU: the reference arm (the FP64 oracle timed on this
-host's cores) prints one JSON line with the main arm's metric, unit and workload, and the
-helpers that set the per-frame consistency controls and report the oracle's threads."""
+host's cores) prints one JSON line with the main arm's metric, unit and workload; the helpers
+that set the per-frame consistency controls and report the oracle's threads; the FLOP count
+behind the roofline, against torch's own FLOP counter; and the summary of the clock samples
+that decides whether a run saw a throttle reason."""
 import argparse
 import json
 
@@ -61,3 +63,62 @@ def test_oracle_threads(monkeypatch):
     assert bench.oracle_threads() == 2
     monkeypatch.delenv("OMP_NUM_THREADS")
     assert bench.oracle_threads() >= 1
+
+
+def test_conv_flops_match_torch_flop_counter():
+    """The roofline's numerator, counted independently: torch's FLOP counter over meta-device
+    convolutions (no arithmetic is done) with the network's layer shapes at the padded 1080p
+    frame, and the correlation as one (1 x c) by (c x (2R+1)^2) product per pixel."""
+    import torch
+    import torch.nn.functional as F
+    from torch.utils.flop_counter import FlopCounterMode
+
+    spec = bench.net_spec()
+    got = bench.conv_flops_per_frame(spec)
+    m = 1 << spec.levels
+    hp, wp = -(-bench.HEIGHT // m) * m, -(-bench.WIDTH // m) * m
+    layers = spec.layer_table()
+    meta = dict(device="meta")
+
+    def count(fn):
+        with FlopCounterMode(display=False) as fc:
+            fn()
+        return fc.get_total_flops()
+
+    def pyramid():  # one frame, the levels chained
+        x = torch.empty(1, 3, hp, wp, **meta)
+        for name, cin, cout, stride, _ in layers:
+            if name.startswith("pyr"):
+                x = F.conv2d(x, torch.empty(cout, cin, 3, 3, **meta), stride=stride, padding=1)
+
+    def estimators(head):  # both flow directions as a batch of two
+        for name, cin, cout, _, _ in layers:
+            if name.startswith("est") and name.endswith("c5") == head:
+                l = int(name[3])
+                F.conv2d(torch.empty(2, cin, hp >> l, wp >> l, **meta), torch.empty(cout, cin, 3, 3, **meta),
+                         padding=1)
+
+    def correlation():
+        d = (2 * spec.radius + 1) ** 2
+        for l in range(2, spec.levels + 1):
+            px, c = 2 * (hp >> l) * (wp >> l), spec.chans[l - 1]
+            torch.bmm(torch.empty(px, 1, c, **meta), torch.empty(px, c, d, **meta))
+
+    assert got["pyramid_conv"] == count(pyramid)
+    assert got["estimator_conv"] == count(lambda: estimators(False))
+    assert got["head"] == count(lambda: estimators(True))
+    assert got["correlation"] == count(correlation)
+
+
+def test_clock_samples_summary():
+    off = "Not Active"
+    lines = [f"0, 2032, 2032, 700.5, 0x0, {off}, {off}, {off}, {off}",
+             f"0, 1965, 2032, 1099.0, 0x4, {off}, {off}, {off}, Active",
+             f"0, 2032, 2032, 810.0, 0x0, {off}, {off}, {off}, {off}",
+             "", "0, [N/A], 2032, 0, 0x0, , , , "]  # an empty and an unparsable line are skipped
+    assert bench.ClockSampler.summarize(lines) == dict(sm_mhz=2032.0, sm_max_mhz=2032.0,
+                                                       reasons=["sw_power_cap"], samples=3)
+    hot = [f"0, 1500, 2032, 900.0, 0x40, {off}, {off}, Active, {off}"] * 2
+    r = bench.ClockSampler.summarize(hot)
+    assert r["reasons"] == ["sw_thermal_slowdown"] and r["sm_mhz"] == 1500.0
+    assert bench.ClockSampler.summarize([])["samples"] == 0
