@@ -122,3 +122,37 @@ def test_clock_samples_summary():
     r = bench.ClockSampler.summarize(hot)
     assert r["reasons"] == ["sw_thermal_slowdown"] and r["sm_mhz"] == 1500.0
     assert bench.ClockSampler.summarize([])["samples"] == 0
+
+
+def test_train_flops_match_torch_flop_counter():
+    """The training roofline's numerator, counted independently: forward and autograd backward
+    of meta-device convolutions with the network's layer shapes (pyramids of 2B images chained
+    from an input that takes no gradient, so the first conv has no data gradient; estimators on
+    B pairs), and the correlation as a per-pixel product whose two operands take gradients."""
+    import torch
+    import torch.nn.functional as F
+    from torch.utils.flop_counter import FlopCounterMode
+
+    spec = bench.net_spec()
+    B, S = bench.TRAIN_BATCH, bench.TRAIN_SIZE
+    meta = dict(device="meta")
+    with FlopCounterMode(display=False) as fc:
+        outs = []
+        x = torch.empty(2 * B, 3, S, S, **meta)
+        for name, cin, cout, stride, _ in spec.layer_table():
+            w = torch.empty(cout, cin, 3, 3, requires_grad=True, **meta)
+            if name.startswith("pyr"):
+                x = F.conv2d(x, w, stride=stride, padding=1)
+                outs.append(x)
+            else:
+                l = int(name[3])
+                xe = torch.empty(B, cin, S >> l, S >> l, requires_grad=True, **meta)
+                outs.append(F.conv2d(xe, w, padding=1))
+        d = (2 * spec.radius + 1) ** 2
+        for l in range(2, spec.levels + 1):
+            px, c = B * (S >> l) ** 2, spec.chans[l - 1]
+            a = torch.empty(px, 1, c, requires_grad=True, **meta)
+            b = torch.empty(px, c, d, requires_grad=True, **meta)
+            outs.append(torch.bmm(a, b))
+        sum(o.sum() for o in outs).backward()
+    assert bench.train_flops_per_step(spec)["total"] == fc.get_total_flops()
