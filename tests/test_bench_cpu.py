@@ -156,3 +156,17 @@ def test_train_flops_match_torch_flop_counter():
             outs.append(torch.bmm(a, b))
         sum(o.sum() for o in outs).backward()
     assert bench.train_flops_per_step(spec)["total"] == fc.get_total_flops()
+
+
+def test_epe_px_closed_forms():
+    """The end-point error behind `at_fixed_epe` (Eq. 10): the mean over pixels of the
+    Euclidean norm of the flow difference, on cases with a closed-form answer."""
+    import torch
+
+    z = torch.zeros(2, 4, 6)
+    d = torch.stack([torch.full((4, 6), 3.0), torch.full((4, 6), -4.0)])
+    assert bench.epe_px(z, d) == 5.0  # |(3, -4)| at every pixel
+    half = torch.zeros(2, 4, 6)
+    half[1, :2] = 2.0  # half of the pixels off by (0, 2), the rest exact
+    assert bench.epe_px(half, z) == 1.0
+    assert bench.epe_px(d, d) == 0.0
