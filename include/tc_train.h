@@ -1,5 +1,5 @@
 /* tc_train.h -- C ABI of the in-project training of the lite flow network (Sec. 3.2), the
- * backward passes of its stages, and the brute-force flow used as fallback and judge.
+ * backward passes of its stages, and the brute-force flow used as fallback and as the yardstick of learned flows.
  *
  * The paper trains its flow network with a multi-scale loss of equal level weights and
  * AdamW (Sec. 3.2 "Training"; supplement "Training Settings"), on datasets this library
@@ -129,7 +129,7 @@ TC_API tc_status tc_op_warp_features_backward(const float *f, const float *flow,
 TC_API tc_status tc_op_upsample_flow_backward(const float *dfine, int n, int h, int w, int s, float *dcoarse,
                                               void *cuda_stream);
 
-/* Brute-force integer flow (the training fallback and the judge of learned flows): for
+/* Brute-force integer flow (the training fallback and the yardstick of learned flows): for
  * every pixel of a the displacement d in [-r, r]^2 minimising the sum over a 3x3 patch and
  * the c channels of (a(x+p) - b(x+p+d))^2, border-clamped, ties to the smaller |d|^2 then
  * the smaller index; writes k = (dy+r)(2r+1) + (dx+r) per pixel to k_out (h, w) int32.

@@ -1,5 +1,5 @@
 """Trains the lite flow network on seeded synthetic pairs with known flow (Sec. 3.2
-"Training"; supplement "Training Settings") and judges the result.
+"Training"; supplement "Training Settings") and scores the result.
 
     python -m paper_2301_00750_b300.train_synthetic [--pairs 20000] [--batch 32] [--epochs 60]
         [--lr 1e-4] [--out learned.tcw] [--precision bf16]
@@ -11,7 +11,7 @@
 * Training: the library's native trainer (tc_trainer_run): forward, multi-scale EPE loss
   with equal level weights, the hand-written backward passes, AdamW on float32 master
   weights; batch ``--batch`` drawn without replacement, reshuffled every epoch (seeded).
-* Judge: held-out EPE (Eq. 10) of the network's final flow (level-2 flow upsampled x4)
+* Score: held-out EPE (Eq. 10) of the network's final flow (level-2 flow upsampled x4)
   against the ground truth, beside the brute-force SSD-argmin flow (tc_op_bruteforce_flow,
   radius 16) and the zero flow.
 * Precision check on the learned weights: a 1920x1080 pair of the seeded sequence through
@@ -34,7 +34,7 @@ import synth
 
 TRAIN_SEED, HELD_SEED = 1_000_000, 9_000_000
 SIZE, MAX_FLOW = 256, 16.0
-JUDGE_RADIUS = 16
+BRUTE_RADIUS = 16
 
 
 def _chunk(args):
@@ -134,12 +134,12 @@ def main():
     t.destroy()
     del A, B, F
 
-    # Judge: brute-force SSD-argmin flow and the zero flow on the same held-out pairs.
+    # Yardsticks: brute-force SSD-argmin flow and the zero flow on the same held-out pairs.
     bf, zero = [], []
     for a, b, f in held:
         for i in range(a.shape[0]):
-            kk = tr.bruteforce_flow(a[i].contiguous(), b[i].contiguous(), JUDGE_RADIUS)
-            bf.append((tr.index_to_flow(kk, JUDGE_RADIUS) - f[i]).square().sum(0).sqrt().mean().item())
+            kk = tr.bruteforce_flow(a[i].contiguous(), b[i].contiguous(), BRUTE_RADIUS)
+            bf.append((tr.index_to_flow(kk, BRUTE_RADIUS) - f[i]).square().sum(0).sqrt().mean().item())
             zero.append(f[i].square().sum(0).sqrt().mean().item())
 
     line = {

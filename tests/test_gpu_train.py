@@ -316,8 +316,8 @@ def test_bruteforce_flow_matches_oracle_exactly():
         assert np.array_equal(got, want), (c, h, w, r)
 
 
-def test_trained_network_beats_brute_force_judge():
-    """The judge: on held-out pairs the network's EPE before and after training is set
+def test_trained_network_against_brute_force_flow():
+    """The yardsticks: on held-out pairs the network's EPE before and after training is set
     beside the brute-force integer flow's (radius 16, which covers the |F| <= 16 px of these
     128x128 pairs) and the zero flow's.  Training on 512 pairs must lower the held-out EPE
     and beat the zero flow."""
